@@ -1,0 +1,238 @@
+"""Plain FP64 CPU oracle for the se_e2_a energy / force / virial path (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference legs of bench.py.  The product path never imports it.
+
+The C++ source (dp_oracle.cpp) restates the DeePMD-kit v2 paper (arXiv 2304.09409)
+directly; see its header for the equation-by-equation map.  This wrapper only marshals
+numpy arrays.  Model configurations are duck-typed: any object with attributes
+ntypes, sel, rcut, rcut_smth, embed, axis, fit, type_one_side.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dp_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libdporacle.so")
+
+# Quintic table layout used by the paper's workloads: s in [0, 2]; stride 0.01 on the
+# first 90 % of the range (180 intervals) and 0.1 on the last 10 % (2 intervals).
+TABLE_S0 = 0.0
+TABLE_STRIDE1 = 0.01
+TABLE_N1 = 180
+TABLE_STRIDE2 = 0.1
+TABLE_N2 = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no fused multiply-add contraction, OpenMP over atoms)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [
+        ("ntypes", ctypes.c_int),
+        ("sel", ctypes.c_int * 8),
+        ("rcut", ctypes.c_double),
+        ("rcut_smth", ctypes.c_double),
+        ("n_embed", ctypes.c_int),
+        ("embed", ctypes.c_int * 8),
+        ("axis", ctypes.c_int),
+        ("n_fit", ctypes.c_int),
+        ("fit", ctypes.c_int * 8),
+        ("type_one_side", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        cp = ctypes.POINTER(_Cfg)
+        _lib.orc_n_params.argtypes = [cp]
+        _lib.orc_n_params.restype = ctypes.c_long
+        _lib.orc_switch.argtypes = [ctypes.c_double] * 3 + [dp, dp]
+        _lib.orc_quintic.argtypes = [ctypes.c_double] * 7 + [dp]
+        _lib.orc_nlist.argtypes = [cp, ctypes.c_int, dp, ip, dp, ip, ip, ip]
+        _lib.orc_nlist.restype = ctypes.c_int
+        _lib.orc_embed_jets.argtypes = [cp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        _lib.orc_table_build.argtypes = [cp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, dp]
+        _lib.orc_compute.argtypes = [cp, dp, ctypes.c_int, dp, ip, dp, ip, ip, dp, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
+        _lib.orc_compute.restype = ctypes.c_int
+        _lib.orc_energy_dual.argtypes = [cp, dp, ctypes.c_int, dp, dp, ip, dp, dp, ip, ip, dp, dp]
+        _lib.orc_energy_dual.restype = ctypes.c_double
+        _lib.orc_energy_plain.argtypes = [cp, dp, ctypes.c_int, dp, ip, dp, ip, ip]
+        _lib.orc_energy_plain.restype = ctypes.c_double
+    return _lib
+
+
+def _cfg(cfg) -> _Cfg:
+    c = _Cfg()
+    c.ntypes = int(cfg.ntypes)
+    for t, v in enumerate(cfg.sel):
+        c.sel[t] = int(v)
+    c.rcut = float(cfg.rcut)
+    c.rcut_smth = float(cfg.rcut_smth)
+    c.n_embed = len(cfg.embed)
+    for k, v in enumerate(cfg.embed):
+        c.embed[k] = int(v)
+    c.axis = int(cfg.axis)
+    c.n_fit = len(cfg.fit)
+    for k, v in enumerate(cfg.fit):
+        c.fit[k] = int(v)
+    c.type_one_side = int(getattr(cfg, "type_one_side", 0))
+    return c
+
+
+def _d(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def n_params(cfg) -> int:
+    c = _cfg(cfg)
+    return int(_L().orc_n_params(ctypes.byref(c)))
+
+
+def switch(r: float, rs: float, rc: float):
+    """Eq. (switch): returns (s(r), ds/dr)."""
+    s = ctypes.c_double()
+    ds = ctypes.c_double()
+    _L().orc_switch(r, rs, rc, ctypes.byref(s), ctypes.byref(ds))
+    return s.value, ds.value
+
+
+def quintic(y0, y1, d0, d1, dd0, dd1, dx) -> np.ndarray:
+    """Eq. (compress): coefficients (a, b, c, d, e, f) of one interval."""
+    out = np.zeros(6)
+    _L().orc_quintic(y0, y1, d0, d1, dd0, dd1, dx, _d(out))
+    return out
+
+
+def nlist(cfg, coord, atype, box):
+    """Brute-force neighbour list.  Returns (nl_j [N, Nc] int32, nl_shift [N, Nc, 3] int32,
+    counts [N, ntypes] int32, n_overflow)."""
+    coord = _f64(coord)
+    atype = _i32(atype)
+    box = _f64(box)
+    N = coord.shape[0]
+    nc = int(sum(cfg.sel))
+    nl_j = np.zeros((N, nc), dtype=np.int32)
+    nl_s = np.zeros((N, nc, 3), dtype=np.int32)
+    counts = np.zeros((N, cfg.ntypes), dtype=np.int32)
+    c = _cfg(cfg)
+    ov = _L().orc_nlist(ctypes.byref(c), N, _d(coord), _i(atype), _d(box), _i(nl_j), _i(nl_s), _i(counts))
+    return nl_j, nl_s, counts, ov
+
+
+def embed_jets(cfg, params, net: int, xs):
+    """Embedding-net outputs y and derivatives y', y'' (w.r.t. the scalar input) at xs."""
+    xs = _f64(np.atleast_1d(xs))
+    M = int(cfg.embed[-1])
+    y = np.zeros((xs.size, M))
+    y1 = np.zeros_like(y)
+    y2 = np.zeros_like(y)
+    c = _cfg(cfg)
+    _L().orc_embed_jets(ctypes.byref(c), _d(_f64(params)), net, xs.size, _d(xs), _d(y), _d(y1), _d(y2))
+    return y, y1, y2
+
+
+def table_build(cfg, params, s0=TABLE_S0, stride1=TABLE_STRIDE1, n1=TABLE_N1, stride2=TABLE_STRIDE2, n2=TABLE_N2):
+    """Eq. (compress) tables for every embedding net: [nets, n1+n2, M, 6] (a..f)."""
+    nets = cfg.ntypes if getattr(cfg, "type_one_side", 0) else cfg.ntypes ** 2
+    M = int(cfg.embed[-1])
+    tab = np.zeros((nets, n1 + n2, M, 6))
+    c = _cfg(cfg)
+    _L().orc_table_build(ctypes.byref(c), _d(_f64(params)), s0, stride1, n1, stride2, n2, _d(tab))
+    return tab
+
+
+class Result:
+    def __init__(self, energy, force, virial, atom_energy, status):
+        self.energy = energy
+        self.force = force
+        self.virial = virial
+        self.atom_energy = atom_energy
+        self.status = status
+
+
+def compute(cfg, params, coord, atype, box, nl=None, table=None, table_layout=None, nthreads: int = 0) -> Result:
+    """E, F [N,3], virial [3,3], per-atom E.  nl = (nl_j, nl_shift) or None (brute force).
+    table = quintic table from `table_build` (compressed embedding) or None (network)."""
+    coord = _f64(coord)
+    atype = _i32(atype)
+    box = _f64(box)
+    params = _f64(params)
+    N = coord.shape[0]
+    force = np.zeros((N, 3))
+    virial = np.zeros((3, 3))
+    ae = np.zeros(N)
+    e = ctypes.c_double()
+    nl_j = nl_s = None
+    if nl is not None:
+        nl_j = _i32(nl[0])
+        nl_s = _i32(nl[1])
+    tab = _f64(table)
+    lay = table_layout or (TABLE_S0, TABLE_STRIDE1, TABLE_N1, TABLE_STRIDE2, TABLE_N2)
+    c = _cfg(cfg)
+    st = _L().orc_compute(ctypes.byref(c), _d(params), N, _d(coord), _i(atype), _d(box), _i(nl_j), _i(nl_s), _d(tab),
+                          lay[0], lay[1], lay[2], lay[3], lay[4], ctypes.byref(e), _d(force), _d(virial), _d(ae),
+                          int(nthreads))
+    return Result(e.value, force, virial, ae, st)
+
+
+def energy_dual(cfg, params, coord, atype, box, nl, dcoord=None, dbox=None):
+    """Forward-mode dual-number derivative of E along (dcoord, dbox), nlist held fixed.
+    Returns (E, dE)."""
+    coord = _f64(coord)
+    N = coord.shape[0]
+    dE = ctypes.c_double()
+    c = _cfg(cfg)
+    E = _L().orc_energy_dual(ctypes.byref(c), _d(_f64(params)), N, _d(coord), _d(_f64(dcoord)), _i(_i32(atype)),
+                             _d(_f64(box)), _d(_f64(dbox)), _i(_i32(nl[0])), _i(_i32(nl[1])), ctypes.byref(dE), None)
+    return E, dE.value
+
+
+def energy_plain(cfg, params, coord, atype, box, nl) -> float:
+    """E through the generic (templated) forward in plain doubles."""
+    coord = _f64(coord)
+    c = _cfg(cfg)
+    return _L().orc_energy_plain(ctypes.byref(c), _d(_f64(params)), coord.shape[0], _d(coord), _i(_i32(atype)),
+                                 _d(_f64(box)), _i(_i32(nl[0])), _i(_i32(nl[1])))

@@ -1,0 +1,763 @@
+// Plain FP64 CPU oracle for the se_e2_a Deep Potential energy / force / virial path.
+//
+// TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
+// cpu_baseline leg (and its --impl reference arm) load this library.  The product path
+// (the CUDA library behind include/dpgb.h) never links, calls or reads anything here,
+// and nothing here is shared with it.
+//
+// Everything is written straight from the DeePMD-kit v2 paper (arXiv 2304.09409):
+//   Eq. (model)      y_i = F(D(x_i, {x_j})),  E = sum_i E_i                 Sec. II.A
+//   Eq. (rij)        R_j = (s, s x/r, s y/r, s z/r),  r_ij = r_j - r_i     Sec. II.A.1
+//   Eq. (switch)     s(r)                                                  Sec. II.A.1
+//   Eq. (G2)         G_j = N_{e,2}^{a_i,a_j}(s(r_ij))                      Sec. II.A.1
+//   descriptor       D = (1/Nc^2) G^T R R^T G_<                            Sec. II.A.1
+//   Eq. (fitting)    E_i = F_0^{a_i}(D^i)                                  Sec. II.A.2
+//   force / virial   F = -dE/dr,  Xi = -sum_g dE/dh_{g a} h_{g b}           Sec. II.A.2
+//   Eq. (NN)         layer y = phi(x w + b) (+ x | + {x,x})                Sec. II.A.6
+//   Eq. (compress)   quintic tabulation of the embedding net               Sec. II.A.6
+//   neighbour order  by (type, distance, index)                            Sec. III.B.1
+//
+// Readings of the paper used here (each listed in the design notes):
+//   * Nc in 1/Nc^2 is the padded sum of sel; padded rows of R are zero.
+//   * The virial is dE/dh at fixed fractional coordinates, which equals
+//     Xi_ab = -sum_{pairs} (dE/d r_ij)_a (r_ij)_b.
+//   * Neighbour order is the exact total order (type, r^2 as IEEE bits, j, image shift);
+//     a pair displacement is (x_j + t) - x_i with t = n0 h0 + n1 h1 + n2 h2 evaluated
+//     left to right without fused multiply-add (build flag -ffp-contract=off).
+//   * ResNet timestep w_hat = 1; the last fitting layer (width 1) is linear.
+//   * Quintic pieces are evaluated at t = x - x_l (the offset inside the interval).
+//
+// Forces come from a hand-written reverse pass in plain loops.  A second, independent
+// mechanism -- forward-mode dual numbers through a templated energy -- exists only to
+// pin that reverse pass (orc_energy_dual).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+extern "C" {
+
+struct OrcConfig {
+  int ntypes;
+  int sel[8];
+  double rcut;
+  double rcut_smth;
+  int n_embed;
+  int embed[8];
+  int axis;
+  int n_fit;
+  int fit[8];
+  int type_one_side;
+};
+
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Scalar types: double, first-order dual, and second-order jet (value, d1, d2) used for the
+// table nodes (y, y', y'') and for pins.
+// ------------------------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual(double a = 0.0, double b = 0.0) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+inline bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+inline Dual dsqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+inline Dual dtanh(Dual a) { double t = std::tanh(a.v); return Dual(t, (1.0 - t * t) * a.d); }
+inline double val(Dual a) { return a.v; }
+
+inline double dsqrt(double a) { return std::sqrt(a); }
+inline double dtanh(double a) { return std::tanh(a); }
+inline double val(double a) { return a; }
+
+struct Jet {  // f, f', f'' along one input direction
+  double v, d1, d2;
+  Jet(double a = 0.0, double b = 0.0, double c = 0.0) : v(a), d1(b), d2(c) {}
+};
+inline Jet operator+(Jet a, Jet b) { return Jet(a.v + b.v, a.d1 + b.d1, a.d2 + b.d2); }
+inline Jet operator*(Jet a, double w) { return Jet(a.v * w, a.d1 * w, a.d2 * w); }
+inline Jet jtanh(Jet a) {
+  double t = std::tanh(a.v), g = 1.0 - t * t;
+  return Jet(t, g * a.d1, g * a.d2 - 2.0 * t * g * a.d1 * a.d1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Parameter layout helpers (flat FP64 array, see the inputs module)
+// ------------------------------------------------------------------------------------------
+struct Layout {
+  int ntypes, nc, m, axis, n_embed_nets;
+  std::vector<int> ein, eout;   // embedding layer shapes
+  std::vector<int> fin, fout;   // fitting layer shapes (last has fout = 1)
+  std::vector<long> eoff;       // per embedding net, per layer: offset of W (b follows W)
+  std::vector<long> foff;       // per fitting net, per layer
+  int sel_off[9];
+  long n_params;
+};
+
+Layout make_layout(const OrcConfig& c) {
+  Layout L;
+  L.ntypes = c.ntypes;
+  L.nc = 0;
+  for (int t = 0; t < c.ntypes; ++t) { L.sel_off[t] = L.nc; L.nc += c.sel[t]; }
+  L.sel_off[c.ntypes] = L.nc;
+  L.m = c.embed[c.n_embed - 1];
+  L.axis = c.axis;
+  L.n_embed_nets = c.type_one_side ? c.ntypes : c.ntypes * c.ntypes;
+  int prev = 1;
+  for (int l = 0; l < c.n_embed; ++l) { L.ein.push_back(prev); L.eout.push_back(c.embed[l]); prev = c.embed[l]; }
+  prev = L.m * c.axis;
+  for (int l = 0; l < c.n_fit; ++l) { L.fin.push_back(prev); L.fout.push_back(c.fit[l]); prev = c.fit[l]; }
+  L.fin.push_back(prev); L.fout.push_back(1);
+  long off = 0;
+  for (int n = 0; n < L.n_embed_nets; ++n)
+    for (size_t l = 0; l < L.ein.size(); ++l) { L.eoff.push_back(off); off += (long)L.ein[l] * L.eout[l] + L.eout[l]; }
+  for (int n = 0; n < c.ntypes; ++n)
+    for (size_t l = 0; l < L.fin.size(); ++l) { L.foff.push_back(off); off += (long)L.fin[l] * L.fout[l] + L.fout[l]; }
+  L.n_params = off;
+  return L;
+}
+
+inline int embed_net_index(const OrcConfig& c, int ai, int aj) {
+  return c.type_one_side ? aj : ai * c.ntypes + aj;
+}
+
+// Eq. (NN): the skip term of a layer with n_in inputs and n_out outputs (ResNet on).
+//   n_out == n_in   : + x
+//   n_out == 2 n_in : + {x, x}
+//   otherwise       : none
+inline int skip_kind(int n_in, int n_out) { return n_out == n_in ? 1 : (n_out == 2 * n_in ? 2 : 0); }
+
+// ------------------------------------------------------------------------------------------
+// Eq. (switch) and its derivative ds/dr
+// ------------------------------------------------------------------------------------------
+template <class T>
+T switch_fn(T r, double rs, double rc) {
+  if (val(r) < rs) return T(1.0) / r;
+  if (val(r) >= rc) return T(0.0);
+  T x = (r - T(rs)) / T(rc - rs);
+  T poly = x * x * x * (T(-6.0) * x * x + T(15.0) * x - T(10.0)) + T(1.0);
+  return poly / r;
+}
+
+double switch_deriv(double r, double rs, double rc) {
+  if (r < rs) return -1.0 / (r * r);
+  if (r >= rc) return 0.0;
+  double x = (r - rs) / (rc - rs);
+  double u = x * x * x * (-6.0 * x * x + 15.0 * x - 10.0) + 1.0;
+  double du = -30.0 * x * x * (x - 1.0) * (x - 1.0) / (rc - rs);
+  return -u / (r * r) + du / r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Dense layer, Eq. (NN), generic scalar
+// ------------------------------------------------------------------------------------------
+template <class T>
+void layer_forward(const double* W, const double* b, int n_in, int n_out, const T* x, T* y, bool tanh_act,
+                   bool resnet) {
+  int sk = resnet ? skip_kind(n_in, n_out) : 0;
+  for (int o = 0; o < n_out; ++o) {
+    T z = T(b[o]);
+    for (int i = 0; i < n_in; ++i) z = z + x[i] * T(W[(long)i * n_out + o]);
+    T a = tanh_act ? dtanh(z) : z;
+    if (sk == 1) a = a + x[o];
+    if (sk == 2) a = a + x[o % n_in];
+    y[o] = a;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Neighbour list: brute force over all atoms and all periodic images (Sec. III.B.1 order)
+// ------------------------------------------------------------------------------------------
+struct Cand {
+  int type;
+  uint64_t r2bits;
+  int j;
+  int code;
+};
+inline bool cand_less(const Cand& a, const Cand& b) {
+  if (a.type != b.type) return a.type < b.type;
+  if (a.r2bits != b.r2bits) return a.r2bits < b.r2bits;
+  if (a.j != b.j) return a.j < b.j;
+  return (unsigned)a.code < (unsigned)b.code;
+}
+inline int pack_shift(int n0, int n1, int n2) { return ((n0 + 512) << 20) | ((n1 + 512) << 10) | (n2 + 512); }
+inline void unpack_shift(int code, int* n) {
+  n[0] = ((code >> 20) & 1023) - 512;
+  n[1] = ((code >> 10) & 1023) - 512;
+  n[2] = (code & 1023) - 512;
+}
+
+// Pair displacement (x_j + t) - x_i, t = n0 h0 + n1 h1 + n2 h2, left to right.
+inline void pair_disp(const double* xi, const double* xj, const int* n, const double* box, double* d) {
+  for (int a = 0; a < 3; ++a) {
+    double t = 0.0;
+    if (box) t = ((double)n[0] * box[0 * 3 + a] + (double)n[1] * box[1 * 3 + a]) + (double)n[2] * box[2 * 3 + a];
+    double p = xj[a] + t;
+    d[a] = p - xi[a];
+  }
+}
+inline double norm2(const double* d) { return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]; }
+
+void inverse3(const double* h, double* inv) {
+  double c00 = h[4] * h[8] - h[5] * h[7], c01 = h[5] * h[6] - h[3] * h[8], c02 = h[3] * h[7] - h[4] * h[6];
+  double det = h[0] * c00 + h[1] * c01 + h[2] * c02;
+  inv[0] = c00 / det; inv[1] = (h[2] * h[7] - h[1] * h[8]) / det; inv[2] = (h[1] * h[5] - h[2] * h[4]) / det;
+  inv[3] = c01 / det; inv[4] = (h[0] * h[8] - h[2] * h[6]) / det; inv[5] = (h[2] * h[3] - h[0] * h[5]) / det;
+  inv[6] = c02 / det; inv[7] = (h[1] * h[6] - h[0] * h[7]) / det; inv[8] = (h[0] * h[4] - h[1] * h[3]) / det;
+}
+
+// Returns the number of (atom, type) blocks whose candidate count exceeded sel.
+int build_nlist(const OrcConfig& c, const Layout& L, int N, const double* coord, const int* type, const double* box,
+                int* nl_j, int* nl_code, int* counts /*[N*ntypes] or null*/) {
+  const double rc2 = c.rcut * c.rcut;
+  std::vector<int> lo(3 * N, 0), hi(3 * N, 0);
+  int K[3] = {0, 0, 0};
+  std::vector<long> m(3 * (size_t)N, 0);
+  if (box) {
+    double inv[9];
+    inverse3(box, inv);
+    double vol = std::fabs(box[0] * (box[4] * box[8] - box[5] * box[7]) - box[1] * (box[3] * box[8] - box[5] * box[6]) +
+                           box[2] * (box[3] * box[7] - box[4] * box[6]));
+    for (int d = 0; d < 3; ++d) {
+      const double* u = box + 3 * ((d + 1) % 3);
+      const double* v = box + 3 * ((d + 2) % 3);
+      double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+      double width = vol / std::sqrt(cx * cx + cy * cy + cz * cz);
+      K[d] = (int)std::ceil(c.rcut / width) + 1;
+    }
+    for (int i = 0; i < N; ++i)
+      for (int d = 0; d < 3; ++d) {
+        double f = coord[3 * i + 0] * inv[0 * 3 + d] + coord[3 * i + 1] * inv[1 * 3 + d] + coord[3 * i + 2] * inv[2 * 3 + d];
+        m[3 * i + d] = (long)std::floor(f);
+      }
+  }
+  int overflow = 0;
+  std::vector<Cand> cand;
+  for (int i = 0; i < N; ++i) {
+    cand.clear();
+    for (int j = 0; j < N; ++j) {
+      int base[3] = {0, 0, 0};
+      if (box)
+        for (int d = 0; d < 3; ++d) base[d] = (int)(m[3 * i + d] - m[3 * j + d]);
+      int n[3];
+      for (n[0] = base[0] - K[0]; n[0] <= base[0] + K[0]; ++n[0])
+        for (n[1] = base[1] - K[1]; n[1] <= base[1] + K[1]; ++n[1])
+          for (n[2] = base[2] - K[2]; n[2] <= base[2] + K[2]; ++n[2]) {
+            if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+            double d[3];
+            pair_disp(coord + 3 * i, coord + 3 * j, n, box, d);
+            double r2 = norm2(d);
+            if (r2 < rc2) {
+              Cand e;
+              e.type = type[j];
+              std::memcpy(&e.r2bits, &r2, 8);
+              e.j = j;
+              e.code = pack_shift(n[0], n[1], n[2]);
+              cand.push_back(e);
+            }
+          }
+    }
+    std::sort(cand.begin(), cand.end(), cand_less);
+    for (int k = 0; k < L.nc; ++k) { nl_j[(long)i * L.nc + k] = -1; nl_code[(long)i * L.nc + k] = pack_shift(0, 0, 0); }
+    std::vector<int> cnt(c.ntypes, 0);
+    for (const Cand& e : cand) {
+      int t = e.type;
+      if (cnt[t] < c.sel[t]) {
+        long slot = (long)i * L.nc + L.sel_off[t] + cnt[t];
+        nl_j[slot] = e.j;
+        nl_code[slot] = e.code;
+      }
+      cnt[t]++;
+    }
+    for (int t = 0; t < c.ntypes; ++t) {
+      if (cnt[t] > c.sel[t]) overflow++;
+      if (counts) counts[(long)i * c.ntypes + t] = cnt[t];
+    }
+  }
+  return overflow;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-atom forward + reverse pass (FP64).  Embedding either by the network (Eq. G2) or by
+// the quintic table (Eq. compress).
+// ------------------------------------------------------------------------------------------
+struct Table {
+  const double* coef;  // [nets][L_c][M][6] : a b c d e f
+  double s0, stride1, stride2;
+  int n1, n2;
+  int lc() const { return n1 + n2; }
+  double node(int l) const { return l <= n1 ? s0 + l * stride1 : s0 + n1 * stride1 + (l - n1) * stride2; }
+  int interval(double s, int* out_of_range) const {
+    double split = s0 + n1 * stride1;
+    int l;
+    if (s < s0) { l = 0; *out_of_range = 1; }
+    else if (s < split) { l = (int)std::floor((s - s0) / stride1); if (l > n1 - 1) l = n1 - 1; }
+    else {
+      l = n1 + (int)std::floor((s - split) / stride2);
+      if (l > n1 + n2 - 1) { l = n1 + n2 - 1; }
+      if (s > node(n1 + n2)) *out_of_range = 1;
+    }
+    return l;
+  }
+};
+
+struct AtomOut {
+  double e;
+  int range_err;
+};
+
+// Embedding forward for one scalar input: returns G (M) and stores tanh outputs per layer.
+void embed_forward(const OrcConfig& c, const Layout& L, const double* params, int net, double s,
+                   std::vector<std::vector<double>>& act, std::vector<std::vector<double>>& outs) {
+  std::vector<double> x(1, s);
+  for (int l = 0; l < c.n_embed; ++l) {
+    const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
+    const double* b = W + (long)L.ein[l] * L.eout[l];
+    int ni = L.ein[l], no = L.eout[l];
+    act[l].assign(no, 0.0);
+    outs[l].assign(no, 0.0);
+    int sk = skip_kind(ni, no);
+    for (int o = 0; o < no; ++o) {
+      double z = b[o];
+      for (int i = 0; i < ni; ++i) z += x[i] * W[(long)i * no + o];
+      double t = std::tanh(z);
+      act[l][o] = t;
+      outs[l][o] = t + (sk == 1 ? x[o] : (sk == 2 ? x[o % ni] : 0.0));
+    }
+    x = outs[l];
+  }
+}
+
+// Reverse pass of the embedding net: given dE/dG (M), returns dE/ds.
+double embed_backward(const OrcConfig& c, const Layout& L, const double* params, int net, double s,
+                      const std::vector<std::vector<double>>& act, const std::vector<std::vector<double>>& outs,
+                      std::vector<double> gy) {
+  for (int l = c.n_embed - 1; l >= 0; --l) {
+    const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
+    int ni = L.ein[l], no = L.eout[l];
+    int sk = skip_kind(ni, no);
+    std::vector<double> gx(ni, 0.0);
+    for (int o = 0; o < no; ++o) {
+      double gz = gy[o] * (1.0 - act[l][o] * act[l][o]);
+      for (int i = 0; i < ni; ++i) gx[i] += gz * W[(long)i * no + o];
+      if (sk == 1) gx[o] += gy[o];
+      if (sk == 2) gx[o % ni] += gy[o];
+    }
+    gy = gx;
+  }
+  (void)s;
+  return gy[0];
+}
+
+void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const Table* tab, int i, const double* coord,
+               const int* type, const double* box, const int* nl_j, const int* nl_code, double* gd /*[Nc*3]*/,
+               AtomOut* out) {
+  const int nc = L.nc, M = L.m, A = L.axis;
+  const int ai = type[i];
+  const double rs = c.rcut_smth, rc = c.rcut;
+  std::vector<double> R((size_t)nc * 4, 0.0), dvec((size_t)nc * 3, 0.0), rr(nc, 0.0), ss(nc, 0.0);
+  std::vector<int> valid(nc, 0), netk(nc, 0);
+  std::vector<double> G((size_t)nc * M, 0.0), dG((size_t)nc * M, 0.0);
+  std::vector<std::vector<std::vector<double>>> act(nc), outs(nc);
+  out->range_err = 0;
+  // Eq. (rij) with Eq. (switch)
+  for (int t = 0; t < c.ntypes; ++t)
+    for (int q = 0; q < c.sel[t]; ++q) {
+      int k = L.sel_off[t] + q;
+      int j = nl_j[(long)i * nc + k];
+      netk[k] = embed_net_index(c, ai, t);
+      if (j < 0) continue;
+      int n[3];
+      unpack_shift(nl_code[(long)i * nc + k], n);
+      double d[3];
+      pair_disp(coord + 3 * i, coord + 3 * j, n, box, d);
+      double r = std::sqrt(norm2(d));
+      double s = switch_fn(r, rs, rc);
+      valid[k] = 1;
+      rr[k] = r;
+      ss[k] = s;
+      for (int a = 0; a < 3; ++a) dvec[(size_t)k * 3 + a] = d[a];
+      R[(size_t)k * 4 + 0] = s;
+      for (int a = 0; a < 3; ++a) R[(size_t)k * 4 + 1 + a] = s * d[a] / r;
+    }
+  // Eq. (G2): embedding rows of real neighbours (padded rows of R are zero and contribute nothing)
+  for (int k = 0; k < nc; ++k) {
+    if (!valid[k]) continue;
+    if (!tab) {
+      act[k].resize(c.n_embed);
+      outs[k].resize(c.n_embed);
+      embed_forward(c, L, params, netk[k], ss[k], act[k], outs[k]);
+      for (int mm = 0; mm < M; ++mm) G[(size_t)k * M + mm] = outs[k][c.n_embed - 1][mm];
+    } else {
+      // Eq. (compress): g(t) with t = s - x_l inside interval l
+      int oor = 0;
+      int l = tab->interval(ss[k], &oor);
+      if (oor) out->range_err = 1;
+      double t = ss[k] - tab->node(l);
+      const double* co = tab->coef + (((size_t)netk[k] * tab->lc() + l) * M) * 6;
+      for (int mm = 0; mm < M; ++mm) {
+        const double* p = co + (size_t)mm * 6;
+        double g = ((((p[0] * t + p[1]) * t + p[2]) * t + p[3]) * t + p[4]) * t + p[5];
+        double gp = (((5.0 * p[0] * t + 4.0 * p[1]) * t + 3.0 * p[2]) * t + 2.0 * p[3]) * t + p[4];
+        G[(size_t)k * M + mm] = g;
+        dG[(size_t)k * M + mm] = gp;
+      }
+    }
+  }
+  // T = (1/Nc) G^T R   (M x 4)
+  std::vector<double> T((size_t)M * 4, 0.0);
+  for (int mm = 0; mm < M; ++mm)
+    for (int q = 0; q < 4; ++q) {
+      double acc = 0.0;
+      for (int k = 0; k < nc; ++k) acc += G[(size_t)k * M + mm] * R[(size_t)k * 4 + q];
+      T[(size_t)mm * 4 + q] = acc / nc;
+    }
+  // D = T T_<^T  (M x M_<), flattened row-major
+  std::vector<double> D((size_t)M * A, 0.0);
+  for (int mm = 0; mm < M; ++mm)
+    for (int l = 0; l < A; ++l) {
+      double acc = 0.0;
+      for (int q = 0; q < 4; ++q) acc += T[(size_t)mm * 4 + q] * T[(size_t)l * 4 + q];
+      D[(size_t)mm * A + l] = acc;
+    }
+  // Eq. (fitting): E_i = F_0^{a_i}(D)
+  const int nfl = (int)L.fin.size();
+  std::vector<std::vector<double>> fx(nfl + 1), fa(nfl);
+  fx[0] = D;
+  for (int l = 0; l < nfl; ++l) {
+    const double* W = params + L.foff[(size_t)ai * nfl + l];
+    const double* b = W + (long)L.fin[l] * L.fout[l];
+    int ni = L.fin[l], no = L.fout[l];
+    bool last = (l == nfl - 1);
+    int sk = last ? 0 : skip_kind(ni, no);
+    fx[l + 1].assign(no, 0.0);
+    fa[l].assign(no, 0.0);
+    for (int o = 0; o < no; ++o) {
+      double z = b[o];
+      for (int q = 0; q < ni; ++q) z += fx[l][q] * W[(long)q * no + o];
+      double t = last ? z : std::tanh(z);
+      fa[l][o] = t;
+      fx[l + 1][o] = t + (sk == 1 ? fx[l][o] : (sk == 2 ? fx[l][o % ni] : 0.0));
+    }
+  }
+  out->e = fx[nfl][0];
+  // ---------------- reverse pass ----------------
+  std::vector<double> gy(1, 1.0);
+  for (int l = nfl - 1; l >= 0; --l) {
+    const double* W = params + L.foff[(size_t)ai * nfl + l];
+    int ni = L.fin[l], no = L.fout[l];
+    bool last = (l == nfl - 1);
+    int sk = last ? 0 : skip_kind(ni, no);
+    std::vector<double> gx(ni, 0.0);
+    for (int o = 0; o < no; ++o) {
+      double gz = last ? gy[o] : gy[o] * (1.0 - fa[l][o] * fa[l][o]);
+      for (int q = 0; q < ni; ++q) gx[q] += gz * W[(long)q * no + o];
+      if (sk == 1) gx[o] += gy[o];
+      if (sk == 2) gx[o % ni] += gy[o];
+    }
+    gy = gx;
+  }
+  const std::vector<double>& gD = gy;  // dE_i/dD, M x M_<
+  // dE/dT[p][q] = sum_l gD[p][l] T[l][q] + [p < M_<] sum_m gD[m][p] T[m][q]
+  std::vector<double> gT((size_t)M * 4, 0.0);
+  for (int p = 0; p < M; ++p)
+    for (int q = 0; q < 4; ++q) {
+      double acc = 0.0;
+      for (int l = 0; l < A; ++l) acc += gD[(size_t)p * A + l] * T[(size_t)l * 4 + q];
+      if (p < A)
+        for (int mm = 0; mm < M; ++mm) acc += gD[(size_t)mm * A + p] * T[(size_t)mm * 4 + q];
+      gT[(size_t)p * 4 + q] = acc;
+    }
+  for (int k = 0; k < nc * 3; ++k) gd[k] = 0.0;
+  for (int k = 0; k < nc; ++k) {
+    if (!valid[k]) continue;
+    // dE/dR_k[q] = (1/Nc) sum_m gT[m][q] G_k[m];  dE/dG_k[m] = (1/Nc) sum_q gT[m][q] R_k[q]
+    double gR[4];
+    for (int q = 0; q < 4; ++q) {
+      double acc = 0.0;
+      for (int mm = 0; mm < M; ++mm) acc += gT[(size_t)mm * 4 + q] * G[(size_t)k * M + mm];
+      gR[q] = acc / nc;
+    }
+    std::vector<double> gG(M);
+    for (int mm = 0; mm < M; ++mm) {
+      double acc = 0.0;
+      for (int q = 0; q < 4; ++q) acc += gT[(size_t)mm * 4 + q] * R[(size_t)k * 4 + q];
+      gG[mm] = acc / nc;
+    }
+    double gs_embed;
+    if (!tab) {
+      gs_embed = embed_backward(c, L, params, netk[k], ss[k], act[k], outs[k], gG);
+    } else {
+      gs_embed = 0.0;
+      for (int mm = 0; mm < M; ++mm) gs_embed += gG[mm] * dG[(size_t)k * M + mm];
+    }
+    // chain through R_k = (s, s u) with u = d / r, and s = s(r), r = |d|
+    double r = rr[k], s = ss[k];
+    double sp = switch_deriv(r, rs, rc);
+    const double* d = &dvec[(size_t)k * 3];
+    double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+    double gvu = gR[1] * u[0] + gR[2] * u[1] + gR[3] * u[2];
+    double gs = gs_embed + gR[0] + gvu;  // total dE/ds at fixed u
+    for (int a = 0; a < 3; ++a) gd[(size_t)k * 3 + a] = sp * gs * u[a] + (s / r) * (gR[1 + a] - gvu * u[a]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Templated energy (for the dual-number pins only): same definitions, generic scalar.
+// ------------------------------------------------------------------------------------------
+template <class T>
+T energy_generic(const OrcConfig& c, const Layout& L, const double* params, int N, const T* coord, const int* type,
+                 const T* box, const int* nl_j, const int* nl_code, T* atom_e) {
+  const int nc = L.nc, M = L.m, A = L.axis;
+  T E(0.0);
+  for (int i = 0; i < N; ++i) {
+    int ai = type[i];
+    std::vector<T> Tm((size_t)M * 4, T(0.0));
+    for (int t = 0; t < c.ntypes; ++t)
+      for (int q = 0; q < c.sel[t]; ++q) {
+        int k = L.sel_off[t] + q;
+        int j = nl_j[(long)i * nc + k];
+        if (j < 0) continue;
+        int n[3];
+        unpack_shift(nl_code[(long)i * nc + k], n);
+        T d[3];
+        for (int a = 0; a < 3; ++a) {
+          T tt(0.0);
+          if (box) tt = T((double)n[0]) * box[a] + T((double)n[1]) * box[3 + a] + T((double)n[2]) * box[6 + a];
+          d[a] = (coord[3 * j + a] + tt) - coord[3 * i + a];
+        }
+        T r = dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        T s = switch_fn(r, c.rcut_smth, c.rcut);
+        T Rk[4] = {s, s * d[0] / r, s * d[1] / r, s * d[2] / r};
+        int net = embed_net_index(c, ai, t);
+        std::vector<T> x(1, s), y;
+        for (int l = 0; l < c.n_embed; ++l) {
+          const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
+          y.assign(L.eout[l], T(0.0));
+          layer_forward(W, W + (long)L.ein[l] * L.eout[l], L.ein[l], L.eout[l], x.data(), y.data(), true, true);
+          x = y;
+        }
+        for (int mm = 0; mm < M; ++mm)
+          for (int q = 0; q < 4; ++q) Tm[(size_t)mm * 4 + q] = Tm[(size_t)mm * 4 + q] + x[mm] * Rk[q];
+      }
+    for (auto& v : Tm) v = v / T((double)nc);
+    std::vector<T> x((size_t)M * A);
+    for (int mm = 0; mm < M; ++mm)
+      for (int l = 0; l < A; ++l) {
+        T acc(0.0);
+        for (int q = 0; q < 4; ++q) acc = acc + Tm[(size_t)mm * 4 + q] * Tm[(size_t)l * 4 + q];
+        x[(size_t)mm * A + l] = acc;
+      }
+    const int nfl = (int)L.fin.size();
+    for (int l = 0; l < nfl; ++l) {
+      const double* W = params + L.foff[(size_t)ai * nfl + l];
+      std::vector<T> y(L.fout[l]);
+      bool last = l == nfl - 1;
+      layer_forward(W, W + (long)L.fin[l] * L.fout[l], L.fin[l], L.fout[l], x.data(), y.data(), !last, !last);
+      x = y;
+    }
+    if (atom_e) atom_e[i] = x[0];
+    E = E + x[0];
+  }
+  return E;
+}
+
+// Node values y, y', y'' of every output of embedding net `net` at input s (second-order jets).
+void embed_jets(const OrcConfig& c, const Layout& L, const double* params, int net, double s, double* y, double* y1,
+                double* y2) {
+  std::vector<Jet> x(1, Jet(s, 1.0, 0.0));
+  for (int l = 0; l < c.n_embed; ++l) {
+    const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
+    const double* b = W + (long)L.ein[l] * L.eout[l];
+    int ni = L.ein[l], no = L.eout[l];
+    int sk = skip_kind(ni, no);
+    std::vector<Jet> yv(no);
+    for (int o = 0; o < no; ++o) {
+      Jet z(b[o], 0.0, 0.0);
+      for (int i = 0; i < ni; ++i) z = z + x[i] * W[(long)i * no + o];
+      Jet a = jtanh(z);
+      if (sk == 1) a = a + x[o];
+      if (sk == 2) a = a + x[o % ni];
+      yv[o] = a;
+    }
+    x = yv;
+  }
+  for (int mm = 0; mm < L.m; ++mm) { y[mm] = x[mm].v; y1[mm] = x[mm].d1; y2[mm] = x[mm].d2; }
+}
+
+// Eq. (compress): quintic coefficients (a..f) on an interval of width dx from the values,
+// first and second derivatives at its two ends.
+void quintic(double y0, double y1, double d0, double d1, double dd0, double dd1, double dx, double* out) {
+  double h = y1 - y0;
+  double dx2 = dx * dx, dx3 = dx2 * dx, dx4 = dx3 * dx, dx5 = dx4 * dx;
+  out[0] = (12.0 * h - 6.0 * (d1 + d0) * dx + (dd1 - dd0) * dx2) / (2.0 * dx5);
+  out[1] = (-30.0 * h + (14.0 * d1 + 16.0 * d0) * dx + (-2.0 * dd1 + 3.0 * dd0) * dx2) / (2.0 * dx4);
+  out[2] = (20.0 * h - (8.0 * d1 + 12.0 * d0) * dx + (dd1 - 3.0 * dd0) * dx2) / (2.0 * dx3);
+  out[3] = 0.5 * dd0;
+  out[4] = d0;
+  out[5] = y0;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C entry points (ctypes)
+// ==========================================================================================
+extern "C" {
+
+long orc_n_params(const OrcConfig* c) { return make_layout(*c).n_params; }
+
+void orc_switch(double r, double rs, double rc, double* s, double* ds) {
+  *s = switch_fn(r, rs, rc);
+  *ds = switch_deriv(r, rs, rc);
+}
+
+void orc_quintic(double y0, double y1, double d0, double d1, double dd0, double dd1, double dx, double* out) {
+  quintic(y0, y1, d0, d1, dd0, dd1, dx, out);
+}
+
+// Brute-force neighbour list.  nl_shift is [N*Nc*3] image integers (0 for padding).
+int orc_nlist(const OrcConfig* c, int N, const double* coord, const int* type, const double* box, int* nl_j,
+              int* nl_shift, int* counts) {
+  Layout L = make_layout(*c);
+  std::vector<int> code((size_t)N * L.nc);
+  int ov = build_nlist(*c, L, N, coord, type, box, nl_j, code.data(), counts);
+  for (size_t k = 0; k < code.size(); ++k) unpack_shift(code[k], nl_shift + 3 * k);
+  return ov;
+}
+
+// Embedding-net outputs and their first/second derivatives at inputs xs[n] for net `net`.
+void orc_embed_jets(const OrcConfig* c, const double* params, int net, int n, const double* xs, double* y,
+                    double* y1, double* y2) {
+  Layout L = make_layout(*c);
+  for (int q = 0; q < n; ++q)
+    embed_jets(*c, L, params, net, xs[q], y + (size_t)q * L.m, y1 + (size_t)q * L.m, y2 + (size_t)q * L.m);
+}
+
+// Quintic table over nodes x_0 .. x_{n1+n2}: first n1 intervals of width stride1 from s0,
+// then n2 intervals of width stride2.  table: [nets][n1+n2][M][6].
+void orc_table_build(const OrcConfig* c, const double* params, double s0, double stride1, int n1, double stride2,
+                     int n2, double* table) {
+  Layout L = make_layout(*c);
+  Table tb{nullptr, s0, stride1, stride2, n1, n2};
+  int lc = n1 + n2, M = L.m;
+  std::vector<double> y((size_t)(lc + 1) * M), y1(y.size()), y2(y.size());
+  for (int net = 0; net < L.n_embed_nets; ++net) {
+    for (int l = 0; l <= lc; ++l)
+      embed_jets(*c, L, params, net, tb.node(l), &y[(size_t)l * M], &y1[(size_t)l * M], &y2[(size_t)l * M]);
+    for (int l = 0; l < lc; ++l) {
+      double dx = tb.node(l + 1) - tb.node(l);
+      for (int mm = 0; mm < M; ++mm) {
+        size_t a = (size_t)l * M + mm, b = (size_t)(l + 1) * M + mm;
+        quintic(y[a], y[b], y1[a], y1[b], y2[a], y2[b], dx, table + (((size_t)net * lc + l) * M + mm) * 6);
+      }
+    }
+  }
+}
+
+// Energy, forces, virial (and per-atom energies).  If nl_j is null the brute-force
+// neighbour list is built here.  table null => embedding network; else quintic table.
+// Returns (number of overflowing neighbour blocks) + 1000000 * (any table range error).
+int orc_compute(const OrcConfig* cfg, const double* params, int N, const double* coord, const int* type,
+                const double* box, const int* nl_j_in, const int* nl_shift_in, const double* table, double s0,
+                double stride1, int n1, double stride2, int n2, double* energy, double* force, double* virial,
+                double* atom_energy, int nthreads) {
+  const OrcConfig& c = *cfg;
+  Layout L = make_layout(c);
+  const int nc = L.nc;
+  std::vector<int> nl_j((size_t)N * nc), code((size_t)N * nc);
+  int ov = 0;
+  if (!nl_j_in) {
+    ov = build_nlist(c, L, N, coord, type, box, nl_j.data(), code.data(), nullptr);
+  } else {
+    for (size_t k = 0; k < nl_j.size(); ++k) {
+      nl_j[k] = nl_j_in[k];
+      code[k] = pack_shift(nl_shift_in[3 * k], nl_shift_in[3 * k + 1], nl_shift_in[3 * k + 2]);
+    }
+  }
+  Table tb{table, s0, stride1, stride2, n1, n2};
+  const Table* tp = table ? &tb : nullptr;
+  std::vector<double> gd((size_t)N * nc * 3, 0.0);
+  std::vector<AtomOut> ao(N);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < N; ++i)
+    atom_pass(c, L, params, tp, i, coord, type, box, nl_j.data(), code.data(), &gd[(size_t)i * nc * 3], &ao[i]);
+  (void)nthreads;
+  // E = sum_i E_i ; F_i += dE/dr_ij, F_j -= dE/dr_ij ; Xi_ab = -sum (dE/dr_ij)_a (r_ij)_b
+  double E = 0.0;
+  int rerr = 0;
+  for (int i = 0; i < N; ++i) {
+    E += ao[i].e;
+    rerr |= ao[i].range_err;
+    if (atom_energy) atom_energy[i] = ao[i].e;
+  }
+  *energy = E;
+  for (int k = 0; k < 3 * N; ++k) force[k] = 0.0;
+  for (int k = 0; k < 9; ++k) virial[k] = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < nc; ++k) {
+      int j = nl_j[(size_t)i * nc + k];
+      if (j < 0) continue;
+      int n[3];
+      unpack_shift(code[(size_t)i * nc + k], n);
+      double d[3];
+      pair_disp(coord + 3 * i, coord + 3 * j, n, box, d);
+      const double* g = &gd[((size_t)i * nc + k) * 3];
+      for (int a = 0; a < 3; ++a) {
+        force[3 * i + a] += g[a];
+        force[3 * j + a] -= g[a];
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) virial[3 * a + b] -= g[a] * d[b];
+    }
+  return ov + (rerr ? 1000000 : 0);
+}
+
+// Dual-number directional derivative of E along a coordinate direction dcoord [N*3] and a
+// box direction dbox [9] (the neighbour list is given and held fixed).  Returns E; writes
+// the derivative into *dE.  Per-atom energies (values) are written to atom_energy if given.
+double orc_energy_dual(const OrcConfig* c, const double* params, int N, const double* coord, const double* dcoord,
+                       const int* type, const double* box, const double* dbox, const int* nl_j, const int* nl_shift,
+                       double* dE, double* atom_energy) {
+  Layout L = make_layout(*c);
+  std::vector<int> code((size_t)N * L.nc);
+  for (size_t k = 0; k < code.size(); ++k)
+    code[k] = pack_shift(nl_shift[3 * k], nl_shift[3 * k + 1], nl_shift[3 * k + 2]);
+  std::vector<Dual> x((size_t)N * 3), h(9), ae(N);
+  for (int k = 0; k < 3 * N; ++k) x[k] = Dual(coord[k], dcoord ? dcoord[k] : 0.0);
+  if (box)
+    for (int k = 0; k < 9; ++k) h[k] = Dual(box[k], dbox ? dbox[k] : 0.0);
+  Dual E = energy_generic<Dual>(*c, L, params, N, x.data(), type, box ? h.data() : nullptr, nl_j, code.data(),
+                                ae.data());
+  if (atom_energy)
+    for (int i = 0; i < N; ++i) atom_energy[i] = ae[i].v;
+  *dE = E.d;
+  return E.v;
+}
+
+// Plain-double energy through the generic template (pins the reverse-pass forward).
+double orc_energy_plain(const OrcConfig* c, const double* params, int N, const double* coord, const int* type,
+                        const double* box, const int* nl_j, const int* nl_shift) {
+  Layout L = make_layout(*c);
+  std::vector<int> code((size_t)N * L.nc);
+  for (size_t k = 0; k < code.size(); ++k)
+    code[k] = pack_shift(nl_shift[3 * k], nl_shift[3 * k + 1], nl_shift[3 * k + 2]);
+  return energy_generic<double>(*c, L, params, N, coord, type, box, nl_j, code.data(), nullptr);
+}
+
+}  // extern "C"

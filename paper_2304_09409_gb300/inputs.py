@@ -1,0 +1,306 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module holds no arithmetic of the Deep Potential method itself: it only draws
+random numbers and lays out atoms, model configurations and network parameters.
+Both the oracle and the CUDA path receive the arrays produced here.
+
+Random numbers: a counter-based SplitMix64 stream (Steele, Lea, Flood 2014) turned
+into uniforms on [0, 1) with the top 53 bits, and into normals with the Box-Muller
+transform.  The paper's datasets (water, Cu) are not available; the generators below
+stand in for them with the system sizes and densities of the workloads described in
+the paper's benchmark section (Sec. IV): liquid-water-like boxes at 1 g/cm^3 and a
+Cu-like FCC crystal with a = 3.634 A.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _splitmix64(counter: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for each 64-bit counter value (state = counter * golden)."""
+    with np.errstate(over="ignore"):
+        z = counter * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+class Rng:
+    """Counter-based SplitMix64 stream: value k of stream `seed` is mix((seed<<32) + k + 1)."""
+
+    def __init__(self, seed: int):
+        self.base = np.uint64((int(seed) & 0xFFFFFFFF) << 32)
+        self.k = 0
+
+    def bits(self, n: int) -> np.ndarray:
+        ctr = self.base + np.arange(self.k + 1, self.k + 1 + n, dtype=np.uint64)
+        self.k += n
+        return _splitmix64(ctr)
+
+    def uniform(self, n: int) -> np.ndarray:
+        return (self.bits(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+    def normal(self, n: int) -> np.ndarray:
+        m = (n + 1) // 2
+        u1 = 1.0 - self.uniform(m)  # (0, 1]
+        u2 = self.uniform(m)
+        rad = np.sqrt(-2.0 * np.log(u1))
+        z = np.concatenate([rad * np.cos(2.0 * math.pi * u2), rad * np.sin(2.0 * math.pi * u2)])
+        return z[:n]
+
+
+# ----------------------------------------------------------------------------------------------
+# Model configuration (se_e2_a, Sec. II.A.1 and II.A.2) and parameter layout
+# ----------------------------------------------------------------------------------------------
+
+MAX_TYPES = 8
+MAX_LAYERS = 8
+
+
+@dataclasses.dataclass
+class ModelConfig:
+    ntypes: int
+    rcut: float
+    rcut_smth: float
+    sel: Tuple[int, ...]
+    embed: Tuple[int, ...]        # embedding net widths, input width 1 implied
+    axis: int                     # M_<
+    fit: Tuple[int, ...]          # fitting net hidden widths; a final width-1 linear layer is implied
+    type_one_side: int = 0        # 0: nets N^{a_i,a_j}; 1: nets N^{a_j}
+
+    @property
+    def nc(self) -> int:
+        return int(sum(self.sel))
+
+    @property
+    def m(self) -> int:
+        return int(self.embed[-1])
+
+    @property
+    def n_embed_nets(self) -> int:
+        return self.ntypes if self.type_one_side else self.ntypes * self.ntypes
+
+    @property
+    def descriptor_dim(self) -> int:
+        return self.m * self.axis
+
+    def embed_layer_shapes(self) -> List[Tuple[int, int]]:
+        dims = [1] + list(self.embed)
+        return [(dims[k], dims[k + 1]) for k in range(len(self.embed))]
+
+    def fit_layer_shapes(self) -> List[Tuple[int, int]]:
+        dims = [self.descriptor_dim] + list(self.fit) + [1]
+        return [(dims[k], dims[k + 1]) for k in range(len(dims) - 1)]
+
+    def n_params(self) -> int:
+        ne = sum(a * b + b for a, b in self.embed_layer_shapes())
+        nf = sum(a * b + b for a, b in self.fit_layer_shapes())
+        return self.n_embed_nets * ne + self.ntypes * nf
+
+
+def water_model() -> ModelConfig:
+    """Water-like se_e2_a model: r_c 6, r_s 0.5, sel [46, 92], embedding 25/50/100, M_< 16, fitting 240^3."""
+    return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92), embed=(25, 50, 100), axis=16,
+                       fit=(240, 240, 240))
+
+
+def metal_model() -> ModelConfig:
+    """Metal-like single-type model: r_c 8, r_s 0.5, sel [512], embedding 32/64/128, M_< 16, fitting 240^3."""
+    return ModelConfig(ntypes=1, rcut=8.0, rcut_smth=0.5, sel=(512,), embed=(32, 64, 128), axis=16,
+                       fit=(240, 240, 240))
+
+
+def make_params(cfg: ModelConfig, seed: int = 0) -> np.ndarray:
+    """Xavier-normal weights W ~ N(0, 2/(fan_in+fan_out)) and biases b ~ N(0, 1), FP64, flat.
+
+    Layout (shared by every consumer): embedding nets in order of net index
+    (a_i * ntypes + a_j, or a_j when type_one_side), then fitting nets by type; inside a
+    net, layer by layer, W row-major [in][out] followed by b [out].
+    """
+    rng = Rng(seed)
+    out = []
+    nets = [(cfg.embed_layer_shapes(), cfg.n_embed_nets), (cfg.fit_layer_shapes(), cfg.ntypes)]
+    for shapes, count in nets:
+        for _ in range(count):
+            for fi, fo in shapes:
+                std = math.sqrt(2.0 / (fi + fo))
+                out.append(rng.normal(fi * fo) * std)
+                out.append(rng.normal(fo))
+    p = np.concatenate(out).astype(np.float64)
+    assert p.size == cfg.n_params()
+    return p
+
+
+# ----------------------------------------------------------------------------------------------
+# Configurations (atoms)
+# ----------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Frame:
+    coord: np.ndarray  # [N, 3] float64
+    atype: np.ndarray  # [N] int32
+    box: np.ndarray    # [3, 3] float64, rows are the cell vectors h_0, h_1, h_2
+
+    @property
+    def natoms(self) -> int:
+        return int(self.coord.shape[0])
+
+
+WATER_ML_PER_MOL_A3 = 18.01528 / 0.602214076  # A^3 per molecule at 1 g/cm^3 (29.915)
+OH_BOND = 0.96
+HOH_ANGLE_DEG = 104.52
+
+
+def _unit_vectors(rng: Rng, n: int) -> np.ndarray:
+    z = 2.0 * rng.uniform(n) - 1.0
+    phi = 2.0 * math.pi * rng.uniform(n)
+    rxy = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([rxy * np.cos(phi), rxy * np.sin(phi), z], axis=1)
+
+
+def _place_hydrogens(rng: Rng, o: np.ndarray) -> np.ndarray:
+    """Two H per O at 0.96 A: the first direction uniform on the sphere, the second at the
+    HOH angle from it with a uniformly random azimuth."""
+    n = o.shape[0]
+    u = _unit_vectors(rng, n)
+    # a vector not parallel to u, then an orthonormal pair (e1, e2) perpendicular to u
+    helper = np.where(np.abs(u[:, :1]) < 0.9, np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 1.0, 0.0]]))
+    e1 = np.cross(u, helper)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(u, e1)
+    psi = 2.0 * math.pi * rng.uniform(n)
+    th = math.radians(HOH_ANGLE_DEG)
+    v = math.cos(th) * u + math.sin(th) * (np.cos(psi)[:, None] * e1 + np.sin(psi)[:, None] * e2)
+    h1 = o + OH_BOND * u
+    h2 = o + OH_BOND * v
+    return h1, h2
+
+
+def _min_image_dist(o: np.ndarray, L: float) -> float:
+    d = o[:, None, :] - o[None, :, :]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    return float(r.min()) if o.shape[0] > 1 else np.inf
+
+
+def water_frame(seed: int = 0, n_side: int = 4, spacing: float = 3.105, jitter: float = 0.2,
+                min_oo: float = 2.5) -> Frame:
+    """Water-like frame: O on an n_side^3 cubic lattice (spacing 3.105 A, box 12.42 A for
+    n_side = 4, i.e. 1 g/cm^3) with uniform jitter of +-0.2 A, resampled until the minimum
+    image O-O distance is >= 2.5 A; two H per O (see `_place_hydrogens`).  Atom order is
+    O, H, H per molecule (types 0, 1, 1)."""
+    rng = Rng(seed)
+    L = n_side * spacing
+    g = np.arange(n_side) * spacing
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    for _ in range(1000):
+        o = lat + (2.0 * rng.uniform(lat.size).reshape(lat.shape) - 1.0) * jitter
+        if _min_image_dist(o, L) >= min_oo:
+            break
+    h1, h2 = _place_hydrogens(rng, o)
+    coord = np.stack([o, h1, h2], axis=1).reshape(-1, 3)
+    atype = np.tile(np.array([0, 1, 1], dtype=np.int32), o.shape[0])
+    return Frame(coord.astype(np.float64), atype, np.eye(3) * L)
+
+
+def water_frame_n(n_mol: int, seed: int, min_oo: float = 2.5) -> Frame:
+    """Water-like frame with n_mol molecules at 1 g/cm^3: when n_mol is a cube the lattice
+    generator above is used; otherwise O atoms are placed by random sequential addition
+    with a 2.5 A minimum image O-O distance."""
+    L = (n_mol * WATER_ML_PER_MOL_A3) ** (1.0 / 3.0)
+    k = round(n_mol ** (1.0 / 3.0))
+    if k ** 3 == n_mol:
+        return water_frame(seed=seed, n_side=k, spacing=L / k)
+    rng = Rng(seed)
+    o = np.zeros((0, 3))
+    tries = 0
+    while o.shape[0] < n_mol:
+        c = rng.uniform(3) * L
+        if o.shape[0]:
+            d = o - c
+            d -= L * np.round(d / L)
+            if (d * d).sum(-1).min() < min_oo * min_oo:
+                tries += 1
+                if tries > 200000:
+                    raise RuntimeError("random sequential addition failed")
+                continue
+        o = np.vstack([o, c[None]])
+    h1, h2 = _place_hydrogens(rng, o)
+    coord = np.stack([o, h1, h2], axis=1).reshape(-1, 3)
+    atype = np.tile(np.array([0, 1, 1], dtype=np.int32), n_mol)
+    return Frame(coord.astype(np.float64), atype, np.eye(3) * L)
+
+
+def replicate(fr: Frame, reps: Sequence[int]) -> Frame:
+    """Tile a periodic frame reps[0] x reps[1] x reps[2] times (atom order: image-major)."""
+    out = []
+    for a in range(reps[0]):
+        for b in range(reps[1]):
+            for c in range(reps[2]):
+                out.append(fr.coord + a * fr.box[0] + b * fr.box[1] + c * fr.box[2])
+    box = fr.box * np.array(reps, dtype=np.float64)[:, None]
+    n = int(np.prod(reps))
+    return Frame(np.concatenate(out), np.tile(fr.atype, n), box)
+
+
+def fcc_frame(n_cells: Sequence[int] = (20, 20, 20), a: float = 3.634, sigma: float = 0.05,
+              seed: int = 0) -> Frame:
+    """Cu-like FCC crystal: conventional 4-atom cell of edge a, n_cells copies, Gaussian
+    jitter N(0, sigma^2) per Cartesian component; single type 0."""
+    rng = Rng(seed)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]], dtype=np.float64)
+    nx, ny, nz = n_cells
+    g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), -1).reshape(-1, 3)
+    pos = ((g[:, None, :] + basis[None]) * a).reshape(-1, 3)
+    pos = pos + rng.normal(pos.size).reshape(pos.shape) * sigma
+    box = np.diag([nx * a, ny * a, nz * a]).astype(np.float64)
+    return Frame(pos, np.zeros(pos.shape[0], dtype=np.int32), box)
+
+
+def perturbed(fr: Frame, seed: int, sigma: float) -> Frame:
+    """Copy of a frame with N(0, sigma^2) noise added to every coordinate."""
+    rng = Rng(seed)
+    return Frame(fr.coord + rng.normal(fr.coord.size).reshape(fr.coord.shape) * sigma, fr.atype.copy(),
+                 fr.box.copy())
+
+
+def triclinic_box(L: float, tilt: Tuple[float, float, float]) -> np.ndarray:
+    """Lower-triangular cell (rows h_0, h_1, h_2) with off-diagonal tilts (xy, xz, yz)."""
+    xy, xz, yz = tilt
+    return np.array([[L, 0.0, 0.0], [xy, L, 0.0], [xz, yz, L]], dtype=np.float64)
+
+
+def random_frame(n: int, ntypes: int, box: np.ndarray, seed: int, min_dist: float = 0.8) -> Frame:
+    """Random atoms in a (possibly triclinic) periodic cell with a minimum image distance,
+    types drawn uniformly; used for small edge-case tests."""
+    rng = Rng(seed)
+    inv = np.linalg.inv(box)
+    pts = []
+    tries = 0
+    while len(pts) < n:
+        f = rng.uniform(3)
+        c = f @ box
+        ok = True
+        for p in pts:
+            d = (c - p) @ inv
+            d -= np.round(d)
+            if np.linalg.norm(d @ box) < min_dist:
+                ok = False
+                break
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place atoms")
+        if ok:
+            pts.append(c)
+    atype = (rng.bits(n) % np.uint64(ntypes)).astype(np.int32)
+    return Frame(np.array(pts), atype, box.astype(np.float64))

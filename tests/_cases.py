@@ -1,0 +1,23 @@
+"""Small seeded cases shared by the oracle pins and the GPU parity tests."""
+import numpy as np
+
+from paper_2304_09409_gb300 import inputs as I
+
+
+def tiny_model(type_one_side: int = 0) -> I.ModelConfig:
+    """Two species, short cutoff, narrow nets: every code path of the full model
+    (type-pair nets, {x,x} and +x skips, linear output layer) at a size the oracle's
+    dual-number and finite-difference checks finish quickly."""
+    return I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(4, 8, 16), axis=4,
+                         fit=(12, 12), type_one_side=type_one_side)
+
+
+def tiny_frame(seed: int = 3, n: int = 14, triclinic: bool = True) -> I.Frame:
+    """14 atoms in a small triclinic cell narrower than 2 r_c, so periodic images of the
+    same atom (and of atom i itself) appear in the neighbour list."""
+    box = I.triclinic_box(5.2, (0.9, -0.6, 0.4)) if triclinic else np.eye(3) * 5.2
+    return I.random_frame(n, 2, box, seed=seed, min_dist=1.0)
+
+
+def scaled_params(cfg, seed=0, scale=1.0):
+    return I.make_params(cfg, seed) * scale
