@@ -1,0 +1,150 @@
+/*
+ * dpgb.h -- C ABI of the GB300 (sm_103a) Deep Potential se_e2_a engine.
+ *
+ * The library evaluates the energy E, forces F and virial Xi of a smooth-edition
+ * two-body-embedding Deep Potential (DeePMD-kit v2, arXiv 2304.09409):
+ *
+ *   neighbour list n(i) with a fixed per-type sel       (Sec. II.A.1 "Handling the
+ *                                                        systems composed of multiple
+ *                                                        chemical species"; Sec. III.B.1)
+ *   environment matrix R with the switch s(r)           (Eqs. (rij), (switch))
+ *   embedding G = N_{e,2}^{a_i,a_j}(s)  or its quintic  (Eqs. (G2), (NN), (compress))
+ *   descriptor D = (1/Nc^2) G^T R R^T G_<               (Sec. II.A.1, se_e2_a)
+ *   E_i = F_0^{a_i}(D^i),  E = sum_i E_i                (Eq. (fitting_energy))
+ *   F = -dE/dr,  Xi_ab = -sum_g dE/dh_ga h_gb            (Sec. II.A.2)
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a status code (DP_OK = 0); nothing aborts.  On error,
+ *     dp_last_error() returns a message for the calling thread.
+ *   - The caller owns every input and output buffer.  The library owns models,
+ *     neighbour lists and the scratch memory it allocates for them.
+ *   - Array arguments may be host or device pointers (detected per pointer).  Host
+ *     inputs are copied to the device inside the call and host outputs are copied back
+ *     before the call returns.  `box` is always a host pointer: it fixes the cell grid.
+ *   - Coordinates are FP64 [natoms][3] (Angstrom), types are int32 [natoms] in
+ *     [0, ntypes).  box is FP64 [3][3] row-major, row g is the cell vector h_g; box ==
+ *     NULL means open boundaries (no periodic images).
+ *   - Output atom order equals input atom order.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that return
+ *     results synchronise that stream before returning.
+ */
+#ifndef DPGB_H
+#define DPGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DP_OK 0
+#define DP_E_ARG 1          /* invalid argument (null pointer, bad size, bad type, bad box)   */
+#define DP_E_CUDA 2         /* a CUDA runtime call failed                                    */
+#define DP_E_OOM 3          /* device memory could not be allocated                          */
+#define DP_E_SEL_OVERFLOW 4 /* some atom had more neighbours of a type than sel: the list
+                               keeps the sel nearest and the results are computed (warning) */
+#define DP_E_TIMEOUT 5      /* a bounded device wait gave up                                 */
+#define DP_E_RANGE 6        /* compressed model: some s fell outside the table (the last
+                               piece was extrapolated; results are computed, warning)       */
+#define DP_E_CAPACITY 7     /* more than DP_MAX_CANDIDATES atoms inside r_c of one atom     */
+#define DP_E_UNSUPPORTED 8  /* configuration outside what the kernels implement              */
+
+/* ---- precision of the network arithmetic ---- */
+#define DP_PREC_FP64 0 /* every step in FP64                                                 */
+#define DP_PREC_FP32 1 /* networks and contractions in FP32; FP64 for the pair distance, the
+                          switch near r_c, the energy sum and the force/virial accumulation */
+#define DP_PREC_TF32 2 /* as FP32, with the embedding and fitting GEMMs on TF32 tensor cores */
+#define DP_PREC_BF16 3 /* as FP32, with the embedding and fitting GEMMs on BF16 tensor cores */
+
+#define DP_MAX_TYPES 8
+#define DP_MAX_LAYERS 8
+#define DP_MAX_CANDIDATES 1024 /* atoms within r_c of one atom the list builder can hold */
+
+/* Model hyper-parameters (Sec. II.A.1, II.A.2, II.A.6).  embed[] are the embedding-net
+ * widths (input width 1 is implied), fit[] the fitting-net hidden widths (a final linear
+ * width-1 layer is implied).  ResNet skips follow Eq. (NN) with w_hat = 1. */
+typedef struct {
+  int ntypes;
+  int sel[DP_MAX_TYPES];
+  double rcut;
+  double rcut_smth;
+  int n_embed;
+  int embed[DP_MAX_LAYERS];
+  int axis; /* M_< */
+  int n_fit;
+  int fit[DP_MAX_LAYERS];
+  int type_one_side; /* 0: nets N^{a_i,a_j}; 1: nets N^{a_j} */
+} dp_model_config;
+
+typedef struct dp_model dp_model;
+typedef struct dp_nlist dp_nlist;
+
+/* Create a model on `device` from host FP64 parameters.
+ *   params: host, n_params doubles.  Layout: embedding nets in order of net index
+ *           (a_i*ntypes + a_j, or a_j if type_one_side), then fitting nets by type;
+ *           per net, layer by layer, W row-major [in][out] then b[out].
+ *   precision: DP_PREC_*.  compressed: 1 = replace the embedding nets by quintic
+ *           tables (Eq. (compress)) built on the device at creation, over s in
+ *           [0, 2] with stride 0.01 on [0, 1.8) and 0.1 on [1.8, 2].
+ * Errors: DP_E_ARG (bad config / n_params mismatch), DP_E_OOM, DP_E_CUDA,
+ *         DP_E_UNSUPPORTED (e.g. widths beyond the kernels' limits). */
+int dp_model_create(const dp_model_config* cfg, const double* params, long n_params, int device, int precision,
+                    int compressed, dp_model** out);
+
+/* Same as dp_model_create, reading a weight file: 8-byte magic "DPGBW001", the
+ * dp_model_config struct as stored in memory, an int64 n_params, then n_params FP64. */
+int dp_init_model(const char* weight_path, int device, int precision, int compressed, dp_model** out);
+
+int dp_free_model(dp_model* model);
+
+/* Number of FP64 parameters the configuration needs (-1 on a bad config). */
+long dp_model_n_params(const dp_model_config* cfg);
+
+/* Build the neighbour list of one frame on the model's device (Sec. III.B.1 order).
+ * Per atom i and neighbour type t, the first sel[t] entries of the type-t block hold
+ * the neighbours (j, image n) with |r_j + n.h - r_i| < r_c sorted by (r^2, j, n); the
+ * rest hold j = -1.  Displacements are evaluated as (r_j + (n0 h0 + n1 h1 + n2 h2)) - r_i
+ * left to right in FP64 without fused multiply-add, so lists are bit-reproducible.
+ *   n_overflow (host, may be NULL): number of (atom, type) blocks that overflowed sel.
+ * Returns DP_OK, or DP_E_SEL_OVERFLOW (list still valid) / DP_E_CAPACITY / DP_E_ARG. */
+int dp_build_nlist(dp_model* model, int natoms, const double* coord, const int* type, const double* box,
+                   dp_nlist** out, int* n_overflow, void* stream);
+
+/* Copy a neighbour list to host arrays nl_j [natoms*Nc] and nl_shift [natoms*Nc*3]. */
+int dp_nlist_export(const dp_nlist* nlist, int* nl_j, int* nl_shift);
+
+int dp_free_nlist(dp_nlist* nlist);
+
+/* Energy, forces and virial of one frame.
+ *   nlist: a list built by dp_build_nlist from the same coordinates, or NULL to build
+ *          one inside the call (the full path).
+ *   energy [1], force [natoms*3], virial [9] (row-major Xi_ab), atom_energy [natoms]
+ *   (may be NULL).  Outputs may be host or device pointers.
+ * Returns DP_OK or a warning/error code as documented above. */
+int dp_compute(dp_model* model, dp_nlist* nlist, int natoms, const double* coord, const int* type,
+               const double* box, double* energy, double* force, double* virial, double* atom_energy, void* stream);
+
+/* Compressed models: copy the device-built quintic tables (FP64) to host `out`, laid out
+ * [net][interval][M][6] with coefficients (a, b, c, d, e, f) of Eq. (compress) for the
+ * piece g(t) = a t^5 + ... + f, t = s - x_l.  *n_intervals receives L_c.
+ * Returns DP_E_ARG for an uncompressed model. */
+int dp_model_export_table(const dp_model* model, double* out, int* n_intervals);
+
+/* ---- tracing (no counterpart in the paper; its TensorBoard profiles play this role) ----
+ * dp_profile_enable: when on, every kernel launch of the model's calls is bracketed by CUDA
+ * events on the launch stream; per-kernel-name totals are folded in when a call
+ * synchronises.  dp_profile_count / dp_profile_read enumerate (name, total ms, launches);
+ * dp_profile_reset clears them.  dp_launch_count returns the number of kernels the model's
+ * calls have launched since creation or the last reset (counted whether or not timing is on). */
+int dp_profile_enable(dp_model* model, int on);
+int dp_profile_reset(dp_model* model);
+int dp_profile_count(const dp_model* model);
+int dp_profile_read(const dp_model* model, int k, char* name, int name_len, double* total_ms, long* count);
+long dp_launch_count(const dp_model* model);
+
+/* Message for the last error raised on the calling thread ("" if none). */
+const char* dp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPGB_H */

@@ -85,6 +85,8 @@ def _L():
         _lib.orc_energy_dual.restype = ctypes.c_double
         _lib.orc_energy_plain.argtypes = [cp, dp, ctypes.c_int, dp, ip, dp, ip, ip]
         _lib.orc_energy_plain.restype = ctypes.c_double
+        _lib.orc_atom_subset.argtypes = [cp, dp, ctypes.c_int, dp, ip, dp, ctypes.c_int, ip, ip, ip, dp]
+        _lib.orc_atom_subset.restype = ctypes.c_int
     return _lib
 
 
@@ -236,3 +238,19 @@ def energy_plain(cfg, params, coord, atype, box, nl) -> float:
     c = _cfg(cfg)
     return _L().orc_energy_plain(ctypes.byref(c), _d(_f64(params)), coord.shape[0], _d(coord), _i(_i32(atype)),
                                  _d(_f64(box)), _i(_i32(nl[0])), _i(_i32(nl[1])))
+
+
+def atom_subset(cfg, params, coord, atype, box, idx):
+    """Neighbour rows (nl_j [S, Nc], nl_shift [S, Nc, 3]) and atomic energies [S] of the atoms
+    `idx` only, for sampled checks of frames too large for the full oracle."""
+    coord = _f64(coord)
+    idx = _i32(np.atleast_1d(idx))
+    S = idx.size
+    nc = int(sum(cfg.sel))
+    nl_j = np.zeros((S, nc), dtype=np.int32)
+    nl_s = np.zeros((S, nc, 3), dtype=np.int32)
+    e = np.zeros(S)
+    c = _cfg(cfg)
+    _L().orc_atom_subset(ctypes.byref(c), _d(_f64(params)), coord.shape[0], _d(coord), _i(_i32(atype)), _d(_f64(box)),
+                         S, _i(idx), _i(nl_j), _i(nl_s), _d(e))
+    return nl_j, nl_s, e

@@ -750,6 +750,84 @@ double orc_energy_dual(const OrcConfig* c, const double* params, int N, const do
   return E.v;
 }
 
+// Neighbour rows and atomic energies of a subset of atoms only (brute force over all j and
+// images for each selected atom), for sampled checks of frames too large for the full oracle.
+int orc_atom_subset(const OrcConfig* cfg, const double* params, int N, const double* coord, const int* type,
+                    const double* box, int nsel, const int* idx, int* nl_j_out, int* nl_shift_out, double* e_out) {
+  const OrcConfig& c = *cfg;
+  Layout L = make_layout(c);
+  const int nc = L.nc;
+  const double rc2 = c.rcut * c.rcut;
+  double inv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int K[3] = {0, 0, 0};
+  if (box) {
+    inverse3(box, inv);
+    double vol = std::fabs(box[0] * (box[4] * box[8] - box[5] * box[7]) - box[1] * (box[3] * box[8] - box[5] * box[6]) +
+                           box[2] * (box[3] * box[7] - box[4] * box[6]));
+    for (int d = 0; d < 3; ++d) {
+      const double* u = box + 3 * ((d + 1) % 3);
+      const double* v = box + 3 * ((d + 2) % 3);
+      double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+      K[d] = (int)std::ceil(c.rcut / (vol / std::sqrt(cx * cx + cy * cy + cz * cz))) + 1;
+    }
+  }
+  auto mfloor = [&](int a, int d) -> long {
+    if (!box) return 0;
+    double f = coord[3 * a] * inv[d] + coord[3 * a + 1] * inv[3 + d] + coord[3 * a + 2] * inv[6 + d];
+    return (long)std::floor(f);
+  };
+  std::vector<int> nl_j((size_t)N * nc, -1), nl_code((size_t)N * nc, pack_shift(0, 0, 0));
+  int ov = 0;
+  std::vector<Cand> cand;
+  for (int s = 0; s < nsel; ++s) {
+    const int i = idx[s];
+    cand.clear();
+    for (int j = 0; j < N; ++j) {
+      int base[3];
+      for (int d = 0; d < 3; ++d) base[d] = (int)(mfloor(i, d) - mfloor(j, d));
+      int n[3];
+      for (n[0] = base[0] - K[0]; n[0] <= base[0] + K[0]; ++n[0])
+        for (n[1] = base[1] - K[1]; n[1] <= base[1] + K[1]; ++n[1])
+          for (n[2] = base[2] - K[2]; n[2] <= base[2] + K[2]; ++n[2]) {
+            if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+            double d[3];
+            pair_disp(coord + 3 * i, coord + 3 * j, n, box, d);
+            double r2 = norm2(d);
+            if (r2 < rc2) {
+              Cand e;
+              e.type = type[j];
+              std::memcpy(&e.r2bits, &r2, 8);
+              e.j = j;
+              e.code = pack_shift(n[0], n[1], n[2]);
+              cand.push_back(e);
+            }
+          }
+    }
+    std::sort(cand.begin(), cand.end(), cand_less);
+    std::vector<int> cnt(c.ntypes, 0);
+    for (const Cand& e : cand) {
+      if (cnt[e.type] < c.sel[e.type]) {
+        nl_j[(size_t)i * nc + L.sel_off[e.type] + cnt[e.type]] = e.j;
+        nl_code[(size_t)i * nc + L.sel_off[e.type] + cnt[e.type]] = e.code;
+      }
+      cnt[e.type]++;
+    }
+    for (int t = 0; t < c.ntypes; ++t) ov += cnt[t] > c.sel[t];
+  }
+  std::vector<double> gd((size_t)nc * 3);
+  for (int s = 0; s < nsel; ++s) {
+    const int i = idx[s];
+    AtomOut ao;
+    atom_pass(c, L, params, nullptr, i, coord, type, box, nl_j.data(), nl_code.data(), gd.data(), &ao);
+    if (e_out) e_out[s] = ao.e;
+    for (int k = 0; k < nc; ++k) {
+      if (nl_j_out) nl_j_out[(size_t)s * nc + k] = nl_j[(size_t)i * nc + k];
+      if (nl_shift_out) unpack_shift(nl_code[(size_t)i * nc + k], nl_shift_out + 3 * ((size_t)s * nc + k));
+    }
+  }
+  return ov;
+}
+
 // Plain-double energy through the generic template (pins the reverse-pass forward).
 double orc_energy_plain(const OrcConfig* c, const double* params, int N, const double* coord, const int* type,
                         const double* box, const int* nl_j, const int* nl_shift) {

@@ -1,0 +1,151 @@
+// Internal declarations shared by the CUDA translation units of libdpgb.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dpgb.h"
+
+namespace dpgb {
+
+// ------------------------------------------------------------------------------------------
+// Geometry of one neighbour-list build (host-computed launch configuration)
+// ------------------------------------------------------------------------------------------
+struct NlGeom {
+  int natoms, ntypes, nc;
+  int sel[DP_MAX_TYPES];
+  int sel_off[DP_MAX_TYPES + 1];
+  int periodic;
+  double h[9];       // cell rows h0, h1, h2 (periodic)
+  double inv[9];     // inverse of h (periodic)
+  double origin[3];  // open boundary: fractional = (x - origin) / ext
+  double ext[3];
+  float hf[9];       // float cell rows used by the FP32 prefilter (diag(ext) when open)
+  int ncell[3];
+  int K[3];          // virtual-cell search half-width per axis
+  double rc2;        // r_c^2 (exact membership test)
+  float rc2_loose;   // (r_c + 1e-3)^2 (FP32 prefilter)
+};
+
+// Image shift (n0, n1, n2) packed as 10-bit offsets; |n| < 512.
+__host__ __device__ inline int pack_shift(int n0, int n1, int n2) {
+  return ((n0 + 512) << 20) | ((n1 + 512) << 10) | (n2 + 512);
+}
+__host__ __device__ inline void unpack_shift(int code, int& n0, int& n1, int& n2) {
+  n0 = ((code >> 20) & 1023) - 512;
+  n1 = ((code >> 10) & 1023) - 512;
+  n2 = (code & 1023) - 512;
+}
+
+// Pair displacement (x_j + t) - x_i with t = n0 h0 + n1 h1 + n2 h2, evaluated left to right
+// with explicitly rounded FP64 operations (never contracted into FMA), so every kernel that
+// needs r_ij reproduces the neighbour builder's value bit for bit.
+__device__ __forceinline__ void pair_disp_exact(const double* __restrict__ xi, const double* __restrict__ xj,
+                                                int n0, int n1, int n2, const double* h, int periodic,
+                                                double& d0, double& d1, double& d2) {
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double t = 0.0;
+    if (periodic)
+      t = __dadd_rn(__dadd_rn(__dmul_rn((double)n0, h[0 * 3 + a]), __dmul_rn((double)n1, h[1 * 3 + a])),
+                    __dmul_rn((double)n2, h[2 * 3 + a]));
+    d[a] = __dsub_rn(__dadd_rn(xj[a], t), xi[a]);
+  }
+  d0 = d[0];
+  d1 = d[1];
+  d2 = d[2];
+}
+__device__ __forceinline__ double norm2_exact(double d0, double d1, double d2) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+}
+
+// ------------------------------------------------------------------------------------------
+// Model as held on the device
+// ------------------------------------------------------------------------------------------
+struct LayerDesc {
+  int n_in, n_out;
+  long w_off;  // offset of W [n_in][n_out] in the parameter arrays; b follows W
+  int skip;    // 0 none, 1 +x, 2 +{x,x}
+  int tanh_act;
+};
+
+struct TableDesc {
+  double s0, stride1, stride2;
+  int n1, n2;
+};
+
+struct DeviceModel {
+  dp_model_config cfg;
+  int device;
+  int precision;
+  int compressed;
+  int nc, M, A, n_embed_nets;
+  int sel_off[DP_MAX_TYPES + 1];
+  std::vector<LayerDesc> emb;  // per net * n_embed + layer
+  std::vector<LayerDesc> fit;  // per type * n_fit_layers + layer
+  int n_fit_layers;
+  long n_params;
+  double* p64 = nullptr;  // device FP64 parameters
+  float* p32 = nullptr;   // device FP32 copy
+  TableDesc tab{};
+  double* tab64 = nullptr;  // [nets][lc][M][6]
+  float* tab32 = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------
+// Error state and helpers (capi.cu)
+// ------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+#define DP_CUDA_TRY(expr)                                                                   \
+  do {                                                                                      \
+    cudaError_t _e = (expr);                                                                \
+    if (_e != cudaSuccess) {                                                                \
+      dpgb::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                  \
+      return _e == cudaErrorMemoryAllocation ? DP_E_OOM : DP_E_CUDA;                        \
+    }                                                                                       \
+  } while (0)
+
+// Device status words written by kernels.
+struct DevStatus {
+  int sel_overflow;   // number of (atom, type) blocks beyond sel
+  int capacity;       // an atom had more than DP_MAX_CANDIDATES candidates
+  int table_range;    // compressed: an s outside the table
+  int bad_type;       // a type outside [0, ntypes)
+};
+
+// ------------------------------------------------------------------------------------------
+// Launchers (nlist.cu)
+// ------------------------------------------------------------------------------------------
+int host_geometry(const dp_model_config& cfg, int natoms, const double* box_host, const double* bbox_lohi,
+                  NlGeom& g);
+cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi /*device [6]*/, cudaStream_t st);
+cudaError_t launch_nlist_build(const NlGeom& g, const double* coord, const int* type, int* cell_count,
+                               int* cell_start, int* cell_cursor, int* cell_atoms, int* atom_cell, int* atom_img,
+                               float4* atom_wf, int* nl_j, int* nl_code, int* counts, DevStatus* status,
+                               cudaStream_t st);
+cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, int* bad_type,
+                             cudaStream_t st);
+
+// ------------------------------------------------------------------------------------------
+// Generic (CUDA-core) path, templated on the network scalar (dense.cu / path.cu)
+// ------------------------------------------------------------------------------------------
+struct RowMap {
+  int kind;  // 0: rows r0 + r ; 1: slots (p0 + r / nk) * nc + k0 + r % nk
+  long r0;
+  int p0, nk, k0, nc;
+  int nrows;
+};
+
+template <class R>
+cudaError_t launch_dense_fwd(const RowMap& rm, const R* X, int n_in, const R* W, const R* b, int n_out, int skip,
+                             int tanh_act, R* Y, R* Tact, cudaStream_t st);
+template <class R>
+cudaError_t launch_dense_bwd(const RowMap& rm, const R* GY, const R* Tact, int n_in, const R* W, int n_out,
+                             int skip, R* GX, cudaStream_t st);
+
+}  // namespace dpgb

@@ -1,0 +1,283 @@
+"""Thin Python binding of libdpgb (include/dpgb.h): argument marshalling only.
+
+Every step of the energy / force / virial path runs in the library's CUDA kernels.
+Arrays may be numpy arrays (host; the library copies them) or torch CUDA tensors
+(device; the library reads and writes them in place).  There is no CPU fallback:
+loading fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdpgb.so")
+
+DP_OK = 0
+DP_E_ARG = 1
+DP_E_CUDA = 2
+DP_E_OOM = 3
+DP_E_SEL_OVERFLOW = 4
+DP_E_TIMEOUT = 5
+DP_E_RANGE = 6
+DP_E_CAPACITY = 7
+DP_E_UNSUPPORTED = 8
+
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+
+EXPORTED = [
+    "dp_model_create", "dp_init_model", "dp_free_model", "dp_model_n_params", "dp_build_nlist",
+    "dp_nlist_export", "dp_free_nlist", "dp_compute", "dp_model_export_table", "dp_last_error",
+]
+
+
+class DPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dpgb error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    """dp_model_config of include/dpgb.h."""
+    _fields_ = [
+        ("ntypes", ctypes.c_int),
+        ("sel", ctypes.c_int * 8),
+        ("rcut", ctypes.c_double),
+        ("rcut_smth", ctypes.c_double),
+        ("n_embed", ctypes.c_int),
+        ("embed", ctypes.c_int * 8),
+        ("axis", ctypes.c_int),
+        ("n_fit", ctypes.c_int),
+        ("fit", ctypes.c_int * 8),
+        ("type_one_side", ctypes.c_int),
+    ]
+
+    @classmethod
+    def from_model(cls, cfg) -> "Config":
+        c = cls()
+        c.ntypes = int(cfg.ntypes)
+        for t, v in enumerate(cfg.sel):
+            c.sel[t] = int(v)
+        c.rcut = float(cfg.rcut)
+        c.rcut_smth = float(cfg.rcut_smth)
+        c.n_embed = len(cfg.embed)
+        for k, v in enumerate(cfg.embed):
+            c.embed[k] = int(v)
+        c.axis = int(cfg.axis)
+        c.n_fit = len(cfg.fit)
+        for k, v in enumerate(cfg.fit):
+            c.fit[k] = int(v)
+        c.type_one_side = int(getattr(cfg, "type_one_side", 0))
+        return c
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdpgb is not built ({LIB_PATH} missing): run paper_2304_09409_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        ip = ctypes.c_int
+        L.dp_model_create.argtypes = [ctypes.POINTER(Config), vp, ctypes.c_long, ip, ip, ip, ctypes.POINTER(vp)]
+        L.dp_init_model.argtypes = [ctypes.c_char_p, ip, ip, ip, ctypes.POINTER(vp)]
+        L.dp_free_model.argtypes = [vp]
+        L.dp_model_n_params.argtypes = [ctypes.POINTER(Config)]
+        L.dp_model_n_params.restype = ctypes.c_long
+        L.dp_build_nlist.argtypes = [vp, ip, vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(ip), vp]
+        L.dp_nlist_export.argtypes = [vp, vp, vp]
+        L.dp_free_nlist.argtypes = [vp]
+        L.dp_compute.argtypes = [vp, vp, ip, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.dp_model_export_table.argtypes = [vp, vp, ctypes.POINTER(ip)]
+        L.dp_last_error.restype = ctypes.c_char_p
+        L.dp_profile_enable.argtypes = [vp, ip]
+        L.dp_profile_reset.argtypes = [vp]
+        L.dp_profile_count.argtypes = [vp]
+        L.dp_profile_read.argtypes = [vp, ip, ctypes.c_char_p, ip, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_long)]
+        L.dp_launch_count.argtypes = [vp]
+        L.dp_launch_count.restype = ctypes.c_long
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().dp_last_error().decode()
+
+
+def _check(code: int, allow=()):
+    if code != DP_OK and code not in allow:
+        raise DPError(code, last_error())
+    return code
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class NList:
+    def __init__(self, handle, natoms: int, nc: int, n_overflow: int):
+        self.handle = handle
+        self.natoms = natoms
+        self.nc = nc
+        self.n_overflow = n_overflow
+
+    def export(self):
+        nl_j = np.zeros((self.natoms, self.nc), dtype=np.int32)
+        nl_s = np.zeros((self.natoms, self.nc, 3), dtype=np.int32)
+        _check(lib().dp_nlist_export(self.handle, nl_j.ctypes.data, nl_s.ctypes.data))
+        return nl_j, nl_s
+
+    def free(self):
+        if self.handle:
+            lib().dp_free_nlist(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Model:
+    """A se_e2_a model resident on one GPU."""
+
+    def __init__(self, cfg, params: np.ndarray, device: int = 0, precision: str = "fp64", compressed: bool = False):
+        self.cfg = cfg
+        self.c = Config.from_model(cfg)
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib().dp_model_create(ctypes.byref(self.c), p.ctypes.data, p.size, device, PREC[precision],
+                                     1 if compressed else 0, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+        self.nc = int(sum(cfg.sel))
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().dp_free_model(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # ---- tracing ----
+    def profile(self, on: bool = True):
+        _check(lib().dp_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_reset(self):
+        _check(lib().dp_profile_reset(self.handle))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} accumulated while profiling was on."""
+        out = {}
+        buf = ctypes.create_string_buffer(64)
+        for k in range(lib().dp_profile_count(self.handle)):
+            ms = ctypes.c_double()
+            n = ctypes.c_long()
+            _check(lib().dp_profile_read(self.handle, k, buf, 64, ctypes.byref(ms), ctypes.byref(n)))
+            out[buf.value.decode()] = (ms.value, n.value)
+        return out
+
+    def launch_count(self) -> int:
+        return int(lib().dp_launch_count(self.handle))
+
+    def build_nlist(self, coord, atype, box, stream=None) -> NList:
+        N = int(coord.shape[0])
+        h = ctypes.c_void_p()
+        ov = ctypes.c_int(0)
+        boxp = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+        _check(lib().dp_build_nlist(self.handle, N, _ptr(coord), _ptr(atype), _ptr(boxp), ctypes.byref(h),
+                                    ctypes.byref(ov), _stream_handle(stream)), allow=(DP_E_SEL_OVERFLOW,))
+        return NList(h, N, self.nc, ov.value)
+
+    def export_table(self) -> np.ndarray:
+        nets = self.cfg.ntypes if getattr(self.cfg, "type_one_side", 0) else self.cfg.ntypes ** 2
+        M = int(self.cfg.embed[-1])
+        lc = ctypes.c_int(0)
+        smax = 1.0 / float(self.cfg.rcut_smth)
+        n1 = int(np.floor(0.9 * smax / 0.01 + 0.5))
+        n2 = max(1, int(np.ceil((smax - n1 * 0.01) / 0.1 - 1e-9)))
+        out = np.zeros(nets * (n1 + n2) * M * 6)
+        _check(lib().dp_model_export_table(self.handle, out.ctypes.data, ctypes.byref(lc)))
+        return out[: nets * lc.value * M * 6].reshape(nets, lc.value, M, 6)
+
+    def compute(self, coord, atype, box, nlist: Optional[NList] = None, atom_energy: bool = False, stream=None,
+                out=None, allow=(DP_E_SEL_OVERFLOW,)):
+        """Energy, forces [N,3] and virial [3,3] (and per-atom energies).
+
+        Host (numpy) inputs give numpy outputs; torch CUDA inputs give torch CUDA outputs
+        written in place by the kernels (pass `out=(e, f, v, ae)` to reuse buffers)."""
+        N = int(coord.shape[0])
+        boxp = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+        if _is_torch(coord) and coord.is_cuda:
+            import torch
+            if out is None:
+                e = torch.empty(1, dtype=torch.float64, device=coord.device)
+                f = torch.empty((N, 3), dtype=torch.float64, device=coord.device)
+                v = torch.empty((3, 3), dtype=torch.float64, device=coord.device)
+                ae = torch.empty(N, dtype=torch.float64, device=coord.device) if atom_energy else None
+            else:
+                e, f, v, ae = out
+        else:
+            coord = np.ascontiguousarray(coord, dtype=np.float64)
+            atype = np.ascontiguousarray(atype, dtype=np.int32)
+            if out is None:
+                e = np.zeros(1)
+                f = np.zeros((N, 3))
+                v = np.zeros((3, 3))
+                ae = np.zeros(N) if atom_energy else None
+            else:
+                e, f, v, ae = out
+        code = lib().dp_compute(self.handle, nlist.handle if nlist is not None else None, N, _ptr(coord), _ptr(atype),
+                                _ptr(boxp), _ptr(e), _ptr(f), _ptr(v), _ptr(ae), _stream_handle(stream))
+        _check(code, allow=allow)
+        self.last_status = code
+        return e, f, v, ae
+
+
+def n_params(cfg) -> int:
+    c = Config.from_model(cfg)
+    return int(lib().dp_model_n_params(ctypes.byref(c)))
+
+
+def write_weight_file(path: str, cfg, params: np.ndarray) -> None:
+    """Weight file read by dp_init_model: magic, dp_model_config, int64 n, n FP64."""
+    c = Config.from_model(cfg)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    with open(path, "wb") as fh:
+        fh.write(b"DPGBW001")
+        fh.write(bytes(c))
+        fh.write(np.int64(p.size).tobytes())
+        fh.write(p.tobytes())
+
+
+def load_model_file(path: str, device: int = 0, precision: str = "fp64", compressed: bool = False):
+    h = ctypes.c_void_p()
+    _check(lib().dp_init_model(path.encode(), device, PREC[precision], 1 if compressed else 0, ctypes.byref(h)))
+    return h
