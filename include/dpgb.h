@@ -109,6 +109,29 @@ long dp_model_n_params(const dp_model_config* cfg);
 int dp_build_nlist(dp_model* model, int natoms, const double* coord, const int* type, const double* box,
                    dp_nlist** out, int* n_overflow, void* stream);
 
+/* ---- neighbour list without any allocation ----
+ * The paper has no counterpart to this entry point.  It is for callers that cannot
+ * allocate device memory at the point where they need a list: an MD engine that owns all
+ * device memory and forbids other allocations, or a loop being captured into a CUDA graph.
+ * It computes exactly what dp_build_nlist computes (same kernels, same bit-exact result)
+ * but needs no model object and calls no allocating routine: its cell-list scratch is one
+ * static device array of about 10.5 MiB that every GPU loading the library keeps until exit.
+ *   cfg: only ntypes, sel and rcut are used.
+ *   coord [natoms*3] FP64, type [natoms]: device pointers.  box: host pointer (or NULL for
+ *   open boundaries).  nl_j [natoms*Nc], nl_shift [natoms*Nc*3] int32: device pointers the
+ *   caller owns, filled exactly as dp_nlist_export fills its host arrays.
+ * Limits: natoms <= DP_NOALLOC_MAX_ATOMS, natoms*Nc <= DP_NOALLOC_MAX_SLOTS, cell grid <=
+ * DP_NOALLOC_MAX_CELLS cells; larger frames are rejected with DP_E_ARG and a message.
+ * The first call on a device looks up the array's device address (one-time set-up), so
+ * make that first call before any stream capture.  All calls on a device share the array:
+ * calls that overlap on the GPU race with each other; serialise them (one stream, or
+ * events).  Returns as dp_build_nlist; the call synchronises `stream` to read its status. */
+#define DP_NOALLOC_MAX_ATOMS 32768
+#define DP_NOALLOC_MAX_SLOTS 2097152
+#define DP_NOALLOC_MAX_CELLS 32768
+int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, const double* coord, const int* type,
+                           const double* box, int* nl_j, int* nl_shift, int* n_overflow, void* stream);
+
 /* Copy a neighbour list to host arrays nl_j [natoms*Nc] and nl_shift [natoms*Nc*3]. */
 int dp_nlist_export(const dp_nlist* nlist, int* nl_j, int* nl_shift);
 

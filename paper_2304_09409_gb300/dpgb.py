@@ -31,6 +31,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 EXPORTED = [
     "dp_model_create", "dp_init_model", "dp_free_model", "dp_model_n_params", "dp_build_nlist",
     "dp_nlist_export", "dp_free_nlist", "dp_compute", "dp_model_export_table", "dp_last_error",
+    "dp_build_nlist_noalloc",
 ]
 
 
@@ -281,3 +282,27 @@ def load_model_file(path: str, device: int = 0, precision: str = "fp64", compres
     h = ctypes.c_void_p()
     _check(lib().dp_init_model(path.encode(), device, PREC[precision], 1 if compressed else 0, ctypes.byref(h)))
     return h
+
+
+def build_nlist_noalloc(cfg, coord, atype, box, nl_j=None, nl_shift=None, stream=None):
+    """dp_build_nlist_noalloc: neighbour list of a frame whose coordinates and types are
+    torch CUDA tensors, written into caller-owned device buffers (allocated here with torch
+    when not given).  The library call itself allocates nothing."""
+    import torch
+    c = Config.from_model(cfg)
+    N = int(coord.shape[0])
+    nc = int(sum(cfg.sel))
+    if nl_j is None:
+        nl_j = torch.empty((N, nc), dtype=torch.int32, device=coord.device)
+    if nl_shift is None:
+        nl_shift = torch.empty((N, nc, 3), dtype=torch.int32, device=coord.device)
+    boxp = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    ov = ctypes.c_int(0)
+    L = lib()
+    L.dp_build_nlist_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.c_void_p]
+    _check(L.dp_build_nlist_noalloc(ctypes.byref(c), N, _ptr(coord), _ptr(atype), _ptr(boxp), _ptr(nl_j),
+                                    _ptr(nl_shift), ctypes.byref(ov), _stream_handle(stream)),
+           allow=(DP_E_SEL_OVERFLOW,))
+    return nl_j, nl_shift, ov.value
