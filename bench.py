@@ -250,7 +250,8 @@ def run_ours(args):
     m64.free()
 
     cands = {}
-    for name, prec, comp in (("fp32", "fp32", False), ("fp32-compressed", "fp32", True)):
+    for name, prec, comp in (("fp32", "fp32", False), ("fp32-compressed", "fp32", True),
+                             ("bf16-compressed", "bf16", True)):
         m = dpgb.Model(cfg, params, device=local, precision=prec, compressed=comp)
         ms, _, _, out = time_path(m, coord, atype, big.box, steps=3, warmup=2, flush=flush)
         err = float(np.abs(out[1].cpu().numpy() - f64).max())
@@ -327,7 +328,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if sel["prec"] == "fp32" else sel["prec"], "data": "synthetic",
+        "dtype": {"fp32": "f32", "bf16": "bf16+f32"}.get(sel["prec"], sel["prec"]), "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "natoms_per_gpu": big.natoms, "path": best,
                    "l2": "512 MB buffer written between timed steps (L2 flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -152,6 +152,15 @@ int dp_compute(dp_model* model, dp_nlist* nlist, int natoms, const double* coord
  * Returns DP_E_ARG for an uncompressed model. */
 int dp_model_export_table(const dp_model* model, double* out, int* n_intervals);
 
+/* ---- tensor-core GEMM used by the fitting net ----
+ * C[rows][N] = A[rows][K] . B[K][N] with BF16 operands and FP32 accumulation on the tcgen05
+ * tensor cores (the dense layers of Eq. (NN) in the fitting net are this product plus a
+ * fused epilogue).  A is [rows][K] row-major, Bt is B transposed ([N][K] row-major), C is
+ * [rows][N] row-major FP32; all three are device pointers, K a multiple of 8, both row
+ * pitches 16-byte aligned.  Synchronises `stream`.  DP_E_TIMEOUT if a bounded pipeline wait
+ * of the kernel gave up (the result is then invalid). */
+int dp_gemm_bf16(int rows, int K, int N, const void* A, const void* Bt, float* C, void* stream);
+
 /* ---- tracing (no counterpart in the paper; its TensorBoard profiles play this role) ----
  * dp_profile_enable: when on, every kernel launch of the model's calls is bracketed by CUDA
  * events on the launch stream; per-kernel-name totals are folded in when a call

@@ -6,8 +6,10 @@
 #include <vector>
 
 #include "dp_internal.cuh"
+#include "fit_tc.cuh"
 #include "path.cuh"
 #include "table.cuh"
+#include "tc_gemm.cuh"
 
 struct dp_model {
   dpgb::DeviceModel m;
@@ -16,6 +18,9 @@ struct dp_model {
   dpgb::DevStatus* status = nullptr;  // device
   dpgb::DevStatus* status_host = nullptr;  // pinned
   dpgb::Prof prof;
+  // set once a frame overflowed the density-sized candidate buffer: later builds use the
+  // full DP_MAX_CANDIDATES buffer
+  bool nl_full_cap = false;
 };
 
 struct dp_nlist {
@@ -30,6 +35,9 @@ namespace dpgb {
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+// error word of the stand-alone tensor-core GEMM entry point
+__device__ int g_gemm_err;
 
 namespace {
 
@@ -193,7 +201,9 @@ int frame_geometry(dp_model* md, int N, const double* dcoord, const double* box,
     DP_CUDA_TRY(cudaMemcpyAsync(lohi, dbbox, sizeof(lohi), cudaMemcpyDeviceToHost, st));
     DP_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  return host_geometry(md->m.cfg, N, box, lohi, g);
+  const int rc = host_geometry(md->m.cfg, N, box, lohi, g);
+  if (md->nl_full_cap) g.cap = DP_MAX_CANDIDATES;
+  return rc;
 }
 
 // Host-side per-type atom counts when types are on the host; else read back.
@@ -271,8 +281,8 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   m.M = cfg->embed[cfg->n_embed - 1];
   m.A = cfg->axis;
   m.n_embed_nets = cfg->type_one_side ? cfg->ntypes : cfg->ntypes * cfg->ntypes;
-  if (precision == DP_PREC_TF32 || precision == DP_PREC_BF16) {
-    set_error("tensor-core precisions are not available in this build");
+  if (precision == DP_PREC_TF32 || (precision == DP_PREC_BF16 && !compressed)) {
+    set_error("this precision needs the compressed embedding (BF16) or is not available (TF32)");
     delete md;
     return DP_E_UNSUPPORTED;
   }
@@ -296,6 +306,17 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   }
   if (compressed) {
     int rc = build_tables(m);
+    if (rc != DP_OK) {
+      dp_free_model(md);
+      return rc;
+    }
+  }
+  for (int t = 0; t < cfg->ntypes; ++t) {
+    const LayerDesc& Lo = m.fit[(size_t)t * m.n_fit_layers + m.n_fit_layers - 1];
+    m.fit_out_bias[t] = (float)params[Lo.w_off + Lo.n_in];
+  }
+  if (precision == DP_PREC_BF16) {
+    int rc = prepare_fit_bf16(m, params);
     if (rc != DP_OK) {
       dp_free_model(md);
       return rc;
@@ -332,6 +353,41 @@ int dp_init_model(const char* path, int device, int precision, int compressed, d
     return DP_E_ARG;
   }
   return dp_model_create(&cfg, p.data(), (long)n, device, precision, compressed, out);
+}
+
+int dp_gemm_bf16(int rows, int K, int N, const void* A, const void* Bt, float* C, void* stream) {
+  if (rows < 1 || K < 8 || K % 8 || N < 1 || !is_device_ptr(A) || !is_device_ptr(Bt) || !is_device_ptr(C)) {
+    set_error("dp_gemm_bf16: device pointers, rows >= 1, K a multiple of 8, N >= 1");
+    return DP_E_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  DP_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_gemm_err));
+  TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.ntypes = 1;
+  a.row_start[1] = rows;
+  a.tile_start[1] = (rows + 127) / 128;
+  a.K = K;
+  a.N = N;
+  a.BN = tc_pick_bn(N, a.tile_start[1], false);
+  a.out_f32 = C;
+  a.err = err;
+  CUtensorMap ta;
+  TcMaps tb;
+  int rc = make_tmap_bf16(&ta, A, rows, K, 128);
+  if (rc == DP_OK) rc = make_tmap_bf16(&tb.m[0], Bt, N, K, a.BN);
+  if (rc != DP_OK) return rc;
+  DP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  DP_CUDA_TRY(launch_tc_gemm(TC_EPI_PLAIN, ta, tb, a, st));
+  int herr = 0;
+  DP_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("tensor-core GEMM: a bounded pipeline wait timed out");
+    return DP_E_TIMEOUT;
+  }
+  return DP_OK;
 }
 
 int dp_model_export_table(const dp_model* md, double* out, int* n_intervals) {
@@ -379,6 +435,8 @@ int dp_free_model(dp_model* md) {
   cudaFree(md->m.p32);
   cudaFree(md->m.tab64);
   cudaFree(md->m.tab32);
+  cudaFree(md->m.fit_wt_bf16);
+  cudaFree(md->m.fit_w_bf16);
   cudaFree(md->ws);
   cudaFree(md->status);
   if (md->status_host) cudaFreeHost(md->status_host);
@@ -439,6 +497,10 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
   rc = read_status(md, st, n_overflow);
   if (rc != DP_OK && rc != DP_E_SEL_OVERFLOW) {
     dp_free_nlist(nl);
+    if (rc == DP_E_CAPACITY && !md->nl_full_cap) {
+      md->nl_full_cap = true;  // retry once with the full candidate buffer
+      return dp_build_nlist(md, N, coord, type, box, out, n_overflow, stream);
+    }
     return rc;
   }
   *out = nl;
@@ -564,7 +626,12 @@ int dp_compute(dp_model* md, dp_nlist* nlist, int N, const double* coord, const 
   if (host_f) DP_CUDA_TRY(cudaMemcpyAsync(force, io.force, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
   if (host_ae)
     DP_CUDA_TRY(cudaMemcpyAsync(atom_energy, io.atom_energy, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  return read_status(md, st, nullptr);
+  rc = read_status(md, st, nullptr);
+  if (rc == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
+    md->nl_full_cap = true;  // retry once with the full candidate buffer
+    return dp_compute(md, nlist, N, coord, type, box, energy, force, virial, atom_energy, stream);
+  }
+  return rc;
 }
 
 }  // extern "C"

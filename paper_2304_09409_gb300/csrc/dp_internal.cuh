@@ -29,6 +29,7 @@ struct NlGeom {
   int K[3];          // virtual-cell search half-width per axis
   double rc2;        // r_c^2 (exact membership test)
   float rc2_loose;   // (r_c + 1e-3)^2 (FP32 prefilter)
+  int cap;           // candidate buffer per centre atom (rounded up to 128..DP_MAX_CANDIDATES)
 };
 
 // Image shift (n0, n1, n2) packed as 10-bit offsets; |n| < 512.
@@ -95,6 +96,14 @@ struct DeviceModel {
   TableDesc tab{};
   double* tab64 = nullptr;  // [nets][lc][M][6]
   float* tab32 = nullptr;
+  // BF16 operands of the tensor-core fitting net: per (type, hidden layer) W^T [n_out][n_in]
+  // (forward) and W [n_in][n_out] (backward), at fit_bf16_off[type * n_fit + layer].
+  void* fit_wt_bf16 = nullptr;
+  void* fit_w_bf16 = nullptr;
+  float fit_out_bias[DP_MAX_TYPES] = {};  // bias of the final linear layer, per type
+  std::vector<long> fit_bf16_off;
+  // tensor maps of those operands, keyed by (type, layer, direction, box rows)
+  mutable std::vector<std::pair<long, std::vector<unsigned char>>> tmap_cache;
 };
 
 // ------------------------------------------------------------------------------------------

@@ -135,12 +135,12 @@ struct KeyLess {
   }
 };
 
+template <int CAP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_nlist(NlGeom g, const double* __restrict__ coord, const int* __restrict__ type,
             const int* __restrict__ cell_start, const int* __restrict__ cell_atoms, const int* __restrict__ atom_cell,
             const int* __restrict__ atom_img, const float4* __restrict__ atom_wf, int* __restrict__ nl_j,
             int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
-  constexpr int CAP = DP_MAX_CANDIDATES;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned long long* k_r2 = reinterpret_cast<unsigned long long*>(smem) + (size_t)warp * CAP;
@@ -148,8 +148,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   int* k_code = reinterpret_cast<int*>(smem + (size_t)kWarpsPerBlock * CAP * 12) + (size_t)warp * CAP;
   unsigned char* k_t = smem + (size_t)kWarpsPerBlock * CAP * 16 + (size_t)warp * CAP;
 
-  const int i = blockIdx.x * kWarpsPerBlock + warp;
-  if (i >= g.natoms) return;  // warp-uniform
+  const int w = blockIdx.x * kWarpsPerBlock + warp;
+  if (w >= g.natoms) return;  // warp-uniform
+  // consecutive warps take atoms of the same cell, so their candidates share the L1 cache
+  const int i = cell_atoms[w];
 
   const double xi[3] = {coord[3 * i], coord[3 * i + 1], coord[3 * i + 2]};
   const int mi0 = atom_img[3 * i], mi1 = atom_img[3 * i + 1], mi2 = atom_img[3 * i + 2];
@@ -355,6 +357,9 @@ int host_geometry(const dp_model_config& cfg, int natoms, const double* box, con
       total *= n;
     }
     (void)total;
+    // candidate buffer: twice the mean neighbour count of this density, plus a margin
+    const double expect = natoms / vol * (4.0 / 3.0) * 3.141592653589793 * rc * rc * rc;
+    g.cap = (int)(2.0 * expect + 32.0);
   } else {
     g.periodic = 0;
     for (int d = 0; d < 3; ++d) {
@@ -367,6 +372,7 @@ int host_geometry(const dp_model_config& cfg, int natoms, const double* box, con
       g.ncell[d] = n;
       g.K[d] = 1;
     }
+    g.cap = DP_MAX_CANDIDATES;  // clusters: no meaningful density
     g.hf[0] = (float)g.ext[0];
     g.hf[4] = (float)g.ext[1];
     g.hf[8] = (float)g.ext[2];
@@ -390,11 +396,25 @@ cudaError_t launch_nlist_build(const NlGeom& g, const double* coord, const int* 
   k_bin<<<nb, 256, 0, st>>>(g, coord, cell_count, atom_cell, atom_img, atom_wf);
   k_scan_excl<<<1, 1024, 0, st>>>(cell_count, ncells, cell_start, cell_cursor);
   k_fill<<<nb, 256, 0, st>>>(g.natoms, atom_cell, cell_cursor, cell_atoms);
-  const size_t smem = (size_t)kWarpsPerBlock * DP_MAX_CANDIDATES * 17;
-  e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_nlist<<<(g.natoms + kWarpsPerBlock - 1) / kWarpsPerBlock, kWarpsPerBlock * 32, smem, st>>>(
-      g, coord, type, cell_start, cell_atoms, atom_cell, atom_img, atom_wf, nl_j, nl_code, counts, status);
+  const int cap = g.cap <= 128 ? 128 : (g.cap <= 256 ? 256 : (g.cap <= 512 ? 512 : 1024));
+  const size_t smem = (size_t)kWarpsPerBlock * cap * 17;
+  const unsigned blocks = (g.natoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
+#define DPGB_NL_LAUNCH(C)                                                                                  \
+  do {                                                                                                     \
+    e = cudaFuncSetAttribute(k_nlist<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+    if (e != cudaSuccess) return e;                                                                        \
+    k_nlist<C><<<blocks, kWarpsPerBlock * 32, smem, st>>>(g, coord, type, cell_start, cell_atoms, atom_cell, \
+                                                         atom_img, atom_wf, nl_j, nl_code, counts, status); \
+  } while (0)
+  if (cap == 128)
+    DPGB_NL_LAUNCH(128);
+  else if (cap == 256)
+    DPGB_NL_LAUNCH(256);
+  else if (cap == 512)
+    DPGB_NL_LAUNCH(512);
+  else
+    DPGB_NL_LAUNCH(1024);
+#undef DPGB_NL_LAUNCH
   return cudaGetLastError();
 }
 

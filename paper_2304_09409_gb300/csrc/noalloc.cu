@@ -141,6 +141,7 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   NlGeom g;
   rc = host_geometry(*cfg, natoms, box, lohi, g);
   if (rc != DP_OK) return rc;
+  g.cap = DP_MAX_CANDIDATES;  // one pass, never a retry
   if ((long)g.ncell[0] * g.ncell[1] * g.ncell[2] > kMaxCells) {
     set_error("cell grid larger than the no-allocation limit of " + std::to_string(kMaxCells) + " cells");
     return DP_E_ARG;

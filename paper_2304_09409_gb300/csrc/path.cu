@@ -462,6 +462,12 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   return DP_OK;
 }
 
+cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
+                              cudaStream_t st) {
+  k_energy<float><<<1, 1024, 0, st>>>(Esorted, perm, n, atom_e, energy);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sum_rows(const double* in, long n, int w, double* out, cudaStream_t st) {
   k_sum_rows<<<1, 1024, 0, st>>>(in, n, w, out);
   return cudaGetLastError();

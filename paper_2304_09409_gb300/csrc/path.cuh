@@ -171,6 +171,9 @@ template <class R>
 int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, const R* D, const PathIO& io, Arena& ar,
                 cudaStream_t st, const R** gD_out);
 cudaError_t launch_sum_rows(const double* in, long n, int w, double* out, cudaStream_t st);
+// Per-atom energies (sorted order, FP32) to input order and their FP64 sum.
+cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
+                              cudaStream_t st);
 
 template <class R>
 int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, const PathIO& io, Arena& ar,

@@ -12,9 +12,13 @@
 // each take one neighbour, recompute G and G' from the table, reduce dE/dR and dE/ds over
 // the eight lanes, and scatter the pair force with FP64 atomics; F_i is accumulated in
 // registers and written once per atom.
+#include <cuda_bf16.h>
+
+#include <type_traits>
 #include <vector>
 
 #include "env.cuh"
+#include "fit_tc.cuh"
 #include "table.cuh"
 
 namespace dpgb {
@@ -160,11 +164,20 @@ __device__ __forceinline__ R horner_value(const R* __restrict__ c, int M, int m,
 }
 
 // ---- forward: T = G^T R / Nc with G from the table, then D = T T_<^T --------------------------
-template <class R, int MPL>
+template <class DT, class R>
+__device__ __forceinline__ DT to_dt(R v) {
+  return (DT)v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_dt<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+template <class R, int MPL, class DT>
 __global__ void __launch_bounds__(128)
     k_tab_fwd(PathConst pc, TabConst tc, const R* __restrict__ tab, const double* __restrict__ coord,
               const int* __restrict__ perm, const int* __restrict__ type, const int* __restrict__ nl_j,
-              const int* __restrict__ nl_code, R* __restrict__ Tm, R* __restrict__ D, DevStatus* __restrict__ st) {
+              const int* __restrict__ nl_code, R* __restrict__ Tm, DT* __restrict__ D, DevStatus* __restrict__ st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * 4 + warp;
   if (p >= pc.natoms) return;
@@ -233,14 +246,14 @@ __global__ void __launch_bounds__(128)
     if (m < M) reinterpret_cast<typename Vec4<R>::T*>(Tm)[(long)p * M + m] =
         Vec4<R>::make(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
   }
-  R* Dp = D + (long)p * M * A;
+  DT* Dp = D + (long)p * M * A;
   for (int lq = 0; lq < A; ++lq) {
     const R t0 = __shfl_sync(0xffffffffu, acc[0][0], lq), t1 = __shfl_sync(0xffffffffu, acc[0][1], lq);
     const R t2 = __shfl_sync(0xffffffffu, acc[0][2], lq), t3 = __shfl_sync(0xffffffffu, acc[0][3], lq);
 #pragma unroll
     for (int u = 0; u < MPL; ++u) {
       const int m = lane + 32 * u;
-      if (m < M) Dp[m * A + lq] = acc[u][0] * t0 + acc[u][1] * t1 + acc[u][2] * t2 + acc[u][3] * t3;
+      if (m < M) Dp[m * A + lq] = to_dt<DT, R>(acc[u][0] * t0 + acc[u][1] * t1 + acc[u][2] * t2 + acc[u][3] * t3);
     }
   }
 }
@@ -394,17 +407,25 @@ __global__ void __launch_bounds__(128)
         sv[0][threadIdx.x] + sv[1][threadIdx.x] + sv[2][threadIdx.x] + sv[3][threadIdx.x];
 }
 
-template <class R>
+template <class R, class DT>
 int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& ar, cudaStream_t st,
             const R* params, const R* tab) {
+  constexpr bool kTensor = std::is_same<DT, __nv_bfloat16>::value;
   const long N = pc.natoms;
   const int M = pc.M, A = pc.A;
   R* Tm = ar.get<R>(N * M * 4);
-  R* D = ar.get<R>(N * M * A);
+  DT* D = ar.get<DT>(N * M * A);
   const unsigned blocks = (unsigned)((N + 3) / 4);
   double* vpart = ar.get<double>((long)blocks * 9);
   const R* gD = nullptr;
-  if (ar.measure) return run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
+  if (ar.measure) {
+    if constexpr (kTensor) {
+      const float* g = nullptr;
+      return run_fitting_tc(m, pc, D, io, ar, st, &g);
+    } else {
+      return run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
+    }
+  }
   if (!ar.ok()) {
     set_error("scratch allocation failed");
     return DP_E_OOM;
@@ -412,22 +433,29 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const TabConst tc = tab_const(m);
   const int mpl = (M + 31) / 32;
   {
-  ProfScope _ps(io.prof, "tab_fwd", st);
-  if (mpl <= 1)
-    k_tab_fwd<R, 1><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm, D,
-                                            io.status);
-  else if (mpl <= 2)
-    k_tab_fwd<R, 2><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm, D,
-                                            io.status);
-  else if (mpl <= 4)
-    k_tab_fwd<R, 4><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm, D,
-                                            io.status);
-  else
-    k_tab_fwd<R, 8><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm, D,
-                                            io.status);
+    ProfScope _ps(io.prof, "tab_fwd", st);
+    if (mpl <= 1)
+      k_tab_fwd<R, 1, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+                                                  D, io.status);
+    else if (mpl <= 2)
+      k_tab_fwd<R, 2, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+                                                  D, io.status);
+    else if (mpl <= 4)
+      k_tab_fwd<R, 4, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+                                                  D, io.status);
+    else
+      k_tab_fwd<R, 8, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+                                                  D, io.status);
   }
   DP_CUDA_TRY(cudaGetLastError());
-  int rc = run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
+  int rc;
+  if constexpr (kTensor) {
+    const float* g = nullptr;
+    rc = run_fitting_tc(m, pc, D, io, ar, st, &g);
+    gD = g;
+  } else {
+    rc = run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
+  }
   if (rc != DP_OK) return rc;
   const size_t smem = sizeof(R) * 4 * (size_t)(M * 8 + M * A);
   DP_CUDA_TRY(cudaFuncSetAttribute(k_tab_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -506,8 +534,9 @@ int export_tables(const DeviceModel& m, double* out) {
 }
 
 int run_compressed(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& ar, cudaStream_t st) {
-  if (m.precision == DP_PREC_FP64) return run_tab<double>(m, pc, io, ar, st, m.p64, m.tab64);
-  return run_tab<float>(m, pc, io, ar, st, m.p32, m.tab32);
+  if (m.precision == DP_PREC_FP64) return run_tab<double, double>(m, pc, io, ar, st, m.p64, m.tab64);
+  if (m.precision == DP_PREC_BF16) return run_tab<float, __nv_bfloat16>(m, pc, io, ar, st, m.p32, m.tab32);
+  return run_tab<float, float>(m, pc, io, ar, st, m.p32, m.tab32);
 }
 
 }  // namespace dpgb
