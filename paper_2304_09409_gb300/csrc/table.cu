@@ -30,6 +30,10 @@ struct TabConst {
   int n1, n2, lc;
 };
 
+// Coefficients of one (interval, output) pair: a..f padded to 8 values (two 16-byte loads in
+// FP32), table layout [net][interval][output][8].
+constexpr int kCoefStride = 8;
+
 TabConst tab_const(const DeviceModel& m) {
   TabConst c;
   c.s0 = m.tab.s0;
@@ -127,12 +131,37 @@ __global__ void k_table_coef(TabConst tc, int M, int nets, const double* __restr
   c[3] = 0.5 * dd0;
   c[4] = d0;
   c[5] = y[a];
-  const size_t o = (((size_t)net * tc.lc + l) * 6) * M + m;
+  const size_t o = (((size_t)net * tc.lc + l) * M + m) * kCoefStride;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    tab64[o + (size_t)q * M] = c[q];
-    tab32[o + (size_t)q * M] = (float)c[q];
+  for (int q = 0; q < kCoefStride; ++q) {
+    tab64[o + q] = q < 6 ? c[q] : 0.0;
+    tab32[o + q] = q < 6 ? (float)c[q] : 0.f;
   }
+}
+
+// One interval's coefficients of one output, loaded with 16-byte vector loads.
+template <class R>
+struct Quint {
+  R a, b, c, d, e, f;
+};
+__device__ __forceinline__ Quint<float> load_quint(const float* __restrict__ p) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  const float4 y = *reinterpret_cast<const float4*>(p + 4);
+  return Quint<float>{x.x, x.y, x.z, x.w, y.x, y.y};
+}
+__device__ __forceinline__ Quint<double> load_quint(const double* __restrict__ p) {
+  const double2 x = reinterpret_cast<const double2*>(p)[0];
+  const double2 y = reinterpret_cast<const double2*>(p)[1];
+  const double2 z = reinterpret_cast<const double2*>(p)[2];
+  return Quint<double>{x.x, x.y, y.x, y.y, z.x, z.y};
+}
+template <class R>
+__device__ __forceinline__ R quint_value(const Quint<R>& q, R t) {
+  return ((((q.a * t + q.b) * t + q.c) * t + q.d) * t + q.e) * t + q.f;
+}
+template <class R>
+__device__ __forceinline__ R quint_slope(const Quint<R>& q, R t) {
+  return (((R(5) * q.a * t + R(4) * q.b) * t + R(3) * q.c) * t + R(2) * q.d) * t + q.e;
 }
 
 template <class R>
@@ -151,17 +180,6 @@ __device__ __forceinline__ int tab_interval(const TabConst& tc, R s, R& tt, bool
   return l;
 }
 
-template <class R>
-__device__ __forceinline__ void horner(const R* __restrict__ c, int M, int m, R t, R& g, R& gp) {
-  const R a = c[m], b = c[M + m], cc = c[2 * M + m], d = c[3 * M + m], e = c[4 * M + m], f = c[5 * M + m];
-  g = ((((a * t + b) * t + cc) * t + d) * t + e) * t + f;
-  gp = (((R(5) * a * t + R(4) * b) * t + R(3) * cc) * t + R(2) * d) * t + e;
-}
-
-template <class R>
-__device__ __forceinline__ R horner_value(const R* __restrict__ c, int M, int m, R t) {
-  return ((((c[m] * t + c[M + m]) * t + c[2 * M + m]) * t + c[3 * M + m]) * t + c[4 * M + m]) * t + c[5 * M + m];
-}
 
 // ---- forward: T = G^T R / Nc with G from the table, then D = T T_<^T --------------------------
 template <class DT, class R>
@@ -188,9 +206,11 @@ __global__ void __launch_bounds__(128)
   for (int u = 0; u < MPL; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = R(0);
   bool oor = false;
   const double* xi = coord + 3 * i;
+  Quint<R> cq[MPL];  // coefficients of the current interval for this lane's outputs
   for (int t = 0; t < pc.ntypes; ++t) {
-    const R* tabn = tab + (size_t)net_of(pc, ti, t) * tc.lc * 6 * M;
+    const R* tabn = tab + (size_t)net_of(pc, ti, t) * tc.lc * M * kCoefStride;
     const int kend = pc.sel_off[t + 1];
+    int cur = -1;  // interval whose coefficients sit in cq (warp-uniform)
     for (int base = pc.sel_off[t]; base < kend; base += 32) {
       const int k = base + lane;
       const int j = (k < kend) ? nl_j[(long)i * nc + k] : -1;
@@ -218,12 +238,20 @@ __global__ void __launch_bounds__(128)
         const int lq = __shfl_sync(0xffffffffu, l, q);
         const R r0 = __shfl_sync(0xffffffffu, e0, q), r1 = __shfl_sync(0xffffffffu, e1, q);
         const R r2 = __shfl_sync(0xffffffffu, e2, q), r3 = __shfl_sync(0xffffffffu, e3, q);
-        const R* c = tabn + (size_t)lq * 6 * M;
+        if (lq != cur) {  // neighbours are sorted by distance: runs share an interval
+          cur = lq;
+          const R* c = tabn + (size_t)lq * M * kCoefStride;
+#pragma unroll
+          for (int u = 0; u < MPL; ++u) {
+            const int m = lane + 32 * u;
+            if (m < M) cq[u] = load_quint(c + (size_t)m * kCoefStride);
+          }
+        }
 #pragma unroll
         for (int u = 0; u < MPL; ++u) {
           const int m = lane + 32 * u;
           if (m < M) {
-            const R g = horner_value<R>(c, M, m, tq);
+            const R g = quint_value<R>(cq[u], tq);
             acc[u][0] += g * r0;
             acc[u][1] += g * r1;
             acc[u][2] += g * r2;
@@ -268,9 +296,8 @@ __global__ void __launch_bounds__(128)
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = pc.M, nc = pc.nc, A = pc.A;
-  R* Ts = reinterpret_cast<R*>(sm_raw) + (size_t)warp * (M * 8 + M * A);
+  R* Ts = reinterpret_cast<R*>(sm_raw) + (size_t)warp * (M * 8);
   R* gTs = Ts + M * 4;
-  R* gDs = gTs + M * 4;
   const int p = blockIdx.x * 4 + warp;
   double v[9];
 #pragma unroll
@@ -278,14 +305,15 @@ __global__ void __launch_bounds__(128)
   if (p < pc.natoms) {
     const int i = perm[p], ti = type[i];
     for (int e = lane; e < M * 4; e += 32) Ts[e] = Tm[(long)p * M * 4 + e];
-    for (int e = lane; e < M * A; e += 32) gDs[e] = gD[(long)p * M * A + e];
     __syncwarp();
+    // dE/dT[m][c] = sum_l dE/dD[m][l] T[l][c] + [m < M_<] sum_q dE/dD[q][m] T[q][c]
+    const R* gDp = gD + (long)p * M * A;
     for (int e = lane; e < M * 4; e += 32) {
       const int m = e >> 2, c = e & 3;
       R acc = 0;
-      for (int lq = 0; lq < A; ++lq) acc += gDs[m * A + lq] * Ts[lq * 4 + c];
+      for (int lq = 0; lq < A; ++lq) acc += gDp[m * A + lq] * Ts[lq * 4 + c];
       if (m < A)
-        for (int q = 0; q < M; ++q) acc += gDs[q * A + m] * Ts[q * 4 + c];
+        for (int q = 0; q < M; ++q) acc += gDp[q * A + m] * Ts[q * 4 + c];
       gTs[e] = acc;
     }
     __syncwarp();
@@ -294,7 +322,7 @@ __global__ void __launch_bounds__(128)
     double fi0 = 0.0, fi1 = 0.0, fi2 = 0.0;
     const double* xi = coord + 3 * i;
     for (int t = 0; t < pc.ntypes; ++t) {
-      const R* tabn = tab + (size_t)net_of(pc, ti, t) * tc.lc * 6 * M;
+      const R* tabn = tab + (size_t)net_of(pc, ti, t) * tc.lc * M * kCoefStride;
       const int kend = pc.sel_off[t + 1];
       for (int base = pc.sel_off[t]; base < kend; base += 32) {
         const int k = base + lane;
@@ -334,12 +362,13 @@ __global__ void __launch_bounds__(128)
           const double dq2 = __shfl_sync(0xffffffffu, d2, q);
           R g0 = 0, g1 = 0, g2 = 0, g3 = 0, gse = 0;
           if (have) {
-            const R* c = tabn + (size_t)lq * 6 * M;
+            const R* c = tabn + (size_t)lq * M * kCoefStride;
             const R e1 = sq * uq0, e2 = sq * uq1, e3 = sq * uq2;
             for (int m = sub; m < M; m += 8) {
-              R G, Gp;
-              horner<R>(c, M, m, tq, G, Gp);
-              const R a0 = gTs[m * 4], a1 = gTs[m * 4 + 1], a2 = gTs[m * 4 + 2], a3 = gTs[m * 4 + 3];
+              const Quint<R> cq = load_quint(c + (size_t)m * kCoefStride);
+              const R G = quint_value<R>(cq, tq), Gp = quint_slope<R>(cq, tq);
+              const typename Vec4<R>::T g4 = reinterpret_cast<const typename Vec4<R>::T*>(gTs)[m];
+              const R a0 = g4.x, a1 = g4.y, a2 = g4.z, a3 = g4.w;
               g0 += a0 * G;
               g1 += a1 * G;
               g2 += a2 * G;
@@ -457,7 +486,7 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
     rc = run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
   }
   if (rc != DP_OK) return rc;
-  const size_t smem = sizeof(R) * 4 * (size_t)(M * 8 + M * A);
+  const size_t smem = sizeof(R) * 4 * (size_t)(M * 8);
   DP_CUDA_TRY(cudaFuncSetAttribute(k_tab_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     ProfScope _ps(io.prof, "tab_bwd", st);
@@ -494,7 +523,7 @@ int build_tables(DeviceModel& m) {
   for (int l = 0; l < c.n_embed; ++l) maxw = std::max(maxw, c.embed[l]);
   const int nets = m.n_embed_nets;
   const size_t nodes = (size_t)nets * (tc.lc + 1) * m.M;
-  const size_t ncoef = (size_t)nets * tc.lc * 6 * m.M;
+  const size_t ncoef = (size_t)nets * tc.lc * kCoefStride * m.M;
   double *y = nullptr, *y1 = nullptr, *y2 = nullptr;
   LayerDesc* dl = nullptr;
   DP_CUDA_TRY(cudaMalloc(&y, sizeof(double) * nodes * 3));
@@ -522,14 +551,11 @@ int export_tables(const DeviceModel& m, double* out) {
     return DP_E_ARG;
   }
   const int lc = m.tab.n1 + m.tab.n2, M = m.M;
-  const size_t ncoef = (size_t)m.n_embed_nets * lc * 6 * M;
-  std::vector<double> h(ncoef);
-  DP_CUDA_TRY(cudaMemcpy(h.data(), m.tab64, sizeof(double) * ncoef, cudaMemcpyDeviceToHost));
-  for (int net = 0; net < m.n_embed_nets; ++net)
-    for (int l = 0; l < lc; ++l)
-      for (int q = 0; q < 6; ++q)
-        for (int mm = 0; mm < M; ++mm)
-          out[(((size_t)net * lc + l) * M + mm) * 6 + q] = h[(((size_t)net * lc + l) * 6 + q) * M + mm];
+  const size_t nrow = (size_t)m.n_embed_nets * lc * M;
+  std::vector<double> h(nrow * kCoefStride);
+  DP_CUDA_TRY(cudaMemcpy(h.data(), m.tab64, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+  for (size_t r = 0; r < nrow; ++r)
+    for (int q = 0; q < 6; ++q) out[r * 6 + q] = h[r * kCoefStride + q];
   return DP_OK;
 }
 
