@@ -129,6 +129,8 @@ struct FrameBufs {
   double* virial;
   double* atom_energy;
   double* bbox;
+  double* tshift;
+  double* epart;
 };
 
 // Carve the per-call buffers that precede the path scratch.
@@ -158,6 +160,8 @@ void carve(Arena& ar, const DeviceModel& m, int N, const NlGeom* g, bool own_nli
   if (host_force) b.force = ar.get<double>(3L * N);
   if (host_ae) b.atom_energy = ar.get<double>(N);
   b.bbox = ar.get<double>(6);
+  b.tshift = ar.get<double>(81);
+  b.epart = ar.get<double>((N + 255) / 256);
 }
 
 int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
@@ -605,6 +609,11 @@ int dp_compute(dp_model* md, dp_nlist* nlist, int N, const double* coord, const 
   if (rc != DP_OK) return rc;
   for (int k = 0; k < 9; ++k) pc.h[k] = g.h[k];
   pc.periodic = g.periodic;
+  if (g.periodic) {
+    pc.tshift = b.tshift;
+    ProfScope _ps(&md->prof, "shift_table", st);
+    DP_CUDA_TRY(launch_shift_table(pc, b.tshift, st));
+  }
   io.coord = dcoord;
   io.type = dtype;
   io.perm = b.perm;
@@ -615,6 +624,7 @@ int dp_compute(dp_model* md, dp_nlist* nlist, int N, const double* coord, const 
   io.force = host_f ? b.force : force;
   io.atom_energy = atom_energy ? (host_ae ? b.atom_energy : atom_energy) : nullptr;
   io.status = md->status;
+  io.epart = b.epart;
   io.prof = &md->prof;
   DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, st));
   rc = m.compressed ? run_compressed(m, pc, io, ar, st)

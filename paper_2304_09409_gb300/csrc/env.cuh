@@ -40,26 +40,68 @@ __device__ __forceinline__ void pair_env<double>(double d0, double d1, double d2
 }
 
 template <>
-__device__ __forceinline__ void pair_env<float>(double d0, double d1, double d2, double r2, double rs, double rc,
-                                                double near2, float& r, float& s, float& ds, float* u) {
-  if (r2 >= near2) {
-    const double rd = sqrt(r2);
-    double sd, dsd;
-    switch_eval<double>(rd, rs, rc, sd, dsd);
-    r = (float)rd;
-    s = (float)sd;
-    ds = (float)dsd;
-    const double ir = 1.0 / rd;
-    u[0] = (float)(d0 * ir);
-    u[1] = (float)(d1 * ir);
-    u[2] = (float)(d2 * ir);
+__device__ __forceinline__ void pair_env<float>(double d0, double d1, double d2, double, double rs, double rc,
+                                                double, float& r, float& s, float& ds, float* u) {
+  // The displacement itself is exact FP64 (it cancels large coordinates); everything after
+  // it is FP32.  Near r_c the polynomial of Eq. (switch) is evaluated in the equivalent form
+  // 1 - x^3 (6x^2 - 15x + 10) = y^3 (6y^2 - 15y + 10) with y = 1 - x = (r_c - r)/(r_c - r_s),
+  // which has no cancellation as r -> r_c, so FP32 keeps full relative precision there.
+  const float x0 = (float)d0, x1 = (float)d1, x2 = (float)d2;
+  r = sqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+  const float frs = (float)rs, frc = (float)rc;
+  if (r < frs) {
+    s = 1.0f / r;
+    ds = -s / r;
+  } else if (r >= frc) {
+    s = 0.0f;
+    ds = 0.0f;
   } else {
-    r = sqrtf((float)r2);
-    switch_eval<float>(r, (float)rs, (float)rc, s, ds);
-    const float ir = 1.0f / r;
-    u[0] = (float)d0 * ir;
-    u[1] = (float)d1 * ir;
-    u[2] = (float)d2 * ir;
+    const float w = frc - frs;
+    const float y = (frc - r) / w;
+    const float y3 = y * y * y;
+    const float uu = y3 * ((6.0f * y - 15.0f) * y + 10.0f);
+    const float du_dy = 30.0f * y * y * (y - 1.0f) * (y - 1.0f);
+    s = uu / r;
+    ds = -uu / (r * r) - du_dy / (w * r);
+  }
+  const float ir = 1.0f / r;
+  u[0] = x0 * ir;
+  u[1] = x1 * ir;
+  u[2] = x2 * ir;
+}
+
+// FP32 -> FP64 widening with integer operations: exact for normal numbers (subnormals flush to
+// zero), and it keeps the conversion off GB300's narrow FP64 pipe.
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  unsigned long long bits = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0xFFu)
+    bits |= 0x7FF0000000000000ull | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  else if (e != 0u)
+    bits |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(float x) { return widen_f32(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+
+// Exact FP64 displacement of a listed pair; the same-image case needs no shift term.
+__device__ __forceinline__ void listed_disp(const double* __restrict__ xi, const double* __restrict__ xj, int code,
+                                            const PathConst& pc, double& d0, double& d1, double& d2) {
+  int n0, n1, n2;
+  unpack_shift(code, n0, n1, n2);
+  if ((n0 | n1 | n2) == 0) {
+    d0 = __dsub_rn(xj[0], xi[0]);
+    d1 = __dsub_rn(xj[1], xi[1]);
+    d2 = __dsub_rn(xj[2], xi[2]);
+  } else if (pc.tshift && n0 >= -1 && n0 <= 1 && n1 >= -1 && n1 <= 1 && n2 >= -1 && n2 <= 1) {
+    // t(n) precomputed with the builder's formula: (x_j + t) - x_i, bit for bit
+    const double* t = pc.tshift + 3 * ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1));
+    d0 = __dsub_rn(__dadd_rn(xj[0], t[0]), xi[0]);
+    d1 = __dsub_rn(__dadd_rn(xj[1], t[1]), xi[1]);
+    d2 = __dsub_rn(__dadd_rn(xj[2], t[2]), xi[2]);
+  } else {
+    pair_disp_exact(xi, xj, n0, n1, n2, pc.h, pc.periodic, d0, d1, d2);
   }
 }
 

@@ -165,7 +165,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
   }
   {
     ProfScope _ps(io.prof, "energy_sum", st);
-    DP_CUDA_TRY(launch_energy_f32(E, io.perm, (int)N, io.atom_energy, io.energy, st));
+    DP_CUDA_TRY(launch_energy_f32(E, io.perm, (int)N, io.atom_energy, io.energy, io.epart, st));
   }
   // ---- backward ----
   for (int l = nh - 1; l >= 0; --l) {

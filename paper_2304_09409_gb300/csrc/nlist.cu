@@ -18,6 +18,7 @@ namespace dpgb {
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr int kQueue = 64;  // prefilter survivors waiting for the exact test (per warp)
 
 __device__ __forceinline__ int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 
@@ -162,6 +163,62 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int c0 = ci / (g.ncell[2] * g.ncell[1]);
   int cnt = 0;
   bool bad_shift = false;
+  // survivors of the FP32 prefilter wait in a per-warp queue, so the exact FP64 test always
+  // runs on full warps (GB300's FP64 pipe is narrow)
+  int* q_j = reinterpret_cast<int*>(smem + (size_t)kWarpsPerBlock * CAP * 17) + (size_t)warp * 2 * kQueue;
+  int* q_c = q_j + kQueue;
+  int qn = 0;
+  auto drain = [&](int take) {
+    bool acc = false;
+    unsigned long long r2bits = 0ull;
+    int j = -1, code = 0;
+    if (lane < take) {
+      j = q_j[lane];
+      code = q_c[lane];
+      int n0, n1, n2;
+      unpack_shift(code, n0, n1, n2);
+      const double* xj = coord + 3 * j;
+      double dx, dy, dz;
+      if ((n0 | n1 | n2) == 0) {  // same image: (x_j + 0) - x_i needs no shift term
+        dx = __dsub_rn(xj[0], xi[0]);
+        dy = __dsub_rn(xj[1], xi[1]);
+        dz = __dsub_rn(xj[2], xi[2]);
+      } else {
+        pair_disp_exact(xi, xj, n0, n1, n2, g.h, g.periodic, dx, dy, dz);
+      }
+      const double r2 = norm2_exact(dx, dy, dz);
+      if (r2 < g.rc2) {
+        acc = true;
+        r2bits = (unsigned long long)__double_as_longlong(r2);
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, acc);
+    if (acc) {
+      const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+      if (pos < CAP) {
+        k_r2[pos] = r2bits;
+        k_j[pos] = j;
+        k_code[pos] = code;
+        k_t[pos] = (unsigned char)type[j];
+      }
+    }
+    cnt += __popc(mask);
+    // move the entries beyond the first `take` to the front of the queue
+    __syncwarp();
+    const int rest = qn - take;
+    int mj = 0, mc = 0;
+    if (lane < rest) {
+      mj = q_j[take + lane];
+      mc = q_c[take + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      q_j[lane] = mj;
+      q_c[lane] = mc;
+    }
+    __syncwarp();
+    qn = rest;
+  };
 
   for (int d0 = -g.K[0]; d0 <= g.K[0]; ++d0)
     for (int d1 = -g.K[1]; d1 <= g.K[1]; ++d1)
@@ -182,8 +239,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         const int beg = cell_start[cell], end = cell_start[cell + 1];
         for (int base = beg; base < end; base += 32) {
           const int idx = base + lane;
-          bool acc = false;
-          unsigned long long r2bits = 0ull;
+          bool pass = false;
           int j = -1, code = 0;
           if (idx < end) {
             j = cell_atoms[idx];
@@ -210,31 +266,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
               if (n0 <= -512 || n0 >= 512 || n1 <= -512 || n1 >= 512 || n2 <= -512 || n2 >= 512) {
                 bad_shift = true;
               } else if (!(j == i && n0 == 0 && n1 == 0 && n2 == 0)) {
-                const double xj[3] = {coord[3 * j], coord[3 * j + 1], coord[3 * j + 2]};
-                double dx, dy, dz;
-                pair_disp_exact(xi, xj, n0, n1, n2, g.h, g.periodic, dx, dy, dz);
-                const double r2 = norm2_exact(dx, dy, dz);
-                if (r2 < g.rc2) {
-                  acc = true;
-                  r2bits = (unsigned long long)__double_as_longlong(r2);
-                  code = pack_shift(n0, n1, n2);
-                }
+                pass = true;
+                code = pack_shift(n0, n1, n2);
               }
             }
           }
-          const unsigned mask = __ballot_sync(0xffffffffu, acc);
-          if (acc) {
-            const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-            if (pos < CAP) {
-              k_r2[pos] = r2bits;
-              k_j[pos] = j;
-              k_code[pos] = code;
-              k_t[pos] = (unsigned char)type[j];
-            }
+          const unsigned mask = __ballot_sync(0xffffffffu, pass);
+          if (pass) {
+            const int pos = qn + __popc(mask & ((1u << lane) - 1u));
+            q_j[pos] = j;
+            q_c[pos] = code;
           }
-          cnt += __popc(mask);
+          qn += __popc(mask);
+          __syncwarp();
+          if (qn >= 32) drain(32);
         }
       }
+  if (qn > 0) drain(qn);
   if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
   if (cnt > CAP) {
     if (lane == 0) atomicExch(&st->capacity, 1);
@@ -272,38 +320,64 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
-// Stable partition of atoms by type (one block): perm[p] = atom index, type_start[t].
-__global__ void k_type_perm(const int* __restrict__ type, int n, int ntypes, int* __restrict__ perm,
-                            int* __restrict__ type_start, int* __restrict__ bad_type) {
-  __shared__ int wsum[32];
-  __shared__ int base;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = 0; t < ntypes; ++t) {
-    if (threadIdx.x == 0) type_start[t] = base;
-    for (int chunk = 0; chunk < n; chunk += blockDim.x) {
-      const int idx = chunk + threadIdx.x;
-      const int flag = (idx < n && type[idx] == t) ? 1 : 0;
-      const unsigned m = __ballot_sync(0xffffffffu, flag);
-      const int inwarp = __popc(m & ((1u << lane) - 1u));
-      if (lane == 0) wsum[w] = __popc(m);
-      __syncthreads();
-      int before = 0, total = 0;
-      for (int k = 0; k < nw; ++k) {
-        if (k < w) before += wsum[k];
-        total += wsum[k];
-      }
-      if (flag) perm[base + before + inwarp] = idx;
-      __syncthreads();
-      if (threadIdx.x == 0) base += total;
-      __syncthreads();
+// Stable partition of atoms by type (one block, one pass): each thread takes a contiguous
+// chunk of atoms, counts per type, and a block-wide exclusive scan of the counts gives every
+// thread its output offset per type.  perm[p] = atom index, type_start[t].
+__global__ void __launch_bounds__(1024)
+    k_type_perm(const int* __restrict__ type, int n, int ntypes, int* __restrict__ perm, int* __restrict__ type_start,
+                int* __restrict__ bad_type) {
+  __shared__ int wtot[32][DP_MAX_TYPES];
+  __shared__ int tstart[DP_MAX_TYPES + 1];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = tid * per, hi = min(n, lo + per);
+  int cnt[DP_MAX_TYPES], incl[DP_MAX_TYPES];
+#pragma unroll
+  for (int t = 0; t < DP_MAX_TYPES; ++t) cnt[t] = 0;
+  bool bad = false;
+  for (int i = lo; i < hi; ++i) {
+    const int t = type[i];
+    if (t < 0 || t >= ntypes) bad = true;
+#pragma unroll
+    for (int q = 0; q < DP_MAX_TYPES; ++q) cnt[q] += (t == q);
+  }
+#pragma unroll
+  for (int t = 0; t < DP_MAX_TYPES; ++t) {
+    int v = cnt[t];
+    for (int off = 1; off < 32; off <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += x;
     }
+    incl[t] = v;
+    if (lane == 31) wtot[w][t] = v;
   }
-  if (threadIdx.x == 0) {
-    type_start[ntypes] = base;
-    if (base != n) *bad_type = 1;
+  __syncthreads();
+  if (tid < ntypes) {  // exclusive offsets of the warps, per type
+    int acc = 0;
+    for (int k = 0; k < nw; ++k) {
+      const int x = wtot[k][tid];
+      wtot[k][tid] = acc;
+      acc += x;
+    }
+    tstart[tid + 1] = acc;  // total of type tid for now
   }
+  __syncthreads();
+  if (tid == 0) {
+    tstart[0] = 0;
+    for (int t = 0; t < ntypes; ++t) tstart[t + 1] += tstart[t];
+  }
+  __syncthreads();
+  int off[DP_MAX_TYPES];
+#pragma unroll
+  for (int t = 0; t < DP_MAX_TYPES; ++t) off[t] = (t < ntypes) ? tstart[t] + wtot[w][t] + incl[t] - cnt[t] : 0;
+  for (int i = lo; i < hi; ++i) {
+    const int t = type[i];
+#pragma unroll
+    for (int q = 0; q < DP_MAX_TYPES; ++q)
+      if (t == q && q < ntypes) perm[off[q]++] = i;
+  }
+  if (bad) atomicExch(bad_type, 1);
+  if (tid <= ntypes) type_start[tid] = tstart[tid];
 }
 
 }  // namespace
@@ -397,7 +471,7 @@ cudaError_t launch_nlist_build(const NlGeom& g, const double* coord, const int* 
   k_scan_excl<<<1, 1024, 0, st>>>(cell_count, ncells, cell_start, cell_cursor);
   k_fill<<<nb, 256, 0, st>>>(g.natoms, atom_cell, cell_cursor, cell_atoms);
   const int cap = g.cap <= 128 ? 128 : (g.cap <= 256 ? 256 : (g.cap <= 512 ? 512 : 1024));
-  const size_t smem = (size_t)kWarpsPerBlock * cap * 17;
+  const size_t smem = (size_t)kWarpsPerBlock * cap * 17 + (size_t)kWarpsPerBlock * 2 * kQueue * sizeof(int);
   const unsigned blocks = (g.natoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
 #define DPGB_NL_LAUNCH(C)                                                                                  \
   do {                                                                                                     \

@@ -230,42 +230,54 @@ __global__ void __launch_bounds__(256)
 }
 
 // Sum of `n` vectors of width `w` in order (one block) -> out[w]  (virial partials).
+// Column sums of an [n][w] FP64 array, one block per column, fixed summation order (the
+// FP64 pipe of one SM is narrow on GB300: spread the columns over SMs).
 __global__ void k_sum_rows(const double* __restrict__ in, long n, int w, double* __restrict__ out) {
   __shared__ double red[32];
-  for (int c = 0; c < w; ++c) {
-    double acc = 0.0;
-    for (long r = threadIdx.x; r < n; r += blockDim.x) acc += in[r * w + c];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-      out[c] = t;
-    }
-    __syncthreads();
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (long r = threadIdx.x; r < n; r += blockDim.x) acc += in[r * w + c];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (threadIdx.x == 0) out[c] = t;
   }
 }
 
-// Per-atom energies in input order and their FP64 sum.
+// Per-atom energies in input order and per-block partial FP64 sums (one value per thread,
+// widened with integer operations for FP32 inputs).
 template <class R>
 __global__ void k_energy(const R* __restrict__ Esorted, const int* __restrict__ perm, int n,
-                         double* __restrict__ atom_e, double* __restrict__ energy) {
-  __shared__ double red[32];
-  double acc = 0.0;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const double e = (double)Esorted[p];
+                         double* __restrict__ atom_e, double* __restrict__ partial) {
+  __shared__ double red[8];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (p < n) {
+    e = widen(Esorted[p]);
     if (atom_e) atom_e[perm[p]] = e;
-    acc += e;
   }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-    *energy = t;
+    partial[blockIdx.x] = t;
   }
+}
+
+// Translation vectors t(n) = n0 h0 + n1 h1 + n2 h2 for n in {-1,0,1}^3, formed exactly as the
+// neighbour builder forms them.
+__global__ void k_shift_table(PathConst pc, double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= 27) return;
+  const int n0 = q / 9 - 1, n1 = (q / 3) % 3 - 1, n2 = q % 3 - 1;
+  for (int a = 0; a < 3; ++a)
+    out[q * 3 + a] = __dadd_rn(__dadd_rn(__dmul_rn((double)n0, pc.h[a]), __dmul_rn((double)n1, pc.h[3 + a])),
+                               __dmul_rn((double)n2, pc.h[6 + a]));
 }
 
 __global__ void k_sorted_types(const int* __restrict__ type, const int* __restrict__ perm, int n,
@@ -323,7 +335,9 @@ int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, cons
   }
   {
     ProfScope _ps(io.prof, "energy_sum", st);
-    k_energy<R><<<1, 1024, 0, st>>>(Yf[nfl - 1], io.perm, (int)N, io.atom_energy, io.energy);
+    const unsigned eb = nblk(N, 256);
+    k_energy<R><<<eb, 256, 0, st>>>(Yf[nfl - 1], io.perm, (int)N, io.atom_energy, io.epart);
+    k_sum_rows<<<1, 256, 0, st>>>(io.epart, eb, 1, io.energy);
   }
   // backward through the fitting net, seeded with dE_i/dE_i = 1
   {
@@ -456,20 +470,27 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   }
   {
     ProfScope _ps(io.prof, "virial_sum", st);
-    k_sum_rows<<<1, 1024, 0, st>>>(vpart, fblocks, 9, io.virial);
+    k_sum_rows<<<9, 256, 0, st>>>(vpart, fblocks, 9, io.virial);
   }
   DP_CUDA_TRY(cudaGetLastError());
   return DP_OK;
 }
 
 cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
-                              cudaStream_t st) {
-  k_energy<float><<<1, 1024, 0, st>>>(Esorted, perm, n, atom_e, energy);
+                              double* epart, cudaStream_t st) {
+  const unsigned eb = (unsigned)((n + 255) / 256);
+  k_energy<float><<<eb, 256, 0, st>>>(Esorted, perm, n, atom_e, epart);
+  k_sum_rows<<<1, 256, 0, st>>>(epart, eb, 1, energy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_table(const PathConst& pc, double* out, cudaStream_t st) {
+  k_shift_table<<<1, 32, 0, st>>>(pc, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum_rows(const double* in, long n, int w, double* out, cudaStream_t st) {
-  k_sum_rows<<<1, 1024, 0, st>>>(in, n, w, out);
+  k_sum_rows<<<w, 256, 0, st>>>(in, n, w, out);
   return cudaGetLastError();
 }
 

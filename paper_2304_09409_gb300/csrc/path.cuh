@@ -13,7 +13,8 @@ struct PathConst {
   double h[9];
   int periodic;
   double rs, rc;
-  double near2;  // FP32 mode: pairs with r^2 >= near2 evaluate the switch in FP64
+  double near2;  // unused (kept for layout)
+  const double* tshift;  // device [27][3]: t(n) for n in {-1,0,1}^3, or null
 };
 
 // Per-kernel CUDA-event timing and launch counting.  Every kernel launch of the path sits in
@@ -114,6 +115,7 @@ struct PathIO {
   double* virial;       // device [9]
   double* atom_energy;  // device [N] or null
   DevStatus* status;    // device status words
+  double* epart;        // device scratch for per-block energy partials [ceil(N/256)]
 };
 
 struct __align__(32) D4 {
@@ -173,7 +175,9 @@ int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, cons
 cudaError_t launch_sum_rows(const double* in, long n, int w, double* out, cudaStream_t st);
 // Per-atom energies (sorted order, FP32) to input order and their FP64 sum.
 cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
-                              cudaStream_t st);
+                              double* epart, cudaStream_t st);
+// t(n) for n in {-1,0,1}^3 into out [27][3] (device)
+cudaError_t launch_shift_table(const PathConst& pc, double* out, cudaStream_t st);
 
 template <class R>
 int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, const PathIO& io, Arena& ar,

@@ -181,6 +181,26 @@ __device__ __forceinline__ int tab_interval(const TabConst& tc, R s, R& tt, bool
 }
 
 
+// ---- per-slot environment of the listed pairs: (s, u) and (ds/dr, r), once per step --------
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_env_tab(PathConst pc, const double* __restrict__ coord, const int* __restrict__ perm,
+              const int* __restrict__ nl_j, const int* __restrict__ nl_code, typename Vec4<R>::T* __restrict__ env) {
+  const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (long)pc.natoms * pc.nc) return;
+  const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
+  const int i = perm[p];
+  const long slot = (long)i * pc.nc + k;
+  const int j = nl_j[slot];
+  if (j < 0) return;  // padding is never read
+  double d0, d1, d2;
+  listed_disp(coord + 3 * i, coord + 3 * j, nl_code[slot], pc, d0, d1, d2);
+  R r, s, ds, u[3];
+  pair_env<R>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
+  env[row * 2] = Vec4<R>::make(s, u[0], u[1], u[2]);
+  env[row * 2 + 1] = Vec4<R>::make(ds, r, R(0), R(0));
+}
+
 // ---- forward: T = G^T R / Nc with G from the table, then D = T T_<^T --------------------------
 template <class DT, class R>
 __device__ __forceinline__ DT to_dt(R v) {
@@ -195,7 +215,8 @@ template <class R, int MPL, class DT>
 __global__ void __launch_bounds__(128)
     k_tab_fwd(PathConst pc, TabConst tc, const R* __restrict__ tab, const double* __restrict__ coord,
               const int* __restrict__ perm, const int* __restrict__ type, const int* __restrict__ nl_j,
-              const int* __restrict__ nl_code, R* __restrict__ Tm, DT* __restrict__ D, DevStatus* __restrict__ st) {
+              const typename Vec4<R>::T* __restrict__ env, R* __restrict__ Tm, DT* __restrict__ D,
+              DevStatus* __restrict__ st) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * 4 + warp;
   if (p >= pc.natoms) return;
@@ -217,16 +238,12 @@ __global__ void __launch_bounds__(128)
       R e0 = 0, e1 = 0, e2 = 0, e3 = 0, tt = 0;
       int l = 0;
       if (j >= 0) {
-        int n0, n1, n2;
-        unpack_shift(nl_code[(long)i * nc + k], n0, n1, n2);
-        double d0, d1, d2;
-        pair_disp_exact(xi, coord + 3 * j, n0, n1, n2, pc.h, pc.periodic, d0, d1, d2);
-        R r, s, ds, u[3];
-        pair_env<R>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
+        const typename Vec4<R>::T a4 = env[((long)p * nc + k) * 2];  // (s, u)
+        const R s = a4.x;
         e0 = s;
-        e1 = s * u[0];
-        e2 = s * u[1];
-        e3 = s * u[2];
+        e1 = s * a4.y;
+        e2 = s * a4.z;
+        e3 = s * a4.w;
         l = tab_interval<R>(tc, s, tt, oor);
       }
       const unsigned valid = __ballot_sync(0xffffffffu, j >= 0);
@@ -291,17 +308,19 @@ template <class R>
 __global__ void __launch_bounds__(128)
     k_tab_bwd(PathConst pc, TabConst tc, const R* __restrict__ tab, const double* __restrict__ coord,
               const int* __restrict__ perm, const int* __restrict__ type, const int* __restrict__ nl_j,
-              const int* __restrict__ nl_code, const R* __restrict__ Tm, const R* __restrict__ gD,
-              double* __restrict__ force, double* __restrict__ vpart) {
+              const typename Vec4<R>::T* __restrict__ env, const R* __restrict__ Tm,
+              const R* __restrict__ gD, double* __restrict__ force, double* __restrict__ vpart) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = pc.M, nc = pc.nc, A = pc.A;
   R* Ts = reinterpret_cast<R*>(sm_raw) + (size_t)warp * (M * 8);
   R* gTs = Ts + M * 4;
   const int p = blockIdx.x * 4 + warp;
-  double v[9];
+  // per-atom partial sums over the atom's neighbours stay in the path's precision; every
+  // accumulation across atoms (the force scatter, the virial sum) is FP64
+  R v[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) v[q] = 0.0;
+  for (int q = 0; q < 9; ++q) v[q] = R(0);
   if (p < pc.natoms) {
     const int i = perm[p], ti = type[i];
     for (int e = lane; e < M * 4; e += 32) Ts[e] = Tm[(long)p * M * 4 + e];
@@ -319,8 +338,7 @@ __global__ void __launch_bounds__(128)
     __syncwarp();
     const int grp = lane >> 3, sub = lane & 7;
     const R inv_nc = R(1) / R(nc);
-    double fi0 = 0.0, fi1 = 0.0, fi2 = 0.0;
-    const double* xi = coord + 3 * i;
+    R fi0 = 0, fi1 = 0, fi2 = 0;
     for (int t = 0; t < pc.ntypes; ++t) {
       const R* tabn = tab + (size_t)net_of(pc, ti, t) * tc.lc * M * kCoefStride;
       const int kend = pc.sel_off[t + 1];
@@ -328,17 +346,16 @@ __global__ void __launch_bounds__(128)
         const int k = base + lane;
         const int j = (k < kend) ? nl_j[(long)i * nc + k] : -1;
         R s = 0, ds = 0, r = 1, u0 = 0, u1 = 0, u2 = 0, tt = 0;
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0;
         int l = 0;
         if (j >= 0) {
-          int n0, n1, n2;
-          unpack_shift(nl_code[(long)i * nc + k], n0, n1, n2);
-          pair_disp_exact(xi, coord + 3 * j, n0, n1, n2, pc.h, pc.periodic, d0, d1, d2);
-          R u[3];
-          pair_env<R>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
-          u0 = u[0];
-          u1 = u[1];
-          u2 = u[2];
+          const long row = (long)p * nc + k;
+          const typename Vec4<R>::T a4 = env[row * 2], b4 = env[row * 2 + 1];  // (s, u), (ds, r)
+          s = a4.x;
+          u0 = a4.y;
+          u1 = a4.z;
+          u2 = a4.w;
+          ds = b4.x;
+          r = b4.y;
           bool oor = false;
           l = tab_interval<R>(tc, s, tt, oor);
         }
@@ -358,8 +375,7 @@ __global__ void __launch_bounds__(128)
           const R uq0 = __shfl_sync(0xffffffffu, u0, q), uq1 = __shfl_sync(0xffffffffu, u1, q);
           const R uq2 = __shfl_sync(0xffffffffu, u2, q);
           const int lq = __shfl_sync(0xffffffffu, l, q), jq = __shfl_sync(0xffffffffu, j, q);
-          const double dq0 = __shfl_sync(0xffffffffu, d0, q), dq1 = __shfl_sync(0xffffffffu, d1, q);
-          const double dq2 = __shfl_sync(0xffffffffu, d2, q);
+
           R g0 = 0, g1 = 0, g2 = 0, g3 = 0, gse = 0;
           if (have) {
             const R* c = tabn + (size_t)lq * M * kCoefStride;
@@ -392,16 +408,17 @@ __global__ void __launch_bounds__(128)
             gse *= inv_nc;
             const R gvu = g1 * uq0 + g2 * uq1 + g3 * uq2;
             const R a = dsq * (gse + g0 + gvu), b = sq / rq;
-            const double gd0 = (double)(a * uq0 + b * (g1 - gvu * uq0));
-            const double gd1 = (double)(a * uq1 + b * (g2 - gvu * uq1));
-            const double gd2 = (double)(a * uq2 + b * (g3 - gvu * uq2));
+            const R gd0 = a * uq0 + b * (g1 - gvu * uq0);
+            const R gd1 = a * uq1 + b * (g2 - gvu * uq1);
+            const R gd2 = a * uq2 + b * (g3 - gvu * uq2);
             fi0 += gd0;
             fi1 += gd1;
             fi2 += gd2;
-            atomicAdd(force + 3 * jq, -gd0);
-            atomicAdd(force + 3 * jq + 1, -gd1);
-            atomicAdd(force + 3 * jq + 2, -gd2);
-            const double gdv[3] = {gd0, gd1, gd2}, dv[3] = {dq0, dq1, dq2};
+            atomicAdd(force + 3 * jq, widen(-gd0));
+            atomicAdd(force + 3 * jq + 1, widen(-gd1));
+            atomicAdd(force + 3 * jq + 2, widen(-gd2));
+            const R gdv[3] = {gd0, gd1, gd2};
+            const R dv[3] = {rq * uq0, rq * uq1, rq * uq2};
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
@@ -418,17 +435,17 @@ __global__ void __launch_bounds__(128)
       fi2 += __shfl_xor_sync(0xffffffffu, fi2, off);
     }
     if (lane == 0) {
-      atomicAdd(force + 3 * i, fi0);
-      atomicAdd(force + 3 * i + 1, fi1);
-      atomicAdd(force + 3 * i + 2, fi2);
+      atomicAdd(force + 3 * i, widen(fi0));
+      atomicAdd(force + 3 * i + 1, widen(fi1));
+      atomicAdd(force + 3 * i + 2, widen(fi2));
     }
   }
   __shared__ double sv[4][9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    double x = v[q];
+    R x = v[q];
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) sv[warp][q] = x;
+    if (lane == 0) sv[warp][q] = widen(x);
   }
   __syncthreads();
   if (threadIdx.x < 9)
@@ -444,6 +461,8 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const int M = pc.M, A = pc.A;
   R* Tm = ar.get<R>(N * M * 4);
   DT* D = ar.get<DT>(N * M * A);
+  typedef typename Vec4<R>::T V4;
+  V4* env = ar.get<V4>(N * pc.nc * 2);
   const unsigned blocks = (unsigned)((N + 3) / 4);
   double* vpart = ar.get<double>((long)blocks * 9);
   const R* gD = nullptr;
@@ -462,18 +481,23 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const TabConst tc = tab_const(m);
   const int mpl = (M + 31) / 32;
   {
+    ProfScope _ps(io.prof, "env", st);
+    const long rows = N * pc.nc;
+    k_env_tab<R><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(pc, io.coord, io.perm, io.nl_j, io.nl_code, env);
+  }
+  {
     ProfScope _ps(io.prof, "tab_fwd", st);
     if (mpl <= 1)
-      k_tab_fwd<R, 1, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+      k_tab_fwd<R, 1, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,
                                                   D, io.status);
     else if (mpl <= 2)
-      k_tab_fwd<R, 2, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+      k_tab_fwd<R, 2, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,
                                                   D, io.status);
     else if (mpl <= 4)
-      k_tab_fwd<R, 4, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+      k_tab_fwd<R, 4, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,
                                                   D, io.status);
     else
-      k_tab_fwd<R, 8, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm,
+      k_tab_fwd<R, 8, DT><<<blocks, 128, 0, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,
                                                   D, io.status);
   }
   DP_CUDA_TRY(cudaGetLastError());
@@ -490,8 +514,8 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   DP_CUDA_TRY(cudaFuncSetAttribute(k_tab_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     ProfScope _ps(io.prof, "tab_bwd", st);
-    k_tab_bwd<R><<<blocks, 128, smem, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, io.nl_code, Tm, gD,
-                                            io.force, vpart);
+    k_tab_bwd<R><<<blocks, 128, smem, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,
+                                            gD, io.force, vpart);
   }
   DP_CUDA_TRY(cudaGetLastError());
   {

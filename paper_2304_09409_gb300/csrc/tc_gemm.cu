@@ -185,41 +185,110 @@ __global__ void __launch_bounds__(128, 1)
     const int cb = col0 + c;
     if (!rv || cb >= g.N) continue;
     const long ro = (long)row * g.N;
+    // rows of 16-byte-aligned chunks take vector loads/stores; a ragged last chunk goes scalar
+    const bool vec = (cb + 16 <= g.N) && ((g.N & 7) == 0);
+    float o[16], aux[16];
+    if (EPI == TC_EPI_PLAIN) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int col = cb + i;
-      if (col >= g.N) break;
-      if (EPI == TC_EPI_PLAIN) {
-        g.out_f32[ro + col] = v[i];
-      } else if (EPI == TC_EPI_FWD || EPI == TC_EPI_FWD_LAST) {
-        const float z = v[i] + g.bias[t][col];
-        const float th = tanhf(z);
-        float y = th;
-        if (g.skip_kind == 1) y += g.skip_mat[(long)row * g.skip_ld + col];
-        if (g.skip_kind == 2) y += g.skip_mat[(long)row * g.skip_ld + (col % g.skip_ld)];
+      for (int i = 0; i < 16; ++i) o[i] = v[i];
+    } else if (EPI == TC_EPI_FWD || EPI == TC_EPI_FWD_LAST) {
+      float sk[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sk[i] = 0.f;
+      if (g.skip_kind && vec && (g.skip_ld & 15) == 0) {
+        const int sc = (g.skip_kind == 1) ? cb : (cb % g.skip_ld);
+        const float4* s4 = reinterpret_cast<const float4*>(g.skip_mat + (long)row * g.skip_ld + sc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 x = s4[q];
+          sk[4 * q] = x.x;
+          sk[4 * q + 1] = x.y;
+          sk[4 * q + 2] = x.z;
+          sk[4 * q + 3] = x.w;
+        }
+      } else if (g.skip_kind) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (cb + i < g.N)
+            sk[i] = g.skip_mat[(long)row * g.skip_ld + (g.skip_kind == 1 ? cb + i : (cb + i) % g.skip_ld)];
+      }
+      const float* bias = g.bias[t];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = cb + i < g.N ? cb + i : g.N - 1;
+        const float th = tanhf(v[i] + bias[col]);
         if (EPI == TC_EPI_FWD) {
-          if (g.out_f32) g.out_f32[ro + col] = y;
-          g.out_bf16[ro + col] = __float2bfloat16_rn(y);
-          if (g.out_t) g.out_t[ro + col] = th;
+          o[i] = th + sk[i];
+          aux[i] = th;
         } else {
           const float wl = g.w_last[t][col];
-          e_acc += y * wl;
-          g.out_bf16[ro + col] = __float2bfloat16_rn(wl * (1.f - th * th));
+          if (cb + i < g.N) e_acc += (th + sk[i]) * wl;
+          aux[i] = wl * (1.f - th * th);
         }
-      } else {  // TC_EPI_BWD
+      }
+    } else {  // TC_EPI_BWD
+      float tb[16];
+      if (vec) {
+        const float4* t4 = reinterpret_cast<const float4*>(g.tact + ro + cb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 x = t4[q];
+          tb[4 * q] = x.x;
+          tb[4 * q + 1] = x.y;
+          tb[4 * q + 2] = x.z;
+          tb[4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tb[i] = cb + i < g.N ? g.tact[ro + cb + i] : 0.f;
+      }
+      const float* sv = g.skip_vec ? g.w_last[t] : (g.skip_mat ? g.skip_mat + (long)row * g.skip_ld : nullptr);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = cb + i < g.N ? cb + i : g.N - 1;
         float gy = v[i];
-        if (g.skip_vec) {
-          const float* w = g.w_last[t];
-          if (g.skip_kind == 1) gy += w[col];
-          if (g.skip_kind == 2) gy += w[col] + w[col + g.N];
-        } else if (g.skip_mat) {
-          const float* s = g.skip_mat + (long)row * g.skip_ld;
-          if (g.skip_kind == 1) gy += s[col];
-          if (g.skip_kind == 2) gy += s[col] + s[col + g.N];
+        if (sv) {
+          if (g.skip_kind == 1) gy += sv[col];
+          if (g.skip_kind == 2) gy += sv[col] + sv[col + g.N];
         }
-        if (g.out_f32) g.out_f32[ro + col] = gy;
-        const float tb_ = g.tact[ro + col];
-        g.out_bf16[ro + col] = __float2bfloat16_rn(gy * (1.f - tb_ * tb_));
+        o[i] = gy;
+        aux[i] = gy * (1.f - tb[i] * tb[i]);
+      }
+    }
+    // ---- stores ----
+    float* of = (EPI == TC_EPI_FWD_LAST) ? nullptr : g.out_f32;
+    float* ot = (EPI == TC_EPI_FWD) ? g.out_t : nullptr;
+    const float* bsrc = (EPI == TC_EPI_FWD) ? o : aux;  // values stored as BF16
+    if (vec) {
+      if (of) {
+        float4* d4 = reinterpret_cast<float4*>(of + ro + cb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      }
+      if (ot) {
+        float4* d4 = reinterpret_cast<float4*>(ot + ro + cb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d4[q] = make_float4(aux[4 * q], aux[4 * q + 1], aux[4 * q + 2], aux[4 * q + 3]);
+      }
+      if (EPI != TC_EPI_PLAIN) {
+        uint4 pk[2];
+        uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(bsrc[2 * q], bsrc[2 * q + 1]);
+          w[q] = *reinterpret_cast<const uint32_t*>(&h2);
+        }
+        uint4* d = reinterpret_cast<uint4*>(g.out_bf16 + ro + cb);
+        d[0] = pk[0];
+        d[1] = pk[1];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (cb + i >= g.N) break;
+        if (of) of[ro + cb + i] = o[i];
+        if (ot) ot[ro + cb + i] = aux[i];
+        if (EPI != TC_EPI_PLAIN) g.out_bf16[ro + cb + i] = __float2bfloat16_rn(bsrc[i]);
       }
     }
   }

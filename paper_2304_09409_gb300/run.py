@@ -4,7 +4,7 @@
 
 Workloads: water192 (the 192-atom water frame), water12288 (it tiled 4x4x4), water1536
 (tiled 2x2x2), fcc32000 (Cu-like FCC, 20^3 cells), fcc4000 (10^3 cells).  Paths: fp64,
-fp32, fp32-compressed, fp64-compressed.  Inputs live on the device; each step is one full
+fp32, fp32-compressed, fp64-compressed, bf16-compressed.  Inputs live on the device; each step is one full
 dp_compute (neighbour list included).  Prints the mean device time per step.
 """
 from __future__ import annotations
@@ -34,7 +34,7 @@ def workload(name: str):
 
 
 PATHS = {"fp64": ("fp64", False), "fp32": ("fp32", False), "fp32-compressed": ("fp32", True),
-         "fp64-compressed": ("fp64", True)}
+         "fp64-compressed": ("fp64", True), "bf16-compressed": ("bf16", True)}
 
 
 def main(argv=None):
