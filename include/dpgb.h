@@ -173,6 +173,19 @@ int dp_profile_count(const dp_model* model);
 int dp_profile_read(const dp_model* model, int k, char* name, int name_len, double* total_ms, long* count);
 long dp_launch_count(const dp_model* model);
 
+/* Energies, forces and virials of several frames of one model in one pass (serving).
+ * The frames keep their own periodic cells and atom counts; their atoms are concatenated.
+ *   natoms [nframes] (host): atoms of each frame, in order.
+ *   coord [sum(natoms)*3] FP64, type [sum(natoms)] int32: host or device, frames concatenated.
+ *   boxes [nframes*9] (host): cell rows of every frame (periodic frames only).
+ *   energy [nframes], force [sum(natoms)*3], virial [nframes*9], atom_energy [sum(natoms)] or
+ *   NULL: host or device.
+ * Each frame's result equals dp_compute on that frame alone up to the order of floating-point
+ * accumulation.  Returns as dp_compute; DP_E_UNSUPPORTED for boxes == NULL. */
+int dp_compute_batch(dp_model* model, int nframes, const int* natoms, const double* coord, const int* type,
+                     const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
+                     void* stream);
+
 /* Message for the last error raised on the calling thread ("" if none). */
 const char* dp_last_error(void);
 

@@ -5,31 +5,12 @@
 #include <string>
 #include <vector>
 
+#include "capi_internal.cuh"
 #include "dp_internal.cuh"
 #include "fit_tc.cuh"
 #include "path.cuh"
 #include "table.cuh"
 #include "tc_gemm.cuh"
-
-struct dp_model {
-  dpgb::DeviceModel m;
-  char* ws = nullptr;  // cached scratch
-  size_t ws_cap = 0;
-  dpgb::DevStatus* status = nullptr;  // device
-  dpgb::DevStatus* status_host = nullptr;  // pinned
-  dpgb::Prof prof;
-  // set once a frame overflowed the density-sized candidate buffer: later builds use the
-  // full DP_MAX_CANDIDATES buffer
-  bool nl_full_cap = false;
-};
-
-struct dp_nlist {
-  int device;
-  int natoms, nc, ntypes;
-  int* nl_j = nullptr;
-  int* nl_code = nullptr;
-  int* counts = nullptr;
-};
 
 namespace dpgb {
 
@@ -85,6 +66,8 @@ long layout(const dp_model_config& c, std::vector<LayerDesc>* emb, std::vector<L
   return off;
 }
 
+}  // namespace
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -107,61 +90,6 @@ int ensure_ws(dp_model* md, size_t bytes) {
   DP_CUDA_TRY(cudaMalloc(&md->ws, cap));
   md->ws_cap = cap;
   return DP_OK;
-}
-
-struct FrameBufs {
-  double* coord;
-  int* type;
-  int* nl_j;
-  int* nl_code;
-  int* counts;
-  int* cell_count;
-  int* cell_start;
-  int* cell_cursor;
-  int* cell_atoms;
-  int* atom_cell;
-  int* atom_img;
-  float4* atom_wf;
-  int* perm;
-  int* type_start;
-  double* energy;
-  double* force;
-  double* virial;
-  double* atom_energy;
-  double* bbox;
-  double* tshift;
-  double* epart;
-};
-
-// Carve the per-call buffers that precede the path scratch.
-void carve(Arena& ar, const DeviceModel& m, int N, const NlGeom* g, bool own_nlist, bool copy_coord,
-           bool copy_type, bool host_force, bool host_ae, FrameBufs& b) {
-  std::memset(&b, 0, sizeof(b));
-  const long nc = m.nc;
-  if (copy_coord) b.coord = ar.get<double>(3L * N);
-  if (copy_type) b.type = ar.get<int>(N);
-  if (own_nlist) {
-    const int ncells = g->ncell[0] * g->ncell[1] * g->ncell[2];
-    b.nl_j = ar.get<int>(N * nc);
-    b.nl_code = ar.get<int>(N * nc);
-    b.counts = ar.get<int>((long)N * m.cfg.ntypes);
-    b.cell_count = ar.get<int>(ncells);
-    b.cell_start = ar.get<int>(ncells + 1);
-    b.cell_cursor = ar.get<int>(ncells);
-    b.cell_atoms = ar.get<int>(N);
-    b.atom_cell = ar.get<int>(N);
-    b.atom_img = ar.get<int>(3L * N);
-    b.atom_wf = ar.get<float4>(N);
-  }
-  b.perm = ar.get<int>(N);
-  b.type_start = ar.get<int>(DP_MAX_TYPES + 1);
-  b.energy = ar.get<double>(1);
-  b.virial = ar.get<double>(9);
-  if (host_force) b.force = ar.get<double>(3L * N);
-  if (host_ae) b.atom_energy = ar.get<double>(N);
-  b.bbox = ar.get<double>(6);
-  b.tshift = ar.get<double>(81);
-  b.epart = ar.get<double>((N + 255) / 256);
 }
 
 int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
@@ -193,23 +121,6 @@ int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
   return DP_OK;
 }
 
-// Geometry for this frame (open boundary needs the bounding box of the coordinates).
-int frame_geometry(dp_model* md, int N, const double* dcoord, const double* box, double* dbbox, cudaStream_t st,
-                   NlGeom& g) {
-  double lohi[6] = {0, 0, 0, 0, 0, 0};
-  if (!box) {
-    {
-      ProfScope _ps(&md->prof, "bbox", st);
-      DP_CUDA_TRY(launch_bbox(dcoord, N, dbbox, st));
-    }
-    DP_CUDA_TRY(cudaMemcpyAsync(lohi, dbbox, sizeof(lohi), cudaMemcpyDeviceToHost, st));
-    DP_CUDA_TRY(cudaStreamSynchronize(st));
-  }
-  const int rc = host_geometry(md->m.cfg, N, box, lohi, g);
-  if (md->nl_full_cap) g.cap = DP_MAX_CANDIDATES;
-  return rc;
-}
-
 // Host-side per-type atom counts when types are on the host; else read back.
 int type_starts(const int* type_host, const int* dtype_start, int N, int ntypes, cudaStream_t st, int* out) {
   if (type_host) {
@@ -234,7 +145,17 @@ int type_starts(const int* type_host, const int* dtype_start, int N, int ntypes,
   return DP_OK;
 }
 
-}  // namespace
+int ensure_stage(dp_model* md, size_t bytes) {
+  if (bytes <= md->stage_cap) return DP_OK;
+  if (md->stage) cudaFreeHost(md->stage);
+  md->stage = nullptr;
+  md->stage_cap = 0;
+  const size_t cap = bytes + bytes / 4 + 4096;
+  DP_CUDA_TRY(cudaMallocHost(&md->stage, cap));
+  md->stage_cap = cap;
+  return DP_OK;
+}
+
 }  // namespace dpgb
 
 using namespace dpgb;
@@ -444,71 +365,9 @@ int dp_free_model(dp_model* md) {
   cudaFree(md->ws);
   cudaFree(md->status);
   if (md->status_host) cudaFreeHost(md->status_host);
+  if (md->stage) cudaFreeHost(md->stage);
   delete md;
   return DP_OK;
-}
-
-int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, const double* box, dp_nlist** out,
-                   int* n_overflow, void* stream) {
-  if (!md || !coord || !type || !out || N < 1) {
-    set_error("invalid argument");
-    return DP_E_ARG;
-  }
-  *out = nullptr;
-  DP_CUDA_TRY(cudaSetDevice(md->m.device));
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool copy_coord = !is_device_ptr(coord), copy_type = !is_device_ptr(type);
-  // first pass: sizes (geometry needs device coordinates only for open boundaries)
-  Arena pre;
-  pre.measure = true;
-  FrameBufs b;
-  NlGeom g;
-  std::memset(&g, 0, sizeof(g));
-  g.ncell[0] = g.ncell[1] = g.ncell[2] = 256;  // upper bound for sizing
-  carve(pre, md->m, N, &g, true, copy_coord, copy_type, false, false, b);
-  int rc = ensure_ws(md, pre.used);
-  if (rc != DP_OK) return rc;
-  Arena ar;
-  ar.base = md->ws;
-  ar.cap = md->ws_cap;
-  carve(ar, md->m, N, &g, true, copy_coord, copy_type, false, false, b);
-  const double* dcoord = copy_coord ? b.coord : coord;
-  const int* dtype = copy_type ? b.type : type;
-  if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
-  if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-  rc = frame_geometry(md, N, dcoord, box, b.bbox, st, g);
-  if (rc != DP_OK) return rc;
-  dp_nlist* nl = new dp_nlist();
-  nl->device = md->m.device;
-  nl->natoms = N;
-  nl->nc = md->m.nc;
-  nl->ntypes = md->m.cfg.ntypes;
-  cudaError_t e = cudaMalloc(&nl->nl_j, sizeof(int) * (size_t)N * nl->nc);
-  if (e == cudaSuccess) e = cudaMalloc(&nl->nl_code, sizeof(int) * (size_t)N * nl->nc);
-  if (e == cudaSuccess) e = cudaMalloc(&nl->counts, sizeof(int) * (size_t)N * nl->ntypes);
-  if (e != cudaSuccess) {
-    set_error(std::string("nlist allocation: ") + cudaGetErrorString(e));
-    dp_free_nlist(nl);
-    return DP_E_OOM;
-  }
-  DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
-  {
-    ProfScope _ps(&md->prof, "nlist", st, 4);
-    DP_CUDA_TRY(launch_nlist_build(g, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor, b.cell_atoms,
-                                   b.atom_cell, b.atom_img, b.atom_wf, nl->nl_j, nl->nl_code, nl->counts, md->status,
-                                   st));
-  }
-  rc = read_status(md, st, n_overflow);
-  if (rc != DP_OK && rc != DP_E_SEL_OVERFLOW) {
-    dp_free_nlist(nl);
-    if (rc == DP_E_CAPACITY && !md->nl_full_cap) {
-      md->nl_full_cap = true;  // retry once with the full candidate buffer
-      return dp_build_nlist(md, N, coord, type, box, out, n_overflow, stream);
-    }
-    return rc;
-  }
-  *out = nl;
-  return rc;
 }
 
 int dp_nlist_export(const dp_nlist* nl, int* nl_j, int* nl_shift) {
@@ -533,115 +392,6 @@ int dp_free_nlist(dp_nlist* nl) {
   cudaFree(nl->counts);
   delete nl;
   return DP_OK;
-}
-
-int dp_compute(dp_model* md, dp_nlist* nlist, int N, const double* coord, const int* type, const double* box,
-               double* energy, double* force, double* virial, double* atom_energy, void* stream) {
-  if (!md || !coord || !type || !energy || !force || !virial || N < 1) {
-    set_error("invalid argument");
-    return DP_E_ARG;
-  }
-  if (nlist && (nlist->natoms != N || nlist->nc != md->m.nc || nlist->device != md->m.device)) {
-    set_error("neighbour list does not match this frame/model");
-    return DP_E_ARG;
-  }
-  DP_CUDA_TRY(cudaSetDevice(md->m.device));
-  cudaStream_t st = (cudaStream_t)stream;
-  const DeviceModel& m = md->m;
-  const bool copy_coord = !is_device_ptr(coord), copy_type = !is_device_ptr(type);
-  const bool host_e = !is_device_ptr(energy), host_f = !is_device_ptr(force), host_v = !is_device_ptr(virial);
-  const bool host_ae = atom_energy && !is_device_ptr(atom_energy);
-  const bool own_nlist = (nlist == nullptr);
-  const bool fp64 = (m.precision == DP_PREC_FP64);
-  // sizing pass
-  NlGeom g;
-  std::memset(&g, 0, sizeof(g));
-  g.ncell[0] = g.ncell[1] = g.ncell[2] = 256;
-  PathConst pc;
-  std::memset(&pc, 0, sizeof(pc));
-  pc.natoms = N;
-  pc.nc = m.nc;
-  pc.M = m.M;
-  pc.A = m.A;
-  pc.ntypes = m.cfg.ntypes;
-  pc.type_one_side = m.cfg.type_one_side;
-  for (int t = 0; t < m.cfg.ntypes; ++t) pc.sel[t] = m.cfg.sel[t];
-  for (int t = 0; t <= m.cfg.ntypes; ++t) pc.sel_off[t] = m.sel_off[t];
-  pc.rs = m.cfg.rcut_smth;
-  pc.rc = m.cfg.rcut;
-  {
-    const double rn = m.cfg.rcut - 1.0 > 0.0 ? m.cfg.rcut - 1.0 : 0.0;
-    pc.near2 = rn * rn;
-  }
-  PathIO io;
-  std::memset(&io, 0, sizeof(io));
-  Arena pre;
-  pre.measure = true;
-  FrameBufs b;
-  carve(pre, m, N, &g, own_nlist, copy_coord, copy_type, host_f, host_ae, b);
-  int rc = m.compressed ? run_compressed(m, pc, io, pre, st)
-                        : (fp64 ? run_generic<double>(m, pc, m.p64, io, pre, st)
-                                : run_generic<float>(m, pc, m.p32, io, pre, st));
-  if (rc != DP_OK) return rc;
-  rc = ensure_ws(md, pre.used);
-  if (rc != DP_OK) return rc;
-  Arena ar;
-  ar.base = md->ws;
-  ar.cap = md->ws_cap;
-  carve(ar, m, N, &g, own_nlist, copy_coord, copy_type, host_f, host_ae, b);
-  const double* dcoord = copy_coord ? b.coord : coord;
-  const int* dtype = copy_type ? b.type : type;
-  if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
-  if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-  DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
-  rc = frame_geometry(md, N, dcoord, box, b.bbox, st, g);
-  if (rc != DP_OK) return rc;
-  if (own_nlist) {
-    ProfScope _ps(&md->prof, "nlist", st, 4);
-    DP_CUDA_TRY(launch_nlist_build(g, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor, b.cell_atoms,
-                                   b.atom_cell, b.atom_img, b.atom_wf, b.nl_j, b.nl_code, b.counts, md->status, st));
-  }
-  {
-    ProfScope _ps(&md->prof, "type_perm", st);
-    DP_CUDA_TRY(launch_type_perm(dtype, N, m.cfg.ntypes, b.perm, b.type_start, &md->status->bad_type, st));
-  }
-  rc = type_starts(copy_type ? type : nullptr, b.type_start, N, m.cfg.ntypes, st, io.type_start);
-  if (rc != DP_OK) return rc;
-  for (int k = 0; k < 9; ++k) pc.h[k] = g.h[k];
-  pc.periodic = g.periodic;
-  if (g.periodic) {
-    pc.tshift = b.tshift;
-    ProfScope _ps(&md->prof, "shift_table", st);
-    DP_CUDA_TRY(launch_shift_table(pc, b.tshift, st));
-  }
-  io.coord = dcoord;
-  io.type = dtype;
-  io.perm = b.perm;
-  io.nl_j = own_nlist ? b.nl_j : nlist->nl_j;
-  io.nl_code = own_nlist ? b.nl_code : nlist->nl_code;
-  io.energy = host_e ? b.energy : energy;
-  io.virial = host_v ? b.virial : virial;
-  io.force = host_f ? b.force : force;
-  io.atom_energy = atom_energy ? (host_ae ? b.atom_energy : atom_energy) : nullptr;
-  io.status = md->status;
-  io.epart = b.epart;
-  io.prof = &md->prof;
-  DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, st));
-  rc = m.compressed ? run_compressed(m, pc, io, ar, st)
-                    : (fp64 ? run_generic<double>(m, pc, m.p64, io, ar, st)
-                            : run_generic<float>(m, pc, m.p32, io, ar, st));
-  if (rc != DP_OK) return rc;
-  if (host_e) DP_CUDA_TRY(cudaMemcpyAsync(energy, io.energy, sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (host_v) DP_CUDA_TRY(cudaMemcpyAsync(virial, io.virial, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
-  if (host_f) DP_CUDA_TRY(cudaMemcpyAsync(force, io.force, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
-  if (host_ae)
-    DP_CUDA_TRY(cudaMemcpyAsync(atom_energy, io.atom_energy, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  rc = read_status(md, st, nullptr);
-  if (rc == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
-    md->nl_full_cap = true;  // retry once with the full candidate buffer
-    return dp_compute(md, nlist, N, coord, type, box, energy, force, virial, atom_energy, stream);
-  }
-  return rc;
 }
 
 }  // extern "C"

@@ -133,7 +133,16 @@ struct DevStatus {
 int host_geometry(const dp_model_config& cfg, int natoms, const double* box_host, const double* bbox_lohi,
                   NlGeom& g);
 cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi /*device [6]*/, cudaStream_t st);
-cudaError_t launch_nlist_build(const NlGeom& g, const double* coord, const int* type, int* cell_count,
+// One neighbour-list build over one or more frames of the same model.
+struct NlLaunch {
+  int natoms;             // atoms of all frames
+  int ncells_total;       // cells of all frames
+  int cap;                // candidate buffer per atom (max over frames)
+  const NlGeom* geoms;    // device [frames]
+  const int* atom_frame;  // device [natoms] frame of each atom, or null (one frame)
+  const int* cell_off;    // device [frames] first cell of each frame, or null (one frame)
+};
+cudaError_t launch_nlist_build(const NlLaunch& L, const double* coord, const int* type, int* cell_count,
                                int* cell_start, int* cell_cursor, int* cell_atoms, int* atom_cell, int* atom_img,
                                float4* atom_wf, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st);

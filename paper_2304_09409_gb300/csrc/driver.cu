@@ -1,0 +1,481 @@
+// Host driver of the path over one or more frames of one model: dp_compute (one frame),
+// dp_compute_batch (many frames with their own cells and atom counts, evaluated together by
+// the same kernels), and dp_build_nlist.
+//
+// Frames are concatenated; every per-atom kernel is frame-agnostic except for the frame's
+// cell (neighbour search, image shifts), which it reads from small per-frame tables uploaded
+// once per call from pinned host memory.  Per-frame energy and virial are FP64 sums of the
+// per-atom values over fixed 512-atom chunks (deterministic order), then over each frame's
+// chunks.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "capi_internal.cuh"
+#include "table.cuh"
+
+namespace dpgb {
+
+namespace {
+
+constexpr int kChunk = 512;
+
+__global__ void k_atom_frame(const int* __restrict__ frame_start, int F, int N, int* __restrict__ atom_frame) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int lo = 0, hi = F - 1;  // last frame f with frame_start[f] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frame_start[mid] <= i)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  atom_frame[i] = lo;
+}
+
+__global__ void k_shift_tables(const double* __restrict__ boxes, double* __restrict__ out) {
+  const int f = blockIdx.x, q = threadIdx.x;
+  if (q >= 27) return;
+  const double* h = boxes + 9L * f;
+  const int n0 = q / 9 - 1, n1 = (q / 3) % 3 - 1, n2 = q % 3 - 1;
+  for (int a = 0; a < 3; ++a)
+    out[81L * f + q * 3 + a] = __dadd_rn(__dadd_rn(__dmul_rn((double)n0, h[a]), __dmul_rn((double)n1, h[3 + a])),
+                                         __dmul_rn((double)n2, h[6 + a]));
+}
+
+// Per-chunk sums of atom energies and atom virials (10 values), fixed order.
+__global__ void __launch_bounds__(256)
+    k_chunk_sums(const int* __restrict__ chunk, const double* __restrict__ ae, const double* __restrict__ av,
+                 double* __restrict__ cpart) {
+  __shared__ double red[8][10];
+  const int c = blockIdx.x;
+  const int beg = chunk[2 * c], end = chunk[2 * c + 1];
+  double acc[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+  for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    acc[0] += ae[i];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[1 + q] += av[9L * i + q];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    double x = acc[q];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 10) {
+    double x = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x += red[k][threadIdx.x];
+    cpart[10L * c + threadIdx.x] = x;
+  }
+}
+
+__global__ void k_frame_sums(const int* __restrict__ frame_chunk, const double* __restrict__ cpart,
+                             double* __restrict__ energy, double* __restrict__ virial) {
+  const int f = blockIdx.x, q = threadIdx.x;
+  if (q >= 10) return;
+  double x = 0.0;
+  for (int c = frame_chunk[f]; c < frame_chunk[f + 1]; ++c) x += cpart[10L * c + q];
+  if (q == 0)
+    energy[f] = x;
+  else
+    virial[9L * f + q - 1] = x;
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Per-frame tables, laid out identically in pinned staging and on the device.
+struct FrameTables {
+  int F = 0, N = 0, C = 0;
+  int ncells = 0, cap = 0, periodic = 1;
+  std::vector<int> start, cell_off, chunk, frame_chunk;
+  std::vector<NlGeom> geoms;
+  std::vector<double> boxes;
+  size_t off_geoms = 0, off_celloff = 0, off_start = 0, off_chunk = 0, off_fchunk = 0, off_boxes = 0, bytes = 0;
+
+  void layout() {
+    size_t o = 0;
+    off_geoms = o;
+    o += a256(sizeof(NlGeom) * F);
+    off_celloff = o;
+    o += a256(sizeof(int) * (F + 1));
+    off_start = o;
+    o += a256(sizeof(int) * (F + 1));
+    off_chunk = o;
+    o += a256(sizeof(int) * 2 * C);
+    off_fchunk = o;
+    o += a256(sizeof(int) * (F + 1));
+    off_boxes = o;
+    o += a256(sizeof(double) * 9 * F);
+    bytes = o;
+  }
+  void pack(unsigned char* p) const {
+    std::memcpy(p + off_geoms, geoms.data(), sizeof(NlGeom) * F);
+    std::memcpy(p + off_celloff, cell_off.data(), sizeof(int) * (F + 1));
+    std::memcpy(p + off_start, start.data(), sizeof(int) * (F + 1));
+    std::memcpy(p + off_chunk, chunk.data(), sizeof(int) * 2 * C);
+    std::memcpy(p + off_fchunk, frame_chunk.data(), sizeof(int) * (F + 1));
+    std::memcpy(p + off_boxes, boxes.data(), sizeof(double) * 9 * F);
+  }
+};
+
+int build_tables_host(dp_model* md, int F, const int* natoms, const double* boxes, const double* lohi,
+                      FrameTables& T) {
+  T.F = F;
+  T.start.assign(F + 1, 0);
+  for (int f = 0; f < F; ++f) {
+    if (natoms[f] < 1) {
+      set_error("every frame needs at least one atom");
+      return DP_E_ARG;
+    }
+    T.start[f + 1] = T.start[f] + natoms[f];
+  }
+  T.N = T.start[F];
+  T.periodic = boxes ? 1 : 0;
+  T.geoms.resize(F);
+  T.cell_off.assign(F + 1, 0);
+  T.boxes.assign(9 * (size_t)F, 0.0);
+  T.cap = 0;
+  for (int f = 0; f < F; ++f) {
+    const int rc = host_geometry(md->m.cfg, natoms[f], boxes ? boxes + 9 * f : nullptr, lohi, T.geoms[f]);
+    if (rc != DP_OK) return rc;
+    NlGeom& g = T.geoms[f];
+    if (md->nl_full_cap) g.cap = DP_MAX_CANDIDATES;
+    T.cap = std::max(T.cap, g.cap);
+    T.cell_off[f + 1] = T.cell_off[f] + g.ncell[0] * g.ncell[1] * g.ncell[2];
+    if (boxes)
+      for (int k = 0; k < 9; ++k) T.boxes[9 * f + k] = boxes[9 * f + k];
+  }
+  T.ncells = T.cell_off[F];
+  T.chunk.clear();
+  T.frame_chunk.assign(F + 1, 0);
+  for (int f = 0; f < F; ++f) {
+    for (int b = T.start[f]; b < T.start[f + 1]; b += kChunk) {
+      T.chunk.push_back(b);
+      T.chunk.push_back(std::min(b + kChunk, T.start[f + 1]));
+    }
+    T.frame_chunk[f + 1] = (int)T.chunk.size() / 2;
+  }
+  T.C = (int)T.chunk.size() / 2;
+  T.layout();
+  return DP_OK;
+}
+
+struct Bufs {
+  double* coord;
+  int* type;
+  int *nl_j, *nl_code, *counts;
+  int *cell_count, *cell_start, *cell_cursor, *cell_atoms, *atom_cell, *atom_img;
+  float4* atom_wf;
+  unsigned char* ftab;
+  int* atom_frame;
+  double* tshift;
+  int *perm, *type_start;
+  double *energy, *virial, *force, *atom_energy, *atom_virial, *cpart, *epart;
+};
+
+void carve(Arena& ar, const DeviceModel& m, const FrameTables& T, bool own_nlist, bool copy_coord, bool copy_type,
+           bool host_e, bool host_v, bool host_f, bool dev_ae, Bufs& b) {
+  std::memset(&b, 0, sizeof(b));
+  const long N = T.N, nc = m.nc;
+  if (copy_coord) b.coord = ar.get<double>(3 * N);
+  if (copy_type) b.type = ar.get<int>(N);
+  if (own_nlist) {
+    b.nl_j = ar.get<int>(N * nc);
+    b.nl_code = ar.get<int>(N * nc);
+    b.counts = ar.get<int>(N * m.cfg.ntypes);
+    b.cell_count = ar.get<int>(T.ncells);
+    b.cell_start = ar.get<int>(T.ncells + 1);
+    b.cell_cursor = ar.get<int>(T.ncells);
+    b.cell_atoms = ar.get<int>(N);
+    b.atom_cell = ar.get<int>(N);
+    b.atom_img = ar.get<int>(3 * N);
+    b.atom_wf = ar.get<float4>(N);
+  }
+  b.ftab = ar.get<unsigned char>((long)T.bytes);
+  if (T.F > 1) b.atom_frame = ar.get<int>(N);
+  b.tshift = ar.get<double>(81L * T.F);
+  b.perm = ar.get<int>(N);
+  b.type_start = ar.get<int>(DP_MAX_TYPES + 1);
+  if (host_e) b.energy = ar.get<double>(T.F);
+  if (host_v) b.virial = ar.get<double>(9L * T.F);
+  if (host_f) b.force = ar.get<double>(3 * N);
+  if (!dev_ae) b.atom_energy = ar.get<double>(N);
+  b.atom_virial = ar.get<double>(9 * N);
+  b.cpart = ar.get<double>(10L * T.C);
+  b.epart = ar.get<double>((N + 255) / 256);
+}
+
+int host_bbox(const double* coord, int N, double* lohi) {
+  for (int a = 0; a < 3; ++a) {
+    lohi[a] = 1e300;
+    lohi[3 + a] = -1e300;
+  }
+  for (int i = 0; i < N; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lohi[a] = std::min(lohi[a], coord[3 * i + a]);
+      lohi[3 + a] = std::max(lohi[3 + a], coord[3 * i + a]);
+    }
+  return DP_OK;
+}
+
+// Bounding box of device coordinates (open boundaries), read back once.
+int device_bbox(dp_model* md, const double* dcoord, int N, cudaStream_t st, double* lohi) {
+  double* d = nullptr;
+  DP_CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * 6, st));
+  {
+    ProfScope _ps(&md->prof, "bbox", st);
+    DP_CUDA_TRY(launch_bbox(dcoord, N, d, st));
+  }
+  DP_CUDA_TRY(cudaMemcpyAsync(lohi, d, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+  DP_CUDA_TRY(cudaFreeAsync(d, st));
+  DP_CUDA_TRY(cudaStreamSynchronize(st));
+  return DP_OK;
+}
+
+PathConst make_pc(const DeviceModel& m, int N) {
+  PathConst pc;
+  std::memset(&pc, 0, sizeof(pc));
+  pc.natoms = N;
+  pc.nc = m.nc;
+  pc.M = m.M;
+  pc.A = m.A;
+  pc.ntypes = m.cfg.ntypes;
+  pc.type_one_side = m.cfg.type_one_side;
+  for (int t = 0; t < m.cfg.ntypes; ++t) pc.sel[t] = m.cfg.sel[t];
+  for (int t = 0; t <= m.cfg.ntypes; ++t) pc.sel_off[t] = m.sel_off[t];
+  pc.rs = m.cfg.rcut_smth;
+  pc.rc = m.cfg.rcut;
+  return pc;
+}
+
+int run_path(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& ar, cudaStream_t st) {
+  if (m.compressed) return run_compressed(m, pc, io, ar, st);
+  if (m.precision == DP_PREC_FP64) return run_generic<double>(m, pc, m.p64, io, ar, st);
+  return run_generic<float>(m, pc, m.p32, io, ar, st);
+}
+
+// The whole path over F frames.  nlist (F == 1 only) replaces the internal list build.
+int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const double* coord, const int* type,
+               const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
+               cudaStream_t st) {
+  const DeviceModel& m = md->m;
+  DP_CUDA_TRY(cudaSetDevice(m.device));
+  const bool copy_coord = !is_device_ptr(coord), copy_type = !is_device_ptr(type);
+  const bool host_e = !is_device_ptr(energy), host_f = !is_device_ptr(force), host_v = !is_device_ptr(virial);
+  const bool dev_ae = atom_energy && is_device_ptr(atom_energy);
+  const bool own_nlist = (nlist == nullptr);
+  int Ntot = 0;
+  for (int f = 0; f < F; ++f) Ntot += natoms[f];
+  // open boundaries (one frame): the cell grid needs the bounding box first
+  double lohi[6] = {0, 0, 0, 0, 0, 0};
+  if (!boxes) {
+    if (F != 1) {
+      set_error("batches of frames need periodic cells");
+      return DP_E_UNSUPPORTED;
+    }
+    const int rc = copy_coord ? host_bbox(coord, Ntot, lohi) : device_bbox(md, coord, Ntot, st, lohi);
+    if (rc != DP_OK) return rc;
+  }
+  FrameTables T;
+  int rc = build_tables_host(md, F, natoms, boxes, lohi, T);
+  if (rc != DP_OK) return rc;
+  const int N = T.N;
+  PathConst pc = make_pc(m, N);
+  PathIO io;
+  std::memset(&io, 0, sizeof(io));
+  // sizing pass, then the real carve
+  Arena pre;
+  pre.measure = true;
+  Bufs b;
+  carve(pre, m, T, own_nlist, copy_coord, copy_type, host_e, host_v, host_f, dev_ae, b);
+  rc = run_path(m, pc, io, pre, st);
+  if (rc != DP_OK) return rc;
+  rc = ensure_ws(md, pre.used);
+  if (rc == DP_OK) rc = ensure_stage(md, T.bytes);
+  if (rc != DP_OK) return rc;
+  Arena ar;
+  ar.base = md->ws;
+  ar.cap = md->ws_cap;
+  carve(ar, m, T, own_nlist, copy_coord, copy_type, host_e, host_v, host_f, dev_ae, b);
+  const double* dcoord = copy_coord ? b.coord : coord;
+  const int* dtype = copy_type ? b.type : type;
+  if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
+  if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  T.pack(md->stage);
+  DP_CUDA_TRY(cudaMemcpyAsync(b.ftab, md->stage, T.bytes, cudaMemcpyHostToDevice, st));
+  const NlGeom* d_geoms = reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms);
+  const int* d_celloff = reinterpret_cast<const int*>(b.ftab + T.off_celloff);
+  const int* d_start = reinterpret_cast<const int*>(b.ftab + T.off_start);
+  const int* d_chunk = reinterpret_cast<const int*>(b.ftab + T.off_chunk);
+  const int* d_fchunk = reinterpret_cast<const int*>(b.ftab + T.off_fchunk);
+  const double* d_boxes = reinterpret_cast<const double*>(b.ftab + T.off_boxes);
+  DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
+  if (F > 1) {
+    ProfScope _ps(&md->prof, "atom_frame", st);
+    k_atom_frame<<<(N + 255) / 256, 256, 0, st>>>(d_start, F, N, b.atom_frame);
+  }
+  if (own_nlist) {
+    NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr};
+    ProfScope _ps(&md->prof, "nlist", st, 4);
+    DP_CUDA_TRY(launch_nlist_build(L, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor, b.cell_atoms,
+                                   b.atom_cell, b.atom_img, b.atom_wf, b.nl_j, b.nl_code, b.counts, md->status, st));
+  }
+  {
+    ProfScope _ps(&md->prof, "type_perm", st);
+    DP_CUDA_TRY(launch_type_perm(dtype, N, m.cfg.ntypes, b.perm, b.type_start, &md->status->bad_type, st));
+  }
+  rc = type_starts(copy_type ? type : nullptr, b.type_start, N, m.cfg.ntypes, st, io.type_start);
+  if (rc != DP_OK) return rc;
+  pc.nframes = F;
+  pc.periodic = T.periodic;
+  pc.atom_frame = b.atom_frame;
+  pc.boxes = F > 1 ? d_boxes : nullptr;
+  for (int k = 0; k < 9; ++k) pc.h[k] = T.geoms[0].h[k];
+  if (T.periodic) {
+    pc.tshift = b.tshift;
+    ProfScope _ps(&md->prof, "shift_table", st);
+    k_shift_tables<<<F, 32, 0, st>>>(d_boxes, b.tshift);
+  }
+  io.prof = &md->prof;
+  io.coord = dcoord;
+  io.type = dtype;
+  io.perm = b.perm;
+  io.nl_j = own_nlist ? b.nl_j : nlist->nl_j;
+  io.nl_code = own_nlist ? b.nl_code : nlist->nl_code;
+  io.force = host_f ? b.force : force;
+  io.atom_energy = dev_ae ? atom_energy : b.atom_energy;
+  io.atom_virial = b.atom_virial;
+  io.status = md->status;
+  io.epart = b.epart;
+  DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, st));
+  if (!m.compressed) DP_CUDA_TRY(cudaMemsetAsync(io.atom_virial, 0, sizeof(double) * 9 * N, st));
+  rc = run_path(m, pc, io, ar, st);
+  if (rc != DP_OK) return rc;
+  double* d_energy = host_e ? b.energy : energy;
+  double* d_virial = host_v ? b.virial : virial;
+  {
+    ProfScope _ps(&md->prof, "frame_sums", st, 2);
+    k_chunk_sums<<<T.C, 256, 0, st>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
+    k_frame_sums<<<F, 32, 0, st>>>(d_fchunk, b.cpart, d_energy, d_virial);
+  }
+  DP_CUDA_TRY(cudaGetLastError());
+  if (host_e) DP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+  if (host_v) DP_CUDA_TRY(cudaMemcpyAsync(virial, d_virial, sizeof(double) * 9 * F, cudaMemcpyDeviceToHost, st));
+  if (host_f) DP_CUDA_TRY(cudaMemcpyAsync(force, io.force, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
+  if (atom_energy && !dev_ae)
+    DP_CUDA_TRY(cudaMemcpyAsync(atom_energy, io.atom_energy, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  rc = read_status(md, st, nullptr);
+  if (rc == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
+    md->nl_full_cap = true;  // retry once with the full candidate buffer
+    return run_frames(md, nlist, F, natoms, coord, type, boxes, energy, force, virial, atom_energy, st);
+  }
+  return rc;
+}
+
+}  // namespace
+}  // namespace dpgb
+
+using namespace dpgb;
+
+extern "C" {
+
+int dp_compute(dp_model* md, dp_nlist* nlist, int N, const double* coord, const int* type, const double* box,
+               double* energy, double* force, double* virial, double* atom_energy, void* stream) {
+  if (!md || !coord || !type || !energy || !force || !virial || N < 1) {
+    set_error("invalid argument");
+    return DP_E_ARG;
+  }
+  if (nlist && (nlist->natoms != N || nlist->nc != md->m.nc || nlist->device != md->m.device)) {
+    set_error("neighbour list does not match this frame/model");
+    return DP_E_ARG;
+  }
+  return run_frames(md, nlist, 1, &N, coord, type, box, energy, force, virial, atom_energy, (cudaStream_t)stream);
+}
+
+int dp_compute_batch(dp_model* md, int nframes, const int* natoms, const double* coord, const int* type,
+                     const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
+                     void* stream) {
+  if (!md || nframes < 1 || !natoms || !coord || !type || !boxes || !energy || !force || !virial) {
+    set_error("invalid argument");
+    return DP_E_ARG;
+  }
+  return run_frames(md, nullptr, nframes, natoms, coord, type, boxes, energy, force, virial, atom_energy,
+                    (cudaStream_t)stream);
+}
+
+int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, const double* box, dp_nlist** out,
+                   int* n_overflow, void* stream) {
+  if (!md || !coord || !type || !out || N < 1) {
+    set_error("invalid argument");
+    return DP_E_ARG;
+  }
+  *out = nullptr;
+  DP_CUDA_TRY(cudaSetDevice(md->m.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const DeviceModel& m = md->m;
+  const bool copy_coord = !is_device_ptr(coord), copy_type = !is_device_ptr(type);
+  double lohi[6] = {0, 0, 0, 0, 0, 0};
+  if (!box) {
+    const int rc = copy_coord ? host_bbox(coord, N, lohi) : device_bbox(md, coord, N, st, lohi);
+    if (rc != DP_OK) return rc;
+  }
+  FrameTables T;
+  int rc = build_tables_host(md, 1, &N, box, lohi, T);
+  if (rc != DP_OK) return rc;
+  Arena pre;
+  pre.measure = true;
+  Bufs b;
+  carve(pre, m, T, true, copy_coord, copy_type, false, false, false, false, b);
+  rc = ensure_ws(md, pre.used);
+  if (rc == DP_OK) rc = ensure_stage(md, T.bytes);
+  if (rc != DP_OK) return rc;
+  Arena ar;
+  ar.base = md->ws;
+  ar.cap = md->ws_cap;
+  carve(ar, m, T, true, copy_coord, copy_type, false, false, false, false, b);
+  const double* dcoord = copy_coord ? b.coord : coord;
+  const int* dtype = copy_type ? b.type : type;
+  if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
+  if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  T.pack(md->stage);
+  DP_CUDA_TRY(cudaMemcpyAsync(b.ftab, md->stage, T.bytes, cudaMemcpyHostToDevice, st));
+  dp_nlist* nl = new dp_nlist();
+  nl->device = m.device;
+  nl->natoms = N;
+  nl->nc = m.nc;
+  nl->ntypes = m.cfg.ntypes;
+  cudaError_t e = cudaMalloc(&nl->nl_j, sizeof(int) * (size_t)N * nl->nc);
+  if (e == cudaSuccess) e = cudaMalloc(&nl->nl_code, sizeof(int) * (size_t)N * nl->nc);
+  if (e == cudaSuccess) e = cudaMalloc(&nl->counts, sizeof(int) * (size_t)N * nl->ntypes);
+  if (e != cudaSuccess) {
+    set_error(std::string("nlist allocation: ") + cudaGetErrorString(e));
+    dp_free_nlist(nl);
+    return DP_E_OOM;
+  }
+  DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
+  {
+    NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr};
+    ProfScope _ps(&md->prof, "nlist", st, 4);
+    DP_CUDA_TRY(launch_nlist_build(L, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor, b.cell_atoms,
+                                   b.atom_cell, b.atom_img, b.atom_wf, nl->nl_j, nl->nl_code, nl->counts, md->status,
+                                   st));
+  }
+  rc = read_status(md, st, n_overflow);
+  if (rc != DP_OK && rc != DP_E_SEL_OVERFLOW) {
+    dp_free_nlist(nl);
+    if (rc == DP_E_CAPACITY && !md->nl_full_cap) {
+      md->nl_full_cap = true;  // retry once with the full candidate buffer
+      return dp_build_nlist(md, N, coord, type, box, out, n_overflow, stream);
+    }
+    return rc;
+  }
+  *out = nl;
+  return rc;
+}
+
+}  // extern "C"

@@ -85,9 +85,12 @@ __device__ __forceinline__ double widen_f32(float x) {
 __device__ __forceinline__ double widen(float x) { return widen_f32(x); }
 __device__ __forceinline__ double widen(double x) { return x; }
 
-// Exact FP64 displacement of a listed pair; the same-image case needs no shift term.
+// Frame of atom i and that frame's cell rows / image-shift table.
+__device__ __forceinline__ int frame_of(const PathConst& pc, int i) { return pc.atom_frame ? pc.atom_frame[i] : 0; }
+
+// Exact FP64 displacement of a listed pair of frame fr; the same-image case needs no shift term.
 __device__ __forceinline__ void listed_disp(const double* __restrict__ xi, const double* __restrict__ xj, int code,
-                                            const PathConst& pc, double& d0, double& d1, double& d2) {
+                                            const PathConst& pc, int fr, double& d0, double& d1, double& d2) {
   int n0, n1, n2;
   unpack_shift(code, n0, n1, n2);
   if ((n0 | n1 | n2) == 0) {
@@ -96,15 +99,15 @@ __device__ __forceinline__ void listed_disp(const double* __restrict__ xi, const
     d2 = __dsub_rn(xj[2], xi[2]);
   } else if (pc.tshift && n0 >= -1 && n0 <= 1 && n1 >= -1 && n1 <= 1 && n2 >= -1 && n2 <= 1) {
     // t(n) precomputed with the builder's formula: (x_j + t) - x_i, bit for bit
-    const double* t = pc.tshift + 3 * ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1));
+    const double* t = pc.tshift + (long)fr * 81 + 3 * ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1));
     d0 = __dsub_rn(__dadd_rn(xj[0], t[0]), xi[0]);
     d1 = __dsub_rn(__dadd_rn(xj[1], t[1]), xi[1]);
     d2 = __dsub_rn(__dadd_rn(xj[2], t[2]), xi[2]);
   } else {
-    pair_disp_exact(xi, xj, n0, n1, n2, pc.h, pc.periodic, d0, d1, d2);
+    const double* h = pc.boxes ? pc.boxes + 9L * fr : pc.h;
+    pair_disp_exact(xi, xj, n0, n1, n2, h, pc.periodic, d0, d1, d2);
   }
 }
-
 
 __device__ __forceinline__ int slot_block(const PathConst& pc, int k) {
   int t = 0;

@@ -51,10 +51,14 @@ __global__ void k_bbox(const double* __restrict__ coord, int n, double* __restri
   }
 }
 
-__global__ void k_bin(NlGeom g, const double* __restrict__ coord, int* __restrict__ cell_count,
-                      int* __restrict__ atom_cell, int* __restrict__ atom_img, float4* __restrict__ atom_wf) {
+__global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame,
+                      const int* __restrict__ cell_off, int natoms, const double* __restrict__ coord,
+                      int* __restrict__ cell_count, int* __restrict__ atom_cell, int* __restrict__ atom_img,
+                      float4* __restrict__ atom_wf) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.natoms) return;
+  if (i >= natoms) return;
+  const int fr = atom_frame ? atom_frame[i] : 0;
+  const NlGeom& g = G[fr];
   double x[3] = {coord[3 * i], coord[3 * i + 1], coord[3 * i + 2]};
   int c[3], m[3];
   float w[3];
@@ -73,7 +77,7 @@ __global__ void k_bin(NlGeom g, const double* __restrict__ coord, int* __restric
     c[d] = cd < 0 ? 0 : (cd >= g.ncell[d] ? g.ncell[d] - 1 : cd);
     w[d] = (float)wd;
   }
-  int flat = (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
+  int flat = (cell_off ? cell_off[fr] : 0) + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
   atom_cell[i] = flat;
   atom_img[3 * i] = m[0];
   atom_img[3 * i + 1] = m[1];
@@ -138,7 +142,8 @@ struct KeyLess {
 
 template <int CAP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_nlist(NlGeom g, const double* __restrict__ coord, const int* __restrict__ type,
+    k_nlist(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, const int* __restrict__ cell_off,
+            int natoms, const double* __restrict__ coord, const int* __restrict__ type,
             const int* __restrict__ cell_start, const int* __restrict__ cell_atoms, const int* __restrict__ atom_cell,
             const int* __restrict__ atom_img, const float4* __restrict__ atom_wf, int* __restrict__ nl_j,
             int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
@@ -150,14 +155,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   unsigned char* k_t = smem + (size_t)kWarpsPerBlock * CAP * 16 + (size_t)warp * CAP;
 
   const int w = blockIdx.x * kWarpsPerBlock + warp;
-  if (w >= g.natoms) return;  // warp-uniform
+  if (w >= natoms) return;  // warp-uniform
   // consecutive warps take atoms of the same cell, so their candidates share the L1 cache
   const int i = cell_atoms[w];
+  const int fr = atom_frame ? atom_frame[i] : 0;
+  const NlGeom& g = G[fr];
+  const int coff = cell_off ? cell_off[fr] : 0;
 
   const double xi[3] = {coord[3 * i], coord[3 * i + 1], coord[3 * i + 2]};
   const int mi0 = atom_img[3 * i], mi1 = atom_img[3 * i + 1], mi2 = atom_img[3 * i + 2];
   const float4 wi = atom_wf[i];
-  const int ci = atom_cell[i];
+  const int ci = atom_cell[i] - coff;
   const int c2 = ci % g.ncell[2];
   const int c1 = (ci / g.ncell[2]) % g.ncell[1];
   const int c0 = ci / (g.ncell[2] * g.ncell[1]);
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         } else if (v0 < 0 || v1 < 0 || v2 < 0 || v0 >= g.ncell[0] || v1 >= g.ncell[1] || v2 >= g.ncell[2]) {
           continue;
         }
-        const int cell = (v0 * g.ncell[1] + v1) * g.ncell[2] + v2;
+        const int cell = coff + (v0 * g.ncell[1] + v1) * g.ncell[2] + v2;
         const int beg = cell_start[cell], end = cell_start[cell + 1];
         for (int base = beg; base < end; base += 32) {
           const int idx = base + lane;
@@ -459,26 +467,28 @@ cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_nlist_build(const NlGeom& g, const double* coord, const int* type, int* cell_count,
+cudaError_t launch_nlist_build(const NlLaunch& L, const double* coord, const int* type, int* cell_count,
                                int* cell_start, int* cell_cursor, int* cell_atoms, int* atom_cell, int* atom_img,
                                float4* atom_wf, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st) {
-  const int ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
+  const int ncells = L.ncells_total;
   cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncells, st);
   if (e != cudaSuccess) return e;
-  const int nb = (g.natoms + 255) / 256;
-  k_bin<<<nb, 256, 0, st>>>(g, coord, cell_count, atom_cell, atom_img, atom_wf);
+  const int nb = (L.natoms + 255) / 256;
+  k_bin<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, coord, cell_count, atom_cell, atom_img,
+                            atom_wf);
   k_scan_excl<<<1, 1024, 0, st>>>(cell_count, ncells, cell_start, cell_cursor);
-  k_fill<<<nb, 256, 0, st>>>(g.natoms, atom_cell, cell_cursor, cell_atoms);
-  const int cap = g.cap <= 128 ? 128 : (g.cap <= 256 ? 256 : (g.cap <= 512 ? 512 : 1024));
+  k_fill<<<nb, 256, 0, st>>>(L.natoms, atom_cell, cell_cursor, cell_atoms);
+  const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));
   const size_t smem = (size_t)kWarpsPerBlock * cap * 17 + (size_t)kWarpsPerBlock * 2 * kQueue * sizeof(int);
-  const unsigned blocks = (g.natoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
-#define DPGB_NL_LAUNCH(C)                                                                                  \
-  do {                                                                                                     \
-    e = cudaFuncSetAttribute(k_nlist<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
-    if (e != cudaSuccess) return e;                                                                        \
-    k_nlist<C><<<blocks, kWarpsPerBlock * 32, smem, st>>>(g, coord, type, cell_start, cell_atoms, atom_cell, \
-                                                         atom_img, atom_wf, nl_j, nl_code, counts, status); \
+  const unsigned blocks = (L.natoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
+#define DPGB_NL_LAUNCH(C)                                                                                   \
+  do {                                                                                                      \
+    e = cudaFuncSetAttribute(k_nlist<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    if (e != cudaSuccess) return e;                                                                         \
+    k_nlist<C><<<blocks, kWarpsPerBlock * 32, smem, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, coord, \
+                                                         type, cell_start, cell_atoms, atom_cell, atom_img,   \
+                                                         atom_wf, nl_j, nl_code, counts, status);             \
   } while (0)
   if (cap == 128)
     DPGB_NL_LAUNCH(128);

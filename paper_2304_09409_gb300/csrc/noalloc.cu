@@ -38,7 +38,8 @@ constexpr size_t kOffCode = kOffAtomWf + align256(sizeof(float4) * kMaxAtoms);
 constexpr size_t kOffCounts = kOffCode + align256(sizeof(int) * kMaxSlots);
 constexpr size_t kOffStatus = kOffCounts + align256(sizeof(int) * DP_MAX_TYPES * kMaxAtoms);
 constexpr size_t kOffBbox = kOffStatus + align256(sizeof(DevStatus));
-constexpr size_t kScratchBytes = kOffBbox + align256(sizeof(double) * 6);
+constexpr size_t kOffGeom = kOffBbox + align256(sizeof(double) * 6);
+constexpr size_t kScratchBytes = kOffGeom + align256(sizeof(NlGeom));
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -131,6 +132,7 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   int* counts = reinterpret_cast<int*>(s + kOffCounts);
   DevStatus* status = reinterpret_cast<DevStatus*>(s + kOffStatus);
   double* bbox = reinterpret_cast<double*>(s + kOffBbox);
+  NlGeom* geom = reinterpret_cast<NlGeom*>(s + kOffGeom);
 
   double lohi[6] = {0, 0, 0, 0, 0, 0};
   if (!box) {
@@ -147,7 +149,9 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
     return DP_E_ARG;
   }
   DP_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
-  DP_CUDA_TRY(launch_nlist_build(g, coord, type, cell_count, cell_start, cell_cursor, cell_atoms, atom_cell, atom_img,
+  DP_CUDA_TRY(cudaMemcpyAsync(geom, &g, sizeof(NlGeom), cudaMemcpyHostToDevice, st));
+  const NlLaunch L{natoms, g.ncell[0] * g.ncell[1] * g.ncell[2], g.cap, geom, nullptr, nullptr};
+  DP_CUDA_TRY(launch_nlist_build(L, coord, type, cell_count, cell_start, cell_cursor, cell_atoms, atom_cell, atom_img,
                                  atom_wf, nl_j, code, counts, status, st));
   const long n = (long)natoms * nc;
   k_unpack_shift<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(code, n, nl_shift);

@@ -32,10 +32,8 @@ __global__ void k_env(PathConst pc, const double* __restrict__ coord, const int*
   const int j = nl_j[(long)i * pc.nc + k];
   R o[4] = {R(0), R(0), R(0), R(0)};
   if (j >= 0) {
-    int n0, n1, n2;
-    unpack_shift(nl_code[(long)i * pc.nc + k], n0, n1, n2);
     double d0, d1, d2;
-    pair_disp_exact(coord + 3 * i, coord + 3 * j, n0, n1, n2, pc.h, pc.periodic, d0, d1, d2);
+    listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d0, d1, d2);
     const double r2 = norm2_exact(d0, d1, d2);
     R r, s, ds, u[3];
     pair_env<R>(d0, d1, d2, r2, pc.rs, pc.rc, pc.near2, r, s, ds, u);
@@ -177,20 +175,15 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_force(PathConst pc, const double* __restrict__ coord, const int* __restrict__ perm,
             const int* __restrict__ nl_j, const int* __restrict__ nl_code, const R* __restrict__ gs_emb,
-            const R* __restrict__ gR, double* __restrict__ force, double* __restrict__ vpart) {
+            const R* __restrict__ gR, double* __restrict__ force, double* __restrict__ avir) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  double v[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) v[q] = 0.0;
   if (row < (long)pc.natoms * pc.nc) {
     const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
     const int i = perm[p];
     const int j = nl_j[(long)i * pc.nc + k];
     if (j >= 0) {
-      int n0, n1, n2;
-      unpack_shift(nl_code[(long)i * pc.nc + k], n0, n1, n2);
       double d[3];
-      pair_disp_exact(coord + 3 * i, coord + 3 * j, n0, n1, n2, pc.h, pc.periodic, d[0], d[1], d[2]);
+      listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d[0], d[1], d[2]);
       const double r2 = norm2_exact(d[0], d[1], d[2]);
       R r, s, ds, u[3];
       pair_env<R>(d[0], d[1], d[2], r2, pc.rs, pc.rc, pc.near2, r, s, ds, u);
@@ -210,22 +203,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-        for (int bb = 0; bb < 3; ++bb) v[aa * 3 + bb] = -gd[aa] * d[bb];
+        for (int bb = 0; bb < 3; ++bb) atomicAdd(avir + 9L * i + aa * 3 + bb, -gd[aa] * d[bb]);
     }
-  }
-  __shared__ double sv[8][9];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    double x = v[q];
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) sv[warp][q] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 9) {
-    double x = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += sv[w][threadIdx.x];
-    vpart[(long)blockIdx.x * 9 + threadIdx.x] = x;
   }
 }
 
@@ -247,26 +226,12 @@ __global__ void k_sum_rows(const double* __restrict__ in, long n, int w, double*
   }
 }
 
-// Per-atom energies in input order and per-block partial FP64 sums (one value per thread,
-// widened with integer operations for FP32 inputs).
+// Per-atom energies from the sorted order to input order, widened to FP64.
 template <class R>
 __global__ void k_energy(const R* __restrict__ Esorted, const int* __restrict__ perm, int n,
-                         double* __restrict__ atom_e, double* __restrict__ partial) {
-  __shared__ double red[8];
+                         double* __restrict__ atom_e) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0;
-  if (p < n) {
-    e = widen(Esorted[p]);
-    if (atom_e) atom_e[perm[p]] = e;
-  }
-  for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-    partial[blockIdx.x] = t;
-  }
+  if (p < n) atom_e[perm[p]] = widen(Esorted[p]);
 }
 
 // Translation vectors t(n) = n0 h0 + n1 h1 + n2 h2 for n in {-1,0,1}^3, formed exactly as the
@@ -335,9 +300,7 @@ int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, cons
   }
   {
     ProfScope _ps(io.prof, "energy_sum", st);
-    const unsigned eb = nblk(N, 256);
-    k_energy<R><<<eb, 256, 0, st>>>(Yf[nfl - 1], io.perm, (int)N, io.atom_energy, io.epart);
-    k_sum_rows<<<1, 256, 0, st>>>(io.epart, eb, 1, io.energy);
+    k_energy<R><<<nblk(N, 256), 256, 0, st>>>(Yf[nfl - 1], io.perm, (int)N, io.atom_energy);
   }
   // backward through the fitting net, seeded with dE_i/dE_i = 1
   {
@@ -383,7 +346,6 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   R* gs = ar.get<R>(rows);
   int* tsorted = ar.get<int>(N);
   const unsigned fblocks = nblk(rows, 256);
-  double* vpart = ar.get<double>((long)fblocks * 9);
   const R* gD = nullptr;
   if (ar.measure) return run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
   if (!ar.ok()) {
@@ -466,11 +428,8 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   // ---- forces and virial ----
   {
     ProfScope _ps(io.prof, "force", st);
-    k_force<R><<<fblocks, 256, 0, st>>>(pc, io.coord, io.perm, io.nl_j, io.nl_code, gs, gR, io.force, vpart);
-  }
-  {
-    ProfScope _ps(io.prof, "virial_sum", st);
-    k_sum_rows<<<9, 256, 0, st>>>(vpart, fblocks, 9, io.virial);
+    k_force<R><<<fblocks, 256, 0, st>>>(pc, io.coord, io.perm, io.nl_j, io.nl_code, gs, gR, io.force,
+                                         io.atom_virial);
   }
   DP_CUDA_TRY(cudaGetLastError());
   return DP_OK;
@@ -478,9 +437,7 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
 
 cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
                               double* epart, cudaStream_t st) {
-  const unsigned eb = (unsigned)((n + 255) / 256);
-  k_energy<float><<<eb, 256, 0, st>>>(Esorted, perm, n, atom_e, epart);
-  k_sum_rows<<<1, 256, 0, st>>>(epart, eb, 1, energy);
+  k_energy<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Esorted, perm, n, atom_e);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,10 @@ struct PathConst {
   int periodic;
   double rs, rc;
   double near2;  // unused (kept for layout)
-  const double* tshift;  // device [27][3]: t(n) for n in {-1,0,1}^3, or null
+  const double* tshift;  // device [frames][27][3]: t(n) for n in {-1,0,1}^3, or null
+  int nframes;
+  const int* atom_frame;  // device [natoms] frame of each atom, or null (one frame)
+  const double* boxes;    // device [frames][9] cell rows, or null (one frame: h)
 };
 
 // Per-kernel CUDA-event timing and launch counting.  Every kernel launch of the path sits in
@@ -113,7 +116,8 @@ struct PathIO {
   double* energy;       // device [1]
   double* force;        // device [N][3], zeroed by the caller
   double* virial;       // device [9]
-  double* atom_energy;  // device [N] or null
+  double* atom_energy;  // device [N] (always written, input order)
+  double* atom_virial;  // device [N][9] per-atom virial (input order)
   DevStatus* status;    // device status words
   double* epart;        // device scratch for per-block energy partials [ceil(N/256)]
 };

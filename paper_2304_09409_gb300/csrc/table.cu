@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256)
   const int j = nl_j[slot];
   if (j < 0) return;  // padding is never read
   double d0, d1, d2;
-  listed_disp(coord + 3 * i, coord + 3 * j, nl_code[slot], pc, d0, d1, d2);
+  listed_disp(coord + 3 * i, coord + 3 * j, nl_code[slot], pc, frame_of(pc, i), d0, d1, d2);
   R r, s, ds, u[3];
   pair_env<R>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
   env[row * 2] = Vec4<R>::make(s, u[0], u[1], u[2]);
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(128)
     k_tab_bwd(PathConst pc, TabConst tc, const R* __restrict__ tab, const double* __restrict__ coord,
               const int* __restrict__ perm, const int* __restrict__ type, const int* __restrict__ nl_j,
               const typename Vec4<R>::T* __restrict__ env, const R* __restrict__ Tm,
-              const R* __restrict__ gD, double* __restrict__ force, double* __restrict__ vpart) {
+              const R* __restrict__ gD, double* __restrict__ force, double* __restrict__ avir) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = pc.M, nc = pc.nc, A = pc.A;
@@ -440,17 +440,13 @@ __global__ void __launch_bounds__(128)
       atomicAdd(force + 3 * i + 2, widen(fi2));
     }
   }
-  __shared__ double sv[4][9];
+  // per-atom virial (input order): one warp owns one atom
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     R x = v[q];
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) sv[warp][q] = widen(x);
+    if (lane == 0 && p < pc.natoms) avir[9L * perm[p] + q] = widen(x);
   }
-  __syncthreads();
-  if (threadIdx.x < 9)
-    vpart[(long)blockIdx.x * 9 + threadIdx.x] =
-        sv[0][threadIdx.x] + sv[1][threadIdx.x] + sv[2][threadIdx.x] + sv[3][threadIdx.x];
 }
 
 template <class R, class DT>
@@ -464,7 +460,6 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   typedef typename Vec4<R>::T V4;
   V4* env = ar.get<V4>(N * pc.nc * 2);
   const unsigned blocks = (unsigned)((N + 3) / 4);
-  double* vpart = ar.get<double>((long)blocks * 9);
   const R* gD = nullptr;
   if (ar.measure) {
     if constexpr (kTensor) {
@@ -515,13 +510,9 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   {
     ProfScope _ps(io.prof, "tab_bwd", st);
     k_tab_bwd<R><<<blocks, 128, smem, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,
-                                            gD, io.force, vpart);
+                                            gD, io.force, io.atom_virial);
   }
   DP_CUDA_TRY(cudaGetLastError());
-  {
-    ProfScope _ps(io.prof, "virial_sum", st);
-    DP_CUDA_TRY(launch_sum_rows(vpart, blocks, 9, io.virial, st));
-  }
   return DP_OK;
 }
 

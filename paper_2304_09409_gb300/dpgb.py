@@ -31,7 +31,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 EXPORTED = [
     "dp_model_create", "dp_init_model", "dp_free_model", "dp_model_n_params", "dp_build_nlist",
     "dp_nlist_export", "dp_free_nlist", "dp_compute", "dp_model_export_table", "dp_last_error",
-    "dp_build_nlist_noalloc",
+    "dp_build_nlist_noalloc", "dp_compute_batch",
 ]
 
 
@@ -260,6 +260,47 @@ class Model:
         _check(code, allow=allow)
         self.last_status = code
         return e, f, v, ae
+
+
+def _batch_argtypes():
+    L = lib()
+    vp = ctypes.c_void_p
+    L.dp_compute_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    return L
+
+
+def compute_batch(model: "Model", natoms, coord, atype, boxes, atom_energy: bool = False, stream=None, out=None,
+                  allow=(DP_E_SEL_OVERFLOW,)):
+    """dp_compute_batch: several frames of one model in one pass.
+
+    natoms: int32 array [F]; coord [sum(natoms), 3], atype [sum(natoms)] (numpy or torch CUDA);
+    boxes [F, 3, 3] numpy.  Returns (energy [F], force [sum, 3], virial [F, 3, 3], atom_energy)."""
+    L = _batch_argtypes()
+    nat = np.ascontiguousarray(natoms, dtype=np.int32)
+    F = int(nat.size)
+    N = int(nat.sum())
+    bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(F, 9)
+    if _is_torch(coord) and coord.is_cuda:
+        import torch
+        if out is None:
+            e = torch.empty(F, dtype=torch.float64, device=coord.device)
+            f = torch.empty((N, 3), dtype=torch.float64, device=coord.device)
+            v = torch.empty((F, 3, 3), dtype=torch.float64, device=coord.device)
+            ae = torch.empty(N, dtype=torch.float64, device=coord.device) if atom_energy else None
+        else:
+            e, f, v, ae = out
+    else:
+        coord = np.ascontiguousarray(coord, dtype=np.float64)
+        atype = np.ascontiguousarray(atype, dtype=np.int32)
+        if out is None:
+            e, f, v = np.zeros(F), np.zeros((N, 3)), np.zeros((F, 3, 3))
+            ae = np.zeros(N) if atom_energy else None
+        else:
+            e, f, v, ae = out
+    code = L.dp_compute_batch(model.handle, F, nat.ctypes.data, _ptr(coord), _ptr(atype), bx.ctypes.data, _ptr(e),
+                              _ptr(f), _ptr(v), _ptr(ae), _stream_handle(stream))
+    _check(code, allow=allow)
+    return e, f, v, ae
 
 
 def n_params(cfg) -> int:
