@@ -254,3 +254,38 @@ def atom_subset(cfg, params, coord, atype, box, idx):
     _L().orc_atom_subset(ctypes.byref(c), _d(_f64(params)), coord.shape[0], _d(coord), _i(_i32(atype)), _d(_f64(box)),
                          S, _i(idx), _i(nl_j), _i(nl_s), _d(e))
     return nl_j, nl_s, e
+
+
+def _pack_frames(cfg, frames):
+    nat = np.array([f.natoms for f in frames], dtype=np.int32)
+    coord = np.ascontiguousarray(np.concatenate([f.coord for f in frames]), dtype=np.float64)
+    atype = np.ascontiguousarray(np.concatenate([f.atype for f in frames]), dtype=np.int32)
+    boxes = np.ascontiguousarray(np.stack([f.box for f in frames]).reshape(-1, 9), dtype=np.float64)
+    njs, nss, off = [], [], 0
+    for f in frames:
+        nj, ns, _, _ = nlist(cfg, f.coord, f.atype, f.box)
+        njs.append(np.where(nj >= 0, nj + off, -1))
+        nss.append(ns)
+        off += f.natoms
+    return nat, coord, atype, boxes, np.ascontiguousarray(np.concatenate(njs), dtype=np.int32), \
+        np.ascontiguousarray(np.concatenate(nss), dtype=np.int32)
+
+
+def loss_dir(cfg, params, vdir, frames, e_ref, f_ref, pE=1.0, pF=1.0):
+    """Energy+force loss of a batch of frames (Sec. II.B) and its derivative along the
+    parameter direction vdir (hyper-dual numbers).  Returns (L, dL . vdir)."""
+    L_ = _L()
+    if not hasattr(L_, "_loss_set"):
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L_.orc_loss_dir.argtypes = [ctypes.POINTER(_Cfg), dp, dp, ctypes.c_int, ip, dp, ip, dp, ip, ip, dp, dp,
+                                    ctypes.c_double, ctypes.c_double, dp]
+        L_.orc_loss_dir.restype = ctypes.c_double
+        L_._loss_set = True
+    nat, coord, atype, boxes, nj, ns = _pack_frames(cfg, frames)
+    dL = ctypes.c_double()
+    c = _cfg(cfg)
+    val = L_.orc_loss_dir(ctypes.byref(c), _d(_f64(params)), _d(_f64(vdir)), len(frames), _i(nat), _d(coord),
+                          _i(atype), _d(boxes), _i(nj), _i(ns), _d(_f64(e_ref)), _d(_f64(np.concatenate(f_ref))),
+                          float(pE), float(pF), ctypes.byref(dL))
+    return val, dL.value

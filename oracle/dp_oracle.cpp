@@ -93,6 +93,37 @@ inline Jet jtanh(Jet a) {
   return Jet(t, g * a.d1, g * a.d2 - 2.0 * t * g * a.d1 * a.d1);
 }
 
+// Hyper-dual number v + a e1 + b e2 + ab e1 e2 (e1^2 = e2^2 = 0): the e1 e2 part of f(x) is an
+// exact mixed second derivative.  Used with e1 along a coordinate direction and e2 along a
+// parameter direction to differentiate the force term of the loss with respect to parameters.
+struct HD {
+  double v, a, b, ab;
+  HD(double x = 0.0, double p = 0.0, double q = 0.0, double r = 0.0) : v(x), a(p), b(q), ab(r) {}
+};
+inline HD operator+(HD x, HD y) { return HD(x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab); }
+inline HD operator-(HD x, HD y) { return HD(x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab); }
+inline HD operator*(HD x, HD y) {
+  return HD(x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b, x.ab * y.v + x.a * y.b + x.b * y.a + x.v * y.ab);
+}
+// f applied to x given f(v), f'(v), f''(v)
+inline HD hd_apply(HD x, double f, double f1, double f2) {
+  return HD(f, f1 * x.a, f1 * x.b, f1 * x.ab + f2 * x.a * x.b);
+}
+inline HD operator/(HD x, HD y) {
+  const double iv = 1.0 / y.v;
+  return x * hd_apply(y, iv, -iv * iv, 2.0 * iv * iv * iv);
+}
+inline bool operator<(HD x, HD y) { return x.v < y.v; }
+inline double val(HD x) { return x.v; }
+inline HD dsqrt(HD x) {
+  const double s = std::sqrt(x.v);
+  return hd_apply(x, s, 0.5 / s, -0.25 / (s * x.v));
+}
+inline HD dtanh(HD x) {
+  const double t = std::tanh(x.v), g = 1.0 - t * t;
+  return hd_apply(x, t, g, -2.0 * t * g);
+}
+
 // ------------------------------------------------------------------------------------------
 // Parameter layout helpers (flat FP64 array, see the inputs module)
 // ------------------------------------------------------------------------------------------
@@ -163,9 +194,8 @@ double switch_deriv(double r, double rs, double rc) {
 // ------------------------------------------------------------------------------------------
 // Dense layer, Eq. (NN), generic scalar
 // ------------------------------------------------------------------------------------------
-template <class T>
-void layer_forward(const double* W, const double* b, int n_in, int n_out, const T* x, T* y, bool tanh_act,
-                   bool resnet) {
+template <class T, class P>
+void layer_forward(const P* W, const P* b, int n_in, int n_out, const T* x, T* y, bool tanh_act, bool resnet) {
   int sk = resnet ? skip_kind(n_in, n_out) : 0;
   for (int o = 0; o < n_out; ++o) {
     T z = T(b[o]);
@@ -517,8 +547,8 @@ void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const 
 // ------------------------------------------------------------------------------------------
 // Templated energy (for the dual-number pins only): same definitions, generic scalar.
 // ------------------------------------------------------------------------------------------
-template <class T>
-T energy_generic(const OrcConfig& c, const Layout& L, const double* params, int N, const T* coord, const int* type,
+template <class T, class P>
+T energy_generic(const OrcConfig& c, const Layout& L, const P* params, int N, const T* coord, const int* type,
                  const T* box, const int* nl_j, const int* nl_code, T* atom_e) {
   const int nc = L.nc, M = L.m, A = L.axis;
   T E(0.0);
@@ -544,7 +574,7 @@ T energy_generic(const OrcConfig& c, const Layout& L, const double* params, int 
         int net = embed_net_index(c, ai, t);
         std::vector<T> x(1, s), y;
         for (int l = 0; l < c.n_embed; ++l) {
-          const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
+          const P* W = params + L.eoff[(size_t)net * c.n_embed + l];
           y.assign(L.eout[l], T(0.0));
           layer_forward(W, W + (long)L.ein[l] * L.eout[l], L.ein[l], L.eout[l], x.data(), y.data(), true, true);
           x = y;
@@ -562,7 +592,7 @@ T energy_generic(const OrcConfig& c, const Layout& L, const double* params, int 
       }
     const int nfl = (int)L.fin.size();
     for (int l = 0; l < nfl; ++l) {
-      const double* W = params + L.foff[(size_t)ai * nfl + l];
+      const P* W = params + L.foff[(size_t)ai * nfl + l];
       std::vector<T> y(L.fout[l]);
       bool last = l == nfl - 1;
       layer_forward(W, W + (long)L.fin[l] * L.fout[l], L.fin[l], L.fout[l], x.data(), y.data(), !last, !last);
@@ -826,6 +856,57 @@ int orc_atom_subset(const OrcConfig* cfg, const double* params, int N, const dou
     }
   }
   return ov;
+}
+
+// Loss of a batch of frames, Sec. II.B (loss function):
+//   L = (1/B) sum_f [ pE (E_f - E*_f)^2 / N_f + pF sum_i |F_i - F*_i|^2 / (3 N_f) ]
+// and its derivative along the parameter direction v.  Forces come from the reverse pass.
+// With Delta F = F - F*, sum_i Delta F_i . dF_i/dtheta . v = -d2E/(de1 de2) for the
+// perturbation r + e1 Delta F, theta + e2 v, which one hyper-dual evaluation gives exactly.
+// Frames are concatenated (natoms[f] atoms each); boxes [B][9]; lists [sum natoms][Nc] (+shift).
+double orc_loss_dir(const OrcConfig* cfg, const double* params, const double* vdir, int B, const int* natoms,
+                    const double* coord, const int* type, const double* boxes, const int* nl_j, const int* nl_shift,
+                    const double* e_ref, const double* f_ref, double pE, double pF, double* dL) {
+  Layout L = make_layout(*cfg);
+  const int nc = L.nc;
+  const long np = L.n_params;
+  std::vector<HD> hp(np);
+  for (long k = 0; k < np; ++k) hp[k] = HD(params[k], 0.0, vdir ? vdir[k] : 0.0, 0.0);
+  double loss = 0.0, dloss = 0.0;
+  long off = 0;
+  for (int f = 0; f < B; ++f) {
+    const int n = natoms[f];
+    const double* x = coord + 3 * off;
+    const int* ty = type + off;
+    const double* box = boxes + 9 * f;
+    std::vector<int> nj(nl_j + off * nc, nl_j + (off + n) * nc);
+    std::vector<int> ns(nl_shift + off * nc * 3, nl_shift + (off + n) * nc * 3);
+    // shift the frame's neighbour indices to frame-local numbering
+    for (auto& j : nj)
+      if (j >= 0) j -= (int)off;
+    std::vector<double> force((size_t)3 * n), vir(9), ae(n);
+    double e = 0.0;
+    orc_compute(cfg, params, n, x, ty, box, nj.data(), ns.data(), nullptr, 0, 0, 0, 0, 0, &e, force.data(), vir.data(),
+                ae.data(), 0);
+    const double dE = e - e_ref[f];
+    double f2 = 0.0;
+    std::vector<HD> hx((size_t)3 * n), hb(9);
+    for (int i = 0; i < 3 * n; ++i) {
+      const double dF = force[i] - f_ref[3 * off + i];
+      f2 += dF * dF;
+      hx[i] = HD(x[i], dF, 0.0, 0.0);
+    }
+    for (int k = 0; k < 9; ++k) hb[k] = HD(box[k]);
+    std::vector<int> code((size_t)n * nc);
+    for (size_t k = 0; k < code.size(); ++k) code[k] = pack_shift(ns[3 * k], ns[3 * k + 1], ns[3 * k + 2]);
+    const HD E = energy_generic<HD, HD>(*cfg, L, hp.data(), n, hx.data(), ty, hb.data(), nj.data(), code.data(),
+                                        nullptr);
+    loss += pE * dE * dE / n + pF * f2 / (3.0 * n);
+    dloss += 2.0 * pE * dE / n * E.b - 2.0 * pF / (3.0 * n) * E.ab;
+    off += n;
+  }
+  if (dL) *dL = dloss / B;
+  return loss / B;
 }
 
 // Plain-double energy through the generic template (pins the reverse-pass forward).
