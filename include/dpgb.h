@@ -186,6 +186,29 @@ int dp_compute_batch(dp_model* model, int nframes, const int* natoms, const doub
                      const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
                      void* stream);
 
+/* ---- training: parameter gradient of an energy + force objective (Sec. II.B) ----
+ * The loss of Sec. II.B weighs energy and force errors (prefactors p_e, p_f).  Its gradient
+ * with respect to the parameters needs the derivative of the force F = -dE/dr with respect
+ * to every weight: a second-order ("double backward") derivative of E.  This entry point
+ * returns, for the model's current parameters,
+ *   grad = d/dtheta [ sum_f g_energy[f] E_f + sum_i g_force[i] . F_i ]
+ * i.e. the vector-Jacobian product of (E, F) with the cotangents (g_energy, g_force); with
+ * g_energy[f] = dL/dE_f and g_force = dL/dF it is dL/dtheta for any loss L(E, F).  All of it
+ * runs on the GPU: a tangent pass along g_force through the whole path, then a reverse pass
+ * over the primal and tangent computations.
+ *   Frames are passed as for dp_compute_batch (boxes may be NULL only when nframes == 1).
+ *   g_energy [nframes], g_force [sum natoms][3] (input atom order), grad [n_params] in the
+ *   parameter layout of dp_model_create; each may be a host or a device pointer.
+ * Only uncompressed FP64 and FP32 models (DP_E_UNSUPPORTED otherwise); the arithmetic runs
+ * in the model's precision.  Synchronises `stream`.  Returns as dp_compute. */
+int dp_param_grad(dp_model* model, int nframes, const int* natoms, const double* coord, const int* type,
+                  const double* boxes, const double* g_energy, const double* g_force, double* grad, void* stream);
+
+/* Replace the parameters of an uncompressed model in place (a training step's update).
+ * params [n_params] FP64, host or device, in the layout of dp_model_create.  Synchronises
+ * `stream`.  DP_E_ARG on a size mismatch, DP_E_UNSUPPORTED for compressed models. */
+int dp_model_set_params(dp_model* model, const double* params, long n_params, void* stream);
+
 /* Message for the last error raised on the calling thread ("" if none). */
 const char* dp_last_error(void);
 

@@ -22,6 +22,11 @@ __device__ int g_gemm_err;
 
 namespace {
 
+__global__ void k_narrow(const double* __restrict__ x, long n, float* __restrict__ y) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = (float)x[e];
+}
+
 int skip_kind(int n_in, int n_out) { return n_out == n_in ? 1 : (n_out == 2 * n_in ? 2 : 0); }
 
 int check_config(const dp_model_config* c) {
@@ -248,6 +253,26 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
     }
   }
   *out = md;
+  return DP_OK;
+}
+
+int dp_model_set_params(dp_model* md, const double* params, long n_params, void* stream) {
+  if (!md || !params || n_params != md->m.n_params) {
+    set_error("invalid argument (params must hold exactly the model's n_params values)");
+    return DP_E_ARG;
+  }
+  DeviceModel& m = md->m;
+  if (m.compressed) {
+    set_error("compressed models hold tabulated nets: create a new model to change parameters");
+    return DP_E_UNSUPPORTED;
+  }
+  DP_CUDA_TRY(cudaSetDevice(m.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const cudaMemcpyKind kind = is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  DP_CUDA_TRY(cudaMemcpyAsync(m.p64, params, sizeof(double) * n_params, kind, st));
+  k_narrow<<<(unsigned)((n_params + 255) / 256), 256, 0, st>>>(m.p64, n_params, m.p32);
+  DP_CUDA_TRY(cudaGetLastError());
+  DP_CUDA_TRY(cudaStreamSynchronize(st));
   return DP_OK;
 }
 

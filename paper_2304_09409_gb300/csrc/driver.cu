@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "capi_internal.cuh"
+#include "grad.cuh"
 #include "table.cuh"
 
 namespace dpgb {
@@ -259,10 +260,18 @@ int run_path(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena&
   return run_generic<float>(m, pc, m.p32, io, ar, st);
 }
 
-// The whole path over F frames.  nlist (F == 1 only) replaces the internal list build.
+// Parameter-gradient request: dPhi/dtheta for Phi = sum_f g_energy[f] E_f + sum_i g_force[i] . F_i.
+struct GradReq {
+  const double* g_energy;  // [F] host or device
+  const double* g_force;   // [N][3] host or device
+  double* grad;            // [n_params] host or device
+};
+
+// The whole path over F frames.  nlist (F == 1 only) replaces the internal list build.  With
+// gr set, the call computes the parameter gradient instead of energy / force / virial.
 int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const double* coord, const int* type,
                const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
-               cudaStream_t st) {
+               cudaStream_t st, const GradReq* gr = nullptr) {
   const DeviceModel& m = md->m;
   DP_CUDA_TRY(cudaSetDevice(m.device));
   const bool copy_coord = !is_device_ptr(coord), copy_type = !is_device_ptr(type);
@@ -293,7 +302,17 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   pre.measure = true;
   Bufs b;
   carve(pre, m, T, own_nlist, copy_coord, copy_type, host_e, host_v, host_f, dev_ae, b);
-  rc = run_path(m, pc, io, pre, st);
+  // gradient mode: device copies of the seeds and of the result where the caller's are host arrays
+  const bool g_a_host = gr && !is_device_ptr(gr->g_energy), g_w_host = gr && !is_device_ptr(gr->g_force),
+             g_out_host = gr && !is_device_ptr(gr->grad);
+  double *d_ga = nullptr, *d_gw = nullptr, *d_gout = nullptr;
+  auto carve_grad = [&](Arena& a) {
+    d_ga = g_a_host ? a.get<double>(F) : const_cast<double*>(gr ? gr->g_energy : nullptr);
+    d_gw = g_w_host ? a.get<double>(3L * N) : const_cast<double*>(gr ? gr->g_force : nullptr);
+    d_gout = g_out_host ? a.get<double>(m.n_params) : (gr ? gr->grad : nullptr);
+  };
+  carve_grad(pre);
+  rc = gr ? run_param_grad(m, pc, io, nullptr, nullptr, -1.0, nullptr, pre, st) : run_path(m, pc, io, pre, st);
   if (rc != DP_OK) return rc;
   rc = ensure_ws(md, pre.used);
   if (rc == DP_OK) rc = ensure_stage(md, T.bytes);
@@ -302,10 +321,13 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   ar.base = md->ws;
   ar.cap = md->ws_cap;
   carve(ar, m, T, own_nlist, copy_coord, copy_type, host_e, host_v, host_f, dev_ae, b);
+  carve_grad(ar);
   const double* dcoord = copy_coord ? b.coord : coord;
   const int* dtype = copy_type ? b.type : type;
   if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
   if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  if (g_a_host) DP_CUDA_TRY(cudaMemcpyAsync(d_ga, gr->g_energy, sizeof(double) * F, cudaMemcpyHostToDevice, st));
+  if (g_w_host) DP_CUDA_TRY(cudaMemcpyAsync(d_gw, gr->g_force, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
   T.pack(md->stage);
   DP_CUDA_TRY(cudaMemcpyAsync(b.ftab, md->stage, T.bytes, cudaMemcpyHostToDevice, st));
   const NlGeom* d_geoms = reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms);
@@ -352,6 +374,21 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   io.atom_virial = b.atom_virial;
   io.status = md->status;
   io.epart = b.epart;
+  if (gr) {
+    {
+      ProfScope _ps(&md->prof, "param_grad", st);
+      rc = run_param_grad(m, pc, io, d_gw, d_ga, -1.0, d_gout, ar, st);
+    }
+    if (rc != DP_OK) return rc;
+    if (g_out_host)
+      DP_CUDA_TRY(cudaMemcpyAsync(gr->grad, d_gout, sizeof(double) * m.n_params, cudaMemcpyDeviceToHost, st));
+    rc = read_status(md, st, nullptr);
+    if (rc == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
+      md->nl_full_cap = true;
+      return run_frames(md, nlist, F, natoms, coord, type, boxes, energy, force, virial, atom_energy, st, gr);
+    }
+    return rc;
+  }
   DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, st));
   if (!m.compressed) DP_CUDA_TRY(cudaMemsetAsync(io.atom_virial, 0, sizeof(double) * 9 * N, st));
   rc = run_path(m, pc, io, ar, st);
@@ -406,6 +443,21 @@ int dp_compute_batch(dp_model* md, int nframes, const int* natoms, const double*
   }
   return run_frames(md, nullptr, nframes, natoms, coord, type, boxes, energy, force, virial, atom_energy,
                     (cudaStream_t)stream);
+}
+
+int dp_param_grad(dp_model* md, int nframes, const int* natoms, const double* coord, const int* type,
+                  const double* boxes, const double* g_energy, const double* g_force, double* grad, void* stream) {
+  if (!md || nframes < 1 || !natoms || !coord || !type || !g_energy || !g_force || !grad) {
+    set_error("invalid argument");
+    return DP_E_ARG;
+  }
+  if (!boxes && nframes != 1) {
+    set_error("batches of frames need periodic cells");
+    return DP_E_UNSUPPORTED;
+  }
+  const GradReq gr{g_energy, g_force, grad};
+  return run_frames(md, nullptr, nframes, natoms, coord, type, boxes, nullptr, nullptr, nullptr, nullptr,
+                    (cudaStream_t)stream, &gr);
 }
 
 int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, const double* box, dp_nlist** out,

@@ -31,7 +31,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 EXPORTED = [
     "dp_model_create", "dp_init_model", "dp_free_model", "dp_model_n_params", "dp_build_nlist",
     "dp_nlist_export", "dp_free_nlist", "dp_compute", "dp_model_export_table", "dp_last_error",
-    "dp_build_nlist_noalloc", "dp_compute_batch",
+    "dp_build_nlist_noalloc", "dp_compute_batch", "dp_param_grad", "dp_model_set_params",
 ]
 
 
@@ -208,6 +208,17 @@ class Model:
     def launch_count(self) -> int:
         return int(lib().dp_launch_count(self.handle))
 
+    def set_params(self, params, stream=None):
+        """dp_model_set_params: replace the parameters (numpy or torch CUDA FP64, n_params)."""
+        L = lib()
+        L.dp_model_set_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p]
+        if not (_is_torch(params) and params.is_cuda):
+            params = np.ascontiguousarray(params, dtype=np.float64)
+        else:
+            params = params.detach().contiguous()
+        n = int(params.numel() if _is_torch(params) else params.size)
+        _check(L.dp_model_set_params(self.handle, _ptr(params), n, _stream_handle(stream)))
+
     def build_nlist(self, coord, atype, box, stream=None) -> NList:
         N = int(coord.shape[0])
         h = ctypes.c_void_p()
@@ -301,6 +312,34 @@ def compute_batch(model: "Model", natoms, coord, atype, boxes, atom_energy: bool
                               _ptr(f), _ptr(v), _ptr(ae), _stream_handle(stream))
     _check(code, allow=allow)
     return e, f, v, ae
+
+
+def param_grad(model: "Model", natoms, coord, atype, boxes, g_energy, g_force, stream=None, out=None):
+    """dp_param_grad: d/dtheta [sum_f g_energy[f] E_f + sum_i g_force[i] . F_i] for the model's
+    current parameters.  natoms int32 [F]; coord [N, 3] and atype [N] (numpy or torch CUDA);
+    boxes [F, 3, 3] numpy, or None for one open-boundary frame; g_energy [F], g_force [N, 3].
+    Returns [n_params] FP64 (a torch CUDA tensor when coord is one, else numpy)."""
+    L = lib()
+    vp = ctypes.c_void_p
+    L.dp_param_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+    nat = np.ascontiguousarray(natoms, dtype=np.int32)
+    F = int(nat.size)
+    bx = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64).reshape(F, 9)
+    npar = n_params(model.cfg)
+    if _is_torch(coord) and coord.is_cuda:
+        import torch
+        g_energy = torch.as_tensor(g_energy, dtype=torch.float64, device=coord.device).contiguous()
+        g_force = torch.as_tensor(g_force, dtype=torch.float64, device=coord.device).contiguous()
+        grad = out if out is not None else torch.empty(npar, dtype=torch.float64, device=coord.device)
+    else:
+        coord = np.ascontiguousarray(coord, dtype=np.float64)
+        atype = np.ascontiguousarray(atype, dtype=np.int32)
+        g_energy = np.ascontiguousarray(g_energy, dtype=np.float64)
+        g_force = np.ascontiguousarray(g_force, dtype=np.float64)
+        grad = out if out is not None else np.zeros(npar)
+    _check(L.dp_param_grad(model.handle, F, nat.ctypes.data, _ptr(coord), _ptr(atype), _ptr(bx), _ptr(g_energy),
+                           _ptr(g_force), _ptr(grad), _stream_handle(stream)))
+    return grad
 
 
 def n_params(cfg) -> int:

@@ -473,3 +473,42 @@ def test_compressed_forces_vs_dual_of_compressed_energy():
         ep = oracle.compute(cfg, p, cp, fr.atype, fr.box, nl=nl, table=tab).energy
         em = oracle.compute(cfg, p, cm, fr.atype, fr.box, nl=nl, table=tab).energy
         assert r.force[i, a] == pytest.approx(-(ep - em) / (2 * h), abs=2e-7)
+
+
+def _loss_from_compute(cfg, p, frames, e_ref, f_ref, pE, pF):
+    """The Sec. II.B loss evaluated from the oracle's plain energy/force results."""
+    L = 0.0
+    for fr, er, fref in zip(frames, e_ref, f_ref):
+        r = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
+        n = fr.natoms
+        L += pE * (r.energy - er) ** 2 / n + pF * float(((r.force - fref) ** 2).sum()) / (3 * n)
+    return L / len(frames)
+
+
+def test_loss_direction_derivative_vs_central_differences():
+    """The hyper-dual loss derivative (energy and force terms, the latter a mixed second
+    derivative of E) against central differences of the loss computed from plain results,
+    for random parameter directions and for directions confined to one net."""
+    cfg = tiny_model()
+    p = I.make_params(cfg, 5)
+    frames = [tiny_frame(seed=s) for s in (3, 4)]
+    q = I.make_params(cfg, 6)
+    e_ref, f_ref = [], []
+    for fr in frames:
+        r = oracle.compute(cfg, q, fr.coord, fr.atype, fr.box)
+        e_ref.append(r.energy)
+        f_ref.append(r.force)
+    e_ref = np.array(e_ref)
+    rng = I.Rng(17)
+    n = p.size
+    n_emb = sum(a * b + b for a, b in cfg.embed_layer_shapes()) * cfg.n_embed_nets
+    dirs = [rng.normal(n), np.r_[rng.normal(n_emb), np.zeros(n - n_emb)], np.r_[np.zeros(n_emb), rng.normal(n - n_emb)]]
+    for pE, pF in ((1.0, 0.0), (0.0, 1.0), (0.3, 2.0)):
+        L0 = _loss_from_compute(cfg, p, frames, e_ref, f_ref, pE, pF)
+        for v in dirs:
+            L, dL = oracle.loss_dir(cfg, p, v, frames, e_ref, f_ref, pE, pF)
+            assert abs(L - L0) <= 1e-12 * max(1.0, abs(L0))
+            h = 1e-5
+            fd = (_loss_from_compute(cfg, p + h * v, frames, e_ref, f_ref, pE, pF)
+                  - _loss_from_compute(cfg, p - h * v, frames, e_ref, f_ref, pE, pF)) / (2 * h)
+            assert abs(dL - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(L0)), (pE, pF, dL, fd)
