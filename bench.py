@@ -266,6 +266,65 @@ def run_serving(n_frames=3000, rate=2000.0, slots=3, max_batch_atoms=65536):
     return st
 
 
+def run_training(steps=5, warmup=3, n_frames=32):
+    """Training-style differentiation: one batch of 32 water frames (192 atoms, seeds 1..32),
+    targets E*, F* from a second random-weight model on the FP64 GPU path, loss of Sec. II.B
+    (pE 0.02, pF 1).  Times dp_param_grad alone (FP32 and FP64) and a whole Adam step through
+    the torch.autograd.Function (FP32): forward E/F, loss, backward, update."""
+    import torch
+    from paper_2304_09409_gb300 import dpgb, inputs as I
+    from paper_2304_09409_gb300.autograd import Trainer
+    cfg = I.water_model()
+    p, q = I.make_params(cfg, 0), I.make_params(cfg, 1)
+    frames = [I.water_frame(s) for s in range(1, n_frames + 1)]
+    nat = np.array([f.natoms for f in frames], dtype=np.int32)
+    coord = torch.tensor(np.concatenate([f.coord for f in frames]), device="cuda")
+    atype = torch.tensor(np.concatenate([f.atype for f in frames]).astype(np.int32), device="cuda")
+    boxes = np.stack([f.box for f in frames])
+    ref = dpgb.Model(cfg, q, precision="fp64")
+    e_ref, f_ref, _, _ = dpgb.compute_batch(ref, nat, coord, atype, boxes)
+    ref.free()
+    B, N = len(frames), int(nat.sum())
+    per_n = torch.tensor(np.repeat(nat, nat).astype(np.float64), device="cuda")[:, None]
+    nat_t = torch.tensor(nat.astype(np.float64), device="cuda")
+    out = {"workload": f"{B} water frames x 192 atoms (seeds 1..{B}), targets from a second random-weight model",
+           "loss": "pE dE^2/N + pF |dF|^2/(3N), pE 0.02, pF 1, mean over frames"}
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        m = dpgb.Model(cfg, p, precision=prec)
+        e, f, _, _ = dpgb.compute_batch(m, nat, coord, atype, boxes)
+        g_e = 2 * 0.02 * (e - e_ref) / (nat_t * B)
+        g_f = 2 * (f - f_ref) / (3 * per_n * B)
+        g = dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f)
+        for _ in range(warmup):
+            dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, out=g)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, out=g)
+        b.record()
+        torch.cuda.synchronize()
+        grads[prec] = g.clone()
+        out[f"param_grad_ms_{prec}"] = a.elapsed_time(b) / steps
+        m.free()
+    out["fp32_grad_rel_err_vs_fp64"] = float(torch.linalg.norm(grads["fp32"] - grads["fp64"])
+                                             / torch.linalg.norm(grads["fp64"]))
+    m = dpgb.Model(cfg, p, precision="fp32")
+    tr = Trainer(m, p, lr=1e-3, pE=0.02, pF=1.0)
+    for _ in range(warmup):
+        tr.step(nat, coord, atype, boxes, e_ref, f_ref)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = [tr.step(nat, coord, atype, boxes, e_ref, f_ref) for _ in range(steps)]
+    torch.cuda.synchronize()
+    out["adam_step_ms_fp32"] = (time.perf_counter() - t0) / steps * 1e3
+    out["atoms_per_batch"] = N
+    out["loss_first_last"] = [losses[0], losses[-1]]
+    m.free()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2304_09409_gb300 import dpgb
@@ -377,6 +436,11 @@ def run_ours(args):
         "clocks": clk,
         "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
     }
+    if not args.no_training:
+        try:
+            line["training"] = run_training()
+        except Exception as exc:
+            line["training"] = {"error": repr(exc)}
     if not args.no_serving:
         try:
             srv = run_serving()
@@ -402,6 +466,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-serving", dest="no_serving", action="store_true",
                     help="skip the continuous-batching serving measurement")
+    ap.add_argument("--no-training", dest="no_training", action="store_true",
+                    help="skip the parameter-gradient (training step) measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -10,9 +10,8 @@
 //   virial   Xi_ab = -sum (dE/dr_ij)_a (r_ij)_b (FP64, deterministic two-stage reduction)
 //
 // The pair displacement is always rebuilt from the neighbour list with the exact FP64
-// formula.  In FP32 mode the switch and its derivative are evaluated in FP64 within 1 A
-// of r_c (where the polynomial cancels) and in FP32 elsewhere; energy, force and virial
-// accumulate in FP64.
+// formula.  In FP32 mode the switch and its derivative are evaluated in FP32 in a form without
+// cancellation near r_c (env.cuh); energy, force and virial accumulate in FP64.
 #include "dp_internal.cuh"
 #include "path.cuh"
 #include "env.cuh"
