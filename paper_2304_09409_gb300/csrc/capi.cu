@@ -119,6 +119,10 @@ int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
     set_error("neighbour count exceeded sel for " + std::to_string(s.sel_overflow) + " (atom, type) blocks");
     return DP_E_SEL_OVERFLOW;
   }
+  if (s.timeout) {
+    set_error("a bounded wait inside a tensor-core kernel gave up; results are invalid");
+    return DP_E_TIMEOUT;
+  }
   if (s.table_range) {
     set_error("compressed model: s outside the tabulated range (last piece extrapolated)");
     return DP_E_RANGE;
@@ -385,6 +389,7 @@ int dp_free_model(dp_model* md) {
   cudaFree(md->m.p32);
   cudaFree(md->m.tab64);
   cudaFree(md->m.tab32);
+  cudaFree(md->m.mom_tab);
   cudaFree(md->m.fit_wt_bf16);
   cudaFree(md->m.fit_w_bf16);
   cudaFree(md->ws);

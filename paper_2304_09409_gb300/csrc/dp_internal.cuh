@@ -104,6 +104,11 @@ struct DeviceModel {
   std::vector<long> fit_bf16_off;
   // tensor maps of those operands, keyed by (type, layer, direction, box rows)
   mutable std::vector<std::pair<long, std::vector<unsigned char>>> tmap_cache;
+  // interval-moment operands of the compressed embedding on the tensor cores (mom.cu)
+  int mom_npass = 0;  // 0 none; 1 FP16 single pass; 3 BF16 high/low, three passes
+  int mom_npad = 0, mom_lcp = 0;
+  void* mom_tab = nullptr;               // forward and backward coefficient tables
+  std::vector<unsigned char> mom_maps;   // four CUtensorMaps: forward hi/lo, backward hi/lo
 };
 
 // ------------------------------------------------------------------------------------------
@@ -125,6 +130,7 @@ struct DevStatus {
   int capacity;       // an atom had more than DP_MAX_CANDIDATES candidates
   int table_range;    // compressed: an s outside the table
   int bad_type;       // a type outside [0, ntypes)
+  int timeout;        // a bounded wait of a tensor-core kernel gave up
 };
 
 // ------------------------------------------------------------------------------------------

@@ -19,6 +19,7 @@
 
 #include "env.cuh"
 #include "fit_tc.cuh"
+#include "mom.cuh"
 #include "table.cuh"
 
 namespace dpgb {
@@ -557,7 +558,7 @@ int build_tables(DeviceModel& m) {
   DP_CUDA_TRY(cudaDeviceSynchronize());
   cudaFree(y);
   cudaFree(dl);
-  return DP_OK;
+  return build_mom_tables(m);
 }
 
 int export_tables(const DeviceModel& m, double* out) {
@@ -575,6 +576,7 @@ int export_tables(const DeviceModel& m, double* out) {
 }
 
 int run_compressed(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& ar, cudaStream_t st) {
+  if (m.mom_npass) return run_mom(m, pc, io, ar, st);
   if (m.precision == DP_PREC_FP64) return run_tab<double, double>(m, pc, io, ar, st, m.p64, m.tab64);
   if (m.precision == DP_PREC_BF16) return run_tab<float, __nv_bfloat16>(m, pc, io, ar, st, m.p32, m.tab32);
   return run_tab<float, float>(m, pc, io, ar, st, m.p32, m.tab32);
