@@ -26,7 +26,10 @@
 // Neighbours of each type block are sorted by distance, so their intervals are non-increasing
 // along the list and every (atom, interval) is a contiguous run; the few FP32 rounding
 // inversions are folded into the run of the previous neighbour (its polynomial piece evaluated
-// a rounding error beyond its end, where the pieces join with C^2 continuity).
+// a rounding error beyond its end, where the pieces join with C^2 continuity).  Most
+// neighbours sit in the first intervals (s < 0.01 reaches from about 0.6 r_c to r_c), so the
+// walks are spread evenly: the four warps of a CTA take every fourth slot of each list and the
+// 32 lanes of a warp take the 32 atoms of the tile, all in step.
 //
 // Precision: FP16 operands in one pass (mixed mode), or BF16 operands split into high and low
 // parts with three passes (hi.hi + hi.lo + lo.hi; FP32 mode); FP32 accumulation.  The rows of
@@ -51,7 +54,6 @@ using namespace ptx;
 
 constexpr int kAtoms = 32;        // centre atoms per CTA
 constexpr int kRows = 128;        // accumulator rows: (atom, c)
-constexpr int kStages = 3;        // shared-memory ring depth
 constexpr int kThreads = 160;     // 4 builder / epilogue warps + 1 control warp
 constexpr int kABlock = kRows * 128;  // one 64-column K block of 128 rows (bytes)
 constexpr int kGroupAtoms = 4;        // backward: atoms per staged group of dE/dD rows
@@ -116,91 +118,80 @@ __device__ __forceinline__ float tau_at(const MomArgs& g, float s, int l) {
                   : (s - (g.split + (float)(l - g.n1) * g.stride2)) * g.inv2;
 }
 
-// Walk of one atom's neighbour list of one type.  The per-slot records (s, u), (ds, r, tau, l)
-// come from k_env_mom; the four lanes of the atom (consecutive lanes, identical walks) stream
-// them through two 8-slot shared-memory windows with cp.async, one window ahead of the one
-// being read.
-constexpr int kWin = 8;
+// Walk of one atom's neighbour list of one type, visiting the slots kbeg, kbeg + STEP, ...
+// (the backward splits each list into STEP = 4 interleaved phases, one per warp; the forward
+// walks whole lists, STEP = 1); lane a of a warp takes atom a, so a warp advances 32 atoms in
+// step.  Each thread streams its own slots' records (s, u), (ds, r, tau, l) through two private
+// 4-slot shared-memory windows with cp.async, one window ahead of the one it reads: no other
+// thread touches them, so no synchronisation is needed.  The records carry intervals already
+// made non-increasing along the list (k_env_mom).
+constexpr int kWin = 4;
 struct Walk {
-  int k, kend, lprev, wbase, cur;
+  int k, kend, wbase, cur;  // next slot, end of the block, first slot of the current window, its buffer
   bool have;
   int l, j;
-  float tau, inv_d;
+  float tau;
   float4 e0, e1;  // (s, u), (ds, r, tau, l)
 };
-struct Window {
-  float4* e0;  // [32 atoms][2][kWin]
-  float4* e1;  // [32 atoms][2][kWin]
-  int* j;      // [32 atoms][2][kWin] (backward only)
+struct Window {  // this thread's two windows
+  float4* e0;    // [2][kWin]
+  float4* e1;    // [2][kWin]
+  int* j;        // [2][kWin] (backward only)
 };
 
-template <bool kJ>
-__device__ __forceinline__ void win_fill(const MomArgs& g, int p, int i, int a, int c, const Window& win, int buf,
-                                         int k0, int kend) {
-  for (int q = c; q < kWin; q += 4) {
-    const int slot = k0 + q;
+template <bool kJ, int STEP>
+__device__ __forceinline__ void win_fill(const MomArgs& g, int p, int i, const Window& win, int buf, int k0,
+                                         int kend) {
+#pragma unroll
+  for (int q = 0; q < kWin; ++q) {
+    const int slot = k0 + STEP * q;
     if (slot < kend) {
       const long row = (long)p * g.nc + slot;
-      const int o = (a * 2 + buf) * kWin + q;
-      cp_async16(win.e0 + o, g.env + row * 2);
-      cp_async16(win.e1 + o, g.env + row * 2 + 1);
-      if (kJ) cp_async4(win.j + o, g.nl_j + (long)i * g.nc + slot);
+      cp_async16(win.e0 + buf * kWin + q, g.env + row * 2);
+      cp_async16(win.e1 + buf * kWin + q, g.env + row * 2 + 1);
+      if (kJ) cp_async4(win.j + buf * kWin + q, g.nl_j + (long)i * g.nc + slot);
     }
   }
   cp_async_commit();
 }
 
-template <bool kJ>
-__device__ __forceinline__ void walk_start(const MomArgs& g, int p, int i, int a, int c, unsigned gmask,
-                                           const Window& win, Walk& w, int kbeg, int kend) {
+template <bool kJ, int STEP>
+__device__ __forceinline__ void walk_start(const MomArgs& g, int p, int i, const Window& win, Walk& w, int kbeg,
+                                           int kend) {
   w.k = kbeg;
   w.kend = kend;
-  w.lprev = INT_MAX;
   w.wbase = kbeg;
   w.cur = 0;
   w.have = false;
-  cp_async_wait0();   // no copy of an earlier walk is still in flight into the windows
-  __syncwarp(gmask);  // and every lane of the atom is done reading them
-  win_fill<kJ>(g, p, i, a, c, win, 0, kbeg, kend);
-  win_fill<kJ>(g, p, i, a, c, win, 1, kbeg + kWin, kend);
+  cp_async_wait0();  // no copy of an earlier walk is still in flight into the windows
+  win_fill<kJ, STEP>(g, p, i, win, 0, kbeg, kend);
+  win_fill<kJ, STEP>(g, p, i, win, 1, kbeg + STEP * kWin, kend);
   cp_async_wait1();
-  __syncwarp(gmask);
 }
 
-template <bool kJ>
-__device__ __forceinline__ void walk_next(const MomArgs& g, int p, int i, int a, int c, unsigned gmask,
-                                          const Window& win, Walk& w) {
+template <bool kJ, int STEP>
+__device__ __forceinline__ void walk_next(const MomArgs& g, int p, int i, const Window& win, Walk& w) {
   w.have = false;
   if (w.k >= w.kend) return;
-  if (w.k >= w.wbase + kWin) {
-    __syncwarp(gmask);  // every lane of the atom is done with the current window: refill it
-    win_fill<kJ>(g, p, i, a, c, win, w.cur, w.wbase + 2 * kWin, w.kend);
+  if (w.k >= w.wbase + STEP * kWin) {  // current window used up: refill it two windows ahead, switch
+    win_fill<kJ, STEP>(g, p, i, win, w.cur, w.wbase + 2 * STEP * kWin, w.kend);
     w.cur ^= 1;
-    w.wbase += kWin;
+    w.wbase += STEP * kWin;
     cp_async_wait1();
-    __syncwarp(gmask);
   }
-  const int o = (a * 2 + w.cur) * kWin + (w.k - w.wbase);
-  w.e1 = win.e1[o];
-  const int lraw = __float_as_int(w.e1.w);
-  if (lraw < 0) return;  // padding: real neighbours fill the front of the type block
-  w.e0 = win.e0[o];
-  if (kJ) w.j = win.j[o];
-  if (lraw <= w.lprev) {
-    w.l = lraw;
-    w.tau = w.e1.z;
-  } else {
-    w.l = w.lprev;
-    w.tau = tau_at(g, w.e0.x, w.l);
+  const int q = w.cur * kWin + (w.k - w.wbase) / STEP;
+  w.e1 = win.e1[q];
+  const int l = __float_as_int(w.e1.w);
+  if (l < 0) {  // padding: real neighbours fill the front of the type block
+    w.kend = w.k;
+    return;
   }
-  w.inv_d = w.l < g.n1 ? g.inv1 : g.inv2;
-  w.lprev = w.l;
+  w.e0 = win.e0[q];
+  if (kJ) w.j = win.j[q];
+  w.l = l;
+  w.tau = w.e1.z;
   w.have = true;
-  ++w.k;
-}
-
-__device__ __forceinline__ float comp_of(const float4& e, int c) {
-  return c == 0 ? e.x : e.x * (c == 1 ? e.y : (c == 2 ? e.z : e.w));
+  w.k += STEP;
 }
 
 // Largest 8-interval group holding a neighbour of each type, over the tile's atoms.
@@ -248,42 +239,88 @@ __device__ __forceinline__ uint32_t sw_off(int r, int q) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
 }
 
+// Ring depth: three stages for the single-pass operands, two for the high/low pairs.
+template <int NPASS>
+struct MomStages {
+  static constexpr int value = NPASS == 1 ? 3 : 2;
+};
+
+// FP32 rows of one atom in the staging / P buffers: 4 rows of 68 floats (8 chunks of 8 and a
+// pad), atoms 276 floats apart, which spreads a warp's 32 atoms over the banks.
+constexpr int kRowPitch = 68;
+constexpr int kAtomPitch = 276;
+constexpr uint32_t kRowBufBytes = kAtoms * kAtomPitch * 4;
+constexpr uint32_t kFwdWinBytes = kRows * 2 * kWin * 32;  // per thread: two windows of (e0, e1)
+constexpr uint32_t kBwdWinBytes = kRows * 2 * kWin * 36;  // per thread: two windows of (e0, e1, j)
+
+__host__ __device__ inline uint32_t fwd_ring_bytes(int npass, int npad) {
+  const uint32_t parts = npass == 1 ? 1 : 2, stages = npass == 1 ? 3 : 2;
+  return stages * parts * (uint32_t)(kABlock + npad * 128);
+}
 // Backward shared-memory region after the A operand: phase 1 holds two staged groups of dE/dD
-// and T rows plus a 16-row FP32 scratch, phase 2 the B ring and the neighbour windows.
+// and T rows plus a 16-row FP32 scratch; phase 2 the B ring, the P buffer and the windows.
+__host__ __device__ inline uint32_t bwd_ring_bytes(int npass) {
+  const uint32_t parts = npass == 1 ? 1 : 2, stages = npass == 1 ? 3 : 2;
+  return stages * parts * 2u * 64u * 128u;
+}
 __host__ __device__ inline uint32_t bwd_region(int npass, int npad, int M, int A) {
-  const uint32_t parts = npass == 1 ? 1 : 2;
   const uint32_t ph1 = 2u * kGroupAtoms * (uint32_t)(M * A * 4 + M * 16) + 16u * (uint32_t)(npad + 4) * 4u;
-  const uint32_t ph2 = (uint32_t)kStages * parts * 2u * 64u * 128u + (uint32_t)kAtoms * 2u * kWin * 36u;
+  const uint32_t ph2 = bwd_ring_bytes(npass) + kRowBufBytes + kBwdWinBytes;
   const uint32_t r = ph1 > ph2 ? ph1 : ph2;
   return (r + 15u) & ~15u;
 }
 
 // Per-slot records of the listed pairs (sorted atom order): (s, u) and (ds/dr, r, tau, l), with
-// l = -1 marking padding; exact FP64 displacement, FP32 switch (Eq. (switch)) and interval.
+// l = -1 marking padding; exact FP64 displacement, FP32 switch (Eq. (switch)).  One warp takes
+// one (atom, neighbour type) block: the interval is lowered to the running minimum along the
+// list (a prefix-minimum scan), so intervals never increase from slot to slot even where FP32
+// rounding of s inverts two nearly equal distances.
 __global__ void __launch_bounds__(256)
     k_env_mom(PathConst pc, MomArgs g, const double* __restrict__ coord, const int* __restrict__ nl_code,
               float4* __restrict__ env) {
-  const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long task = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (task >= (long)pc.natoms * pc.ntypes) return;  // warp-uniform
+  const int p = (int)(task / pc.ntypes), t = (int)(task % pc.ntypes);
+  const int i = g.perm[p];
+  int carry = INT_MAX;
   bool oor = false;
-  if (row < (long)pc.natoms * pc.nc) {
-    const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
-    const int i = g.perm[p];
-    const long slot = (long)i * pc.nc + k;
-    const int j = g.nl_j[slot];
-    if (j < 0) {
-      env[row * 2 + 1] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    } else {
+  for (int base = g.sel_off[t]; base < g.sel_off[t + 1]; base += 32) {
+    const int k = base + lane;
+    const bool in = k < g.sel_off[t + 1];
+    const long row = (long)p * pc.nc + k;
+    const int j = in ? g.nl_j[(long)i * pc.nc + k] : -1;
+    int l = INT_MAX;
+    float r = 0.f, s = 0.f, ds = 0.f, u[3] = {0.f, 0.f, 0.f}, tau = 0.f;
+    if (j >= 0) {
       double d0, d1, d2;
-      listed_disp(coord + 3 * i, coord + 3 * j, nl_code[slot], pc, frame_of(pc, i), d0, d1, d2);
-      float r, s, ds, u[3];
+      listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d0, d1, d2);
       pair_env<float>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
-      float tau, invd;
-      const int l = mom_interval(g, s, INT_MAX, tau, invd, oor);
-      env[row * 2] = make_float4(s, u[0], u[1], u[2]);
-      env[row * 2 + 1] = make_float4(ds, r, tau, __int_as_float(l));
+      float invd;
+      l = mom_interval(g, s, INT_MAX, tau, invd, oor);
     }
+    int m = l;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, m, off);
+      if (lane >= off) m = min(m, o);
+    }
+    m = min(m, carry);
+    if (j >= 0 && m < l) {
+      l = m;
+      tau = tau_at(g, s, l);
+    }
+    if (in) {
+      if (j >= 0) {
+        env[row * 2] = make_float4(s, u[0], u[1], u[2]);
+        env[row * 2 + 1] = make_float4(ds, r, tau, __int_as_float(l));
+      } else {
+        env[row * 2 + 1] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+      }
+    }
+    carry = __shfl_sync(0xffffffffu, m, 31);
   }
-  if (__any_sync(0xffffffffu, oor) && (threadIdx.x & 31) == 0) atomicOr(g.table_range, 1);
+  if (__any_sync(0xffffffffu, oor) && lane == 0) atomicOr(g.table_range, 1);
 }
 
 // =============================================================================================
@@ -293,18 +330,16 @@ template <int NPASS, int NPAD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mom_fwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
+  constexpr int S = MomStages<NPASS>::value;
   constexpr int B_BYTES = NPAD * 128;
   constexpr int STAGE = PARTS * (kABlock + B_BYTES);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  Window win;
-  win.e0 = reinterpret_cast<float4*>(smem + kStages * STAGE);
-  win.e1 = win.e0 + kAtoms * 2 * kWin;
-  win.j = nullptr;
-  uint64_t* full = reinterpret_cast<uint64_t*>(win.e1 + kAtoms * 2 * kWin);
-  uint64_t* empty = full + kStages;
-  uint64_t* accf = empty + kStages;
+  unsigned char* wins = smem + S * STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(wins + kFwdWinBytes);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
   int* ghi = reinterpret_cast<int*>(tmem_holder + 1);
 
@@ -315,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int row_end = g.row_start[ti + 1];
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], kRows + 1);
       mbar_init(&empty[s], 1);
     }
@@ -324,18 +359,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_fence_init();
   }
   if (warp == 4) tmem_alloc(tmem_holder, 128);
+  // thread r < 128 owns accumulator row r = (atom r / 4, component r % 4) in the epilogue and
+  // the conversion of staging row r; as a builder it walks phase `warp` of atom `lane`
+  const int r = threadIdx.x;
+  const int ae = r >> 2, c = r & 3;
+  const int pe = row0 + ae;
+  const bool valid_e = warp < 4 && pe < row_end;
+  const int pb = row0 + lane;
+  const bool valid_b = warp < 4 && pb < row_end;
+  const int ib = valid_b ? g.perm[pb] : 0;
+  if (warp == 0) tile_groups(g, pb, ib, valid_b, ghi);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-
-  const int r = threadIdx.x;  // accumulator row of a builder thread
-  const int a = r >> 2, c = r & 3;
-  const int p = row0 + a;
-  const bool valid = warp < 4 && p < row_end;
-  const int i = valid ? g.perm[p] : 0;
-  if (c == 0) tile_groups(g, p, i, valid, ghi);
-  __syncthreads();
   int nkb = 0;
   for (int t = 0; t < g.ntypes; ++t) nkb += ghi[t] + 1;
 
@@ -346,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       auto issue = [&](int kb) {
         int t, grp;
         block_of(kb, ghi, g.ntypes, t, grp);
-        const int s = kb % kStages;
+        const int s = kb % S;
         unsigned char* bs = smem + s * STAGE + PARTS * kABlock;
         mbar_expect_tx(&full[s], PARTS * B_BYTES);
         const int x = (t * g.lcp + 8 * grp) * 8;
@@ -354,12 +391,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (PARTS == 2) tma_load_2d(bs + B_BYTES, &blo, &full[s], x, ti * NPAD);
       };
       int issued = 0;
-      for (; issued < kStages - 1 && issued < nkb; ++issued) issue(issued);
+      for (; issued < S - 1 && issued < nkb; ++issued) issue(issued);
       bool ok = true;
       int done = 0;  // blocks whose loads were consumed
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages;
-        if (!mbar_wait(&full[s], (kb / kStages) & 1, g.err)) {
+        const int s = kb % S;
+        if (!mbar_wait(&full[s], (kb / S) & 1, g.err)) {
           ok = false;
           break;
         }
@@ -377,9 +414,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         mma_commit(&empty[s]);
-        const int kn = kb + kStages - 1;
+        const int kn = kb + S - 1;
         if (kn < nkb) {
-          if (kn >= kStages && !mbar_wait(&empty[kn % kStages], ((kn / kStages) - 1) & 1, g.err)) {
+          if (kn >= S && !mbar_wait(&empty[kn % S], ((kn / S) - 1) & 1, g.err)) {
             ok = false;
             break;
           }
@@ -392,55 +429,78 @@ __global__ void __launch_bounds__(kThreads, 1)
       else
         mbar_arrive(accf);
       // loads still in flight after an error must land before the CTA leaves
-      for (int kb = done; kb < issued; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1, g.err);
+      for (int kb = done; kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1, g.err);
     }
   } else {
-    // ---- moment builders: thread r owns accumulator row r = (atom a, component c) ----
+    // ---- moment builders: warp c builds component c of the 32 atoms (lane = atom), i.e. A
+    //      row (lane, c); each thread walks its atom's whole list and owns its row outright ----
+    const int crow = warp;            // component built by this warp
+    const int arow = lane * 4 + crow;  // A row written by this thread
+    Window win;
+    win.e0 = reinterpret_cast<float4*>(wins) + r * 2 * kWin;
+    win.e1 = reinterpret_cast<float4*>(wins) + (kRows + r) * 2 * kWin;
+    win.j = nullptr;
     Walk w;
     w.have = false;
     int cur_t = -1;
-    const unsigned gmask = 0xFu << (lane & 28);
-    const uint32_t rowoff0 = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
-    const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool dead = false;  // after a timed-out wait: stop waiting, keep going through the blocks
+    const uint32_t rowoff0 = (uint32_t)((arow >> 3) * 1024 + (arow & 7) * 128);
     for (int kb = 0; kb < nkb; ++kb) {
       int t, grp;
       block_of(kb, ghi, g.ntypes, t, grp);
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, g.err)) break;
+      const int s = kb % S;
+      if (kb >= S && !dead && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, g.err)) dead = true;
       if (t != cur_t) {
         cur_t = t;
-        if (valid) {
-          walk_start<false>(g, p, i, a, c, gmask, win, w, g.sel_off[t], g.sel_off[t + 1]);
-          walk_next<false>(g, p, i, a, c, gmask, win, w);
+        w.have = false;
+        if (valid_b) {
+          walk_start<false, 1>(g, pb, ib, win, w, g.sel_off[t], g.sel_off[t + 1]);
+          walk_next<false, 1>(g, pb, ib, win, w);
         }
       }
       unsigned char* ahi = smem + s * STAGE;
       unsigned char* alo = ahi + kABlock;
-      // empty intervals hold zeros; each run of neighbours in one interval then fills its chunk
+      // runs of equal interval, accumulated in registers; intervals without neighbours get zeros
+      float mu[8];
+      int cur_q = -1;
+      unsigned written = 0;
+      for (;;) {
+        const bool act = w.have && w.l >= 8 * grp;
+        if (!__any_sync(0xffffffffu, act)) break;
+        if (act) {
+          const int q = (w.l - 8 * grp) & 7;
+          if (q != cur_q) {
+            if (cur_q >= 0) {
+              const uint32_t off = rowoff0 + (uint32_t)((cur_q ^ (arow & 7)) << 4);
+              store_chunk<NPASS>(ahi + off, alo + off, mu);
+              written |= 1u << cur_q;
+            }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t off = rowoff0 + (uint32_t)((q ^ (r & 7)) << 4);
-        store_chunk<NPASS>(ahi + off, alo + off, zero8);
-      }
-      while (w.have && w.l >= 8 * grp) {
-        const int l0 = w.l;
-        float mu[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        while (w.have && w.l == l0) {
-          const float R = comp_of(w.e0, c), tau = w.tau;
-          float pw = R;
+            for (int pp = 0; pp < 8; ++pp) mu[pp] = 0.f;
+            cur_q = q;
+          }
+          const float sv = w.e0.x;
+          float pw = crow == 0 ? sv : sv * (crow == 1 ? w.e0.y : (crow == 2 ? w.e0.z : w.e0.w));
 #pragma unroll
           for (int pp = 0; pp < 6; ++pp) {
             mu[pp] += pw;
-            pw *= tau;
+            pw *= w.tau;
           }
-          walk_next<false>(g, p, i, a, c, gmask, win, w);
-        }
-        const int q = l0 - 8 * grp;  // < 8: every interval above this block was consumed earlier
-        if (q < 8) {
-          const uint32_t off = rowoff0 + (uint32_t)((q ^ (r & 7)) << 4);
-          store_chunk<NPASS>(ahi + off, alo + off, mu);
+          walk_next<false, 1>(g, pb, ib, win, w);
         }
       }
+      if (cur_q >= 0) {
+        const uint32_t off = rowoff0 + (uint32_t)((cur_q ^ (arow & 7)) << 4);
+        store_chunk<NPASS>(ahi + off, alo + off, mu);
+        written |= 1u << cur_q;
+      }
+      const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (!((written >> q) & 1u)) {
+          const uint32_t off = rowoff0 + (uint32_t)((q ^ (arow & 7)) << 4);
+          store_chunk<NPASS>(ahi + off, alo + off, zero8);
+        }
       fence_async_smem();
       mbar_arrive(&full[s]);
     }
@@ -461,14 +521,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const float x = nkb > 0 ? v[q] * g.inv_nc : 0.f;
-        smT[(a * (NPAD + 1) + c0 + q) * 4 + c] = x;
-        if (valid && c0 + q < g.M) g.Tm[((long)p * g.M + c0 + q) * 4 + c] = x;
+        smT[(ae * (NPAD + 1) + c0 + q) * 4 + c] = x;
+        if (valid_e && c0 + q < g.M) g.Tm[((long)pe * g.M + c0 + q) * 4 + c] = x;
       }
     }
     tc_fence_before();
     bar_sync(1, kRows);
-    if (valid) {
-      const float4* T4 = reinterpret_cast<const float4*>(smT) + a * (NPAD + 1);
+    if (valid_e) {
+      const float4* T4 = reinterpret_cast<const float4*>(smT) + ae * (NPAD + 1);
       float4 tl[16];
 #pragma unroll
       for (int l = 0; l < 16; ++l) tl[l] = l < g.A ? T4[l] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -477,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float d[16];
 #pragma unroll
         for (int l = 0; l < 16; ++l) d[l] = tm.x * tl[l].x + tm.y * tl[l].y + tm.z * tl[l].z + tm.w * tl[l].w;
-        const long o = ((long)p * g.M + m) * g.A;
+        const long o = ((long)pe * g.M + m) * g.A;
         if (g.d_bf16) {
           __nv_bfloat16* Db = reinterpret_cast<__nv_bfloat16*>(g.D) + o;
           if (g.A == 16) {
@@ -516,6 +576,7 @@ template <int NPASS, int NPAD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
+  constexpr int S = MomStages<NPASS>::value;
   constexpr int A_BYTES = 2 * kABlock;  // K = m in two 64-column blocks
   constexpr int B_KBLK = 64 * 128;      // 64 rows (8 intervals x 8 powers) x 128 B
   constexpr int B_STAGE = PARTS * 2 * B_KBLK;
@@ -528,18 +589,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bytesD = (uint32_t)(g.M * g.A * 4), bytesT = (uint32_t)(g.M * 16);
   const uint32_t gbuf = kGroupAtoms * (bytesD + bytesT);
   const uint32_t region = bwd_region(NPASS, NPAD, g.M, g.A);
-  unsigned char* As = smem;                      // PARTS x A_BYTES, dE/dT rows (A operand)
-  unsigned char* reg = smem + PARTS * A_BYTES;   // phase 1: staged dE/dD, T and scratch; phase 2: ring, windows
+  unsigned char* As = smem;                     // PARTS x A_BYTES, dE/dT rows (A operand)
+  unsigned char* reg = smem + PARTS * A_BYTES;  // phase 1: staged rows + scratch; phase 2: below
   unsigned char* ring = reg;
-  Window win;
-  win.e0 = reinterpret_cast<float4*>(reg + kStages * B_STAGE);
-  win.e1 = win.e0 + kAtoms * 2 * kWin;
-  win.j = reinterpret_cast<int*>(win.e1 + kAtoms * 2 * kWin);
+  float* Ps = reinterpret_cast<float*>(reg + bwd_ring_bytes(NPASS));  // P of one block [atom][c][chunk][8]
+  unsigned char* wins = reg + bwd_ring_bytes(NPASS) + kRowBufBytes;
   float* scr = reinterpret_cast<float*>(reg + 2 * gbuf);
   uint64_t* bar = reinterpret_cast<uint64_t*>(reg + region);
   uint64_t* bfull = bar;
-  uint64_t* bempty = bar + kStages;
-  uint64_t* afull = bar + 2 * kStages;
+  uint64_t* bempty = bar + S;
+  uint64_t* afull = bar + 2 * S;
   uint64_t* accfull = afull + 1;     // [2]
   uint64_t* accempty = accfull + 2;  // [2]
   uint64_t* gfull = accempty + 2;    // [2]
@@ -555,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int row_end = g.row_start[ti + 1];
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&bfull[s], 1);
       mbar_init(&bempty[s], 1);
     }
@@ -570,18 +629,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_fence_init();
   }
   if (warp == 4) tmem_alloc(tmem_holder, 128);
+  const int r = threadIdx.x;  // accumulator row (atom r / 4, component r % 4)
+  const int c = r & 3;
+  const int pb = row0 + lane;  // phase-2 walker: atom `lane`, phase `warp`
+  const bool valid_b = warp < 4 && pb < row_end;
+  const int ib = valid_b ? g.perm[pb] : 0;
+  if (warp == 0) tile_groups(g, pb, ib, valid_b, ghi);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-
-  const int r = threadIdx.x;
-  const int a = r >> 2, c = r & 3;
-  const int p = row0 + a;
-  const bool valid = warp < 4 && p < row_end;
-  const int i = valid ? g.perm[p] : 0;
-  if (c == 0) tile_groups(g, p, i, valid, ghi);
-  __syncthreads();
   int nch = 0;
   for (int t = 0; t < g.ntypes; ++t) nch += ghi[t] + 1;
 
@@ -612,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       auto issue = [&](int ch) {
         int t, grp;
         block_of(ch, ghi, g.ntypes, t, grp);
-        const int s = ch % kStages;
+        const int s = ch % S;
         unsigned char* bs = ring + s * B_STAGE;
         mbar_expect_tx(&bfull[s], B_STAGE);
         const int y = ((ti * g.ntypes + t) * g.lcp + 8 * grp) * 8;
@@ -625,10 +682,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       };
       int issued = 0, done = 0;
       if (ok)
-        for (; issued < kStages - 1 && issued < nch; ++issued) issue(issued);
+        for (; issued < S - 1 && issued < nch; ++issued) issue(issued);
       for (int ch = 0; ok && ch < nch; ++ch) {
-        const int s = ch % kStages, buf = ch & 1;
-        if (!mbar_wait(&bfull[s], (ch / kStages) & 1, g.err)) {
+        const int s = ch % S, buf = ch & 1;
+        if (!mbar_wait(&bfull[s], (ch / S) & 1, g.err)) {
           ok = false;
           break;
         }
@@ -655,9 +712,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mma_commit(&bempty[s]);
         mma_commit(&accfull[buf]);
-        const int kn = ch + kStages - 1;
+        const int kn = ch + S - 1;
         if (kn < nch) {
-          if (kn >= kStages && !mbar_wait(&bempty[kn % kStages], ((kn / kStages) - 1) & 1, g.err)) {
+          if (kn >= S && !mbar_wait(&bempty[kn % S], ((kn / S) - 1) & 1, g.err)) {
             ok = false;
             break;
           }
@@ -665,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           issued = kn + 1;
         }
       }
-      for (int ch = done; ch < issued; ++ch) mbar_wait(&bfull[ch % kStages], (ch / kStages) & 1, g.err);
+      for (int ch = done; ch < issued; ++ch) mbar_wait(&bfull[ch % S], (ch / S) & 1, g.err);
     }
   } else {
     // ---- phase 1: dE/dT rows; warp w takes atom w of each group, lane = (part, c) ----
@@ -761,90 +818,103 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_async_smem();
       mbar_arrive(afull);
-      bar_sync(1, kRows);  // phase-1 buffers become the ring and the neighbour windows
+      bar_sync(1, kRows);  // phase-1 buffers become the ring, P and the neighbour windows
     }
 
-    // ---- phase 2, per 8-interval block: P from TMEM, then this atom's neighbours in the block ----
+    // ---- phase 2, per 8-interval block: P from TMEM to shared memory, then every warp walks
+    //      its phase of the 32 atoms' neighbours in the block ----
     const float pscale = ldexpf(g.inv_nc, ex_s[r]);
-    const int base = lane & 28;
-    const unsigned gmask = 0xFu << base;
+    float* prow = Ps + (r >> 2) * kAtomPitch + c * kRowPitch;  // this thread's P row
+    const float* patom = Ps + lane * kAtomPitch;                // the walked atom's four rows
+    Window win;
+    win.e0 = reinterpret_cast<float4*>(wins) + r * 2 * kWin;
+    win.e1 = reinterpret_cast<float4*>(wins) + (kRows + r) * 2 * kWin;
+    win.j = reinterpret_cast<int*>(wins + 2 * kRows * 2 * kWin * 16) + r * 2 * kWin;
     Walk w;
     w.have = false;
     int cur_t = -1;
-    float fi = 0.f, v0 = 0.f, v1 = 0.f, v2 = 0.f;  // force on i (component c - 1), virial row c - 1
+    bool dead = false;  // after a timed-out wait: stop waiting, keep taking part in the barriers
+    float fi[3] = {0.f, 0.f, 0.f}, vir[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
     for (int ch = 0; ch < nch; ++ch) {
       const int buf = ch & 1;
-      const bool got = mbar_wait(&accfull[buf], (ch >> 1) & 1, g.err);
-      if (!__all_sync(0xffffffffu, got)) break;  // warp-uniform: tcgen05.ld below is warp-collective
+      if (!dead && !mbar_wait(&accfull[buf], (ch >> 1) & 1, g.err)) dead = true;
+      __syncwarp();  // tcgen05.ld is warp-collective
       tc_fence_after();
-      float P[64];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) tmem_ld16(tb + (uint32_t)(buf * 64 + 16 * q), P + 16 * q);
+      for (int q = 0; q < 4; ++q) {
+        float v[16];
+        tmem_ld16(tb + (uint32_t)(buf * 64 + 16 * q), v);
+#pragma unroll
+        for (int e = 0; e < 16; e += 4)
+          *reinterpret_cast<float4*>(prow + 16 * q + e) =
+              make_float4(v[e] * pscale, v[e + 1] * pscale, v[e + 2] * pscale, v[e + 3] * pscale);
+      }
       tc_fence_before();
       mbar_arrive(&accempty[buf]);
+      bar_sync(1, kRows);  // the whole P block is in shared memory
       int t, grp;
       block_of(ch, ghi, g.ntypes, t, grp);
       if (t != cur_t) {
         cur_t = t;
-        if (valid) {
-          walk_start<true>(g, p, i, a, c, gmask, win, w, g.sel_off[t], g.sel_off[t + 1]);
-          walk_next<true>(g, p, i, a, c, gmask, win, w);
+        w.have = false;
+        if (valid_b) {
+          walk_start<true, 4>(g, pb, ib, win, w, g.sel_off[t] + warp, g.sel_off[t + 1]);
+          walk_next<true, 4>(g, pb, ib, win, w);
         }
       }
-      while (w.have && w.l >= 8 * grp) {
-        const int q = w.l - 8 * grp;
-        float pq[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        switch (q) {
-#define DPGB_SEL(Q)                                             \
-  case Q:                                                       \
-    _Pragma("unroll") for (int e = 0; e < 6; ++e) pq[e] = P[8 * Q + e]; \
-    break;
-          DPGB_SEL(0)
-          DPGB_SEL(1)
-          DPGB_SEL(2)
-          DPGB_SEL(3)
-          DPGB_SEL(4)
-          DPGB_SEL(5)
-          DPGB_SEL(6)
-          DPGB_SEL(7)
-#undef DPGB_SEL
-          default:
-            break;
+      for (;;) {
+        const bool act = w.have && w.l >= 8 * grp;
+        if (!__any_sync(0xffffffffu, act)) break;
+        if (act) {
+          const int q = w.l - 8 * grp;
+          const float tau = w.tau;
+          float gR[4], dg[4];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float4* p4 = reinterpret_cast<const float4*>(patom + cc * kRowPitch + (q & 7) * 8);
+            const float4 x = p4[0], y = p4[1];
+            gR[cc] = x.x + tau * (x.y + tau * (x.z + tau * (x.w + tau * (y.x + tau * y.y))));
+            dg[cc] = x.y + tau * (2.f * x.z + tau * (3.f * x.w + tau * (4.f * y.x + tau * (5.f * y.y))));
+          }
+          const float s = w.e0.x, u0 = w.e0.y, u1 = w.e0.z, u2 = w.e0.w, ds = w.e1.x, rr = w.e1.y;
+          const float invd = w.l < g.n1 ? g.inv1 : g.inv2;
+          const float gs = s * (dg[0] + u0 * dg[1] + u1 * dg[2] + u2 * dg[3]) * invd;
+          const float gvu = gR[1] * u0 + gR[2] * u1 + gR[3] * u2;
+          const float A_ = ds * (gs + gR[0] + gvu), B_ = s / rr;
+          const float gd[3] = {A_ * u0 + B_ * (gR[1] - gvu * u0), A_ * u1 + B_ * (gR[2] - gvu * u1),
+                               A_ * u2 + B_ * (gR[3] - gvu * u2)};
+          const float dv[3] = {rr * u0, rr * u1, rr * u2};
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa) {
+            atomicAdd(g.force + 3 * w.j + aa, widen(-gd[aa]));
+            fi[aa] += gd[aa];
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= gd[aa] * dv[bb];
+          }
+          walk_next<true, 4>(g, pb, ib, win, w);
         }
-        const float tau = w.tau;
-        const float gRc =
-            pscale * (pq[0] + tau * (pq[1] + tau * (pq[2] + tau * (pq[3] + tau * (pq[4] + tau * pq[5])))));
-        const float dgc =
-            pscale * (pq[1] + tau * (2.f * pq[2] + tau * (3.f * pq[3] + tau * (4.f * pq[4] + tau * (5.f * pq[5])))));
-        const float s = w.e0.x, u0 = w.e0.y, u1 = w.e0.z, u2 = w.e0.w, ds = w.e1.x, rr = w.e1.y;
-        float gs = comp_of(w.e0, c) * dgc * w.inv_d;
-        gs += __shfl_xor_sync(gmask, gs, 1);
-        gs += __shfl_xor_sync(gmask, gs, 2);
-        const float g0 = __shfl_sync(gmask, gRc, base), g1 = __shfl_sync(gmask, gRc, base + 1);
-        const float g2 = __shfl_sync(gmask, gRc, base + 2), g3 = __shfl_sync(gmask, gRc, base + 3);
-        const float gvu = g1 * u0 + g2 * u1 + g3 * u2;
-        const float A_ = ds * (gs + g0 + gvu), B_ = s / rr;
-        if (c > 0) {
-          const float uc = c == 1 ? u0 : (c == 2 ? u1 : u2);
-          const float gc = c == 1 ? g1 : (c == 2 ? g2 : g3);
-          const float gd = A_ * uc + B_ * (gc - gvu * uc);
-          atomicAdd(g.force + 3 * w.j + (c - 1), widen(-gd));
-          fi += gd;
-          v0 -= gd * rr * u0;
-          v1 -= gd * rr * u1;
-          v2 -= gd * rr * u2;
-        }
-        walk_next<true>(g, p, i, a, c, gmask, win, w);
       }
+      bar_sync(1, kRows);  // every walker is done with this P block
     }
     cp_async_wait0();
-    if (valid && c > 0) {
-      atomicAdd(g.force + 3 * i + (c - 1), widen(fi));
-      double* av = g.avir + 9L * i + 3 * (c - 1);
-      av[0] = widen(v0);
-      av[1] = widen(v1);
-      av[2] = widen(v2);
+    // force on i and the atom's virial: the four phases' partial sums meet in shared memory
+    float* red = Ps;  // [4 phases][32 atoms][12]
+#pragma unroll
+    for (int e = 0; e < 3; ++e) red[(warp * kAtoms + lane) * 12 + e] = fi[e];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) red[(warp * kAtoms + lane) * 12 + 3 + e] = vir[e];
+    bar_sync(1, kRows);
+    if (warp == 0 && valid_b) {
+      float tot[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e)
+        tot[e] = red[lane * 12 + e] + red[(kAtoms + lane) * 12 + e] + red[(2 * kAtoms + lane) * 12 + e] +
+                 red[(3 * kAtoms + lane) * 12 + e];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) atomicAdd(g.force + 3 * ib + e, widen(tot[e]));
+#pragma unroll
+      for (int e = 0; e < 9; ++e) g.avir[9L * ib + e] = widen(tot[3 + e]);
     }
   }
   tc_fence_before();
@@ -895,13 +965,14 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
 }
 
 size_t fwd_smem(int npass, int npad) {
-  const int parts = npass == 1 ? 1 : 2;
-  return (size_t)kStages * parts * (kABlock + npad * 128) + (size_t)kAtoms * 2 * kWin * 32 + 1024 + 256;
+  const int S = npass == 1 ? 3 : 2;
+  return (size_t)fwd_ring_bytes(npass, npad) + kFwdWinBytes + (2 * S + 1) * 8 + 4 +
+         4 * DP_MAX_TYPES + 1024 + 64;
 }
 size_t bwd_smem(int npass, int npad, int M, int A) {
-  const int parts = npass == 1 ? 1 : 2;
-  return (size_t)parts * 2 * kABlock + bwd_region(npass, npad, M, A) + 15 * 8 + 4 + 4 * (DP_MAX_TYPES + kRows) +
-         1024 + 64;
+  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 3 : 2;
+  return (size_t)parts * 2 * kABlock + bwd_region(npass, npad, M, A) + (2 * S + 9) * 8 + 4 +
+         4 * (DP_MAX_TYPES + kRows) + 1024 + 64;
 }
 
 template <int NPASS, int NPAD>
@@ -1036,8 +1107,8 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.err = reinterpret_cast<int*>(stw + offsetof(DevStatus, timeout));
   {
     ProfScope _ps(io.prof, "env", st);
-    const long rows = N * pc.nc;
-    k_env_mom<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(pc, g, io.coord, io.nl_code, env);
+    const long tasks = N * pc.ntypes;  // one warp per (atom, neighbour type)
+    k_env_mom<<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code, env);
     DP_CUDA_TRY(cudaGetLastError());
   }
   if (tiles > 0) {
