@@ -66,13 +66,18 @@ struct MomArgs {
   int tile_start[DP_MAX_TYPES + 1];
   const int* perm;
   const int* nl_j;
-  const float4* env;  // [N * nc][2]: (s, u), (ds, r), rows in sorted order
+  // per-slot records, rows in sorted atom order [N * nc]: (s, s u), (s, u), (ds/dr, r, tau, l)
+  const float4* envR;
+  const float4* envU;
+  const float4* envB;
   float* Tm;          // [N][M][4]
   void* D;            // [N][M * A], BF16 or FP32
   int d_bf16;
   const float* gD;  // [N][M * A]
   double* force;    // [N][3] input order
   double* avir;     // [N][9] input order
+  unsigned char* gta;  // backward A operand per tile: the shared-memory image of dE/dT rows
+  int* gtx;            // its row scales [tiles][128]
   int* table_range;
   int* err;
 };
@@ -118,14 +123,81 @@ __device__ __forceinline__ float tau_at(const MomArgs& g, float s, int l) {
                   : (s - (g.split + (float)(l - g.n1) * g.stride2)) * g.inv2;
 }
 
-// Walk of one atom's neighbour list of one type, visiting the slots kbeg, kbeg + STEP, ...
-// (the backward splits each list into STEP = 4 interleaved phases, one per warp; the forward
-// walks whole lists, STEP = 1); lane a of a warp takes atom a, so a warp advances 32 atoms in
-// step.  Each thread streams its own slots' records (s, u), (ds, r, tau, l) through two private
-// 4-slot shared-memory windows with cp.async, one window ahead of the one it reads: no other
-// thread touches them, so no synchronisation is needed.  The records carry intervals already
-// made non-increasing along the list (k_env_mom).
+// Walks of one atom's neighbour list of one type; lane a of a warp takes atom a, so a warp
+// advances 32 atoms in step.  Each thread streams its own slots' records through two private
+// shared-memory windows with cp.async, one window ahead of the one it reads: no other thread
+// touches them, so no synchronisation is needed.  The records carry intervals already made
+// non-increasing along the list (k_env_mom).
+//
+// Forward: warp c walks whole lists for component c, reading R_c and (tau, l) of each slot.
+constexpr int kWinF = 8;
+struct FWalk {
+  int k, kend, wbase, cur;
+  bool have;
+  int l;
+  float tau, R;
+};
+struct FWindow {  // this thread's two windows
+  float* R;       // [2][kWinF]
+  float2* tl;     // [2][kWinF]
+};
+__device__ __forceinline__ void fwin_fill(const MomArgs& g, int p, int c, const FWindow& win, int buf, int k0,
+                                          int kend) {
+#pragma unroll
+  for (int q = 0; q < kWinF; ++q) {
+    const int slot = k0 + q;
+    if (slot < kend) {
+      const long row = (long)p * g.nc + slot;
+      cp_async4(win.R + buf * kWinF + q, reinterpret_cast<const float*>(g.envR + row) + c);
+      cp_async8(win.tl + buf * kWinF + q, reinterpret_cast<const float*>(g.envB + row) + 2);
+    }
+  }
+  cp_async_commit();
+}
+__device__ __forceinline__ void fwalk_start(const MomArgs& g, int p, int c, const FWindow& win, FWalk& w, int kbeg,
+                                            int kend) {
+  w.k = kbeg;
+  w.kend = kend;
+  w.wbase = kbeg;
+  w.cur = 0;
+  w.have = false;
+  for (int slot = kbeg + 2 * kWinF + c * 8; slot < kend; slot += 32) {  // the four warps split the lines
+    const long row = (long)p * g.nc + slot;
+    prefetch_l2(g.envR + row);
+    prefetch_l2(g.envB + row);
+  }
+  cp_async_wait0();  // no copy of an earlier walk is still in flight into the windows
+  fwin_fill(g, p, c, win, 0, kbeg, kend);
+  fwin_fill(g, p, c, win, 1, kbeg + kWinF, kend);
+  cp_async_wait1();
+}
+__device__ __forceinline__ void fwalk_next(const MomArgs& g, int p, int c, const FWindow& win, FWalk& w) {
+  w.have = false;
+  if (w.k >= w.kend) return;
+  if (w.k >= w.wbase + kWinF) {  // current window used up: refill it two windows ahead, switch
+    fwin_fill(g, p, c, win, w.cur, w.wbase + 2 * kWinF, w.kend);
+    w.cur ^= 1;
+    w.wbase += kWinF;
+    cp_async_wait1();
+  }
+  const int q = w.cur * kWinF + (w.k - w.wbase);
+  const float2 tl = win.tl[q];
+  const int l = __float_as_int(tl.y);
+  if (l < 0) {  // padding: real neighbours fill the front of the type block
+    w.kend = w.k;
+    return;
+  }
+  w.R = win.R[q];
+  w.l = l;
+  w.tau = tl.x;
+  w.have = true;
+  ++w.k;
+}
+
+// Backward: the four warps take every fourth slot (phase = warp) and read (s, u), (ds, r, tau, l)
+// and the neighbour index; the phase's slots are also prefetched into L2 when its walk starts.
 constexpr int kWin = 4;
+constexpr int kStep = 4;
 struct Walk {
   int k, kend, wbase, cur;  // next slot, end of the block, first slot of the current window, its buffer
   bool have;
@@ -136,26 +208,24 @@ struct Walk {
 struct Window {  // this thread's two windows
   float4* e0;    // [2][kWin]
   float4* e1;    // [2][kWin]
-  int* j;        // [2][kWin] (backward only)
+  int* j;        // [2][kWin]
 };
 
-template <bool kJ, int STEP>
 __device__ __forceinline__ void win_fill(const MomArgs& g, int p, int i, const Window& win, int buf, int k0,
                                          int kend) {
 #pragma unroll
   for (int q = 0; q < kWin; ++q) {
-    const int slot = k0 + STEP * q;
+    const int slot = k0 + kStep * q;
     if (slot < kend) {
       const long row = (long)p * g.nc + slot;
-      cp_async16(win.e0 + buf * kWin + q, g.env + row * 2);
-      cp_async16(win.e1 + buf * kWin + q, g.env + row * 2 + 1);
-      if (kJ) cp_async4(win.j + buf * kWin + q, g.nl_j + (long)i * g.nc + slot);
+      cp_async16(win.e0 + buf * kWin + q, g.envU + row);
+      cp_async16(win.e1 + buf * kWin + q, g.envB + row);
+      cp_async4(win.j + buf * kWin + q, g.nl_j + (long)i * g.nc + slot);
     }
   }
   cp_async_commit();
 }
 
-template <bool kJ, int STEP>
 __device__ __forceinline__ void walk_start(const MomArgs& g, int p, int i, const Window& win, Walk& w, int kbeg,
                                            int kend) {
   w.k = kbeg;
@@ -163,23 +233,27 @@ __device__ __forceinline__ void walk_start(const MomArgs& g, int p, int i, const
   w.wbase = kbeg;
   w.cur = 0;
   w.have = false;
+  for (int slot = kbeg + 2 * kStep * kWin; slot < kend; slot += kStep) {
+    const long row = (long)p * g.nc + slot;
+    prefetch_l2(g.envU + row);
+    prefetch_l2(g.envB + row);
+  }
   cp_async_wait0();  // no copy of an earlier walk is still in flight into the windows
-  win_fill<kJ, STEP>(g, p, i, win, 0, kbeg, kend);
-  win_fill<kJ, STEP>(g, p, i, win, 1, kbeg + STEP * kWin, kend);
+  win_fill(g, p, i, win, 0, kbeg, kend);
+  win_fill(g, p, i, win, 1, kbeg + kStep * kWin, kend);
   cp_async_wait1();
 }
 
-template <bool kJ, int STEP>
 __device__ __forceinline__ void walk_next(const MomArgs& g, int p, int i, const Window& win, Walk& w) {
   w.have = false;
   if (w.k >= w.kend) return;
-  if (w.k >= w.wbase + STEP * kWin) {  // current window used up: refill it two windows ahead, switch
-    win_fill<kJ, STEP>(g, p, i, win, w.cur, w.wbase + 2 * STEP * kWin, w.kend);
+  if (w.k >= w.wbase + kStep * kWin) {  // current window used up: refill it two windows ahead, switch
+    win_fill(g, p, i, win, w.cur, w.wbase + 2 * kStep * kWin, w.kend);
     w.cur ^= 1;
-    w.wbase += STEP * kWin;
+    w.wbase += kStep * kWin;
     cp_async_wait1();
   }
-  const int q = w.cur * kWin + (w.k - w.wbase) / STEP;
+  const int q = w.cur * kWin + (w.k - w.wbase) / kStep;
   w.e1 = win.e1[q];
   const int l = __float_as_int(w.e1.w);
   if (l < 0) {  // padding: real neighbours fill the front of the type block
@@ -187,11 +261,11 @@ __device__ __forceinline__ void walk_next(const MomArgs& g, int p, int i, const 
     return;
   }
   w.e0 = win.e0[q];
-  if (kJ) w.j = win.j[q];
+  w.j = win.j[q];
   w.l = l;
   w.tau = w.e1.z;
   w.have = true;
-  w.k += STEP;
+  w.k += kStep;
 }
 
 // Largest 8-interval group holding a neighbour of each type, over the tile's atoms.
@@ -200,7 +274,7 @@ __device__ __forceinline__ void tile_groups(const MomArgs& g, int p, int i, bool
   for (int t = 0; t < g.ntypes; ++t) {
     const int k = g.sel_off[t];
     if (k < g.sel_off[t + 1]) {
-      const int l = __float_as_int(g.env[((long)p * g.nc + k) * 2 + 1].w);
+      const int l = __float_as_int(g.envB[(long)p * g.nc + k].w);
       if (l >= 0) atomicMax(&ghi[t], l >> 3);
     }
   }
@@ -239,10 +313,10 @@ __device__ __forceinline__ uint32_t sw_off(int r, int q) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
 }
 
-// Ring depth: three stages for the single-pass operands, two for the high/low pairs.
+// Ring depth of the operand stages.
 template <int NPASS>
 struct MomStages {
-  static constexpr int value = NPASS == 1 ? 3 : 2;
+  static constexpr int value = 2;
 };
 
 // FP32 rows of one atom in the staging / P buffers: 4 rows of 68 floats (8 chunks of 8 and a
@@ -250,24 +324,21 @@ struct MomStages {
 constexpr int kRowPitch = 68;
 constexpr int kAtomPitch = 276;
 constexpr uint32_t kRowBufBytes = kAtoms * kAtomPitch * 4;
-constexpr uint32_t kFwdWinBytes = kRows * 2 * kWin * 32;  // per thread: two windows of (e0, e1)
+constexpr uint32_t kFwdWinBytes = kRows * 2 * kWinF * 12;  // per thread: two windows of R_c, (tau, l)
 constexpr uint32_t kBwdWinBytes = kRows * 2 * kWin * 36;  // per thread: two windows of (e0, e1, j)
 
 __host__ __device__ inline uint32_t fwd_ring_bytes(int npass, int npad) {
-  const uint32_t parts = npass == 1 ? 1 : 2, stages = npass == 1 ? 3 : 2;
+  const uint32_t parts = npass == 1 ? 1 : 2, stages = 2;
   return stages * parts * (uint32_t)(kABlock + npad * 128);
 }
-// Backward shared-memory region after the A operand: phase 1 holds two staged groups of dE/dD
-// and T rows plus a 16-row FP32 scratch; phase 2 the B ring, the P buffer and the windows.
+// Backward shared memory after the A operand: the B ring, the P buffer, the neighbour windows
+// and the row scales.
 __host__ __device__ inline uint32_t bwd_ring_bytes(int npass) {
-  const uint32_t parts = npass == 1 ? 1 : 2, stages = npass == 1 ? 3 : 2;
+  const uint32_t parts = npass == 1 ? 1 : 2, stages = 2;
   return stages * parts * 2u * 64u * 128u;
 }
-__host__ __device__ inline uint32_t bwd_region(int npass, int npad, int M, int A) {
-  const uint32_t ph1 = 2u * kGroupAtoms * (uint32_t)(M * A * 4 + M * 16) + 16u * (uint32_t)(npad + 4) * 4u;
-  const uint32_t ph2 = bwd_ring_bytes(npass) + kRowBufBytes + kBwdWinBytes;
-  const uint32_t r = ph1 > ph2 ? ph1 : ph2;
-  return (r + 15u) & ~15u;
+__host__ __device__ inline uint32_t bwd_region(int npass) {
+  return bwd_ring_bytes(npass) + kRowBufBytes + kBwdWinBytes + kRows * 4;
 }
 
 // Per-slot records of the listed pairs (sorted atom order): (s, u) and (ds/dr, r, tau, l), with
@@ -277,7 +348,7 @@ __host__ __device__ inline uint32_t bwd_region(int npass, int npad, int M, int A
 // rounding of s inverts two nearly equal distances.
 __global__ void __launch_bounds__(256)
     k_env_mom(PathConst pc, MomArgs g, const double* __restrict__ coord, const int* __restrict__ nl_code,
-              float4* __restrict__ env) {
+              float4* __restrict__ envR, float4* __restrict__ envU, float4* __restrict__ envB) {
   const long task = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (task >= (long)pc.natoms * pc.ntypes) return;  // warp-uniform
@@ -312,10 +383,11 @@ __global__ void __launch_bounds__(256)
     }
     if (in) {
       if (j >= 0) {
-        env[row * 2] = make_float4(s, u[0], u[1], u[2]);
-        env[row * 2 + 1] = make_float4(ds, r, tau, __int_as_float(l));
+        envR[row] = make_float4(s, s * u[0], s * u[1], s * u[2]);
+        envU[row] = make_float4(s, u[0], u[1], u[2]);
+        envB[row] = make_float4(ds, r, tau, __int_as_float(l));
       } else {
-        env[row * 2 + 1] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        envB[row] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
       }
     }
     carry = __shfl_sync(0xffffffffu, m, 31);
@@ -436,11 +508,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     //      row (lane, c); each thread walks its atom's whole list and owns its row outright ----
     const int crow = warp;            // component built by this warp
     const int arow = lane * 4 + crow;  // A row written by this thread
-    Window win;
-    win.e0 = reinterpret_cast<float4*>(wins) + r * 2 * kWin;
-    win.e1 = reinterpret_cast<float4*>(wins) + (kRows + r) * 2 * kWin;
-    win.j = nullptr;
-    Walk w;
+    FWindow win;
+    win.R = reinterpret_cast<float*>(wins) + r * 2 * kWinF;
+    win.tl = reinterpret_cast<float2*>(wins + kRows * 2 * kWinF * 4) + r * 2 * kWinF;
+    FWalk w;
     w.have = false;
     int cur_t = -1;
     bool dead = false;  // after a timed-out wait: stop waiting, keep going through the blocks
@@ -454,8 +525,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         cur_t = t;
         w.have = false;
         if (valid_b) {
-          walk_start<false, 1>(g, pb, ib, win, w, g.sel_off[t], g.sel_off[t + 1]);
-          walk_next<false, 1>(g, pb, ib, win, w);
+          fwalk_start(g, pb, crow, win, w, g.sel_off[t], g.sel_off[t + 1]);
+          fwalk_next(g, pb, crow, win, w);
         }
       }
       unsigned char* ahi = smem + s * STAGE;
@@ -479,14 +550,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int pp = 0; pp < 8; ++pp) mu[pp] = 0.f;
             cur_q = q;
           }
-          const float sv = w.e0.x;
-          float pw = crow == 0 ? sv : sv * (crow == 1 ? w.e0.y : (crow == 2 ? w.e0.z : w.e0.w));
+          float pw = w.R;
 #pragma unroll
           for (int pp = 0; pp < 6; ++pp) {
             mu[pp] += pw;
             pw *= w.tau;
           }
-          walk_next<false, 1>(g, pb, ib, win, w);
+          fwalk_next(g, pb, crow, win, w);
         }
       }
       if (cur_q >= 0) {
@@ -570,173 +640,38 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // =============================================================================================
-// Backward: dE/dT -> P -> per-neighbour dE/dr_ij -> forces and per-atom virial
+// dE/dT rows of every tile as the backward's A operand (the shared-memory image, 128-byte
+// swizzle, FP16 or BF16 high/low parts, each row scaled by a power of two):
+//   gT_m = sum_l gD[m][l] T[l][c] + [m < A] sum_q gD[q][m] T[q][c]
+// One CTA per group of four atoms of a tile (blockIdx.y); many CTAs per SM hide the latency of
+// the dE/dD rows.
 // =============================================================================================
 template <int NPASS, int NPAD>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
+__global__ void __launch_bounds__(kRows)
+    k_mom_gT(const MomArgs g) {
+  constexpr int A_BYTES = 2 * kABlock;
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
-  constexpr int S = MomStages<NPASS>::value;
-  constexpr int A_BYTES = 2 * kABlock;  // K = m in two 64-column blocks
-  constexpr int B_KBLK = 64 * 128;      // 64 rows (8 intervals x 8 powers) x 128 B
-  constexpr int B_STAGE = PARTS * 2 * B_KBLK;
-  constexpr int KSTEPS = NPAD / 16;
   constexpr int NGRP = kAtoms / kGroupAtoms;
   constexpr int SCRP = NPAD + 4;  // FP32 scratch row pitch
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const uint32_t bytesD = (uint32_t)(g.M * g.A * 4), bytesT = (uint32_t)(g.M * 16);
-  const uint32_t gbuf = kGroupAtoms * (bytesD + bytesT);
-  const uint32_t region = bwd_region(NPASS, NPAD, g.M, g.A);
-  unsigned char* As = smem;                     // PARTS x A_BYTES, dE/dT rows (A operand)
-  unsigned char* reg = smem + PARTS * A_BYTES;  // phase 1: staged rows + scratch; phase 2: below
-  unsigned char* ring = reg;
-  float* Ps = reinterpret_cast<float*>(reg + bwd_ring_bytes(NPASS));  // P of one block [atom][c][chunk][8]
-  unsigned char* wins = reg + bwd_ring_bytes(NPASS) + kRowBufBytes;
-  float* scr = reinterpret_cast<float*>(reg + 2 * gbuf);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(reg + region);
-  uint64_t* bfull = bar;
-  uint64_t* bempty = bar + S;
-  uint64_t* afull = bar + 2 * S;
-  uint64_t* accfull = afull + 1;     // [2]
-  uint64_t* accempty = accfull + 2;  // [2]
-  uint64_t* gfull = accempty + 2;    // [2]
-  uint64_t* gempty = gfull + 2;      // [2]
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gempty + 2);
-  int* ghi = reinterpret_cast<int*>(tmem_holder + 1);
-  int* ex_s = ghi + DP_MAX_TYPES;  // [128] power-of-two scale of each dE/dT row
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ __align__(16) float scr[16 * SCRP];
+  static_assert(NGRP == 8, "eight groups of four atoms per tile");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = lane & 3;
   int ti = 0;
   while (ti + 1 < g.ntypes && (int)blockIdx.x >= g.tile_start[ti + 1]) ++ti;
   const int row0 = g.row_start[ti] + ((int)blockIdx.x - g.tile_start[ti]) * kAtoms;
   const int row_end = g.row_start[ti + 1];
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&bfull[s], 1);
-      mbar_init(&bempty[s], 1);
-    }
-    mbar_init(afull, kRows);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&accfull[b], 1);
-      mbar_init(&accempty[b], kRows);
-      mbar_init(&gfull[b], 1);
-      mbar_init(&gempty[b], kRows);
-    }
-    for (int t = 0; t < DP_MAX_TYPES; ++t) ghi[t] = -1;
-    mbar_fence_init();
-  }
-  if (warp == 4) tmem_alloc(tmem_holder, 128);
-  const int r = threadIdx.x;  // accumulator row (atom r / 4, component r % 4)
-  const int c = r & 3;
-  const int pb = row0 + lane;  // phase-2 walker: atom `lane`, phase `warp`
-  const bool valid_b = warp < 4 && pb < row_end;
-  const int ib = valid_b ? g.perm[pb] : 0;
-  if (warp == 0) tile_groups(g, pb, ib, valid_b, ghi);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_holder;
-  int nch = 0;
-  for (int t = 0; t < g.ntypes; ++t) nch += ghi[t] + 1;
-
-  if (warp == 4) {
-    if (lane == 0) {
-      // ---- phase 1: dE/dD and T rows of four atoms at a time, double-buffered bulk copies ----
-      bool ok = true;
-      for (int q = 0; q < NGRP; ++q) {
-        const int b = q & 1;
-        if (q >= 2 && !mbar_wait(&gempty[b], ((q >> 1) - 1) & 1, g.err)) {
-          ok = false;
-          break;
-        }
-        const int p0 = row0 + q * kGroupAtoms;
-        const int nv = max(0, min(kGroupAtoms, row_end - p0));
-        unsigned char* dst = reg + b * gbuf;
-        if (nv > 0) {
-          mbar_expect_tx(&gfull[b], (uint32_t)nv * (bytesD + bytesT));
-          bulk_load(dst, g.gD + (long)p0 * g.M * g.A, (uint32_t)nv * bytesD, &gfull[b]);
-          bulk_load(dst + kGroupAtoms * bytesD, g.Tm + (long)p0 * g.M * 4, (uint32_t)nv * bytesT, &gfull[b]);
-        } else {
-          mbar_arrive(&gfull[b]);
-        }
-      }
-      // ---- phase 2: TMA producer and MMA issuer ----
-      if (ok) ok = mbar_wait(afull, 0, g.err);  // dE/dT rows in place, phase-1 buffers released
-      const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
-      auto issue = [&](int ch) {
-        int t, grp;
-        block_of(ch, ghi, g.ntypes, t, grp);
-        const int s = ch % S;
-        unsigned char* bs = ring + s * B_STAGE;
-        mbar_expect_tx(&bfull[s], B_STAGE);
-        const int y = ((ti * g.ntypes + t) * g.lcp + 8 * grp) * 8;
-        tma_load_2d(bs, &bhi, &bfull[s], 0, y);
-        tma_load_2d(bs + B_KBLK, &bhi, &bfull[s], 64, y);
-        if (PARTS == 2) {
-          tma_load_2d(bs + 2 * B_KBLK, &blo, &bfull[s], 0, y);
-          tma_load_2d(bs + 3 * B_KBLK, &blo, &bfull[s], 64, y);
-        }
-      };
-      int issued = 0, done = 0;
-      if (ok)
-        for (; issued < S - 1 && issued < nch; ++issued) issue(issued);
-      for (int ch = 0; ok && ch < nch; ++ch) {
-        const int s = ch % S, buf = ch & 1;
-        if (!mbar_wait(&bfull[s], (ch / S) & 1, g.err)) {
-          ok = false;
-          break;
-        }
-        done = ch + 1;
-        if (ch >= 2 && !mbar_wait(&accempty[buf], ((ch >> 1) - 1) & 1, g.err)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t sa = su32(As), sb = su32(ring + s * B_STAGE);
-        const uint32_t acc = tmem + (uint32_t)(buf * 64);
-#pragma unroll
-        for (int ks = 0; ks < KSTEPS; ++ks) {
-          const uint32_t kbk = (uint32_t)(ks >> 2), ko = (uint32_t)(ks & 3) * 2;
-          const uint64_t ah = sdesc_sw128(sa + kbk * kABlock) + ko;
-          const uint64_t bh = sdesc_sw128(sb + kbk * B_KBLK) + ko;
-          mma_f16(acc, ah, bh, idesc, ks != 0);
-          if (NPASS == 3) {
-            const uint64_t al = sdesc_sw128(sa + A_BYTES + kbk * kABlock) + ko;
-            const uint64_t bl = sdesc_sw128(sb + 2 * B_KBLK + kbk * B_KBLK) + ko;
-            mma_f16(acc, ah, bl, idesc, 1);
-            mma_f16(acc, al, bh, idesc, 1);
-          }
-        }
-        mma_commit(&bempty[s]);
-        mma_commit(&accfull[buf]);
-        const int kn = ch + S - 1;
-        if (kn < nch) {
-          if (kn >= S && !mbar_wait(&bempty[kn % S], ((kn / S) - 1) & 1, g.err)) {
-            ok = false;
-            break;
-          }
-          issue(kn);
-          issued = kn + 1;
-        }
-      }
-      for (int ch = done; ch < issued; ++ch) mbar_wait(&bfull[ch % S], (ch / S) & 1, g.err);
-    }
-  } else {
-    // ---- phase 1: dE/dT rows; warp w takes atom w of each group, lane = (part, c) ----
+    // warp w takes atom w of each group of four, lane = (part, c)
     //   gT_m = sum_l gD[m][l] T[l][c] + [m < A] sum_q gD[q][m] T[q][c],  m = part + 8k
     {
       const int part = lane >> 2;
       float* srow = scr + (warp * 4 + c) * SCRP;
-      for (int q = 0; q < NGRP; ++q) {
-        const int b = q & 1;
-        mbar_wait(&gfull[b], (q >> 1) & 1, g.err);
+      unsigned char* At = g.gta + (long)blockIdx.x * PARTS * A_BYTES;
+      {
+        const int q = blockIdx.y;
         const int at = q * kGroupAtoms + warp;  // atom of the tile
         const bool va = row0 + at < row_end;   // warp-uniform
-        const float* gDa = reinterpret_cast<const float*>(reg + b * gbuf) + warp * g.M * g.A;
-        const float* Ta = reinterpret_cast<const float*>(reg + b * gbuf + kGroupAtoms * bytesD) + warp * g.M * 4;
+        const float* gDa = g.gD + (long)(row0 + at) * g.M * g.A;
+        const float* Ta = g.Tm + (long)(row0 + at) * g.M * 4;
         int ex = 0;
         if (va) {
           float tl[16], ext[16];
@@ -810,16 +745,147 @@ __global__ void __launch_bounds__(kThreads, 1)
             v[e] = (va && m < g.M) ? ldexpf(srow[m], -ex) : 0.f;
           }
           const uint32_t off = (uint32_t)((qq >> 3) * kABlock) + sw_off(rr, qq & 7);
-          store_chunk<NPASS>(As + off, As + A_BYTES + off, v);
+          store_chunk<NPASS>(At + off, At + A_BYTES + off, v);
         }
-        if (part == 0) ex_s[rr] = ex;
-        __syncwarp();  // the scratch row is read before the next group overwrites it
-        mbar_arrive(&gempty[b]);
+        if (part == 0) g.gtx[(long)blockIdx.x * kRows + rr] = ex;
+        __syncwarp();  // the scratch row is read before the next atom overwrites it
       }
-      fence_async_smem();
-      mbar_arrive(afull);
-      bar_sync(1, kRows);  // phase-1 buffers become the ring, P and the neighbour windows
     }
+}
+
+// =============================================================================================
+// Backward: dE/dT -> P -> per-neighbour dE/dr_ij -> forces and per-atom virial
+// =============================================================================================
+template <int NPASS, int NPAD>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
+  constexpr int PARTS = NPASS == 1 ? 1 : 2;
+  constexpr int S = MomStages<NPASS>::value;
+  constexpr int A_BYTES = 2 * kABlock;  // K = m in two 64-column blocks
+  constexpr int B_KBLK = 64 * 128;      // 64 rows (8 intervals x 8 powers) x 128 B
+  constexpr int B_STAGE = PARTS * 2 * B_KBLK;
+  constexpr int KSTEPS = NPAD / 16;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* As = smem;                      // PARTS x A_BYTES, dE/dT rows (A operand)
+  unsigned char* ring = smem + PARTS * A_BYTES;  // B stages
+  float* Ps = reinterpret_cast<float*>(ring + bwd_ring_bytes(NPASS));  // P of one block [atom][c][chunk][8]
+  unsigned char* wins = ring + bwd_ring_bytes(NPASS) + kRowBufBytes;
+  int* ex_s = reinterpret_cast<int*>(wins + kBwdWinBytes);  // [128] power-of-two scale of each dE/dT row
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ex_s + kRows);
+  uint64_t* bfull = bar;
+  uint64_t* bempty = bar + S;
+  uint64_t* afull = bar + 2 * S;
+  uint64_t* accfull = afull + 1;     // [2]
+  uint64_t* accempty = accfull + 2;  // [2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accempty + 2);
+  int* ghi = reinterpret_cast<int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ti = 0;
+  while (ti + 1 < g.ntypes && (int)blockIdx.x >= g.tile_start[ti + 1]) ++ti;
+  const int row0 = g.row_start[ti] + ((int)blockIdx.x - g.tile_start[ti]) * kAtoms;
+  const int row_end = g.row_start[ti + 1];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&bfull[s], 1);
+      mbar_init(&bempty[s], 1);
+    }
+    mbar_init(afull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], kRows);
+    }
+    for (int t = 0; t < DP_MAX_TYPES; ++t) ghi[t] = -1;
+    mbar_fence_init();
+  }
+  if (warp == 4) tmem_alloc(tmem_holder, 128);
+  const int r = threadIdx.x;  // accumulator row (atom r / 4, component r % 4)
+  const int c = r & 3;
+  const int pb = row0 + lane;  // phase-2 walker: atom `lane`, phase `warp`
+  const bool valid_b = warp < 4 && pb < row_end;
+  const int ib = valid_b ? g.perm[pb] : 0;
+  if (warp == 0) tile_groups(g, pb, ib, valid_b, ghi);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  int nch = 0;
+  for (int t = 0; t < g.ntypes; ++t) nch += ghi[t] + 1;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---- the A operand of this tile and its row scales ----
+      mbar_expect_tx(afull, PARTS * A_BYTES + kRows * 4);
+      bulk_load(As, g.gta + (long)blockIdx.x * PARTS * A_BYTES, PARTS * A_BYTES, afull);
+      bulk_load(ex_s, g.gtx + (long)blockIdx.x * kRows, kRows * 4, afull);
+      bool ok = true;
+      // ---- phase 2: TMA producer and MMA issuer ----
+      ok = mbar_wait(afull, 0, g.err);
+      const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
+      auto issue = [&](int ch) {
+        int t, grp;
+        block_of(ch, ghi, g.ntypes, t, grp);
+        const int s = ch % S;
+        unsigned char* bs = ring + s * B_STAGE;
+        mbar_expect_tx(&bfull[s], B_STAGE);
+        const int y = ((ti * g.ntypes + t) * g.lcp + 8 * grp) * 8;
+        tma_load_2d(bs, &bhi, &bfull[s], 0, y);
+        tma_load_2d(bs + B_KBLK, &bhi, &bfull[s], 64, y);
+        if (PARTS == 2) {
+          tma_load_2d(bs + 2 * B_KBLK, &blo, &bfull[s], 0, y);
+          tma_load_2d(bs + 3 * B_KBLK, &blo, &bfull[s], 64, y);
+        }
+      };
+      int issued = 0, done = 0;
+      if (ok)
+        for (; issued < S - 1 && issued < nch; ++issued) issue(issued);
+      for (int ch = 0; ok && ch < nch; ++ch) {
+        const int s = ch % S, buf = ch & 1;
+        if (!mbar_wait(&bfull[s], (ch / S) & 1, g.err)) {
+          ok = false;
+          break;
+        }
+        done = ch + 1;
+        if (ch >= 2 && !mbar_wait(&accempty[buf], ((ch >> 1) - 1) & 1, g.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = su32(As), sb = su32(ring + s * B_STAGE);
+        const uint32_t acc = tmem + (uint32_t)(buf * 64);
+#pragma unroll
+        for (int ks = 0; ks < KSTEPS; ++ks) {
+          const uint32_t kbk = (uint32_t)(ks >> 2), ko = (uint32_t)(ks & 3) * 2;
+          const uint64_t ah = sdesc_sw128(sa + kbk * kABlock) + ko;
+          const uint64_t bh = sdesc_sw128(sb + kbk * B_KBLK) + ko;
+          mma_f16(acc, ah, bh, idesc, ks != 0);
+          if (NPASS == 3) {
+            const uint64_t al = sdesc_sw128(sa + A_BYTES + kbk * kABlock) + ko;
+            const uint64_t bl = sdesc_sw128(sb + 2 * B_KBLK + kbk * B_KBLK) + ko;
+            mma_f16(acc, ah, bl, idesc, 1);
+            mma_f16(acc, al, bh, idesc, 1);
+          }
+        }
+        mma_commit(&bempty[s]);
+        mma_commit(&accfull[buf]);
+        const int kn = ch + S - 1;
+        if (kn < nch) {
+          if (kn >= S && !mbar_wait(&bempty[kn % S], ((kn / S) - 1) & 1, g.err)) {
+            ok = false;
+            break;
+          }
+          issue(kn);
+          issued = kn + 1;
+        }
+      }
+      for (int ch = done; ch < issued; ++ch) mbar_wait(&bfull[ch % S], (ch / S) & 1, g.err);
+    }
+  } else {
+    // ---- the A operand (dE/dT rows, k_mom_gT) and the row scales arrive by bulk copy ----
+    mbar_wait(afull, 0, g.err);
 
     // ---- phase 2, per 8-interval block: P from TMEM to shared memory, then every warp walks
     //      its phase of the 32 atoms' neighbours in the block ----
@@ -859,8 +925,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         cur_t = t;
         w.have = false;
         if (valid_b) {
-          walk_start<true, 4>(g, pb, ib, win, w, g.sel_off[t] + warp, g.sel_off[t + 1]);
-          walk_next<true, 4>(g, pb, ib, win, w);
+          walk_start(g, pb, ib, win, w, g.sel_off[t] + warp, g.sel_off[t + 1]);
+          walk_next(g, pb, ib, win, w);
         }
       }
       for (;;) {
@@ -892,7 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= gd[aa] * dv[bb];
           }
-          walk_next<true, 4>(g, pb, ib, win, w);
+          walk_next(g, pb, ib, win, w);
         }
       }
       bar_sync(1, kRows);  // every walker is done with this P block
@@ -965,20 +1031,21 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
 }
 
 size_t fwd_smem(int npass, int npad) {
-  const int S = npass == 1 ? 3 : 2;
+  const int S = 2;
   return (size_t)fwd_ring_bytes(npass, npad) + kFwdWinBytes + (2 * S + 1) * 8 + 4 +
          4 * DP_MAX_TYPES + 1024 + 64;
 }
 size_t bwd_smem(int npass, int npad, int M, int A) {
-  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 3 : 2;
-  return (size_t)parts * 2 * kABlock + bwd_region(npass, npad, M, A) + (2 * S + 9) * 8 + 4 +
-         4 * (DP_MAX_TYPES + kRows) + 1024 + 64;
+  const int parts = npass == 1 ? 1 : 2, S = 2;
+  return (size_t)parts * 2 * kABlock + bwd_region(npass) + (2 * S + 5) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
 }
 
 template <int NPASS, int NPAD>
-int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, bool fwd, cudaStream_t st) {
+int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, int which, cudaStream_t st) {
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(m.mom_maps.data());
-  if (fwd) {
+  if (which == 1) {
+    k_mom_gT<NPASS, NPAD><<<dim3(tiles, kAtoms / kGroupAtoms), kRows, 0, st>>>(g);
+  } else if (which == 0) {
     const size_t sm = fwd_smem(NPASS, NPAD);
     DP_CUDA_TRY(cudaFuncSetAttribute(k_mom_fwd<NPASS, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_mom_fwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[0], maps[1], g);
@@ -992,12 +1059,12 @@ int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, bool fwd, cuda
 }
 
 template <int NPASS>
-int launch_mom_np(const DeviceModel& m, const MomArgs& g, int tiles, bool fwd, cudaStream_t st) {
-  if (m.mom_npad == 16) return launch_mom<NPASS, 16>(m, g, tiles, fwd, st);
-  if (m.mom_npad == 32) return launch_mom<NPASS, 32>(m, g, tiles, fwd, st);
-  if (m.mom_npad == 64) return launch_mom<NPASS, 64>(m, g, tiles, fwd, st);
-  if (m.mom_npad == 112) return launch_mom<NPASS, 112>(m, g, tiles, fwd, st);
-  if (m.mom_npad == 128) return launch_mom<NPASS, 128>(m, g, tiles, fwd, st);
+int launch_mom_np(const DeviceModel& m, const MomArgs& g, int tiles, int which, cudaStream_t st) {
+  if (m.mom_npad == 16) return launch_mom<NPASS, 16>(m, g, tiles, which, st);
+  if (m.mom_npad == 32) return launch_mom<NPASS, 32>(m, g, tiles, which, st);
+  if (m.mom_npad == 64) return launch_mom<NPASS, 64>(m, g, tiles, which, st);
+  if (m.mom_npad == 112) return launch_mom<NPASS, 112>(m, g, tiles, which, st);
+  if (m.mom_npad == 128) return launch_mom<NPASS, 128>(m, g, tiles, which, st);
   set_error("moment path: unsupported padded width");
   return DP_E_UNSUPPORTED;
 }
@@ -1059,7 +1126,12 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const bool bf16 = m.mom_npass == 1;
   float* Tm = ar.get<float>(N * M * 4);
   void* D = bf16 ? (void*)ar.get<__nv_bfloat16>(N * M * A) : (void*)ar.get<float>(N * M * A);
-  float4* env = ar.get<float4>(N * pc.nc * 2);
+  float4* envR = ar.get<float4>(N * pc.nc);
+  float4* envU = ar.get<float4>(N * pc.nc);
+  float4* envB = ar.get<float4>(N * pc.nc);
+  const long max_tiles = (N + kAtoms - 1) / kAtoms + pc.ntypes;  // every type's last tile may be short
+  unsigned char* gta = ar.get<unsigned char>(max_tiles * (bf16 ? 1 : 2) * 2 * kABlock);
+  int* gtx = ar.get<int>(max_tiles * kRows);
   const float* gD = nullptr;
   if (ar.measure) {
     if (bf16) return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD);
@@ -1096,24 +1168,28 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const int tiles = g.tile_start[pc.ntypes];
   g.perm = io.perm;
   g.nl_j = io.nl_j;
-  g.env = env;
+  g.envR = envR;
+  g.envU = envU;
+  g.envB = envB;
   g.Tm = Tm;
   g.D = D;
   g.d_bf16 = bf16 ? 1 : 0;
   g.force = io.force;
   g.avir = io.atom_virial;
+  g.gta = gta;
+  g.gtx = gtx;
   char* stw = reinterpret_cast<char*>(io.status);
   g.table_range = reinterpret_cast<int*>(stw + offsetof(DevStatus, table_range));
   g.err = reinterpret_cast<int*>(stw + offsetof(DevStatus, timeout));
   {
     ProfScope _ps(io.prof, "env", st);
     const long tasks = N * pc.ntypes;  // one warp per (atom, neighbour type)
-    k_env_mom<<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code, env);
+    k_env_mom<<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code, envR, envU, envB);
     DP_CUDA_TRY(cudaGetLastError());
   }
   if (tiles > 0) {
     ProfScope _ps(io.prof, "mom_fwd", st);
-    const int rc = bf16 ? launch_mom_np<1>(m, g, tiles, true, st) : launch_mom_np<3>(m, g, tiles, true, st);
+    const int rc = bf16 ? launch_mom_np<1>(m, g, tiles, 0, st) : launch_mom_np<3>(m, g, tiles, 0, st);
     if (rc != DP_OK) return rc;
   }
   int rc;
@@ -1124,8 +1200,13 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   if (rc != DP_OK) return rc;
   g.gD = gD;
   if (tiles > 0) {
+    {
+      ProfScope _ps(io.prof, "mom_gT", st);
+      rc = bf16 ? launch_mom_np<1>(m, g, tiles, 1, st) : launch_mom_np<3>(m, g, tiles, 1, st);
+      if (rc != DP_OK) return rc;
+    }
     ProfScope _ps(io.prof, "mom_bwd", st);
-    rc = bf16 ? launch_mom_np<1>(m, g, tiles, false, st) : launch_mom_np<3>(m, g, tiles, false, st);
+    rc = bf16 ? launch_mom_np<1>(m, g, tiles, 2, st) : launch_mom_np<3>(m, g, tiles, 2, st);
     if (rc != DP_OK) return rc;
   }
   return DP_OK;
