@@ -19,17 +19,16 @@
 // dE/ds_j = (1/Nc) sum_c R_{j,c} sum_m gT_{m,c} G'_m(s_j), with gT = dE/dT.  With
 //   P_{(t,l,p),c} = sum_m C^{(t)}_{(l,p),m} gT_{m,c}      (tensor cores: [128 rows] x [M] x [K blocks])
 // both are short polynomials per neighbour: dE/dR_c = (1/Nc) sum_p tau^p P_{p,c} and
-// dE/ds = (1/Nc) sum_c R_c sum_p p tau^{p-1} P_{p,c} / Delta_l.  The epilogue reads P for one
-// 8-interval block from TMEM, walks each atom's neighbours in that block and scatters the pair
-// forces (FP64 atomics) and the per-atom virial, as the CUDA-core compressed kernel does.
+// dE/ds = (1/Nc) sum_c R_c sum_p p tau^{p-1} P_{p,c} / Delta_l.
 //
 // Neighbours of each type block are sorted by distance, so their intervals are non-increasing
 // along the list and every (atom, interval) is a contiguous run; the few FP32 rounding
 // inversions are folded into the run of the previous neighbour (its polynomial piece evaluated
-// a rounding error beyond its end, where the pieces join with C^2 continuity).  Most
-// neighbours sit in the first intervals (s < 0.01 reaches from about 0.6 r_c to r_c), so the
-// walks are spread evenly: the four warps of a CTA take every fourth slot of each list and the
-// 32 lanes of a warp take the 32 atoms of the tile, all in step.
+// a rounding error beyond its end, where the pieces join with C^2 continuity).  Work is split
+// by its shape: everything per neighbour runs in lane-per-slot kernels at full occupancy
+// (k_env_mom forms the slot records and, by a segmented warp reduction, each run's moments;
+// k_force_mom turns each slot's run P into the pair force), while the tensor-core kernels only
+// move per-run data (a run's moments into the A tile, a run's P out of TMEM).
 //
 // Precision: FP16 operands in one pass (mixed mode), or BF16 operands split into high and low
 // parts with three passes (hi.hi + hi.lo + lo.hi; FP32 mode); FP32 accumulation.  The rows of
@@ -66,10 +65,14 @@ struct MomArgs {
   int tile_start[DP_MAX_TYPES + 1];
   const int* perm;
   const int* nl_j;
-  // per-slot records, rows in sorted atom order [N * nc]: (s, s u), (s, u), (ds/dr, r, tau, l)
-  const float4* envR;
-  const float4* envU;
-  const float4* envB;
+  // per-slot records, rows in sorted atom order [N * nc]: (s, u), (ds/dr, r, tau, l), run index
+  float4* envU;
+  float4* envB;
+  int* slot_run;
+  // per-run records, run r of type block t of atom p at row p * nc + sel_off[t] + r
+  int* run_l;      // interval of the run; -1 after the last run
+  uint4* run_rec;  // moments as A-operand chunks [row][4 components][parts]
+  float4* run_P;   // P of the run [row][4 components][2] (shares memory with run_rec)
   float* Tm;          // [N][M][4]
   void* D;            // [N][M * A], BF16 or FP32
   int d_bf16;
@@ -123,163 +126,6 @@ __device__ __forceinline__ float tau_at(const MomArgs& g, float s, int l) {
                   : (s - (g.split + (float)(l - g.n1) * g.stride2)) * g.inv2;
 }
 
-// Walks of one atom's neighbour list of one type; lane a of a warp takes atom a, so a warp
-// advances 32 atoms in step.  Each thread streams its own slots' records through two private
-// shared-memory windows with cp.async, one window ahead of the one it reads: no other thread
-// touches them, so no synchronisation is needed.  The records carry intervals already made
-// non-increasing along the list (k_env_mom).
-//
-// Forward: warp c walks whole lists for component c, reading R_c and (tau, l) of each slot.
-constexpr int kWinF = 8;
-struct FWalk {
-  int k, kend, wbase, cur;
-  bool have;
-  int l;
-  float tau, R;
-};
-struct FWindow {  // this thread's two windows
-  float* R;       // [2][kWinF]
-  float2* tl;     // [2][kWinF]
-};
-__device__ __forceinline__ void fwin_fill(const MomArgs& g, int p, int c, const FWindow& win, int buf, int k0,
-                                          int kend) {
-#pragma unroll
-  for (int q = 0; q < kWinF; ++q) {
-    const int slot = k0 + q;
-    if (slot < kend) {
-      const long row = (long)p * g.nc + slot;
-      cp_async4(win.R + buf * kWinF + q, reinterpret_cast<const float*>(g.envR + row) + c);
-      cp_async8(win.tl + buf * kWinF + q, reinterpret_cast<const float*>(g.envB + row) + 2);
-    }
-  }
-  cp_async_commit();
-}
-__device__ __forceinline__ void fwalk_start(const MomArgs& g, int p, int c, const FWindow& win, FWalk& w, int kbeg,
-                                            int kend) {
-  w.k = kbeg;
-  w.kend = kend;
-  w.wbase = kbeg;
-  w.cur = 0;
-  w.have = false;
-  for (int slot = kbeg + 2 * kWinF + c * 8; slot < kend; slot += 32) {  // the four warps split the lines
-    const long row = (long)p * g.nc + slot;
-    prefetch_l2(g.envR + row);
-    prefetch_l2(g.envB + row);
-  }
-  cp_async_wait0();  // no copy of an earlier walk is still in flight into the windows
-  fwin_fill(g, p, c, win, 0, kbeg, kend);
-  fwin_fill(g, p, c, win, 1, kbeg + kWinF, kend);
-  cp_async_wait1();
-}
-__device__ __forceinline__ void fwalk_next(const MomArgs& g, int p, int c, const FWindow& win, FWalk& w) {
-  w.have = false;
-  if (w.k >= w.kend) return;
-  if (w.k >= w.wbase + kWinF) {  // current window used up: refill it two windows ahead, switch
-    fwin_fill(g, p, c, win, w.cur, w.wbase + 2 * kWinF, w.kend);
-    w.cur ^= 1;
-    w.wbase += kWinF;
-    cp_async_wait1();
-  }
-  const int q = w.cur * kWinF + (w.k - w.wbase);
-  const float2 tl = win.tl[q];
-  const int l = __float_as_int(tl.y);
-  if (l < 0) {  // padding: real neighbours fill the front of the type block
-    w.kend = w.k;
-    return;
-  }
-  w.R = win.R[q];
-  w.l = l;
-  w.tau = tl.x;
-  w.have = true;
-  ++w.k;
-}
-
-// Backward: the four warps take every fourth slot (phase = warp) and read (s, u), (ds, r, tau, l)
-// and the neighbour index; the phase's slots are also prefetched into L2 when its walk starts.
-constexpr int kWin = 4;
-constexpr int kStep = 4;
-struct Walk {
-  int k, kend, wbase, cur;  // next slot, end of the block, first slot of the current window, its buffer
-  bool have;
-  int l, j;
-  float tau;
-  float4 e0, e1;  // (s, u), (ds, r, tau, l)
-};
-struct Window {  // this thread's two windows
-  float4* e0;    // [2][kWin]
-  float4* e1;    // [2][kWin]
-  int* j;        // [2][kWin]
-};
-
-__device__ __forceinline__ void win_fill(const MomArgs& g, int p, int i, const Window& win, int buf, int k0,
-                                         int kend) {
-#pragma unroll
-  for (int q = 0; q < kWin; ++q) {
-    const int slot = k0 + kStep * q;
-    if (slot < kend) {
-      const long row = (long)p * g.nc + slot;
-      cp_async16(win.e0 + buf * kWin + q, g.envU + row);
-      cp_async16(win.e1 + buf * kWin + q, g.envB + row);
-      cp_async4(win.j + buf * kWin + q, g.nl_j + (long)i * g.nc + slot);
-    }
-  }
-  cp_async_commit();
-}
-
-__device__ __forceinline__ void walk_start(const MomArgs& g, int p, int i, const Window& win, Walk& w, int kbeg,
-                                           int kend) {
-  w.k = kbeg;
-  w.kend = kend;
-  w.wbase = kbeg;
-  w.cur = 0;
-  w.have = false;
-  for (int slot = kbeg + 2 * kStep * kWin; slot < kend; slot += kStep) {
-    const long row = (long)p * g.nc + slot;
-    prefetch_l2(g.envU + row);
-    prefetch_l2(g.envB + row);
-  }
-  cp_async_wait0();  // no copy of an earlier walk is still in flight into the windows
-  win_fill(g, p, i, win, 0, kbeg, kend);
-  win_fill(g, p, i, win, 1, kbeg + kStep * kWin, kend);
-  cp_async_wait1();
-}
-
-__device__ __forceinline__ void walk_next(const MomArgs& g, int p, int i, const Window& win, Walk& w) {
-  w.have = false;
-  if (w.k >= w.kend) return;
-  if (w.k >= w.wbase + kStep * kWin) {  // current window used up: refill it two windows ahead, switch
-    win_fill(g, p, i, win, w.cur, w.wbase + 2 * kStep * kWin, w.kend);
-    w.cur ^= 1;
-    w.wbase += kStep * kWin;
-    cp_async_wait1();
-  }
-  const int q = w.cur * kWin + (w.k - w.wbase) / kStep;
-  w.e1 = win.e1[q];
-  const int l = __float_as_int(w.e1.w);
-  if (l < 0) {  // padding: real neighbours fill the front of the type block
-    w.kend = w.k;
-    return;
-  }
-  w.e0 = win.e0[q];
-  w.j = win.j[q];
-  w.l = l;
-  w.tau = w.e1.z;
-  w.have = true;
-  w.k += kStep;
-}
-
-// Largest 8-interval group holding a neighbour of each type, over the tile's atoms.
-__device__ __forceinline__ void tile_groups(const MomArgs& g, int p, int i, bool valid, int* ghi) {
-  if (!valid) return;
-  for (int t = 0; t < g.ntypes; ++t) {
-    const int k = g.sel_off[t];
-    if (k < g.sel_off[t + 1]) {
-      const int l = __float_as_int(g.envB[(long)p * g.nc + k].w);
-      if (l >= 0) atomicMax(&ghi[t], l >> 3);
-    }
-  }
-}
-
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   const __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -314,56 +160,83 @@ __device__ __forceinline__ uint32_t sw_off(int r, int q) {
 }
 
 // Ring depth of the operand stages.
+// The run intervals of the tile's 32 atoms, every type block ([atom][nc], -1 past a tile's end),
+// loaded once with many independent loads in flight per thread.
+__device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_end, int* runl_s, int tid, int nthreads) {
+  const int n = kAtoms * g.nc;
+  for (int e0 = tid; e0 < n; e0 += 8 * nthreads) {
+    int v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nthreads;
+      const int a = e / g.nc;
+      v[u] = (e < n && row0 + a < row_end) ? __ldg(g.run_l + (long)row0 * g.nc + e) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nthreads;
+      if (e < n) runl_s[e] = v[u];
+    }
+  }
+}
+
+// Ring depth of the forward's operand stages.
 template <int NPASS>
 struct MomStages {
-  static constexpr int value = 2;
+  static constexpr int value = NPASS == 1 ? 4 : 2;
 };
 
-// FP32 rows of one atom in the staging / P buffers: 4 rows of 68 floats (8 chunks of 8 and a
-// pad), atoms 276 floats apart, which spreads a warp's 32 atoms over the banks.
-constexpr int kRowPitch = 68;
-constexpr int kAtomPitch = 276;
-constexpr uint32_t kRowBufBytes = kAtoms * kAtomPitch * 4;
-constexpr uint32_t kFwdWinBytes = kRows * 2 * kWinF * 12;  // per thread: two windows of R_c, (tau, l)
-constexpr uint32_t kBwdWinBytes = kRows * 2 * kWin * 36;  // per thread: two windows of (e0, e1, j)
 
-__host__ __device__ inline uint32_t fwd_ring_bytes(int npass, int npad) {
-  const uint32_t parts = npass == 1 ? 1 : 2, stages = 2;
-  return stages * parts * (uint32_t)(kABlock + npad * 128);
-}
-// Backward shared memory after the A operand: the B ring, the P buffer, the neighbour windows
-// and the row scales.
-__host__ __device__ inline uint32_t bwd_ring_bytes(int npass) {
-  const uint32_t parts = npass == 1 ? 1 : 2, stages = 2;
-  return stages * parts * 2u * 64u * 128u;
-}
-__host__ __device__ inline uint32_t bwd_region(int npass) {
-  return bwd_ring_bytes(npass) + kRowBufBytes + kBwdWinBytes + kRows * 4;
+// Largest 8-interval group holding a neighbour of each type, over the tile's atoms (the first
+// run of each list has the largest interval; runl_s holds the tile's run lists).
+__device__ __forceinline__ void tile_groups(const MomArgs& g, const int* runl_s, int a, int* ghi) {
+  for (int t = 0; t < g.ntypes; ++t) {
+    const int l = runl_s[a * g.nc + g.sel_off[t]];
+    if (l >= 0) atomicMax(&ghi[t], l >> 3);
+  }
 }
 
-// Per-slot records of the listed pairs (sorted atom order): (s, u) and (ds/dr, r, tau, l), with
-// l = -1 marking padding; exact FP64 displacement, FP32 switch (Eq. (switch)).  One warp takes
-// one (atom, neighbour type) block: the interval is lowered to the running minimum along the
-// list (a prefix-minimum scan), so intervals never increase from slot to slot even where FP32
-// rounding of s inverts two nearly equal distances.
+// =============================================================================================
+// Per-slot records and per-run moments.  One warp takes one (atom, neighbour type) list, 32
+// slots at a time: exact FP64 displacement, FP32 switch (Eq. (switch)), interval and tau; the
+// interval is lowered to the running minimum along the list (a prefix-minimum scan) so that it
+// never increases from slot to slot, even where FP32 rounding of s inverts two nearly equal
+// distances.  Equal intervals then form contiguous runs, and a segmented reduction across the
+// lanes sums each run's moments mu_{p,c} = sum tau^p R_c (runs that cross a 32-slot batch are
+// carried to the next).  Each run's moments are written in the backward's A-operand chunk
+// format (FP16, or BF16 high and low parts): the forward kernel copies them into its tiles
+// without conversion.  Outputs, for slot k of atom p (row p * Nc + k):
+//   envU (s, u), envB (ds/dr, r, tau, l) with l = -1 marking padding, slot_run (run index);
+// and for run r of type block t (row p * Nc + sel_off[t] + r): run_l (-1 after the last run)
+// and run_rec.
+// =============================================================================================
+template <int NPASS>
 __global__ void __launch_bounds__(256)
-    k_env_mom(PathConst pc, MomArgs g, const double* __restrict__ coord, const int* __restrict__ nl_code,
-              float4* __restrict__ envR, float4* __restrict__ envU, float4* __restrict__ envB) {
+    k_env_mom(PathConst pc, MomArgs g, const double* __restrict__ coord, const int* __restrict__ nl_code) {
+  constexpr int PARTS = NPASS == 1 ? 1 : 2;
   const long task = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (task >= (long)pc.natoms * pc.ntypes) return;  // warp-uniform
   const int p = (int)(task / pc.ntypes), t = (int)(task % pc.ntypes);
   const int i = g.perm[p];
-  int carry = INT_MAX;
+  const int kb0 = g.sel_off[t], kb1 = g.sel_off[t + 1];
+  const long rbase = (long)p * pc.nc + kb0;  // first run record of this list
+  int lmin = INT_MAX;                        // running minimum of the interval
+  int carry_l = -1;                          // interval of the run open at the last batch's end
+  float carry[24];
+#pragma unroll
+  for (int e = 0; e < 24; ++e) carry[e] = 0.f;
+  int nruns = 0;
   bool oor = false;
-  for (int base = g.sel_off[t]; base < g.sel_off[t + 1]; base += 32) {
+  for (int base = kb0; base < kb1; base += 32) {
     const int k = base + lane;
-    const bool in = k < g.sel_off[t + 1];
+    const bool in = k < kb1;
     const long row = (long)p * pc.nc + k;
     const int j = in ? g.nl_j[(long)i * pc.nc + k] : -1;
+    const bool valid = j >= 0;
     int l = INT_MAX;
     float r = 0.f, s = 0.f, ds = 0.f, u[3] = {0.f, 0.f, 0.f}, tau = 0.f;
-    if (j >= 0) {
+    if (valid) {
       double d0, d1, d2;
       listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d0, d1, d2);
       pair_env<float>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
@@ -376,40 +249,121 @@ __global__ void __launch_bounds__(256)
       const int o = __shfl_up_sync(0xffffffffu, m, off);
       if (lane >= off) m = min(m, o);
     }
-    m = min(m, carry);
-    if (j >= 0 && m < l) {
+    m = min(m, lmin);
+    if (valid && m < l) {
       l = m;
       tau = tau_at(g, s, l);
     }
+    lmin = __shfl_sync(0xffffffffu, m, 31);
     if (in) {
-      if (j >= 0) {
-        envR[row] = make_float4(s, s * u[0], s * u[1], s * u[2]);
-        envU[row] = make_float4(s, u[0], u[1], u[2]);
-        envB[row] = make_float4(ds, r, tau, __int_as_float(l));
+      if (valid) {
+        g.envU[row] = make_float4(s, u[0], u[1], u[2]);
+        g.envB[row] = make_float4(ds, r, tau, __int_as_float(l));
       } else {
-        envB[row] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        g.envB[row] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
       }
     }
-    carry = __shfl_sync(0xffffffffu, m, 31);
+    // moments of this slot
+    const int lk = valid ? l : -2;
+    float v[24];
+    {
+      const float R[4] = {s, s * u[0], s * u[1], s * u[2]};
+      float pw = 1.f;
+#pragma unroll
+      for (int pp = 0; pp < 6; ++pp) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c * 6 + pp] = valid ? pw * R[c] : 0.f;
+        pw *= tau;
+      }
+    }
+    // run structure of the batch: a head starts a new run (the first lane may continue the run
+    // left open by the previous batch)
+    const int lprev_lane = __shfl_up_sync(0xffffffffu, lk, 1);
+    const int lprev = lane == 0 ? carry_l : lprev_lane;
+    const bool head = valid && lk != lprev;
+    const bool seg = valid && (lane == 0 || lk != lprev_lane);  // first lane of its run in this batch
+    const unsigned headmask = __ballot_sync(0xffffffffu, head);
+    const unsigned segmask = __ballot_sync(0xffffffffu, seg);
+    const unsigned validmask = __ballot_sync(0xffffffffu, valid);
+    // segmented sums towards the first lane of each run
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int lo = __shfl_down_sync(0xffffffffu, lk, off);
+      const bool same = lane + off < 32 && lo == lk;
+#pragma unroll
+      for (int e = 0; e < 24; ++e) {
+        const float o = __shfl_down_sync(0xffffffffu, v[e], off);
+        if (same) v[e] += o;
+      }
+    }
+    const bool cont0 = __shfl_sync(0xffffffffu, valid && lk == carry_l, 0);  // lane 0 continues the open run
+    if (lane == 0 && cont0)
+#pragma unroll
+      for (int e = 0; e < 24; ++e) v[e] += carry[e];
+    if (carry_l >= 0 && !cont0 && lane == 0) {  // the open run ended exactly at the batch boundary
+      const long rec = rbase + nruns - 1;
+      g.run_l[rec] = carry_l;
+      uint4* dst = g.run_rec + rec * 4 * PARTS;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float w8[8] = {carry[c * 6], carry[c * 6 + 1], carry[c * 6 + 2], carry[c * 6 + 3], carry[c * 6 + 4],
+                             carry[c * 6 + 5], 0.f, 0.f};
+        store_chunk<NPASS>(reinterpret_cast<unsigned char*>(dst + c * PARTS),
+                           reinterpret_cast<unsigned char*>(dst + c * PARTS + 1), w8);
+      }
+    }
+    // run index of every slot: runs so far + heads up to this lane - 1
+    const int myrun = nruns + __popc(headmask & (0xffffffffu >> (31 - lane))) - 1;
+    if (valid) g.slot_run[row] = myrun;
+    // every run of the batch is complete except the one holding the last valid lane, unless
+    // the list ends in this batch
+    const int lastvalid = validmask ? 31 - __clz(validmask) : -1;
+    const bool ends = lastvalid < 31 || base + 32 >= kb1;
+    const int open = (!ends && lastvalid >= 0) ? 31 - __clz(segmask & (0xffffffffu >> (31 - lastvalid))) : -1;
+    if (seg && lane != open) {
+      const long rec = rbase + myrun;
+      g.run_l[rec] = lk;
+      uint4* dst = g.run_rec + rec * 4 * PARTS;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float w8[8] = {v[c * 6], v[c * 6 + 1], v[c * 6 + 2], v[c * 6 + 3], v[c * 6 + 4], v[c * 6 + 5], 0.f, 0.f};
+        store_chunk<NPASS>(reinterpret_cast<unsigned char*>(dst + c * PARTS),
+                           reinterpret_cast<unsigned char*>(dst + c * PARTS + 1), w8);
+      }
+    }
+    if (open >= 0) {
+      carry_l = __shfl_sync(0xffffffffu, lk, open);
+#pragma unroll
+      for (int e = 0; e < 24; ++e) carry[e] = __shfl_sync(0xffffffffu, v[e], open);
+    } else {
+      carry_l = -1;
+    }
+    nruns += __popc(headmask);
+    if (ends) break;  // warp-uniform: the rest of the block is padding
   }
+  if (lane == 0 && nruns < kb1 - kb0) g.run_l[rbase + nruns] = -1;
   if (__any_sync(0xffffffffu, oor) && lane == 0) atomicOr(g.table_range, 1);
 }
 
 // =============================================================================================
-// Forward: T and D
+// Forward: T and D.  Thread r < 128 owns A row r = (atom r / 4, component r % 4): for every
+// 8-interval block it copies the chunks of its atom's runs in the block from the run records
+// (cp.async, already in operand format) and clears the chunks of empty intervals; the copies of
+// block kb are released to the MMA once they have landed, up to S - 1 blocks later.
 // =============================================================================================
 template <int NPASS, int NPAD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mom_fwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
   constexpr int S = MomStages<NPASS>::value;
+  constexpr int D = S - 1;  // blocks in flight per builder thread
   constexpr int B_BYTES = NPAD * 128;
   constexpr int STAGE = PARTS * (kABlock + B_BYTES);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  unsigned char* wins = smem + S * STAGE;
-  uint64_t* full = reinterpret_cast<uint64_t*>(wins + kFwdWinBytes);
+  int* runl_s = reinterpret_cast<int*>(smem + S * STAGE);  // [32 atoms][nc] run intervals of the tile
+  uint64_t* full = reinterpret_cast<uint64_t*>(runl_s + kAtoms * g.nc);
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
@@ -431,16 +385,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_fence_init();
   }
   if (warp == 4) tmem_alloc(tmem_holder, 128);
-  // thread r < 128 owns accumulator row r = (atom r / 4, component r % 4) in the epilogue and
-  // the conversion of staging row r; as a builder it walks phase `warp` of atom `lane`
   const int r = threadIdx.x;
   const int ae = r >> 2, c = r & 3;
   const int pe = row0 + ae;
   const bool valid_e = warp < 4 && pe < row_end;
-  const int pb = row0 + lane;
-  const bool valid_b = warp < 4 && pb < row_end;
-  const int ib = valid_b ? g.perm[pb] : 0;
-  if (warp == 0) tile_groups(g, pb, ib, valid_b, ghi);
+  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kThreads);
+  __syncthreads();
+  if (warp == 0) tile_groups(g, runl_s, lane, ghi);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -504,77 +455,54 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = done; kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1, g.err);
     }
   } else {
-    // ---- moment builders: warp c builds component c of the 32 atoms (lane = atom), i.e. A
-    //      row (lane, c); each thread walks its atom's whole list and owns its row outright ----
-    const int crow = warp;            // component built by this warp
-    const int arow = lane * 4 + crow;  // A row written by this thread
-    FWindow win;
-    win.R = reinterpret_cast<float*>(wins) + r * 2 * kWinF;
-    win.tl = reinterpret_cast<float2*>(wins + kRows * 2 * kWinF * 4) + r * 2 * kWinF;
-    FWalk w;
-    w.have = false;
-    int cur_t = -1;
+    // ---- operand builders ----
+    int cur_t = -1, ptr = 0, selt = 0;
+    long rbase = 0;
     bool dead = false;  // after a timed-out wait: stop waiting, keep going through the blocks
-    const uint32_t rowoff0 = (uint32_t)((arow >> 3) * 1024 + (arow & 7) * 128);
+    const uint32_t rowoff0 = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
     for (int kb = 0; kb < nkb; ++kb) {
       int t, grp;
       block_of(kb, ghi, g.ntypes, t, grp);
       const int s = kb % S;
+      if (kb >= D) {  // block kb - D: its copies have landed (the D - 1 later groups may still be in flight)
+        cp_async_wait<D - 1>();
+        fence_async_smem();
+        mbar_arrive(&full[(kb - D) % S]);
+      }
       if (kb >= S && !dead && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, g.err)) dead = true;
       if (t != cur_t) {
         cur_t = t;
-        w.have = false;
-        if (valid_b) {
-          fwalk_start(g, pb, crow, win, w, g.sel_off[t], g.sel_off[t + 1]);
-          fwalk_next(g, pb, crow, win, w);
-        }
+        selt = g.sel_off[t + 1] - g.sel_off[t];
+        ptr = 0;
+        rbase = (long)pe * g.nc + g.sel_off[t];
       }
+      const int* myruns = runl_s + ae * g.nc + g.sel_off[t];
       unsigned char* ahi = smem + s * STAGE;
       unsigned char* alo = ahi + kABlock;
-      // runs of equal interval, accumulated in registers; intervals without neighbours get zeros
-      float mu[8];
-      int cur_q = -1;
-      unsigned written = 0;
-      for (;;) {
-        const bool act = w.have && w.l >= 8 * grp;
-        if (!__any_sync(0xffffffffu, act)) break;
-        if (act) {
-          const int q = (w.l - 8 * grp) & 7;
-          if (q != cur_q) {
-            if (cur_q >= 0) {
-              const uint32_t off = rowoff0 + (uint32_t)((cur_q ^ (arow & 7)) << 4);
-              store_chunk<NPASS>(ahi + off, alo + off, mu);
-              written |= 1u << cur_q;
-            }
-#pragma unroll
-            for (int pp = 0; pp < 8; ++pp) mu[pp] = 0.f;
-            cur_q = q;
-          }
-          float pw = w.R;
-#pragma unroll
-          for (int pp = 0; pp < 6; ++pp) {
-            mu[pp] += pw;
-            pw *= w.tau;
-          }
-          fwalk_next(g, pb, crow, win, w);
-        }
+      unsigned covered = 0;
+      while (ptr < selt) {
+        const int l = myruns[ptr];
+        if (l < 8 * grp) break;  // also the end marker -1
+        const int q = (l - 8 * grp) & 7;
+        const uint32_t off = rowoff0 + (uint32_t)((q ^ (r & 7)) << 4);
+        const uint4* src = g.run_rec + ((rbase + ptr) * 4 + c) * PARTS;
+        cp_async16(ahi + off, src);
+        if (PARTS == 2) cp_async16(alo + off, src + 1);
+        covered |= 1u << q;
+        ++ptr;
       }
-      if (cur_q >= 0) {
-        const uint32_t off = rowoff0 + (uint32_t)((cur_q ^ (arow & 7)) << 4);
-        store_chunk<NPASS>(ahi + off, alo + off, mu);
-        written |= 1u << cur_q;
-      }
-      const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (!((written >> q) & 1u)) {
-          const uint32_t off = rowoff0 + (uint32_t)((q ^ (arow & 7)) << 4);
-          store_chunk<NPASS>(ahi + off, alo + off, zero8);
+        if (!((covered >> q) & 1u)) {
+          const uint32_t off = rowoff0 + (uint32_t)((q ^ (r & 7)) << 4);
+          *reinterpret_cast<uint4*>(ahi + off) = make_uint4(0u, 0u, 0u, 0u);
+          if (PARTS == 2) *reinterpret_cast<uint4*>(alo + off) = make_uint4(0u, 0u, 0u, 0u);
         }
-      fence_async_smem();
-      mbar_arrive(&full[s]);
+      cp_async_commit();
     }
-    cp_async_wait0();  // window copies still in flight land before the CTA leaves
+    cp_async_wait0();
+    fence_async_smem();
+    for (int kb = max(0, nkb - D); kb < nkb; ++kb) mbar_arrive(&full[kb % S]);
   }
 
   // ---- epilogue: T = acc / Nc, then D = T T_<^T ----
@@ -754,13 +682,16 @@ __global__ void __launch_bounds__(kRows)
 }
 
 // =============================================================================================
-// Backward: dE/dT -> P -> per-neighbour dE/dr_ij -> forces and per-atom virial
+// Backward, tensor-core part: P = C . dE/dT per 8-interval block (TMEM), written out per run.
+// Thread r < 128 reads accumulator row r = (atom r / 4, component r % 4) and stores, for each
+// run of its atom in the block, the six values of its interval (scaled back by 2^ex / Nc) to the
+// run's P record; the per-slot part of the backward is k_force_mom.
 // =============================================================================================
 template <int NPASS, int NPAD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
-  constexpr int S = MomStages<NPASS>::value;
+  constexpr int S = 3;
   constexpr int A_BYTES = 2 * kABlock;  // K = m in two 64-column blocks
   constexpr int B_KBLK = 64 * 128;      // 64 rows (8 intervals x 8 powers) x 128 B
   constexpr int B_STAGE = PARTS * 2 * B_KBLK;
@@ -770,9 +701,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* As = smem;                      // PARTS x A_BYTES, dE/dT rows (A operand)
   unsigned char* ring = smem + PARTS * A_BYTES;  // B stages
-  float* Ps = reinterpret_cast<float*>(ring + bwd_ring_bytes(NPASS));  // P of one block [atom][c][chunk][8]
-  unsigned char* wins = ring + bwd_ring_bytes(NPASS) + kRowBufBytes;
-  int* ex_s = reinterpret_cast<int*>(wins + kBwdWinBytes);  // [128] power-of-two scale of each dE/dT row
+  int* runl_s = reinterpret_cast<int*>(ring + S * B_STAGE);  // [32 atoms][nc] run intervals of the tile
+  int* ex_s = runl_s + kAtoms * g.nc;                        // [128] power-of-two scale of each row
   uint64_t* bar = reinterpret_cast<uint64_t*>(ex_s + kRows);
   uint64_t* bfull = bar;
   uint64_t* bempty = bar + S;
@@ -802,12 +732,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_fence_init();
   }
   if (warp == 4) tmem_alloc(tmem_holder, 128);
-  const int r = threadIdx.x;  // accumulator row (atom r / 4, component r % 4)
-  const int c = r & 3;
-  const int pb = row0 + lane;  // phase-2 walker: atom `lane`, phase `warp`
-  const bool valid_b = warp < 4 && pb < row_end;
-  const int ib = valid_b ? g.perm[pb] : 0;
-  if (warp == 0) tile_groups(g, pb, ib, valid_b, ghi);
+  const int r = threadIdx.x;
+  const int ae = r >> 2, c = r & 3;
+  const int pe = row0 + ae;
+  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kThreads);
+  __syncthreads();
+  if (warp == 0) tile_groups(g, runl_s, lane, ghi);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -821,9 +751,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_expect_tx(afull, PARTS * A_BYTES + kRows * 4);
       bulk_load(As, g.gta + (long)blockIdx.x * PARTS * A_BYTES, PARTS * A_BYTES, afull);
       bulk_load(ex_s, g.gtx + (long)blockIdx.x * kRows, kRows * 4, afull);
-      bool ok = true;
-      // ---- phase 2: TMA producer and MMA issuer ----
-      ok = mbar_wait(afull, 0, g.err);
+      bool ok = mbar_wait(afull, 0, g.err);
+      // ---- TMA producer and MMA issuer ----
       const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
       auto issue = [&](int ch) {
         int t, grp;
@@ -884,108 +813,126 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int ch = done; ch < issued; ++ch) mbar_wait(&bfull[ch % S], (ch / S) & 1, g.err);
     }
   } else {
-    // ---- the A operand (dE/dT rows, k_mom_gT) and the row scales arrive by bulk copy ----
-    mbar_wait(afull, 0, g.err);
-
-    // ---- phase 2, per 8-interval block: P from TMEM to shared memory, then every warp walks
-    //      its phase of the 32 atoms' neighbours in the block ----
+    mbar_wait(afull, 0, g.err);  // the row scales arrived with the A operand
     const float pscale = ldexpf(g.inv_nc, ex_s[r]);
-    float* prow = Ps + (r >> 2) * kAtomPitch + c * kRowPitch;  // this thread's P row
-    const float* patom = Ps + lane * kAtomPitch;                // the walked atom's four rows
-    Window win;
-    win.e0 = reinterpret_cast<float4*>(wins) + r * 2 * kWin;
-    win.e1 = reinterpret_cast<float4*>(wins) + (kRows + r) * 2 * kWin;
-    win.j = reinterpret_cast<int*>(wins + 2 * kRows * 2 * kWin * 16) + r * 2 * kWin;
-    Walk w;
-    w.have = false;
-    int cur_t = -1;
+    int cur_t = -1, ptr = 0, selt = 0;
+    long rbase = 0;
     bool dead = false;  // after a timed-out wait: stop waiting, keep taking part in the barriers
-    float fi[3] = {0.f, 0.f, 0.f}, vir[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
     for (int ch = 0; ch < nch; ++ch) {
       const int buf = ch & 1;
       if (!dead && !mbar_wait(&accfull[buf], (ch >> 1) & 1, g.err)) dead = true;
       __syncwarp();  // tcgen05.ld is warp-collective
       tc_fence_after();
+      float P[64];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float v[16];
-        tmem_ld16(tb + (uint32_t)(buf * 64 + 16 * q), v);
-#pragma unroll
-        for (int e = 0; e < 16; e += 4)
-          *reinterpret_cast<float4*>(prow + 16 * q + e) =
-              make_float4(v[e] * pscale, v[e + 1] * pscale, v[e + 2] * pscale, v[e + 3] * pscale);
-      }
+      for (int q = 0; q < 4; ++q) tmem_ld16(tb + (uint32_t)(buf * 64 + 16 * q), P + 16 * q);
       tc_fence_before();
       mbar_arrive(&accempty[buf]);
-      bar_sync(1, kRows);  // the whole P block is in shared memory
       int t, grp;
       block_of(ch, ghi, g.ntypes, t, grp);
       if (t != cur_t) {
         cur_t = t;
-        w.have = false;
-        if (valid_b) {
-          walk_start(g, pb, ib, win, w, g.sel_off[t] + warp, g.sel_off[t + 1]);
-          walk_next(g, pb, ib, win, w);
-        }
+        selt = g.sel_off[t + 1] - g.sel_off[t];
+        ptr = 0;
+        rbase = (long)pe * g.nc + g.sel_off[t];
       }
-      for (;;) {
-        const bool act = w.have && w.l >= 8 * grp;
-        if (!__any_sync(0xffffffffu, act)) break;
-        if (act) {
-          const int q = w.l - 8 * grp;
-          const float tau = w.tau;
-          float gR[4], dg[4];
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const float4* p4 = reinterpret_cast<const float4*>(patom + cc * kRowPitch + (q & 7) * 8);
-            const float4 x = p4[0], y = p4[1];
-            gR[cc] = x.x + tau * (x.y + tau * (x.z + tau * (x.w + tau * (y.x + tau * y.y))));
-            dg[cc] = x.y + tau * (2.f * x.z + tau * (3.f * x.w + tau * (4.f * y.x + tau * (5.f * y.y))));
-          }
-          const float s = w.e0.x, u0 = w.e0.y, u1 = w.e0.z, u2 = w.e0.w, ds = w.e1.x, rr = w.e1.y;
-          const float invd = w.l < g.n1 ? g.inv1 : g.inv2;
-          const float gs = s * (dg[0] + u0 * dg[1] + u1 * dg[2] + u2 * dg[3]) * invd;
-          const float gvu = gR[1] * u0 + gR[2] * u1 + gR[3] * u2;
-          const float A_ = ds * (gs + gR[0] + gvu), B_ = s / rr;
-          const float gd[3] = {A_ * u0 + B_ * (gR[1] - gvu * u0), A_ * u1 + B_ * (gR[2] - gvu * u1),
-                               A_ * u2 + B_ * (gR[3] - gvu * u2)};
-          const float dv[3] = {rr * u0, rr * u1, rr * u2};
-#pragma unroll
-          for (int aa = 0; aa < 3; ++aa) {
-            atomicAdd(g.force + 3 * w.j + aa, widen(-gd[aa]));
-            fi[aa] += gd[aa];
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= gd[aa] * dv[bb];
-          }
-          walk_next(g, pb, ib, win, w);
+      const int* myruns = runl_s + ae * g.nc + g.sel_off[t];
+      while (ptr < selt) {
+        const int l = myruns[ptr];
+        if (l < 8 * grp) break;  // also the end marker -1
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        switch ((l - 8 * grp) & 7) {
+#define DPGB_SEL(Q)                                              \
+  case Q:                                                        \
+    _Pragma("unroll") for (int e = 0; e < 6; ++e) v[e] = P[8 * Q + e] * pscale; \
+    break;
+          DPGB_SEL(0)
+          DPGB_SEL(1)
+          DPGB_SEL(2)
+          DPGB_SEL(3)
+          DPGB_SEL(4)
+          DPGB_SEL(5)
+          DPGB_SEL(6)
+          DPGB_SEL(7)
+#undef DPGB_SEL
         }
+        float4* dst = g.run_P + ((rbase + ptr) * 4 + c) * 2;
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], 0.f, 0.f);
+        ++ptr;
       }
-      bar_sync(1, kRows);  // every walker is done with this P block
-    }
-    cp_async_wait0();
-    // force on i and the atom's virial: the four phases' partial sums meet in shared memory
-    float* red = Ps;  // [4 phases][32 atoms][12]
-#pragma unroll
-    for (int e = 0; e < 3; ++e) red[(warp * kAtoms + lane) * 12 + e] = fi[e];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) red[(warp * kAtoms + lane) * 12 + 3 + e] = vir[e];
-    bar_sync(1, kRows);
-    if (warp == 0 && valid_b) {
-      float tot[12];
-#pragma unroll
-      for (int e = 0; e < 12; ++e)
-        tot[e] = red[lane * 12 + e] + red[(kAtoms + lane) * 12 + e] + red[(2 * kAtoms + lane) * 12 + e] +
-                 red[(3 * kAtoms + lane) * 12 + e];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) atomicAdd(g.force + 3 * ib + e, widen(tot[e]));
-#pragma unroll
-      for (int e = 0; e < 9; ++e) g.avir[9L * ib + e] = widen(tot[3 + e]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 4) tmem_dealloc(tmem, 128);
+}
+
+// =============================================================================================
+// Backward, per-slot part: dE/dr_ij of every listed pair from its run's P record, the force
+// scatter (FP64 atomics on the neighbours, F_i accumulated per atom) and the per-atom virial.
+// One warp per atom, lanes over its slots:
+//   dE/dR_c = sum_p tau^p P_{p,c},  dE/ds = sum_c R_c sum_p p tau^{p-1} P_{p,c} / Delta_l
+//   dE/dr_ij = ds/dr (dE/ds + dE/dR_0 + g.u) u + (s / r) (g - (g.u) u),  g = dE/dR_{1..3}
+// =============================================================================================
+__global__ void __launch_bounds__(256)
+    k_force_mom(PathConst pc, MomArgs g) {
+  const int p = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= pc.natoms) return;  // warp-uniform
+  const int i = g.perm[p];
+  float fi[3] = {0.f, 0.f, 0.f}, vir[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int t = 0; t < pc.ntypes; ++t) {
+    const int kb0 = g.sel_off[t], kb1 = g.sel_off[t + 1];
+    const long rbase = (long)p * pc.nc + kb0;
+    for (int base = kb0; base < kb1; base += 32) {
+      const int k = base + lane;
+      const int j = k < kb1 ? g.nl_j[(long)i * pc.nc + k] : -1;
+      if (!__any_sync(0xffffffffu, j >= 0)) break;  // real neighbours fill the front of the block
+      if (j < 0) continue;
+      const long row = (long)p * pc.nc + k;
+      const float4 e0 = g.envU[row], e1 = g.envB[row];
+      const float4* P4 = g.run_P + (rbase + g.slot_run[row]) * 8;
+      const float tau = e1.z;
+      const int l = __float_as_int(e1.w);
+      float gR[4], dg[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float4 x = P4[2 * c], y = P4[2 * c + 1];
+        gR[c] = x.x + tau * (x.y + tau * (x.z + tau * (x.w + tau * (y.x + tau * y.y))));
+        dg[c] = x.y + tau * (2.f * x.z + tau * (3.f * x.w + tau * (4.f * y.x + tau * (5.f * y.y))));
+      }
+      const float s = e0.x, u0 = e0.y, u1 = e0.z, u2 = e0.w, ds = e1.x, rr = e1.y;
+      const float invd = l < g.n1 ? g.inv1 : g.inv2;
+      const float gs = s * (dg[0] + u0 * dg[1] + u1 * dg[2] + u2 * dg[3]) * invd;
+      const float gvu = gR[1] * u0 + gR[2] * u1 + gR[3] * u2;
+      const float A_ = ds * (gs + gR[0] + gvu), B_ = s / rr;
+      const float gd[3] = {A_ * u0 + B_ * (gR[1] - gvu * u0), A_ * u1 + B_ * (gR[2] - gvu * u1),
+                           A_ * u2 + B_ * (gR[3] - gvu * u2)};
+      const float dv[3] = {rr * u0, rr * u1, rr * u2};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        atomicAdd(g.force + 3 * j + a, widen(-gd[a]));
+        fi[a] += gd[a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) vir[a * 3 + b] -= gd[a] * dv[b];
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fi[a] += __shfl_xor_sync(0xffffffffu, fi[a], off);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) atomicAdd(g.force + 3 * i + a, widen(fi[a]));
+#pragma unroll
+    for (int q = 0; q < 9; ++q) g.avir[9L * i + q] = widen(vir[q]);
+  }
 }
 
 // Tables of the moment contraction from the quintic coefficients (FP64, [net][l][m][8]).
@@ -1030,14 +977,15 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
   }
 }
 
-size_t fwd_smem(int npass, int npad) {
-  const int S = 2;
-  return (size_t)fwd_ring_bytes(npass, npad) + kFwdWinBytes + (2 * S + 1) * 8 + 4 +
+size_t fwd_smem(int npass, int npad, int nc) {
+  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 4 : 2;
+  return (size_t)S * parts * (kABlock + npad * 128) + (size_t)kAtoms * nc * 4 + (2 * S + 1) * 8 + 4 +
          4 * DP_MAX_TYPES + 1024 + 64;
 }
-size_t bwd_smem(int npass, int npad, int M, int A) {
-  const int parts = npass == 1 ? 1 : 2, S = 2;
-  return (size_t)parts * 2 * kABlock + bwd_region(npass) + (2 * S + 5) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
+size_t bwd_smem(int npass, int nc) {
+  const int parts = npass == 1 ? 1 : 2;
+  return (size_t)parts * 2 * kABlock + 3 * (size_t)parts * 2 * 64 * 128 + (size_t)kAtoms * nc * 4 + kRows * 4 +
+         11 * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
 }
 
 template <int NPASS, int NPAD>
@@ -1046,11 +994,11 @@ int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, int which, cud
   if (which == 1) {
     k_mom_gT<NPASS, NPAD><<<dim3(tiles, kAtoms / kGroupAtoms), kRows, 0, st>>>(g);
   } else if (which == 0) {
-    const size_t sm = fwd_smem(NPASS, NPAD);
+    const size_t sm = fwd_smem(NPASS, NPAD, g.nc);
     DP_CUDA_TRY(cudaFuncSetAttribute(k_mom_fwd<NPASS, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_mom_fwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[0], maps[1], g);
   } else {
-    const size_t sm = bwd_smem(NPASS, NPAD, g.M, g.A);
+    const size_t sm = bwd_smem(NPASS, g.nc);
     DP_CUDA_TRY(cudaFuncSetAttribute(k_mom_bwd<NPASS, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_mom_bwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[2], maps[3], g);
   }
@@ -1081,8 +1029,11 @@ int mom_npad_of(int M) {
 }
 
 bool mom_supported(const DeviceModel& m) {
+  int nc = 0;
+  for (int t = 0; t < m.cfg.ntypes; ++t) nc += m.cfg.sel[t];
+  // the run lists of a tile's 32 atoms stay in shared memory beside the operand rings
   return m.compressed && (m.precision == DP_PREC_FP32 || m.precision == DP_PREC_BF16) && mom_npad_of(m.M) > 0 &&
-         m.A <= 16 && (m.M * m.A) % 4 == 0;
+         m.A <= 16 && (m.M * m.A) % 4 == 0 && nc <= 512;
 }
 
 int build_mom_tables(DeviceModel& m) {
@@ -1126,9 +1077,14 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const bool bf16 = m.mom_npass == 1;
   float* Tm = ar.get<float>(N * M * 4);
   void* D = bf16 ? (void*)ar.get<__nv_bfloat16>(N * M * A) : (void*)ar.get<float>(N * M * A);
-  float4* envR = ar.get<float4>(N * pc.nc);
-  float4* envU = ar.get<float4>(N * pc.nc);
-  float4* envB = ar.get<float4>(N * pc.nc);
+  const long slots = N * pc.nc;
+  const int parts = bf16 ? 1 : 2;
+  float4* envU = ar.get<float4>(slots);
+  float4* envB = ar.get<float4>(slots);
+  int* slot_run = ar.get<int>(slots);
+  int* run_l = ar.get<int>(slots);
+  // run moments (forward) and run P (backward) share one buffer: the moments are dead by then
+  void* runs = ar.get<float4>(slots * 8 > slots * 4 * parts ? slots * 8 : slots * 4 * parts);
   const long max_tiles = (N + kAtoms - 1) / kAtoms + pc.ntypes;  // every type's last tile may be short
   unsigned char* gta = ar.get<unsigned char>(max_tiles * (bf16 ? 1 : 2) * 2 * kABlock);
   int* gtx = ar.get<int>(max_tiles * kRows);
@@ -1168,9 +1124,12 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const int tiles = g.tile_start[pc.ntypes];
   g.perm = io.perm;
   g.nl_j = io.nl_j;
-  g.envR = envR;
   g.envU = envU;
   g.envB = envB;
+  g.slot_run = slot_run;
+  g.run_l = run_l;
+  g.run_rec = reinterpret_cast<uint4*>(runs);
+  g.run_P = reinterpret_cast<float4*>(runs);
   g.Tm = Tm;
   g.D = D;
   g.d_bf16 = bf16 ? 1 : 0;
@@ -1184,7 +1143,10 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   {
     ProfScope _ps(io.prof, "env", st);
     const long tasks = N * pc.ntypes;  // one warp per (atom, neighbour type)
-    k_env_mom<<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code, envR, envU, envB);
+    if (bf16)
+      k_env_mom<1><<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code);
+    else
+      k_env_mom<3><<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code);
     DP_CUDA_TRY(cudaGetLastError());
   }
   if (tiles > 0) {
@@ -1205,9 +1167,14 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
       rc = bf16 ? launch_mom_np<1>(m, g, tiles, 1, st) : launch_mom_np<3>(m, g, tiles, 1, st);
       if (rc != DP_OK) return rc;
     }
-    ProfScope _ps(io.prof, "mom_bwd", st);
-    rc = bf16 ? launch_mom_np<1>(m, g, tiles, 2, st) : launch_mom_np<3>(m, g, tiles, 2, st);
-    if (rc != DP_OK) return rc;
+    {
+      ProfScope _ps(io.prof, "mom_bwd", st);
+      rc = bf16 ? launch_mom_np<1>(m, g, tiles, 2, st) : launch_mom_np<3>(m, g, tiles, 2, st);
+      if (rc != DP_OK) return rc;
+    }
+    ProfScope _ps(io.prof, "mom_force", st);
+    k_force_mom<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(pc, g);
+    DP_CUDA_TRY(cudaGetLastError());
   }
   return DP_OK;
 }
