@@ -24,11 +24,14 @@ struct NlGeom {
   double inv[9];     // inverse of h (periodic)
   double origin[3];  // open boundary: fractional = (x - origin) / ext
   double ext[3];
-  float hf[9];       // float cell rows used by the FP32 prefilter (diag(ext) when open)
+  float hc[9];       // edge vectors of one cell, h_e / ncell_e (diag(ext / ncell) when open), FP32
   int ncell[3];
   int K[3];          // virtual-cell search half-width per axis
   double rc2;        // r_c^2 (exact membership test)
-  float rc2_loose;   // (r_c + 1e-3)^2 (FP32 prefilter)
+  // FP32 screening of the cell-local distance (error below eps in r^2, bounded on the host):
+  float rc2_in;      // r2_32 < rc2_in: certainly inside (rc2_in <= rc2 - eps)
+  float rc2_out;     // r2_32 > rc2_out: certainly outside (rc2_out >= rc2 + eps)
+  float tie_w;       // FP32 keys further apart than tie_w are ordered as their FP64 values
   int cap;           // candidate buffer per centre atom (rounded up to 128..DP_MAX_CANDIDATES)
 };
 
@@ -148,9 +151,11 @@ struct NlLaunch {
   const int* atom_frame;  // device [natoms] frame of each atom, or null (one frame)
   const int* cell_off;    // device [frames] first cell of each frame, or null (one frame)
 };
-cudaError_t launch_nlist_build(const NlLaunch& L, const double* coord, const int* type, int* cell_count,
-                               int* cell_start, int* cell_cursor, int* cell_atoms, int* atom_cell, int* atom_img,
-                               float4* atom_wf, int* nl_j, int* nl_code, int* counts, DevStatus* status,
+// Cell arrays are indexed by (type, cell): cell_count, cell_cursor [ntypes * ncells_total],
+// cell_start [ntypes * ncells_total + 1]; atom_key [natoms]; sorted_l, sorted_m [natoms].
+cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
+                               int* cell_count, int* cell_start, int* cell_cursor, int* atom_key, float4* sorted_l,
+                               int4* sorted_m, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st);
 cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, int* bad_type,
                              cudaStream_t st);

@@ -170,8 +170,9 @@ struct Bufs {
   double* coord;
   int* type;
   int *nl_j, *nl_code, *counts;
-  int *cell_count, *cell_start, *cell_cursor, *cell_atoms, *atom_cell, *atom_img;
-  float4* atom_wf;
+  int *cell_count, *cell_start, *cell_cursor, *atom_key;
+  float4* sorted_l;
+  int4* sorted_m;
   unsigned char* ftab;
   int* atom_frame;
   double* tshift;
@@ -189,13 +190,13 @@ void carve(Arena& ar, const DeviceModel& m, const FrameTables& T, bool own_nlist
     b.nl_j = ar.get<int>(N * nc);
     b.nl_code = ar.get<int>(N * nc);
     b.counts = ar.get<int>(N * m.cfg.ntypes);
-    b.cell_count = ar.get<int>(T.ncells);
-    b.cell_start = ar.get<int>(T.ncells + 1);
-    b.cell_cursor = ar.get<int>(T.ncells);
-    b.cell_atoms = ar.get<int>(N);
-    b.atom_cell = ar.get<int>(N);
-    b.atom_img = ar.get<int>(3 * N);
-    b.atom_wf = ar.get<float4>(N);
+    const long nkeys = (long)T.ncells * m.cfg.ntypes;
+    b.cell_count = ar.get<int>(nkeys);
+    b.cell_start = ar.get<int>(nkeys + 1);
+    b.cell_cursor = ar.get<int>(nkeys);
+    b.atom_key = ar.get<int>(N);
+    b.sorted_l = ar.get<float4>(N);
+    b.sorted_m = ar.get<int4>(N);
   }
   b.ftab = ar.get<unsigned char>((long)T.bytes);
   if (T.F > 1) b.atom_frame = ar.get<int>(N);
@@ -344,8 +345,8 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   if (own_nlist) {
     NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr};
     ProfScope _ps(&md->prof, "nlist", st, 4);
-    DP_CUDA_TRY(launch_nlist_build(L, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor, b.cell_atoms,
-                                   b.atom_cell, b.atom_img, b.atom_wf, b.nl_j, b.nl_code, b.counts, md->status, st));
+    DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
+                                   b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, st));
   }
   {
     ProfScope _ps(&md->prof, "type_perm", st);
@@ -513,9 +514,9 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
   {
     NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr};
     ProfScope _ps(&md->prof, "nlist", st, 4);
-    DP_CUDA_TRY(launch_nlist_build(L, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor, b.cell_atoms,
-                                   b.atom_cell, b.atom_img, b.atom_wf, nl->nl_j, nl->nl_code, nl->counts, md->status,
-                                   st));
+    DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
+                                   b.atom_key, b.sorted_l, b.sorted_m, nl->nl_j, nl->nl_code, nl->counts,
+                                   md->status, st));
   }
   rc = read_status(md, st, n_overflow);
   if (rc != DP_OK && rc != DP_E_SEL_OVERFLOW) {

@@ -1,14 +1,19 @@
 // Cell-list neighbour search with a fixed per-type sel (Sec. II.A.1 per-type blocks padded
 // to N_c^{a_j}; Sec. III.B.1 ordering by type, distance, index).
 //
-// GB300 design: atoms are binned into cells at least r_c wide (fractional coordinates in
-// FP64, any rounding is harmless because binning only bounds the search).  One warp owns
-// one centre atom: it walks the (2K+1)^3 virtual cells around it, tests each candidate
-// first with an FP32 distance in wrapped fractional coordinates (loose cutoff), and only
-// survivors pay for the exact FP64 displacement that defines membership and order.  The
-// accepted entries are kept in shared memory and ranked within their type by the exact
-// total order (r^2 bits, j, image code); rank < sel[t] gives the slot directly, so no
-// sort pass and no global scratch beyond the cell list is needed.
+// GB300 design.  Atoms are binned into cells at least r_c wide and sorted by (type, cell), so
+// that the atoms of one type in one cell are contiguous.  Each sorted entry carries the
+// atom's position relative to the corner of its cell in FP32 (cell-local coordinates, small
+// numbers, so FP32 keeps them to ~1e-6 A) and its index.  One warp owns one centre atom and,
+// for each neighbour type, streams the concatenated candidates of the (2K+1)^3 surrounding
+// cells in full 32-lane batches.  The displacement is l_j - l_i + (cell offset) in FP32, with
+// an error bound on r^2 computed on the host from the cell geometry; candidates that the bound
+// cannot place on one side of r_c (a vanishing fraction) take the exact FP64 test that defines
+// membership.  The accepted entries of each type are ranked under the exact total order
+// (r^2, j, image code): FP32 keys further apart than twice the bound decide directly, and only
+// pairs inside that window compare their exact FP64 r^2.  rank < sel[t] gives the slot, so no
+// sort pass and no global scratch beyond the cell arrays is needed.
+#include <algorithm>
 #include <cstdio>
 
 #include "dp_internal.cuh"
@@ -17,8 +22,7 @@ namespace dpgb {
 
 namespace {
 
-constexpr int kWarpsPerBlock = 4;
-constexpr int kQueue = 64;  // prefilter survivors waiting for the exact test (per warp)
+constexpr int kNlWarps = 4;  // centre atoms (warps) per block
 
 __device__ __forceinline__ int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 
@@ -51,17 +55,15 @@ __global__ void k_bbox(const double* __restrict__ coord, int n, double* __restri
   }
 }
 
-__global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame,
-                      const int* __restrict__ cell_off, int natoms, const double* __restrict__ coord,
-                      int* __restrict__ cell_count, int* __restrict__ atom_cell, int* __restrict__ atom_img,
-                      float4* __restrict__ atom_wf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= natoms) return;
-  const int fr = atom_frame ? atom_frame[i] : 0;
-  const NlGeom& g = G[fr];
-  double x[3] = {coord[3 * i], coord[3 * i + 1], coord[3 * i + 2]};
+// Cell of an atom, its periodic image index m (x = wrapped + m h) and its position relative to
+// the corner of its cell, all from FP64 fractional coordinates.
+struct Binned {
   int c[3], m[3];
-  float w[3];
+  double l[3];
+};
+__device__ __forceinline__ Binned bin_atom(const NlGeom& g, const double* x) {
+  Binned b;
+  double s[3];
   for (int d = 0; d < 3; ++d) {
     double f;
     if (g.periodic)
@@ -72,21 +74,42 @@ __global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom
     double wd = f - fl;
     if (g.periodic && wd >= 1.0) { wd = 0.0; fl += 1.0; }
     if (wd < 0.0) wd = 0.0;
-    m[d] = (int)fl;
+    b.m[d] = (int)fl;
     int cd = (int)(wd * g.ncell[d]);
-    c[d] = cd < 0 ? 0 : (cd >= g.ncell[d] ? g.ncell[d] - 1 : cd);
-    w[d] = (float)wd;
+    b.c[d] = cd < 0 ? 0 : (cd >= g.ncell[d] ? g.ncell[d] - 1 : cd);
+    s[d] = (double)b.m[d] + (double)b.c[d] / (double)g.ncell[d];
   }
-  int flat = (cell_off ? cell_off[fr] : 0) + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
-  atom_cell[i] = flat;
-  atom_img[3 * i] = m[0];
-  atom_img[3 * i + 1] = m[1];
-  atom_img[3 * i + 2] = m[2];
-  atom_wf[i] = make_float4(w[0], w[1], w[2], 0.f);
-  atomicAdd(cell_count + flat, 1);
+  for (int d = 0; d < 3; ++d) {
+    if (g.periodic)
+      b.l[d] = x[d] - (s[0] * g.h[0 * 3 + d] + s[1] * g.h[1 * 3 + d] + s[2] * g.h[2 * 3 + d]);
+    else
+      b.l[d] = x[d] - (g.origin[d] + s[d] * g.ext[d]);
+  }
+  return b;
 }
 
-// Exclusive scan of n ints by one block (n is the number of cells: small).
+// Key (type, cell) of every atom and the count of each key.
+__global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame,
+                      const int* __restrict__ cell_off, int natoms, int ncells_total, int ntypes,
+                      const double* __restrict__ coord, const int* __restrict__ type, int* __restrict__ cell_count,
+                      int* __restrict__ atom_key, DevStatus* __restrict__ st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= natoms) return;
+  const int fr = atom_frame ? atom_frame[i] : 0;
+  const NlGeom& g = G[fr];
+  const Binned b = bin_atom(g, coord + 3 * i);
+  const int t = type[i];
+  if (t < 0 || t >= ntypes) {  // reported; the atom takes part in no list
+    atom_key[i] = -1;
+    atomicExch(&st->bad_type, 1);
+    return;
+  }
+  const int key = t * ncells_total + (cell_off ? cell_off[fr] : 0) + (b.c[0] * g.ncell[1] + b.c[1]) * g.ncell[2] + b.c[2];
+  atom_key[i] = key;
+  atomicAdd(cell_count + key, 1);
+}
+
+// Exclusive scan of n ints by one block.
 __global__ void k_scan_excl(const int* __restrict__ in, int n, int* __restrict__ out, int* __restrict__ out2) {
   __shared__ int wsum[32];
   __shared__ int carry;
@@ -124,115 +147,82 @@ __global__ void k_scan_excl(const int* __restrict__ in, int n, int* __restrict__
   if (threadIdx.x == 0) out[n] = carry;
 }
 
-__global__ void k_fill(int natoms, const int* __restrict__ atom_cell, int* __restrict__ cursor,
-                       int* __restrict__ cell_atoms) {
+// Sorted entries: cell-local position (FP32) with the atom index, and the image index m.
+__global__ void k_fill(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, int natoms,
+                       const double* __restrict__ coord, const int* __restrict__ atom_key, int* __restrict__ cursor,
+                       float4* __restrict__ sorted_l, int4* __restrict__ sorted_m) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= natoms) return;
-  int pos = atomicAdd(cursor + atom_cell[i], 1);
-  cell_atoms[pos] = i;
+  const int key = atom_key[i];
+  if (key < 0) return;
+  const Binned b = bin_atom(G[atom_frame ? atom_frame[i] : 0], coord + 3 * i);
+  const int pos = atomicAdd(cursor + key, 1);
+  sorted_l[pos] = make_float4((float)b.l[0], (float)b.l[1], (float)b.l[2], __int_as_float(i));
+  sorted_m[pos] = make_int4(b.m[0], b.m[1], b.m[2], key);
 }
 
-struct KeyLess {
-  __device__ static bool less(unsigned long long ra, int ja, int ca, unsigned long long rb, int jb, int cb) {
-    if (ra != rb) return ra < rb;
-    if (ja != jb) return ja < jb;
-    return (unsigned)ca < (unsigned)cb;
-  }
+// Exact order of two accepted neighbours: r^2 (FP64), then j, then the image code.
+__device__ __forceinline__ bool key_less(double ra, int ja, int ca, double rb, int jb, int cb) {
+  if (ra != rb) return ra < rb;
+  if (ja != jb) return ja < jb;
+  return (unsigned)ca < (unsigned)cb;
+}
+
+// One surrounding cell of the centre's cell, as staged for the batch walk.
+struct NbCell {
+  float o0, o1, o2;  // FP32 offset of the cell's corner from the centre cell's corner (image included)
+  int beg;           // first sorted entry of the cell (this type)
+  int pex;           // position of that entry in the concatenated candidate stream
+  int w0, w1, w2;    // periodic wrap of the cell
 };
 
 template <int CAP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kNlWarps * 32)
     k_nlist(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, const int* __restrict__ cell_off,
-            int natoms, const double* __restrict__ coord, const int* __restrict__ type,
-            const int* __restrict__ cell_start, const int* __restrict__ cell_atoms, const int* __restrict__ atom_cell,
-            const int* __restrict__ atom_img, const float4* __restrict__ atom_wf, int* __restrict__ nl_j,
+            const int* __restrict__ n_sorted, int ncells_total, const double* __restrict__ coord, const int* __restrict__ cell_start,
+            const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m, int* __restrict__ nl_j,
             int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long* k_r2 = reinterpret_cast<unsigned long long*>(smem) + (size_t)warp * CAP;
-  int* k_j = reinterpret_cast<int*>(smem + (size_t)kWarpsPerBlock * CAP * 8) + (size_t)warp * CAP;
-  int* k_code = reinterpret_cast<int*>(smem + (size_t)kWarpsPerBlock * CAP * 12) + (size_t)warp * CAP;
-  unsigned char* k_t = smem + (size_t)kWarpsPerBlock * CAP * 16 + (size_t)warp * CAP;
+  unsigned char* wb = smem + (size_t)warp * (CAP * 12 + 32 * sizeof(NbCell));
+  float* e_key = reinterpret_cast<float*>(wb);      // FP32 r^2 of each accepted entry
+  int* e_j = reinterpret_cast<int*>(wb + CAP * 4);  // neighbour index
+  int* e_code = reinterpret_cast<int*>(wb + CAP * 8);  // packed image shift
+  NbCell* cells = reinterpret_cast<NbCell*>(wb + CAP * 12);
 
-  const int w = blockIdx.x * kWarpsPerBlock + warp;
-  if (w >= natoms) return;  // warp-uniform
-  // consecutive warps take atoms of the same cell, so their candidates share the L1 cache
-  const int i = cell_atoms[w];
+  const int w = blockIdx.x * kNlWarps + warp;
+  if (w >= *n_sorted) return;  // warp-uniform; atoms of an invalid type were left out
+  // warps take centre atoms in sorted (type, cell) order: neighbouring warps share candidates
+  const float4 li = sorted_l[w];
+  const int4 mi = sorted_m[w];
+  const int i = __float_as_int(li.w);
   const int fr = atom_frame ? atom_frame[i] : 0;
   const NlGeom& g = G[fr];
   const int coff = cell_off ? cell_off[fr] : 0;
-
-  const double xi[3] = {coord[3 * i], coord[3 * i + 1], coord[3 * i + 2]};
-  const int mi0 = atom_img[3 * i], mi1 = atom_img[3 * i + 1], mi2 = atom_img[3 * i + 2];
-  const float4 wi = atom_wf[i];
-  const int ci = atom_cell[i] - coff;
+  const int ci = mi.w % ncells_total - coff;
   const int c2 = ci % g.ncell[2];
   const int c1 = (ci / g.ncell[2]) % g.ncell[1];
   const int c0 = ci / (g.ncell[2] * g.ncell[1]);
+  const int n0c = 2 * g.K[0] + 1, n1c = 2 * g.K[1] + 1, n2c = 2 * g.K[2] + 1;
+  const int noff = n0c * n1c * n2c;
+  const double* xi = coord + 3 * i;
+
   int cnt = 0;
   bool bad_shift = false;
-  // survivors of the FP32 prefilter wait in a per-warp queue, so the exact FP64 test always
-  // runs on full warps (GB300's FP64 pipe is narrow)
-  int* q_j = reinterpret_cast<int*>(smem + (size_t)kWarpsPerBlock * CAP * 17) + (size_t)warp * 2 * kQueue;
-  int* q_c = q_j + kQueue;
-  int qn = 0;
-  auto drain = [&](int take) {
-    bool acc = false;
-    unsigned long long r2bits = 0ull;
-    int j = -1, code = 0;
-    if (lane < take) {
-      j = q_j[lane];
-      code = q_c[lane];
-      int n0, n1, n2;
-      unpack_shift(code, n0, n1, n2);
-      const double* xj = coord + 3 * j;
-      double dx, dy, dz;
-      if ((n0 | n1 | n2) == 0) {  // same image: (x_j + 0) - x_i needs no shift term
-        dx = __dsub_rn(xj[0], xi[0]);
-        dy = __dsub_rn(xj[1], xi[1]);
-        dz = __dsub_rn(xj[2], xi[2]);
-      } else {
-        pair_disp_exact(xi, xj, n0, n1, n2, g.h, g.periodic, dx, dy, dz);
-      }
-      const double r2 = norm2_exact(dx, dy, dz);
-      if (r2 < g.rc2) {
-        acc = true;
-        r2bits = (unsigned long long)__double_as_longlong(r2);
-      }
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, acc);
-    if (acc) {
-      const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-      if (pos < CAP) {
-        k_r2[pos] = r2bits;
-        k_j[pos] = j;
-        k_code[pos] = code;
-        k_t[pos] = (unsigned char)type[j];
-      }
-    }
-    cnt += __popc(mask);
-    // move the entries beyond the first `take` to the front of the queue
-    __syncwarp();
-    const int rest = qn - take;
-    int mj = 0, mc = 0;
-    if (lane < rest) {
-      mj = q_j[take + lane];
-      mc = q_c[take + lane];
-    }
-    __syncwarp();
-    if (lane < rest) {
-      q_j[lane] = mj;
-      q_c[lane] = mc;
-    }
-    __syncwarp();
-    qn = rest;
-  };
-
-  for (int d0 = -g.K[0]; d0 <= g.K[0]; ++d0)
-    for (int d1 = -g.K[1]; d1 <= g.K[1]; ++d1)
-      for (int d2 = -g.K[2]; d2 <= g.K[2]; ++d2) {
+  for (int tj = 0; tj < g.ntypes; ++tj) {
+    const int gs = cnt;  // this type's entries start here
+    const int kbase = tj * ncells_total + coff;
+    for (int o0 = 0; o0 < noff; o0 += 32) {
+      // ---- the chunk's surrounding cells: one per lane ----
+      const int o = o0 + lane;
+      int num = 0, beg = 0, W0 = 0, W1 = 0, W2 = 0;
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+      if (o < noff) {
+        const int d0 = o / (n1c * n2c) - g.K[0];
+        const int d1 = (o / n2c) % n1c - g.K[1];
+        const int d2 = o % n2c - g.K[2];
         int v0 = c0 + d0, v1 = c1 + d1, v2 = c2 + d2;
-        int W0 = 0, W1 = 0, W2 = 0;
+        bool inside = true;
         if (g.periodic) {
           W0 = floordiv(v0, g.ncell[0]);
           W1 = floordiv(v1, g.ncell[1]);
@@ -240,92 +230,140 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           v0 -= W0 * g.ncell[0];
           v1 -= W1 * g.ncell[1];
           v2 -= W2 * g.ncell[2];
-        } else if (v0 < 0 || v1 < 0 || v2 < 0 || v0 >= g.ncell[0] || v1 >= g.ncell[1] || v2 >= g.ncell[2]) {
-          continue;
+        } else {
+          inside = v0 >= 0 && v1 >= 0 && v2 >= 0 && v0 < g.ncell[0] && v1 < g.ncell[1] && v2 < g.ncell[2];
         }
-        const int cell = coff + (v0 * g.ncell[1] + v1) * g.ncell[2] + v2;
-        const int beg = cell_start[cell], end = cell_start[cell + 1];
-        for (int base = beg; base < end; base += 32) {
-          const int idx = base + lane;
-          bool pass = false;
-          int j = -1, code = 0;
-          if (idx < end) {
-            j = cell_atoms[idx];
-            const float4 wj = atom_wf[j];
-            // FP32 prefilter in wrapped fractional coordinates
-            float f0 = (wj.x + (float)W0) - wi.x, f1 = (wj.y + (float)W1) - wi.y, f2 = (wj.z + (float)W2) - wi.z;
-            float e0, e1, e2;
-            if (g.periodic) {
-              e0 = f0 * g.hf[0] + f1 * g.hf[3] + f2 * g.hf[6];
-              e1 = f0 * g.hf[1] + f1 * g.hf[4] + f2 * g.hf[7];
-              e2 = f0 * g.hf[2] + f1 * g.hf[5] + f2 * g.hf[8];
-            } else {
-              e0 = f0 * g.hf[0];
-              e1 = f1 * g.hf[4];
-              e2 = f2 * g.hf[8];
-            }
-            if (e0 * e0 + e1 * e1 + e2 * e2 < g.rc2_loose) {
-              int n0 = 0, n1 = 0, n2 = 0;
-              if (g.periodic) {
-                n0 = W0 - atom_img[3 * j] + mi0;
-                n1 = W1 - atom_img[3 * j + 1] + mi1;
-                n2 = W2 - atom_img[3 * j + 2] + mi2;
+        if (inside) {
+          const int key = kbase + (v0 * g.ncell[1] + v1) * g.ncell[2] + v2;
+          beg = cell_start[key];
+          num = cell_start[key + 1] - beg;
+        }
+        const float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
+        f0 = fmaf(e2, g.hc[6], fmaf(e1, g.hc[3], e0 * g.hc[0]));
+        f1 = fmaf(e2, g.hc[7], fmaf(e1, g.hc[4], e0 * g.hc[1]));
+        f2 = fmaf(e2, g.hc[8], fmaf(e1, g.hc[5], e0 * g.hc[2]));
+      }
+      int incl = num;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += x;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const bool nonempty = num > 0;
+      const unsigned nemask = __ballot_sync(0xffffffffu, nonempty);
+      __syncwarp();
+      if (nonempty) {
+        NbCell& c = cells[__popc(nemask & ((1u << lane) - 1u))];
+        c.o0 = f0;
+        c.o1 = f1;
+        c.o2 = f2;
+        c.beg = beg;
+        c.pex = incl - num;
+        c.w0 = W0;
+        c.w1 = W1;
+        c.w2 = W2;
+      }
+      __syncwarp();
+      // ---- the concatenated candidates of these cells, 32 at a time ----
+      for (int G0 = 0; G0 < total; G0 += 32) {
+        const int gp = G0 + lane;
+        // nonempty cells ending at or before G0, and the ends inside this batch
+        const int before = __popc(__ballot_sync(0xffffffffu, nonempty && incl <= G0));
+        const int e = incl - G0;
+        const unsigned ends = __reduce_or_sync(0xffffffffu, (nonempty && e > 0 && e < 32) ? (1u << e) : 0u);
+        const int r = before + __popc(ends & ((2u << lane) - 1u));
+        bool pass = false;
+        int j = -1, code = 0;
+        float r2 = 0.f;
+        if (gp < total) {
+          const NbCell& c = cells[r];
+          const int idx = c.beg + gp - c.pex;
+          const float4 lj = __ldg(sorted_l + idx);
+          const float dx = (lj.x - li.x) + c.o0, dy = (lj.y - li.y) + c.o1, dz = (lj.z - li.z) + c.o2;
+          r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 <= g.rc2_out) {
+            j = __float_as_int(lj.w);
+            const int4 mj = __ldg(sorted_m + idx);
+            const int n0 = c.w0 + mi.x - mj.x, n1 = c.w1 + mi.y - mj.y, n2 = c.w2 + mi.z - mj.z;
+            if (n0 <= -512 || n0 >= 512 || n1 <= -512 || n1 >= 512 || n2 <= -512 || n2 >= 512) {
+              bad_shift = true;
+            } else if (!(j == i && n0 == 0 && n1 == 0 && n2 == 0)) {
+              pass = r2 < g.rc2_in;
+              if (!pass) {  // within the FP32 error of r_c: the exact FP64 test decides
+                double dd0, dd1, dd2;
+                pair_disp_exact(xi, coord + 3 * j, n0, n1, n2, g.h, g.periodic, dd0, dd1, dd2);
+                pass = norm2_exact(dd0, dd1, dd2) < g.rc2;
               }
-              if (n0 <= -512 || n0 >= 512 || n1 <= -512 || n1 >= 512 || n2 <= -512 || n2 >= 512) {
-                bad_shift = true;
-              } else if (!(j == i && n0 == 0 && n1 == 0 && n2 == 0)) {
-                pass = true;
-                code = pack_shift(n0, n1, n2);
-              }
+              code = pack_shift(n0, n1, n2);
             }
           }
-          const unsigned mask = __ballot_sync(0xffffffffu, pass);
-          if (pass) {
-            const int pos = qn + __popc(mask & ((1u << lane) - 1u));
-            q_j[pos] = j;
-            q_c[pos] = code;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, pass);
+        if (pass) {
+          const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+          if (pos < CAP) {
+            e_key[pos] = r2;
+            e_j[pos] = j;
+            e_code[pos] = code;
           }
-          qn += __popc(mask);
-          __syncwarp();
-          if (qn >= 32) drain(32);
+        }
+        cnt += __popc(mask);
+      }
+      __syncwarp();  // cells[] is rewritten by the next chunk
+    }
+    // ---- rank this type's entries under the exact total order ----
+    __syncwarp();
+    const int ge = min(cnt, CAP);
+    const int ng = cnt - gs;
+    const float tw = g.tie_w;
+    for (int e0 = gs; e0 < ge; e0 += 32) {
+      const int e = e0 + lane;
+      if (e < ge) {
+        const float ke = e_key[e];
+        int lo = 0, nothi = 0;  // certainly smaller; not certainly larger (self included)
+        for (int f = gs; f < ge; ++f) {
+          const float kf = e_key[f];
+          lo += (kf + tw < ke);
+          nothi += !(ke + tw < kf);
+        }
+        int rank = lo;
+        if (nothi - lo > 1) {  // FP32 cannot order some pairs: compare their exact r^2
+          const int je = e_j[e], cde = e_code[e];
+          int a0, a1, a2;
+          unpack_shift(cde, a0, a1, a2);
+          double q0, q1, q2;
+          pair_disp_exact(xi, coord + 3 * je, a0, a1, a2, g.h, g.periodic, q0, q1, q2);
+          const double re = norm2_exact(q0, q1, q2);
+          for (int f = gs; f < ge; ++f) {
+            const float kf = e_key[f];
+            if (f == e || kf + tw < ke || ke + tw < kf) continue;
+            const int jf = e_j[f], cf = e_code[f];
+            unpack_shift(cf, a0, a1, a2);
+            pair_disp_exact(xi, coord + 3 * jf, a0, a1, a2, g.h, g.periodic, q0, q1, q2);
+            rank += key_less(norm2_exact(q0, q1, q2), jf, cf, re, je, cde);
+          }
+        }
+        if (rank < g.sel[tj]) {
+          const long slot = (long)i * g.nc + g.sel_off[tj] + rank;
+          nl_j[slot] = e_j[e];
+          nl_code[slot] = e_code[e];
         }
       }
-  if (qn > 0) drain(qn);
-  if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
-  if (cnt > CAP) {
-    if (lane == 0) atomicExch(&st->capacity, 1);
-    cnt = CAP;
-  }
-  __syncwarp();
-  // rank of each entry among entries of the same type under the exact total order
-  for (int e = lane; e < cnt; e += 32) {
-    const unsigned long long re = k_r2[e];
-    const int je = k_j[e], ce = k_code[e];
-    const int te = k_t[e];
-    int rank = 0;
-    for (int f = 0; f < cnt; ++f)
-      if (k_t[f] == te && KeyLess::less(k_r2[f], k_j[f], k_code[f], re, je, ce)) ++rank;
-    if (rank < g.sel[te]) {
-      const long slot = (long)i * g.nc + g.sel_off[te] + rank;
-      nl_j[slot] = je;
-      nl_code[slot] = ce;
     }
-  }
-  // per-type counts, padding and overflow accounting
-  for (int t = 0; t < g.ntypes; ++t) {
-    int c = 0;
-    for (int e = lane; e < cnt; e += 32) c += (k_t[e] == t);
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    for (int q = c + lane; q < g.sel[t]; q += 32) {
-      const long slot = (long)i * g.nc + g.sel_off[t] + q;
+    // padding, counts and overflow accounting of this type
+    for (int q = ng + lane; q < g.sel[tj]; q += 32) {
+      const long slot = (long)i * g.nc + g.sel_off[tj] + q;
       nl_j[slot] = -1;
       nl_code[slot] = pack_shift(0, 0, 0);
     }
     if (lane == 0) {
-      if (counts) counts[(long)i * g.ntypes + t] = c;
-      if (c > g.sel[t]) atomicAdd(&st->sel_overflow, 1);
+      if (counts) counts[(long)i * g.ntypes + tj] = ng;
+      if (ng > g.sel[tj]) atomicAdd(&st->sel_overflow, 1);
     }
   }
+  if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
+  if (cnt > CAP && lane == 0) atomicExch(&st->capacity, 1);
 }
 
 // Stable partition of atoms by type (one block, one pass): each thread takes a contiguous
@@ -390,6 +428,61 @@ __global__ void __launch_bounds__(1024)
 
 }  // namespace
 
+namespace {
+
+float round_down(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float round_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+// Cell edge vectors and the FP32 screening thresholds.  The walk forms the displacement as
+// (l_j - l_i) + o with l the FP32 cell-local positions (|l_d| <= A) and o the FP32 offset of a
+// surrounding cell (|o_d| <= B, three FP32 operations from the rounded edge vectors).  With
+// u = 2^-24 each component is within u (6A + 5B) of the exact FP64 displacement, plus a slack
+// for FP64 rounding of coordinates up to 1e6 A.  For |d| <= R = r_c + 1 the FP32 r^2 (three
+// rounded operations) is then within 2 sqrt(3) R dc + 3 dc^2 + 3 u R^2 of the FP64 r^2; eps
+// doubles that.  Keys further apart than 2 eps (plus the rounding of the comparison itself)
+// keep their FP64 order.
+int screening_bounds(NlGeom& g, double rc) {
+  double hc[9];
+  for (int e = 0; e < 3; ++e)
+    for (int d = 0; d < 3; ++d)
+      hc[e * 3 + d] = g.periodic ? g.h[e * 3 + d] / g.ncell[e] : (e == d ? g.ext[d] / g.ncell[d] : 0.0);
+  double A = 0.0, B = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double a = 0.0, b = 0.0;
+    for (int e = 0; e < 3; ++e) {
+      a += std::fabs(hc[e * 3 + d]);
+      b += g.K[e] * std::fabs(hc[e * 3 + d]);
+    }
+    A = std::max(A, a);
+    B = std::max(B, b);
+  }
+  for (int k = 0; k < 9; ++k) g.hc[k] = (float)hc[k];
+  A = 1.01 * A + 1e-6;
+  B = 1.01 * B + 1e-6;
+  const double u = std::ldexp(1.0, -24);
+  const double dc = u * (6.0 * A + 5.0 * B) + 1e-9;
+  if (dc > 1e-2) {
+    set_error("cells too large for the FP32 distance screening of the neighbour search");
+    return DP_E_ARG;
+  }
+  const double R = rc + 1.0;
+  const double eps = 2.0 * (2.0 * std::sqrt(3.0) * R * dc + 3.0 * dc * dc + 3.0 * u * R * R);
+  g.rc2_in = round_down(g.rc2 - eps);
+  g.rc2_out = round_up(g.rc2 + eps);
+  g.tie_w = round_up(2.5 * eps + 8.0 * u * (g.rc2_out + 1.0));
+  return DP_OK;
+}
+
+}  // namespace
+
 int host_geometry(const dp_model_config& cfg, int natoms, const double* box, const double* lohi, NlGeom& g) {
   std::memset(&g, 0, sizeof(g));
   g.natoms = natoms;
@@ -404,12 +497,11 @@ int host_geometry(const dp_model_config& cfg, int natoms, const double* box, con
   g.nc = off;
   const double rc = cfg.rcut;
   g.rc2 = rc * rc;
-  g.rc2_loose = (float)((rc + 1e-3) * (rc + 1e-3));
   const double cellmin = rc * (1.0 + 1e-9) + 1e-9;
   if (box) {
     g.periodic = 1;
     const double* h = box;
-    for (int k = 0; k < 9; ++k) { g.h[k] = h[k]; g.hf[k] = (float)h[k]; }
+    for (int k = 0; k < 9; ++k) g.h[k] = h[k];
     double c00 = h[4] * h[8] - h[5] * h[7], c01 = h[5] * h[6] - h[3] * h[8], c02 = h[3] * h[7] - h[4] * h[6];
     double det = h[0] * c00 + h[1] * c01 + h[2] * c02;
     if (!(std::fabs(det) > 1e-12)) {
@@ -455,11 +547,8 @@ int host_geometry(const dp_model_config& cfg, int natoms, const double* box, con
       g.K[d] = 1;
     }
     g.cap = DP_MAX_CANDIDATES;  // clusters: no meaningful density
-    g.hf[0] = (float)g.ext[0];
-    g.hf[4] = (float)g.ext[1];
-    g.hf[8] = (float)g.ext[2];
   }
-  return DP_OK;
+  return screening_bounds(g, rc);
 }
 
 cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi, cudaStream_t st) {
@@ -467,28 +556,28 @@ cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_nlist_build(const NlLaunch& L, const double* coord, const int* type, int* cell_count,
-                               int* cell_start, int* cell_cursor, int* cell_atoms, int* atom_cell, int* atom_img,
-                               float4* atom_wf, int* nl_j, int* nl_code, int* counts, DevStatus* status,
+cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
+                               int* cell_count, int* cell_start, int* cell_cursor, int* atom_key, float4* sorted_l,
+                               int4* sorted_m, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st) {
-  const int ncells = L.ncells_total;
-  cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncells, st);
+  const int nkeys = L.ncells_total * ntypes;
+  cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * nkeys, st);
   if (e != cudaSuccess) return e;
   const int nb = (L.natoms + 255) / 256;
-  k_bin<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, coord, cell_count, atom_cell, atom_img,
-                            atom_wf);
-  k_scan_excl<<<1, 1024, 0, st>>>(cell_count, ncells, cell_start, cell_cursor);
-  k_fill<<<nb, 256, 0, st>>>(L.natoms, atom_cell, cell_cursor, cell_atoms);
+  k_bin<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, L.ncells_total, ntypes, coord, type,
+                            cell_count, atom_key, status);
+  k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, cell_cursor);
+  k_fill<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.natoms, coord, atom_key, cell_cursor, sorted_l, sorted_m);
   const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));
-  const size_t smem = (size_t)kWarpsPerBlock * cap * 17 + (size_t)kWarpsPerBlock * 2 * kQueue * sizeof(int);
-  const unsigned blocks = (L.natoms + kWarpsPerBlock - 1) / kWarpsPerBlock;
-#define DPGB_NL_LAUNCH(C)                                                                                   \
-  do {                                                                                                      \
-    e = cudaFuncSetAttribute(k_nlist<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
-    if (e != cudaSuccess) return e;                                                                         \
-    k_nlist<C><<<blocks, kWarpsPerBlock * 32, smem, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, coord, \
-                                                         type, cell_start, cell_atoms, atom_cell, atom_img,   \
-                                                         atom_wf, nl_j, nl_code, counts, status);             \
+  const size_t smem = (size_t)kNlWarps * ((size_t)cap * 12 + 32 * sizeof(NbCell));
+  const unsigned blocks = (L.natoms + kNlWarps - 1) / kNlWarps;
+#define DPGB_NL_LAUNCH(C)                                                                                       \
+  do {                                                                                                          \
+    e = cudaFuncSetAttribute(k_nlist<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
+    if (e != cudaSuccess) return e;                                                                             \
+    k_nlist<C><<<blocks, kNlWarps * 32, smem, st>>>(L.geoms, L.atom_frame, L.cell_off, cell_start + nkeys,      \
+                                                   L.ncells_total, coord, cell_start, sorted_l, sorted_m, nl_j, \
+                                                   nl_code, counts, status);                                    \
   } while (0)
   if (cap == 128)
     DPGB_NL_LAUNCH(128);

@@ -27,14 +27,15 @@ constexpr long kMaxSlots = DP_NOALLOC_MAX_SLOTS;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // byte offsets of the pieces of the static scratch
+// (type, cell) keys
+constexpr size_t kMaxKeys = (size_t)kMaxCells * DP_MAX_TYPES;
 constexpr size_t kOffCellCount = 0;
-constexpr size_t kOffCellStart = kOffCellCount + align256(sizeof(int) * kMaxCells);
-constexpr size_t kOffCellCursor = kOffCellStart + align256(sizeof(int) * (kMaxCells + 1));
-constexpr size_t kOffCellAtoms = kOffCellCursor + align256(sizeof(int) * kMaxCells);
-constexpr size_t kOffAtomCell = kOffCellAtoms + align256(sizeof(int) * kMaxAtoms);
-constexpr size_t kOffAtomImg = kOffAtomCell + align256(sizeof(int) * kMaxAtoms);
-constexpr size_t kOffAtomWf = kOffAtomImg + align256(sizeof(int) * 3 * kMaxAtoms);
-constexpr size_t kOffCode = kOffAtomWf + align256(sizeof(float4) * kMaxAtoms);
+constexpr size_t kOffCellStart = kOffCellCount + align256(sizeof(int) * kMaxKeys);
+constexpr size_t kOffCellCursor = kOffCellStart + align256(sizeof(int) * (kMaxKeys + 1));
+constexpr size_t kOffAtomKey = kOffCellCursor + align256(sizeof(int) * kMaxKeys);
+constexpr size_t kOffSortedL = kOffAtomKey + align256(sizeof(int) * kMaxAtoms);
+constexpr size_t kOffSortedM = kOffSortedL + align256(sizeof(float4) * kMaxAtoms);
+constexpr size_t kOffCode = kOffSortedM + align256(sizeof(int4) * kMaxAtoms);
 constexpr size_t kOffCounts = kOffCode + align256(sizeof(int) * kMaxSlots);
 constexpr size_t kOffStatus = kOffCounts + align256(sizeof(int) * DP_MAX_TYPES * kMaxAtoms);
 constexpr size_t kOffBbox = kOffStatus + align256(sizeof(DevStatus));
@@ -124,10 +125,9 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   int* cell_count = reinterpret_cast<int*>(s + kOffCellCount);
   int* cell_start = reinterpret_cast<int*>(s + kOffCellStart);
   int* cell_cursor = reinterpret_cast<int*>(s + kOffCellCursor);
-  int* cell_atoms = reinterpret_cast<int*>(s + kOffCellAtoms);
-  int* atom_cell = reinterpret_cast<int*>(s + kOffAtomCell);
-  int* atom_img = reinterpret_cast<int*>(s + kOffAtomImg);
-  float4* atom_wf = reinterpret_cast<float4*>(s + kOffAtomWf);
+  int* atom_key = reinterpret_cast<int*>(s + kOffAtomKey);
+  float4* sorted_l = reinterpret_cast<float4*>(s + kOffSortedL);
+  int4* sorted_m = reinterpret_cast<int4*>(s + kOffSortedM);
   int* code = reinterpret_cast<int*>(s + kOffCode);
   int* counts = reinterpret_cast<int*>(s + kOffCounts);
   DevStatus* status = reinterpret_cast<DevStatus*>(s + kOffStatus);
@@ -151,8 +151,8 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   DP_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   DP_CUDA_TRY(cudaMemcpyAsync(geom, &g, sizeof(NlGeom), cudaMemcpyHostToDevice, st));
   const NlLaunch L{natoms, g.ncell[0] * g.ncell[1] * g.ncell[2], g.cap, geom, nullptr, nullptr};
-  DP_CUDA_TRY(launch_nlist_build(L, coord, type, cell_count, cell_start, cell_cursor, cell_atoms, atom_cell, atom_img,
-                                 atom_wf, nl_j, code, counts, status, st));
+  DP_CUDA_TRY(launch_nlist_build(L, cfg->ntypes, coord, type, cell_count, cell_start, cell_cursor, atom_key, sorted_l,
+                                 sorted_m, nl_j, code, counts, status, st));
   const long n = (long)natoms * nc;
   k_unpack_shift<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(code, n, nl_shift);
   DP_CUDA_TRY(cudaGetLastError());
@@ -160,6 +160,10 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   DP_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   DP_CUDA_TRY(cudaStreamSynchronize(st));
   if (n_overflow) *n_overflow = hs.sel_overflow;
+  if (hs.bad_type) {
+    set_error("atom type outside [0, ntypes)");
+    return DP_E_ARG;
+  }
   if (hs.capacity == 2) {
     set_error("periodic image index beyond +-511 cells: coordinates too far outside the box");
     return DP_E_ARG;
