@@ -24,7 +24,10 @@ struct NlGeom {
   double inv[9];     // inverse of h (periodic)
   double origin[3];  // open boundary: fractional = (x - origin) / ext
   double ext[3];
+  double rext[3];    // open boundary: 1 / ext
+  double rn[3];      // 1 / ncell
   float hc[9];       // edge vectors of one cell, h_e / ncell_e (diag(ext / ncell) when open), FP32
+  float r_n2c, r_n12c;  // 1 / (2K_2 + 1), 1 / ((2K_1 + 1)(2K_2 + 1)): decoding a surrounding-cell index
   int ncell[3];
   int K[3];          // virtual-cell search half-width per axis
   double rc2;        // r_c^2 (exact membership test)

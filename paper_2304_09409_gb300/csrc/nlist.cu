@@ -23,8 +23,7 @@ namespace dpgb {
 namespace {
 
 constexpr int kNlWarps = 4;  // centre atoms (warps) per block
-
-__device__ __forceinline__ int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+constexpr int kNlEntryBytes = 24;  // shared bytes per accepted entry
 
 __global__ void k_bbox(const double* __restrict__ coord, int n, double* __restrict__ out) {
   __shared__ double s[6][32];
@@ -69,7 +68,7 @@ __device__ __forceinline__ Binned bin_atom(const NlGeom& g, const double* x) {
     if (g.periodic)
       f = x[0] * g.inv[0 * 3 + d] + x[1] * g.inv[1 * 3 + d] + x[2] * g.inv[2 * 3 + d];
     else
-      f = (x[d] - g.origin[d]) / g.ext[d];
+      f = (x[d] - g.origin[d]) * g.rext[d];
     double fl = g.periodic ? floor(f) : 0.0;
     double wd = f - fl;
     if (g.periodic && wd >= 1.0) { wd = 0.0; fl += 1.0; }
@@ -77,7 +76,7 @@ __device__ __forceinline__ Binned bin_atom(const NlGeom& g, const double* x) {
     b.m[d] = (int)fl;
     int cd = (int)(wd * g.ncell[d]);
     b.c[d] = cd < 0 ? 0 : (cd >= g.ncell[d] ? g.ncell[d] - 1 : cd);
-    s[d] = (double)b.m[d] + (double)b.c[d] / (double)g.ncell[d];
+    s[d] = (double)b.m[d] + (double)b.c[d] * g.rn[d];
   }
   for (int d = 0; d < 3; ++d) {
     if (g.periodic)
@@ -147,7 +146,8 @@ __global__ void k_scan_excl(const int* __restrict__ in, int n, int* __restrict__
   if (threadIdx.x == 0) out[n] = carry;
 }
 
-// Sorted entries: cell-local position (FP32) with the atom index, and the image index m.
+// Sorted entries: cell-local position (FP32) with the atom index, and the image index m with
+// the cell's coordinates packed in 10-bit fields.
 __global__ void k_fill(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, int natoms,
                        const double* __restrict__ coord, const int* __restrict__ atom_key, int* __restrict__ cursor,
                        float4* __restrict__ sorted_l, int4* __restrict__ sorted_m) {
@@ -158,14 +158,22 @@ __global__ void k_fill(const NlGeom* __restrict__ G, const int* __restrict__ ato
   const Binned b = bin_atom(G[atom_frame ? atom_frame[i] : 0], coord + 3 * i);
   const int pos = atomicAdd(cursor + key, 1);
   sorted_l[pos] = make_float4((float)b.l[0], (float)b.l[1], (float)b.l[2], __int_as_float(i));
-  sorted_m[pos] = make_int4(b.m[0], b.m[1], b.m[2], key);
+  sorted_m[pos] = make_int4(b.m[0], b.m[1], b.m[2], (b.c[0] << 20) | (b.c[1] << 10) | b.c[2]);
 }
 
-// Exact order of two accepted neighbours: r^2 (FP64), then j, then the image code.
-__device__ __forceinline__ bool key_less(double ra, int ja, int ca, double rb, int jb, int cb) {
-  if (ra != rb) return ra < rb;
-  if (ja != jb) return ja < jb;
-  return (unsigned)ca < (unsigned)cb;
+// Small integers to and from FP32 through the bit pattern (exact for |v| < 2^22): no
+// conversion instructions, which issue on a narrow pipe on this part.
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+__device__ __forceinline__ int small_float_to_int(float f) {  // nearest integer, |f| < 2^22
+  return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000;
+}
+// floor(o / m) for 0 <= o < 2^21 from r = fl(1/m): x = (o + 1/2)/m lies at least 1/(2m) away
+// from an integer, further than the error of fma(o + 1/2, r, -1/2) (relative 2^-23 of x), so
+// rounding x - 1/2 to the nearest integer gives floor(x).
+__device__ __forceinline__ int div_small(int o, float r) {
+  return small_float_to_int(fmaf(small_int_to_float(o) + 0.5f, r, -0.5f));
 }
 
 // One surrounding cell of the centre's cell, as staged for the batch walk.
@@ -173,22 +181,58 @@ struct NbCell {
   float o0, o1, o2;  // FP32 offset of the cell's corner from the centre cell's corner (image included)
   int beg;           // first sorted entry of the cell (this type)
   int pex;           // position of that entry in the concatenated candidate stream
-  int w0, w1, w2;    // periodic wrap of the cell
+  int wcode;         // periodic wrap W of the cell, packed as an image code
+  int wzero;         // W == 0 (the centre's own image of its cell)
+  int pad;
 };
+
+// Neighbour index j and image code n = W + m_i - m_j of a sorted entry seen through a cell of
+// wrap code wcode; false when n leaves the packable range.
+__device__ __forceinline__ bool entry_code(const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m,
+                                           int idx, int wcode, const int4& mi, int& j, int& code) {
+  j = __float_as_int(__ldg(&sorted_l[idx].w));
+  const int4 mj = __ldg(sorted_m + idx);
+  int w0, w1, w2;
+  unpack_shift(wcode, w0, w1, w2);
+  const int n0 = w0 + mi.x - mj.x, n1 = w1 + mi.y - mj.y, n2 = w2 + mi.z - mj.z;
+  code = 0;
+  if (n0 <= -512 || n0 >= 512 || n1 <= -512 || n1 >= 512 || n2 <= -512 || n2 >= 512) return false;
+  code = pack_shift(n0, n1, n2);
+  return true;
+}
+
+__device__ __forceinline__ double exact_r2(const NlGeom& g, const double* xi, const double* __restrict__ coord, int j,
+                                           int code) {
+  const double* xj = coord + 3 * j;
+  double d0, d1, d2;
+  if (code == pack_shift(0, 0, 0)) {  // same image: (x_j + 0) - x_i is x_j - x_i
+    d0 = __dsub_rn(xj[0], xi[0]);
+    d1 = __dsub_rn(xj[1], xi[1]);
+    d2 = __dsub_rn(xj[2], xi[2]);
+  } else {
+    int n0, n1, n2;
+    unpack_shift(code, n0, n1, n2);
+    pair_disp_exact(xi, xj, n0, n1, n2, g.h, g.periodic, d0, d1, d2);
+  }
+  return norm2_exact(d0, d1, d2);
+}
 
 template <int CAP>
 __global__ void __launch_bounds__(kNlWarps * 32)
     k_nlist(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, const int* __restrict__ cell_off,
-            const int* __restrict__ n_sorted, int ncells_total, const double* __restrict__ coord, const int* __restrict__ cell_start,
-            const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m, int* __restrict__ nl_j,
-            int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
+            const int* __restrict__ n_sorted, int ncells_total, const double* __restrict__ coord,
+            const int* __restrict__ cell_start, const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m,
+            int* __restrict__ nl_j, int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
+  constexpr int CAPP = CAP + 4 * DP_MAX_TYPES;  // room for aligning each type's group to 4 entries
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wb = smem + (size_t)warp * (CAP * 12 + 32 * sizeof(NbCell));
-  float* e_key = reinterpret_cast<float*>(wb);      // FP32 r^2 of each accepted entry
-  int* e_j = reinterpret_cast<int*>(wb + CAP * 4);  // neighbour index
-  int* e_code = reinterpret_cast<int*>(wb + CAP * 8);  // packed image shift
-  NbCell* cells = reinterpret_cast<NbCell*>(wb + CAP * 12);
+  unsigned char* wb = smem + (size_t)warp * (CAPP * kNlEntryBytes + 32 * sizeof(NbCell));
+  unsigned long long* e_x = reinterpret_cast<unsigned long long*>(wb);  // exact r^2 bits (window entries)
+  float* e_key = reinterpret_cast<float*>(wb + CAPP * 8);  // FP32 r^2 of each accepted entry
+  int* e_idx = reinterpret_cast<int*>(wb + CAPP * 12);     // its sorted position, then j
+  int* e_w = reinterpret_cast<int*>(wb + CAPP * 16);       // wrap code of its cell, then the image code
+  int* e_rk = reinterpret_cast<int*>(wb + CAPP * 20);      // certain part of the rank; -1 - it for window entries
+  NbCell* cells = reinterpret_cast<NbCell*>(wb + CAPP * 24);
 
   const int w = blockIdx.x * kNlWarps + warp;
   if (w >= *n_sorted) return;  // warp-uniform; atoms of an invalid type were left out
@@ -199,18 +243,17 @@ __global__ void __launch_bounds__(kNlWarps * 32)
   const int fr = atom_frame ? atom_frame[i] : 0;
   const NlGeom& g = G[fr];
   const int coff = cell_off ? cell_off[fr] : 0;
-  const int ci = mi.w % ncells_total - coff;
-  const int c2 = ci % g.ncell[2];
-  const int c1 = (ci / g.ncell[2]) % g.ncell[1];
-  const int c0 = ci / (g.ncell[2] * g.ncell[1]);
+  const int c0 = (mi.w >> 20) & 1023, c1 = (mi.w >> 10) & 1023, c2 = mi.w & 1023;
   const int n0c = 2 * g.K[0] + 1, n1c = 2 * g.K[1] + 1, n2c = 2 * g.K[2] + 1;
   const int noff = n0c * n1c * n2c;
   const double* xi = coord + 3 * i;
+  const float rc2_in = g.rc2_in, rc2_out = g.rc2_out, tw = g.tie_w;
 
   int cnt = 0;
   bool bad_shift = false;
   for (int tj = 0; tj < g.ntypes; ++tj) {
-    const int gs = cnt;  // this type's entries start here
+    cnt = (cnt + 3) & ~3;
+    const int gs = cnt;  // this type's entries start here (a multiple of 4)
     const int kbase = tj * ncells_total + coff;
     for (int o0 = 0; o0 < noff; o0 += 32) {
       // ---- the chunk's surrounding cells: one per lane ----
@@ -218,18 +261,21 @@ __global__ void __launch_bounds__(kNlWarps * 32)
       int num = 0, beg = 0, W0 = 0, W1 = 0, W2 = 0;
       float f0 = 0.f, f1 = 0.f, f2 = 0.f;
       if (o < noff) {
-        const int d0 = o / (n1c * n2c) - g.K[0];
-        const int d1 = (o / n2c) % n1c - g.K[1];
-        const int d2 = o % n2c - g.K[2];
+        const int q0 = div_small(o, g.r_n12c);
+        const int rem = o - q0 * (n1c * n2c);
+        const int q1 = div_small(rem, g.r_n2c);
+        const int d0 = q0 - g.K[0];
+        const int d1 = q1 - g.K[1];
+        const int d2 = rem - q1 * n2c - g.K[2];
         int v0 = c0 + d0, v1 = c1 + d1, v2 = c2 + d2;
         bool inside = true;
-        if (g.periodic) {
-          W0 = floordiv(v0, g.ncell[0]);
-          W1 = floordiv(v1, g.ncell[1]);
-          W2 = floordiv(v2, g.ncell[2]);
-          v0 -= W0 * g.ncell[0];
-          v1 -= W1 * g.ncell[1];
-          v2 -= W2 * g.ncell[2];
+        if (g.periodic) {  // |W| <= ceil(K / ncell): a few steps at most
+          while (v0 < 0) { v0 += g.ncell[0]; --W0; }
+          while (v0 >= g.ncell[0]) { v0 -= g.ncell[0]; ++W0; }
+          while (v1 < 0) { v1 += g.ncell[1]; --W1; }
+          while (v1 >= g.ncell[1]) { v1 -= g.ncell[1]; ++W1; }
+          while (v2 < 0) { v2 += g.ncell[2]; --W2; }
+          while (v2 >= g.ncell[2]) { v2 -= g.ncell[2]; ++W2; }
         } else {
           inside = v0 >= 0 && v1 >= 0 && v2 >= 0 && v0 < g.ncell[0] && v1 < g.ncell[1] && v2 < g.ncell[2];
         }
@@ -238,7 +284,7 @@ __global__ void __launch_bounds__(kNlWarps * 32)
           beg = cell_start[key];
           num = cell_start[key + 1] - beg;
         }
-        const float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
+        const float e0 = small_int_to_float(d0), e1 = small_int_to_float(d1), e2 = small_int_to_float(d2);
         f0 = fmaf(e2, g.hc[6], fmaf(e1, g.hc[3], e0 * g.hc[0]));
         f1 = fmaf(e2, g.hc[7], fmaf(e1, g.hc[4], e0 * g.hc[1]));
         f2 = fmaf(e2, g.hc[8], fmaf(e1, g.hc[5], e0 * g.hc[2]));
@@ -254,49 +300,63 @@ __global__ void __launch_bounds__(kNlWarps * 32)
       const unsigned nemask = __ballot_sync(0xffffffffu, nonempty);
       __syncwarp();
       if (nonempty) {
-        NbCell& c = cells[__popc(nemask & ((1u << lane) - 1u))];
+        NbCell c;
         c.o0 = f0;
         c.o1 = f1;
         c.o2 = f2;
         c.beg = beg;
         c.pex = incl - num;
-        c.w0 = W0;
-        c.w1 = W1;
-        c.w2 = W2;
+        c.wcode = pack_shift(W0, W1, W2);
+        c.wzero = (W0 | W1 | W2) == 0;
+        c.pad = 0;
+        cells[__popc(nemask & ((1u << lane) - 1u))] = c;
       }
       __syncwarp();
       // ---- the concatenated candidates of these cells, 32 at a time ----
-      for (int G0 = 0; G0 < total; G0 += 32) {
-        const int gp = G0 + lane;
-        // nonempty cells ending at or before G0, and the ends inside this batch
+      // position -> cell: nonempty cells ending at or before the batch start, plus the cell ends
+      // inside the batch up to this lane
+      auto locate = [&](int G0, int& r) {
         const int before = __popc(__ballot_sync(0xffffffffu, nonempty && incl <= G0));
         const int e = incl - G0;
         const unsigned ends = __reduce_or_sync(0xffffffffu, (nonempty && e > 0 && e < 32) ? (1u << e) : 0u);
-        const int r = before + __popc(ends & ((2u << lane) - 1u));
+        r = before + __popc(ends & ((2u << lane) - 1u));
+      };
+      int r_nx;
+      locate(0, r_nx);
+      float4 lj_nx = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lane < total) {
+        const NbCell& c = cells[r_nx];
+        lj_nx = __ldg(sorted_l + c.beg + lane - c.pex);
+      }
+      for (int G0 = 0; G0 < total; G0 += 32) {
+        const int gp = G0 + lane;
+        const int r = r_nx;
+        const float4 lj = lj_nx;
+        if (G0 + 32 < total) {  // the next batch's positions are in flight while this one is tested
+          locate(G0 + 32, r_nx);
+          if (gp + 32 < total) {
+            const NbCell& c = cells[r_nx];
+            lj_nx = __ldg(sorted_l + c.beg + gp + 32 - c.pex);
+          }
+        }
         bool pass = false;
-        int j = -1, code = 0;
+        int idx = 0, wcode = 0;
         float r2 = 0.f;
         if (gp < total) {
           const NbCell& c = cells[r];
-          const int idx = c.beg + gp - c.pex;
-          const float4 lj = __ldg(sorted_l + idx);
+          idx = c.beg + gp - c.pex;
+          wcode = c.wcode;
           const float dx = (lj.x - li.x) + c.o0, dy = (lj.y - li.y) + c.o1, dz = (lj.z - li.z) + c.o2;
           r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 <= g.rc2_out) {
-            j = __float_as_int(lj.w);
-            const int4 mj = __ldg(sorted_m + idx);
-            const int n0 = c.w0 + mi.x - mj.x, n1 = c.w1 + mi.y - mj.y, n2 = c.w2 + mi.z - mj.z;
-            if (n0 <= -512 || n0 >= 512 || n1 <= -512 || n1 >= 512 || n2 <= -512 || n2 >= 512) {
+          const bool self = idx == w && c.wzero;
+          if (r2 < rc2_in) {
+            pass = !self;
+          } else if (r2 <= rc2_out && !self) {  // within the FP32 error of r_c: the exact FP64 test decides
+            int j, code;
+            if (entry_code(sorted_l, sorted_m, idx, wcode, mi, j, code))
+              pass = exact_r2(g, xi, coord, j, code) < g.rc2;
+            else
               bad_shift = true;
-            } else if (!(j == i && n0 == 0 && n1 == 0 && n2 == 0)) {
-              pass = r2 < g.rc2_in;
-              if (!pass) {  // within the FP32 error of r_c: the exact FP64 test decides
-                double dd0, dd1, dd2;
-                pair_disp_exact(xi, coord + 3 * j, n0, n1, n2, g.h, g.periodic, dd0, dd1, dd2);
-                pass = norm2_exact(dd0, dd1, dd2) < g.rc2;
-              }
-              code = pack_shift(n0, n1, n2);
-            }
           }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, pass);
@@ -304,8 +364,8 @@ __global__ void __launch_bounds__(kNlWarps * 32)
           const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
           if (pos < CAP) {
             e_key[pos] = r2;
-            e_j[pos] = j;
-            e_code[pos] = code;
+            e_idx[pos] = idx;
+            e_w[pos] = wcode;
           }
         }
         cnt += __popc(mask);
@@ -313,41 +373,60 @@ __global__ void __launch_bounds__(kNlWarps * 32)
       __syncwarp();  // cells[] is rewritten by the next chunk
     }
     // ---- rank this type's entries under the exact total order ----
-    __syncwarp();
-    const int ge = min(cnt, CAP);
     const int ng = cnt - gs;
-    const float tw = g.tie_w;
+    const int ge = min(cnt, CAP);
+    const int ge4 = gs + ((max(ge - gs, 0) + 3) & ~3);
+    if (ge + lane < ge4) e_key[ge + lane] = __int_as_float(0x7f800000);  // +inf: never smaller, always larger
+    __syncwarp();
+    // pass 1: certain ranks from the FP32 keys; entries whose FP32 key cannot be ordered against
+    // some other entry compute their exact r^2 (all such lanes at once)
     for (int e0 = gs; e0 < ge; e0 += 32) {
       const int e = e0 + lane;
       if (e < ge) {
         const float ke = e_key[e];
-        int lo = 0, nothi = 0;  // certainly smaller; not certainly larger (self included)
-        for (int f = gs; f < ge; ++f) {
-          const float kf = e_key[f];
-          lo += (kf + tw < ke);
-          nothi += !(ke + tw < kf);
+        const float lo_t = ke - tw, hi_t = ke + tw;
+        int lo = 0, hi = 0;  // certainly smaller; certainly larger
+        for (int f = gs; f < ge4; f += 4) {
+          const float4 k4 = *reinterpret_cast<const float4*>(e_key + f);
+          lo += (k4.x < lo_t) + (k4.y < lo_t) + (k4.z < lo_t) + (k4.w < lo_t);
+          hi += (k4.x > hi_t) + (k4.y > hi_t) + (k4.z > hi_t) + (k4.w > hi_t);
         }
-        int rank = lo;
-        if (nothi - lo > 1) {  // FP32 cannot order some pairs: compare their exact r^2
-          const int je = e_j[e], cde = e_code[e];
-          int a0, a1, a2;
-          unpack_shift(cde, a0, a1, a2);
-          double q0, q1, q2;
-          pair_disp_exact(xi, coord + 3 * je, a0, a1, a2, g.h, g.periodic, q0, q1, q2);
-          const double re = norm2_exact(q0, q1, q2);
+        int je, ce;
+        if (!entry_code(sorted_l, sorted_m, e_idx[e], e_w[e], mi, je, ce)) bad_shift = true;
+        const bool window = ge4 - gs - lo - hi > 1;
+        if (window) e_x[e] = (unsigned long long)__double_as_longlong(exact_r2(g, xi, coord, je, ce));
+        e_idx[e] = je;
+        e_w[e] = ce;
+        e_rk[e] = window ? -1 - lo : lo;
+      }
+    }
+    __syncwarp();
+    // pass 2: window entries add the partners their exact key (r^2 bits, j, image code) puts first
+    for (int e0 = gs; e0 < ge; e0 += 32) {
+      const int e = e0 + lane;
+      if (e < ge) {
+        int rank = e_rk[e];
+        const int je = e_idx[e], ce = e_w[e];
+        if (rank < 0) {
+          rank = -1 - rank;
+          const float ke = e_key[e];
+          const float lo_t = ke - tw, hi_t = ke + tw;
+          const unsigned long long xe = e_x[e];
           for (int f = gs; f < ge; ++f) {
             const float kf = e_key[f];
-            if (f == e || kf + tw < ke || ke + tw < kf) continue;
-            const int jf = e_j[f], cf = e_code[f];
-            unpack_shift(cf, a0, a1, a2);
-            pair_disp_exact(xi, coord + 3 * jf, a0, a1, a2, g.h, g.periodic, q0, q1, q2);
-            rank += key_less(norm2_exact(q0, q1, q2), jf, cf, re, je, cde);
+            if (f == e || kf < lo_t || kf > hi_t) continue;
+            const int jf = e_idx[f];
+            // f's own window test, rounded from its side, may have left f unflagged
+            const unsigned long long xf =
+                e_rk[f] < 0 ? e_x[f] : (unsigned long long)__double_as_longlong(exact_r2(g, xi, coord, jf, e_w[f]));
+            // non-negative doubles order as their bit patterns
+            rank += xf != xe ? xf < xe : (jf != je ? jf < je : (unsigned)e_w[f] < (unsigned)ce);
           }
         }
         if (rank < g.sel[tj]) {
           const long slot = (long)i * g.nc + g.sel_off[tj] + rank;
-          nl_j[slot] = e_j[e];
-          nl_code[slot] = e_code[e];
+          nl_j[slot] = je;
+          nl_code[slot] = ce;
         }
       }
     }
@@ -361,6 +440,7 @@ __global__ void __launch_bounds__(kNlWarps * 32)
       if (counts) counts[(long)i * g.ntypes + tj] = ng;
       if (ng > g.sel[tj]) atomicAdd(&st->sel_overflow, 1);
     }
+    __syncwarp();
   }
   if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
   if (cnt > CAP && lane == 0) atomicExch(&st->capacity, 1);
@@ -450,6 +530,17 @@ float round_up(double v) {
 // doubles that.  Keys further apart than 2 eps (plus the rounding of the comparison itself)
 // keep their FP64 order.
 int screening_bounds(NlGeom& g, double rc) {
+  const int n2c = 2 * g.K[2] + 1, n12c = (2 * g.K[1] + 1) * n2c;
+  if ((long)(2 * g.K[0] + 1) * n12c >= (1L << 21)) {
+    set_error("too many periodic images of the cell grid (box far narrower than r_c)");
+    return DP_E_ARG;
+  }
+  g.r_n2c = (float)(1.0 / n2c);
+  g.r_n12c = (float)(1.0 / n12c);
+  for (int d = 0; d < 3; ++d) {
+    g.rn[d] = 1.0 / g.ncell[d];
+    g.rext[d] = g.periodic ? 0.0 : 1.0 / g.ext[d];
+  }
   double hc[9];
   for (int e = 0; e < 3; ++e)
     for (int d = 0; d < 3; ++d)
@@ -569,7 +660,7 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, cell_cursor);
   k_fill<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.natoms, coord, atom_key, cell_cursor, sorted_l, sorted_m);
   const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));
-  const size_t smem = (size_t)kNlWarps * ((size_t)cap * 12 + 32 * sizeof(NbCell));
+  const size_t smem = (size_t)kNlWarps * ((size_t)(cap + 4 * DP_MAX_TYPES) * kNlEntryBytes + 32 * sizeof(NbCell));
   const unsigned blocks = (L.natoms + kNlWarps - 1) / kNlWarps;
 #define DPGB_NL_LAUNCH(C)                                                                                       \
   do {                                                                                                          \

@@ -83,6 +83,63 @@ def test_nlist_bit_exact(name, cfg, fr):
     np.testing.assert_array_equal(gs, rs)
 
 
+# Frames built to reach the rarely taken branches of the list builder: exact and near-exact
+# distance ties (ordered by j, then image, under the exact FP64 r^2), pairs at r_c and within
+# 1e-15 .. 1e-4 of it (the FP64 membership test), coincident atoms (r = 0), coordinates a
+# thousand boxes away from the origin, and cells so large that the FP32 screening window is
+# widest.
+def _shell_frame():
+    rng = np.random.default_rng(11)
+    L, rc = 20.0, 6.0
+    c0 = np.array([5.0, 5.0, 5.0])
+    pts = [c0, c0 + [6, 0, 0], c0 + [0, 6, 0], c0 + [0, 0, -6], c0 + [3, 4, 0], c0 + [4, 3, 0], c0 + [0, 5, 0],
+           c0 + [0, 0, 5], c0 + [-5, 0, 0], c0 + 6 / np.sqrt(3) * np.ones(3)]
+    for rel in (1e-15, 1e-12, 1e-9, 1e-7, 1e-6, 1e-5, 1e-4):
+        for sgn in (-1.0, 1.0):
+            u = rng.normal(size=3)
+            u /= np.linalg.norm(u)
+            pts.append(c0 + u * rc * (1 + sgn * rel))
+    # the same distances across the periodic boundary
+    c1 = np.array([L - 1.0, 10.0, 10.0])
+    pts += [c1, c1 + [6, 0, 0], c1 + [6 * (1 + 1e-12), 0, 0], c1 + [6 * (1 - 1e-12), 0, 0.0]]
+    coord = np.array(pts, dtype=np.float64)
+    atype = (np.arange(len(pts)) % 2).astype(np.int32)
+    cfg = I.ModelConfig(ntypes=2, rcut=rc, rcut_smth=0.5, sel=(24, 24), embed=(4, 8, 16), axis=4, fit=(12, 12))
+    return cfg, I.Frame(coord, atype, np.eye(3) * L)
+
+
+def _hard_nl_cases():
+    out = []
+    out.append(("fcc_perfect_images", I.metal_model(), I.fcc_frame((3, 3, 3), sigma=0.0, seed=0)))
+    out.append(("fcc_perfect", I.metal_model(), I.fcc_frame((5, 5, 5), sigma=0.0, seed=0)))
+    cfg, fr = _shell_frame()
+    out.append(("cutoff_shell", cfg, fr))
+    w = I.water_frame(0)
+    dup = np.concatenate([w.coord, w.coord[:10]])
+    out.append(("water_coincident", I.water_model(),
+                I.Frame(dup, np.concatenate([w.atype, w.atype[:10]]).astype(np.int32), w.box)))
+    out.append(("water_far_images", I.water_model(),
+                I.Frame(w.coord + 1000 * w.box[0] - 700 * w.box[1] + 3 * w.box[2], w.atype, w.box)))
+    rng = np.random.default_rng(5)
+    centres = rng.uniform(0, 3000.0, size=(20, 3))
+    pts = (centres[:, None, :] + rng.uniform(-4, 4, size=(20, 12, 3))).reshape(-1, 3)
+    out.append(("sparse_3000A", I.water_model(),
+                I.Frame(pts, (np.arange(len(pts)) % 2).astype(np.int32), np.eye(3) * 3000.0)))
+    return out
+
+
+@pytest.mark.parametrize("name,cfg,fr", _hard_nl_cases(), ids=[c[0] for c in _hard_nl_cases()])
+def test_nlist_ties_cutoff_and_extremes_bit_exact(name, cfg, fr):
+    dpgb = _dp()
+    m = dpgb.Model(cfg, I.make_params(cfg, 0), precision="fp64")
+    nl = m.build_nlist(fr.coord, fr.atype, fr.box)
+    gj, gs = nl.export()
+    rj, rs, counts, ov = oracle.nlist(cfg, fr.coord, fr.atype, fr.box)
+    assert nl.n_overflow == ov
+    np.testing.assert_array_equal(gj, rj)
+    np.testing.assert_array_equal(gs, rs)
+
+
 def test_nlist_open_boundary_bit_exact():
     dpgb = _dp()
     cfg = tiny_model()
