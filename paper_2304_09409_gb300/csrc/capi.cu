@@ -324,7 +324,7 @@ int dp_gemm_bf16(int rows, int K, int N, const void* A, const void* Bt, float* C
   a.tile_start[1] = (rows + 127) / 128;
   a.K = K;
   a.N = N;
-  a.BN = tc_pick_bn(N, a.tile_start[1], false);
+  a.BN = tc_pick_bn(N, a.tile_start[1]);
   a.out_f32 = C;
   a.err = err;
   CUtensorMap ta;

@@ -152,7 +152,9 @@ struct NlLaunch {
   int cap;                // candidate buffer per atom (max over frames)
   const NlGeom* geoms;    // device [frames]
   const int* atom_frame;  // device [natoms] frame of each atom, or null (one frame)
-  const int* cell_off;    // device [frames] first cell of each frame, or null (one frame)
+  const int* cell_off;    // device [frames + 1] first cell of each frame, or null (one frame)
+  int nframes;            // frames in the launch
+  int max_noff;           // largest (2K_0+1)(2K_1+1)(2K_2+1) over the frames
 };
 // Cell arrays are indexed by (type, cell): cell_count, cell_cursor [ntypes * ncells_total],
 // cell_start [ntypes * ncells_total + 1]; atom_key [natoms]; sorted_l, sorted_m [natoms].

@@ -114,6 +114,11 @@ struct FrameTables {
     o += a256(sizeof(double) * 9 * F);
     bytes = o;
   }
+  int max_noff() const {
+    int m = 0;
+    for (const NlGeom& g : geoms) m = std::max(m, (2 * g.K[0] + 1) * (2 * g.K[1] + 1) * (2 * g.K[2] + 1));
+    return m;
+  }
   void pack(unsigned char* p) const {
     std::memcpy(p + off_geoms, geoms.data(), sizeof(NlGeom) * F);
     std::memcpy(p + off_celloff, cell_off.data(), sizeof(int) * (F + 1));
@@ -343,7 +348,7 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     k_atom_frame<<<(N + 255) / 256, 256, 0, st>>>(d_start, F, N, b.atom_frame);
   }
   if (own_nlist) {
-    NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr};
+    NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff()};
     ProfScope _ps(&md->prof, "nlist", st, 4);
     DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
                                    b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, st));
@@ -512,7 +517,8 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
   }
   DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
   {
-    NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr};
+    NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr, 1,
+               T.max_noff()};
     ProfScope _ps(&md->prof, "nlist", st, 4);
     DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
                                    b.atom_key, b.sorted_l, b.sorted_m, nl->nl_j, nl->nl_code, nl->counts,

@@ -105,7 +105,9 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     gY[l] = ar.get<float>(N * w);
     gZ[l] = ar.get<__nv_bfloat16>(N * w);
   }
-  float* E = ar.get<float>(N);
+  // per-atom energy partials, one per output-column block of the last hidden layer (blocks are at
+  // least 64 columns wide)
+  float* E = ar.get<float>(N * ((m.fit[nh - 1].n_out + 63) / 64));
   float* gD = ar.get<float>(N * D);
   int* err = ar.get<int>(1);
   if (ar.measure) return DP_OK;
@@ -132,7 +134,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     TcArgs a = base;
     a.K = L0.n_in;
     a.N = L0.n_out;
-    a.BN = tc_pick_bn(a.N, tiles, last);
+    a.BN = tc_pick_bn(a.N, tiles);
     CUtensorMap ta;
     int rc = make_tmap_bf16(&ta, l == 0 ? (const void*)Dbf : (const void*)Yb[l - 1], N, a.K, 128);
     if (rc != DP_OK) return rc;
@@ -159,13 +161,15 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     } else {
       a.out_bf16 = gZ[l];
       a.e_out = E;
+      a.e_ld = N;
     }
     ProfScope _ps(io.prof, last ? "fit_fwd_last_tc" : "fit_fwd_tc", st);
     DP_CUDA_TRY(launch_tc_gemm(last ? TC_EPI_FWD_LAST : TC_EPI_FWD, ta, tb, a, st));
   }
   {
     ProfScope _ps(io.prof, "energy_sum", st);
-    DP_CUDA_TRY(launch_energy_f32(E, io.perm, (int)N, io.atom_energy, io.energy, io.epart, st));
+    const int bn = tc_pick_bn(m.fit[nh - 1].n_out, tiles);
+    DP_CUDA_TRY(launch_energy_f32(E, (m.fit[nh - 1].n_out + bn - 1) / bn, io.perm, (int)N, io.atom_energy, st));
   }
   // ---- backward ----
   for (int l = nh - 1; l >= 0; --l) {
@@ -173,7 +177,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     TcArgs a = base;
     a.K = L0.n_out;
     a.N = L0.n_in;
-    a.BN = tc_pick_bn(a.N, tiles, false);
+    a.BN = tc_pick_bn(a.N, tiles);
     CUtensorMap ta;
     int rc = make_tmap_bf16(&ta, gZ[l], N, a.K, 128);
     if (rc != DP_OK) return rc;

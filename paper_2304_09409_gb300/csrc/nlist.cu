@@ -23,7 +23,7 @@ namespace dpgb {
 namespace {
 
 constexpr int kNlWarps = 4;  // centre atoms (warps) per block
-constexpr int kNlEntryBytes = 24;  // shared bytes per accepted entry
+constexpr int kNlEntryBytes = 12;  // shared bytes per accepted entry
 
 __global__ void k_bbox(const double* __restrict__ coord, int n, double* __restrict__ out) {
   __shared__ double s[6][32];
@@ -217,6 +217,52 @@ __device__ __forceinline__ double exact_r2(const NlGeom& g, const double* xi, co
   return norm2_exact(d0, d1, d2);
 }
 
+// Rank of each accepted entry of one type among the entries of that type under the exact
+// total order (r^2 in FP64, then j, then the image code), and its slot in the list.  FP32 keys
+// further apart than tw order their entries directly; an entry with other keys inside its
+// window computes the exact r^2 of itself and of those partners (rare: O-H bonds, lattice
+// shells) and compares.  The keys [gs, ge) are padded with +inf to ge4 (a multiple of 4).
+// wcode_of maps the stored e_w to the wrap code of the cell the entry was seen through.
+template <class WcodeOf>
+__device__ __forceinline__ void rank_group(const NlGeom& g, int tj, int i, const double* xi,
+                                           const double* __restrict__ coord, const float4* __restrict__ sorted_l,
+                                           const int4* __restrict__ sorted_m, const int4& mi, const float* e_key,
+                                           const int* e_idx, const int* e_w, int gs, int ge, int ge4, float tw,
+                                           WcodeOf wcode_of, int lane, bool& bad_shift, int* __restrict__ nl_j,
+                                           int* __restrict__ nl_code) {
+  for (int e0 = gs; e0 < ge; e0 += 32) {
+    const int e = e0 + lane;
+    if (e >= ge) continue;
+    const float ke = e_key[e];
+    const float lo_t = ke - tw, hi_t = ke + tw;
+    int lo = 0, hi = 0;  // certainly smaller; certainly larger
+    for (int f = gs; f < ge4; f += 4) {
+      const float4 k4 = *reinterpret_cast<const float4*>(e_key + f);
+      lo += (k4.x < lo_t) + (k4.y < lo_t) + (k4.z < lo_t) + (k4.w < lo_t);
+      hi += (k4.x > hi_t) + (k4.y > hi_t) + (k4.z > hi_t) + (k4.w > hi_t);
+    }
+    int je, ce;
+    if (!entry_code(sorted_l, sorted_m, e_idx[e], wcode_of(e_w[e]), mi, je, ce)) bad_shift = true;
+    int rank = lo;
+    if (ge4 - gs - lo - hi > 1) {  // FP32 cannot order some pairs: compare their exact keys
+      const double re = exact_r2(g, xi, coord, je, ce);
+      for (int f = gs; f < ge; ++f) {
+        const float kf = e_key[f];
+        if (f == e || kf < lo_t || kf > hi_t) continue;
+        int jf, cf;
+        entry_code(sorted_l, sorted_m, e_idx[f], wcode_of(e_w[f]), mi, jf, cf);
+        const double rf = exact_r2(g, xi, coord, jf, cf);
+        rank += rf != re ? rf < re : (jf != je ? jf < je : (unsigned)cf < (unsigned)ce);
+      }
+    }
+    if (rank < g.sel[tj]) {
+      const long slot = (long)i * g.nc + g.sel_off[tj] + rank;
+      nl_j[slot] = je;
+      nl_code[slot] = ce;
+    }
+  }
+}
+
 template <int CAP>
 __global__ void __launch_bounds__(kNlWarps * 32)
     k_nlist(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, const int* __restrict__ cell_off,
@@ -227,12 +273,10 @@ __global__ void __launch_bounds__(kNlWarps * 32)
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wb = smem + (size_t)warp * (CAPP * kNlEntryBytes + 32 * sizeof(NbCell));
-  unsigned long long* e_x = reinterpret_cast<unsigned long long*>(wb);  // exact r^2 bits (window entries)
-  float* e_key = reinterpret_cast<float*>(wb + CAPP * 8);  // FP32 r^2 of each accepted entry
-  int* e_idx = reinterpret_cast<int*>(wb + CAPP * 12);     // its sorted position, then j
-  int* e_w = reinterpret_cast<int*>(wb + CAPP * 16);       // wrap code of its cell, then the image code
-  int* e_rk = reinterpret_cast<int*>(wb + CAPP * 20);      // certain part of the rank; -1 - it for window entries
-  NbCell* cells = reinterpret_cast<NbCell*>(wb + CAPP * 24);
+  float* e_key = reinterpret_cast<float*>(wb);         // FP32 r^2 of each accepted entry
+  int* e_idx = reinterpret_cast<int*>(wb + CAPP * 4);  // its sorted position
+  int* e_w = reinterpret_cast<int*>(wb + CAPP * 8);    // wrap code of the cell it was seen through
+  NbCell* cells = reinterpret_cast<NbCell*>(wb + CAPP * 12);
 
   const int w = blockIdx.x * kNlWarps + warp;
   if (w >= *n_sorted) return;  // warp-uniform; atoms of an invalid type were left out
@@ -378,58 +422,8 @@ __global__ void __launch_bounds__(kNlWarps * 32)
     const int ge4 = gs + ((max(ge - gs, 0) + 3) & ~3);
     if (ge + lane < ge4) e_key[ge + lane] = __int_as_float(0x7f800000);  // +inf: never smaller, always larger
     __syncwarp();
-    // pass 1: certain ranks from the FP32 keys; entries whose FP32 key cannot be ordered against
-    // some other entry compute their exact r^2 (all such lanes at once)
-    for (int e0 = gs; e0 < ge; e0 += 32) {
-      const int e = e0 + lane;
-      if (e < ge) {
-        const float ke = e_key[e];
-        const float lo_t = ke - tw, hi_t = ke + tw;
-        int lo = 0, hi = 0;  // certainly smaller; certainly larger
-        for (int f = gs; f < ge4; f += 4) {
-          const float4 k4 = *reinterpret_cast<const float4*>(e_key + f);
-          lo += (k4.x < lo_t) + (k4.y < lo_t) + (k4.z < lo_t) + (k4.w < lo_t);
-          hi += (k4.x > hi_t) + (k4.y > hi_t) + (k4.z > hi_t) + (k4.w > hi_t);
-        }
-        int je, ce;
-        if (!entry_code(sorted_l, sorted_m, e_idx[e], e_w[e], mi, je, ce)) bad_shift = true;
-        const bool window = ge4 - gs - lo - hi > 1;
-        if (window) e_x[e] = (unsigned long long)__double_as_longlong(exact_r2(g, xi, coord, je, ce));
-        e_idx[e] = je;
-        e_w[e] = ce;
-        e_rk[e] = window ? -1 - lo : lo;
-      }
-    }
-    __syncwarp();
-    // pass 2: window entries add the partners their exact key (r^2 bits, j, image code) puts first
-    for (int e0 = gs; e0 < ge; e0 += 32) {
-      const int e = e0 + lane;
-      if (e < ge) {
-        int rank = e_rk[e];
-        const int je = e_idx[e], ce = e_w[e];
-        if (rank < 0) {
-          rank = -1 - rank;
-          const float ke = e_key[e];
-          const float lo_t = ke - tw, hi_t = ke + tw;
-          const unsigned long long xe = e_x[e];
-          for (int f = gs; f < ge; ++f) {
-            const float kf = e_key[f];
-            if (f == e || kf < lo_t || kf > hi_t) continue;
-            const int jf = e_idx[f];
-            // f's own window test, rounded from its side, may have left f unflagged
-            const unsigned long long xf =
-                e_rk[f] < 0 ? e_x[f] : (unsigned long long)__double_as_longlong(exact_r2(g, xi, coord, jf, e_w[f]));
-            // non-negative doubles order as their bit patterns
-            rank += xf != xe ? xf < xe : (jf != je ? jf < je : (unsigned)e_w[f] < (unsigned)ce);
-          }
-        }
-        if (rank < g.sel[tj]) {
-          const long slot = (long)i * g.nc + g.sel_off[tj] + rank;
-          nl_j[slot] = je;
-          nl_code[slot] = ce;
-        }
-      }
-    }
+    rank_group(g, tj, i, xi, coord, sorted_l, sorted_m, mi, e_key, e_idx, e_w, gs, ge, ge4, tw,
+               [](int wc) { return wc; }, lane, bad_shift, nl_j, nl_code);
     // padding, counts and overflow accounting of this type
     for (int q = ng + lane; q < g.sel[tj]; q += 32) {
       const long slot = (long)i * g.nc + g.sel_off[tj] + q;
@@ -444,6 +438,240 @@ __global__ void __launch_bounds__(kNlWarps * 32)
   }
   if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
   if (cnt > CAP && lane == 0) atomicExch(&st->capacity, 1);
+}
+
+
+// =============================================================================================
+// Cell-centred search: one CTA per cell.  The candidates of every (type, surrounding cell)
+// range are staged once in shared memory, already moved into the frame of this cell's corner
+// (l_j + o), so that each warp walks them for one centre atom of the cell with a shared load and
+// three subtractions per candidate.  Membership, ranking and outputs are those of k_nlist.
+// =============================================================================================
+constexpr int kCellWarps = 8;
+constexpr int kStageMax = 1024;   // staged candidates per pass (more are staged in several passes)
+constexpr int kMaxRanges = 256;   // (type, surrounding cell) ranges of one cell
+
+__host__ __device__ constexpr size_t cell_smem_bytes(int cap) {
+  return (size_t)kStageMax * 17 + (size_t)kCellWarps * (size_t)(cap + 4 * DP_MAX_TYPES) * kNlEntryBytes;
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kCellWarps * 32)
+    k_nlist_cell(const NlGeom* __restrict__ G, const int* __restrict__ cell_off, int nframes, int ncells_total,
+                 int ntypes, const double* __restrict__ coord, const int* __restrict__ cell_start,
+                 const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m, int* __restrict__ nl_j,
+                 int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
+  constexpr int CAPP = CAP + 4 * DP_MAX_TYPES;
+  constexpr int NT = kCellWarps * 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* stg = reinterpret_cast<float4*>(smem);               // l_j + o, and the sorted index
+  unsigned char* stg_o = smem + (size_t)kStageMax * 16;         // surrounding cell of each staged entry
+  __shared__ int s_rbeg[kMaxRanges], s_rpex[kMaxRanges + 1];  // first sorted entry, stream position
+  __shared__ float4 s_off[kMaxRanges];                        // per surrounding cell: o, and its wrap code
+  __shared__ unsigned char s_rslot[kMaxRanges];
+  __shared__ int s_cbeg[DP_MAX_TYPES], s_cpre[DP_MAX_TYPES + 1], s_wsum[kCellWarps];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  unsigned char* wb = smem + (size_t)kStageMax * 17 + (size_t)warp * CAPP * kNlEntryBytes;
+  float* e_key = reinterpret_cast<float*>(wb);
+  int* e_idx = reinterpret_cast<int*>(wb + CAPP * 4);
+  int* e_w = reinterpret_cast<int*>(wb + CAPP * 8);  // surrounding cell the entry was seen through
+
+  const int gc = blockIdx.x;  // cell, all frames
+  int fr = 0;
+  if (cell_off) {  // frame holding this cell
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cell_off[mid] <= gc) lo = mid; else hi = mid - 1;
+    }
+    fr = lo;
+  }
+  const NlGeom& g = G[fr];
+  const int ci = gc - (cell_off ? cell_off[fr] : 0);
+  const int kb0 = gc - ci;  // first cell of the frame
+  if (tid == 0) {
+    int acc = 0;
+    for (int t = 0; t < ntypes; ++t) {
+      const int b = cell_start[t * ncells_total + gc];
+      s_cbeg[t] = b;
+      s_cpre[t] = acc;
+      acc += cell_start[t * ncells_total + gc + 1] - b;
+    }
+    s_cpre[ntypes] = acc;
+  }
+  __syncthreads();
+  const int nce = s_cpre[ntypes];
+  if (nce == 0) return;  // CTA-uniform: no centre atom in this cell
+  const int c2 = ci % g.ncell[2];
+  const int c1 = (ci / g.ncell[2]) % g.ncell[1];
+  const int c0 = ci / (g.ncell[2] * g.ncell[1]);
+  const int n0c = 2 * g.K[0] + 1, n1c = 2 * g.K[1] + 1, n2c = 2 * g.K[2] + 1;
+  const int noff = n0c * n1c * n2c;
+  const int R = ntypes * noff;  // <= kMaxRanges (checked on the host)
+
+  // ---- the (type, surrounding cell) ranges and their stream positions ----
+  int num = 0;
+  if (tid < R) {
+    const int t = tid / noff, o = tid - t * noff;
+    const int q0 = o / (n1c * n2c), rem = o - q0 * (n1c * n2c), q1 = rem / n2c;
+    const int d0 = q0 - g.K[0], d1 = q1 - g.K[1], d2 = rem - q1 * n2c - g.K[2];
+    int v0 = c0 + d0, v1 = c1 + d1, v2 = c2 + d2, W0 = 0, W1 = 0, W2 = 0;
+    bool inside = true;
+    if (g.periodic) {
+      while (v0 < 0) { v0 += g.ncell[0]; --W0; }
+      while (v0 >= g.ncell[0]) { v0 -= g.ncell[0]; ++W0; }
+      while (v1 < 0) { v1 += g.ncell[1]; --W1; }
+      while (v1 >= g.ncell[1]) { v1 -= g.ncell[1]; ++W1; }
+      while (v2 < 0) { v2 += g.ncell[2]; --W2; }
+      while (v2 >= g.ncell[2]) { v2 -= g.ncell[2]; ++W2; }
+    } else {
+      inside = v0 >= 0 && v1 >= 0 && v2 >= 0 && v0 < g.ncell[0] && v1 < g.ncell[1] && v2 < g.ncell[2];
+    }
+    int beg = 0;
+    if (inside) {
+      const int key = t * ncells_total + kb0 + (v0 * g.ncell[1] + v1) * g.ncell[2] + v2;
+      beg = cell_start[key];
+      num = cell_start[key + 1] - beg;
+    }
+    s_rbeg[tid] = beg;
+    s_rslot[tid] = (unsigned char)o;
+    if (t == 0) {
+      const float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
+      s_off[o] = make_float4(fmaf(e2, g.hc[6], fmaf(e1, g.hc[3], e0 * g.hc[0])),
+                             fmaf(e2, g.hc[7], fmaf(e1, g.hc[4], e0 * g.hc[1])),
+                             fmaf(e2, g.hc[8], fmaf(e1, g.hc[5], e0 * g.hc[2])), __int_as_float(pack_shift(W0, W1, W2)));
+    }
+  }
+  int incl = num;  // block-wide inclusive scan of the range sizes (R <= NT)
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += x;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  int wbase = 0;
+  for (int k = 0; k < warp; ++k) wbase += s_wsum[k];
+  if (tid < R) s_rpex[tid] = wbase + incl - num;
+  if (tid == NT - 1) s_rpex[R] = wbase + incl;  // threads >= R hold no range: this is the total
+  __syncthreads();
+  const int total = s_rpex[R];
+
+  // stage stream positions [p0, p1) of the ranges into stg[0, p1 - p0)
+  auto stage = [&](int p0, int p1) {
+    for (int p = p0 + tid; p < p1; p += NT) {
+      int lo = 0, hi = R - 1;  // last range starting at or before p (it holds p)
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_rpex[mid] <= p) lo = mid; else hi = mid - 1;
+      }
+      const int src = s_rbeg[lo] + p - s_rpex[lo];
+      const int o = s_rslot[lo];
+      const float4 lj = __ldg(sorted_l + src);
+      const float4 of = s_off[o];
+      stg[p - p0] = make_float4(lj.x + of.x, lj.y + of.y, lj.z + of.z, __int_as_float(src));
+      stg_o[p - p0] = (unsigned char)o;
+    }
+  };
+  const bool single = total <= kStageMax;
+  if (single) {
+    stage(0, total);
+    __syncthreads();
+  }
+  const float rc2_in = g.rc2_in, rc2_out = g.rc2_out, tw = g.tie_w;
+
+  for (int q0 = 0; q0 < nce; q0 += kCellWarps) {
+    const int q = q0 + warp;
+    const bool active = q < nce;  // warp-uniform
+    int w = 0;
+    if (active) {
+      int tc = 0;
+      while (tc + 1 < ntypes && s_cpre[tc + 1] <= q) ++tc;
+      w = s_cbeg[tc] + q - s_cpre[tc];
+    }
+    const float4 li = active ? sorted_l[w] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 mi = active ? sorted_m[w] : make_int4(0, 0, 0, 0);
+    const int i = __float_as_int(li.w);
+    const double* xi = coord + 3 * (active ? i : 0);
+    int cnt = 0;
+    bool bad_shift = false;
+    for (int tj = 0; tj < ntypes; ++tj) {
+      cnt = (cnt + 3) & ~3;
+      const int gs = cnt;
+      const int ts = s_rpex[tj * noff], te = s_rpex[(tj + 1) * noff];
+      for (int p0 = ts; p0 < te; p0 += kStageMax) {
+        const int p1 = min(te, p0 + kStageMax);
+        const int sb = single ? 0 : p0;  // stream position of stg[0]
+        if (!single) {  // CTA-uniform
+          __syncthreads();
+          stage(p0, p1);
+          __syncthreads();
+        }
+        if (active) {
+          for (int base = p0; base < p1; base += 32) {
+            const int p = base + lane;
+            bool pass = false;
+            int idx = 0, o = 0;
+            float r2 = 0.f;
+            if (p < p1) {
+              const float4 sj = stg[p - sb];
+              idx = __float_as_int(sj.w);
+              const float dx = sj.x - li.x, dy = sj.y - li.y, dz = sj.z - li.z;
+              r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              if (r2 <= rc2_out) {
+                o = stg_o[p - sb];
+                const int wcode = __float_as_int(s_off[o].w);
+                const bool self = idx == w && wcode == pack_shift(0, 0, 0);
+                if (r2 < rc2_in) {
+                  pass = !self;
+                } else if (!self) {  // within the FP32 error of r_c: the exact FP64 test decides
+                  int j, code;
+                  if (entry_code(sorted_l, sorted_m, idx, wcode, mi, j, code))
+                    pass = exact_r2(g, xi, coord, j, code) < g.rc2;
+                  else
+                    bad_shift = true;
+                }
+              }
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+              const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+              if (pos < CAP) {
+                e_key[pos] = r2;
+                e_idx[pos] = idx;
+                e_w[pos] = o;
+              }
+            }
+            cnt += __popc(mask);
+          }
+        }
+      }
+      if (!active) continue;
+      // ---- rank this type's entries (as in k_nlist) ----
+      const int ng = cnt - gs;
+      const int ge = min(cnt, CAP);
+      const int ge4 = gs + ((max(ge - gs, 0) + 3) & ~3);
+      if (ge + lane < ge4) e_key[ge + lane] = __int_as_float(0x7f800000);
+      __syncwarp();
+      rank_group(g, tj, i, xi, coord, sorted_l, sorted_m, mi, e_key, e_idx, e_w, gs, ge, ge4, tw,
+                 [&](int o) { return __float_as_int(s_off[o].w); }, lane, bad_shift, nl_j, nl_code);
+      for (int qq = ng + lane; qq < g.sel[tj]; qq += 32) {
+        const long slot = (long)i * g.nc + g.sel_off[tj] + qq;
+        nl_j[slot] = -1;
+        nl_code[slot] = pack_shift(0, 0, 0);
+      }
+      if (lane == 0) {
+        if (counts) counts[(long)i * g.ntypes + tj] = ng;
+        if (ng > g.sel[tj]) atomicAdd(&st->sel_overflow, 1);
+      }
+      __syncwarp();
+    }
+    if (active) {
+      if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
+      if (cnt > CAP && lane == 0) atomicExch(&st->capacity, 1);
+    }
+  }
 }
 
 // Stable partition of atoms by type (one block, one pass): each thread takes a contiguous
@@ -521,11 +749,11 @@ float round_up(double v) {
   return f;
 }
 
-// Cell edge vectors and the FP32 screening thresholds.  The walk forms the displacement as
-// (l_j - l_i) + o with l the FP32 cell-local positions (|l_d| <= A) and o the FP32 offset of a
-// surrounding cell (|o_d| <= B, three FP32 operations from the rounded edge vectors).  With
-// u = 2^-24 each component is within u (6A + 5B) of the exact FP64 displacement, plus a slack
-// for FP64 rounding of coordinates up to 1e6 A.  For |d| <= R = r_c + 1 the FP32 r^2 (three
+// Cell edge vectors and the FP32 screening thresholds.  The walks form the displacement as
+// (l_j - l_i) + o or (l_j + o) - l_i with l the FP32 cell-local positions (|l_d| <= A) and o the
+// FP32 offset of a surrounding cell (|o_d| <= B, three FP32 operations from the rounded edge
+// vectors).  With u = 2^-24 each component is within u (6A + 6B) of the exact FP64
+// displacement, plus a slack for FP64 rounding of coordinates up to 1e6 A.  For |d| <= R = r_c + 1 the FP32 r^2 (three
 // rounded operations) is then within 2 sqrt(3) R dc + 3 dc^2 + 3 u R^2 of the FP64 r^2; eps
 // doubles that.  Keys further apart than 2 eps (plus the rounding of the comparison itself)
 // keep their FP64 order.
@@ -559,7 +787,7 @@ int screening_bounds(NlGeom& g, double rc) {
   A = 1.01 * A + 1e-6;
   B = 1.01 * B + 1e-6;
   const double u = std::ldexp(1.0, -24);
-  const double dc = u * (6.0 * A + 5.0 * B) + 1e-9;
+  const double dc = u * (6.0 * A + 6.0 * B) + 1e-9;
   if (dc > 1e-2) {
     set_error("cells too large for the FP32 distance screening of the neighbour search");
     return DP_E_ARG;
@@ -660,6 +888,27 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, cell_cursor);
   k_fill<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.natoms, coord, atom_key, cell_cursor, sorted_l, sorted_m);
   const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));
+  if (L.max_noff > 0 && (long)L.max_noff * ntypes <= kMaxRanges && cap <= 512) {
+    // cell-centred search: one CTA per cell
+    const size_t csm = cell_smem_bytes(cap);
+#define DPGB_NLC_LAUNCH(C)                                                                                       \
+  do {                                                                                                           \
+    e = cudaFuncSetAttribute(k_nlist_cell<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);            \
+    if (e != cudaSuccess) return e;                                                                              \
+    k_nlist_cell<C><<<L.ncells_total, kCellWarps * 32, csm, st>>>(L.geoms, L.cell_off, L.nframes,               \
+                                                                  L.ncells_total, ntypes, coord, cell_start,     \
+                                                                  sorted_l, sorted_m, nl_j, nl_code, counts,     \
+                                                                  status);                                       \
+  } while (0)
+    if (cap == 128)
+      DPGB_NLC_LAUNCH(128);
+    else if (cap == 256)
+      DPGB_NLC_LAUNCH(256);
+    else
+      DPGB_NLC_LAUNCH(512);
+#undef DPGB_NLC_LAUNCH
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)kNlWarps * ((size_t)(cap + 4 * DP_MAX_TYPES) * kNlEntryBytes + 32 * sizeof(NbCell));
   const unsigned blocks = (L.natoms + kNlWarps - 1) / kNlWarps;
 #define DPGB_NL_LAUNCH(C)                                                                                       \

@@ -225,6 +225,17 @@ __global__ void k_sum_rows(const double* __restrict__ in, long n, int w, double*
   }
 }
 
+// Per-atom energies as nparts column-block partial sums [nparts][n] (sorted order), added in
+// a fixed order and scattered to input order in FP64.
+__global__ void k_energy_parts(const float* __restrict__ parts, int nparts, const int* __restrict__ perm, int n,
+                               double* __restrict__ atom_e) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  float e = parts[p];
+  for (int k = 1; k < nparts; ++k) e += parts[(long)k * n + p];
+  atom_e[perm[p]] = (double)e;
+}
+
 // Per-atom energies from the sorted order to input order, widened to FP64.
 template <class R>
 __global__ void k_energy(const R* __restrict__ Esorted, const int* __restrict__ perm, int n,
@@ -434,9 +445,9 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   return DP_OK;
 }
 
-cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
-                              double* epart, cudaStream_t st) {
-  k_energy<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Esorted, perm, n, atom_e);
+cudaError_t launch_energy_f32(const float* Eparts, int nparts, const int* perm, int n, double* atom_e,
+                              cudaStream_t st) {
+  k_energy_parts<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Eparts, nparts, perm, n, atom_e);
   return cudaGetLastError();
 }
 

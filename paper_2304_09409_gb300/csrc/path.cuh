@@ -177,9 +177,10 @@ template <class R>
 int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, const R* D, const PathIO& io, Arena& ar,
                 cudaStream_t st, const R** gD_out);
 cudaError_t launch_sum_rows(const double* in, long n, int w, double* out, cudaStream_t st);
-// Per-atom energies (sorted order, FP32) to input order and their FP64 sum.
-cudaError_t launch_energy_f32(const float* Esorted, const int* perm, int n, double* atom_e, double* energy,
-                              double* epart, cudaStream_t st);
+// Per-atom energies given as nparts FP32 partial sums [nparts][n] (sorted order), summed in a
+// fixed order, to input order in FP64.
+cudaError_t launch_energy_f32(const float* Eparts, int nparts, const int* perm, int n, double* atom_e,
+                              cudaStream_t st);
 // t(n) for n in {-1,0,1}^3 into out [27][3] (device)
 cudaError_t launch_shift_table(const PathConst& pc, double* out, cudaStream_t st);
 

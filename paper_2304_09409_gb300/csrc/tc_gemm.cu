@@ -1,13 +1,14 @@
 // Fitting-net GEMMs on the 5th-generation tensor cores of GB300 (sm_103a).
 //
-// One CTA (4 warps) computes a 128 x BN output tile.  Thread 0 streams 128 x 64 (A) and
-// BN x 64 (B) BF16 tiles into a 4-stage shared-memory ring with TMA (128-byte swizzle);
-// thread 32 issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) from the ring into
-// an FP32 accumulator in tensor memory and releases each stage with tcgen05.commit; after the
-// last stage all four warps read their 32 accumulator rows back with tcgen05.ld and apply the
-// layer's epilogue (bias, tanh, ResNet skip, the 1 - t^2 gate of the backward pass, the final
-// linear layer) in registers, so every layer of the fitting net -- forward and backward --
-// is a single launch.  All atom types go into one launch: their rows are contiguous and each
+// One CTA (8 warps) computes a 128 x BN output tile.  Thread 0 streams 128 x 64 (A) and
+// BN x 64 (B) BF16 tiles into a shared-memory ring (4 stages for long reductions, 2 for short
+// ones so that several CTAs share an SM) with TMA (128-byte swizzle); thread 32 issues
+// tcgen05.mma (M = 128, N = BN, K = 16 per instruction) from the ring into an FP32 accumulator
+// in tensor memory and releases each stage with tcgen05.commit; after the last stage the eight
+// warps read the accumulator back with tcgen05.ld (two warps per 32-row lane quadrant, taking
+// alternate 16-column chunks) and apply the layer's epilogue (bias, tanh, ResNet skip, the
+// 1 - t^2 gate of the backward pass, the final linear layer) in registers, so every layer of
+// the fitting net -- forward and backward -- is a single launch.  All atom types go into one launch: their rows are contiguous and each
 // tile picks its type's weight tensor map.  Every mbarrier wait is bounded: on time-out the
 // CTA records an error, waits (bounded) for its outstanding copies, frees its tensor memory
 // and returns.
@@ -22,15 +23,19 @@ namespace dpgb {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 4;  // ring stages at most
+constexpr int kThreads = 256;
 constexpr int BM = 128;
 constexpr int BK = 64;  // 64 BF16 = 128 bytes = one swizzle atom per row
 
 using namespace ptx;
 
+__host__ __device__ inline int ring_stages(int K) { return (K + BK - 1) / BK >= 8 ? kStages : 2; }
+
 template <int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ TcMaps tb, const TcArgs g) {
+  __shared__ float s_e[2][BM];  // FWD_LAST: energy partial of each row from each column half
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -38,7 +43,8 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t a_bytes = BM * BK * 2;
   const uint32_t b_bytes = (uint32_t)BN * BK * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes);
+  const int NS = ring_stages(g.K);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * stage_bytes);
   uint64_t* empty = full + kStages;
   uint64_t* accf = empty + kStages;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
@@ -54,7 +60,7 @@ __global__ void __launch_bounds__(128, 1)
   while ((int)ncols < BN) ncols <<= 1;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -73,8 +79,8 @@ __global__ void __launch_bounds__(128, 1)
     // ---- TMA producer ----
     int issued[kStages] = {0, 0, 0, 0};
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, g.err)) break;
+      const int s = kb % NS;
+      if (kb >= NS && !mbar_wait(&empty[s], ((kb / NS) - 1) & 1, g.err)) break;
       unsigned char* st = smem + s * stage_bytes;
       mbar_expect_tx(&full[s], stage_bytes);
       tma_load_2d(st, &ta, &full[s], kb * BK, row0);
@@ -82,14 +88,14 @@ __global__ void __launch_bounds__(128, 1)
       issued[s]++;
     }
     // every copy this thread started has landed before the CTA may exit
-    for (int s = 0; s < kStages; ++s)
+    for (int s = 0; s < NS; ++s)
       if (issued[s] > 0) mbar_wait(&full[s], (issued[s] - 1) & 1, g.err);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     const uint32_t idesc = idesc_f16(BM, BN, 1);
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      if (!mbar_wait(&full[s], (kb / kStages) & 1, g.err)) break;
+      const int s = kb % NS;
+      if (!mbar_wait(&full[s], (kb / NS) & 1, g.err)) break;
       tc_fence_after();
       const uint32_t sa = su32(smem + s * stage_bytes);
       const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sa + a_bytes);
@@ -101,14 +107,15 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  // ---- epilogue: warp w owns accumulator rows 32w .. 32w+31 ----
+  // ---- epilogue: warps w and w + 4 own accumulator rows 32(w % 4) .. +31, alternate chunks ----
   mbar_wait(accf, 0, g.err);
   tc_fence_after();
-  const int row = row0 + warp * 32 + lane;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = row0 + quad * 32 + lane;
   const bool rv = row < row_end;
-  const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
   float e_acc = 0.f;
-  for (int c = 0; c < BN; c += 16) {
+  for (int c = half * 16; c < BN; c += 32) {
     float v[16];
     tmem_ld16(tbase + c, v);
     const int cb = col0 + c;
@@ -221,9 +228,12 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
-  if (EPI == TC_EPI_FWD_LAST && rv) g.e_out[row] = e_acc + g.b_last[t];
+  if (EPI == TC_EPI_FWD_LAST) s_e[half][quad * 32 + lane] = e_acc;
   tc_fence_before();
   __syncthreads();
+  if (EPI == TC_EPI_FWD_LAST && half == 0 && rv)
+    g.e_out[(long)blockIdx.y * g.e_ld + row] =
+        s_e[0][quad * 32 + lane] + s_e[1][quad * 32 + lane] + (blockIdx.y == 0 ? g.b_last[t] : 0.f);
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
@@ -264,10 +274,9 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int
   return DP_OK;
 }
 
-int tc_pick_bn(int N, int row_tiles, bool full_row) {
+int tc_pick_bn(int N, int row_tiles) {
   int bn = ((N + 15) / 16) * 16;
   if (bn > 256) bn = 256;
-  if (full_row) return bn;
   while (bn > 64 && (long)row_tiles * ((N + bn - 1) / bn) < 2L * 152) bn = ((bn / 2 + 15) / 16) * 16;
   return bn;
 }
@@ -276,24 +285,24 @@ cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, con
   const int tiles = a.tile_start[a.ntypes];
   if (tiles <= 0) return cudaSuccess;
   dim3 grid(tiles, (a.N + a.BN - 1) / a.BN);
-  const size_t smem = (size_t)kStages * (BM * BK * 2 + (size_t)a.BN * BK * 2) + 1024 + 256;
+  const size_t smem = (size_t)ring_stages(a.K) * (BM * BK * 2 + (size_t)a.BN * BK * 2) + 1024 + 256;
   cudaError_t e = cudaSuccess;
   switch (epi) {
     case TC_EPI_PLAIN:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_PLAIN><<<grid, 128, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_PLAIN><<<grid, kThreads, smem, st>>>(ta, tb, a);
       break;
     case TC_EPI_FWD:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD><<<grid, 128, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD><<<grid, kThreads, smem, st>>>(ta, tb, a);
       break;
     case TC_EPI_FWD_LAST:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_FWD_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD_LAST><<<grid, 128, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD_LAST><<<grid, kThreads, smem, st>>>(ta, tb, a);
       break;
     default:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_BWD><<<grid, 128, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_BWD><<<grid, kThreads, smem, st>>>(ta, tb, a);
       break;
   }
   if (e != cudaSuccess) return e;

@@ -37,7 +37,8 @@ struct TcArgs {
   float* out_f32;           // [rows][N]
   __nv_bfloat16* out_bf16;  // [rows][N]
   float* out_t;             // [rows][N]
-  float* e_out;             // FWD_LAST: per-row energy [rows]
+  float* e_out;             // FWD_LAST: per-row energy partial of each column block [col blocks][e_ld]
+  long e_ld;
   int* err;                 // device error word (bounded waits)
 };
 
@@ -49,6 +50,6 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int
 cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st);
 
 // Output columns per CTA for an N-wide output with `row_tiles` 128-row tiles in total.
-int tc_pick_bn(int N, int row_tiles, bool full_row);
+int tc_pick_bn(int N, int row_tiles);
 
 }  // namespace dpgb
