@@ -141,6 +141,77 @@ def _traffic(kernel: str):
     return None
 
 
+def _candidate_pairs(frame, rc):
+    """Candidate pairs a cell-list search with cells at least r_c wide tests: for every atom,
+    the atoms of the 27 cells around its own (the grid of the GPU builder, K = 1)."""
+    box = np.asarray(frame.box, dtype=np.float64)
+    inv = np.linalg.inv(box)
+    vol = abs(np.linalg.det(box))
+    n = []
+    for d in range(3):
+        u, v = box[(d + 1) % 3], box[(d + 2) % 3]
+        width = vol / np.linalg.norm(np.cross(u, v))
+        n.append(max(1, min(256, int(np.floor(width / (rc * (1 + 1e-9) + 1e-9))))))
+    f = frame.coord @ inv
+    f -= np.floor(f)
+    c = np.minimum((f * np.array(n)).astype(np.int64), np.array(n) - 1)
+    counts = np.zeros(n, dtype=np.int64)
+    np.add.at(counts, (c[:, 0], c[:, 1], c[:, 2]), 1)
+    around = np.zeros_like(counts)
+    for d0 in (-1, 0, 1):
+        for d1 in (-1, 0, 1):
+            for d2 in (-1, 0, 1):
+                around += np.roll(counts, (d0, d1, d2), axis=(0, 1, 2))
+    return int((counts * around).sum())
+
+
+def _kernel_rooflines(cfg, big, real_nb, prof, steps, peaks):
+    """Roofline of each timed scope.  Algorithmic work per launch:
+      nlist      FP32 ALU: 8 FLOP (3 sub, 3 mul, 2 add) per candidate pair of the 27-cell stencil
+      env        HBM: list read 8 B/slot, (ds, r, tau, l) 16 B/slot, (s, u) 16 B + run index 4 B per
+                 real neighbour, coordinates 24 B/atom (run moment records not counted)
+      mom_fwd    FP32-ALU equivalent of the compressed contraction: 18 M FLOP per real neighbour
+                 (quintic 5 FMA + outer product 4 FMA per output m), run as tensor-core MMAs
+      mom_bwd    36 M FLOP per real neighbour (G' 4 FMA, dE/dR 4, dE/dG 4, dE/ds 1, ... per m)
+      mom_gT     HBM: dE/dD read 4 M M_< B/atom, T and T_< 16 (M + M_<) B/atom
+      mom_force  HBM: env rows 32 B + run index 4 B per real neighbour, run P 32 B per real
+                 neighbour (upper bound of runs), force and virial 96 B/atom
+      fit_*      tensor: 2 rows K N per GEMM of the scope
+    Peaks: FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz; HBM and BF16 tensor as measured (the
+    sustained tensor figure: these kernels run inside a long step)."""
+    N = big.natoms
+    nc = int(sum(cfg.sel))
+    M, A = cfg.m, cfg.axis
+    fit = [M * A] + list(cfg.fit)
+    fwd = sum(2 * N * fit[k] * fit[k + 1] for k in range(len(fit) - 2))
+    fwd_last = 2 * N * fit[-2] * fit[-1]
+    bwd = sum(2 * N * fit[k] * fit[k + 1] for k in range(len(fit) - 1))
+    pairs = _candidate_pairs(big, cfg.rcut)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ten = peaks.get("bf16_tflops_sustained", 1700.0)
+    work = {
+        "nlist": ("alu", 8.0 * pairs / 1e12, ALU_FP32_PEAK_TFLOPS, "TFLOP/s"),
+        "env": ("hbm", (N * nc * 24 + real_nb * 20 + N * 24) / 1e9, hbm, "GB/s"),
+        "mom_fwd": ("alu", 18.0 * M * real_nb / 1e12, ALU_FP32_PEAK_TFLOPS, "TFLOP/s"),
+        "mom_bwd": ("alu", 36.0 * M * real_nb / 1e12, ALU_FP32_PEAK_TFLOPS, "TFLOP/s"),
+        "mom_gT": ("hbm", (N * (4 * M * A + 16 * (M + A))) / 1e9, hbm, "GB/s"),
+        "mom_force": ("hbm", (real_nb * 68 + N * 96) / 1e9, hbm, "GB/s"),
+        "fit_fwd_tc": ("tensor", fwd / 1e12, ten, "TFLOP/s"),
+        "fit_fwd_last_tc": ("tensor", fwd_last / 1e12, ten, "TFLOP/s"),
+        "fit_bwd_tc": ("tensor", bwd / 1e12, ten, "TFLOP/s"),
+    }
+    out = {}
+    for name, (ms_tot, nl) in prof.items():
+        if name not in work:
+            continue
+        bound, amount, peak, unit = work[name]
+        t_step = ms_tot / max(steps, 1) * 1e-3  # every listed scope runs once per step
+        ach = amount / t_step
+        out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                     "us_per_step": t_step * 1e6, "launches_per_step": nl / max(steps, 1)}
+    return out, pairs
+
+
 def _real_neighbours(cfg, frame, model):
     nl = model.build_nlist(frame.coord, frame.atype, frame.box)
     nj, _ = nl.export()
@@ -394,27 +465,16 @@ def run_ours(args):
     e2e_ms = e2e_total / args.steps * 1e3
     e2e_value = world * big.natoms / (e2e_ms * 1e-3)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (the scope with the largest time per step)
     peaks, peak_src = _peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
-    dom_avg_s = dom_ms / max(dom_n, 1) * 1e-3
-    M, A = cfg.m, cfg.axis
-    if dom_name == "tab_bwd":
-        # per real neighbour and output m: G (5 FMA), G' (4 FMA), dE/dR (4 FMA), dE/dG (4 FMA), dE/ds (1 FMA)
-        flops = real_nb * M * 36
-        roof = {"bound": "alu", "achieved": flops / dom_avg_s / 1e12, "peak": ALU_FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
-    elif dom_name == "tab_fwd":
-        flops = real_nb * M * 18  # G (5 FMA) + outer product (4 FMA)
-        roof = {"bound": "alu", "achieved": flops / dom_avg_s / 1e12, "peak": ALU_FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": ALU_FP32_PEAK_TFLOPS, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
+    table, pairs = _kernel_rooflines(cfg, big, real_nb, prof, args.steps, peaks)
+    dom_name = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    roof = dict(table.get(dom_name, {"bound": "alu", "achieved": None, "peak": ALU_FP32_PEAK_TFLOPS,
+                                     "unit": "TFLOP/s", "frac": None}))
     roof["kernel"] = dom_name
-    roof["avg_launch_us"] = dom_avg_s * 1e6
     roof["traffic"] = _traffic(dom_name)
+    roof["peak_source"] = ("measured" if peak_src == "measured" else "fallback") + (
+        "" if roof["bound"] != "alu" else "; alu: derived 152 SM x 128 FP32 lanes x 2 x 2070 MHz")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -429,6 +489,8 @@ def run_ours(args):
                          "force_err_vs_fp64_gpu": v["force_err"]} for k, v in cands.items()}},
         "speedup_vs_fp64_gpu": ms64 / ms_max,
         "roofline": roof,
+        "kernel_rooflines": table,
+        "candidate_pairs": pairs, "real_neighbours": real_nb,
         "kernels_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hc.nbytes + ht.nbytes),
                 "d2h_bytes_per_step": int(hout[1].nbytes + 8 + 72)},

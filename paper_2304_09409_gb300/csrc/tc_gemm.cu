@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads)
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
-    int issued[kStages] = {0, 0, 0, 0};
+    int nissued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % NS;
       if (kb >= NS && !mbar_wait(&empty[s], ((kb / NS) - 1) & 1, g.err)) break;
@@ -85,11 +85,14 @@ __global__ void __launch_bounds__(kThreads)
       mbar_expect_tx(&full[s], stage_bytes);
       tma_load_2d(st, &ta, &full[s], kb * BK, row0);
       tma_load_2d(st + a_bytes, &tb.m[t], &full[s], kb * BK, col0);
-      issued[s]++;
+      nissued = kb + 1;
     }
-    // every copy this thread started has landed before the CTA may exit
-    for (int s = 0; s < NS; ++s)
-      if (issued[s] > 0) mbar_wait(&full[s], (issued[s] - 1) & 1, g.err);
+    // every copy this thread started has landed before the CTA may exit: the last block issued
+    // to stage s is s + NS * ((nissued - 1 - s) / NS)
+    for (int s = 0; s < NS && s < nissued; ++s) {
+      const int last = s + NS * ((nissued - 1 - s) / NS);
+      mbar_wait(&full[s], (last / NS) & 1, g.err);
+    }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     const uint32_t idesc = idesc_f16(BM, BN, 1);
