@@ -83,8 +83,22 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+void drop_graph(dp_model* md) {
+  DpGraph& g = md->graph;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  for (auto& r : g.prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g.prof.clear();
+  g.sig.clear();
+  g.launches = 0;
+}
+
 int ensure_ws(dp_model* md, size_t bytes) {
   if (bytes <= md->ws_cap) return DP_OK;
+  drop_graph(md);  // a recorded graph points into the old scratch
   if (md->ws) {
     DP_CUDA_TRY(cudaDeviceSynchronize());
     cudaFree(md->ws);
@@ -107,6 +121,7 @@ int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
     set_error("atom type outside [0, ntypes)");
     return DP_E_ARG;
   }
+  if (s.type_change) return kStatusTypeChange;
   if (s.capacity == 2) {
     set_error("periodic image index beyond +-511 cells: coordinates too far outside the box");
     return DP_E_ARG;
@@ -396,6 +411,9 @@ int dp_free_model(dp_model* md) {
   cudaFree(md->status);
   if (md->status_host) cudaFreeHost(md->status_host);
   if (md->stage) cudaFreeHost(md->stage);
+  drop_graph(md);
+  if (md->graph.stage) cudaFreeHost(md->graph.stage);
+  if (md->cap_st) cudaStreamDestroy(md->cap_st);
   delete md;
   return DP_OK;
 }

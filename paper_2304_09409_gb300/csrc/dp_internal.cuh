@@ -137,6 +137,14 @@ struct DevStatus {
   int table_range;    // compressed: an s outside the table
   int bad_type;       // a type outside [0, ntypes)
   int timeout;        // a bounded wait of a tensor-core kernel gave up
+  int type_change;    // the per-type atom counts differ from the ones the call was set up with
+};
+
+// Per-type starts of the type-sorted atom order that a call was set up with (checked on the
+// device against the counts of the types actually given).
+struct TypeStartCheck {
+  int on;
+  int v[DP_MAX_TYPES + 1];
 };
 
 // ------------------------------------------------------------------------------------------
@@ -162,7 +170,8 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
                                int* cell_count, int* cell_start, int* cell_cursor, int* atom_key, float4* sorted_l,
                                int4* sorted_m, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st);
-cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, int* bad_type,
+cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, DevStatus* status,
+                             const TypeStartCheck& chk,
                              cudaStream_t st);
 
 // ------------------------------------------------------------------------------------------

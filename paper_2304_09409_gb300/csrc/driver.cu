@@ -330,94 +330,217 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   carve_grad(ar);
   const double* dcoord = copy_coord ? b.coord : coord;
   const int* dtype = copy_type ? b.type : type;
-  if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
-  if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-  if (g_a_host) DP_CUDA_TRY(cudaMemcpyAsync(d_ga, gr->g_energy, sizeof(double) * F, cudaMemcpyHostToDevice, st));
-  if (g_w_host) DP_CUDA_TRY(cudaMemcpyAsync(d_gw, gr->g_force, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
-  T.pack(md->stage);
-  DP_CUDA_TRY(cudaMemcpyAsync(b.ftab, md->stage, T.bytes, cudaMemcpyHostToDevice, st));
-  const NlGeom* d_geoms = reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms);
-  const int* d_celloff = reinterpret_cast<const int*>(b.ftab + T.off_celloff);
-  const int* d_start = reinterpret_cast<const int*>(b.ftab + T.off_start);
-  const int* d_chunk = reinterpret_cast<const int*>(b.ftab + T.off_chunk);
-  const int* d_fchunk = reinterpret_cast<const int*>(b.ftab + T.off_fchunk);
-  const double* d_boxes = reinterpret_cast<const double*>(b.ftab + T.off_boxes);
-  DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
-  if (F > 1) {
-    ProfScope _ps(&md->prof, "atom_frame", st);
-    k_atom_frame<<<(N + 255) / 256, 256, 0, st>>>(d_start, F, N, b.atom_frame);
-  }
-  if (own_nlist) {
-    NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff()};
-    ProfScope _ps(&md->prof, "nlist", st, 4);
-    DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
-                                   b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, st));
-  }
-  {
-    ProfScope _ps(&md->prof, "type_perm", st);
-    DP_CUDA_TRY(launch_type_perm(dtype, N, m.cfg.ntypes, b.perm, b.type_start, &md->status->bad_type, st));
-  }
-  rc = type_starts(copy_type ? type : nullptr, b.type_start, N, m.cfg.ntypes, st, io.type_start);
-  if (rc != DP_OK) return rc;
-  pc.nframes = F;
-  pc.periodic = T.periodic;
-  pc.atom_frame = b.atom_frame;
-  pc.boxes = F > 1 ? d_boxes : nullptr;
-  for (int k = 0; k < 9; ++k) pc.h[k] = T.geoms[0].h[k];
-  if (T.periodic) {
-    pc.tshift = b.tshift;
-    ProfScope _ps(&md->prof, "shift_table", st);
-    k_shift_tables<<<F, 32, 0, st>>>(d_boxes, b.tshift);
-  }
-  io.prof = &md->prof;
-  io.coord = dcoord;
-  io.type = dtype;
-  io.perm = b.perm;
-  io.nl_j = own_nlist ? b.nl_j : nlist->nl_j;
-  io.nl_code = own_nlist ? b.nl_code : nlist->nl_code;
-  io.force = host_f ? b.force : force;
-  io.atom_energy = dev_ae ? atom_energy : b.atom_energy;
-  io.atom_virial = b.atom_virial;
-  io.status = md->status;
-  io.epart = b.epart;
-  if (gr) {
-    {
-      ProfScope _ps(&md->prof, "param_grad", st);
-      rc = run_param_grad(m, pc, io, d_gw, d_ga, -1.0, d_gout, ar, st);
-    }
+
+  // per-type starts of the type-sorted order: counted here for host types, the counts of the
+  // last call for the same device array (checked on the device), else read back mid-call
+  TypeStartCheck chk;
+  std::memset(&chk, 0, sizeof(chk));
+  bool ts_known = false;
+  if (copy_type) {
+    rc = type_starts(type, nullptr, N, m.cfg.ntypes, st, io.type_start);
     if (rc != DP_OK) return rc;
-    if (g_out_host)
-      DP_CUDA_TRY(cudaMemcpyAsync(gr->grad, d_gout, sizeof(double) * m.n_params, cudaMemcpyDeviceToHost, st));
-    rc = read_status(md, st, nullptr);
-    if (rc == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
-      md->nl_full_cap = true;
+    ts_known = true;
+  } else if (md->ts_ptr == type && md->ts_n == N) {
+    for (int t = 0; t <= m.cfg.ntypes; ++t) io.type_start[t] = md->ts_v[t];
+    ts_known = true;
+  }
+  if (ts_known) {
+    chk.on = 1;
+    for (int t = 0; t <= m.cfg.ntypes; ++t) chk.v[t] = io.type_start[t];
+  }
+
+  // All device work of the call, in stream order on s (tables uploaded from `stage`); the
+  // path's scratch is carved afresh from the same arena position every time.
+  const size_t ar_used0 = ar.used;
+  auto enqueue = [&](cudaStream_t s, unsigned char* stage) -> int {
+    ar.used = ar_used0;
+    ar.fail = false;
+    if (copy_coord) DP_CUDA_TRY(cudaMemcpyAsync(b.coord, coord, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    if (g_a_host) DP_CUDA_TRY(cudaMemcpyAsync(d_ga, gr->g_energy, sizeof(double) * F, cudaMemcpyHostToDevice, s));
+    if (g_w_host) DP_CUDA_TRY(cudaMemcpyAsync(d_gw, gr->g_force, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    T.pack(stage);
+    DP_CUDA_TRY(cudaMemcpyAsync(b.ftab, stage, T.bytes, cudaMemcpyHostToDevice, s));
+    const NlGeom* d_geoms = reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms);
+    const int* d_celloff = reinterpret_cast<const int*>(b.ftab + T.off_celloff);
+    const int* d_start = reinterpret_cast<const int*>(b.ftab + T.off_start);
+    const int* d_chunk = reinterpret_cast<const int*>(b.ftab + T.off_chunk);
+    const int* d_fchunk = reinterpret_cast<const int*>(b.ftab + T.off_fchunk);
+    const double* d_boxes = reinterpret_cast<const double*>(b.ftab + T.off_boxes);
+    DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), s));
+    if (F > 1) {
+      ProfScope _ps(&md->prof, "atom_frame", s);
+      k_atom_frame<<<(N + 255) / 256, 256, 0, s>>>(d_start, F, N, b.atom_frame);
+    }
+    if (own_nlist) {
+      NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff()};
+      ProfScope _ps(&md->prof, "nlist", s, 4);
+      DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
+                                     b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, s));
+    }
+    {
+      ProfScope _ps(&md->prof, "type_perm", s);
+      DP_CUDA_TRY(launch_type_perm(dtype, N, m.cfg.ntypes, b.perm, b.type_start, md->status, chk, s));
+    }
+    if (!ts_known) {  // first call on this device type array: read the counts back (synchronises)
+      int r = type_starts(nullptr, b.type_start, N, m.cfg.ntypes, s, io.type_start);
+      if (r != DP_OK) return r;
+      md->ts_ptr = type;
+      md->ts_n = N;
+      for (int t = 0; t <= m.cfg.ntypes; ++t) md->ts_v[t] = io.type_start[t];
+    }
+    pc.nframes = F;
+    pc.periodic = T.periodic;
+    pc.atom_frame = b.atom_frame;
+    pc.boxes = F > 1 ? d_boxes : nullptr;
+    for (int k = 0; k < 9; ++k) pc.h[k] = T.geoms[0].h[k];
+    if (T.periodic) {
+      pc.tshift = b.tshift;
+      ProfScope _ps(&md->prof, "shift_table", s);
+      k_shift_tables<<<F, 32, 0, s>>>(d_boxes, b.tshift);
+    }
+    io.prof = &md->prof;
+    io.coord = dcoord;
+    io.type = dtype;
+    io.perm = b.perm;
+    io.nl_j = own_nlist ? b.nl_j : nlist->nl_j;
+    io.nl_code = own_nlist ? b.nl_code : nlist->nl_code;
+    io.force = host_f ? b.force : force;
+    io.atom_energy = dev_ae ? atom_energy : b.atom_energy;
+    io.atom_virial = b.atom_virial;
+    io.status = md->status;
+    io.epart = b.epart;
+    if (gr) {
+      {
+        ProfScope _ps(&md->prof, "param_grad", s);
+        int r = run_param_grad(m, pc, io, d_gw, d_ga, -1.0, d_gout, ar, s);
+        if (r != DP_OK) return r;
+      }
+      if (g_out_host)
+        DP_CUDA_TRY(cudaMemcpyAsync(gr->grad, d_gout, sizeof(double) * m.n_params, cudaMemcpyDeviceToHost, s));
+      return DP_OK;
+    }
+    DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, s));
+    if (!m.compressed) DP_CUDA_TRY(cudaMemsetAsync(io.atom_virial, 0, sizeof(double) * 9 * N, s));
+    int r = run_path(m, pc, io, ar, s);
+    if (r != DP_OK) return r;
+    double* d_energy = host_e ? b.energy : energy;
+    double* d_virial = host_v ? b.virial : virial;
+    {
+      ProfScope _ps(&md->prof, "frame_sums", s, 2);
+      k_chunk_sums<<<T.C, 256, 0, s>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
+      k_frame_sums<<<F, 32, 0, s>>>(d_fchunk, b.cpart, d_energy, d_virial);
+    }
+    DP_CUDA_TRY(cudaGetLastError());
+    if (host_e) DP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
+    if (host_v) DP_CUDA_TRY(cudaMemcpyAsync(virial, d_virial, sizeof(double) * 9 * F, cudaMemcpyDeviceToHost, s));
+    if (host_f) DP_CUDA_TRY(cudaMemcpyAsync(force, io.force, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s));
+    if (atom_energy && !dev_ae)
+      DP_CUDA_TRY(cudaMemcpyAsync(atom_energy, io.atom_energy, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    return DP_OK;
+  };
+
+  // After the call: a changed type count or an overflowing candidate buffer re-runs it.
+  auto finish = [&](int r) -> int {
+    if (r == kStatusTypeChange) {
+      md->ts_ptr = nullptr;
+      md->ts_n = -1;
+      drop_graph(md);
       return run_frames(md, nlist, F, natoms, coord, type, boxes, energy, force, virial, atom_energy, st, gr);
     }
-    return rc;
+    if (r == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
+      md->nl_full_cap = true;  // retry once with the full candidate buffer
+      drop_graph(md);
+      return run_frames(md, nlist, F, natoms, coord, type, boxes, energy, force, virial, atom_energy, st, gr);
+    }
+    return r;
+  };
+
+  // Repeated call shapes (same sizes, buffers and cell) replay one CUDA graph of the whole call:
+  // recorded on the second call of a shape, replayed from the third.  Host buffers must be
+  // pinned (the graph's copies read them at replay).
+  std::vector<unsigned long long> sig;
+  bool graphable = !gr && ts_known && boxes;
+  auto pinned_or_device = [](const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost;
+  };
+  if (graphable)
+    graphable = pinned_or_device(coord) && pinned_or_device(type) && pinned_or_device(energy) &&
+                pinned_or_device(force) && pinned_or_device(virial) && pinned_or_device(atom_energy);
+  if (graphable) {
+    auto put = [&](const void* p) { sig.push_back((unsigned long long)(uintptr_t)p); };
+    sig.push_back((unsigned long long)F);
+    for (int f = 0; f < F; ++f) sig.push_back((unsigned long long)natoms[f]);
+    put(coord); put(type); put(energy); put(force); put(virial); put(atom_energy); put(nlist); put(md->ws);
+    for (int k = 0; k < 9 * F; ++k) {
+      unsigned long long u;
+      std::memcpy(&u, boxes + k, 8);
+      sig.push_back(u);
+    }
+    for (int t = 0; t <= m.cfg.ntypes; ++t) sig.push_back((unsigned long long)(unsigned)chk.v[t]);
+    sig.push_back((unsigned long long)md->nl_full_cap | ((unsigned long long)md->prof.timing << 1));
+    sig.push_back((unsigned long long)(copy_coord | (copy_type << 1) | (host_e << 2) | (host_v << 3) |
+                                       (host_f << 4) | (dev_ae << 5)));
   }
-  DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, st));
-  if (!m.compressed) DP_CUDA_TRY(cudaMemsetAsync(io.atom_virial, 0, sizeof(double) * 9 * N, st));
-  rc = run_path(m, pc, io, ar, st);
+  DpGraph& G = md->graph;
+  if (graphable && G.exec && G.sig == sig) {  // replay
+    DP_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+    md->prof.launches += G.launches;
+    int r = read_status(md, st, nullptr);
+    if (md->prof.timing) md->prof.collect_from(G.prof);
+    return finish(r);
+  }
+  if (graphable && sig == md->last_sig) {  // second call of this shape: record it
+    drop_graph(md);
+    if (!md->cap_st) DP_CUDA_TRY(cudaStreamCreateWithFlags(&md->cap_st, cudaStreamNonBlocking));
+    if (G.stage_cap < T.bytes) {
+      if (G.stage) cudaFreeHost(G.stage);
+      G.stage = nullptr;
+      G.stage_cap = 0;
+      DP_CUDA_TRY(cudaMallocHost(&G.stage, T.bytes + 4096));
+      G.stage_cap = T.bytes + 4096;
+    }
+    const long l0 = md->prof.launches;
+    const size_t p0 = md->prof.pending.size();
+    DP_CUDA_TRY(cudaStreamBeginCapture(md->cap_st, cudaStreamCaptureModeRelaxed));
+    int r = enqueue(md->cap_st, G.stage);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(md->cap_st, &graph);
+    cudaError_t ie = cudaErrorUnknown;
+    if (r == DP_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&G.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    // timing events recorded during capture belong to the graph now
+    G.prof.assign(md->prof.pending.begin() + (long)p0, md->prof.pending.end());
+    md->prof.pending.resize(p0);
+    G.launches = md->prof.launches - l0;
+    md->prof.launches = l0;
+    if (r == DP_OK && ie == cudaSuccess) {
+      G.sig = sig;
+      DP_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+      md->prof.launches += G.launches;
+      int r2 = read_status(md, st, nullptr);
+      if (md->prof.timing) md->prof.collect_from(G.prof);
+      return finish(r2);
+    }
+    drop_graph(md);  // recording failed: run the call directly (and do not try this shape again)
+    md->last_sig.clear();
+    rc = ensure_stage(md, T.bytes);
+    if (rc != DP_OK) return rc;
+    rc = enqueue(st, md->stage);
+    if (rc != DP_OK) return rc;
+    return finish(read_status(md, st, nullptr));
+  }
+  md->last_sig = sig;
+  rc = enqueue(st, md->stage);
   if (rc != DP_OK) return rc;
-  double* d_energy = host_e ? b.energy : energy;
-  double* d_virial = host_v ? b.virial : virial;
-  {
-    ProfScope _ps(&md->prof, "frame_sums", st, 2);
-    k_chunk_sums<<<T.C, 256, 0, st>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
-    k_frame_sums<<<F, 32, 0, st>>>(d_fchunk, b.cpart, d_energy, d_virial);
-  }
-  DP_CUDA_TRY(cudaGetLastError());
-  if (host_e) DP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
-  if (host_v) DP_CUDA_TRY(cudaMemcpyAsync(virial, d_virial, sizeof(double) * 9 * F, cudaMemcpyDeviceToHost, st));
-  if (host_f) DP_CUDA_TRY(cudaMemcpyAsync(force, io.force, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, st));
-  if (atom_energy && !dev_ae)
-    DP_CUDA_TRY(cudaMemcpyAsync(atom_energy, io.atom_energy, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-  rc = read_status(md, st, nullptr);
-  if (rc == DP_E_CAPACITY && own_nlist && !md->nl_full_cap) {
-    md->nl_full_cap = true;  // retry once with the full candidate buffer
-    return run_frames(md, nlist, F, natoms, coord, type, boxes, energy, force, virial, atom_energy, st);
-  }
-  return rc;
+  return finish(read_status(md, st, nullptr));
 }
 
 }  // namespace

@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(kCellWarps * 32)
 // thread its output offset per type.  perm[p] = atom index, type_start[t].
 __global__ void __launch_bounds__(1024)
     k_type_perm(const int* __restrict__ type, int n, int ntypes, int* __restrict__ perm, int* __restrict__ type_start,
-                int* __restrict__ bad_type) {
+                DevStatus* __restrict__ status, const TypeStartCheck chk) {
   __shared__ int wtot[32][DP_MAX_TYPES];
   __shared__ int tstart[DP_MAX_TYPES + 1];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
@@ -730,7 +730,8 @@ __global__ void __launch_bounds__(1024)
     for (int q = 0; q < DP_MAX_TYPES; ++q)
       if (t == q && q < ntypes) perm[off[q]++] = i;
   }
-  if (bad) atomicExch(bad_type, 1);
+  if (bad) atomicExch(&status->bad_type, 1);
+  if (chk.on && tid <= ntypes && tstart[tid] != chk.v[tid]) atomicExch(&status->type_change, 1);
   if (tid <= ntypes) type_start[tid] = tstart[tid];
 }
 
@@ -931,9 +932,10 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   return cudaGetLastError();
 }
 
-cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, int* bad_type,
+cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, DevStatus* status,
+                             const TypeStartCheck& chk,
                              cudaStream_t st) {
-  k_type_perm<<<1, 1024, 0, st>>>(type, natoms, ntypes, perm, type_start, bad_type);
+  k_type_perm<<<1, 1024, 0, st>>>(type, natoms, ntypes, perm, type_start, status, chk);
   return cudaGetLastError();
 }
 

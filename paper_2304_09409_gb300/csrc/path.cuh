@@ -67,6 +67,17 @@ struct Prof {
     pending.clear();
     cudaGetLastError();
   }
+  // Fold the timings of events recorded inside a graph replay (the events stay with the graph).
+  void collect_from(const std::vector<Rec>& recs) {
+    for (const Rec& r : recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        total_ms[r.id] += ms;
+        count[r.id] += 1;
+      }
+    }
+    cudaGetLastError();
+  }
   void reset() {
     collect();
     for (auto& t : total_ms) t = 0.0;
@@ -94,12 +105,22 @@ struct ProfScope {
       id = p->id_of(name);
       a = p->ev();
       b = p->ev();
-      cudaEventRecord(a, st);
+      record(a);
     }
+  }
+  // Inside a stream capture the record must be external, so that it becomes a graph node that
+  // records on every replay (a plain record would only order the capture).
+  void record(cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, st);
   }
   ~ProfScope() {
     if (p && p->timing) {
-      cudaEventRecord(b, st);
+      record(b);
       p->pending.push_back(Prof::Rec{id, a, b});
     }
   }
