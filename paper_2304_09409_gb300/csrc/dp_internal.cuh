@@ -164,12 +164,23 @@ struct NlLaunch {
   int nframes;            // frames in the launch
   int max_noff;           // largest (2K_0+1)(2K_1+1)(2K_2+1) over the frames
 };
+// What a path call also takes from the list build: the (type, cell) order of the atoms as its
+// type-sorted order (perm [natoms], type_start [ntypes + 1], checked against chk) and the 27
+// image translations of every frame (tshift [nframes][27][3] from boxes [nframes][9]).
+struct NlExtras {
+  int* perm;
+  int* type_start;
+  TypeStartCheck chk;
+  const double* boxes;
+  int nframes;
+  double* tshift;
+};
 // Cell arrays are indexed by (type, cell): cell_count, cell_cursor [ntypes * ncells_total],
 // cell_start [ntypes * ncells_total + 1]; atom_key [natoms]; sorted_l, sorted_m [natoms].
 cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
                                int* cell_count, int* cell_start, int* cell_cursor, int* atom_key, float4* sorted_l,
                                int4* sorted_m, int* nl_j, int* nl_code, int* counts, DevStatus* status,
-                               cudaStream_t st);
+                               cudaStream_t st, const NlExtras* ex = nullptr);
 cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, DevStatus* status,
                              const TypeStartCheck& chk,
                              cudaStream_t st);

@@ -19,7 +19,7 @@ namespace dpgb {
 
 namespace {
 
-constexpr int kChunk = 512;
+constexpr int kChunk = 128;  // atoms per fixed-order partial sum of the per-frame energy and virial
 
 __global__ void k_atom_frame(const int* __restrict__ frame_start, int F, int N, int* __restrict__ atom_frame) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,12 +373,15 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
       k_atom_frame<<<(N + 255) / 256, 256, 0, s>>>(d_start, F, N, b.atom_frame);
     }
     if (own_nlist) {
+      // the list build's (type, cell) order is the path's type-sorted order, and its first
+      // launch also forms the image translations
       NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff()};
+      NlExtras ex{b.perm, b.type_start, chk, d_boxes, T.periodic ? F : 0, T.periodic ? b.tshift : nullptr};
       ProfScope _ps(&md->prof, "nlist", s, 4);
       DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
-                                     b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, s));
-    }
-    {
+                                     b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, s,
+                                     &ex));
+    } else {
       ProfScope _ps(&md->prof, "type_perm", s);
       DP_CUDA_TRY(launch_type_perm(dtype, N, m.cfg.ntypes, b.perm, b.type_start, md->status, chk, s));
     }
@@ -396,8 +399,10 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     for (int k = 0; k < 9; ++k) pc.h[k] = T.geoms[0].h[k];
     if (T.periodic) {
       pc.tshift = b.tshift;
-      ProfScope _ps(&md->prof, "shift_table", s);
-      k_shift_tables<<<F, 32, 0, s>>>(d_boxes, b.tshift);
+      if (!own_nlist) {
+        ProfScope _ps(&md->prof, "shift_table", s);
+        k_shift_tables<<<F, 32, 0, s>>>(d_boxes, b.tshift);
+      }
     }
     io.prof = &md->prof;
     io.coord = dcoord;
@@ -428,7 +433,7 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     double* d_virial = host_v ? b.virial : virial;
     {
       ProfScope _ps(&md->prof, "frame_sums", s, 2);
-      k_chunk_sums<<<T.C, 256, 0, s>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
+      k_chunk_sums<<<T.C, kChunk, 0, s>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
       k_frame_sums<<<F, 32, 0, s>>>(d_fchunk, b.cpart, d_energy, d_virial);
     }
     DP_CUDA_TRY(cudaGetLastError());
