@@ -61,8 +61,8 @@ int prepare_fit_bf16(DeviceModel& m, const double* params_host) {
   for (int t = 0; t < m.cfg.ntypes; ++t)
     for (int l = 0; l < nh; ++l) {
       const LayerDesc& L = m.fit[(size_t)t * nfl + l];
-      if (L.n_in % 8 || L.n_out % 16 || L.n_out > 256 || (l == 0 && L.skip)) {
-        set_error("tensor-core fitting needs hidden widths that are multiples of 16 and <= 256, inputs multiple of 8");
+      if (L.n_in % 8 || L.n_out % 16 || L.n_out > 256 || (l == 0 && L.skip) || L.skip == 2) {
+        set_error("tensor-core fitting needs hidden widths that are multiples of 16 and <= 256, inputs multiple of 8, skips of kind 0 or 1");
         return DP_E_UNSUPPORTED;
       }
       m.fit_bf16_off[(size_t)t * nh + l] = total;

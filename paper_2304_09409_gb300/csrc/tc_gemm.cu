@@ -1,8 +1,8 @@
 // Fitting-net GEMMs on the 5th-generation tensor cores of GB300 (sm_103a).
 //
 // One CTA (8 warps) computes a 128 x BN output tile.  Thread 0 streams 128 x 64 (A) and
-// BN x 64 (B) BF16 tiles into a shared-memory ring (4 stages for long reductions, 2 for short
-// ones so that several CTAs share an SM) with TMA (128-byte swizzle); thread 32 issues
+// BN x 64 (B) BF16 tiles into a shared-memory ring of up to 4 stages with TMA (128-byte
+// swizzle); thread 32 issues
 // tcgen05.mma (M = 128, N = BN, K = 16 per instruction) from the ring into an FP32 accumulator
 // in tensor memory and releases each stage with tcgen05.commit; after the last stage the eight
 // warps read the accumulator back with tcgen05.ld (two warps per 32-row lane quadrant, taking
@@ -30,11 +30,32 @@ constexpr int BK = 64;  // 64 BF16 = 128 bytes = one swizzle atom per row
 
 using namespace ptx;
 
-__host__ __device__ inline int ring_stages(int K) { return (K + BK - 1) / BK >= 8 ? kStages : 2; }
+// Ring depth: every K block of a short reduction in flight at once (one TMA round trip), at
+// most kStages for long ones.
+__host__ __device__ inline int ring_stages(int K) {
+  const int nk = (K + BK - 1) / BK;
+  return nk < kStages ? (nk < 1 ? 1 : nk) : kStages;
+}
+
+// Shared-memory staging of the epilogue (all but the plain epilogue): FP32 tiles [128][BN] as
+// 32-column boxes of 16 KB laid out by the TMA 128-byte swizzle (row r at r * 128 B, 16-byte
+// chunk q at position q ^ (r & 7)), so a thread that owns a row reads and writes its 16-byte
+// chunks without bank conflicts; BF16 tiles as 64-column boxes of the same layout.
+//   slot 0: the skip input (in place: the FP32 output y or g), slot 1: tanh output t (forward)
+//   or the gate input t_below (backward), then the BF16 output.
+__host__ __device__ inline uint32_t epi_f32_bytes(int BN) { return (uint32_t)(BN / 32) * 16384u; }
+__host__ __device__ inline uint32_t epi_bf16_bytes(int BN) { return (uint32_t)((BN + 63) / 64) * 16384u; }
+__host__ __device__ inline uint32_t epi_bytes(int epi, int BN) {
+  if (epi == TC_EPI_PLAIN) return 0;
+  const uint32_t f = epi_f32_bytes(BN), h = epi_bf16_bytes(BN);
+  return epi == TC_EPI_FWD_LAST ? f + h : 2 * f + h;
+}
+__device__ __forceinline__ uint32_t sw_off(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
 
 template <int EPI>
 __global__ void __launch_bounds__(kThreads)
-    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ TcMaps tb, const TcArgs g) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ TcMaps tb,
+              const __grid_constant__ TcEpiMaps em, const TcArgs g) {
   __shared__ float s_e[2][BM];  // FWD_LAST: energy partial of each row from each column half
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -44,10 +65,15 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t b_bytes = (uint32_t)BN * BK * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   const int NS = ring_stages(g.K);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * stage_bytes);
+  const uint32_t ring = (uint32_t)NS * stage_bytes, ep = epi_bytes(EPI, BN);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (ring > ep ? ring : ep));
   uint64_t* empty = full + kStages;
   uint64_t* accf = empty + kStages;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* efull = accf + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(efull + 1);
+  unsigned char* S0 = smem;                           // epilogue slots reuse the ring
+  unsigned char* S1 = smem + epi_f32_bytes(BN);
+  unsigned char* SB = smem + (EPI == TC_EPI_FWD_LAST ? 1 : 2) * epi_f32_bytes(BN);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int t = 0;
@@ -58,6 +84,9 @@ __global__ void __launch_bounds__(kThreads)
   const int nk = (g.K + BK - 1) / BK;
   uint32_t ncols = 32;
   while ((int)ncols < BN) ncols <<= 1;
+  const bool has_skip = (EPI != TC_EPI_PLAIN) && g.skip_kind == 1 && g.skip_mat != nullptr;
+  const bool has_tact = (EPI == TC_EPI_BWD);
+  const int nb = BN / 32;  // 32-column boxes
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -65,11 +94,10 @@ __global__ void __launch_bounds__(kThreads)
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
+    mbar_init(efull, 1);
     mbar_fence_init();
   }
-  if (warp == 0) {
-    tmem_alloc(tmem_holder, ncols);
-  }
+  if (warp == 0) tmem_alloc(tmem_holder, ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -93,6 +121,21 @@ __global__ void __launch_bounds__(kThreads)
       const int last = s + NS * ((nissued - 1 - s) / NS);
       mbar_wait(&full[s], (last / NS) & 1, g.err);
     }
+    // epilogue inputs into the ring once the MMAs have read it
+    if (has_skip || has_tact) {
+      bool ok = mbar_wait(accf, 0, g.err);
+      tc_fence_after();
+      if (ok) {
+        mbar_expect_tx(efull, (uint32_t)((has_skip ? 1 : 0) + (has_tact ? 1 : 0)) * epi_f32_bytes(BN));
+        for (int b = 0; b < nb; ++b) {
+          if (has_skip) tma_load_2d(S0 + b * 16384, &em.skip, efull, col0 + 32 * b, row0);
+          if (has_tact) tma_load_2d(S1 + b * 16384, &em.tact, efull, col0 + 32 * b, row0);
+        }
+        mbar_wait(efull, 0, g.err);
+      } else {
+        mbar_arrive(efull);  // release the epilogue of a failed CTA
+      }
+    }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     const uint32_t idesc = idesc_f16(BM, BN, 1);
@@ -110,133 +153,126 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncwarp();
 
-  // ---- epilogue: warps w and w + 4 own accumulator rows 32(w % 4) .. +31, alternate chunks ----
+  // ---- epilogue: warps w and w + 4 own accumulator rows 32(w % 4) .. +31 ----
   mbar_wait(accf, 0, g.err);
   tc_fence_after();
   const int quad = warp & 3, half = warp >> 2;
-  const int row = row0 + quad * 32 + lane;
+  const int rl = quad * 32 + lane;  // row within the tile
+  const int row = row0 + rl;
   const bool rv = row < row_end;
   const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
   float e_acc = 0.f;
-  for (int c = half * 16; c < BN; c += 32) {
-    float v[16];
-    tmem_ld16(tbase + c, v);
-    const int cb = col0 + c;
-    if (!rv || cb >= g.N) continue;
-    const long ro = (long)row * g.N;
-    // rows of 16-byte-aligned chunks take vector loads/stores; a ragged last chunk goes scalar
-    const bool vec = (cb + 16 <= g.N) && ((g.N & 7) == 0);
-    float o[16], aux[16];
-    if (EPI == TC_EPI_PLAIN) {
+  if (EPI == TC_EPI_PLAIN) {
+    for (int c = half * 16; c < BN; c += 32) {
+      float v[16];
+      tmem_ld16(tbase + c, v);
+      const int cb = col0 + c;
+      if (!rv || cb >= g.N) continue;
+      float* dst = g.out_f32 + (long)row * g.N + cb;
+      if (cb + 16 <= g.N && (g.N & 3) == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) o[i] = v[i];
-    } else if (EPI == TC_EPI_FWD || EPI == TC_EPI_FWD_LAST) {
-      float sk[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) sk[i] = 0.f;
-      if (g.skip_kind && vec && (g.skip_ld & 15) == 0) {
-        const int sc = (g.skip_kind == 1) ? cb : (cb % g.skip_ld);
-        const float4* s4 = reinterpret_cast<const float4*>(g.skip_mat + (long)row * g.skip_ld + sc);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 x = s4[q];
-          sk[4 * q] = x.x;
-          sk[4 * q + 1] = x.y;
-          sk[4 * q + 2] = x.z;
-          sk[4 * q + 3] = x.w;
-        }
-      } else if (g.skip_kind) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (cb + i < g.N)
-            sk[i] = g.skip_mat[(long)row * g.skip_ld + (g.skip_kind == 1 ? cb + i : (cb + i) % g.skip_ld)];
-      }
-      const float* bias = g.bias[t];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = cb + i < g.N ? cb + i : g.N - 1;
-        const float th = tanhf(v[i] + bias[col]);
-        if (EPI == TC_EPI_FWD) {
-          o[i] = th + sk[i];
-          aux[i] = th;
-        } else {
-          const float wl = g.w_last[t][col];
-          if (cb + i < g.N) e_acc += (th + sk[i]) * wl;
-          aux[i] = wl * (1.f - th * th);
-        }
-      }
-    } else {  // TC_EPI_BWD
-      float tb[16];
-      if (vec) {
-        const float4* t4 = reinterpret_cast<const float4*>(g.tact + ro + cb);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 x = t4[q];
-          tb[4 * q] = x.x;
-          tb[4 * q + 1] = x.y;
-          tb[4 * q + 2] = x.z;
-          tb[4 * q + 3] = x.w;
-        }
+        for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) tb[i] = cb + i < g.N ? g.tact[ro + cb + i] : 0.f;
-      }
-      const float* sv = g.skip_vec ? g.w_last[t] : (g.skip_mat ? g.skip_mat + (long)row * g.skip_ld : nullptr);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = cb + i < g.N ? cb + i : g.N - 1;
-        float gy = v[i];
-        if (sv) {
-          if (g.skip_kind == 1) gy += sv[col];
-          if (g.skip_kind == 2) gy += sv[col] + sv[col + g.N];
-        }
-        o[i] = gy;
-        aux[i] = gy * (1.f - tb[i] * tb[i]);
+        for (int i = 0; i < 16; ++i)
+          if (cb + i < g.N) dst[i] = v[i];
       }
     }
-    // ---- stores ----
-    float* of = (EPI == TC_EPI_FWD_LAST) ? nullptr : g.out_f32;
-    float* ot = (EPI == TC_EPI_FWD) ? g.out_t : nullptr;
-    const float* bsrc = (EPI == TC_EPI_FWD) ? o : aux;  // values stored as BF16
-    if (vec) {
-      if (of) {
-        float4* d4 = reinterpret_cast<float4*>(of + ro + cb);
+  } else {
+    if (has_skip || has_tact) mbar_wait(efull, 0, g.err);
+    const float* bias = g.bias[t];
+    const float* sv = (EPI == TC_EPI_BWD && g.skip_vec) ? g.w_last[t] : nullptr;
+    for (int b = half; b < nb; b += 2) {  // one 32-column box at a time
+      float v[32];
+      tmem_ld16(tbase + 32 * b, v);
+      tmem_ld16(tbase + 32 * b + 16, v + 16);
+      unsigned char* s0 = S0 + b * 16384;
+      unsigned char* s1 = S1 + b * 16384;
+      float o[32], aux[32];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      }
-      if (ot) {
-        float4* d4 = reinterpret_cast<float4*>(ot + ro + cb);
+      for (int q = 0; q < 8; ++q) {
+        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+        if (has_skip) x0 = *reinterpret_cast<const float4*>(s0 + sw_off(rl, q));
+        if (has_tact) x1 = *reinterpret_cast<const float4*>(s1 + sw_off(rl, q));
+        const float sk[4] = {x0.x, x0.y, x0.z, x0.w}, tb4[4] = {x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) d4[q] = make_float4(aux[4 * q], aux[4 * q + 1], aux[4 * q + 2], aux[4 * q + 3]);
-      }
-      if (EPI != TC_EPI_PLAIN) {
-        uint4 pk[2];
-        uint32_t* w = reinterpret_cast<uint32_t*>(pk);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(bsrc[2 * q], bsrc[2 * q + 1]);
-          w[q] = *reinterpret_cast<const uint32_t*>(&h2);
+        for (int k = 0; k < 4; ++k) {
+          const int i = 4 * q + k;
+          const int col = min(col0 + 32 * b + i, g.N - 1);
+          if (EPI == TC_EPI_FWD || EPI == TC_EPI_FWD_LAST) {
+            const float th = tanhf(v[i] + __ldg(bias + col));
+            if (EPI == TC_EPI_FWD) {
+              o[i] = th + sk[k];
+              aux[i] = th;
+            } else {
+              const float wl = __ldg(g.w_last[t] + col);
+              if (col0 + 32 * b + i < g.N) e_acc += (th + sk[k]) * wl;
+              aux[i] = wl * (1.f - th * th);
+            }
+          } else {  // BWD
+            float gy = v[i] + sk[k];
+            if (sv) gy += __ldg(sv + col);
+            o[i] = gy;
+            aux[i] = gy * (1.f - tb4[k] * tb4[k]);
+          }
         }
-        uint4* d = reinterpret_cast<uint4*>(g.out_bf16 + ro + cb);
-        d[0] = pk[0];
-        d[1] = pk[1];
       }
-    } else {
+      // FP32 outputs in place, BF16 output into its own box
+      if (EPI == TC_EPI_FWD || (EPI == TC_EPI_BWD && g.out_f32)) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (cb + i >= g.N) break;
-        if (of) of[ro + cb + i] = o[i];
-        if (ot) ot[ro + cb + i] = aux[i];
-        if (EPI != TC_EPI_PLAIN) g.out_bf16[ro + cb + i] = __float2bfloat16_rn(bsrc[i]);
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(s0 + sw_off(rl, q)) = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      }
+      if (EPI == TC_EPI_FWD) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(s1 + sw_off(rl, q)) =
+              make_float4(aux[4 * q], aux[4 * q + 1], aux[4 * q + 2], aux[4 * q + 3]);
+      }
+      const float* bsrc = (EPI == TC_EPI_FWD) ? o : aux;
+      unsigned char* sb = SB + (b >> 1) * 16384;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // 8 BF16 per 16-byte chunk
+        uint32_t w[4];
+#pragma unroll
+        for (int h2 = 0; h2 < 4; ++h2) {
+          const __nv_bfloat162 pr = __floats2bfloat162_rn(bsrc[8 * k + 2 * h2], bsrc[8 * k + 2 * h2 + 1]);
+          w[h2] = *reinterpret_cast<const uint32_t*>(&pr);
+        }
+        *reinterpret_cast<uint4*>(sb + sw_off(rl, 4 * (b & 1) + k)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
   }
-  if (EPI == TC_EPI_FWD_LAST) s_e[half][quad * 32 + lane] = e_acc;
+  if (EPI == TC_EPI_FWD_LAST) s_e[half][rl] = e_acc;
   tc_fence_before();
   __syncthreads();
   if (EPI == TC_EPI_FWD_LAST && half == 0 && rv)
-    g.e_out[(long)blockIdx.y * g.e_ld + row] =
-        s_e[0][quad * 32 + lane] + s_e[1][quad * 32 + lane] + (blockIdx.y == 0 ? g.b_last[t] : 0.f);
+    g.e_out[(long)blockIdx.y * g.e_ld + row] = s_e[0][rl] + s_e[1][rl] + (blockIdx.y == 0 ? g.b_last[t] : 0.f);
+  if (EPI != TC_EPI_PLAIN) {
+    // ---- coalesced copy-out of the staged tiles (rows of this type only) ----
+    const int c4n = BN / 4, c8n = BN / 8;
+    float* of0 = (EPI == TC_EPI_FWD || EPI == TC_EPI_BWD) ? g.out_f32 : nullptr;
+    float* of1 = (EPI == TC_EPI_FWD) ? g.out_t : nullptr;
+    for (int u = threadIdx.x; u < BM * c4n; u += kThreads) {
+      const int r = u / c4n, c4 = u - r * c4n;
+      const int col = col0 + 4 * c4;
+      if (row0 + r >= row_end || col >= g.N) continue;
+      const uint32_t so = (uint32_t)((c4 >> 3) * 16384) + sw_off(r, c4 & 7);
+      const long go = (long)(row0 + r) * g.N + col;
+      if (of0) *reinterpret_cast<float4*>(of0 + go) = *reinterpret_cast<const float4*>(S0 + so);
+      if (of1) *reinterpret_cast<float4*>(of1 + go) = *reinterpret_cast<const float4*>(S1 + so);
+    }
+    for (int u = threadIdx.x; u < BM * c8n; u += kThreads) {
+      const int r = u / c8n, c8 = u - r * c8n;
+      const int col = col0 + 8 * c8;
+      if (row0 + r >= row_end || col >= g.N) continue;
+      const uint32_t so = (uint32_t)((c8 >> 3) * 16384) + sw_off(r, c8 & 7);
+      *reinterpret_cast<uint4*>(g.out_bf16 + (long)(row0 + r) * g.N + col) = *reinterpret_cast<const uint4*>(SB + so);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
@@ -278,34 +314,69 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int
 }
 
 int tc_pick_bn(int N, int row_tiles) {
-  int bn = ((N + 15) / 16) * 16;
+  int bn = ((N + 31) / 32) * 32;
   if (bn > 256) bn = 256;
-  while (bn > 64 && (long)row_tiles * ((N + bn - 1) / bn) < 2L * 152) bn = ((bn / 2 + 15) / 16) * 16;
+  while (bn > 64 && (long)row_tiles * ((N + bn - 1) / bn) < 2L * 152) bn = ((bn / 2 + 31) / 32) * 32;
   return bn;
+}
+
+int make_tmap_f32(CUtensorMap* map, const void* base, long rows, long cols) {
+  CUtensorMap tmp;
+  if (make_tmap_bf16(&tmp, base, rows, cols, 128) != DP_OK) return DP_E_CUDA;  // loads the encoder
+  if ((cols * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) {
+    set_error("tensor map: FP32 row pitch and base must be 16-byte aligned");
+    return DP_E_UNSUPPORTED;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * 4)};
+  cuuint32_t box[2] = {32, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (FP32) failed (" + std::to_string((int)r) + ")");
+    return DP_E_CUDA;
+  }
+  return DP_OK;
 }
 
 cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st) {
   const int tiles = a.tile_start[a.ntypes];
   if (tiles <= 0) return cudaSuccess;
+  if (epi != TC_EPI_PLAIN && (a.BN % 32 != 0 || a.skip_kind == 2)) {
+    set_error("tensor-core GEMM epilogue: output blocks of 32 columns, skips of kind 0 or 1 only");
+    return cudaErrorInvalidValue;
+  }
   dim3 grid(tiles, (a.N + a.BN - 1) / a.BN);
-  const size_t smem = (size_t)ring_stages(a.K) * (BM * BK * 2 + (size_t)a.BN * BK * 2) + 1024 + 256;
+  const size_t ring = (size_t)ring_stages(a.K) * (BM * BK * 2 + (size_t)a.BN * BK * 2);
+  const size_t ep = epi_bytes(epi, a.BN);
+  const size_t smem = (ring > ep ? ring : ep) + 1024 + 256;
+  // epilogue inputs (skip, gate) as TMA maps over all rows
+  TcEpiMaps em;
+  std::memset(&em, 0, sizeof(em));
+  const long rows = a.row_start[a.ntypes];
+  if (epi != TC_EPI_PLAIN && a.skip_kind == 1 && a.skip_mat &&
+      make_tmap_f32(&em.skip, a.skip_mat, rows, a.skip_ld) != DP_OK)
+    return cudaErrorInvalidValue;
+  if (epi == TC_EPI_BWD && make_tmap_f32(&em.tact, a.tact, rows, a.N) != DP_OK) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   switch (epi) {
     case TC_EPI_PLAIN:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_PLAIN><<<grid, kThreads, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_PLAIN><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
     case TC_EPI_FWD:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD><<<grid, kThreads, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
     case TC_EPI_FWD_LAST:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_FWD_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD_LAST><<<grid, kThreads, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD_LAST><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
     default:
       e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_BWD><<<grid, kThreads, smem, st>>>(ta, tb, a);
+      if (e == cudaSuccess) k_tc_gemm<TC_EPI_BWD><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
   }
   if (e != cudaSuccess) return e;

@@ -42,14 +42,23 @@ struct TcArgs {
   int* err;                 // device error word (bounded waits)
 };
 
+// Epilogue inputs staged by TMA: the skip input and the gate input of the backward pass
+// (row-major FP32 [rows][ld], boxes of 32 columns x 128 rows, 128-byte swizzle).
+struct TcEpiMaps {
+  CUtensorMap skip, tact;
+};
+
 // Tensor map of a row-major [rows][cols] BF16 matrix, 128-byte swizzle, box {64, box_rows}.
 int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int box_rows);
+// Tensor map of a row-major [rows][cols] FP32 matrix, 128-byte swizzle, box {32, 128}.
+int make_tmap_f32(CUtensorMap* map, const void* base, long rows, long cols);
 
 // C[rows][N] (+epilogue) = A[rows][K] . B_t[K][N]; A from `ta` ([rows][K] row-major), B_t from
 // the type's map in `tb` (its transpose, [N][K] row-major); BF16 operands, FP32 accumulation.
 cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st);
 
-// Output columns per CTA for an N-wide output with `row_tiles` 128-row tiles in total.
+// Output columns per CTA for an N-wide output with `row_tiles` 128-row tiles in total (a
+// multiple of 32).
 int tc_pick_bn(int N, int row_tiles);
 
 }  // namespace dpgb
