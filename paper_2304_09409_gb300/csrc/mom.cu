@@ -183,7 +183,7 @@ __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_e
 // Ring depth of the forward's operand stages.
 template <int NPASS>
 struct MomStages {
-  static constexpr int value = NPASS == 1 ? 4 : 2;
+  static constexpr int value = NPASS == 1 ? 3 : 2;  // three stages keep two CTAs on an SM
 };
 
 
@@ -978,7 +978,7 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
 }
 
 size_t fwd_smem(int npass, int npad, int nc) {
-  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 4 : 2;
+  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 3 : 2;
   return (size_t)S * parts * (kABlock + npad * 128) + (size_t)kAtoms * nc * 4 + (2 * S + 1) * 8 + 4 +
          4 * DP_MAX_TYPES + 1024 + 64;
 }

@@ -1,8 +1,8 @@
 // Fitting-net GEMMs on the 5th-generation tensor cores of GB300 (sm_103a).
 //
 // One CTA (8 warps) computes a 128 x BN output tile.  Thread 0 streams 128 x 64 (A) and
-// BN x 64 (B) BF16 tiles into a shared-memory ring of up to 4 stages with TMA (128-byte
-// swizzle); thread 32 issues
+// BN x 64 (B) BF16 tiles into a shared-memory ring (4 stages for long reductions, 2 for short
+// ones so that several CTAs share an SM) with TMA (128-byte swizzle); thread 32 issues
 // tcgen05.mma (M = 128, N = BN, K = 16 per instruction) from the ring into an FP32 accumulator
 // in tensor memory and releases each stage with tcgen05.commit; after the last stage the eight
 // warps read the accumulator back with tcgen05.ld (two warps per 32-row lane quadrant, taking
@@ -30,12 +30,9 @@ constexpr int BK = 64;  // 64 BF16 = 128 bytes = one swizzle atom per row
 
 using namespace ptx;
 
-// Ring depth: every K block of a short reduction in flight at once (one TMA round trip), at
-// most kStages for long ones.
-__host__ __device__ inline int ring_stages(int K) {
-  const int nk = (K + BK - 1) / BK;
-  return nk < kStages ? (nk < 1 ? 1 : nk) : kStages;
-}
+// Ring depth: kStages for long reductions, two for short ones so that several CTAs (and their
+// epilogues) share an SM.
+__host__ __device__ inline int ring_stages(int K) { return (K + BK - 1) / BK >= 8 ? kStages : 2; }
 
 // Shared-memory staging of the epilogue (all but the plain epilogue): FP32 tiles [128][BN] as
 // 32-column boxes of 16 KB laid out by the TMA 128-byte swizzle (row r at r * 128 B, 16-byte
