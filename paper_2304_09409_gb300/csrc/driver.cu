@@ -75,16 +75,34 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void k_frame_sums(const int* __restrict__ frame_chunk, const double* __restrict__ cpart,
-                             double* __restrict__ energy, double* __restrict__ virial) {
-  const int f = blockIdx.x, q = threadIdx.x;
-  if (q >= 10) return;
-  double x = 0.0;
-  for (int c = frame_chunk[f]; c < frame_chunk[f + 1]; ++c) x += cpart[10L * c + q];
-  if (q == 0)
-    energy[f] = x;
-  else
-    virial[9L * f + q - 1] = x;
+// Per-frame sums of the chunk partials: thread k adds chunks k, k + 128, ... of its frame, then a
+// fixed tree over the threads (the order depends on the frame alone, not on the batch).
+__global__ void __launch_bounds__(128)
+    k_frame_sums(const int* __restrict__ frame_chunk, const double* __restrict__ cpart, double* __restrict__ energy,
+                 double* __restrict__ virial) {
+  __shared__ double red[4][10];
+  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int c0 = frame_chunk[f], c1 = frame_chunk[f + 1];
+  double acc[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+  for (int c = c0 + tid; c < c1; c += 128)
+#pragma unroll
+    for (int q = 0; q < 10; ++q) acc[q] += cpart[10L * c + q];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    double x = acc[q];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][q] = x;
+  }
+  __syncthreads();
+  if (tid < 10) {
+    const double x = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+    if (tid == 0)
+      energy[f] = x;
+    else
+      virial[9L * f + tid - 1] = x;
+  }
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -434,7 +452,7 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     {
       ProfScope _ps(&md->prof, "frame_sums", s, 2);
       k_chunk_sums<<<T.C, kChunk, 0, s>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
-      k_frame_sums<<<F, 32, 0, s>>>(d_fchunk, b.cpart, d_energy, d_virial);
+      k_frame_sums<<<F, 128, 0, s>>>(d_fchunk, b.cpart, d_energy, d_virial);
     }
     DP_CUDA_TRY(cudaGetLastError());
     if (host_e) DP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * F, cudaMemcpyDeviceToHost, s));

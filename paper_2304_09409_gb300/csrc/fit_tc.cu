@@ -89,7 +89,7 @@ int prepare_fit_bf16(DeviceModel& m, const double* params_host) {
 }
 
 int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io, Arena& ar,
-                   cudaStream_t st, const float** gD_out) {
+                   cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out) {
   const long N = pc.natoms;
   const int nfl = m.n_fit_layers, nh = nfl - 1;
   const int D = pc.M * pc.A;
@@ -108,7 +108,8 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
   // per-atom energy partials, one per output-column block of the last hidden layer (blocks are at
   // least 64 columns wide)
   float* E = ar.get<float>(N * ((m.fit[nh - 1].n_out + 63) / 64));
-  float* gD = ar.get<float>(N * D);
+  float* gD = gDh_out ? nullptr : ar.get<float>(N * D);
+  __nv_bfloat16* gDh = gDh_out ? ar.get<__nv_bfloat16>(N * D) : nullptr;
   int* err = ar.get<int>(1);
   if (ar.measure) return DP_OK;
   if (!ar.ok()) {
@@ -191,6 +192,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     }
     if (l == 0) {
       a.out_f32 = gD;
+      a.out_bf16 = gDh;
       ProfScope _ps(io.prof, "fit_bwd_tc", st);
       DP_CUDA_TRY(launch_tc_gemm(TC_EPI_PLAIN, ta, tb, a, st));
     } else {
@@ -206,6 +208,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     }
   }
   *gD_out = gD;
+  if (gDh_out) *gDh_out = gDh;
   (void)skip_kind;
   return DP_OK;
 }

@@ -76,7 +76,8 @@ struct MomArgs {
   float* Tm;          // [N][M][4]
   void* D;            // [N][M * A], BF16 or FP32
   int d_bf16;
-  const float* gD;  // [N][M * A]
+  const float* gD;            // [N][M * A] FP32, or
+  const __nv_bfloat16* gDh;   // [N][M * A] BF16 (mixed mode)
   double* force;    // [N][3] input order
   double* avir;     // [N][9] input order
   unsigned char* gta;  // backward A operand per tile: the shared-memory image of dE/dT rows
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(kRows)
         const int q = blockIdx.y;
         const int at = q * kGroupAtoms + warp;  // atom of the tile
         const bool va = row0 + at < row_end;   // warp-uniform
-        const float* gDa = g.gD + (long)(row0 + at) * g.M * g.A;
+        const long gdo = (long)(row0 + at) * g.M * g.A;
         const float* Ta = g.Tm + (long)(row0 + at) * g.M * 4;
         int ex = 0;
         if (va) {
@@ -613,8 +614,23 @@ __global__ void __launch_bounds__(kRows)
             const int m = part + 8 * k;
             if (m < g.M) {
               float gd[16];
-              if (g.A == 16) {
-                const float4* g4 = reinterpret_cast<const float4*>(gDa + m * 16);
+              if (g.gDh && g.A == 16) {
+                const uint4* h4 = reinterpret_cast<const uint4*>(g.gDh + gdo + m * 16);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  const uint4 x = h4[e];
+                  const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    gd[8 * e + 2 * k] = __uint_as_float(w4[k] << 16);
+                    gd[8 * e + 2 * k + 1] = __uint_as_float(w4[k] & 0xFFFF0000u);
+                  }
+                }
+              } else if (g.gDh) {
+#pragma unroll
+                for (int l = 0; l < 16; ++l) gd[l] = l < g.A ? __bfloat162float(g.gDh[gdo + m * g.A + l]) : 0.f;
+              } else if (g.A == 16) {
+                const float4* g4 = reinterpret_cast<const float4*>(g.gD + gdo + m * 16);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                   const float4 x = g4[e];
@@ -625,7 +641,7 @@ __global__ void __launch_bounds__(kRows)
                 }
               } else {
 #pragma unroll
-                for (int l = 0; l < 16; ++l) gd[l] = l < g.A ? gDa[m * g.A + l] : 0.f;
+                for (int l = 0; l < 16; ++l) gd[l] = l < g.A ? g.gD[gdo + m * g.A + l] : 0.f;
               }
               const float tm = Ta[m * 4 + c];
               float v = 0.f;
@@ -1089,8 +1105,9 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   unsigned char* gta = ar.get<unsigned char>(max_tiles * (bf16 ? 1 : 2) * 2 * kABlock);
   int* gtx = ar.get<int>(max_tiles * kRows);
   const float* gD = nullptr;
+  const __nv_bfloat16* gDh = nullptr;
   if (ar.measure) {
-    if (bf16) return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD);
+    if (bf16) return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, &gDh);
     return run_fitting<float>(m, pc, m.p32, reinterpret_cast<const float*>(D), io, ar, st, &gD);
   }
   if (!ar.ok()) {
@@ -1156,11 +1173,12 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   }
   int rc;
   if (bf16)
-    rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD);
+    rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, &gDh);
   else
     rc = run_fitting<float>(m, pc, m.p32, reinterpret_cast<const float*>(D), io, ar, st, &gD);
   if (rc != DP_OK) return rc;
   g.gD = gD;
+  g.gDh = gDh;
   if (tiles > 0) {
     {
       ProfScope _ps(io.prof, "mom_gT", st);

@@ -9,7 +9,7 @@
 namespace dpgb {
 
 enum TcEpilogue : int {
-  TC_EPI_PLAIN = 0,     // C = acc                                          (fp32 out)
+  TC_EPI_PLAIN = 0,     // C = acc                                          (fp32 or bf16 out)
   TC_EPI_FWD = 1,       // t = tanh(acc + b); y = t + skip(x)               (y fp32, y bf16, t fp32)
   TC_EPI_FWD_LAST = 2,  // as FWD, then E = y . w_last + b_last and the backward seed
                         //   gz = w_last * (1 - t^2) of the last hidden layer (E fp32, gz bf16)
