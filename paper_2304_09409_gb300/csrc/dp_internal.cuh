@@ -147,6 +147,21 @@ struct TypeStartCheck {
   int v[DP_MAX_TYPES + 1];
 };
 
+// Let `kernel` take up to the device's opt-in shared memory per block.  Every caller sets the
+// same value, so launches from several host threads never see the limit lowered under them
+// (the shared memory a block actually gets is the launch's own request).
+template <class K>
+inline cudaError_t allow_max_smem(K kernel) {
+  int dev = 0, mx = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)  // the opt-in limit covers static and dynamic shared memory together
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 // ------------------------------------------------------------------------------------------
 // Launchers (nlist.cu)
 // ------------------------------------------------------------------------------------------

@@ -514,12 +514,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* smT = reinterpret_cast<float*>(smem);  // [32 atoms][NPAD + 1][4]; the ring is idle now
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      float v[16];
-      tmem_ld16(tb + c0, v);
+    for (int c0 = 0; c0 < NPAD; c0 += 32) {  // two 16-column loads in flight, one wait
+      uint32_t raw[32];
+      const bool two = c0 + 16 < NPAD;  // warp-uniform
+      tmem_ld16_async(tb + c0, raw);
+      if (two) tmem_ld16_async(tb + c0 + 16, raw + 16);
+      tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float x = nkb > 0 ? v[q] * g.inv_nc : 0.f;
+      for (int q = 0; q < 32; ++q) {
+        if (q >= 16 && !two) break;
+        const float x = nkb > 0 ? __uint_as_float(raw[q]) * g.inv_nc : 0.f;
         smT[(ae * (NPAD + 1) + c0 + q) * 4 + c] = x;
         if (valid_e && c0 + q < g.M) g.Tm[((long)pe * g.M + c0 + q) * 4 + c] = x;
       }
@@ -842,7 +846,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       float P[64];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) tmem_ld16(tb + (uint32_t)(buf * 64 + 16 * q), P + 16 * q);
+      {
+        uint32_t raw[64];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmem_ld16_async(tb + (uint32_t)(buf * 64 + 16 * q), raw + 16 * q);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 64; ++e) P[e] = __uint_as_float(raw[e]);
+      }
       tc_fence_before();
       mbar_arrive(&accempty[buf]);
       int t, grp;
@@ -1011,11 +1022,11 @@ int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, int which, cud
     k_mom_gT<NPASS, NPAD><<<dim3(tiles, kAtoms / kGroupAtoms), kRows, 0, st>>>(g);
   } else if (which == 0) {
     const size_t sm = fwd_smem(NPASS, NPAD, g.nc);
-    DP_CUDA_TRY(cudaFuncSetAttribute(k_mom_fwd<NPASS, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    DP_CUDA_TRY(allow_max_smem(k_mom_fwd<NPASS, NPAD>));
     k_mom_fwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[0], maps[1], g);
   } else {
     const size_t sm = bwd_smem(NPASS, g.nc);
-    DP_CUDA_TRY(cudaFuncSetAttribute(k_mom_bwd<NPASS, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    DP_CUDA_TRY(allow_max_smem(k_mom_bwd<NPASS, NPAD>));
     k_mom_bwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[2], maps[3], g);
   }
   DP_CUDA_TRY(cudaGetLastError());

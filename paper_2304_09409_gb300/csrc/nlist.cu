@@ -631,11 +631,12 @@ __global__ void __launch_bounds__(kCellWarps * 32)
           __syncthreads();
         }
         if (active) {
-          for (int base = p0; base < p1; base += 32) {
-            const int p = base + lane;
+          // one staged candidate: FP32 screening, the exact test only within the error of r_c
+          auto test = [&](int p, int& idx, int& o, float& r2) -> bool {
             bool pass = false;
-            int idx = 0, o = 0;
-            float r2 = 0.f;
+            idx = 0;
+            o = 0;
+            r2 = 0.f;
             if (p < p1) {
               const float4 sj = stg[p - sb];
               idx = __float_as_int(sj.w);
@@ -647,7 +648,7 @@ __global__ void __launch_bounds__(kCellWarps * 32)
                 const bool self = idx == w && wcode == pack_shift(0, 0, 0);
                 if (r2 < rc2_in) {
                   pass = !self;
-                } else if (!self) {  // within the FP32 error of r_c: the exact FP64 test decides
+                } else if (!self) {
                   int j, code;
                   if (entry_code(sorted_l, sorted_m, idx, wcode, mi, j, code))
                     pass = exact_r2(g, xi, coord, j, code) < g.rc2;
@@ -656,16 +657,33 @@ __global__ void __launch_bounds__(kCellWarps * 32)
                 }
               }
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, pass);
-            if (pass) {
-              const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+            return pass;
+          };
+          const unsigned lt = (1u << lane) - 1u;
+          for (int base = p0; base < p1; base += 64) {  // two independent batches per iteration
+            int ia, oa, ib, ob;
+            float ra, rb;
+            const bool pa = test(base + lane, ia, oa, ra);
+            const bool pb = test(base + 32 + lane, ib, ob, rb);
+            const unsigned ma = __ballot_sync(0xffffffffu, pa), mb = __ballot_sync(0xffffffffu, pb);
+            const int na = __popc(ma);
+            if (pa) {
+              const int pos = cnt + __popc(ma & lt);
               if (pos < CAP) {
-                e_key[pos] = r2;
-                e_idx[pos] = idx;
-                e_w[pos] = o;
+                e_key[pos] = ra;
+                e_idx[pos] = ia;
+                e_w[pos] = oa;
               }
             }
-            cnt += __popc(mask);
+            if (pb) {
+              const int pos = cnt + na + __popc(mb & lt);
+              if (pos < CAP) {
+                e_key[pos] = rb;
+                e_idx[pos] = ib;
+                e_w[pos] = ob;
+              }
+            }
+            cnt += na + __popc(mb);
           }
         }
       }
@@ -921,7 +939,7 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
     const size_t csm = cell_smem_bytes(cap);
 #define DPGB_NLC_LAUNCH(C)                                                                                       \
   do {                                                                                                           \
-    e = cudaFuncSetAttribute(k_nlist_cell<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);            \
+    e = allow_max_smem(k_nlist_cell<C>);            \
     if (e != cudaSuccess) return e;                                                                              \
     k_nlist_cell<C><<<L.ncells_total, kCellWarps * 32, csm, st>>>(L.geoms, L.cell_off, L.nframes,               \
                                                                   L.ncells_total, ntypes, coord, cell_start,     \
@@ -941,7 +959,7 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   const unsigned blocks = (L.natoms + kNlWarps - 1) / kNlWarps;
 #define DPGB_NL_LAUNCH(C)                                                                                       \
   do {                                                                                                          \
-    e = cudaFuncSetAttribute(k_nlist<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
+    e = allow_max_smem(k_nlist<C>);               \
     if (e != cudaSuccess) return e;                                                                             \
     k_nlist<C><<<blocks, kNlWarps * 32, smem, st>>>(L.geoms, L.atom_frame, L.cell_off, cell_start + nkeys,      \
                                                    L.ncells_total, coord, cell_start, sorted_l, sorted_m, nl_j, \

@@ -507,7 +507,7 @@ int run_tab(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   }
   if (rc != DP_OK) return rc;
   const size_t smem = sizeof(R) * 4 * (size_t)(M * 8);
-  DP_CUDA_TRY(cudaFuncSetAttribute(k_tab_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DP_CUDA_TRY(allow_max_smem(k_tab_bwd<R>));
   {
     ProfScope _ps(io.prof, "tab_bwd", st);
     k_tab_bwd<R><<<blocks, 128, smem, st>>>(pc, tc, tab, io.coord, io.perm, io.type, io.nl_j, env, Tm,

@@ -200,8 +200,14 @@ __global__ void __launch_bounds__(kThreads)
     const float* sv = (EPI == TC_EPI_BWD && g.skip_vec) ? g.w_last[t] : nullptr;
     for (int b = half; b < nb; b += 2) {  // one 32-column box at a time
       float v[32];
-      tmem_ld16(tbase + 32 * b, v);
-      tmem_ld16(tbase + 32 * b + 16, v + 16);
+      {
+        uint32_t raw[32];
+        tmem_ld16_async(tbase + 32 * b, raw);
+        tmem_ld16_async(tbase + 32 * b + 16, raw + 16);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(raw[e]);
+      }
       unsigned char* s0 = S0 + b * 16384;
       unsigned char* s1 = S1 + b * 16384;
       float o[32], aux[32];
@@ -378,19 +384,19 @@ cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, con
   cudaError_t e = cudaSuccess;
   switch (epi) {
     case TC_EPI_PLAIN:
-      e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_max_smem(k_tc_gemm<TC_EPI_PLAIN>);
       if (e == cudaSuccess) k_tc_gemm<TC_EPI_PLAIN><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
     case TC_EPI_FWD:
-      e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_max_smem(k_tc_gemm<TC_EPI_FWD>);
       if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
     case TC_EPI_FWD_LAST:
-      e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_FWD_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_max_smem(k_tc_gemm<TC_EPI_FWD_LAST>);
       if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD_LAST><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
     default:
-      e = cudaFuncSetAttribute(k_tc_gemm<TC_EPI_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = allow_max_smem(k_tc_gemm<TC_EPI_BWD>);
       if (e == cudaSuccess) k_tc_gemm<TC_EPI_BWD><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
       break;
   }

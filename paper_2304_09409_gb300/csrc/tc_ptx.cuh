@@ -134,6 +134,18 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t tmem, uint32_t ncols) {
 }
 
 // 16 consecutive FP32 columns of this thread's tensor-memory lane.
+// 16 columns of the warp's 32 TMEM lanes into registers without waiting: several loads can be
+// in flight before one tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t addr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
   uint32_t r[16];
   asm volatile(
