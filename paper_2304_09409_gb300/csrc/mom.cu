@@ -72,7 +72,9 @@ struct MomArgs {
   // per-run records, run r of type block t of atom p at row p * nc + sel_off[t] + r
   int* run_l;      // interval of the run; -1 after the last run
   uint4* run_rec;  // moments as A-operand chunks [row][4 components][parts]
-  float4* run_P;   // P of the run [row][4 components][2] (shares memory with run_rec)
+  float4* run_P;   // P of the run [row][4 components][2] FP32, or [row][4 components] 8 x BF16 when
+                   // p_bf16 (mixed mode); shares memory with run_rec
+  int p_bf16;
   float* Tm;          // [N][M][4]
   void* D;            // [N][M * A], BF16 or FP32
   int d_bf16;
@@ -884,9 +886,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           DPGB_SEL(7)
 #undef DPGB_SEL
         }
-        float4* dst = g.run_P + ((rbase + ptr) * 4 + c) * 2;
-        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-        dst[1] = make_float4(v[4], v[5], 0.f, 0.f);
+        if (NPASS == 1) {  // mixed mode: the six values of the run as BF16 (one 16-byte chunk)
+          uint32_t w[4];
+#pragma unroll
+          for (int h2 = 0; h2 < 3; ++h2) {
+            const __nv_bfloat162 pr = __floats2bfloat162_rn(v[2 * h2], v[2 * h2 + 1]);
+            w[h2] = *reinterpret_cast<const uint32_t*>(&pr);
+          }
+          w[3] = 0u;
+          reinterpret_cast<uint4*>(g.run_P)[(rbase + ptr) * 4 + c] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+          float4* dst = g.run_P + ((rbase + ptr) * 4 + c) * 2;
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], 0.f, 0.f);
+        }
         ++ptr;
       }
     }
@@ -920,15 +933,32 @@ __global__ void __launch_bounds__(256)
       if (j < 0) continue;
       const long row = (long)p * pc.nc + k;
       const float4 e0 = g.envU[row], e1 = g.envB[row];
-      const float4* P4 = g.run_P + (rbase + g.slot_run[row]) * 8;
+      const long run = rbase + g.slot_run[row];
       const float tau = e1.z;
       const int l = __float_as_int(e1.w);
       float gR[4], dg[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const float4 x = P4[2 * c], y = P4[2 * c + 1];
-        gR[c] = x.x + tau * (x.y + tau * (x.z + tau * (x.w + tau * (y.x + tau * y.y))));
-        dg[c] = x.y + tau * (2.f * x.z + tau * (3.f * x.w + tau * (4.f * y.x + tau * (5.f * y.y))));
+        float P[6];
+        if (g.p_bf16) {
+          const uint4 h = reinterpret_cast<const uint4*>(g.run_P)[run * 4 + c];
+          P[0] = __uint_as_float(h.x << 16);
+          P[1] = __uint_as_float(h.x & 0xFFFF0000u);
+          P[2] = __uint_as_float(h.y << 16);
+          P[3] = __uint_as_float(h.y & 0xFFFF0000u);
+          P[4] = __uint_as_float(h.z << 16);
+          P[5] = __uint_as_float(h.z & 0xFFFF0000u);
+        } else {
+          const float4 x = g.run_P[run * 8 + 2 * c], y = g.run_P[run * 8 + 2 * c + 1];
+          P[0] = x.x;
+          P[1] = x.y;
+          P[2] = x.z;
+          P[3] = x.w;
+          P[4] = y.x;
+          P[5] = y.y;
+        }
+        gR[c] = P[0] + tau * (P[1] + tau * (P[2] + tau * (P[3] + tau * (P[4] + tau * P[5]))));
+        dg[c] = P[1] + tau * (2.f * P[2] + tau * (3.f * P[3] + tau * (4.f * P[4] + tau * (5.f * P[5]))));
       }
       const float s = e0.x, u0 = e0.y, u1 = e0.z, u2 = e0.w, ds = e1.x, rr = e1.y;
       const float invd = l < g.n1 ? g.inv1 : g.inv2;
@@ -1158,6 +1188,7 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.run_l = run_l;
   g.run_rec = reinterpret_cast<uint4*>(runs);
   g.run_P = reinterpret_cast<float4*>(runs);
+  g.p_bf16 = bf16 ? 1 : 0;
   g.Tm = Tm;
   g.D = D;
   g.d_bf16 = bf16 ? 1 : 0;
