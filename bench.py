@@ -176,7 +176,7 @@ def _kernel_rooflines(cfg, big, real_nb, prof, steps, peaks):
       mom_gT     HBM: dE/dD read 4 M M_< B/atom, T and T_< 16 (M + M_<) B/atom
       mom_force  HBM: env rows 32 B + run index 4 B per real neighbour, run P 32 B per real
                  neighbour (upper bound of runs), force and virial 96 B/atom
-      fit_*      tensor: 2 rows K N per GEMM of the scope
+      fit_*      tensor: 2 rows K N per GEMM of the scope (fit_fused_tc: the whole net, both ways)
     Peaks: FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz; HBM and BF16 tensor as measured (the
     sustained tensor figure: these kernels run inside a long step)."""
     N = big.natoms
@@ -199,6 +199,7 @@ def _kernel_rooflines(cfg, big, real_nb, prof, steps, peaks):
         "fit_fwd_tc": ("tensor", fwd / 1e12, ten, "TFLOP/s"),
         "fit_fwd_last_tc": ("tensor", fwd_last / 1e12, ten, "TFLOP/s"),
         "fit_bwd_tc": ("tensor", bwd / 1e12, ten, "TFLOP/s"),
+        "fit_fused_tc": ("tensor", (fwd + fwd_last + bwd) / 1e12, ten, "TFLOP/s"),
     }
     out = {}
     for name, (ms_tot, nl) in prof.items():

@@ -29,7 +29,11 @@ uint16_t bf16_bits_rne(float f) {
 
 int skip_kind(int n_in, int n_out) { return n_out == n_in ? 1 : (n_out == 2 * n_in ? 2 : 0); }
 
-const CUtensorMap* weight_map(const DeviceModel& m, int t, int l, int dir, int box_rows) {
+}  // namespace
+
+// Tensor map of fitting layer l of type t: dir 0 the forward B operand W^T [n_out][n_in], dir 1
+// the backward one W [n_in][n_out]; box of 64 columns x box_rows rows; cached on the model.
+const CUtensorMap* fit_weight_map(const DeviceModel& m, int t, int l, int dir, int box_rows) {
   const long key = (((long)t * 64 + l) * 2 + dir) * 1024 + box_rows;
   for (auto& kv : m.tmap_cache)
     if (kv.first == key) return reinterpret_cast<const CUtensorMap*>(kv.second.data());
@@ -47,8 +51,6 @@ const CUtensorMap* weight_map(const DeviceModel& m, int t, int l, int dir, int b
   m.tmap_cache.emplace_back(key, std::move(buf));
   return reinterpret_cast<const CUtensorMap*>(m.tmap_cache.back().second.data());
 }
-
-}  // namespace
 
 int prepare_fit_bf16(DeviceModel& m, const double* params_host) {
   const int nfl = m.n_fit_layers, nh = nfl - 1;
@@ -90,6 +92,10 @@ int prepare_fit_bf16(DeviceModel& m, const double* params_host) {
 
 int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io, Arena& ar,
                    cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out) {
+  if (gDh_out && fit_fused_supported(m)) {  // the whole net in one kernel per tile
+    *gD_out = nullptr;
+    return run_fitting_fused(m, pc, Dbf, io, ar, st, gDh_out);
+  }
   const long N = pc.natoms;
   const int nfl = m.n_fit_layers, nh = nfl - 1;
   const int D = pc.M * pc.A;
@@ -110,7 +116,6 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
   float* E = ar.get<float>(N * ((m.fit[nh - 1].n_out + 63) / 64));
   float* gD = gDh_out ? nullptr : ar.get<float>(N * D);
   __nv_bfloat16* gDh = gDh_out ? ar.get<__nv_bfloat16>(N * D) : nullptr;
-  int* err = ar.get<int>(1);
   if (ar.measure) return DP_OK;
   if (!ar.ok()) {
     set_error("scratch allocation failed");
@@ -125,8 +130,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     base.tile_start[t] = tiles;
     if (t < nt) tiles += (io.type_start[t + 1] - io.type_start[t] + 127) / 128;
   }
-  base.err = err;
-  DP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  base.err = &io.status->timeout;  // bounded waits that give up are reported by the call
   const float* p32 = m.p32;
   // ---- forward ----
   for (int l = 0; l < nh; ++l) {
@@ -143,7 +147,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     for (int t = 0; t < nt; ++t) {
       const LayerDesc& L = m.fit[(size_t)t * nfl + l];
       a.bias[t] = p32 + L.w_off + (long)L.n_in * L.n_out;
-      const CUtensorMap* wm = weight_map(m, t, l, 0, a.BN);
+      const CUtensorMap* wm = fit_weight_map(m, t, l, 0, a.BN);
       if (!wm) return DP_E_CUDA;
       tb.m[t] = *wm;
       if (last) {
@@ -184,7 +188,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     if (rc != DP_OK) return rc;
     TcMaps tb;
     for (int t = 0; t < nt; ++t) {
-      const CUtensorMap* wm = weight_map(m, t, l, 1, a.BN);
+      const CUtensorMap* wm = fit_weight_map(m, t, l, 1, a.BN);
       if (!wm) return DP_E_CUDA;
       tb.m[t] = *wm;
       const LayerDesc& Lo = m.fit[(size_t)t * nfl + nh];

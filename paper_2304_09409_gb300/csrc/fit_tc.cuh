@@ -1,5 +1,6 @@
 // Tensor-core fitting net (BF16 operands, FP32 accumulation).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "path.cuh"
@@ -10,6 +11,16 @@ namespace dpgb {
 int prepare_fit_bf16(DeviceModel& m, const double* params_host);
 
 // Energies (and their FP64 sum) and dE/dD [N][M*M_<] (FP32) from the BF16 descriptor.
+// Tensor map of fitting layer l of type t (dir 0: W^T [n_out][n_in], dir 1: W [n_in][n_out]),
+// box of 64 columns x box_rows rows, cached on the model.
+const CUtensorMap* fit_weight_map(const DeviceModel& m, int t, int l, int dir, int box_rows);
+// The whole fitting net (forward to E_i, backward to dE/dD in BF16) in one kernel per 128-atom
+// tile, for nets of at most four hidden layers of width <= 256 (multiples of 16) with skips of
+// kind 0 or 1.
+bool fit_fused_supported(const DeviceModel& m);
+int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io,
+                      Arena& ar, cudaStream_t st, const __nv_bfloat16** gDh_out);
+
 // dE/dD of every atom: FP32 into *gD_out, or BF16 into *gDh_out when that is given.
 int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io, Arena& ar,
                    cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out = nullptr);
