@@ -115,7 +115,7 @@ int dp_build_nlist(dp_model* model, int natoms, const double* coord, const int* 
  * device memory and forbids other allocations, or a loop being captured into a CUDA graph.
  * It computes exactly what dp_build_nlist computes (same kernels, same bit-exact result)
  * but needs no model object and calls no allocating routine: its cell-list scratch is one
- * static device array of about 10.5 MiB that every GPU loading the library keeps until exit.
+ * static device array of about 13.3 MiB that every GPU loading the library keeps until exit.
  *   cfg: only ntypes, sel and rcut are used.
  *   coord [natoms*3] FP64, type [natoms]: device pointers.  box: host pointer (or NULL for
  *   open boundaries).  nl_j [natoms*Nc], nl_shift [natoms*Nc*3] int32: device pointers the

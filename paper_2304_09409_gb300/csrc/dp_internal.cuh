@@ -190,11 +190,20 @@ struct NlExtras {
   int nframes;
   double* tshift;
 };
-// Cell arrays are indexed by (type, cell): cell_count, cell_cursor [ntypes * ncells_total],
-// cell_start [ntypes * ncells_total + 1]; atom_key [natoms]; sorted_l, sorted_m [natoms].
+// Cell arrays are indexed by (type, cell): cell_count [ntypes * ncells_total], cell_start
+// [ntypes * ncells_total + 1]; per atom its key and rank within the key (atom_key, int2), its
+// entry in input order (atom_l, atom_m) and in sorted order (sorted_l, sorted_m) [natoms].
+struct NlScratch {
+  int* cell_count;
+  int* cell_start;
+  int2* atom_key;
+  float4* atom_l;
+  int4* atom_m;
+  float4* sorted_l;
+  int4* sorted_m;
+};
 cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
-                               int* cell_count, int* cell_start, int* cell_cursor, int* atom_key, float4* sorted_l,
-                               int4* sorted_m, int* nl_j, int* nl_code, int* counts, DevStatus* status,
+                               const NlScratch& sc, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st, const NlExtras* ex = nullptr);
 cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, DevStatus* status,
                              const TypeStartCheck& chk,

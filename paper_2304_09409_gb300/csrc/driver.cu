@@ -193,9 +193,10 @@ struct Bufs {
   double* coord;
   int* type;
   int *nl_j, *nl_code, *counts;
-  int *cell_count, *cell_start, *cell_cursor, *atom_key;
-  float4* sorted_l;
-  int4* sorted_m;
+  int *cell_count, *cell_start;
+  int2* atom_key;
+  float4 *atom_l, *sorted_l;
+  int4 *atom_m, *sorted_m;
   unsigned char* ftab;
   int* atom_frame;
   double* tshift;
@@ -216,8 +217,9 @@ void carve(Arena& ar, const DeviceModel& m, const FrameTables& T, bool own_nlist
     const long nkeys = (long)T.ncells * m.cfg.ntypes;
     b.cell_count = ar.get<int>(nkeys);
     b.cell_start = ar.get<int>(nkeys + 1);
-    b.cell_cursor = ar.get<int>(nkeys);
-    b.atom_key = ar.get<int>(N);
+    b.atom_key = ar.get<int2>(N);
+    b.atom_l = ar.get<float4>(N);
+    b.atom_m = ar.get<int4>(N);
     b.sorted_l = ar.get<float4>(N);
     b.sorted_m = ar.get<int4>(N);
   }
@@ -396,8 +398,8 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
       NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff()};
       NlExtras ex{b.perm, b.type_start, chk, d_boxes, T.periodic ? F : 0, T.periodic ? b.tshift : nullptr};
       ProfScope _ps(&md->prof, "nlist", s, 4);
-      DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
-                                     b.atom_key, b.sorted_l, b.sorted_m, b.nl_j, b.nl_code, b.counts, md->status, s,
+      const NlScratch sc{b.cell_count, b.cell_start, b.atom_key, b.atom_l, b.atom_m, b.sorted_l, b.sorted_m};
+      DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, sc, b.nl_j, b.nl_code, b.counts, md->status, s,
                                      &ex));
     } else {
       ProfScope _ps(&md->prof, "type_perm", s);
@@ -666,9 +668,9 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
     NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr, 1,
                T.max_noff()};
     ProfScope _ps(&md->prof, "nlist", st, 4);
-    DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, b.cell_count, b.cell_start, b.cell_cursor,
-                                   b.atom_key, b.sorted_l, b.sorted_m, nl->nl_j, nl->nl_code, nl->counts,
-                                   md->status, st));
+    const NlScratch sc{b.cell_count, b.cell_start, b.atom_key, b.atom_l, b.atom_m, b.sorted_l, b.sorted_m};
+    DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, sc, nl->nl_j, nl->nl_code, nl->counts, md->status,
+                                   st));
   }
   rc = read_status(md, st, n_overflow);
   if (rc != DP_OK && rc != DP_E_SEL_OVERFLOW) {

@@ -87,14 +87,17 @@ __device__ __forceinline__ Binned bin_atom(const NlGeom& g, const double* x) {
   return b;
 }
 
-// Key (type, cell) of every atom and the count of each key.  When asked, the same launch also
-// forms the 27 image translations t(n) = n0 h0 + n1 h1 + n2 h2, n in {-1,0,1}^3, of every frame
-// (rounded as the exact displacement rounds them).
+// Key (type, cell) of every atom, its rank among the atoms of that key (the count so far) and
+// its sorted entry (cell-local FP32 position with the atom index; image index m with the packed
+// cell coordinates).  When asked, the same launch also forms the 27 image translations
+// t(n) = n0 h0 + n1 h1 + n2 h2, n in {-1,0,1}^3, of every frame (rounded as the exact
+// displacement rounds them).
 __global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame,
                       const int* __restrict__ cell_off, int natoms, int ncells_total, int ntypes,
                       const double* __restrict__ coord, const int* __restrict__ type, int* __restrict__ cell_count,
-                      int* __restrict__ atom_key, DevStatus* __restrict__ st, const double* __restrict__ boxes,
-                      int nframes, double* __restrict__ tshift) {
+                      int2* __restrict__ atom_key, float4* __restrict__ atom_l, int4* __restrict__ atom_m,
+                      DevStatus* __restrict__ st, const double* __restrict__ boxes, int nframes,
+                      double* __restrict__ tshift) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (tshift)
     for (int k = i; k < 27 * nframes; k += gridDim.x * blockDim.x) {
@@ -111,13 +114,14 @@ __global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom
   const Binned b = bin_atom(g, coord + 3 * i);
   const int t = type[i];
   if (t < 0 || t >= ntypes) {  // reported; the atom takes part in no list
-    atom_key[i] = -1;
+    atom_key[i] = make_int2(-1, 0);
     atomicExch(&st->bad_type, 1);
     return;
   }
   const int key = t * ncells_total + (cell_off ? cell_off[fr] : 0) + (b.c[0] * g.ncell[1] + b.c[1]) * g.ncell[2] + b.c[2];
-  atom_key[i] = key;
-  atomicAdd(cell_count + key, 1);
+  atom_key[i] = make_int2(key, atomicAdd(cell_count + key, 1));
+  atom_l[i] = make_float4((float)b.l[0], (float)b.l[1], (float)b.l[2], __int_as_float(i));
+  atom_m[i] = make_int4(b.m[0], b.m[1], b.m[2], (b.c[0] << 20) | (b.c[1] << 10) | b.c[2]);
 }
 
 // Exclusive scan of n ints by one block.
@@ -158,15 +162,13 @@ __global__ void k_scan_excl(const int* __restrict__ in, int n, int* __restrict__
   if (threadIdx.x == 0) out[n] = carry;
 }
 
-// Sorted entries: cell-local position (FP32) with the atom index, and the image index m with
-// the cell's coordinates packed in 10-bit fields.  When asked, the sorted order also serves as
-// the type-sorted order of the path (perm, per-type starts), with the starts checked against
-// the ones the call was set up with.
-__global__ void k_fill(const NlGeom* __restrict__ G, const int* __restrict__ atom_frame, int natoms,
-                       const double* __restrict__ coord, const int* __restrict__ atom_key, int* __restrict__ cursor,
-                       float4* __restrict__ sorted_l, int4* __restrict__ sorted_m, int* __restrict__ perm,
-                       int* __restrict__ type_start, const int* __restrict__ cell_start, int ncells_total,
-                       int ntypes, DevStatus* __restrict__ st, const TypeStartCheck chk) {
+// Sorted entries (scattered from the per-atom ones: key start + rank).  When asked, the sorted
+// order also serves as the type-sorted order of the path (perm, per-type starts), with the starts
+// checked against the ones the call was set up with.
+__global__ void k_fill(int natoms, const int2* __restrict__ atom_key, const float4* __restrict__ atom_l,
+                       const int4* __restrict__ atom_m, float4* __restrict__ sorted_l, int4* __restrict__ sorted_m,
+                       int* __restrict__ perm, int* __restrict__ type_start, const int* __restrict__ cell_start,
+                       int ncells_total, int ntypes, DevStatus* __restrict__ st, const TypeStartCheck chk) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (perm && i <= ntypes) {
     const int v = cell_start[i * ncells_total];
@@ -174,13 +176,12 @@ __global__ void k_fill(const NlGeom* __restrict__ G, const int* __restrict__ ato
     if (chk.on && v != chk.v[i]) atomicExch(&st->type_change, 1);
   }
   if (i >= natoms) return;
-  const int key = atom_key[i];
-  if (key < 0) return;
-  const Binned b = bin_atom(G[atom_frame ? atom_frame[i] : 0], coord + 3 * i);
-  const int pos = atomicAdd(cursor + key, 1);
+  const int2 kr = atom_key[i];
+  if (kr.x < 0) return;
+  const int pos = cell_start[kr.x] + kr.y;
   if (perm) perm[pos] = i;
-  sorted_l[pos] = make_float4((float)b.l[0], (float)b.l[1], (float)b.l[2], __int_as_float(i));
-  sorted_m[pos] = make_int4(b.m[0], b.m[1], b.m[2], (b.c[0] << 20) | (b.c[1] << 10) | b.c[2]);
+  sorted_l[pos] = atom_l[i];
+  sorted_m[pos] = atom_m[i];
 }
 
 // Small integers to and from FP32 through the bit pattern (exact for |v| < 2^22): no
@@ -917,9 +918,12 @@ cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi, cudaS
 }
 
 cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
-                               int* cell_count, int* cell_start, int* cell_cursor, int* atom_key, float4* sorted_l,
-                               int4* sorted_m, int* nl_j, int* nl_code, int* counts, DevStatus* status,
+                               const NlScratch& sc, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st, const NlExtras* ex) {
+  int* cell_count = sc.cell_count;
+  int* cell_start = sc.cell_start;
+  const float4* sorted_l = sc.sorted_l;
+  const int4* sorted_m = sc.sorted_m;
   const int nkeys = L.ncells_total * ntypes;
   cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * nkeys, st);
   if (e != cudaSuccess) return e;
@@ -927,10 +931,10 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   TypeStartCheck nochk;
   std::memset(&nochk, 0, sizeof(nochk));
   k_bin<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, L.ncells_total, ntypes, coord, type,
-                            cell_count, atom_key, status, ex ? ex->boxes : nullptr, ex ? ex->nframes : 0,
-                            ex ? ex->tshift : nullptr);
-  k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, cell_cursor);
-  k_fill<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.natoms, coord, atom_key, cell_cursor, sorted_l, sorted_m,
+                            cell_count, sc.atom_key, sc.atom_l, sc.atom_m, status, ex ? ex->boxes : nullptr,
+                            ex ? ex->nframes : 0, ex ? ex->tshift : nullptr);
+  k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, nullptr);
+  k_fill<<<nb, 256, 0, st>>>(L.natoms, sc.atom_key, sc.atom_l, sc.atom_m, sc.sorted_l, sc.sorted_m,
                              ex ? ex->perm : nullptr, ex ? ex->type_start : nullptr, cell_start, L.ncells_total,
                              ntypes, status, ex ? ex->chk : nochk);
   const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));

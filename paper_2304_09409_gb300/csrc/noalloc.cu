@@ -31,9 +31,10 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kMaxKeys = (size_t)kMaxCells * DP_MAX_TYPES;
 constexpr size_t kOffCellCount = 0;
 constexpr size_t kOffCellStart = kOffCellCount + align256(sizeof(int) * kMaxKeys);
-constexpr size_t kOffCellCursor = kOffCellStart + align256(sizeof(int) * (kMaxKeys + 1));
-constexpr size_t kOffAtomKey = kOffCellCursor + align256(sizeof(int) * kMaxKeys);
-constexpr size_t kOffSortedL = kOffAtomKey + align256(sizeof(int) * kMaxAtoms);
+constexpr size_t kOffAtomKey = kOffCellStart + align256(sizeof(int) * (kMaxKeys + 1));
+constexpr size_t kOffAtomL = kOffAtomKey + align256(sizeof(int2) * kMaxAtoms);
+constexpr size_t kOffAtomM = kOffAtomL + align256(sizeof(float4) * kMaxAtoms);
+constexpr size_t kOffSortedL = kOffAtomM + align256(sizeof(int4) * kMaxAtoms);
 constexpr size_t kOffSortedM = kOffSortedL + align256(sizeof(float4) * kMaxAtoms);
 constexpr size_t kOffCode = kOffSortedM + align256(sizeof(int4) * kMaxAtoms);
 constexpr size_t kOffCounts = kOffCode + align256(sizeof(int) * kMaxSlots);
@@ -124,8 +125,9 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   cudaStream_t st = (cudaStream_t)stream;
   int* cell_count = reinterpret_cast<int*>(s + kOffCellCount);
   int* cell_start = reinterpret_cast<int*>(s + kOffCellStart);
-  int* cell_cursor = reinterpret_cast<int*>(s + kOffCellCursor);
-  int* atom_key = reinterpret_cast<int*>(s + kOffAtomKey);
+  int2* atom_key = reinterpret_cast<int2*>(s + kOffAtomKey);
+  float4* atom_l = reinterpret_cast<float4*>(s + kOffAtomL);
+  int4* atom_m = reinterpret_cast<int4*>(s + kOffAtomM);
   float4* sorted_l = reinterpret_cast<float4*>(s + kOffSortedL);
   int4* sorted_m = reinterpret_cast<int4*>(s + kOffSortedM);
   int* code = reinterpret_cast<int*>(s + kOffCode);
@@ -152,8 +154,8 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   DP_CUDA_TRY(cudaMemcpyAsync(geom, &g, sizeof(NlGeom), cudaMemcpyHostToDevice, st));
   const NlLaunch L{natoms, g.ncell[0] * g.ncell[1] * g.ncell[2], g.cap, geom, nullptr, nullptr, 1,
                    (2 * g.K[0] + 1) * (2 * g.K[1] + 1) * (2 * g.K[2] + 1)};
-  DP_CUDA_TRY(launch_nlist_build(L, cfg->ntypes, coord, type, cell_count, cell_start, cell_cursor, atom_key, sorted_l,
-                                 sorted_m, nl_j, code, counts, status, st));
+  const NlScratch sc{cell_count, cell_start, atom_key, atom_l, atom_m, sorted_l, sorted_m};
+  DP_CUDA_TRY(launch_nlist_build(L, cfg->ntypes, coord, type, sc, nl_j, code, counts, status, st));
   const long n = (long)natoms * nc;
   k_unpack_shift<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(code, n, nl_shift);
   DP_CUDA_TRY(cudaGetLastError());
