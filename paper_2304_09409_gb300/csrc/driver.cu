@@ -435,6 +435,9 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     io.atom_virial = b.atom_virial;
     io.status = md->status;
     io.epart = b.epart;
+    io.atom_l = own_nlist ? b.atom_l : nullptr;
+    io.atom_m = own_nlist ? b.atom_m : nullptr;
+    io.geoms = own_nlist ? d_geoms : nullptr;
     if (gr) {
       {
         ProfScope _ps(&md->prof, "param_grad", s);

@@ -39,14 +39,12 @@ __device__ __forceinline__ void pair_env<double>(double d0, double d1, double d2
   u[2] = d2 * ir;
 }
 
-template <>
-__device__ __forceinline__ void pair_env<float>(double d0, double d1, double d2, double, double rs, double rc,
-                                                double, float& r, float& s, float& ds, float* u) {
-  // The displacement itself is exact FP64 (it cancels large coordinates); everything after
-  // it is FP32.  Near r_c the polynomial of Eq. (switch) is evaluated in the equivalent form
-  // 1 - x^3 (6x^2 - 15x + 10) = y^3 (6y^2 - 15y + 10) with y = 1 - x = (r_c - r)/(r_c - r_s),
-  // which has no cancellation as r -> r_c, so FP32 keeps full relative precision there.
-  const float x0 = (float)d0, x1 = (float)d1, x2 = (float)d2;
+// FP32 form from an FP32 displacement.  Near r_c the polynomial of Eq. (switch) is evaluated in
+// the equivalent form 1 - x^3 (6x^2 - 15x + 10) = y^3 (6y^2 - 15y + 10) with
+// y = 1 - x = (r_c - r)/(r_c - r_s), which has no cancellation as r -> r_c, so FP32 keeps full
+// relative precision there.
+__device__ __forceinline__ void pair_env_f32(float x0, float x1, float x2, double rs, double rc, float& r, float& s,
+                                             float& ds, float* u) {
   r = sqrtf(x0 * x0 + x1 * x1 + x2 * x2);
   const float frs = (float)rs, frc = (float)rc;
   if (r < frs) {
@@ -68,6 +66,13 @@ __device__ __forceinline__ void pair_env<float>(double d0, double d1, double d2,
   u[0] = x0 * ir;
   u[1] = x1 * ir;
   u[2] = x2 * ir;
+}
+
+// FP32 form from the exact FP64 displacement (which cancels large coordinates).
+template <>
+__device__ __forceinline__ void pair_env<float>(double d0, double d1, double d2, double, double rs, double rc,
+                                                double, float& r, float& s, float& ds, float* u) {
+  pair_env_f32((float)d0, (float)d1, (float)d2, rs, rc, r, s, ds, u);
 }
 
 // FP32 -> FP64 widening with integer operations: exact for normal numbers (subnormals flush to

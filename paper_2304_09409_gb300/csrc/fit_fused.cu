@@ -55,7 +55,8 @@ struct FusedArgs {
   const float* w_last[DP_MAX_TYPES];
   float b_last[DP_MAX_TYPES];
   float* gate;          // [nh - 1][rows][kGateLd]: 1 - t_l^2 of the inner hidden layers
-  float* e_out;         // [rows] atomic energies (sorted order)
+  const int* perm;      // sorted row -> atom
+  double* atom_e;       // [atoms] atomic energies, input order
   __nv_bfloat16* gD;    // [rows][KD] dE/dD
   int* err;
 };
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       if (last) {
         s_e[half * FBM + rl] = e_acc;
         bar_sync(1, kEpiThreads);
-        if (half == 0 && rv) g.e_out[row] = s_e[rl] + s_e[FBM + rl] + g.b_last[t];
+        if (half == 0 && rv) g.atom_e[g.perm[row]] = (double)(s_e[rl] + s_e[FBM + rl] + g.b_last[t]);
       }
       release(!last);
     }
@@ -373,7 +374,6 @@ int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bflo
   const int nt = pc.ntypes;
   const int KD = pc.M * pc.A;
   float* gate = ar.get<float>((long)(nh > 1 ? nh - 1 : 1) * N * kGateLd);
-  float* E = ar.get<float>(N);
   __nv_bfloat16* gD = ar.get<__nv_bfloat16>(N * KD);
   if (ar.measure) return DP_OK;
   if (!ar.ok()) {
@@ -415,7 +415,8 @@ int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bflo
     a.b_last[t] = m.fit_out_bias[t];
   }
   a.gate = gate;
-  a.e_out = E;
+  a.perm = io.perm;
+  a.atom_e = io.atom_energy;
   a.gD = gD;
   a.err = &io.status->timeout;  // bounded waits that give up are reported by the call
   if (tiles > 0) {
@@ -424,10 +425,6 @@ int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bflo
     DP_CUDA_TRY(allow_max_smem(k_fit_fused));
     k_fit_fused<<<tiles, kFThreads, smem, st>>>(mp, a);
     DP_CUDA_TRY(cudaGetLastError());
-  }
-  {
-    ProfScope _ps(io.prof, "energy_sum", st);
-    DP_CUDA_TRY(launch_energy_f32(E, 1, io.perm, (int)N, io.atom_energy, st));
   }
   *gDh_out = gD;
   return DP_OK;

@@ -86,6 +86,10 @@ struct MomArgs {
   int* gtx;            // its row scales [tiles][128]
   int* table_range;
   int* err;
+  // mixed mode with the list built in the same call: FP32 displacements from cell-local positions
+  const float4* atom_l;
+  const int4* atom_m;
+  const NlGeom* geoms;
 };
 
 // Interval of s (at most lcap: the list order caps it), tau = (s - x_l) / Delta_l, 1/Delta_l.
@@ -224,6 +228,18 @@ __global__ void __launch_bounds__(256)
   const int i = g.perm[p];
   const int kb0 = g.sel_off[t], kb1 = g.sel_off[t + 1];
   const long rbase = (long)p * pc.nc + kb0;  // first run record of this list
+  // Mixed mode: the displacement in FP32 as (l_j - l_i) + delta . h_c from the cell-local
+  // positions of the list build (delta: the virtual-cell offset of the image of j), with the
+  // list build's error bound; pairs within that bound of r_c take the exact FP64 displacement.
+  const bool f32d = NPASS == 1 && g.atom_l != nullptr;
+  float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+  int4 mi = make_int4(0, 0, 0, 0);
+  const NlGeom* G = nullptr;
+  if (f32d) {
+    li = g.atom_l[i];
+    mi = g.atom_m[i];
+    G = g.geoms + frame_of(pc, i);
+  }
   int lmin = INT_MAX;                        // running minimum of the interval
   int carry_l = -1;                          // interval of the run open at the last batch's end
   float carry[24];
@@ -240,9 +256,32 @@ __global__ void __launch_bounds__(256)
     int l = INT_MAX;
     float r = 0.f, s = 0.f, ds = 0.f, u[3] = {0.f, 0.f, 0.f}, tau = 0.f;
     if (valid) {
-      double d0, d1, d2;
-      listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d0, d1, d2);
-      pair_env<float>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
+      const int code = nl_code[(long)i * pc.nc + k];
+      bool exact = true;
+      if (f32d) {
+        const float4 lj = g.atom_l[j];
+        const int4 mj = g.atom_m[j];
+        int n0, n1, n2;
+        unpack_shift(code, n0, n1, n2);
+        const int e0 = ((mj.w >> 20) & 1023) - ((mi.w >> 20) & 1023) + (n0 + mj.x - mi.x) * G->ncell[0];
+        const int e1 = ((mj.w >> 10) & 1023) - ((mi.w >> 10) & 1023) + (n1 + mj.y - mi.y) * G->ncell[1];
+        const int e2 = (mj.w & 1023) - (mi.w & 1023) + (n2 + mj.z - mi.z) * G->ncell[2];
+        if (abs(e0) <= G->K[0] && abs(e1) <= G->K[1] && abs(e2) <= G->K[2]) {
+          const float f0 = (float)e0, f1 = (float)e1, f2 = (float)e2;
+          const float x0 = (lj.x - li.x) + fmaf(f2, G->hc[6], fmaf(f1, G->hc[3], f0 * G->hc[0]));
+          const float x1 = (lj.y - li.y) + fmaf(f2, G->hc[7], fmaf(f1, G->hc[4], f0 * G->hc[1]));
+          const float x2 = (lj.z - li.z) + fmaf(f2, G->hc[8], fmaf(f1, G->hc[5], f0 * G->hc[2]));
+          if (fmaf(x0, x0, fmaf(x1, x1, x2 * x2)) < G->rc2_in) {
+            pair_env_f32(x0, x1, x2, pc.rs, pc.rc, r, s, ds, u);
+            exact = false;
+          }
+        }
+      }
+      if (exact) {
+        double d0, d1, d2;
+        listed_disp(coord + 3 * i, coord + 3 * j, code, pc, frame_of(pc, i), d0, d1, d2);
+        pair_env<float>(d0, d1, d2, 0.0, pc.rs, pc.rc, pc.near2, r, s, ds, u);
+      }
       float invd;
       l = mom_interval(g, s, INT_MAX, tau, invd, oor);
     }
@@ -1189,6 +1228,9 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.run_rec = reinterpret_cast<uint4*>(runs);
   g.run_P = reinterpret_cast<float4*>(runs);
   g.p_bf16 = bf16 ? 1 : 0;
+  g.atom_l = io.atom_l;
+  g.atom_m = io.atom_m;
+  g.geoms = io.geoms;
   g.Tm = Tm;
   g.D = D;
   g.d_bf16 = bf16 ? 1 : 0;

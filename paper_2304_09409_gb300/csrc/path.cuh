@@ -141,6 +141,11 @@ struct PathIO {
   double* atom_virial;  // device [N][9] per-atom virial (input order)
   DevStatus* status;    // device status words
   double* epart;        // device scratch for per-block energy partials [ceil(N/256)]
+  // from the list build of this call (null with an external list): per atom (input order) its
+  // cell-local FP32 position and its image / packed cell coordinates, and each frame's geometry
+  const float4* atom_l;
+  const int4* atom_m;
+  const NlGeom* geoms;
 };
 
 struct __align__(32) D4 {
