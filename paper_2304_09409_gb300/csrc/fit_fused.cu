@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
   uint64_t* bempty = bfull + 2;     // [2]
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bempty + 2);
   float* s_e = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128]
+  float* s_bias = s_e + 2 * FBM;                           // [kFL][256] biases of the hidden layers
+  float* s_wl = s_bias + kFL * 256;                        // [256] weights of the output layer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int t = 0;
@@ -226,13 +228,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       fence_async_smem();  // the A operand written here is read by the tensor cores next
       mbar_arrive(afree);
     };
-    const float* wl = g.w_last[t];
+    // biases and output weights of this tile's type into shared memory (while the first GEMM runs)
+    for (int l = 0; l < nh; ++l)
+      for (int c = threadIdx.x; c < g.width[l + 1]; c += kEpiThreads) s_bias[l * 256 + c] = __ldg(g.bias[t][l] + c);
+    for (int c = threadIdx.x; c < g.width[nh]; c += kEpiThreads) s_wl[c] = __ldg(g.w_last[t] + c);
+    bar_sync(1, kEpiThreads);
+    const float* wl = s_wl;
     // forward
     for (int l = 0; l < nh; ++l) {
       wait_acc();
       const int N = g.width[l + 1];
       const bool last = (l == nh - 1), sk = g.skip[l] == 1;
-      const float* bias = g.bias[t][l];
+      const float* bias = s_bias + l * 256;
       float* gate = g.gate + ((long)l * rows + row) * kGateLd;
       float e_acc = 0.f;
       for (int q16 = half; q16 < N / 16; q16 += 2) {
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
         float y[16], gt[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const float th = tanhf(__uint_as_float(ra[i]) + __ldg(bias + col + i));
+          const float th = tanhf(__uint_as_float(ra[i]) + bias[col + i]);
           y[i] = th + (sk ? __uint_as_float(ry[i]) : 0.f);
           gt[i] = 1.f - th * th;
         }
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
           float gz[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float w = __ldg(wl + col + i);
+            const float w = wl[col + i];
             e_acc += y[i] * w;
             gz[i] = w * gt[i];
           }
@@ -277,10 +284,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
     }
     // backward of layers nh-1 .. 1: gz_{l-1} into the A operand, gy_{l-1} kept for the next skip
     for (int l = nh - 1; l >= 1; --l) {
-      wait_acc();
       const int N = g.width[l];
       const bool top = (l == nh - 1), sk = g.skip[l] == 1, keep = (l - 1 >= 1);
       const float* gate = g.gate + ((long)(l - 1) * rows + row) * kGateLd;
+      if (rv)  // this row's gates towards L1 while the GEMM of this phase runs
+        for (int q16 = half; q16 < N / 16; q16 += 2) prefetch_l1(gate + q16 * 16);
+      wait_acc();
       for (int q16 = half; q16 < N / 16; q16 += 2) {
         const int col = q16 * 16;
         uint32_t ra[16], ry[16];
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           float v = __uint_as_float(ra[i]);
-          if (sk) v += top ? __ldg(wl + col + i) : __uint_as_float(ry[i]);
+          if (sk) v += top ? wl[col + i] : __uint_as_float(ry[i]);
           gy[i] = v;
           gz[i] = v * gt[i];
         }
@@ -348,7 +357,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
   if (warp == 8) tmem_dealloc(tmem, 512);
 }
 
-size_t fused_smem() { return (size_t)kRing * kStage + kAb + 16 * 8 + 16 + 2 * FBM * 4 + 1024; }
+size_t fused_smem() {
+  return (size_t)kRing * kStage + kAb + 16 * 8 + 16 + (2 * FBM + kFL * 256 + 256) * 4 + 1024;
+}
 
 }  // namespace
 

@@ -75,6 +75,9 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)) : "memory");
 }
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // All but the most recent group (wait1), or every group (wait0), of this thread have landed.
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
@@ -133,7 +136,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t tmem, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// 16 consecutive FP32 columns of this thread's tensor-memory lane.
 // 16 columns of the warp's 32 TMEM lanes into registers without waiting: several loads can be
 // in flight before one tmem_wait_ld().
 __device__ __forceinline__ void tmem_ld16_async(uint32_t addr, uint32_t* r) {
@@ -161,6 +163,7 @@ __device__ __forceinline__ void tmem_st16(uint32_t addr, const float* v) {
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive FP32 columns of this thread's tensor-memory lane (waits for them).
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v) {
   uint32_t r[16];
   asm volatile(
