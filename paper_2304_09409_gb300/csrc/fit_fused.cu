@@ -61,6 +61,14 @@ struct FusedArgs {
   int* err;
 };
 
+// tanh by the hardware approximation (relative error about 2^-11): the activations leave the
+// epilogue as BF16 operands (2^-9), so its error does not survive into the next layer.
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void ab_store16(unsigned char* Ab, int rl, int col, const float* x) {
   uint32_t w[8];
 #pragma unroll
@@ -242,36 +250,46 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       const float* bias = s_bias + l * 256;
       float* gate = g.gate + ((long)l * rows + row) * kGateLd;
       float e_acc = 0.f;
-      for (int q16 = half; q16 < N / 16; q16 += 2) {
-        const int col = q16 * 16;
-        uint32_t ra[16], ry[16];
-        tmem_ld16_async(tb + col, ra);
-        if (sk) tmem_ld16_async(tb + 256 + col, ry);
-        tmem_wait_ld();
-        float y[16], gt[16];
+      const int nq = N / 16;
+      for (int q0 = half; q0 < nq; q0 += 4) {  // two 16-column pieces per wait
+        uint32_t rab[2][16], ryb[2][16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float th = tanhf(__uint_as_float(ra[i]) + bias[col + i]);
-          y[i] = th + (sk ? __uint_as_float(ry[i]) : 0.f);
-          gt[i] = 1.f - th * th;
-        }
-        if (!last) {
-          ab_store16(Ab, rl, col, y);
-          tmem_st16(tb + 256 + col, y);  // the residual stream of the next layer
-          if (rv) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              reinterpret_cast<float4*>(gate + col)[q] = make_float4(gt[4 * q], gt[4 * q + 1], gt[4 * q + 2], gt[4 * q + 3]);
+        for (int u = 0; u < 2; ++u)
+          if (q0 + 2 * u < nq) {
+            tmem_ld16_async(tb + (q0 + 2 * u) * 16, rab[u]);
+            if (sk) tmem_ld16_async(tb + 256 + (q0 + 2 * u) * 16, ryb[u]);
           }
-        } else {
-          float gz[16];
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (q0 + 2 * u >= nq) break;
+          const int col = (q0 + 2 * u) * 16;
+          float y[16], gt[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float w = wl[col + i];
-            e_acc += y[i] * w;
-            gz[i] = w * gt[i];
+            const float th = tanh_hw(__uint_as_float(rab[u][i]) + bias[col + i]);
+            y[i] = th + (sk ? __uint_as_float(ryb[u][i]) : 0.f);
+            gt[i] = 1.f - th * th;
           }
-          ab_store16(Ab, rl, col, gz);
+          if (!last) {
+            ab_store16(Ab, rl, col, y);
+            tmem_st16(tb + 256 + col, y);  // the residual stream of the next layer
+            if (rv) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                reinterpret_cast<float4*>(gate + col)[q] =
+                    make_float4(gt[4 * q], gt[4 * q + 1], gt[4 * q + 2], gt[4 * q + 3]);
+            }
+          } else {
+            float gz[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float w = wl[col + i];
+              e_acc += y[i] * w;
+              gz[i] = w * gt[i];
+            }
+            ab_store16(Ab, rl, col, gz);
+          }
         }
       }
       pad(N);
@@ -290,36 +308,45 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       if (rv)  // this row's gates towards L1 while the GEMM of this phase runs
         for (int q16 = half; q16 < N / 16; q16 += 2) prefetch_l1(gate + q16 * 16);
       wait_acc();
-      for (int q16 = half; q16 < N / 16; q16 += 2) {
-        const int col = q16 * 16;
-        uint32_t ra[16], ry[16];
-        tmem_ld16_async(tb + col, ra);
-        if (sk && !top) tmem_ld16_async(tb + 256 + col, ry);
-        tmem_wait_ld();
-        float gt[16];
-        if (rv) {
+      const int nq = N / 16;
+      for (int q0 = half; q0 < nq; q0 += 4) {  // two 16-column pieces per wait
+        uint32_t rab[2][16], ryb[2][16];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 x = reinterpret_cast<const float4*>(gate + col)[q];
-            gt[4 * q] = x.x;
-            gt[4 * q + 1] = x.y;
-            gt[4 * q + 2] = x.z;
-            gt[4 * q + 3] = x.w;
+        for (int u = 0; u < 2; ++u)
+          if (q0 + 2 * u < nq) {
+            tmem_ld16_async(tb + (q0 + 2 * u) * 16, rab[u]);
+            if (sk && !top) tmem_ld16_async(tb + 256 + (q0 + 2 * u) * 16, ryb[u]);
           }
-        } else {
+        tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 16; ++i) gt[i] = 0.f;
-        }
-        float gy[16], gz[16];
+        for (int u = 0; u < 2; ++u) {
+          if (q0 + 2 * u >= nq) break;
+          const int col = (q0 + 2 * u) * 16;
+          float gt[16];
+          if (rv) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float v = __uint_as_float(ra[i]);
-          if (sk) v += top ? wl[col + i] : __uint_as_float(ry[i]);
-          gy[i] = v;
-          gz[i] = v * gt[i];
+            for (int q = 0; q < 4; ++q) {
+              const float4 x = reinterpret_cast<const float4*>(gate + col)[q];
+              gt[4 * q] = x.x;
+              gt[4 * q + 1] = x.y;
+              gt[4 * q + 2] = x.z;
+              gt[4 * q + 3] = x.w;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) gt[i] = 0.f;
+          }
+          float gy[16], gz[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float v = __uint_as_float(rab[u][i]);
+            if (sk) v += top ? wl[col + i] : __uint_as_float(ryb[u][i]);
+            gy[i] = v;
+            gz[i] = v * gt[i];
+          }
+          ab_store16(Ab, rl, col, gz);
+          if (keep) tmem_st16(tb + 256 + col, gy);
         }
-        ab_store16(Ab, rl, col, gz);
-        if (keep) tmem_st16(tb + 256 + col, gy);
       }
       pad(N);
       release(keep);
@@ -331,19 +358,24 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       __syncwarp();
       tc_fence_after();
       const int N = min(256, KD - c * 256);
-      for (int q16 = half; q16 < N / 16; q16 += 2) {
-        const int col = q16 * 16;
-        uint32_t ra[16];
-        tmem_ld16_async(tb + (uint32_t)(buf * 256) + col, ra);
+      const int nq = N / 16;  // 16-column pieces; this warp takes every other one, four loads per wait
+      for (int q0 = half; q0 < nq; q0 += 8) {
+        uint32_t ra[4][16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (q0 + 2 * u < nq) tmem_ld16_async(tb + (uint32_t)(buf * 256) + (q0 + 2 * u) * 16, ra[u]);
         tmem_wait_ld();
-        if (rv) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (q0 + 2 * u >= nq || !rv) continue;
           uint32_t w[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(__uint_as_float(ra[2 * q]), __uint_as_float(ra[2 * q + 1]));
+            const __nv_bfloat162 pr =
+                __floats2bfloat162_rn(__uint_as_float(ra[u][2 * q]), __uint_as_float(ra[u][2 * q + 1]));
             w[q] = *reinterpret_cast<const uint32_t*>(&pr);
           }
-          uint4* dst = reinterpret_cast<uint4*>(g.gD + (long)row * KD + c * 256 + col);
+          uint4* dst = reinterpret_cast<uint4*>(g.gD + (long)row * KD + c * 256 + (q0 + 2 * u) * 16);
           dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
           dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
         }
