@@ -57,7 +57,7 @@ struct FusedArgs {
   float* gate;          // [nh - 1][rows][kGateLd]: 1 - t_l^2 of the inner hidden layers
   const int* perm;      // sorted row -> atom
   double* atom_e;       // [atoms] atomic energies, input order
-  __nv_bfloat16* gD;    // [rows][KD] dE/dD
+  __nv_bfloat16* gD;    // dE/dD, BF16, tile-blocked (fit_tc.cuh)
   int* err;
 };
 
@@ -359,6 +359,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       tc_fence_after();
       const int N = min(256, KD - c * 256);
       const int nq = N / 16;  // 16-column pieces; this warp takes every other one, four loads per wait
+      const int nr = min(FBM, row_end - row0);  // rows of this tile (tile-blocked layout)
+      __nv_bfloat16* gtile = g.gD + (long)row0 * KD;
       for (int q0 = half; q0 < nq; q0 += 8) {
         uint32_t ra[4][16];
 #pragma unroll
@@ -375,9 +377,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
                 __floats2bfloat162_rn(__uint_as_float(ra[u][2 * q]), __uint_as_float(ra[u][2 * q + 1]));
             w[q] = *reinterpret_cast<const uint32_t*>(&pr);
           }
-          uint4* dst = reinterpret_cast<uint4*>(g.gD + (long)row * KD + c * 256 + (q0 + 2 * u) * 16);
-          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          // two 8-column groups: consecutive rows of the warp write consecutive 16-byte chunks
+          const int g8 = (c * 256 + (q0 + 2 * u) * 16) >> 3;
+          uint4* d0 = reinterpret_cast<uint4*>(gtile + ((long)g8 * nr + rl) * 8);
+          uint4* d1 = reinterpret_cast<uint4*>(gtile + ((long)(g8 + 1) * nr + rl) * 8);
+          *d0 = make_uint4(w[0], w[1], w[2], w[3]);
+          *d1 = make_uint4(w[4], w[5], w[6], w[7]);
         }
       }
       tc_fence_before();

@@ -21,7 +21,11 @@ bool fit_fused_supported(const DeviceModel& m);
 int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io,
                       Arena& ar, cudaStream_t st, const __nv_bfloat16** gDh_out);
 
-// dE/dD of every atom: FP32 into *gD_out, or BF16 into *gDh_out when that is given.
+// dE/dD of every atom: FP32 [rows][KD] into *gD_out, or BF16 into *gDh_out when that is given.
+// The BF16 array is tile-blocked: the rows of each type form tiles of 128 from the type's first
+// row; tile rows [row0, row0 + nr) occupy [row0 * KD, (row0 + nr) * KD) and element (row0 + r, col)
+// sits at ((col / 8) * nr + r) * 8 + col % 8 within it (8-column groups, rows contiguous), so
+// thread-per-row epilogues write whole 512-byte runs per warp.
 int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io, Arena& ar,
                    cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out = nullptr);
 

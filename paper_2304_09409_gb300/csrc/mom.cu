@@ -645,6 +645,12 @@ __global__ void __launch_bounds__(kRows)
         const int at = q * kGroupAtoms + warp;  // atom of the tile
         const bool va = row0 + at < row_end;   // warp-uniform
         const long gdo = (long)(row0 + at) * g.M * g.A;
+        // BF16 dE/dD is tile-blocked: 128-row tiles from the type's first row, 8-column groups
+        const int KD = g.M * g.A;
+        const int fr0 = g.row_start[ti] + (((row0 + at) - g.row_start[ti]) & ~127);
+        const int fnr = min(128, g.row_start[ti + 1] - fr0);
+        const __nv_bfloat16* gtile = g.gDh ? g.gDh + (long)fr0 * KD : nullptr;
+        const int fr = row0 + at - fr0;
         const float* Ta = g.Tm + (long)(row0 + at) * g.M * 4;
         int ex = 0;
         if (va) {
@@ -660,10 +666,9 @@ __global__ void __launch_bounds__(kRows)
             if (m < g.M) {
               float gd[16];
               if (g.gDh && g.A == 16) {
-                const uint4* h4 = reinterpret_cast<const uint4*>(g.gDh + gdo + m * 16);
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                  const uint4 x = h4[e];
+                  const uint4 x = *reinterpret_cast<const uint4*>(gtile + ((long)(2 * m + e) * fnr + fr) * 8);
                   const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                   for (int k = 0; k < 4; ++k) {
@@ -673,7 +678,10 @@ __global__ void __launch_bounds__(kRows)
                 }
               } else if (g.gDh) {
 #pragma unroll
-                for (int l = 0; l < 16; ++l) gd[l] = l < g.A ? __bfloat162float(g.gDh[gdo + m * g.A + l]) : 0.f;
+                for (int l = 0; l < 16; ++l) {
+                  const int col = m * g.A + l;
+                  gd[l] = l < g.A ? __bfloat162float(gtile[((long)(col >> 3) * fnr + fr) * 8 + (col & 7)]) : 0.f;
+                }
               } else if (g.A == 16) {
                 const float4* g4 = reinterpret_cast<const float4*>(g.gD + gdo + m * 16);
 #pragma unroll

@@ -165,21 +165,13 @@ __global__ void __launch_bounds__(kThreads)
       tmem_ld16(tbase + c, v);
       const int cb = col0 + c;
       if (!rv || cb >= g.N) continue;
-      if (g.out_bf16) {  // BF16 output (16 values = two 16-byte chunks)
-        __nv_bfloat16* dh = g.out_bf16 + (long)row * g.N + cb;
-        if (cb + 16 <= g.N && (g.N & 7) == 0) {
-          uint32_t w[8];
+      if (g.out_bf16) {  // BF16 output, tile-blocked (8-column groups, rows of the tile contiguous)
+        const int nr = min(BM, row_end - row0);
+        __nv_bfloat16* tile = g.out_bf16 + (long)row0 * g.N;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            w[q] = *reinterpret_cast<const uint32_t*>(&pr);
-          }
-          reinterpret_cast<uint4*>(dh)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-          reinterpret_cast<uint4*>(dh)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (cb + i < g.N) dh[i] = __float2bfloat16_rn(v[i]);
+        for (int i = 0; i < 16; ++i) {
+          const int col = cb + i;
+          if (col < g.N) tile[((long)(col >> 3) * nr + (row - row0)) * 8 + (col & 7)] = __float2bfloat16_rn(v[i]);
         }
         continue;
       }
