@@ -54,7 +54,8 @@ struct FusedArgs {
   const float* bias[DP_MAX_TYPES][kFL];
   const float* w_last[DP_MAX_TYPES];
   float b_last[DP_MAX_TYPES];
-  float* gate;          // [nh - 1][rows][kGateLd]: 1 - t_l^2 of the inner hidden layers
+  float* gate;          // [nh - 1][rows * kGateLd]: 1 - t_l^2 of the inner hidden layers, tile-blocked
+                        // (4-column groups, the tile's rows contiguous)
   const int* perm;      // sorted row -> atom
   double* atom_e;       // [atoms] atomic energies, input order
   __nv_bfloat16* gD;    // dE/dD, BF16, tile-blocked (fit_tc.cuh)
@@ -215,6 +216,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
     const int rl = quad * 32 + lane;
     const int row = row0 + rl;
     const bool rv = row < row_end;
+    const int nr = min(FBM, row_end - row0);  // rows of this tile (tile-blocked scratch and dE/dD)
+    // gate of (row, col) in layer l's scratch: 4-column groups of the tile's rows, contiguous
+    auto gate_at = [&](int l, int col) -> float* {
+      return g.gate + (long)l * rows * kGateLd + (long)row0 * kGateLd + ((long)(col >> 2) * nr + rl) * 4;
+    };
     const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16);
     int acf = 0;
     auto wait_acc = [&]() {
@@ -248,7 +254,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       const int N = g.width[l + 1];
       const bool last = (l == nh - 1), sk = g.skip[l] == 1;
       const float* bias = s_bias + l * 256;
-      float* gate = g.gate + ((long)l * rows + row) * kGateLd;
       float e_acc = 0.f;
       const int nq = N / 16;
       for (int q0 = half; q0 < nq; q0 += 4) {  // two 16-column pieces per wait
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
             if (rv) {
 #pragma unroll
               for (int q = 0; q < 4; ++q)
-                reinterpret_cast<float4*>(gate + col)[q] =
+                *reinterpret_cast<float4*>(gate_at(l, col + 4 * q)) =
                     make_float4(gt[4 * q], gt[4 * q + 1], gt[4 * q + 2], gt[4 * q + 3]);
             }
           } else {
@@ -304,9 +309,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
     for (int l = nh - 1; l >= 1; --l) {
       const int N = g.width[l];
       const bool top = (l == nh - 1), sk = g.skip[l] == 1, keep = (l - 1 >= 1);
-      const float* gate = g.gate + ((long)(l - 1) * rows + row) * kGateLd;
       if (rv)  // this row's gates towards L1 while the GEMM of this phase runs
-        for (int q16 = half; q16 < N / 16; q16 += 2) prefetch_l1(gate + q16 * 16);
+        for (int q16 = half; q16 < N / 16; q16 += 2)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) prefetch_l1(gate_at(l - 1, q16 * 16 + 4 * q));
       wait_acc();
       const int nq = N / 16;
       for (int q0 = half; q0 < nq; q0 += 4) {  // two 16-column pieces per wait
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
           if (rv) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const float4 x = reinterpret_cast<const float4*>(gate + col)[q];
+              const float4 x = *reinterpret_cast<const float4*>(gate_at(l - 1, col + 4 * q));
               gt[4 * q] = x.x;
               gt[4 * q + 1] = x.y;
               gt[4 * q + 2] = x.z;
@@ -359,7 +365,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fit_fused(const __grid_constan
       tc_fence_after();
       const int N = min(256, KD - c * 256);
       const int nq = N / 16;  // 16-column pieces; this warp takes every other one, four loads per wait
-      const int nr = min(FBM, row_end - row0);  // rows of this tile (tile-blocked layout)
       __nv_bfloat16* gtile = g.gD + (long)row0 * KD;
       for (int q0 = half; q0 < nq; q0 += 8) {
         uint32_t ra[4][16];
