@@ -566,11 +566,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (q >= 16 && !two) break;
         const float x = nkb > 0 ? __uint_as_float(raw[q]) * g.inv_nc : 0.f;
         smT[(ae * (NPAD + 1) + c0 + q) * 4 + c] = x;
-        if (valid_e && c0 + q < g.M) g.Tm[((long)pe * g.M + c0 + q) * 4 + c] = x;
       }
     }
     tc_fence_before();
     bar_sync(1, kRows);
+    {  // T of the tile's atoms (consecutive rows: one contiguous block of Tm), coalesced
+      const int na = min(kAtoms, row_end - row0);
+      const float4* src = reinterpret_cast<const float4*>(smT);
+      float4* dst = reinterpret_cast<float4*>(g.Tm) + (long)row0 * g.M;
+      for (int e = r; e < na * g.M; e += kRows) {
+        const int a = e / g.M, m = e - a * g.M;
+        dst[e] = src[a * (NPAD + 1) + m];
+      }
+    }
     if (valid_e) {
       const float4* T4 = reinterpret_cast<const float4*>(smT) + ae * (NPAD + 1);
       float4 tl[16];
