@@ -466,39 +466,64 @@ __global__ void __launch_bounds__(kNlWarps * 32)
 
 // =============================================================================================
 // Cell-centred search: one CTA per cell.  The candidates of every (type, surrounding cell)
-// range are staged once in shared memory, already moved into the frame of this cell's corner
-// (l_j + o), so that each warp walks them for one centre atom of the cell with a shared load and
-// three subtractions per candidate.  Membership, ranking and outputs are those of k_nlist.
+// range are staged once in shared memory, each type's stretch padded to a multiple of 64 with
+// far-away sentinels: the FP32 position l_j + o (o the surrounding cell's corner offset), the
+// atom index j, and W - m_j (the cell's periodic wrap minus j's image index) for the image
+// code.  Each warp then owns one centre atom of the cell and walks a type's stretch 64
+// candidates at a time with one shared load, three subtractions, three multiply-adds and one
+// comparison against the outer FP32 bound per candidate; the accepted entries keep the FP32 r^2
+// and the stream position.  Everything else happens on the few accepted entries of one type:
+// the exact FP64 membership test of entries inside the FP32 error of r_c, the ranking under the
+// exact total order, and the image codes, all from shared memory.  Membership, ranking and
+// outputs are those of k_nlist.
 // =============================================================================================
 constexpr int kCellWarps = 8;
-constexpr int kStageMax = 1024;   // staged candidates per pass (more are staged in several passes)
-constexpr int kMaxRanges = 256;   // (type, surrounding cell) ranges of one cell
+constexpr int kMaxRanges = 256;  // (type, surrounding cell) ranges of one cell
 
-__host__ __device__ constexpr size_t cell_smem_bytes(int cap) {
-  return (size_t)kStageMax * 17 + (size_t)kCellWarps * (size_t)(cap + 4 * DP_MAX_TYPES) * kNlEntryBytes;
+// Dynamic shared memory: S staged candidates (24 bytes each) and one entry buffer per warp.
+__host__ __device__ constexpr size_t cell_smem_bytes(int cap, int S) {
+  return (size_t)S * 24 + (size_t)kCellWarps * (size_t)(cap + 4) * 8;
+}
+
+// W - m_j as three 21-bit two's-complement fields; bit 63 marks a value outside that range.
+__device__ __forceinline__ unsigned long long pack_wm(int a, int b, int c) {
+  const unsigned long long M = (1ull << 21) - 1;
+  const bool ok = a >= -(1 << 20) && a < (1 << 20) && b >= -(1 << 20) && b < (1 << 20) && c >= -(1 << 20) &&
+                  c < (1 << 20);
+  return ok ? (((unsigned long long)(unsigned)a & M) | (((unsigned long long)(unsigned)b & M) << 21) |
+               (((unsigned long long)(unsigned)c & M) << 42))
+            : (1ull << 63);
+}
+// Image code n = (W - m_j) + m_i of a staged entry; false when n leaves the packable range.
+__device__ __forceinline__ bool staged_code(unsigned long long wm, int mi0, int mi1, int mi2, int& code) {
+  const int n0 = (int)((long long)(wm << 43) >> 43) + mi0;
+  const int n1 = (int)((long long)(wm << 22) >> 43) + mi1;
+  const int n2 = (int)((long long)(wm << 1) >> 43) + mi2;
+  code = 0;
+  if ((wm >> 63) || n0 <= -512 || n0 >= 512 || n1 <= -512 || n1 >= 512 || n2 <= -512 || n2 >= 512) return false;
+  code = pack_shift(n0, n1, n2);
+  return true;
 }
 
 template <int CAP>
-__global__ void __launch_bounds__(kCellWarps * 32)
+__global__ void __launch_bounds__(kCellWarps * 32, 4)
     k_nlist_cell(const NlGeom* __restrict__ G, const int* __restrict__ cell_off, int nframes, int ncells_total,
                  int ntypes, const double* __restrict__ coord, const int* __restrict__ cell_start,
-                 const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m, int* __restrict__ nl_j,
+                 const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m, int S, int* __restrict__ nl_j,
                  int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
-  constexpr int CAPP = CAP + 4 * DP_MAX_TYPES;
   constexpr int NT = kCellWarps * 32;
+  constexpr int CAPP = CAP + 4;
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* stg = reinterpret_cast<float4*>(smem);               // l_j + o, and the sorted index
-  unsigned char* stg_o = smem + (size_t)kStageMax * 16;         // surrounding cell of each staged entry
-  __shared__ int s_rbeg[kMaxRanges], s_rpex[kMaxRanges + 1];  // first sorted entry, stream position
-  __shared__ float4 s_off[kMaxRanges];                        // per surrounding cell: o, and its wrap code
-  __shared__ unsigned char s_rslot[kMaxRanges];
-  __shared__ int s_cbeg[DP_MAX_TYPES], s_cpre[DP_MAX_TYPES + 1], s_wsum[kCellWarps];
+  float4* stg = reinterpret_cast<float4*>(smem);                                        // l_j + o, j
+  unsigned long long* stg_w = reinterpret_cast<unsigned long long*>(smem + (size_t)S * 16);  // W - m_j
+  __shared__ int s_rbeg[kMaxRanges], s_rnum[kMaxRanges], s_rpex[kMaxRanges + 1];
+  __shared__ float4 s_off[kMaxRanges];  // per surrounding cell: o, and its wrap code
+  __shared__ int s_tpex[DP_MAX_TYPES + 1], s_tdel[DP_MAX_TYPES], s_cpre[DP_MAX_TYPES + 1], s_wsum[kCellWarps];
+  __shared__ int s_sel[DP_MAX_TYPES], s_seloff[DP_MAX_TYPES];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-  unsigned char* wb = smem + (size_t)kStageMax * 17 + (size_t)warp * CAPP * kNlEntryBytes;
-  float* e_key = reinterpret_cast<float*>(wb);
-  int* e_idx = reinterpret_cast<int*>(wb + CAPP * 4);
-  int* e_w = reinterpret_cast<int*>(wb + CAPP * 8);  // surrounding cell the entry was seen through
+  float* e_key = reinterpret_cast<float*>(smem + (size_t)S * 24 + (size_t)warp * CAPP * 8);  // FP32 r^2
+  int* e_ref = reinterpret_cast<int*>(e_key + CAPP);                                         // stream position
 
   const int gc = blockIdx.x;  // cell, all frames
   int fr = 0;
@@ -513,27 +538,19 @@ __global__ void __launch_bounds__(kCellWarps * 32)
   const NlGeom& g = G[fr];
   const int ci = gc - (cell_off ? cell_off[fr] : 0);
   const int kb0 = gc - ci;  // first cell of the frame
-  if (tid == 0) {
-    int acc = 0;
-    for (int t = 0; t < ntypes; ++t) {
-      const int b = cell_start[t * ncells_total + gc];
-      s_cbeg[t] = b;
-      s_cpre[t] = acc;
-      acc += cell_start[t * ncells_total + gc + 1] - b;
-    }
-    s_cpre[ntypes] = acc;
-  }
-  __syncthreads();
-  const int nce = s_cpre[ntypes];
-  if (nce == 0) return;  // CTA-uniform: no centre atom in this cell
   const int c2 = ci % g.ncell[2];
   const int c1 = (ci / g.ncell[2]) % g.ncell[1];
   const int c0 = ci / (g.ncell[2] * g.ncell[1]);
   const int n0c = 2 * g.K[0] + 1, n1c = 2 * g.K[1] + 1, n2c = 2 * g.K[2] + 1;
   const int noff = n0c * n1c * n2c;
+  const int oc = (g.K[0] * n1c + g.K[1]) * n2c + g.K[2];  // slot of the cell itself
   const int R = ntypes * noff;  // <= kMaxRanges (checked on the host)
+  if (tid < ntypes) {
+    s_sel[tid] = g.sel[tid];
+    s_seloff[tid] = g.sel_off[tid];
+  }
 
-  // ---- the (type, surrounding cell) ranges and their stream positions ----
+  // ---- the (type, surrounding cell) ranges and their positions in the candidate stream ----
   int num = 0;
   if (tid < R) {
     const int t = tid / noff, o = tid - t * noff;
@@ -558,7 +575,7 @@ __global__ void __launch_bounds__(kCellWarps * 32)
       num = cell_start[key + 1] - beg;
     }
     s_rbeg[tid] = beg;
-    s_rslot[tid] = (unsigned char)o;
+    s_rnum[tid] = num;
     if (t == 0) {
       const float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
       s_off[o] = make_float4(fmaf(e2, g.hc[6], fmaf(e1, g.hc[3], e0 * g.hc[0])),
@@ -579,139 +596,199 @@ __global__ void __launch_bounds__(kCellWarps * 32)
   if (tid < R) s_rpex[tid] = wbase + incl - num;
   if (tid == NT - 1) s_rpex[R] = wbase + incl;  // threads >= R hold no range: this is the total
   __syncthreads();
-  const int total = s_rpex[R];
-
-  // stage stream positions [p0, p1) of the ranges into stg[0, p1 - p0)
-  auto stage = [&](int p0, int p1) {
-    for (int p = p0 + tid; p < p1; p += NT) {
-      int lo = 0, hi = R - 1;  // last range starting at or before p (it holds p)
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_rpex[mid] <= p) lo = mid; else hi = mid - 1;
-      }
-      const int src = s_rbeg[lo] + p - s_rpex[lo];
-      const int o = s_rslot[lo];
-      const float4 lj = __ldg(sorted_l + src);
-      const float4 of = s_off[o];
-      stg[p - p0] = make_float4(lj.x + of.x, lj.y + of.y, lj.z + of.z, __int_as_float(src));
-      stg_o[p - p0] = (unsigned char)o;
+  if (tid == 0) {  // each type's stretch starts at a multiple of 64; centre atoms by type
+    int p = 0, c = 0;
+    for (int t = 0; t < ntypes; ++t) {
+      const int a = s_rpex[t * noff], b = s_rpex[(t + 1) * noff];
+      s_tpex[t] = p;
+      s_tdel[t] = p - a;
+      p += (b - a + 63) & ~63;
+      s_cpre[t] = c;
+      c += s_rnum[t * noff + oc];
     }
-  };
-  const bool single = total <= kStageMax;
-  if (single) {
-    stage(0, total);
-    __syncthreads();
+    s_tpex[ntypes] = p;
+    s_cpre[ntypes] = c;
   }
-  const float rc2_in = g.rc2_in, rc2_out = g.rc2_out, tw = g.tie_w;
+  __syncthreads();
+  if (tid < R) s_rpex[tid] += s_tdel[tid / noff];
+  const int P = s_tpex[ntypes];
+  const int nce = s_cpre[ntypes];
+  if (nce == 0) return;  // CTA-uniform: no centre atom in this cell
+  if (P > S) {           // CTA-uniform: the stream does not fit the staging buffer
+    if (tid == 0) atomicExch(&st->capacity, 1);
+    return;
+  }
+  __syncthreads();
 
-  for (int q0 = 0; q0 < nce; q0 += kCellWarps) {
-    const int q = q0 + warp;
-    const bool active = q < nce;  // warp-uniform
-    int w = 0;
-    if (active) {
-      int tc = 0;
-      while (tc + 1 < ntypes && s_cpre[tc + 1] <= q) ++tc;
-      w = s_cbeg[tc] + q - s_cpre[tc];
+  // ---- stage the stream ----
+  for (int p = tid; p < P; p += NT) {
+    int lo = 0, hi = R - 1;  // last range starting at or before p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_rpex[mid] <= p) lo = mid; else hi = mid - 1;
     }
-    const float4 li = active ? sorted_l[w] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int4 mi = active ? sorted_m[w] : make_int4(0, 0, 0, 0);
+    const int k = p - s_rpex[lo];
+    if (k < s_rnum[lo]) {
+      const int src = s_rbeg[lo] + k;
+      const float4 lj = __ldg(sorted_l + src);
+      const int4 mj = __ldg(sorted_m + src);
+      const float4 of = s_off[lo % noff];
+      int W0, W1, W2;
+      unpack_shift(__float_as_int(of.w), W0, W1, W2);
+      stg[p] = make_float4(lj.x + of.x, lj.y + of.y, lj.z + of.z, lj.w);
+      stg_w[p] = pack_wm(W0 - mj.x, W1 - mj.y, W2 - mj.z);
+    } else {  // padding: never within r_c of anything
+      stg[p] = make_float4(1e30f, 1e30f, 1e30f, __int_as_float(-1));
+      stg_w[p] = 0;
+    }
+  }
+  __syncthreads();
+
+  const float rc2_in = g.rc2_in, rc2_out = g.rc2_out, tw = g.tie_w;
+  const unsigned lt = (1u << lane) - 1u;
+  const float kInf = __int_as_float(0x7f800000);
+  for (int q = warp; q < nce; q += kCellWarps) {
+    int tc = 0;
+    while (tc + 1 < ntypes && s_cpre[tc + 1] <= q) ++tc;
+    const int pc = s_rpex[tc * noff + oc] + q - s_cpre[tc];  // the centre's own entry (W = 0)
+    const float4 li = stg[pc];
     const int i = __float_as_int(li.w);
-    const double* xi = coord + 3 * (active ? i : 0);
-    int cnt = 0;
-    bool bad_shift = false;
+    bool bad_shift, over = false;
+    int mi0, mi1, mi2;
+    {
+      const unsigned long long wm = stg_w[pc];  // -m_i
+      mi0 = -(int)((long long)(wm << 43) >> 43);
+      mi1 = -(int)((long long)(wm << 22) >> 43);
+      mi2 = -(int)((long long)(wm << 1) >> 43);
+      bad_shift = (wm >> 63) != 0;
+    }
+    const double* xi = coord + 3 * i;
     for (int tj = 0; tj < ntypes; ++tj) {
-      cnt = (cnt + 3) & ~3;
-      const int gs = cnt;
-      const int ts = s_rpex[tj * noff], te = s_rpex[(tj + 1) * noff];
-      for (int p0 = ts; p0 < te; p0 += kStageMax) {
-        const int p1 = min(te, p0 + kStageMax);
-        const int sb = single ? 0 : p0;  // stream position of stg[0]
-        if (!single) {  // CTA-uniform
-          __syncthreads();
-          stage(p0, p1);
-          __syncthreads();
-        }
-        if (active) {
-          // one staged candidate: FP32 screening, the exact test only within the error of r_c
-          auto test = [&](int p, int& idx, int& o, float& r2) -> bool {
-            bool pass = false;
-            idx = 0;
-            o = 0;
-            r2 = 0.f;
-            if (p < p1) {
-              const float4 sj = stg[p - sb];
-              idx = __float_as_int(sj.w);
-              const float dx = sj.x - li.x, dy = sj.y - li.y, dz = sj.z - li.z;
-              r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              if (r2 <= rc2_out) {
-                o = stg_o[p - sb];
-                const int wcode = __float_as_int(s_off[o].w);
-                const bool self = idx == w && wcode == pack_shift(0, 0, 0);
-                if (r2 < rc2_in) {
-                  pass = !self;
-                } else if (!self) {
-                  int j, code;
-                  if (entry_code(sorted_l, sorted_m, idx, wcode, mi, j, code))
-                    pass = exact_r2(g, xi, coord, j, code) < g.rc2;
-                  else
-                    bad_shift = true;
-                }
-              }
-            }
-            return pass;
-          };
-          const unsigned lt = (1u << lane) - 1u;
-          for (int base = p0; base < p1; base += 64) {  // two independent batches per iteration
-            int ia, oa, ib, ob;
-            float ra, rb;
-            const bool pa = test(base + lane, ia, oa, ra);
-            const bool pb = test(base + 32 + lane, ib, ob, rb);
-            const unsigned ma = __ballot_sync(0xffffffffu, pa), mb = __ballot_sync(0xffffffffu, pb);
-            const int na = __popc(ma);
-            if (pa) {
-              const int pos = cnt + __popc(ma & lt);
-              if (pos < CAP) {
-                e_key[pos] = ra;
-                e_idx[pos] = ia;
-                e_w[pos] = oa;
-              }
-            }
-            if (pb) {
-              const int pos = cnt + na + __popc(mb & lt);
-              if (pos < CAP) {
-                e_key[pos] = rb;
-                e_idx[pos] = ib;
-                e_w[pos] = ob;
-              }
-            }
-            cnt += na + __popc(mb);
+      // ---- walk: FP32 screening against the outer bound ----
+      const int ts = s_tpex[tj], te = s_tpex[tj + 1];
+      int cnt = 0;
+      for (int p = ts + lane; p < te; p += 64) {
+        const float4 sa = stg[p], sb = stg[p + 32];
+        const float ax = sa.x - li.x, ay = sa.y - li.y, az = sa.z - li.z;
+        const float bx = sb.x - li.x, by = sb.y - li.y, bz = sb.z - li.z;
+        const float ra = fmaf(ax, ax, fmaf(ay, ay, az * az));
+        const float rb = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        const bool pa = ra <= rc2_out && p != pc, pb = rb <= rc2_out && p + 32 != pc;
+        const unsigned ma = __ballot_sync(0xffffffffu, pa), mb = __ballot_sync(0xffffffffu, pb);
+        const int na = __popc(ma);
+        if (pa) {
+          const int pos = cnt + __popc(ma & lt);
+          if (pos < CAP) {
+            e_key[pos] = ra;
+            e_ref[pos] = p;
           }
         }
+        if (pb) {
+          const int pos = cnt + na + __popc(mb & lt);
+          if (pos < CAP) {
+            e_key[pos] = rb;
+            e_ref[pos] = p + 32;
+          }
+        }
+        cnt += na + __popc(mb);
       }
-      if (!active) continue;
-      // ---- rank this type's entries (as in k_nlist) ----
-      const int ng = cnt - gs;
+      over |= cnt > CAP;
       const int ge = min(cnt, CAP);
-      const int ge4 = gs + ((max(ge - gs, 0) + 3) & ~3);
-      if (ge + lane < ge4) e_key[ge + lane] = __int_as_float(0x7f800000);
       __syncwarp();
-      rank_group(g, tj, i, xi, coord, sorted_l, sorted_m, mi, e_key, e_idx, e_w, gs, ge, ge4, tw,
-                 [&](int o) { return __float_as_int(s_off[o].w); }, lane, bad_shift, nl_j, nl_code);
-      for (int qq = ng + lane; qq < g.sel[tj]; qq += 32) {
-        const long slot = (long)i * g.nc + g.sel_off[tj] + qq;
-        nl_j[slot] = -1;
-        nl_code[slot] = pack_shift(0, 0, 0);
+      // ---- entries within the FP32 error of r_c: the exact FP64 test decides membership ----
+      int removed = 0;
+      for (int e0 = 0; e0 < ge; e0 += 32) {
+        const int e = e0 + lane;
+        const bool need = e < ge && e_key[e] >= rc2_in;
+        if (__ballot_sync(0xffffffffu, need)) {
+          bool drop = false;
+          if (need) {
+            const int p = e_ref[e];
+            int code;
+            if (staged_code(stg_w[p], mi0, mi1, mi2, code))
+              drop = !(exact_r2(g, xi, coord, __float_as_int(stg[p].w), code) < g.rc2);
+            else
+              drop = bad_shift = true;
+            if (drop) e_key[e] = kInf;
+          }
+          removed += __popc(__ballot_sync(0xffffffffu, drop));
+        }
+      }
+      const int ge4 = (ge + 3) & ~3;
+      if (ge + lane < ge4) e_key[ge + lane] = kInf;  // +inf: never smaller, always larger
+      __syncwarp();
+      // ---- rank under the exact total order (r^2, j, image code) ----
+      const int sel = s_sel[tj];
+      const long row = (long)i * g.nc + s_seloff[tj];
+      for (int e0 = 0; e0 < ge; e0 += 32) {
+        const int e = e0 + lane;
+        const float ke = e < ge ? e_key[e] : kInf;
+        const bool valid = ke != kInf;
+        const float lo_t = ke - tw, hi_t = ke + tw;
+        int lo = 0, hi = 0;  // certainly smaller; certainly larger
+        if (valid)
+          for (int f = 0; f < ge4; f += 4) {
+            const float4 k4 = *reinterpret_cast<const float4*>(e_key + f);
+            lo += (k4.x < lo_t) + (k4.y < lo_t) + (k4.z < lo_t) + (k4.w < lo_t);
+            hi += (k4.x > hi_t) + (k4.y > hi_t) + (k4.z > hi_t) + (k4.w > hi_t);
+          }
+        int je = 0, ce = 0;
+        if (valid) {
+          const int p = e_ref[e];
+          je = __float_as_int(stg[p].w);
+          if (!staged_code(stg_w[p], mi0, mi1, mi2, ce)) bad_shift = true;
+        }
+        int rank = lo;
+        const bool amb = valid && ge4 - lo - hi > 1;
+        unsigned am = __ballot_sync(0xffffffffu, amb);
+        if (am) {  // FP32 cannot order some pairs: their exact keys decide
+          const double re = amb ? exact_r2(g, xi, coord, je, ce) : 0.0;
+          while (am) {
+            const int s = __ffs(am) - 1;
+            am &= am - 1;
+            const float lo_s = __shfl_sync(0xffffffffu, lo_t, s), hi_s = __shfl_sync(0xffffffffu, hi_t, s);
+            const int je_s = __shfl_sync(0xffffffffu, je, s), ce_s = __shfl_sync(0xffffffffu, ce, s);
+            const double re_s = __shfl_sync(0xffffffffu, re, s);
+            int add = 0;
+            for (int f0 = 0; f0 < ge; f0 += 32) {
+              const int f = f0 + lane;
+              const float kf = f < ge ? e_key[f] : kInf;
+              const bool in = f != e0 + s && kf >= lo_s && kf <= hi_s;
+              if (__ballot_sync(0xffffffffu, in)) {
+                bool less = false;
+                if (in) {
+                  const int p = e_ref[f];
+                  const int jf = __float_as_int(stg[p].w);
+                  int cf;
+                  staged_code(stg_w[p], mi0, mi1, mi2, cf);
+                  const double rf = exact_r2(g, xi, coord, jf, cf);
+                  less = rf != re_s ? rf < re_s : (jf != je_s ? jf < je_s : (unsigned)cf < (unsigned)ce_s);
+                }
+                add += __popc(__ballot_sync(0xffffffffu, less));
+              }
+            }
+            if (lane == s) rank += add;
+          }
+        }
+        if (valid && rank < sel) {
+          nl_j[row + rank] = je;
+          nl_code[row + rank] = ce;
+        }
+      }
+      // ---- padding, counts and overflow accounting of this type ----
+      const int ng = cnt - removed;
+      for (int k = ng + lane; k < sel; k += 32) {
+        nl_j[row + k] = -1;
+        nl_code[row + k] = pack_shift(0, 0, 0);
       }
       if (lane == 0) {
-        if (counts) counts[(long)i * g.ntypes + tj] = ng;
-        if (ng > g.sel[tj]) atomicAdd(&st->sel_overflow, 1);
+        if (counts) counts[(long)i * ntypes + tj] = ng;
+        if (ng > sel) atomicAdd(&st->sel_overflow, 1);
       }
-      __syncwarp();
+      __syncwarp();  // the entry buffer is rewritten by the next type
     }
-    if (active) {
-      if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
-      if (cnt > CAP && lane == 0) atomicExch(&st->capacity, 1);
-    }
+    if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicExch(&st->capacity, 2);
+    if (over && lane == 0) atomicExch(&st->capacity, 1);
   }
 }
 
@@ -938,16 +1015,20 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
                              ex ? ex->perm : nullptr, ex ? ex->type_start : nullptr, cell_start, L.ncells_total,
                              ntypes, status, ex ? ex->chk : nochk);
   const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));
-  if (L.max_noff > 0 && (long)L.max_noff * ntypes <= kMaxRanges && cap <= 512) {
-    // cell-centred search: one CTA per cell
-    const size_t csm = cell_smem_bytes(cap);
+  // cell-centred search, one CTA per cell, when a cell's candidate stream fits shared memory:
+  // room for 1.25 times the mean stream of a cell plus each type's padding (a cell with more
+  // reports a capacity error, and the call is retried on the per-atom kernel below)
+  const double mean_stream = (double)L.natoms / std::max(1, L.ncells_total) * std::max(1, L.max_noff);
+  const int S = std::max(1024, ((int)(1.25 * mean_stream) + 64 * ntypes + 64 + 127) & ~127);
+  const size_t csm = cell_smem_bytes(cap, S);
+  if (L.max_noff > 0 && (long)L.max_noff * ntypes <= kMaxRanges && cap <= 512 && csm <= 160 * 1024) {
 #define DPGB_NLC_LAUNCH(C)                                                                                       \
   do {                                                                                                           \
-    e = allow_max_smem(k_nlist_cell<C>);            \
+    e = allow_max_smem(k_nlist_cell<C>);                                                                         \
     if (e != cudaSuccess) return e;                                                                              \
     k_nlist_cell<C><<<L.ncells_total, kCellWarps * 32, csm, st>>>(L.geoms, L.cell_off, L.nframes,               \
                                                                   L.ncells_total, ntypes, coord, cell_start,     \
-                                                                  sorted_l, sorted_m, nl_j, nl_code, counts,     \
+                                                                  sorted_l, sorted_m, S, nl_j, nl_code, counts,  \
                                                                   status);                                       \
   } while (0)
     if (cap == 128)
