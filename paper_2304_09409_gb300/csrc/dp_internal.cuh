@@ -178,6 +178,7 @@ struct NlLaunch {
   const int* cell_off;    // device [frames + 1] first cell of each frame, or null (one frame)
   int nframes;            // frames in the launch
   int max_noff;           // largest (2K_0+1)(2K_1+1)(2K_2+1) over the frames
+  int max_stream;         // largest mean candidate stream of one cell over the frames (0: unknown)
 };
 // What a path call also takes from the list build: the (type, cell) order of the atoms as its
 // type-sorted order (perm [natoms], type_start [ntypes + 1], checked against chk) and the 27
@@ -189,6 +190,11 @@ struct NlExtras {
   const double* boxes;
   int nframes;
   double* tshift;
+  // optional [natoms][nc] in sorted order: each listed pair's FP32 displacement (l_j + o) - l_i
+  // and, in w, 1 when its FP32 r^2 is certainly inside r_c, 0 when only the exact FP64 test
+  // decided, -1 for padding; written only by the cell-centred search (disp_written says so)
+  float4* disp;
+  bool disp_written;
 };
 // Cell arrays are indexed by (type, cell): cell_count [ntypes * ncells_total], cell_start
 // [ntypes * ncells_total + 1]; per atom its key and rank within the key (atom_key, int2), its
@@ -204,7 +210,7 @@ struct NlScratch {
 };
 cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
                                const NlScratch& sc, int* nl_j, int* nl_code, int* counts, DevStatus* status,
-                               cudaStream_t st, const NlExtras* ex = nullptr);
+                               cudaStream_t st, NlExtras* ex = nullptr);
 cudaError_t launch_type_perm(const int* type, int natoms, int ntypes, int* perm, int* type_start, DevStatus* status,
                              const TypeStartCheck& chk,
                              cudaStream_t st);

@@ -137,6 +137,17 @@ struct FrameTables {
     for (const NlGeom& g : geoms) m = std::max(m, (2 * g.K[0] + 1) * (2 * g.K[1] + 1) * (2 * g.K[2] + 1));
     return m;
   }
+  // Largest mean candidate stream of one cell, frame by frame: atoms per cell times the cells
+  // of its stencil.
+  int max_stream() const {
+    double m = 0.0;
+    for (int f = 0; f < F; ++f) {
+      const NlGeom& g = geoms[f];
+      const double per_cell = (double)(start[f + 1] - start[f]) / std::max(1, g.ncell[0] * g.ncell[1] * g.ncell[2]);
+      m = std::max(m, per_cell * (2 * g.K[0] + 1) * (2 * g.K[1] + 1) * (2 * g.K[2] + 1));
+    }
+    return (int)std::ceil(m);
+  }
   void pack(unsigned char* p) const {
     std::memcpy(p + off_geoms, geoms.data(), sizeof(NlGeom) * F);
     std::memcpy(p + off_celloff, cell_off.data(), sizeof(int) * (F + 1));
@@ -195,7 +206,7 @@ struct Bufs {
   int *nl_j, *nl_code, *counts;
   int *cell_count, *cell_start;
   int2* atom_key;
-  float4 *atom_l, *sorted_l;
+  float4 *atom_l, *sorted_l, *disp;
   int4 *atom_m, *sorted_m;
   unsigned char* ftab;
   int* atom_frame;
@@ -222,6 +233,7 @@ void carve(Arena& ar, const DeviceModel& m, const FrameTables& T, bool own_nlist
     b.atom_m = ar.get<int4>(N);
     b.sorted_l = ar.get<float4>(N);
     b.sorted_m = ar.get<int4>(N);
+    if (m.compressed && m.mom_npass == 1) b.disp = ar.get<float4>(N * nc);  // mixed mode's FP32 displacements
   }
   b.ftab = ar.get<unsigned char>((long)T.bytes);
   if (T.F > 1) b.atom_frame = ar.get<int>(N);
@@ -395,12 +407,15 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     if (own_nlist) {
       // the list build's (type, cell) order is the path's type-sorted order, and its first
       // launch also forms the image translations
-      NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff()};
-      NlExtras ex{b.perm, b.type_start, chk, d_boxes, T.periodic ? F : 0, T.periodic ? b.tshift : nullptr};
+      NlLaunch L{N, T.ncells, T.cap, d_geoms, b.atom_frame, F > 1 ? d_celloff : nullptr, F, T.max_noff(),
+                 T.max_stream()};
+      NlExtras ex{b.perm, b.type_start, chk, d_boxes, T.periodic ? F : 0, T.periodic ? b.tshift : nullptr, b.disp,
+                  false};
       ProfScope _ps(&md->prof, "nlist", s, 4);
       const NlScratch sc{b.cell_count, b.cell_start, b.atom_key, b.atom_l, b.atom_m, b.sorted_l, b.sorted_m};
       DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, sc, b.nl_j, b.nl_code, b.counts, md->status, s,
                                      &ex));
+      io.disp = ex.disp_written ? b.disp : nullptr;
     } else {
       ProfScope _ps(&md->prof, "type_perm", s);
       DP_CUDA_TRY(launch_type_perm(dtype, N, m.cfg.ntypes, b.perm, b.type_start, md->status, chk, s));
@@ -669,7 +684,7 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
   DP_CUDA_TRY(cudaMemsetAsync(md->status, 0, sizeof(DevStatus), st));
   {
     NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr, 1,
-               T.max_noff()};
+               T.max_noff(), T.max_stream()};
     ProfScope _ps(&md->prof, "nlist", st, 4);
     const NlScratch sc{b.cell_count, b.cell_start, b.atom_key, b.atom_l, b.atom_m, b.sorted_l, b.sorted_m};
     DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, sc, nl->nl_j, nl->nl_code, nl->counts, md->status,

@@ -45,7 +45,7 @@ __device__ __forceinline__ void pair_env<double>(double d0, double d1, double d2
 // relative precision there.
 __device__ __forceinline__ void pair_env_f32(float x0, float x1, float x2, double rs, double rc, float& r, float& s,
                                              float& ds, float* u) {
-  r = sqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+  r = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));  // explicit: the same rounding at every call site
   const float frs = (float)rs, frc = (float)rc;
   if (r < frs) {
     s = 1.0f / r;

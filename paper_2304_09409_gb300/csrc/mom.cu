@@ -90,6 +90,9 @@ struct MomArgs {
   const float4* atom_l;
   const int4* atom_m;
   const NlGeom* geoms;
+  // mixed mode with the cell-centred list build: each slot's FP32 displacement, read in place of
+  // the gathers above ([N][nc] in sorted order; w: 1 FP32 usable, 0 exact needed, -1 padding)
+  const float4* disp;
 };
 
 // Interval of s (at most lcap: the list order caps it), tau = (s - x_l) / Delta_l, 1/Delta_l.
@@ -228,10 +231,12 @@ __global__ void __launch_bounds__(256)
   const int i = g.perm[p];
   const int kb0 = g.sel_off[t], kb1 = g.sel_off[t + 1];
   const long rbase = (long)p * pc.nc + kb0;  // first run record of this list
-  // Mixed mode: the displacement in FP32 as (l_j - l_i) + delta . h_c from the cell-local
+  // Mixed mode: the displacement in FP32 as (l_j + delta . h_c) - l_i from the cell-local
   // positions of the list build (delta: the virtual-cell offset of the image of j), with the
   // list build's error bound; pairs within that bound of r_c take the exact FP64 displacement.
-  const bool f32d = NPASS == 1 && g.atom_l != nullptr;
+  // The cell-centred list build hands this same value over per slot (disp); the per-atom one
+  // does not, and then it is formed here from the gathered positions, rounded the same way.
+  const bool f32d = NPASS == 1 && g.atom_l != nullptr && g.disp == nullptr;
   float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
   int4 mi = make_int4(0, 0, 0, 0);
   const NlGeom* G = nullptr;
@@ -251,14 +256,31 @@ __global__ void __launch_bounds__(256)
     const int k = base + lane;
     const bool in = k < kb1;
     const long row = (long)p * pc.nc + k;
-    const int j = in ? g.nl_j[(long)i * pc.nc + k] : -1;
-    const bool valid = j >= 0;
+    float4 dd = make_float4(0.f, 0.f, 0.f, -1.f);
+    int j = -1;
+    if (g.disp) {
+      if (in) dd = g.disp[row];
+    } else if (in) {
+      j = g.nl_j[(long)i * pc.nc + k];
+    }
+    const bool valid = g.disp ? dd.w >= 0.f : j >= 0;
     int l = INT_MAX;
     float r = 0.f, s = 0.f, ds = 0.f, u[3] = {0.f, 0.f, 0.f}, tau = 0.f;
     if (valid) {
-      const int code = nl_code[(long)i * pc.nc + k];
-      bool exact = true;
-      if (f32d) {
+      // the FP32 displacement: handed over by the list build, or formed from the gathered
+      // cell-local positions, or (near r_c) rounded from the exact FP64 one; one call of the
+      // switch below for all three, so that its rounding does not depend on the source
+      float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+      bool have = false;
+      if (g.disp) {
+        if (dd.w > 0.5f) {  // FP32 r^2 certainly inside r_c
+          x0 = dd.x;
+          x1 = dd.y;
+          x2 = dd.z;
+          have = true;
+        }
+      } else if (f32d) {
+        const int code = nl_code[(long)i * pc.nc + k];
         const float4 lj = g.atom_l[j];
         const int4 mj = g.atom_m[j];
         int n0, n1, n2;
@@ -267,21 +289,24 @@ __global__ void __launch_bounds__(256)
         const int e1 = ((mj.w >> 10) & 1023) - ((mi.w >> 10) & 1023) + (n1 + mj.y - mi.y) * G->ncell[1];
         const int e2 = (mj.w & 1023) - (mi.w & 1023) + (n2 + mj.z - mi.z) * G->ncell[2];
         if (abs(e0) <= G->K[0] && abs(e1) <= G->K[1] && abs(e2) <= G->K[2]) {
+          // (l_j + o) - l_i with o the FP32 offset of j's cell, rounded as the list build rounds it
           const float f0 = (float)e0, f1 = (float)e1, f2 = (float)e2;
-          const float x0 = (lj.x - li.x) + fmaf(f2, G->hc[6], fmaf(f1, G->hc[3], f0 * G->hc[0]));
-          const float x1 = (lj.y - li.y) + fmaf(f2, G->hc[7], fmaf(f1, G->hc[4], f0 * G->hc[1]));
-          const float x2 = (lj.z - li.z) + fmaf(f2, G->hc[8], fmaf(f1, G->hc[5], f0 * G->hc[2]));
-          if (fmaf(x0, x0, fmaf(x1, x1, x2 * x2)) < G->rc2_in) {
-            pair_env_f32(x0, x1, x2, pc.rs, pc.rc, r, s, ds, u);
-            exact = false;
-          }
+          x0 = (lj.x + fmaf(f2, G->hc[6], fmaf(f1, G->hc[3], f0 * G->hc[0]))) - li.x;
+          x1 = (lj.y + fmaf(f2, G->hc[7], fmaf(f1, G->hc[4], f0 * G->hc[1]))) - li.y;
+          x2 = (lj.z + fmaf(f2, G->hc[8], fmaf(f1, G->hc[5], f0 * G->hc[2]))) - li.z;
+          have = fmaf(x0, x0, fmaf(x1, x1, x2 * x2)) < G->rc2_in;
         }
       }
-      if (exact) {
+      if (!have) {
+        if (g.disp) j = g.nl_j[(long)i * pc.nc + k];
+        const int code = nl_code[(long)i * pc.nc + k];
         double d0, d1, d2;
         listed_disp(coord + 3 * i, coord + 3 * j, code, pc, frame_of(pc, i), d0, d1, d2);
-        pair_env<float>(d0, d1, d2, 0.0, pc.rs, pc.rc, pc.near2, r, s, ds, u);
+        x0 = (float)d0;
+        x1 = (float)d1;
+        x2 = (float)d2;
       }
+      pair_env_f32(x0, x1, x2, pc.rs, pc.rc, r, s, ds, u);
       float invd;
       l = mom_interval(g, s, INT_MAX, tau, invd, oor);
     }
@@ -1247,6 +1272,7 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.atom_l = io.atom_l;
   g.atom_m = io.atom_m;
   g.geoms = io.geoms;
+  g.disp = io.disp;
   g.Tm = Tm;
   g.D = D;
   g.d_bf16 = bf16 ? 1 : 0;

@@ -447,8 +447,9 @@ __global__ void __launch_bounds__(kNlWarps * 32)
     __syncwarp();
     rank_group(g, tj, i, xi, coord, sorted_l, sorted_m, mi, e_key, e_idx, e_w, gs, ge, ge4, tw,
                [](int wc) { return wc; }, lane, bad_shift, nl_j, nl_code);
-    // padding, counts and overflow accounting of this type
-    for (int q = ng + lane; q < g.sel[tj]; q += 32) {
+    // padding, counts and overflow accounting of this type (entries beyond CAP, an error, are
+    // not in the list)
+    for (int q = max(ge - gs, 0) + lane; q < g.sel[tj]; q += 32) {
       const long slot = (long)i * g.nc + g.sel_off[tj] + q;
       nl_j[slot] = -1;
       nl_code[slot] = pack_shift(0, 0, 0);
@@ -510,7 +511,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
     k_nlist_cell(const NlGeom* __restrict__ G, const int* __restrict__ cell_off, int nframes, int ncells_total,
                  int ntypes, const double* __restrict__ coord, const int* __restrict__ cell_start,
                  const float4* __restrict__ sorted_l, const int4* __restrict__ sorted_m, int S, int* __restrict__ nl_j,
-                 int* __restrict__ nl_code, int* __restrict__ counts, DevStatus* __restrict__ st) {
+                 int* __restrict__ nl_code, int* __restrict__ counts, float4* __restrict__ disp,
+                 DevStatus* __restrict__ st) {
   constexpr int NT = kCellWarps * 32;
   constexpr int CAPP = CAP + 4;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -614,8 +616,22 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
   const int P = s_tpex[ntypes];
   const int nce = s_cpre[ntypes];
   if (nce == 0) return;  // CTA-uniform: no centre atom in this cell
-  if (P > S) {           // CTA-uniform: the stream does not fit the staging buffer
+  if (P > S) {  // CTA-uniform: the stream does not fit the staging buffer.  The call reports it
+                // (and is retried on the per-atom kernel); meanwhile this cell's rows are left
+                // empty, so that the kernels after the list stay in bounds.
     if (tid == 0) atomicExch(&st->capacity, 1);
+    for (int q = warp; q < nce; q += kCellWarps) {
+      int tc = 0;
+      while (tc + 1 < ntypes && s_cpre[tc + 1] <= q) ++tc;
+      const int w = s_rbeg[tc * noff + oc] + q - s_cpre[tc];
+      const int i = __float_as_int(__ldg(&sorted_l[w].w));
+      for (int k = lane; k < g.nc; k += 32) {
+        nl_j[(long)i * g.nc + k] = -1;
+        nl_code[(long)i * g.nc + k] = pack_shift(0, 0, 0);
+        if (disp) disp[(long)w * g.nc + k] = make_float4(0.f, 0.f, 0.f, -1.f);
+      }
+      if (counts && lane < ntypes) counts[(long)i * ntypes + lane] = 0;
+    }
     return;
   }
   __syncthreads();
@@ -645,12 +661,14 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
   __syncthreads();
 
   const float rc2_in = g.rc2_in, rc2_out = g.rc2_out, tw = g.tie_w;
+  const int nc = g.nc;
   const unsigned lt = (1u << lane) - 1u;
   const float kInf = __int_as_float(0x7f800000);
   for (int q = warp; q < nce; q += kCellWarps) {
     int tc = 0;
     while (tc + 1 < ntypes && s_cpre[tc + 1] <= q) ++tc;
     const int pc = s_rpex[tc * noff + oc] + q - s_cpre[tc];  // the centre's own entry (W = 0)
+    const int w = s_rbeg[tc * noff + oc] + q - s_cpre[tc];  // its sorted position
     const float4 li = stg[pc];
     const int i = __float_as_int(li.w);
     bool bad_shift, over = false;
@@ -719,7 +737,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
       __syncwarp();
       // ---- rank under the exact total order (r^2, j, image code) ----
       const int sel = s_sel[tj];
-      const long row = (long)i * g.nc + s_seloff[tj];
+      const long row = (long)i * nc + s_seloff[tj];
       for (int e0 = 0; e0 < ge; e0 += 32) {
         const int e = e0 + lane;
         const float ke = e < ge ? e_key[e] : kInf;
@@ -773,13 +791,19 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
         if (valid && rank < sel) {
           nl_j[row + rank] = je;
           nl_code[row + rank] = ce;
+          if (disp) {
+            const float4 sj = stg[e_ref[e]];
+            disp[(long)w * nc + s_seloff[tj] + rank] =
+                make_float4(sj.x - li.x, sj.y - li.y, sj.z - li.z, ke < rc2_in ? 1.f : 0.f);
+          }
         }
       }
       // ---- padding, counts and overflow accounting of this type ----
-      const int ng = cnt - removed;
-      for (int k = ng + lane; k < sel; k += 32) {
+      const int ng = cnt - removed;  // entries beyond CAP (an error) are not in the list
+      for (int k = ge - removed + lane; k < sel; k += 32) {
         nl_j[row + k] = -1;
         nl_code[row + k] = pack_shift(0, 0, 0);
+        if (disp) disp[(long)w * nc + s_seloff[tj] + k] = make_float4(0.f, 0.f, 0.f, -1.f);
       }
       if (lane == 0) {
         if (counts) counts[(long)i * ntypes + tj] = ng;
@@ -996,7 +1020,8 @@ cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi, cudaS
 
 cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
                                const NlScratch& sc, int* nl_j, int* nl_code, int* counts, DevStatus* status,
-                               cudaStream_t st, const NlExtras* ex) {
+                               cudaStream_t st, NlExtras* ex) {
+  if (ex) ex->disp_written = false;
   int* cell_count = sc.cell_count;
   int* cell_start = sc.cell_start;
   const float4* sorted_l = sc.sorted_l;
@@ -1018,7 +1043,8 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   // cell-centred search, one CTA per cell, when a cell's candidate stream fits shared memory:
   // room for 1.25 times the mean stream of a cell plus each type's padding (a cell with more
   // reports a capacity error, and the call is retried on the per-atom kernel below)
-  const double mean_stream = (double)L.natoms / std::max(1, L.ncells_total) * std::max(1, L.max_noff);
+  const double mean_stream = L.max_stream > 0 ? (double)L.max_stream
+                                              : (double)L.natoms / std::max(1, L.ncells_total) * std::max(1, L.max_noff);
   const int S = std::max(1024, ((int)(1.25 * mean_stream) + 64 * ntypes + 64 + 127) & ~127);
   const size_t csm = cell_smem_bytes(cap, S);
   if (L.max_noff > 0 && (long)L.max_noff * ntypes <= kMaxRanges && cap <= 512 && csm <= 160 * 1024) {
@@ -1029,7 +1055,7 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
     k_nlist_cell<C><<<L.ncells_total, kCellWarps * 32, csm, st>>>(L.geoms, L.cell_off, L.nframes,               \
                                                                   L.ncells_total, ntypes, coord, cell_start,     \
                                                                   sorted_l, sorted_m, S, nl_j, nl_code, counts,  \
-                                                                  status);                                       \
+                                                                  ex ? ex->disp : nullptr, status);              \
   } while (0)
     if (cap == 128)
       DPGB_NLC_LAUNCH(128);
@@ -1038,6 +1064,7 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
     else
       DPGB_NLC_LAUNCH(512);
 #undef DPGB_NLC_LAUNCH
+    if (ex) ex->disp_written = ex->disp != nullptr;
     return cudaGetLastError();
   }
   const size_t smem = (size_t)kNlWarps * ((size_t)(cap + 4 * DP_MAX_TYPES) * kNlEntryBytes + 32 * sizeof(NbCell));

@@ -153,7 +153,7 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   DP_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(DevStatus), st));
   DP_CUDA_TRY(cudaMemcpyAsync(geom, &g, sizeof(NlGeom), cudaMemcpyHostToDevice, st));
   const NlLaunch L{natoms, g.ncell[0] * g.ncell[1] * g.ncell[2], g.cap, geom, nullptr, nullptr, 1,
-                   (2 * g.K[0] + 1) * (2 * g.K[1] + 1) * (2 * g.K[2] + 1)};
+                   (2 * g.K[0] + 1) * (2 * g.K[1] + 1) * (2 * g.K[2] + 1), 0};
   const NlScratch sc{cell_count, cell_start, atom_key, atom_l, atom_m, sorted_l, sorted_m};
   DP_CUDA_TRY(launch_nlist_build(L, cfg->ntypes, coord, type, sc, nl_j, code, counts, status, st));
   const long n = (long)natoms * nc;

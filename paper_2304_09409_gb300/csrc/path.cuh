@@ -146,6 +146,9 @@ struct PathIO {
   const float4* atom_l;
   const int4* atom_m;
   const NlGeom* geoms;
+  // from the cell-centred list build of this call (else null): [N][Nc] in sorted atom order, each
+  // listed pair's FP32 displacement and, in w, 1 (FP32 usable), 0 (exact FP64 needed), -1 (padding)
+  const float4* disp;
 };
 
 struct __align__(32) D4 {

@@ -39,12 +39,12 @@ class Request:
 
 def scratch_bytes_per_atom(cfg, precision: str) -> int:
     """Upper estimate of the device scratch one atom of a batch needs: per neighbour slot the
-    list (8 B), the environment records and run index (36 B) and the per-run moment / P records
-    of the compressed path (136 B); per atom the descriptor and its gradient, the fitting
-    activations and the sort and cell arrays."""
+    list (8 B), its FP32 displacement (16 B), the environment records and run index (36 B) and
+    the per-run moment / P records of the compressed path (136 B); per atom the descriptor and
+    its gradient, the fitting activations and the sort and cell arrays."""
     nc, M, A = cfg.nc, cfg.m, cfg.axis
     w = max(cfg.fit) if cfg.fit else 1
-    b = nc * (8 + 36 + 136) + M * 4 * 4 * 2 + M * A * (2 + 4 + 4) + 6 * w * 6 + 512
+    b = nc * (8 + 16 + 36 + 136) + M * 4 * 4 * 2 + M * A * (2 + 4 + 4) + 6 * w * 6 + 512
     return int(b * (2 if precision == "fp64" else 1) * 1.25)
 
 

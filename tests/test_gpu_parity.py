@@ -165,6 +165,42 @@ def test_nlist_overflow_reported_and_truncated():
     np.testing.assert_array_equal(gs, rs)
 
 
+def _dense_clump():
+    """1331 atoms on a jittered 1.75 A lattice (about twice water's density) in one corner of an
+    otherwise empty 60 A box: the cells around the clump hold far more candidates than the mean
+    density of the box predicts, so the cell-centred search reports that its staging buffer is
+    too small and the call is retried on the per-atom kernel."""
+    rng = np.random.default_rng(11)
+    g = np.arange(11) * 1.75
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pts = lat + rng.uniform(-0.3, 0.3, lat.shape) + 20.0
+    cfg = I.ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(200, 200), embed=(8, 16, 32), axis=4,
+                        fit=(32, 32))
+    return cfg, I.Frame(pts, (np.arange(len(pts)) % 2).astype(np.int32), np.eye(3) * 60.0)
+
+
+def test_nlist_dense_clump_bit_exact():
+    dpgb = _dp()
+    cfg, fr = _dense_clump()
+    m = dpgb.Model(cfg, I.make_params(cfg, 0), precision="fp64")
+    nl = m.build_nlist(fr.coord, fr.atype, fr.box)
+    gj, gs = nl.export()
+    rj, rs, counts, ov = oracle.nlist(cfg, fr.coord, fr.atype, fr.box)
+    assert ov == 0 and nl.n_overflow == 0
+    np.testing.assert_array_equal(gj, rj)
+    np.testing.assert_array_equal(gs, rs)
+
+
+def test_fp64_dense_clump():
+    """The kernels after the list run on the first (reported, retried) attempt too: the rows the
+    cell-centred search could not fill must be left empty, not uninitialised."""
+    cfg, fr = _dense_clump()
+    p = I.make_params(cfg, 0)
+    ref = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
+    m = _dp().Model(cfg, p, precision="fp64")
+    _assert_fp64(m.compute(fr.coord, fr.atype, fr.box, atom_energy=True), ref, fr.natoms)
+
+
 # ---------------------------------------------------------------------------------------------
 # FP64 path: energy, forces, virial
 # ---------------------------------------------------------------------------------------------
