@@ -150,6 +150,19 @@ struct TypeStartCheck {
 // Let `kernel` take up to the device's opt-in shared memory per block.  Every caller sets the
 // same value, so launches from several host threads never see the limit lowered under them
 // (the shared memory a block actually gets is the launch's own request).
+// Streaming multiprocessors of the current device (read once per device).
+inline int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 template <class K>
 inline cudaError_t allow_max_smem(K kernel) {
   int dev = 0, mx = 0;

@@ -221,15 +221,33 @@ __device__ __forceinline__ void tile_groups(const MomArgs& g, const int* runl_s,
 // and run_rec.
 // =============================================================================================
 template <int NPASS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     k_env_mom(PathConst pc, MomArgs g, const double* __restrict__ coord, const int* __restrict__ nl_code) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
-  const long task = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (task >= (long)pc.natoms * pc.ntypes) return;  // warp-uniform
+  __shared__ float s_carry[8][24];  // moments of the run left open at a batch's end, per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* carry = s_carry[warp];
+  const long ntask = (long)pc.natoms * pc.ntypes;
+  const long wstride = (long)gridDim.x * 8;
+  // With the list build's displacements every slot is one coalesced load and no gather: the first
+  // batch of the warp's next task is loaded while the current task runs, and each next batch of
+  // a task while the current batch runs.
+  auto disp_batch = [&](long tk, int base) -> float4 {
+    float4 d = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (g.disp && tk < ntask) {
+      const int pp = (int)(tk / pc.ntypes), tt = (int)(tk % pc.ntypes);
+      if (base + lane < g.sel_off[tt + 1]) d = g.disp[(long)pp * pc.nc + base + lane];
+    }
+    return d;
+  };
+  long task = (long)blockIdx.x * 8 + warp;
+  float4 dnext = disp_batch(task, task < ntask ? g.sel_off[task % pc.ntypes] : 0);
+  for (; task < ntask; task += wstride) {  // warp-uniform
   const int p = (int)(task / pc.ntypes), t = (int)(task % pc.ntypes);
-  const int i = g.perm[p];
   const int kb0 = g.sel_off[t], kb1 = g.sel_off[t + 1];
+  float4 dcur = dnext;
+  dnext = disp_batch(task + wstride, task + wstride < ntask ? g.sel_off[(task + wstride) % pc.ntypes] : 0);
+  const int i = g.disp ? -1 : g.perm[p];  // with displacements: read only for an exact pair
   const long rbase = (long)p * pc.nc + kb0;  // first run record of this list
   // Mixed mode: the displacement in FP32 as (l_j + delta . h_c) - l_i from the cell-local
   // positions of the list build (delta: the virtual-cell offset of the image of j), with the
@@ -247,22 +265,16 @@ __global__ void __launch_bounds__(256)
   }
   int lmin = INT_MAX;                        // running minimum of the interval
   int carry_l = -1;                          // interval of the run open at the last batch's end
-  float carry[24];
-#pragma unroll
-  for (int e = 0; e < 24; ++e) carry[e] = 0.f;
   int nruns = 0;
   bool oor = false;
   for (int base = kb0; base < kb1; base += 32) {
     const int k = base + lane;
     const bool in = k < kb1;
     const long row = (long)p * pc.nc + k;
-    float4 dd = make_float4(0.f, 0.f, 0.f, -1.f);
+    const float4 dd = dcur;
+    if (g.disp && base + 32 < kb1) dcur = disp_batch(task, base + 32);
     int j = -1;
-    if (g.disp) {
-      if (in) dd = g.disp[row];
-    } else if (in) {
-      j = g.nl_j[(long)i * pc.nc + k];
-    }
+    if (!g.disp && in) j = g.nl_j[(long)i * pc.nc + k];
     const bool valid = g.disp ? dd.w >= 0.f : j >= 0;
     int l = INT_MAX;
     float r = 0.f, s = 0.f, ds = 0.f, u[3] = {0.f, 0.f, 0.f}, tau = 0.f;
@@ -298,10 +310,11 @@ __global__ void __launch_bounds__(256)
         }
       }
       if (!have) {
-        if (g.disp) j = g.nl_j[(long)i * pc.nc + k];
-        const int code = nl_code[(long)i * pc.nc + k];
+        const int ie = g.disp ? g.perm[p] : i;
+        if (g.disp) j = g.nl_j[(long)ie * pc.nc + k];
+        const int code = nl_code[(long)ie * pc.nc + k];
         double d0, d1, d2;
-        listed_disp(coord + 3 * i, coord + 3 * j, code, pc, frame_of(pc, i), d0, d1, d2);
+        listed_disp(coord + 3 * ie, coord + 3 * j, code, pc, frame_of(pc, ie), d0, d1, d2);
         x0 = (float)d0;
         x1 = (float)d1;
         x2 = (float)d2;
@@ -398,18 +411,22 @@ __global__ void __launch_bounds__(256)
                            reinterpret_cast<unsigned char*>(dst + c * PARTS + 1), w8);
       }
     }
+    __syncwarp();  // lane 0 has read the previous carry
     if (open >= 0) {
       carry_l = __shfl_sync(0xffffffffu, lk, open);
+      if (lane == open)
 #pragma unroll
-      for (int e = 0; e < 24; ++e) carry[e] = __shfl_sync(0xffffffffu, v[e], open);
+        for (int e = 0; e < 24; ++e) carry[e] = v[e];
     } else {
       carry_l = -1;
     }
+    __syncwarp();
     nruns += __popc(headmask);
     if (ends) break;  // warp-uniform: the rest of the block is padding
   }
   if (lane == 0 && nruns < kb1 - kb0) g.run_l[rbase + nruns] = -1;
   if (__any_sync(0xffffffffu, oor) && lane == 0) atomicOr(g.table_range, 1);
+  }
 }
 
 // =============================================================================================
@@ -1285,11 +1302,13 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.err = reinterpret_cast<int*>(stw + offsetof(DevStatus, timeout));
   {
     ProfScope _ps(io.prof, "env", st);
-    const long tasks = N * pc.ntypes;  // one warp per (atom, neighbour type)
+    // one warp per (atom, neighbour type) task; persistent warps, three 8-warp blocks per SM
+    const long tasks = N * pc.ntypes;
+    const unsigned blocks = (unsigned)std::min<long>((tasks + 7) / 8, 3L * sm_count());
     if (bf16)
-      k_env_mom<1><<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code);
+      k_env_mom<1><<<blocks, 256, 0, st>>>(pc, g, io.coord, io.nl_code);
     else
-      k_env_mom<3><<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(pc, g, io.coord, io.nl_code);
+      k_env_mom<3><<<blocks, 256, 0, st>>>(pc, g, io.coord, io.nl_code);
     DP_CUDA_TRY(cudaGetLastError());
   }
   if (tiles > 0) {
