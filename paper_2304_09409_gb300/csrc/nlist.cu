@@ -745,6 +745,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
         const float lo_t = ke - tw, hi_t = ke + tw;
         int lo = 0, hi = 0;  // certainly smaller; certainly larger
         if (valid)
+#pragma unroll 4
           for (int f = 0; f < ge4; f += 4) {
             const float4 k4 = *reinterpret_cast<const float4*>(e_key + f);
             lo += (k4.x < lo_t) + (k4.y < lo_t) + (k4.z < lo_t) + (k4.w < lo_t);
@@ -775,11 +776,18 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
               if (__ballot_sync(0xffffffffu, in)) {
                 bool less = false;
                 if (in) {
-                  const int p = e_ref[f];
-                  const int jf = __float_as_int(stg[p].w);
-                  int cf;
-                  staged_code(stg_w[p], mi0, mi1, mi2, cf);
-                  const double rf = exact_r2(g, xi, coord, jf, cf);
+                  int jf, cf;
+                  double rf;
+                  if (f0 == e0 && amb) {  // the partner is this lane's own entry: its exact key is known
+                    jf = je;
+                    cf = ce;
+                    rf = re;
+                  } else {
+                    const int p = e_ref[f];
+                    jf = __float_as_int(stg[p].w);
+                    staged_code(stg_w[p], mi0, mi1, mi2, cf);
+                    rf = exact_r2(g, xi, coord, jf, cf);
+                  }
                   less = rf != re_s ? rf < re_s : (jf != je_s ? jf < je_s : (unsigned)cf < (unsigned)ce_s);
                 }
                 add += __popc(__ballot_sync(0xffffffffu, less));
