@@ -54,6 +54,7 @@ using namespace ptx;
 constexpr int kAtoms = 32;        // centre atoms per CTA
 constexpr int kRows = 128;        // accumulator rows: (atom, c)
 constexpr int kThreads = 160;     // 4 builder / epilogue warps + 1 control warp
+constexpr int kFwdThreads = 192;  // forward: 4 builder / epilogue warps, an MMA warp and a TMA warp
 constexpr int kABlock = kRows * 128;  // one 64-column K block of 128 rows (bytes)
 constexpr int kGroupAtoms = 4;        // backward: atoms per staged group of dE/dD rows
 
@@ -169,21 +170,42 @@ __device__ __forceinline__ uint32_t sw_off(int r, int q) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
 }
 
-// Ring depth of the operand stages.
-// The run intervals of the tile's 32 atoms, every type block ([atom][nc], -1 past a tile's end),
-// loaded once with many independent loads in flight per thread.
+// The run intervals of the tile's 32 atoms, every type block ([atom][nc], -1 past a tile's end).
+// The tile's rows are one contiguous stretch of run_l: 16-byte loads where it is aligned, and
+// each thread's loads all in flight before the first store.
 __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_end, int* runl_s, int tid, int nthreads) {
   const int n = kAtoms * g.nc;
-  for (int e0 = tid; e0 < n; e0 += 8 * nthreads) {
-    int v[8];
+  const int nv = min(kAtoms, row_end - row0) * g.nc;  // slots of the tile's real atoms
+  const int* src = g.run_l + (long)row0 * g.nc;
+  int done = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    const int n4 = nv >> 2;
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(runl_s);
+    for (int e0 = tid; e0 < n4; e0 += 8 * nthreads) {
+      int4 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nthreads;
+        if (e < n4) v[u] = __ldg(s4 + e);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nthreads;
+        if (e < n4) d4[e] = v[u];
+      }
+    }
+    done = 4 * n4;
+  }
+  for (int e0 = done + tid; e0 < n; e0 += 16 * nthreads) {
+    int v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
       const int e = e0 + u * nthreads;
-      const int a = e / g.nc;
-      v[u] = (e < n && row0 + a < row_end) ? __ldg(g.run_l + (long)row0 * g.nc + e) : -1;
+      v[u] = e < nv ? __ldg(src + e) : -1;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 16; ++u) {
       const int e = e0 + u * nthreads;
       if (e < n) runl_s[e] = v[u];
     }
@@ -436,7 +458,7 @@ __global__ void __launch_bounds__(256, 3)
 // block kb are released to the MMA once they have landed, up to S - 1 blocks later.
 // =============================================================================================
 template <int NPASS, int NPAD>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kFwdThreads, 1)
     k_mom_fwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
   constexpr int S = MomStages<NPASS>::value;
@@ -473,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int ae = r >> 2, c = r & 3;
   const int pe = row0 + ae;
   const bool valid_e = warp < 4 && pe < row_end;
-  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kThreads);
+  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kFwdThreads);
   __syncthreads();
   if (warp == 0) tile_groups(g, runl_s, lane, ghi);
   tc_fence_before();
@@ -483,31 +505,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   int nkb = 0;
   for (int t = 0; t < g.ntypes; ++t) nkb += ghi[t] + 1;
 
-  if (warp == 4) {
+  if (warp == 5) {
     if (lane == 0) {
-      // ---- TMA producer and MMA issuer ----
-      const uint32_t idesc = idesc_f16(kRows, NPAD, NPASS == 1 ? 0 : 1);
-      auto issue = [&](int kb) {
+      // ---- TMA producer: a stage's coefficient block as soon as the stage is free ----
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % S;
+        if (kb >= S && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, g.err)) break;
         int t, grp;
         block_of(kb, ghi, g.ntypes, t, grp);
-        const int s = kb % S;
         unsigned char* bs = smem + s * STAGE + PARTS * kABlock;
         mbar_expect_tx(&full[s], PARTS * B_BYTES);
         const int x = (t * g.lcp + 8 * grp) * 8;
         tma_load_2d(bs, &bhi, &full[s], x, ti * NPAD);
         if (PARTS == 2) tma_load_2d(bs + B_BYTES, &blo, &full[s], x, ti * NPAD);
-      };
-      int issued = 0;
-      for (; issued < S - 1 && issued < nkb; ++issued) issue(issued);
+        issued = kb + 1;
+      }
+      // only the last S loads can still be in flight (each earlier stage was consumed before its
+      // reuse): they must land before the CTA leaves
+      for (int kb = max(0, issued - S); kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1, g.err);
+    }
+  } else if (warp == 4) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc = idesc_f16(kRows, NPAD, NPASS == 1 ? 0 : 1);
       bool ok = true;
-      int done = 0;  // blocks whose loads were consumed
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % S;
         if (!mbar_wait(&full[s], (kb / S) & 1, g.err)) {
           ok = false;
           break;
         }
-        done = kb + 1;
         tc_fence_after();
         const uint32_t sa = su32(smem + s * STAGE);
         const uint64_t ah = sdesc_sw128(sa), al = sdesc_sw128(sa + kABlock);
@@ -521,22 +549,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         mma_commit(&empty[s]);
-        const int kn = kb + S - 1;
-        if (kn < nkb) {
-          if (kn >= S && !mbar_wait(&empty[kn % S], ((kn / S) - 1) & 1, g.err)) {
-            ok = false;
-            break;
-          }
-          issue(kn);
-          issued = kn + 1;
-        }
       }
       if (ok && nkb > 0)
         mma_commit(accf);
       else
         mbar_arrive(accf);
-      // loads still in flight after an error must land before the CTA leaves
-      for (int kb = done; kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1, g.err);
     }
   } else {
     // ---- operand builders ----
@@ -1150,7 +1167,7 @@ int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, int which, cud
   } else if (which == 0) {
     const size_t sm = fwd_smem(NPASS, NPAD, g.nc);
     DP_CUDA_TRY(allow_max_smem(k_mom_fwd<NPASS, NPAD>));
-    k_mom_fwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[0], maps[1], g);
+    k_mom_fwd<NPASS, NPAD><<<tiles, kFwdThreads, sm, st>>>(maps[0], maps[1], g);
   } else {
     const size_t sm = bwd_smem(NPASS, g.nc);
     DP_CUDA_TRY(allow_max_smem(k_mom_bwd<NPASS, NPAD>));
