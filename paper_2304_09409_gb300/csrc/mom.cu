@@ -53,8 +53,7 @@ using namespace ptx;
 
 constexpr int kAtoms = 32;        // centre atoms per CTA
 constexpr int kRows = 128;        // accumulator rows: (atom, c)
-constexpr int kThreads = 160;     // 4 builder / epilogue warps + 1 control warp
-constexpr int kFwdThreads = 192;  // forward: 4 builder / epilogue warps, an MMA warp and a TMA warp
+constexpr int kMomThreads = 192;  // 4 builder / epilogue warps, an MMA warp and a TMA producer warp
 constexpr int kABlock = kRows * 128;  // one 64-column K block of 128 rows (bytes)
 constexpr int kGroupAtoms = 4;        // backward: atoms per staged group of dE/dD rows
 
@@ -458,7 +457,7 @@ __global__ void __launch_bounds__(256, 3)
 // block kb are released to the MMA once they have landed, up to S - 1 blocks later.
 // =============================================================================================
 template <int NPASS, int NPAD>
-__global__ void __launch_bounds__(kFwdThreads, 1)
+__global__ void __launch_bounds__(kMomThreads, 1)
     k_mom_fwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
   constexpr int S = MomStages<NPASS>::value;
@@ -495,7 +494,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   const int ae = r >> 2, c = r & 3;
   const int pe = row0 + ae;
   const bool valid_e = warp < 4 && pe < row_end;
-  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kFwdThreads);
+  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kMomThreads);
   __syncthreads();
   if (warp == 0) tile_groups(g, runl_s, lane, ghi);
   tc_fence_before();
@@ -824,7 +823,7 @@ __global__ void __launch_bounds__(kRows)
 // run's P record; the per-slot part of the backward is k_force_mom.
 // =============================================================================================
 template <int NPASS, int NPAD>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kMomThreads, 1)
     k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
   constexpr int S = 3;
@@ -871,7 +870,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int r = threadIdx.x;
   const int ae = r >> 2, c = r & 3;
   const int pe = row0 + ae;
-  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kThreads);
+  stage_runs(g, row0, row_end, runl_s, threadIdx.x, kMomThreads);
   __syncthreads();
   if (warp == 0) tile_groups(g, runl_s, lane, ghi);
   tc_fence_before();
@@ -881,19 +880,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   int nch = 0;
   for (int t = 0; t < g.ntypes; ++t) nch += ghi[t] + 1;
 
-  if (warp == 4) {
+  if (warp == 5) {
     if (lane == 0) {
-      // ---- the A operand of this tile and its row scales ----
-      mbar_expect_tx(afull, PARTS * A_BYTES + kRows * 4);
-      bulk_load(As, g.gta + (long)blockIdx.x * PARTS * A_BYTES, PARTS * A_BYTES, afull);
-      bulk_load(ex_s, g.gtx + (long)blockIdx.x * kRows, kRows * 4, afull);
-      bool ok = mbar_wait(afull, 0, g.err);
-      // ---- TMA producer and MMA issuer ----
-      const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
-      auto issue = [&](int ch) {
+      // ---- TMA producer: a stage's coefficient blocks as soon as the stage is free ----
+      int issued = 0;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int s = ch % S;
+        if (ch >= S && !mbar_wait(&bempty[s], ((ch / S) - 1) & 1, g.err)) break;
         int t, grp;
         block_of(ch, ghi, g.ntypes, t, grp);
-        const int s = ch % S;
         unsigned char* bs = ring + s * B_STAGE;
         mbar_expect_tx(&bfull[s], B_STAGE);
         const int y = ((ti * g.ntypes + t) * g.lcp + 8 * grp) * 8;
@@ -903,17 +898,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d(bs + 2 * B_KBLK, &blo, &bfull[s], 0, y);
           tma_load_2d(bs + 3 * B_KBLK, &blo, &bfull[s], 64, y);
         }
-      };
-      int issued = 0, done = 0;
-      if (ok)
-        for (; issued < S - 1 && issued < nch; ++issued) issue(issued);
+        issued = ch + 1;
+      }
+      // only the last S loads can still be in flight: they must land before the CTA leaves
+      for (int ch = max(0, issued - S); ch < issued; ++ch) mbar_wait(&bfull[ch % S], (ch / S) & 1, g.err);
+    }
+  } else if (warp == 4) {
+    if (lane == 0) {
+      // ---- the A operand of this tile and its row scales ----
+      mbar_expect_tx(afull, PARTS * A_BYTES + kRows * 4);
+      bulk_load(As, g.gta + (long)blockIdx.x * PARTS * A_BYTES, PARTS * A_BYTES, afull);
+      bulk_load(ex_s, g.gtx + (long)blockIdx.x * kRows, kRows * 4, afull);
+      bool ok = mbar_wait(afull, 0, g.err);
+      // ---- MMA issuer ----
+      const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
       for (int ch = 0; ok && ch < nch; ++ch) {
         const int s = ch % S, buf = ch & 1;
         if (!mbar_wait(&bfull[s], (ch / S) & 1, g.err)) {
           ok = false;
           break;
         }
-        done = ch + 1;
         if (ch >= 2 && !mbar_wait(&accempty[buf], ((ch >> 1) - 1) & 1, g.err)) {
           ok = false;
           break;
@@ -936,17 +940,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mma_commit(&bempty[s]);
         mma_commit(&accfull[buf]);
-        const int kn = ch + S - 1;
-        if (kn < nch) {
-          if (kn >= S && !mbar_wait(&bempty[kn % S], ((kn / S) - 1) & 1, g.err)) {
-            ok = false;
-            break;
-          }
-          issue(kn);
-          issued = kn + 1;
-        }
       }
-      for (int ch = done; ch < issued; ++ch) mbar_wait(&bfull[ch % S], (ch / S) & 1, g.err);
     }
   } else {
     mbar_wait(afull, 0, g.err);  // the row scales arrived with the A operand
@@ -1167,11 +1161,11 @@ int launch_mom(const DeviceModel& m, const MomArgs& g, int tiles, int which, cud
   } else if (which == 0) {
     const size_t sm = fwd_smem(NPASS, NPAD, g.nc);
     DP_CUDA_TRY(allow_max_smem(k_mom_fwd<NPASS, NPAD>));
-    k_mom_fwd<NPASS, NPAD><<<tiles, kFwdThreads, sm, st>>>(maps[0], maps[1], g);
+    k_mom_fwd<NPASS, NPAD><<<tiles, kMomThreads, sm, st>>>(maps[0], maps[1], g);
   } else {
     const size_t sm = bwd_smem(NPASS, g.nc);
     DP_CUDA_TRY(allow_max_smem(k_mom_bwd<NPASS, NPAD>));
-    k_mom_bwd<NPASS, NPAD><<<tiles, kThreads, sm, st>>>(maps[2], maps[3], g);
+    k_mom_bwd<NPASS, NPAD><<<tiles, kMomThreads, sm, st>>>(maps[2], maps[3], g);
   }
   DP_CUDA_TRY(cudaGetLastError());
   return DP_OK;
