@@ -386,11 +386,14 @@ __global__ void __launch_bounds__(256, 3)
     const unsigned headmask = __ballot_sync(0xffffffffu, head);
     const unsigned segmask = __ballot_sync(0xffffffffu, seg);
     const unsigned validmask = __ballot_sync(0xffffffffu, valid);
-    // segmented sums towards the first lane of each run
+    // segmented sums towards the first lane of each run; after the step of distance off every lane
+    // holds the sum over its run up to 2 off - 1 lanes ahead, so once no run reaches off lanes
+    // ahead the heads hold their runs' sums (runs are short: one to a few slots)
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const int lo = __shfl_down_sync(0xffffffffu, lk, off);
-      const bool same = lane + off < 32 && lo == lk;
+      const bool same = valid && lane + off < 32 && lo == lk;
+      if (!__any_sync(0xffffffffu, same)) break;
 #pragma unroll
       for (int e = 0; e < 24; ++e) {
         const float o = __shfl_down_sync(0xffffffffu, v[e], off);
