@@ -68,6 +68,32 @@ __device__ __forceinline__ void pair_env_f32(float x0, float x1, float x2, doubl
   u[2] = x2 * ir;
 }
 
+// The same with one reciprocal square root and no division (inv_w = 1 / (r_c - r_s)): a few ulps
+// of FP32, for the mixed mode, whose values go on as FP16 / BF16 operands.
+__device__ __forceinline__ void pair_env_f32_fast(float x0, float x1, float x2, float frs, float frc, float inv_w,
+                                                  float& r, float& s, float& ds, float* u) {
+  const float r2 = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+  const float ir = rsqrtf(r2);
+  r = r2 * ir;
+  if (r < frs) {
+    s = ir;
+    ds = -ir * ir;
+  } else if (r >= frc) {
+    s = 0.0f;
+    ds = 0.0f;
+  } else {
+    const float y = (frc - r) * inv_w;
+    const float y3 = y * y * y;
+    const float uu = y3 * fmaf(fmaf(6.0f, y, -15.0f), y, 10.0f);
+    const float du_dy = 30.0f * y * y * (y - 1.0f) * (y - 1.0f);
+    s = uu * ir;
+    ds = -(uu * ir) * ir - du_dy * inv_w * ir;
+  }
+  u[0] = x0 * ir;
+  u[1] = x1 * ir;
+  u[2] = x2 * ir;
+}
+
 // FP32 form from the exact FP64 displacement (which cancels large coordinates).
 template <>
 __device__ __forceinline__ void pair_env<float>(double d0, double d1, double d2, double, double rs, double rc,

@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(256, 3)
   // The cell-centred list build hands this same value over per slot (disp); the per-atom one
   // does not, and then it is formed here from the gathered positions, rounded the same way.
   const bool f32d = NPASS == 1 && g.atom_l != nullptr && g.disp == nullptr;
+  const float frs = (float)pc.rs, frc = (float)pc.rc, inv_w = 1.0f / (frc - frs);
   float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
   int4 mi = make_int4(0, 0, 0, 0);
   const NlGeom* G = nullptr;
@@ -340,22 +341,36 @@ __global__ void __launch_bounds__(256, 3)
         x1 = (float)d1;
         x2 = (float)d2;
       }
-      pair_env_f32(x0, x1, x2, pc.rs, pc.rc, r, s, ds, u);
+      if (NPASS == 1)
+        pair_env_f32_fast(x0, x1, x2, frs, frc, inv_w, r, s, ds, u);
+      else
+        pair_env_f32(x0, x1, x2, pc.rs, pc.rc, r, s, ds, u);
       float invd;
       l = mom_interval(g, s, INT_MAX, tau, invd, oor);
     }
-    int m = l;
+    {
+      // the interval never increases along the list: a prefix minimum over the batch (and the
+      // batches before), needed only where FP32 rounding inverted two nearly equal distances
+      const int lp = __shfl_up_sync(0xffffffffu, l, 1);
+      const bool inverted = valid && l > (lane == 0 ? lmin : lp);  // valid slots are a prefix
+      if (__any_sync(0xffffffffu, inverted)) {
+        int m = l;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int o = __shfl_up_sync(0xffffffffu, m, off);
-      if (lane >= off) m = min(m, o);
+        for (int off = 1; off < 32; off <<= 1) {
+          const int o = __shfl_up_sync(0xffffffffu, m, off);
+          if (lane >= off) m = min(m, o);
+        }
+        m = min(m, lmin);
+        if (valid && m < l) {
+          l = m;
+          tau = tau_at(g, s, l);
+        }
+        lmin = __shfl_sync(0xffffffffu, m, 31);
+      } else {
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (vm) lmin = __shfl_sync(0xffffffffu, l, 31 - __clz(vm));
+      }
     }
-    m = min(m, lmin);
-    if (valid && m < l) {
-      l = m;
-      tau = tau_at(g, s, l);
-    }
-    lmin = __shfl_sync(0xffffffffu, m, 31);
     if (in) {
       if (valid) {
         g.envU[row] = make_float4(s, u[0], u[1], u[2]);
