@@ -221,6 +221,8 @@ struct NlScratch {
   float4* sorted_l;
   int4* sorted_m;
 };
+// Kernel launches one launch_nlist_build makes (the key scan is folded into the fill for few keys).
+int nlist_launches(const NlLaunch& L, int ntypes);
 cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coord, const int* type,
                                const NlScratch& sc, int* nl_j, int* nl_code, int* counts, DevStatus* status,
                                cudaStream_t st, NlExtras* ex = nullptr);

@@ -411,7 +411,7 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
                  T.max_stream()};
       NlExtras ex{b.perm, b.type_start, chk, d_boxes, T.periodic ? F : 0, T.periodic ? b.tshift : nullptr, b.disp,
                   false};
-      ProfScope _ps(&md->prof, "nlist", s, 4);
+      ProfScope _ps(&md->prof, "nlist", s, nlist_launches(L, m.cfg.ntypes));
       const NlScratch sc{b.cell_count, b.cell_start, b.atom_key, b.atom_l, b.atom_m, b.sorted_l, b.sorted_m};
       DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, sc, b.nl_j, b.nl_code, b.counts, md->status, s,
                                      &ex));
@@ -685,7 +685,7 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
   {
     NlLaunch L{N, T.ncells, T.cap, reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms), nullptr, nullptr, 1,
                T.max_noff(), T.max_stream()};
-    ProfScope _ps(&md->prof, "nlist", st, 4);
+    ProfScope _ps(&md->prof, "nlist", st, nlist_launches(L, m.cfg.ntypes));
     const NlScratch sc{b.cell_count, b.cell_start, b.atom_key, b.atom_l, b.atom_m, b.sorted_l, b.sorted_m};
     DP_CUDA_TRY(launch_nlist_build(L, m.cfg.ntypes, dcoord, dtype, sc, nl->nl_j, nl->nl_code, nl->counts, md->status,
                                    st));

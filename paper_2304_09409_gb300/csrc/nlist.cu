@@ -162,6 +162,69 @@ __global__ void k_scan_excl(const int* __restrict__ in, int n, int* __restrict__
   if (threadIdx.x == 0) out[n] = carry;
 }
 
+// Exclusive scan of the key counts into shared memory by one block (a few thousand keys: every
+// block of the fill forms it itself instead of waiting for a separate scan launch).
+__device__ __forceinline__ void block_scan_counts(const int* __restrict__ in, int n, int* s_out) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int idx = base + threadIdx.x;
+    const int v = idx < n ? in[idx] : 0;
+    int incl = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int x = lane < nw ? wsum[lane] : 0;
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += t;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? wsum[w - 1] : 0) + carry;
+    if (idx < n) s_out[idx] = before + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s_out[n] = carry;
+  __syncthreads();
+}
+
+// Sorted entries as below, with the key starts formed in shared memory by every block (block 0
+// also writes them out for the search).
+__global__ void k_fill_scan(int natoms, const int* __restrict__ cell_count, int nkeys, int* __restrict__ cell_start,
+                            const int2* __restrict__ atom_key, const float4* __restrict__ atom_l,
+                            const int4* __restrict__ atom_m, float4* __restrict__ sorted_l, int4* __restrict__ sorted_m,
+                            int* __restrict__ perm, int* __restrict__ type_start, int ncells_total, int ntypes,
+                            DevStatus* __restrict__ st, const TypeStartCheck chk) {
+  extern __shared__ int s_start[];  // [nkeys + 1]
+  block_scan_counts(cell_count, nkeys, s_start);
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k <= nkeys; k += blockDim.x) cell_start[k] = s_start[k];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (perm && i <= ntypes) {
+    const int v = s_start[i * ncells_total];
+    type_start[i] = v;
+    if (chk.on && v != chk.v[i]) atomicExch(&st->type_change, 1);
+  }
+  if (i >= natoms) return;
+  const int2 kr = atom_key[i];
+  if (kr.x < 0) return;
+  const int pos = s_start[kr.x] + kr.y;
+  if (perm) perm[pos] = i;
+  sorted_l[pos] = atom_l[i];
+  sorted_m[pos] = atom_m[i];
+}
+
 // Sorted entries (scattered from the per-atom ones: key start + rank).  When asked, the sorted
 // order also serves as the type-sorted order of the path (perm, per-type starts), with the starts
 // checked against the ones the call was set up with.
@@ -1021,6 +1084,8 @@ int host_geometry(const dp_model_config& cfg, int natoms, const double* box, con
   return screening_bounds(g, rc);
 }
 
+int nlist_launches(const NlLaunch& L, int ntypes) { return (long)L.ncells_total * ntypes <= 8192 ? 3 : 4; }
+
 cudaError_t launch_bbox(const double* coord, int natoms, double* out_lohi, cudaStream_t st) {
   k_bbox<<<1, 1024, 0, st>>>(coord, natoms, out_lohi);
   return cudaGetLastError();
@@ -1043,10 +1108,16 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
   k_bin<<<nb, 256, 0, st>>>(L.geoms, L.atom_frame, L.cell_off, L.natoms, L.ncells_total, ntypes, coord, type,
                             cell_count, sc.atom_key, sc.atom_l, sc.atom_m, status, ex ? ex->boxes : nullptr,
                             ex ? ex->nframes : 0, ex ? ex->tshift : nullptr);
-  k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, nullptr);
-  k_fill<<<nb, 256, 0, st>>>(L.natoms, sc.atom_key, sc.atom_l, sc.atom_m, sc.sorted_l, sc.sorted_m,
-                             ex ? ex->perm : nullptr, ex ? ex->type_start : nullptr, cell_start, L.ncells_total,
-                             ntypes, status, ex ? ex->chk : nochk);
+  if (nkeys <= 8192) {  // few keys: each fill block scans the counts itself (one launch fewer; nlist_launches)
+    k_fill_scan<<<nb, 256, (size_t)(nkeys + 1) * sizeof(int), st>>>(
+        L.natoms, cell_count, nkeys, cell_start, sc.atom_key, sc.atom_l, sc.atom_m, sc.sorted_l, sc.sorted_m,
+        ex ? ex->perm : nullptr, ex ? ex->type_start : nullptr, L.ncells_total, ntypes, status, ex ? ex->chk : nochk);
+  } else {
+    k_scan_excl<<<1, 1024, 0, st>>>(cell_count, nkeys, cell_start, nullptr);
+    k_fill<<<nb, 256, 0, st>>>(L.natoms, sc.atom_key, sc.atom_l, sc.atom_m, sc.sorted_l, sc.sorted_m,
+                               ex ? ex->perm : nullptr, ex ? ex->type_start : nullptr, cell_start, L.ncells_total,
+                               ntypes, status, ex ? ex->chk : nochk);
+  }
   const int cap = L.cap <= 128 ? 128 : (L.cap <= 256 ? 256 : (L.cap <= 512 ? 512 : 1024));
   // cell-centred search, one CTA per cell, when a cell's candidate stream fits shared memory:
   // room for 1.25 times the mean stream of a cell plus each type's padding (a cell with more
