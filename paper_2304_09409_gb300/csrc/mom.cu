@@ -1049,13 +1049,28 @@ __global__ void __launch_bounds__(256)
   if (p >= pc.natoms) return;  // warp-uniform
   const int i = g.perm[p];
   float fi[3] = {0.f, 0.f, 0.f}, vir[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int t = 0; t < pc.ntypes; ++t) {
+  const int* nlrow = g.nl_j + (long)i * pc.nc;
+  // (type, 32-slot batch) in order; the next batch's list entries are loaded before the current
+  // batch is worked on, so one fewer dependent load is exposed per batch
+  int t = 0, base = g.sel_off[0];
+  int jn = lane < g.sel_off[1] - base ? nlrow[base + lane] : -1;
+  while (t < pc.ntypes) {
     const int kb0 = g.sel_off[t], kb1 = g.sel_off[t + 1];
+    const int jc = jn;
+    const bool any = __any_sync(0xffffffffu, jc >= 0);  // real neighbours fill the front of the block
+    int tn = t, bn = base + 32;
+    if (!any || bn >= kb1) {
+      tn = t + 1;
+      bn = tn < pc.ntypes ? g.sel_off[tn] : 0;
+    }
+    jn = (tn < pc.ntypes && bn + lane < g.sel_off[tn + 1]) ? nlrow[bn + lane] : -1;
+    const int k = base + lane;
     const long rbase = (long)p * pc.nc + kb0;
-    for (int base = kb0; base < kb1; base += 32) {
-      const int k = base + lane;
-      const int j = k < kb1 ? g.nl_j[(long)i * pc.nc + k] : -1;
-      if (!__any_sync(0xffffffffu, j >= 0)) break;  // real neighbours fill the front of the block
+    t = tn;
+    base = bn;
+    {
+      if (!any) continue;
+      const int j = jc;
       if (j < 0) continue;
       const long row = (long)p * pc.nc + k;
       const float4 e0 = g.envU[row], e1 = g.envB[row];
