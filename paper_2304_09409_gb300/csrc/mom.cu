@@ -511,7 +511,6 @@ __global__ void __launch_bounds__(kMomThreads, 1)
   const int r = threadIdx.x;
   const int ae = r >> 2, c = r & 3;
   const int pe = row0 + ae;
-  const bool valid_e = warp < 4 && pe < row_end;
   stage_runs(g, row0, row_end, runl_s, threadIdx.x, kMomThreads);
   __syncthreads();
   if (warp == 0) tile_groups(g, runl_s, lane, ghi);
@@ -623,12 +622,12 @@ __global__ void __launch_bounds__(kMomThreads, 1)
     for (int kb = max(0, nkb - D); kb < nkb; ++kb) mbar_arrive(&full[kb % S]);
   }
 
-  // ---- epilogue: T = acc / Nc, then D = T T_<^T ----
+  // ---- epilogue: T = acc / Nc, then D = T T_<^T (all six warps once T is staged) ----
+  float* smT = reinterpret_cast<float*>(smem);  // [32 atoms][NPAD + 1][4]; the ring is idle now
   if (warp < 4) {
     mbar_wait(accf, 0, g.err);
     __syncwarp();  // tcgen05.ld is warp-collective
     tc_fence_after();
-    float* smT = reinterpret_cast<float*>(smem);  // [32 atoms][NPAD + 1][4]; the ring is idle now
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c0 = 0; c0 < NPAD; c0 += 32) {  // two 16-column loads in flight, one wait
@@ -645,27 +644,34 @@ __global__ void __launch_bounds__(kMomThreads, 1)
       }
     }
     tc_fence_before();
-    bar_sync(1, kRows);
-    {  // T of the tile's atoms (consecutive rows: one contiguous block of Tm), coalesced
-      const int na = min(kAtoms, row_end - row0);
-      const float4* src = reinterpret_cast<const float4*>(smT);
-      float4* dst = reinterpret_cast<float4*>(g.Tm) + (long)row0 * g.M;
-      for (int e = r; e < na * g.M; e += kRows) {
-        const int a = e / g.M, m = e - a * g.M;
-        dst[e] = src[a * (NPAD + 1) + m];
-      }
+  } else {
+    __syncwarp();  // the MMA issuer and the TMA producer are done with their loops: converge
+  }
+  bar_sync(1, kMomThreads);  // T staged; the MMA and TMA warps join the rest
+  const int na = min(kAtoms, row_end - row0);
+  {  // T of the tile's atoms (consecutive rows: one contiguous block of Tm), coalesced
+    const float4* src = reinterpret_cast<const float4*>(smT);
+    float4* dst = reinterpret_cast<float4*>(g.Tm) + (long)row0 * g.M;
+    for (int e = r; e < na * g.M; e += kMomThreads) {
+      const int a = e / g.M, m = e - a * g.M;
+      dst[e] = src[a * (NPAD + 1) + m];
     }
-    if (valid_e) {
-      const float4* T4 = reinterpret_cast<const float4*>(smT) + ae * (NPAD + 1);
+  }
+  {  // D: six threads per atom, thread (atom, q) takes m = q, q + 6, ...
+    constexpr int kPer = kMomThreads / kAtoms;
+    const int ad = r / kPer, q = r - ad * kPer;
+    if (ad < na) {
+      const long pd = row0 + ad;
+      const float4* T4 = reinterpret_cast<const float4*>(smT) + ad * (NPAD + 1);
       float4 tl[16];
 #pragma unroll
       for (int l = 0; l < 16; ++l) tl[l] = l < g.A ? T4[l] : make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int m = c; m < g.M; m += 4) {
+      for (int m = q; m < g.M; m += kPer) {
         const float4 tm = T4[m];
         float d[16];
 #pragma unroll
         for (int l = 0; l < 16; ++l) d[l] = tm.x * tl[l].x + tm.y * tl[l].y + tm.z * tl[l].z + tm.w * tl[l].w;
-        const long o = ((long)pe * g.M + m) * g.A;
+        const long o = (pd * g.M + m) * g.A;
         if (g.d_bf16) {
           __nv_bfloat16* Db = reinterpret_cast<__nv_bfloat16*>(g.D) + o;
           if (g.A == 16) {
@@ -683,7 +689,8 @@ __global__ void __launch_bounds__(kMomThreads, 1)
           if (g.A == 16) {
             float4* d4 = reinterpret_cast<float4*>(Df);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+            for (int k4 = 0; k4 < 4; ++k4)
+              d4[k4] = make_float4(d[4 * k4], d[4 * k4 + 1], d[4 * k4 + 2], d[4 * k4 + 3]);
           } else {
 #pragma unroll
             for (int l = 0; l < 16; ++l)
