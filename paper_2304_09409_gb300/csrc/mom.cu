@@ -56,6 +56,7 @@ constexpr int kRows = 128;        // accumulator rows: (atom, c)
 constexpr int kMomThreads = 192;  // 4 builder / epilogue warps, an MMA warp and a TMA producer warp
 constexpr int kABlock = kRows * 128;  // one 64-column K block of 128 rows (bytes)
 constexpr int kGroupAtoms = 4;        // backward: atoms per staged group of dE/dD rows
+constexpr int kAccBufs = 4;           // backward: 64-column TMEM accumulators in rotation
 
 struct MomArgs {
   int ntypes, nc, M, A, lc, lcp, n1;
@@ -867,9 +868,9 @@ __global__ void __launch_bounds__(kMomThreads, 1)
   uint64_t* bfull = bar;
   uint64_t* bempty = bar + S;
   uint64_t* afull = bar + 2 * S;
-  uint64_t* accfull = afull + 1;     // [2]
-  uint64_t* accempty = accfull + 2;  // [2]
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accempty + 2);
+  uint64_t* accfull = afull + 1;     // [kAccBufs]
+  uint64_t* accempty = accfull + kAccBufs;  // [kAccBufs]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accempty + kAccBufs);
   int* ghi = reinterpret_cast<int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -884,14 +885,14 @@ __global__ void __launch_bounds__(kMomThreads, 1)
       mbar_init(&bempty[s], 1);
     }
     mbar_init(afull, 1);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kAccBufs; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], kRows);
     }
     for (int t = 0; t < DP_MAX_TYPES; ++t) ghi[t] = -1;
     mbar_fence_init();
   }
-  if (warp == 4) tmem_alloc(tmem_holder, 128);
+  if (warp == 4) tmem_alloc(tmem_holder, 64 * kAccBufs);
   const int r = threadIdx.x;
   const int ae = r >> 2, c = r & 3;
   const int pe = row0 + ae;
@@ -938,12 +939,12 @@ __global__ void __launch_bounds__(kMomThreads, 1)
       // ---- MMA issuer ----
       const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
       for (int ch = 0; ok && ch < nch; ++ch) {
-        const int s = ch % S, buf = ch & 1;
+        const int s = ch % S, buf = ch % kAccBufs;
         if (!mbar_wait(&bfull[s], (ch / S) & 1, g.err)) {
           ok = false;
           break;
         }
-        if (ch >= 2 && !mbar_wait(&accempty[buf], ((ch >> 1) - 1) & 1, g.err)) {
+        if (ch >= kAccBufs && !mbar_wait(&accempty[buf], ((ch / kAccBufs) - 1) & 1, g.err)) {
           ok = false;
           break;
         }
@@ -975,8 +976,8 @@ __global__ void __launch_bounds__(kMomThreads, 1)
     bool dead = false;  // after a timed-out wait: stop waiting, keep taking part in the barriers
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
     for (int ch = 0; ch < nch; ++ch) {
-      const int buf = ch & 1;
-      if (!dead && !mbar_wait(&accfull[buf], (ch >> 1) & 1, g.err)) dead = true;
+      const int buf = ch % kAccBufs;
+      if (!dead && !mbar_wait(&accfull[buf], (ch / kAccBufs) & 1, g.err)) dead = true;
       __syncwarp();  // tcgen05.ld is warp-collective
       tc_fence_after();
       float P[64];
@@ -1039,7 +1040,7 @@ __global__ void __launch_bounds__(kMomThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 4) tmem_dealloc(tmem, 128);
+  if (warp == 4) tmem_dealloc(tmem, 64 * kAccBufs);
 }
 
 // =============================================================================================
@@ -1190,7 +1191,7 @@ size_t fwd_smem(int npass, int npad, int nc) {
 size_t bwd_smem(int npass, int nc) {
   const int parts = npass == 1 ? 1 : 2;
   return (size_t)parts * 2 * kABlock + 3 * (size_t)parts * 2 * 64 * 128 + (size_t)kAtoms * nc * 4 + kRows * 4 +
-         11 * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
+         (7 + 2 * kAccBufs) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
 }
 
 template <int NPASS, int NPAD>
