@@ -268,6 +268,34 @@ def cpu_baseline(cfg, params, small, budget_s=10.0):
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
+def run_fcc(local, flush):
+    """The metal configuration: Cu-like FCC, 32,000 atoms (20^3 cells, a 3.634 A, seed 0), r_c 8,
+    sel [512], embedding 32/64/128, fitting 2048 -> 240^3.  Each precision path timed on the same
+    synthetic frame (L2 flushed between steps), forces compared with the FP64 GPU path."""
+    import torch
+    from paper_2304_09409_gb300 import dpgb, inputs as I
+    cfg = I.metal_model()
+    params = I.make_params(cfg, 0)
+    fr = I.fcc_frame((20, 20, 20), seed=0)
+    coord = torch.tensor(fr.coord, device="cuda")
+    atype = torch.tensor(fr.atype, device="cuda")
+    m64 = dpgb.Model(cfg, params, device=local, precision="fp64")
+    ms64, _, _, out64 = time_path(m64, coord, atype, fr.box, steps=2, warmup=1, flush=flush)
+    f64 = out64[1].cpu().numpy()
+    m64.free()
+    res = {"workload": "FCC 32,000 atoms (20^3 cells), rc 8, rs 0.5, sel [512], embedding 32/64/128, axis 16, "
+                       "fitting 2048 -> 240x3", "natoms": fr.natoms,
+           "force_rms": float(np.sqrt((f64 ** 2).mean())),
+           "fp64": {"ms_per_step": ms64, "atom_evals_per_s": fr.natoms / (ms64 * 1e-3)}}
+    for name, prec, comp in (("fp32-compressed", "fp32", True), ("bf16-compressed", "bf16", True)):
+        m = dpgb.Model(cfg, params, device=local, precision=prec, compressed=comp)
+        ms, _, _, out = time_path(m, coord, atype, fr.box, steps=5, warmup=3, flush=flush)
+        res[name] = {"ms_per_step": ms, "atom_evals_per_s": fr.natoms / (ms * 1e-3),
+                     "force_err_vs_fp64_gpu": float(np.abs(out[1].cpu().numpy() - f64).max())}
+        m.free()
+    return res
+
+
 def time_path(model, coord, atype, box, steps, warmup, flush, profile=False):
     import torch
     model.profile(profile)  # before the warm-up: calls with and without event scopes differ in shape
@@ -506,6 +534,11 @@ def run_ours(args):
         "clocks": clk,
         "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
     }
+    if not args.no_fcc and rank == 0 and world == 1:
+        try:
+            line["fcc32000"] = run_fcc(local, flush)
+        except Exception as exc:
+            line["fcc32000"] = {"error": repr(exc)}
     if not args.no_training:
         try:
             line["training"] = run_training()
@@ -538,6 +571,8 @@ def main():
                     help="skip the continuous-batching serving measurement")
     ap.add_argument("--no-training", dest="no_training", action="store_true",
                     help="skip the parameter-gradient (training step) measurement")
+    ap.add_argument("--no-fcc", dest="no_fcc", action="store_true",
+                    help="skip the 32,000-atom FCC metal configuration (precision sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
