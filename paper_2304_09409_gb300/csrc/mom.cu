@@ -56,7 +56,8 @@ constexpr int kRows = 128;        // accumulator rows: (atom, c)
 constexpr int kMomThreads = 192;  // 4 builder / epilogue warps, an MMA warp and a TMA producer warp
 constexpr int kABlock = kRows * 128;  // one 64-column K block of 128 rows (bytes)
 constexpr int kGroupAtoms = 4;        // backward: atoms per staged group of dE/dD rows
-constexpr int kAccBufs = 4;           // backward: 64-column TMEM accumulators in rotation
+constexpr int kAccBufs = 2;           // backward: 64-column TMEM accumulators in rotation
+constexpr int kBwdStages = 2;         // backward: coefficient ring depth (three CTAs fit an SM)
 
 struct MomArgs {
   int ntypes, nc, M, A, lc, lcp, n1;
@@ -170,10 +171,12 @@ __device__ __forceinline__ uint32_t sw_off(int r, int q) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
 }
 
-// The run intervals of the tile's 32 atoms, every type block ([atom][nc], -1 past a tile's end).
-// The tile's rows are one contiguous stretch of run_l: 16-byte loads where it is aligned, and
-// each thread's loads all in flight before the first store.
-__device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_end, int* runl_s, int tid, int nthreads) {
+// The run intervals of the tile's 32 atoms, every type block ([atom][nc], -1 past a tile's end),
+// as 16-bit values (intervals are far below 2^15).  The tile's rows are one contiguous stretch of
+// run_l: 16-byte loads where it is aligned, and each thread's loads all in flight before the first
+// store.
+__device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_end, short* runl_s, int tid,
+                                           int nthreads) {
   const int n = kAtoms * g.nc;
   const int nv = min(kAtoms, row_end - row0) * g.nc;  // slots of the tile's real atoms
   const int* src = g.run_l + (long)row0 * g.nc;
@@ -181,7 +184,7 @@ __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_e
   if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
     const int n4 = nv >> 2;
     const int4* s4 = reinterpret_cast<const int4*>(src);
-    int4* d4 = reinterpret_cast<int4*>(runl_s);
+    short4* d4 = reinterpret_cast<short4*>(runl_s);
     for (int e0 = tid; e0 < n4; e0 += 8 * nthreads) {
       int4 v[8];
 #pragma unroll
@@ -192,7 +195,7 @@ __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_e
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int e = e0 + u * nthreads;
-        if (e < n4) d4[e] = v[u];
+        if (e < n4) d4[e] = make_short4((short)v[u].x, (short)v[u].y, (short)v[u].z, (short)v[u].w);
       }
     }
     done = 4 * n4;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_e
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int e = e0 + u * nthreads;
-      if (e < n) runl_s[e] = v[u];
+      if (e < n) runl_s[e] = (short)v[u];
     }
   }
 }
@@ -221,7 +224,7 @@ struct MomStages {
 
 // Largest 8-interval group holding a neighbour of each type, over the tile's atoms (the first
 // run of each list has the largest interval; runl_s holds the tile's run lists).
-__device__ __forceinline__ void tile_groups(const MomArgs& g, const int* runl_s, int a, int* ghi) {
+__device__ __forceinline__ void tile_groups(const MomArgs& g, const short* runl_s, int a, int* ghi) {
   for (int t = 0; t < g.ntypes; ++t) {
     const int l = runl_s[a * g.nc + g.sel_off[t]];
     if (l >= 0) atomicMax(&ghi[t], l >> 3);
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(kMomThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  int* runl_s = reinterpret_cast<int*>(smem + S * STAGE);  // [32 atoms][nc] run intervals of the tile
+  short* runl_s = reinterpret_cast<short*>(smem + S * STAGE);  // [32 atoms][nc] run intervals of the tile
   uint64_t* full = reinterpret_cast<uint64_t*>(runl_s + kAtoms * g.nc);
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;
@@ -594,7 +597,7 @@ __global__ void __launch_bounds__(kMomThreads, 1)
         ptr = 0;
         rbase = (long)pe * g.nc + g.sel_off[t];
       }
-      const int* myruns = runl_s + ae * g.nc + g.sel_off[t];
+      const short* myruns = runl_s + ae * g.nc + g.sel_off[t];
       unsigned char* ahi = smem + s * STAGE;
       unsigned char* alo = ahi + kABlock;
       unsigned covered = 0;
@@ -852,7 +855,7 @@ template <int NPASS, int NPAD>
 __global__ void __launch_bounds__(kMomThreads, 1)
     k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
-  constexpr int S = 3;
+  constexpr int S = kBwdStages;
   constexpr int A_BYTES = 2 * kABlock;  // K = m in two 64-column blocks
   constexpr int B_KBLK = 64 * 128;      // 64 rows (8 intervals x 8 powers) x 128 B
   constexpr int B_STAGE = PARTS * 2 * B_KBLK;
@@ -862,8 +865,8 @@ __global__ void __launch_bounds__(kMomThreads, 1)
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* As = smem;                      // PARTS x A_BYTES, dE/dT rows (A operand)
   unsigned char* ring = smem + PARTS * A_BYTES;  // B stages
-  int* runl_s = reinterpret_cast<int*>(ring + S * B_STAGE);  // [32 atoms][nc] run intervals of the tile
-  int* ex_s = runl_s + kAtoms * g.nc;                        // [128] power-of-two scale of each row
+  short* runl_s = reinterpret_cast<short*>(ring + S * B_STAGE);  // [32 atoms][nc] run intervals of the tile
+  int* ex_s = reinterpret_cast<int*>(runl_s + kAtoms * g.nc);       // [128] power-of-two scale of each row
   uint64_t* bar = reinterpret_cast<uint64_t*>(ex_s + kRows);
   uint64_t* bfull = bar;
   uint64_t* bempty = bar + S;
@@ -1000,7 +1003,7 @@ __global__ void __launch_bounds__(kMomThreads, 1)
         ptr = 0;
         rbase = (long)pe * g.nc + g.sel_off[t];
       }
-      const int* myruns = runl_s + ae * g.nc + g.sel_off[t];
+      const short* myruns = runl_s + ae * g.nc + g.sel_off[t];
       while (ptr < selt) {
         const int l = myruns[ptr];
         if (l < 8 * grp) break;  // also the end marker -1
@@ -1185,13 +1188,13 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
 
 size_t fwd_smem(int npass, int npad, int nc) {
   const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 3 : 2;
-  return (size_t)S * parts * (kABlock + npad * 128) + (size_t)kAtoms * nc * 4 + (2 * S + 1) * 8 + 4 +
+  return (size_t)S * parts * (kABlock + npad * 128) + (size_t)kAtoms * nc * 2 + (2 * S + 1) * 8 + 4 +
          4 * DP_MAX_TYPES + 1024 + 64;
 }
 size_t bwd_smem(int npass, int nc) {
   const int parts = npass == 1 ? 1 : 2;
-  return (size_t)parts * 2 * kABlock + 3 * (size_t)parts * 2 * 64 * 128 + (size_t)kAtoms * nc * 4 + kRows * 4 +
-         (7 + 2 * kAccBufs) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
+  return (size_t)parts * 2 * kABlock + kBwdStages * (size_t)parts * 2 * 64 * 128 + (size_t)kAtoms * nc * 2 +
+         kRows * 4 + (2 * kBwdStages + 1 + 2 * kAccBufs) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
 }
 
 template <int NPASS, int NPAD>
@@ -1311,6 +1314,10 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.M = M;
   g.A = A;
   g.lc = m.tab.n1 + m.tab.n2;
+  if (g.lc > 32767) {  // run intervals are staged as 16-bit values
+    set_error("compressed table with more than 32767 intervals");
+    return DP_E_ARG;
+  }
   g.lcp = m.mom_lcp;
   g.n1 = m.tab.n1;
   g.s0 = (float)m.tab.s0;
