@@ -218,7 +218,7 @@ __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_e
 // Ring depth of the forward's operand stages.
 template <int NPASS>
 struct MomStages {
-  static constexpr int value = NPASS == 1 ? 3 : 2;  // three stages keep two CTAs on an SM
+  static constexpr int value = 2;  // two stages keep three CTAs (mixed mode) on an SM: one wave of tiles
 };
 
 
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(256, 3)
 // block kb are released to the MMA once they have landed, up to S - 1 blocks later.
 // =============================================================================================
 template <int NPASS, int NPAD>
-__global__ void __launch_bounds__(kMomThreads, 1)
+__global__ void __launch_bounds__(kMomThreads, 3)
     k_mom_fwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
   constexpr int S = MomStages<NPASS>::value;
@@ -1187,7 +1187,7 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
 }
 
 size_t fwd_smem(int npass, int npad, int nc) {
-  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? 3 : 2;
+  const int parts = npass == 1 ? 1 : 2, S = 2;
   return (size_t)S * parts * (kABlock + npad * 128) + (size_t)kAtoms * nc * 2 + (2 * S + 1) * 8 + 4 +
          4 * DP_MAX_TYPES + 1024 + 64;
 }
