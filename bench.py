@@ -454,7 +454,7 @@ def run_ours(args):
     atype = torch.tensor(big.atype, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    # FP64 GPU path: the force reference of the metric, and the plain baseline of the goal
+    # FP64 GPU path: the force reference of the metric, and the plain baseline the speed-up is quoted against
     m64 = dpgb.Model(cfg, params, device=local, precision="fp64")
     ms64, _, _, out64 = time_path(m64, coord, atype, big.box, steps=2, warmup=1, flush=flush)
     f64 = out64[1].cpu().numpy()
