@@ -58,13 +58,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-// Asynchronous 16- and 4-byte copies global -> shared (cp.async), committed as groups.
+// Asynchronous 16- and 8-byte copies global -> shared (cp.async), committed as groups.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(__cvta_generic_to_global(src))
                : "memory");
 }
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
@@ -79,8 +75,7 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// All but the most recent group (wait1), or every group (wait0), of this thread have landed.
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// Every group of this thread has landed.
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 // All but the N most recent groups of this thread have landed.
 template <int N>
