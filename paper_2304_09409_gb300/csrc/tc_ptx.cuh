@@ -58,19 +58,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-// Asynchronous 16- and 8-byte copies global -> shared (cp.async), committed as groups.
+// Asynchronous 16-byte copies global -> shared (cp.async), committed as groups.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(__cvta_generic_to_global(src))
                : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-// Hint that a global line will be read soon (fetched into L2).
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)) : "memory");
-}
+// Hint that a global line will be read soon (fetched into L1).
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)) : "memory");
 }
