@@ -182,7 +182,7 @@ def _candidate_pairs(frame, rc):
 
 def _kernel_rooflines(cfg, big, real_nb, prof, steps, peaks):
     """Roofline of each timed scope.  Algorithmic work per launch:
-      nlist      FP32 ALU: 8 FLOP (3 sub, 3 mul, 2 add) per candidate pair of the 27-cell stencil
+      nlist      HBM: coordinates and type in (28 B/atom), list and image code out (8 B/slot)
       env        HBM: the list build's FP32 displacement read 16 B/slot, (ds, r, tau, l) 16 B/slot,
                  (s, u) 16 B + run index 4 B per real neighbour (run moment records not counted)
       mom_fwd    FP32-ALU equivalent of the compressed contraction: 18 M FLOP per real neighbour
@@ -205,7 +205,7 @@ def _kernel_rooflines(cfg, big, real_nb, prof, steps, peaks):
     hbm = peaks.get("hbm_gbs", 6800.0)
     ten = peaks.get("bf16_tflops_sustained", 1700.0)
     work = {
-        "nlist": ("alu", 8.0 * pairs / 1e12, ALU_FP32_PEAK_TFLOPS, "TFLOP/s"),
+        "nlist": ("hbm", (N * 28 + N * nc * 8) / 1e9, hbm, "GB/s"),
         "env": ("hbm", (N * nc * 32 + real_nb * 20) / 1e9, hbm, "GB/s"),
         "mom_fwd": ("alu", 18.0 * M * real_nb / 1e12, ALU_FP32_PEAK_TFLOPS, "TFLOP/s"),
         "mom_bwd": ("alu", 36.0 * M * real_nb / 1e12, ALU_FP32_PEAK_TFLOPS, "TFLOP/s"),
