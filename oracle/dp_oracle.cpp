@@ -17,7 +17,7 @@
 //   Eq. (compress)   quintic tabulation of the embedding net               Sec. II.A.6
 //   neighbour order  by (type, distance, index)                            Sec. III.B.1
 //
-// Readings of the paper used here (each listed in the design notes):
+// Readings of the paper used here (where it is silent or ambiguous):
 //   * Nc in 1/Nc^2 is the padded sum of sel; padded rows of R are zero.
 //   * The virial is dE/dh at fixed fractional coordinates, which equals
 //     Xi_ab = -sum_{pairs} (dE/d r_ij)_a (r_ij)_b.

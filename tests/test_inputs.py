@@ -1,5 +1,5 @@
 """The synthetic inputs the tests and the benchmark share: geometry and composition of the water
-and FCC frames, replication, and seeded parameters (the recipe the design notes state)."""
+and FCC frames, replication, and seeded parameters."""
 import math
 
 import numpy as np

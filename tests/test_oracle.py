@@ -512,3 +512,113 @@ def test_loss_direction_derivative_vs_central_differences():
             fd = (_loss_from_compute(cfg, p + h * v, frames, e_ref, f_ref, pE, pF)
                   - _loss_from_compute(cfg, p - h * v, frames, e_ref, f_ref, pE, pF)) / (2 * h)
             assert abs(dL - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(L0)), (pE, pF, dL, fd)
+
+
+# ----------------------------------------------------------------------------------------
+# Whole forward (descriptor assembly and the fitting net's hidden layers) against numpy
+# ----------------------------------------------------------------------------------------
+
+
+def _numpy_fit(cfg, params, ai, D):
+    """Eq. (NN) for the fitting net of type ai on descriptor rows D [n, M M_<]: tanh hidden
+    layers with the identity skip where the width is kept (the {x,x} skip where it doubles),
+    then the linear width-1 output layer (Eq. (fitting_energy)); numpy matmul and tanh."""
+    off = cfg.n_embed_nets * sum(a * b + b for a, b in cfg.embed_layer_shapes())
+    off += ai * sum(a * b + b for a, b in cfg.fit_layer_shapes())
+    shapes = cfg.fit_layer_shapes()
+    x = D
+    for k, (fi, fo) in enumerate(shapes):
+        W = params[off:off + fi * fo].reshape(fi, fo)
+        b = params[off + fi * fo: off + fi * fo + fo]
+        off += fi * fo + fo
+        z = x @ W + b
+        if k == len(shapes) - 1:
+            x = z
+            continue
+        y = np.tanh(z)
+        if fo == fi:
+            y = y + x
+        elif fo == 2 * fi:
+            y = y + np.concatenate([x, x], axis=1)
+        x = y
+    return x[:, 0]
+
+
+def _numpy_atom_energies(cfg, params, fr, nl_j, nl_shift):
+    """E_i from a given neighbour list with numpy only: r_ij = r_j + n.h - r_i, R rows
+    (s, s x/r, s y/r, s z/r) (s from the pinned switch), G by `_numpy_net`, T = G^T R / Nc,
+    D = T T_<^T flattened row-major, then `_numpy_fit`."""
+    N, nc, M, A = fr.natoms, cfg.nc, cfg.m, cfg.axis
+    valid = nl_j >= 0
+    j = np.where(valid, nl_j, 0)
+    d = fr.coord[j] + nl_shift.astype(np.float64) @ fr.box - fr.coord[:, None, :]
+    r = np.sqrt((d * d).sum(-1))
+    s = np.zeros_like(r)
+    for idx in zip(*np.nonzero(valid)):
+        s[idx] = oracle.switch(float(r[idx]), cfg.rcut_smth, cfg.rcut)[0]
+    R = np.zeros((N, nc, 4))
+    R[..., 0] = s
+    R[..., 1:] = s[..., None] * d / np.where(valid, r, 1.0)[..., None]
+    G = np.zeros((N, nc, M))
+    off = np.cumsum([0] + list(cfg.sel))
+    for ai in range(cfg.ntypes):
+        rows = np.nonzero(fr.atype == ai)[0]
+        for t in range(cfg.ntypes):
+            net = t if cfg.type_one_side else ai * cfg.ntypes + t
+            blk = s[np.ix_(rows, np.arange(off[t], off[t + 1]))]
+            G[np.ix_(rows, np.arange(off[t], off[t + 1]))] = _numpy_net(cfg, params, net, blk.ravel()).reshape(
+                blk.shape + (M,))
+    T = np.einsum("ikm,ikc->imc", G, R) / nc
+    D = np.einsum("imc,ilc->iml", T, T[:, :A, :]).reshape(N, M * A)
+    e = np.zeros(N)
+    for ai in range(cfg.ntypes):
+        rows = fr.atype == ai
+        e[rows] = _numpy_fit(cfg, params, ai, D[rows])
+    return e
+
+
+@pytest.mark.parametrize("case", ["water", "tiny", "tiny_one_side"])
+def test_atom_energies_vs_numpy_forward(case):
+    """The oracle's atomic energies against an independent numpy evaluation of the whole forward
+    (R, embedding, descriptor, and the fitting net with its tanh hidden layers, identity skips
+    and linear output layer) on the oracle's own neighbour list (pinned separately against an
+    independent enumeration).  A wrong skip, activation, layer order or flatten order of D in
+    the oracle's fitting net changes every E_i."""
+    if case == "water":
+        cfg, fr = I.water_model(), I.water_frame(0)
+    else:
+        cfg, fr = tiny_model(type_one_side=int(case == "tiny_one_side")), tiny_frame(seed=4)
+    p = I.make_params(cfg, 2)
+    nl_j, nl_s, _, _ = oracle.nlist(cfg, fr.coord, fr.atype, fr.box)
+    res = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, nl=(nl_j, nl_s))
+    ref = _numpy_atom_energies(cfg, p, fr, nl_j, nl_s)
+    np.testing.assert_allclose(res.atom_energy, ref, rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# Sampled-atom oracle (reference of the full-size GPU checks) against the full oracle
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("case", ["tiny_triclinic", "water_far_images", "fcc"])
+def test_atom_subset_equals_full_oracle(case):
+    """orc_atom_subset builds each sampled atom's rows by its own brute force; they must equal
+    the full oracle's rows bit for bit and its atomic energies, also with coordinates several
+    boxes outside the cell and in a cell narrower than 2 r_c."""
+    if case == "tiny_triclinic":
+        cfg, fr = tiny_model(), tiny_frame(seed=6)
+    elif case == "water_far_images":
+        cfg, fr = I.water_model(), I.water_frame(1)
+        k = np.arange(fr.natoms) % 5 - 2  # shift atoms by -2 .. +2 box vectors
+        fr = I.Frame(fr.coord + k[:, None] * fr.box[0] - (k[:, None] // 2) * fr.box[2], fr.atype, fr.box)
+    else:
+        cfg = I.ModelConfig(ntypes=1, rcut=5.0, rcut_smth=0.5, sel=(80,), embed=(8, 16), axis=4, fit=(16, 16))
+        fr = I.fcc_frame((3, 3, 3), seed=2)
+    p = I.make_params(cfg, 3)
+    nl_j, nl_s, _, _ = oracle.nlist(cfg, fr.coord, fr.atype, fr.box)  # sel overflow included
+    full = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, nl=(nl_j, nl_s))
+    idx = np.arange(0, fr.natoms, 3)
+    sj, ss, se = oracle.atom_subset(cfg, p, fr.coord, fr.atype, fr.box, idx)
+    np.testing.assert_array_equal(sj, nl_j[idx])
+    np.testing.assert_array_equal(ss, nl_s[idx])
+    np.testing.assert_allclose(se, full.atom_energy[idx], rtol=1e-13, atol=1e-13)
