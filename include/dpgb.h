@@ -172,6 +172,11 @@ int dp_profile_reset(dp_model* model);
 int dp_profile_count(const dp_model* model);
 int dp_profile_read(const dp_model* model, int k, char* name, int name_len, double* total_ms, long* count);
 long dp_launch_count(const dp_model* model);
+/* Tensor-core FLOPs that scope k's kernels issued during the profiled calls (2 x M x N x K of every
+ * tcgen05.mma, each pass of a split product counted): counted for the compressed moment
+ * contraction ("mom_fwd", "mom_bwd"), whose work depends on the intervals the neighbours occupy;
+ * 0 for scopes whose work is a fixed function of the sizes.  DP_E_ARG for a bad index. */
+int dp_profile_work(const dp_model* model, int k, double* flop);
 
 /* Energies, forces and virials of several frames of one model in one pass (serving).
  * The frames keep their own periodic cells and atom counts; their atoms are concatenated.

@@ -87,6 +87,8 @@ def _L():
         _lib.orc_energy_plain.restype = ctypes.c_double
         _lib.orc_atom_subset.argtypes = [cp, dp, ctypes.c_int, dp, ip, dp, ctypes.c_int, ip, ip, ip, dp]
         _lib.orc_atom_subset.restype = ctypes.c_int
+        _lib.orc_force_subset.argtypes = [cp, dp, ctypes.c_int, dp, ip, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int]
+        _lib.orc_force_subset.restype = ctypes.c_int
     return _lib
 
 
@@ -254,6 +256,21 @@ def atom_subset(cfg, params, coord, atype, box, idx):
     _L().orc_atom_subset(ctypes.byref(c), _d(_f64(params)), coord.shape[0], _d(coord), _i(_i32(atype)), _d(_f64(box)),
                          S, _i(idx), _i(nl_j), _i(nl_s), _d(e))
     return nl_j, nl_s, e
+
+
+def force_subset(cfg, params, coord, atype, box, idx, nthreads: int = 0):
+    """Forces [S, 3] and atomic energies [S] of the atoms `idx` only (their neighbourhoods
+    within r_c evaluated by brute force), for sampled checks of frames too large for the full
+    oracle.  Network embedding."""
+    coord = _f64(coord)
+    idx = _i32(np.atleast_1d(idx))
+    S = idx.size
+    f = np.zeros((S, 3))
+    e = np.zeros(S)
+    c = _cfg(cfg)
+    _L().orc_force_subset(ctypes.byref(c), _d(_f64(params)), coord.shape[0], _d(coord), _i(_i32(atype)),
+                          _d(_f64(box)), S, _i(idx), _d(f), _d(e), int(nthreads))
+    return f, e
 
 
 def _pack_frames(cfg, frames):

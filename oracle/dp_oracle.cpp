@@ -780,38 +780,41 @@ double orc_energy_dual(const OrcConfig* c, const double* params, int N, const do
   return E.v;
 }
 
-// Neighbour rows and atomic energies of a subset of atoms only (brute force over all j and
-// images for each selected atom), for sampled checks of frames too large for the full oracle.
-int orc_atom_subset(const OrcConfig* cfg, const double* params, int N, const double* coord, const int* type,
-                    const double* box, int nsel, const int* idx, int* nl_j_out, int* nl_shift_out, double* e_out) {
-  const OrcConfig& c = *cfg;
-  Layout L = make_layout(c);
-  const int nc = L.nc;
-  const double rc2 = c.rcut * c.rcut;
+// Brute-force neighbour rows of single atoms (Sec. III.B.1 order), for frames too large for the
+// full list: every j and every image within K cells of the nearest one, sorted by the exact key.
+struct RowBuilder {
+  const OrcConfig& c;
+  const Layout& L;
+  int N;
+  const double* coord;
+  const int* type;
+  const double* box;
+  double rc2;
   double inv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int K[3] = {0, 0, 0};
-  if (box) {
-    inverse3(box, inv);
-    double vol = std::fabs(box[0] * (box[4] * box[8] - box[5] * box[7]) - box[1] * (box[3] * box[8] - box[5] * box[6]) +
-                           box[2] * (box[3] * box[7] - box[4] * box[6]));
-    for (int d = 0; d < 3; ++d) {
-      const double* u = box + 3 * ((d + 1) % 3);
-      const double* v = box + 3 * ((d + 2) % 3);
-      double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
-      K[d] = (int)std::ceil(c.rcut / (vol / std::sqrt(cx * cx + cy * cy + cz * cz))) + 1;
+  RowBuilder(const OrcConfig& c_, const Layout& L_, int N_, const double* coord_, const int* type_,
+             const double* box_)
+      : c(c_), L(L_), N(N_), coord(coord_), type(type_), box(box_), rc2(c_.rcut * c_.rcut) {
+    if (box) {
+      inverse3(box, inv);
+      double vol = std::fabs(box[0] * (box[4] * box[8] - box[5] * box[7]) -
+                             box[1] * (box[3] * box[8] - box[5] * box[6]) + box[2] * (box[3] * box[7] - box[4] * box[6]));
+      for (int d = 0; d < 3; ++d) {
+        const double* u = box + 3 * ((d + 1) % 3);
+        const double* v = box + 3 * ((d + 2) % 3);
+        double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+        K[d] = (int)std::ceil(c.rcut / (vol / std::sqrt(cx * cx + cy * cy + cz * cz))) + 1;
+      }
     }
   }
-  auto mfloor = [&](int a, int d) -> long {
+  long mfloor(int a, int d) const {
     if (!box) return 0;
     double f = coord[3 * a] * inv[d] + coord[3 * a + 1] * inv[3 + d] + coord[3 * a + 2] * inv[6 + d];
     return (long)std::floor(f);
-  };
-  std::vector<int> nl_j((size_t)N * nc, -1), nl_code((size_t)N * nc, pack_shift(0, 0, 0));
-  int ov = 0;
-  std::vector<Cand> cand;
-  for (int s = 0; s < nsel; ++s) {
-    const int i = idx[s];
-    cand.clear();
+  }
+  // Row of atom i into nl_j / nl_code (Nc entries each); returns the number of overflowing blocks.
+  int row(int i, int* nl_j, int* nl_code) const {
+    std::vector<Cand> cand;
     for (int j = 0; j < N; ++j) {
       int base[3];
       for (int d = 0; d < 3; ++d) base[d] = (int)(mfloor(i, d) - mfloor(j, d));
@@ -834,15 +837,37 @@ int orc_atom_subset(const OrcConfig* cfg, const double* params, int N, const dou
           }
     }
     std::sort(cand.begin(), cand.end(), cand_less);
+    for (int k = 0; k < L.nc; ++k) {
+      nl_j[k] = -1;
+      nl_code[k] = pack_shift(0, 0, 0);
+    }
     std::vector<int> cnt(c.ntypes, 0);
     for (const Cand& e : cand) {
       if (cnt[e.type] < c.sel[e.type]) {
-        nl_j[(size_t)i * nc + L.sel_off[e.type] + cnt[e.type]] = e.j;
-        nl_code[(size_t)i * nc + L.sel_off[e.type] + cnt[e.type]] = e.code;
+        nl_j[L.sel_off[e.type] + cnt[e.type]] = e.j;
+        nl_code[L.sel_off[e.type] + cnt[e.type]] = e.code;
       }
       cnt[e.type]++;
     }
+    int ov = 0;
     for (int t = 0; t < c.ntypes; ++t) ov += cnt[t] > c.sel[t];
+    return ov;
+  }
+};
+
+// Neighbour rows and atomic energies of a subset of atoms only (brute force over all j and
+// images for each selected atom), for sampled checks of frames too large for the full oracle.
+int orc_atom_subset(const OrcConfig* cfg, const double* params, int N, const double* coord, const int* type,
+                    const double* box, int nsel, const int* idx, int* nl_j_out, int* nl_shift_out, double* e_out) {
+  const OrcConfig& c = *cfg;
+  Layout L = make_layout(c);
+  const int nc = L.nc;
+  RowBuilder rb(c, L, N, coord, type, box);
+  std::vector<int> nl_j((size_t)N * nc, -1), nl_code((size_t)N * nc, pack_shift(0, 0, 0));
+  int ov = 0;
+  for (int s = 0; s < nsel; ++s) {
+    const int i = idx[s];
+    ov += rb.row(i, &nl_j[(size_t)i * nc], &nl_code[(size_t)i * nc]);
   }
   std::vector<double> gd((size_t)nc * 3);
   for (int s = 0; s < nsel; ++s) {
@@ -854,6 +879,71 @@ int orc_atom_subset(const OrcConfig* cfg, const double* params, int N, const dou
       if (nl_j_out) nl_j_out[(size_t)s * nc + k] = nl_j[(size_t)i * nc + k];
       if (nl_shift_out) unpack_shift(nl_code[(size_t)i * nc + k], nl_shift_out + 3 * ((size_t)s * nc + k));
     }
+  }
+  return ov;
+}
+
+// Forces on a subset of atoms only.  F_k = -dE/dr_k collects, from every atom i whose list holds
+// k, the pair term of each slot (F_i += dE/dr_ij, F_j -= dE/dr_ij, Sec. II.A.2); those atoms lie
+// within r_c of k, so only the rows and atom passes of k's neighbourhood are formed (by brute
+// force, as orc_atom_subset).  Network embedding only.  force_out [nsel][3]; e_out [nsel] or null.
+int orc_force_subset(const OrcConfig* cfg, const double* params, int N, const double* coord, const int* type,
+                     const double* box, int nsel, const int* idx, double* force_out, double* e_out, int nthreads) {
+  const OrcConfig& c = *cfg;
+  Layout L = make_layout(c);
+  const int nc = L.nc;
+  RowBuilder rb(c, L, N, coord, type, box);
+  // the sampled atoms' rows name their neighbourhoods
+  std::vector<int> need(N, 0);
+  std::vector<int> rj(nc), rcode(nc);
+  int ov = 0;
+  for (int s = 0; s < nsel; ++s) {
+    need[idx[s]] = 1;
+    // every atom within r_c of k, listed or beyond sel: a wider row with sel = the atom count
+    OrcConfig wide = c;
+    for (int t = 0; t < c.ntypes; ++t) wide.sel[t] = N * 27;
+    Layout Lw = make_layout(wide);
+    RowBuilder rw(wide, Lw, N, coord, type, box);
+    std::vector<int> wj(Lw.nc), wc(Lw.nc);
+    rw.row(idx[s], wj.data(), wc.data());
+    for (int k = 0; k < Lw.nc; ++k)
+      if (wj[k] >= 0) need[wj[k]] = 1;
+  }
+  std::vector<int> rows;
+  for (int i = 0; i < N; ++i)
+    if (need[i]) rows.push_back(i);
+  std::vector<int> nl_j((size_t)N * nc, -1), nl_code((size_t)N * nc, pack_shift(0, 0, 0));
+  std::vector<double> gd(rows.size() * (size_t)nc * 3, 0.0);
+  std::vector<AtomOut> ao(rows.size());
+  std::vector<int> ovr(rows.size(), 0);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (long q = 0; q < (long)rows.size(); ++q) {
+    const int i = rows[q];
+    ovr[q] = rb.row(i, &nl_j[(size_t)i * nc], &nl_code[(size_t)i * nc]);
+    atom_pass(c, L, params, nullptr, i, coord, type, box, nl_j.data(), nl_code.data(), &gd[(size_t)q * nc * 3], &ao[q]);
+  }
+  (void)nthreads;
+  for (size_t q = 0; q < rows.size(); ++q) ov += ovr[q];
+  for (int s = 0; s < nsel; ++s) {
+    const int k = idx[s];
+    double f[3] = {0.0, 0.0, 0.0};
+    for (size_t q = 0; q < rows.size(); ++q) {
+      const int i = rows[q];
+      for (int sl = 0; sl < nc; ++sl) {
+        const int j = nl_j[(size_t)i * nc + sl];
+        if (j < 0) continue;
+        const double* g = &gd[((size_t)q * nc + sl) * 3];
+        for (int a = 0; a < 3; ++a) {
+          if (i == k) f[a] += g[a];
+          if (j == k) f[a] -= g[a];
+        }
+      }
+      if (e_out && i == k) e_out[s] = ao[q].e;
+    }
+    for (int a = 0; a < 3; ++a) force_out[3 * s + a] = f[a];
   }
   return ov;
 }

@@ -116,6 +116,12 @@ int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
   DP_CUDA_TRY(cudaStreamSynchronize(st));
   md->prof.collect();
   const DevStatus s = *md->status_host;
+  if (md->prof.timing && md->m.mom_npass) {  // issued MMA work of the moment kernels
+    // one block: 128 accumulator rows x 64 x the padded width M, times the passes
+    const double per = 2.0 * 128.0 * 64.0 * md->m.mom_npad * md->m.mom_npass;
+    if (s.mma_blocks[0]) md->prof.work[md->prof.id_of("mom_fwd")] += per * s.mma_blocks[0];
+    if (s.mma_blocks[1]) md->prof.work[md->prof.id_of("mom_bwd")] += per * s.mma_blocks[1];
+  }
   if (n_overflow) *n_overflow = s.sel_overflow;
   if (s.bad_type) {
     set_error("atom type outside [0, ntypes)");
@@ -271,6 +277,15 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
       return rc;
     }
   }
+  // FP32 compressed models run the fitting net on split BF16 operands (three tensor-core passes,
+  // about 16 significant bits per operand) where its shapes fit the tensor-core kernels
+  if (precision == DP_PREC_FP32 && compressed && fit_tc_supported(m)) {
+    int rc = prepare_fit_bf16(m, params, true);
+    if (rc != DP_OK) {
+      dp_free_model(md);
+      return rc;
+    }
+  }
   *out = md;
   return DP_OK;
 }
@@ -397,6 +412,12 @@ int dp_profile_read(const dp_model* md, int k, char* name, int name_len, double*
 
 long dp_launch_count(const dp_model* md) { return md ? md->prof.launches : -1; }
 
+int dp_profile_work(const dp_model* md, int k, double* flop) {
+  if (!md || !flop || k < 0 || k >= (int)md->prof.names.size()) return DP_E_ARG;
+  *flop = md->prof.work[k];
+  return DP_OK;
+}
+
 int dp_free_model(dp_model* md) {
   if (!md) return DP_OK;
   cudaSetDevice(md->m.device);
@@ -407,6 +428,8 @@ int dp_free_model(dp_model* md) {
   cudaFree(md->m.mom_tab);
   cudaFree(md->m.fit_wt_bf16);
   cudaFree(md->m.fit_w_bf16);
+  cudaFree(md->m.fit_wt_bf16_lo);
+  cudaFree(md->m.fit_w_bf16_lo);
   cudaFree(md->ws);
   cudaFree(md->status);
   if (md->status_host) cudaFreeHost(md->status_host);

@@ -106,6 +106,9 @@ struct DeviceModel {
   // (forward) and W [n_in][n_out] (backward), at fit_bf16_off[type * n_fit + layer].
   void* fit_wt_bf16 = nullptr;
   void* fit_w_bf16 = nullptr;
+  // low halves W - bf16(W) of the same operands (split three-pass products of the FP32 mode)
+  void* fit_wt_bf16_lo = nullptr;
+  void* fit_w_bf16_lo = nullptr;
   float fit_out_bias[DP_MAX_TYPES] = {};  // bias of the final linear layer, per type
   std::vector<long> fit_bf16_off;
   // tensor maps of those operands, keyed by (type, layer, direction, box rows)
@@ -138,6 +141,7 @@ struct DevStatus {
   int bad_type;       // a type outside [0, ntypes)
   int timeout;        // a bounded wait of a tensor-core kernel gave up
   int type_change;    // the per-type atom counts differ from the ones the call was set up with
+  unsigned int mma_blocks[2];  // tensor-core blocks the moment kernels issued (forward, backward)
 };
 
 // Per-type starts of the type-sorted atom order that a call was set up with (checked on the

@@ -78,7 +78,8 @@ struct MomArgs {
                    // p_bf16 (mixed mode); shares memory with run_rec
   int p_bf16;
   float* Tm;          // [N][M][4]
-  void* D;            // [N][M * A], BF16 or FP32
+  void* D;            // [N][M * A], BF16 or FP32 (d_bf16 = 2: BF16 high part)
+  void* D_lo;         // d_bf16 = 2: [N][M * A] BF16 low part D - bf16(D)
   int d_bf16;
   const float* gD;            // [N][M * A] FP32, or
   const __nv_bfloat16* gDh;   // [N][M * A] BF16 (mixed mode)
@@ -88,6 +89,7 @@ struct MomArgs {
   int* gtx;            // its row scales [tiles][128]
   int* table_range;
   int* err;
+  unsigned int* mma_blocks;  // [2] blocks issued by the forward / backward MMA threads (work count)
   // mixed mode with the list built in the same call: FP32 displacements from cell-local positions
   const float4* atom_l;
   const int4* atom_m;
@@ -574,6 +576,7 @@ __global__ void __launch_bounds__(kMomThreads, 3)
         mma_commit(accf);
       else
         mbar_arrive(accf);
+      if (ok && nkb > 0) atomicAdd(&g.mma_blocks[0], (unsigned)nkb);
     }
   } else {
     // ---- operand builders ----
@@ -676,7 +679,17 @@ __global__ void __launch_bounds__(kMomThreads, 3)
 #pragma unroll
         for (int l = 0; l < 16; ++l) d[l] = tm.x * tl[l].x + tm.y * tl[l].y + tm.z * tl[l].z + tm.w * tl[l].w;
         const long o = (pd * g.M + m) * g.A;
-        if (g.d_bf16) {
+        if (g.d_bf16 == 2) {  // split operands of the FP32 mode's tensor-core fitting net
+          __nv_bfloat16* Dh = reinterpret_cast<__nv_bfloat16*>(g.D) + o;
+          __nv_bfloat16* Dl = reinterpret_cast<__nv_bfloat16*>(g.D_lo) + o;
+#pragma unroll
+          for (int l = 0; l < 16; ++l) {
+            if (l >= g.A) break;
+            const __nv_bfloat16 h = __float2bfloat16_rn(d[l]);
+            Dh[l] = h;
+            Dl[l] = __float2bfloat16_rn(d[l] - __bfloat162float(h));
+          }
+        } else if (g.d_bf16) {
           __nv_bfloat16* Db = reinterpret_cast<__nv_bfloat16*>(g.D) + o;
           if (g.A == 16) {
             uint4* d4 = reinterpret_cast<uint4*>(Db);
@@ -970,6 +983,7 @@ __global__ void __launch_bounds__(kMomThreads, 1)
         mma_commit(&bempty[s]);
         mma_commit(&accfull[buf]);
       }
+      if (ok && nch > 0) atomicAdd(&g.mma_blocks[1], (unsigned)nch);
     }
   } else {
     mbar_wait(afull, 0, g.err);  // the row scales arrived with the A operand
@@ -1284,8 +1298,12 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const long N = pc.natoms;
   const int M = pc.M, A = pc.A;
   const bool bf16 = m.mom_npass == 1;
+  // FP32 mode: the fitting net on split BF16 operands (three tensor-core passes) when the
+  // model's low weight halves exist, else on the FP32 CUDA-core kernels
+  const bool split_fit = !bf16 && m.fit_wt_bf16_lo != nullptr;
   float* Tm = ar.get<float>(N * M * 4);
-  void* D = bf16 ? (void*)ar.get<__nv_bfloat16>(N * M * A) : (void*)ar.get<float>(N * M * A);
+  void* D = (bf16 || split_fit) ? (void*)ar.get<__nv_bfloat16>(N * M * A) : (void*)ar.get<float>(N * M * A);
+  __nv_bfloat16* D_lo = split_fit ? ar.get<__nv_bfloat16>(N * M * A) : nullptr;
   const long slots = N * pc.nc;
   const int parts = bf16 ? 1 : 2;
   float4* envU = ar.get<float4>(slots);
@@ -1301,6 +1319,8 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const __nv_bfloat16* gDh = nullptr;
   if (ar.measure) {
     if (bf16) return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, &gDh);
+    if (split_fit)
+      return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, nullptr, D_lo);
     return run_fitting<float>(m, pc, m.p32, reinterpret_cast<const float*>(D), io, ar, st, &gD);
   }
   if (!ar.ok()) {
@@ -1351,7 +1371,8 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   g.disp = io.disp;
   g.Tm = Tm;
   g.D = D;
-  g.d_bf16 = bf16 ? 1 : 0;
+  g.D_lo = D_lo;
+  g.d_bf16 = bf16 ? 1 : (split_fit ? 2 : 0);
   g.force = io.force;
   g.avir = io.atom_virial;
   g.gta = gta;
@@ -1359,6 +1380,7 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   char* stw = reinterpret_cast<char*>(io.status);
   g.table_range = reinterpret_cast<int*>(stw + offsetof(DevStatus, table_range));
   g.err = reinterpret_cast<int*>(stw + offsetof(DevStatus, timeout));
+  g.mma_blocks = reinterpret_cast<unsigned int*>(stw + offsetof(DevStatus, mma_blocks));
   {
     ProfScope _ps(io.prof, "env", st);
     // one warp per (atom, neighbour type) task; persistent warps, three 8-warp blocks per SM
@@ -1378,6 +1400,8 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   int rc;
   if (bf16)
     rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, &gDh);
+  else if (split_fit)
+    rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, nullptr, D_lo);
   else
     rc = run_fitting<float>(m, pc, m.p32, reinterpret_cast<const float*>(D), io, ar, st, &gD);
   if (rc != DP_OK) return rc;

@@ -35,12 +35,14 @@ struct Prof {
   std::vector<std::string> names;
   std::vector<double> total_ms;
   std::vector<long> count;
+  std::vector<double> work;  // tensor-core FLOPs the scope's kernels reported issuing (0: not counted)
   int id_of(const char* name) {
     for (size_t k = 0; k < names.size(); ++k)
       if (names[k] == name) return (int)k;
     names.push_back(name);
     total_ms.push_back(0.0);
     count.push_back(0);
+    work.push_back(0.0);
     return (int)names.size() - 1;
   }
   cudaEvent_t ev() {
@@ -82,6 +84,7 @@ struct Prof {
     collect();
     for (auto& t : total_ms) t = 0.0;
     for (auto& c : count) c = 0;
+    for (auto& w : work) w = 0.0;
     launches = 0;
   }
   ~Prof() {

@@ -31,28 +31,44 @@ constexpr int BK = 64;  // 64 BF16 = 128 bytes = one swizzle atom per row
 using namespace ptx;
 
 // Ring depth: kStages for long reductions, two for short ones so that several CTAs (and their
-// epilogues) share an SM.
-__host__ __device__ inline int ring_stages(int K) { return (K + BK - 1) / BK >= 8 ? kStages : 2; }
+// epilogues) share an SM.  Split operands (NP = 3) carry high and low parts of both tiles per
+// stage: as many stages as fit 192 KB (two at least).
+__host__ __device__ inline uint32_t stage_bytes_of(int BN, int NP) {
+  return (uint32_t)(NP == 3 ? 2 : 1) * (uint32_t)(BM * BK * 2 + BN * BK * 2);
+}
+__host__ __device__ inline int ring_stages(int K, int BN, int NP) {
+  if (NP != 3) return (K + BK - 1) / BK >= 8 ? kStages : 2;
+  int ns = (int)(196608u / stage_bytes_of(BN, NP));
+  ns = ns > kStages ? kStages : ns;
+  return ns < 2 ? 2 : ns;
+}
 
 // Shared-memory staging of the epilogue (all but the plain epilogue): FP32 tiles [128][BN] as
 // 32-column boxes of 16 KB laid out by the TMA 128-byte swizzle (row r at r * 128 B, 16-byte
 // chunk q at position q ^ (r & 7)), so a thread that owns a row reads and writes its 16-byte
 // chunks without bank conflicts; BF16 tiles as 64-column boxes of the same layout.
 //   slot 0: the skip input (in place: the FP32 output y or g), slot 1: tanh output t (forward)
-//   or the gate input t_below (backward), then the BF16 output.
+//   or the gate input t_below (backward), then the BF16 output (split operands: its high part,
+//   then its low part).
 __host__ __device__ inline uint32_t epi_f32_bytes(int BN) { return (uint32_t)(BN / 32) * 16384u; }
 __host__ __device__ inline uint32_t epi_bf16_bytes(int BN) { return (uint32_t)((BN + 63) / 64) * 16384u; }
-__host__ __device__ inline uint32_t epi_bytes(int epi, int BN) {
+__host__ __device__ inline uint32_t epi_bytes(int epi, int BN, int NP) {
   if (epi == TC_EPI_PLAIN) return 0;
-  const uint32_t f = epi_f32_bytes(BN), h = epi_bf16_bytes(BN);
+  const uint32_t f = epi_f32_bytes(BN), h = epi_bf16_bytes(BN) * (NP == 3 ? 2u : 1u);
   return epi == TC_EPI_FWD_LAST ? f + h : 2 * f + h;
 }
 __device__ __forceinline__ uint32_t sw_off(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
 
-template <int EPI>
+// High and low BF16 parts of x (x = hi + lo up to the rounding of lo).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+template <int EPI, int NP>
 __global__ void __launch_bounds__(kThreads)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ TcMaps tb,
-              const __grid_constant__ TcEpiMaps em, const TcArgs g) {
+              const __grid_constant__ TcEpiMaps em, const TcArgs g, const __grid_constant__ TcLo lo) {
   __shared__ float s_e[2][BM];  // FWD_LAST: energy partial of each row from each column half
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -60,9 +76,9 @@ __global__ void __launch_bounds__(kThreads)
   const int BN = g.BN;
   const uint32_t a_bytes = BM * BK * 2;
   const uint32_t b_bytes = (uint32_t)BN * BK * 2;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
-  const int NS = ring_stages(g.K);
-  const uint32_t ring = (uint32_t)NS * stage_bytes, ep = epi_bytes(EPI, BN);
+  const uint32_t stage_bytes = stage_bytes_of(BN, NP);  // [A hi | B hi (| A lo | B lo)]
+  const int NS = ring_stages(g.K, BN, NP);
+  const uint32_t ring = (uint32_t)NS * stage_bytes, ep = epi_bytes(EPI, BN, NP);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (ring > ep ? ring : ep));
   uint64_t* empty = full + kStages;
   uint64_t* accf = empty + kStages;
@@ -71,6 +87,7 @@ __global__ void __launch_bounds__(kThreads)
   unsigned char* S0 = smem;                           // epilogue slots reuse the ring
   unsigned char* S1 = smem + epi_f32_bytes(BN);
   unsigned char* SB = smem + (EPI == TC_EPI_FWD_LAST ? 1 : 2) * epi_f32_bytes(BN);
+  unsigned char* SBL = SB + epi_bf16_bytes(BN);  // split operands: low part of the BF16 output
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int t = 0;
@@ -110,6 +127,10 @@ __global__ void __launch_bounds__(kThreads)
       mbar_expect_tx(&full[s], stage_bytes);
       tma_load_2d(st, &ta, &full[s], kb * BK, row0);
       tma_load_2d(st + a_bytes, &tb.m[t], &full[s], kb * BK, col0);
+      if (NP == 3) {
+        tma_load_2d(st + a_bytes + b_bytes, &lo.a, &full[s], kb * BK, row0);
+        tma_load_2d(st + 2 * a_bytes + b_bytes, &lo.b.m[t], &full[s], kb * BK, col0);
+      }
       nissued = kb + 1;
     }
     // every copy this thread started has landed before the CTA may exit: the last block issued
@@ -142,8 +163,17 @@ __global__ void __launch_bounds__(kThreads)
       tc_fence_after();
       const uint32_t sa = su32(smem + s * stage_bytes);
       const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sa + a_bytes);
+      const uint64_t adl = sdesc_sw128(sa + a_bytes + b_bytes), bdl = sdesc_sw128(sa + 2 * a_bytes + b_bytes);
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) mma_f16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+      for (int k = 0; k < BK / 16; ++k) {
+        if (NP == 3) {  // small terms first: lo.hi, hi.lo, then hi.hi
+          mma_f16(tmem, adl + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+          mma_f16(tmem, ad + 2 * k, bdl + 2 * k, idesc, 1);
+          mma_f16(tmem, ad + 2 * k, bd + 2 * k, idesc, 1);
+        } else {
+          mma_f16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+        }
+      }
       mma_commit(&empty[s]);
     }
     mma_commit(accf);
@@ -245,15 +275,25 @@ __global__ void __launch_bounds__(kThreads)
       }
       const float* bsrc = (EPI == TC_EPI_FWD) ? o : aux;
       unsigned char* sb = SB + (b >> 1) * 16384;
+      unsigned char* sbl = SBL + (b >> 1) * 16384;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {  // 8 BF16 per 16-byte chunk
-        uint32_t w[4];
+        uint32_t w[4], wl[4];
 #pragma unroll
         for (int h2 = 0; h2 < 4; ++h2) {
-          const __nv_bfloat162 pr = __floats2bfloat162_rn(bsrc[8 * k + 2 * h2], bsrc[8 * k + 2 * h2 + 1]);
+          __nv_bfloat162 pr, pl;
+          if (NP == 3) {
+            split_bf16(bsrc[8 * k + 2 * h2], pr.x, pl.x);
+            split_bf16(bsrc[8 * k + 2 * h2 + 1], pr.y, pl.y);
+            wl[h2] = *reinterpret_cast<const uint32_t*>(&pl);
+          } else {
+            pr = __floats2bfloat162_rn(bsrc[8 * k + 2 * h2], bsrc[8 * k + 2 * h2 + 1]);
+          }
           w[h2] = *reinterpret_cast<const uint32_t*>(&pr);
         }
         *reinterpret_cast<uint4*>(sb + sw_off(rl, 4 * (b & 1) + k)) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (NP == 3)
+          *reinterpret_cast<uint4*>(sbl + sw_off(rl, 4 * (b & 1) + k)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
       }
     }
   }
@@ -282,6 +322,9 @@ __global__ void __launch_bounds__(kThreads)
       if (row0 + r >= row_end || col >= g.N) continue;
       const uint32_t so = (uint32_t)((c8 >> 3) * 16384) + sw_off(r, c8 & 7);
       *reinterpret_cast<uint4*>(g.out_bf16 + (long)(row0 + r) * g.N + col) = *reinterpret_cast<const uint4*>(SB + so);
+      if (NP == 3)
+        *reinterpret_cast<uint4*>(g.out_bf16_lo + (long)(row0 + r) * g.N + col) =
+            *reinterpret_cast<const uint4*>(SBL + so);
     }
   }
   tc_fence_before();
@@ -354,16 +397,45 @@ int make_tmap_f32(CUtensorMap* map, const void* base, long rows, long cols) {
   return DP_OK;
 }
 
-cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st) {
+template <int EPI, int NP>
+cudaError_t launch_one(dim3 grid, size_t smem, const CUtensorMap& ta, const TcMaps& tb, const TcEpiMaps& em,
+                       const TcArgs& a, const TcLo& lo, cudaStream_t st) {
+  cudaError_t e = allow_max_smem(k_tc_gemm<EPI, NP>);
+  if (e == cudaSuccess) k_tc_gemm<EPI, NP><<<grid, kThreads, smem, st>>>(ta, tb, em, a, lo);
+  return e;
+}
+
+template <int NP>
+cudaError_t launch_np(int epi, dim3 grid, size_t smem, const CUtensorMap& ta, const TcMaps& tb, const TcEpiMaps& em,
+                      const TcArgs& a, const TcLo& lo, cudaStream_t st) {
+  switch (epi) {
+    case TC_EPI_PLAIN:
+      return launch_one<TC_EPI_PLAIN, NP>(grid, smem, ta, tb, em, a, lo, st);
+    case TC_EPI_FWD:
+      return launch_one<TC_EPI_FWD, NP>(grid, smem, ta, tb, em, a, lo, st);
+    case TC_EPI_FWD_LAST:
+      return launch_one<TC_EPI_FWD_LAST, NP>(grid, smem, ta, tb, em, a, lo, st);
+    default:
+      return launch_one<TC_EPI_BWD, NP>(grid, smem, ta, tb, em, a, lo, st);
+  }
+}
+
+cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st,
+                           const TcLo* lo) {
   const int tiles = a.tile_start[a.ntypes];
   if (tiles <= 0) return cudaSuccess;
   if (epi != TC_EPI_PLAIN && (a.BN % 32 != 0 || a.skip_kind == 2)) {
     set_error("tensor-core GEMM epilogue: output blocks of 32 columns, skips of kind 0 or 1 only");
     return cudaErrorInvalidValue;
   }
+  const int NP = lo ? 3 : 1;
+  if (NP == 3 && epi != TC_EPI_PLAIN && !a.out_bf16_lo) {
+    set_error("split tensor-core GEMM: the epilogue needs a low-part output");
+    return cudaErrorInvalidValue;
+  }
   dim3 grid(tiles, (a.N + a.BN - 1) / a.BN);
-  const size_t ring = (size_t)ring_stages(a.K) * (BM * BK * 2 + (size_t)a.BN * BK * 2);
-  const size_t ep = epi_bytes(epi, a.BN);
+  const size_t ring = (size_t)ring_stages(a.K, a.BN, NP) * stage_bytes_of(a.BN, NP);
+  const size_t ep = epi_bytes(epi, a.BN, NP);
   const size_t smem = (ring > ep ? ring : ep) + 1024 + 256;
   // epilogue inputs (skip, gate) as TMA maps over all rows
   TcEpiMaps em;
@@ -373,25 +445,10 @@ cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, con
       make_tmap_f32(&em.skip, a.skip_mat, rows, a.skip_ld) != DP_OK)
     return cudaErrorInvalidValue;
   if (epi == TC_EPI_BWD && make_tmap_f32(&em.tact, a.tact, rows, a.N) != DP_OK) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  switch (epi) {
-    case TC_EPI_PLAIN:
-      e = allow_max_smem(k_tc_gemm<TC_EPI_PLAIN>);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_PLAIN><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
-      break;
-    case TC_EPI_FWD:
-      e = allow_max_smem(k_tc_gemm<TC_EPI_FWD>);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
-      break;
-    case TC_EPI_FWD_LAST:
-      e = allow_max_smem(k_tc_gemm<TC_EPI_FWD_LAST>);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_FWD_LAST><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
-      break;
-    default:
-      e = allow_max_smem(k_tc_gemm<TC_EPI_BWD>);
-      if (e == cudaSuccess) k_tc_gemm<TC_EPI_BWD><<<grid, kThreads, smem, st>>>(ta, tb, em, a);
-      break;
-  }
+  TcLo none;
+  std::memset(&none, 0, sizeof(none));
+  cudaError_t e = NP == 3 ? launch_np<3>(epi, grid, smem, ta, tb, em, a, *lo, st)
+                          : launch_np<1>(epi, grid, smem, ta, tb, em, a, none, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

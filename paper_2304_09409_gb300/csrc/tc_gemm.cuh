@@ -36,6 +36,7 @@ struct TcArgs {
   const float* tact;        // bwd: tanh outputs of the layer below [rows][N]
   float* out_f32;           // [rows][N]
   __nv_bfloat16* out_bf16;  // [rows][N]
+  __nv_bfloat16* out_bf16_lo;  // split operands: [rows][N] low part x - bf16(x) of the BF16 output
   float* out_t;             // [rows][N]
   float* e_out;             // FWD_LAST: per-row energy partial of each column block [col blocks][e_ld]
   long e_ld;
@@ -48,6 +49,14 @@ struct TcEpiMaps {
   CUtensorMap skip, tact;
 };
 
+// Low halves of split BF16 operands (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)): with them
+// every product is formed as hi.hi + hi.lo + lo.hi in three tensor-core passes, which keeps
+// about 16 significant bits of each operand (relative error near 2^-17 per product).
+struct TcLo {
+  CUtensorMap a;  // A low part, same geometry as `ta`
+  TcMaps b;       // B low parts, same geometry as `tb`
+};
+
 // Tensor map of a row-major [rows][cols] BF16 matrix, 128-byte swizzle, box {64, box_rows}.
 int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int box_rows);
 // Tensor map of a row-major [rows][cols] FP32 matrix, 128-byte swizzle, box {32, 128}.
@@ -55,7 +64,10 @@ int make_tmap_f32(CUtensorMap* map, const void* base, long rows, long cols);
 
 // C[rows][N] (+epilogue) = A[rows][K] . B_t[K][N]; A from `ta` ([rows][K] row-major), B_t from
 // the type's map in `tb` (its transpose, [N][K] row-major); BF16 operands, FP32 accumulation.
-cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st);
+// With `lo` the operands are split (three passes) and every BF16 output of the epilogue is
+// written as its high part (out_bf16) and low part (out_bf16_lo).
+cudaError_t launch_tc_gemm(int epi, const CUtensorMap& ta, const TcMaps& tb, const TcArgs& a, cudaStream_t st,
+                           const TcLo* lo = nullptr);
 
 // Output columns per CTA for an N-wide output with `row_tiles` 128-row tiles in total (a
 // multiple of 32).

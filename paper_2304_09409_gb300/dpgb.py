@@ -205,6 +205,20 @@ class Model:
             out[buf.value.decode()] = (ms.value, n.value)
         return out
 
+    def profile_work(self) -> dict:
+        """{kernel name: tensor-core FLOPs issued} for the scopes that count their issued work."""
+        L = lib()
+        L.dp_profile_work.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        out = {}
+        buf = ctypes.create_string_buffer(64)
+        for k in range(L.dp_profile_count(self.handle)):
+            w = ctypes.c_double()
+            _check(L.dp_profile_read(self.handle, k, buf, 64, None, None))
+            _check(L.dp_profile_work(self.handle, k, ctypes.byref(w)))
+            if w.value > 0:
+                out[buf.value.decode()] = w.value
+        return out
+
     def launch_count(self) -> int:
         return int(lib().dp_launch_count(self.handle))
 

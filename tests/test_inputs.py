@@ -76,3 +76,28 @@ def test_parameters_are_seeded_and_laid_out():
     # first embedding layer 1 -> 25: W ~ N(0, 2/26), 25 weights, then 25 biases ~ N(0, 1)
     w = p0[:25]
     assert np.abs(w).max() < 6 * math.sqrt(2 / 26)
+
+
+def test_force_scaled_models_reach_about_one_ev_per_angstrom():
+    """The force-scaled variants scale only the output layer: the oracle's energies, forces and
+    virial scale by exactly the factor, and the force RMS lands near 1 eV/A on the water frame
+    and on an FCC frame of the metal model (the scale at which the 1e-3 eV/A bar means
+    something)."""
+    import oracle
+    cfg = I.water_model()
+    p = I.make_params(cfg, 0)
+    ps = I.water_params_scaled(0)
+    changed = np.nonzero(ps != p)[0]
+    assert changed.size == 2 * (cfg.fit[-1] + 1)  # W and b of the last layer of both types
+    fr = I.water_frame(0)
+    a = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
+    b = oracle.compute(cfg, ps, fr.coord, fr.atype, fr.box)
+    s = I.WATER_FORCE_SCALE
+    np.testing.assert_allclose(b.force, s * a.force, rtol=1e-10, atol=1e-12 * s)
+    np.testing.assert_allclose(b.virial, s * a.virial, rtol=1e-10, atol=1e-12 * s)
+    assert b.energy == pytest.approx(s * a.energy, rel=1e-12)
+    assert 0.7 < np.sqrt((b.force ** 2).mean()) < 1.5
+    cfg = I.metal_model()
+    fr = I.fcc_frame((4, 4, 4), seed=0)
+    r = oracle.compute(cfg, I.metal_params_scaled(0), fr.coord, fr.atype, fr.box)
+    assert 0.7 < np.sqrt((r.force ** 2).mean()) < 1.5

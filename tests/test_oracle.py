@@ -622,3 +622,24 @@ def test_atom_subset_equals_full_oracle(case):
     np.testing.assert_array_equal(sj, nl_j[idx])
     np.testing.assert_array_equal(ss, nl_s[idx])
     np.testing.assert_allclose(se, full.atom_energy[idx], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", ["tiny_triclinic", "water", "fcc"])
+def test_force_subset_equals_full_oracle(case):
+    """orc_force_subset forms only the sampled atoms' neighbourhoods; their forces and energies
+    must equal the full oracle's (up to summation order), including periodic images of the atom
+    itself in a cell narrower than 2 r_c and sel truncation."""
+    if case == "tiny_triclinic":
+        cfg, fr = tiny_model(), tiny_frame(seed=6)
+    elif case == "water":
+        cfg, fr = I.water_model(), I.water_frame(2)
+    else:
+        cfg = I.ModelConfig(ntypes=1, rcut=5.0, rcut_smth=0.5, sel=(80,), embed=(8, 16), axis=4, fit=(16, 16))
+        fr = I.fcc_frame((3, 3, 3), seed=2)
+    p = I.make_params(cfg, 4)
+    full = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
+    idx = np.array([0, 1, fr.natoms // 2, fr.natoms - 1])
+    f, e = oracle.force_subset(cfg, p, fr.coord, fr.atype, fr.box, idx)
+    fs = np.abs(full.force).max()
+    np.testing.assert_allclose(f, full.force[idx], rtol=0, atol=1e-12 * fs)
+    np.testing.assert_allclose(e, full.atom_energy[idx], rtol=1e-13, atol=1e-13)
