@@ -15,7 +15,11 @@
  *
  * Conventions shared by every entry point
  *   - Every call returns a status code (DP_OK = 0); nothing aborts.  On error,
- *     dp_last_error() returns a message for the calling thread.
+ *     dp_last_error() gives a message for the calling thread.
+ *   - Non-finite coordinates (NaN, Inf) are rejected with DP_E_ARG: host arrays before any
+ *     work is launched, device arrays by a flag the list build raises (the frame's atoms are
+ *     then binned as if at the origin, so no kernel leaves its buffers, and the call's results
+ *     are not valid).
  *   - The caller owns every input and output buffer.  The library owns models,
  *     neighbour lists and the scratch memory it allocates for them.
  *   - Array arguments may be host or device pointers (detected per pointer).  Host
@@ -113,7 +117,9 @@ int dp_build_nlist(dp_model* model, int natoms, const double* coord, const int* 
  * The paper has no counterpart to this entry point.  It is for callers that cannot
  * allocate device memory at the point where they need a list: an MD engine that owns all
  * device memory and forbids other allocations, or a loop being captured into a CUDA graph.
- * It computes exactly what dp_build_nlist computes (same kernels, same bit-exact result)
+ * It computes exactly what dp_build_nlist computes (the same bit-exact list, from the same
+ * cell binning; the search always runs the per-atom kernel with the full candidate buffer,
+ * where dp_build_nlist prefers a cell-centred kernel whose staging buffer is sized per frame)
  * but needs no model object and calls no allocating routine: its cell-list scratch is one
  * static device array of about 13.3 MiB that every GPU loading the library keeps until exit.
  *   cfg: only ntypes, sel and rcut are used.
@@ -122,8 +128,8 @@ int dp_build_nlist(dp_model* model, int natoms, const double* coord, const int* 
  *   caller owns, filled exactly as dp_nlist_export fills its host arrays.
  * Limits: natoms <= DP_NOALLOC_MAX_ATOMS, natoms*Nc <= DP_NOALLOC_MAX_SLOTS, cell grid <=
  * DP_NOALLOC_MAX_CELLS cells; larger frames are rejected with DP_E_ARG and a message.
- * The first call on a device looks up the array's device address (one-time set-up), so
- * make that first call before any stream capture.  All calls on a device share the array:
+ * The first call on a device looks up the array's device address (one-time set-up, repeated
+ * only if the device's context was reset), so make that first call before any stream capture.  All calls on a device share the array:
  * calls that overlap on the GPU race with each other; serialise them (one stream, or
  * events).  Returns as dp_build_nlist; the call synchronises `stream` to read its status. */
 #define DP_NOALLOC_MAX_ATOMS 32768
@@ -214,8 +220,21 @@ int dp_param_grad(dp_model* model, int nframes, const int* natoms, const double*
  * `stream`.  DP_E_ARG on a size mismatch, DP_E_UNSUPPORTED for compressed models. */
 int dp_model_set_params(dp_model* model, const double* params, long n_params, void* stream);
 
-/* Message for the last error raised on the calling thread ("" if none). */
-const char* dp_last_error(void);
+/* Message of the last error raised on the calling thread ("" if none), copied into buf
+ * (host, len bytes) and NUL-terminated, truncated to len - 1 characters.  Returns the length of
+ * the whole message (as snprintf does), so a caller can size buf; buf may be NULL when len is 0. */
+int dp_last_error(char* buf, int len);
+
+/* ---- failure detection self-test (no counterpart in the paper) ----
+ * Every wait of the library's tensor-core kernels on an mbarrier (TMA arrivals, MMA completion,
+ * the epilogue's hand-backs) is bounded: after a fixed number of polls it records an error,
+ * the CTA leaves, and the call returns DP_E_TIMEOUT with the context still usable.  This entry
+ * point exercises that mechanism on its own: one CTA initialises an mbarrier that nothing ever
+ * arrives at and waits on it through the same bounded-wait routine, with spin_limit polls
+ * (<= 0: the limit the kernels use).  No copy or MMA is in flight, so giving up is safe.
+ * Returns DP_E_TIMEOUT when the wait gave up (the expected outcome), DP_OK if it completed,
+ * DP_E_CUDA on a launch failure.  Synchronises `stream`. */
+int dp_wait_selftest(long spin_limit, void* stream);
 
 #ifdef __cplusplus
 }

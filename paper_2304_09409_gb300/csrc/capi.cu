@@ -1,5 +1,6 @@
 // C ABI of libdpgb: model and neighbour-list objects, scratch management, and the
 // per-frame driver that chains the kernels of the se_e2_a path.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -11,6 +12,7 @@
 #include "path.cuh"
 #include "table.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace dpgb {
 
@@ -21,6 +23,19 @@ void set_error(const std::string& msg) { g_err = msg; }
 __device__ int g_gemm_err;
 
 namespace {
+
+// One mbarrier that expects one arrival nobody makes; thread 0 waits on it through the bounded
+// wait of the tensor-core kernels, which gives up after `limit` polls and raises *err.
+__global__ void k_wait_selftest(long limit, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    ptx::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ptx::mbar_wait_limit(&bar, 0, err, limit);
+  __syncthreads();
+}
 
 __global__ void k_narrow(const double* __restrict__ x, long n, float* __restrict__ y) {
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,6 +88,15 @@ long layout(const dp_model_config& c, std::vector<LayerDesc>* emb, std::vector<L
 
 }  // namespace
 
+int check_finite_host(const double* x, long n) {
+  for (long k = 0; k < n; ++k)
+    if (!std::isfinite(x[k])) {
+      set_error("non-finite coordinate (NaN or Inf) at atom " + std::to_string(k / 3));
+      return DP_E_ARG;
+    }
+  return DP_OK;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -123,6 +147,10 @@ int read_status(dp_model* md, cudaStream_t st, int* n_overflow) {
     if (s.mma_blocks[1]) md->prof.work[md->prof.id_of("mom_bwd")] += per * s.mma_blocks[1];
   }
   if (n_overflow) *n_overflow = s.sel_overflow;
+  if (s.bad_coord) {
+    set_error("non-finite coordinate (NaN or Inf): results of this call are not valid");
+    return DP_E_ARG;
+  }
   if (s.bad_type) {
     set_error("atom type outside [0, ntypes)");
     return DP_E_ARG;
@@ -192,7 +220,38 @@ using namespace dpgb;
 
 extern "C" {
 
-const char* dp_last_error(void) { return g_err.c_str(); }
+int dp_last_error(char* buf, int len) {
+  if (buf && len > 0) {
+    const size_t n = std::min(g_err.size(), (size_t)len - 1);
+    std::memcpy(buf, g_err.data(), n);
+    buf[n] = 0;
+  }
+  return (int)g_err.size();
+}
+
+int dp_wait_selftest(long spin_limit, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  DP_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  int herr = -1;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, st>>>(spin_limit > 0 ? spin_limit : ptx::kSpin, err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(err);
+  if (e != cudaSuccess) {
+    set_error(std::string("wait self-test: ") + cudaGetErrorString(e));
+    return DP_E_CUDA;
+  }
+  if (herr) {
+    set_error("wait self-test: the bounded wait gave up, as intended");
+    return DP_E_TIMEOUT;
+  }
+  return DP_OK;
+}
 
 long dp_model_n_params(const dp_model_config* cfg) {
   if (check_config(cfg) != DP_OK) return -1;

@@ -46,6 +46,8 @@ struct dp_nlist {
 namespace dpgb {
 
 bool is_device_ptr(const void* p);
+// DP_E_ARG (with a message) when one of the n host values is NaN or infinite.
+int check_finite_host(const double* x, long n);
 int ensure_ws(dp_model* md, size_t bytes);
 int ensure_stage(dp_model* md, size_t bytes);
 int read_status(dp_model* md, cudaStream_t st, int* n_overflow);

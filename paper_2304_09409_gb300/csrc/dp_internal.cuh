@@ -141,6 +141,7 @@ struct DevStatus {
   int bad_type;       // a type outside [0, ntypes)
   int timeout;        // a bounded wait of a tensor-core kernel gave up
   int type_change;    // the per-type atom counts differ from the ones the call was set up with
+  int bad_coord;      // a coordinate was NaN or infinite (the atom was binned as if at the origin)
   unsigned int mma_blocks[2];  // tensor-core blocks the moment kernels issued (forward, backward)
 };
 

@@ -318,6 +318,10 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   const bool own_nlist = (nlist == nullptr);
   int Ntot = 0;
   for (int f = 0; f < F; ++f) Ntot += natoms[f];
+  if (copy_coord) {  // host coordinates are checked before any work is queued
+    const int rc0 = check_finite_host(coord, 3L * Ntot);
+    if (rc0 != DP_OK) return rc0;
+  }
   // open boundaries (one frame): the cell grid needs the bounding box first
   double lohi[6] = {0, 0, 0, 0, 0, 0};
   if (!boxes) {
@@ -643,6 +647,10 @@ int dp_build_nlist(dp_model* md, int N, const double* coord, const int* type, co
   cudaStream_t st = (cudaStream_t)stream;
   const DeviceModel& m = md->m;
   const bool copy_coord = !is_device_ptr(coord), copy_type = !is_device_ptr(type);
+  if (copy_coord) {
+    const int rc0 = check_finite_host(coord, 3L * N);
+    if (rc0 != DP_OK) return rc0;
+  }
   double lohi[6] = {0, 0, 0, 0, 0, 0};
   if (!box) {
     const int rc = copy_coord ? host_bbox(coord, N, lohi) : device_bbox(md, coord, N, st, lohi);

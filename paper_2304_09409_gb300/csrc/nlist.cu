@@ -111,7 +111,14 @@ __global__ void k_bin(const NlGeom* __restrict__ G, const int* __restrict__ atom
   if (i >= natoms) return;
   const int fr = atom_frame ? atom_frame[i] : 0;
   const NlGeom& g = G[fr];
-  const Binned b = bin_atom(g, coord + 3 * i);
+  double x[3] = {coord[3 * i], coord[3 * i + 1], coord[3 * i + 2]};
+  if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+    // reported (the call fails with DP_E_ARG); binned as if at the origin so that every index
+    // derived from the position stays inside its buffer
+    atomicExch(&st->bad_coord, 1);
+    x[0] = x[1] = x[2] = 0.0;
+  }
+  const Binned b = bin_atom(g, x);
   const int t = type[i];
   if (t < 0 || t >= ntypes) {  // reported; the atom takes part in no list
     atom_key[i] = make_int2(-1, 0);

@@ -4,9 +4,13 @@
 // that hands the library a pre-reserved arena and forbids any other allocation, code that
 // runs while another component owns the whole device memory pool, or a driver loop that is
 // being recorded into a CUDA graph (allocation calls are not allowed during capture).  This
-// entry point serves them: it runs the same cell-list kernels as dp_build_nlist, but its
-// cell-list scratch lives in one file-scope device array of fixed size, and its outputs go
-// straight into buffers the caller already owns.
+// entry point serves them: it bins atoms into the same cell list as dp_build_nlist and forms
+// the same bit-exact list, but its cell-list scratch lives in one file-scope device array of
+// fixed size, and its outputs go straight into buffers the caller already owns.  The search
+// itself always runs the per-atom kernel (one warp per centre atom, the full DP_MAX_CANDIDATES
+// buffer): the cell-centred kernel that dp_build_nlist prefers stages a candidate stream sized
+// from each frame's density and retries on the per-atom kernel when a cell overflows it, and
+// this entry point has neither the room to size it nor a second pass.
 //
 // The array is shared by every call on a device and keeps the previous call's contents;
 // everything that must start at zero (cell counters, status words) is cleared by each call.
@@ -47,10 +51,32 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_dev[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};  // the context the cached address belongs to
 std::mutex g_scratch_mu;
 
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn g_ctx_get = nullptr;
+
+// The current driver context (null if it cannot be read): a device reset or a destroyed primary
+// context gives a new one, in which the array has to be looked up again.
+void* current_context() {
+  if (!g_ctx_get) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_ctx_get = reinterpret_cast<CtxGetCurrentFn>(fn);
+  }
+  void* ctx = nullptr;
+  return g_ctx_get(&ctx) == 0 ? ctx : nullptr;
+}
+
 // Device address of the static scratch on the current device.  In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per device.
+// name is only a host-side stand-in, so the address is looked up once per device (again when
+// the device's context has changed since, or when the context cannot be identified).
 int scratch_on_current_device(char** out) {
   int dev = 0;
   DP_CUDA_TRY(cudaGetDevice(&dev));
@@ -59,10 +85,12 @@ int scratch_on_current_device(char** out) {
     return DP_E_ARG;
   }
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_dev[dev]) {
+  void* ctx = current_context();  // null before the runtime has made a context current: look up
+  if (!g_scratch_dev[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     DP_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_scratch_dev[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = static_cast<char*>(g_scratch_dev[dev]);
   return DP_OK;
@@ -163,6 +191,10 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
   DP_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   DP_CUDA_TRY(cudaStreamSynchronize(st));
   if (n_overflow) *n_overflow = hs.sel_overflow;
+  if (hs.bad_coord) {
+    set_error("non-finite coordinate (NaN or Inf): the list is not valid");
+    return DP_E_ARG;
+  }
   if (hs.bad_type) {
     set_error("atom type outside [0, ntypes)");
     return DP_E_ARG;

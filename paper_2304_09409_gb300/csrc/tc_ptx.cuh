@@ -32,12 +32,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false (and *err set) when it runs out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
-  for (long it = 0; it < kSpin; ++it)
+// Bounded wait for the phase with the given parity: at most `limit` polls; false (and *err set)
+// when it runs out.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* b, uint32_t parity, int* err, long limit) {
+  for (long it = 0; it < limit; ++it)
     if (mbar_try(b, parity)) return true;
   atomicExch(err, 1);
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+  return mbar_wait_limit(b, parity, err, kSpin);
 }
 
 // 2-D tiled TMA load into shared memory, completion signalled on `bar` (transaction bytes).

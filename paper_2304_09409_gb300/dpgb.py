@@ -31,7 +31,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 EXPORTED = [
     "dp_model_create", "dp_init_model", "dp_free_model", "dp_model_n_params", "dp_build_nlist",
     "dp_nlist_export", "dp_free_nlist", "dp_compute", "dp_model_export_table", "dp_last_error",
-    "dp_build_nlist_noalloc", "dp_compute_batch", "dp_param_grad", "dp_model_set_params",
+    "dp_build_nlist_noalloc", "dp_compute_batch", "dp_param_grad", "dp_model_set_params", "dp_wait_selftest",
+    "dp_profile_work",
 ]
 
 
@@ -96,7 +97,9 @@ def lib() -> ctypes.CDLL:
         L.dp_free_nlist.argtypes = [vp]
         L.dp_compute.argtypes = [vp, vp, ip, vp, vp, vp, vp, vp, vp, vp, vp]
         L.dp_model_export_table.argtypes = [vp, vp, ctypes.POINTER(ip)]
-        L.dp_last_error.restype = ctypes.c_char_p
+        L.dp_last_error.argtypes = [ctypes.c_char_p, ip]
+        L.dp_last_error.restype = ip
+        L.dp_wait_selftest.argtypes = [ctypes.c_long, vp]
         L.dp_profile_enable.argtypes = [vp, ip]
         L.dp_profile_reset.argtypes = [vp]
         L.dp_profile_count.argtypes = [vp]
@@ -109,7 +112,16 @@ def lib() -> ctypes.CDLL:
 
 
 def last_error() -> str:
-    return lib().dp_last_error().decode()
+    L = lib()
+    n = L.dp_last_error(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    L.dp_last_error(buf, n + 1)
+    return buf.value.decode(errors="replace")
+
+
+def wait_selftest(spin_limit: int = 0, stream=None) -> int:
+    """dp_wait_selftest: a bounded mbarrier wait that nothing releases; DP_E_TIMEOUT expected."""
+    return int(lib().dp_wait_selftest(int(spin_limit), _stream_handle(stream)))
 
 
 def _check(code: int, allow=()):
