@@ -172,10 +172,11 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
   }
   base.err = &io.status->timeout;  // bounded waits that give up are reported by the call
   const float* p32 = m.p32;
-  // the staged epilogues hold at most 128 output columns per CTA
+  // the staged epilogues hold at most 128 output columns per CTA; split operands take 64 (two
+  // CTAs of 97 KB share an SM)
   auto pick_bn = [&](int n, bool staged) {
     const int bn = tc_pick_bn(n, tiles);
-    return staged ? std::min(bn, 128) : bn;
+    return split ? std::min(bn, 64) : (staged ? std::min(bn, 128) : bn);
   };
   // A operand (high part, and the low part when split) and the type's weight maps
   auto maps = [&](const void* A_hi, const void* A_lo, int K, int l, int dir, int BN, CUtensorMap& ta, TcMaps& tb,

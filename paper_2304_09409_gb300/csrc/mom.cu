@@ -682,12 +682,26 @@ __global__ void __launch_bounds__(kMomThreads, 3)
         if (g.d_bf16 == 2) {  // split operands of the FP32 mode's tensor-core fitting net
           __nv_bfloat16* Dh = reinterpret_cast<__nv_bfloat16*>(g.D) + o;
           __nv_bfloat16* Dl = reinterpret_cast<__nv_bfloat16*>(g.D_lo) + o;
+          float dl[16];
 #pragma unroll
-          for (int l = 0; l < 16; ++l) {
-            if (l >= g.A) break;
-            const __nv_bfloat16 h = __float2bfloat16_rn(d[l]);
-            Dh[l] = h;
-            Dl[l] = __float2bfloat16_rn(d[l] - __bfloat162float(h));
+          for (int l = 0; l < 16; ++l) dl[l] = d[l] - __bfloat162float(__float2bfloat16_rn(d[l]));
+          if (g.A == 16) {  // the hi parts are d rounded to BF16, the lo parts the remainders rounded
+            uint4* h4 = reinterpret_cast<uint4*>(Dh);
+            uint4* l4 = reinterpret_cast<uint4*>(Dl);
+            h4[0] = make_uint4(pack_b2(d[0], d[1]), pack_b2(d[2], d[3]), pack_b2(d[4], d[5]), pack_b2(d[6], d[7]));
+            h4[1] = make_uint4(pack_b2(d[8], d[9]), pack_b2(d[10], d[11]), pack_b2(d[12], d[13]),
+                               pack_b2(d[14], d[15]));
+            l4[0] = make_uint4(pack_b2(dl[0], dl[1]), pack_b2(dl[2], dl[3]), pack_b2(dl[4], dl[5]),
+                               pack_b2(dl[6], dl[7]));
+            l4[1] = make_uint4(pack_b2(dl[8], dl[9]), pack_b2(dl[10], dl[11]), pack_b2(dl[12], dl[13]),
+                               pack_b2(dl[14], dl[15]));
+          } else {
+#pragma unroll
+            for (int l = 0; l < 16; ++l)
+              if (l < g.A) {
+                Dh[l] = __float2bfloat16_rn(d[l]);
+                Dl[l] = __float2bfloat16_rn(dl[l]);
+              }
           }
         } else if (g.d_bf16) {
           __nv_bfloat16* Db = reinterpret_cast<__nv_bfloat16*>(g.D) + o;

@@ -32,15 +32,14 @@ using namespace ptx;
 
 // Ring depth: kStages for long reductions, two for short ones so that several CTAs (and their
 // epilogues) share an SM.  Split operands (NP = 3) carry high and low parts of both tiles per
-// stage: as many stages as fit 192 KB (two at least).
+// stage (48 KB at BN = 64): two stages, so that two CTAs share an SM and one's epilogue runs
+// while the other's operands stream in.
 __host__ __device__ inline uint32_t stage_bytes_of(int BN, int NP) {
   return (uint32_t)(NP == 3 ? 2 : 1) * (uint32_t)(BM * BK * 2 + BN * BK * 2);
 }
 __host__ __device__ inline int ring_stages(int K, int BN, int NP) {
-  if (NP != 3) return (K + BK - 1) / BK >= 8 ? kStages : 2;
-  int ns = (int)(196608u / stage_bytes_of(BN, NP));
-  ns = ns > kStages ? kStages : ns;
-  return ns < 2 ? 2 : ns;
+  if (NP == 3) return 2;
+  return (K + BK - 1) / BK >= 8 ? kStages : 2;
 }
 
 // Shared-memory staging of the epilogue (all but the plain epilogue): FP32 tiles [128][BN] as
