@@ -425,12 +425,14 @@ def run_serving(n_frames=3000, rate=2000.0, slots=3, max_batch_atoms=65536, prec
 
 def run_training(steps=5, warmup=3, n_frames=32):
     """Training-style differentiation: one batch of 32 water frames (192 atoms, seeds 1..32),
-    targets E*, F* from a second random-weight model on the FP64 GPU path, loss of Sec. II.B
-    (pE 0.02, pF 1).  Times dp_param_grad alone (FP32 and FP64) and a whole Adam step through
-    the torch.autograd.Function (FP32): forward E/F, loss, backward, update."""
+    targets E*, F*, Xi* from a second random-weight model on the FP64 GPU path, the loss of
+    Eq. (loss) with energy, force and virial terms (pE 0.02, pF 1, pXi 0.5).  Times
+    dp_param_grad alone (FP32 and FP64) and a whole Adam step through the torch.autograd.Function
+    (FP32) with the learning-rate and prefactor schedules of Sec. II.B: forward E/F/Xi, loss,
+    backward, update."""
     import torch
     from paper_2304_09409_gb300 import dpgb, inputs as I
-    from paper_2304_09409_gb300.autograd import Trainer
+    from paper_2304_09409_gb300.autograd import Schedule, Trainer
     cfg = I.water_model()
     p, q = I.make_params(cfg, 0), I.make_params(cfg, 1)
     frames = [I.water_frame(s) for s in range(1, n_frames + 1)]
@@ -439,27 +441,30 @@ def run_training(steps=5, warmup=3, n_frames=32):
     atype = torch.tensor(np.concatenate([f.atype for f in frames]).astype(np.int32), device="cuda")
     boxes = np.stack([f.box for f in frames])
     ref = dpgb.Model(cfg, q, precision="fp64")
-    e_ref, f_ref, _, _ = dpgb.compute_batch(ref, nat, coord, atype, boxes)
+    e_ref, f_ref, v_ref, _ = dpgb.compute_batch(ref, nat, coord, atype, boxes)
     ref.free()
     B, N = len(frames), int(nat.sum())
     per_n = torch.tensor(np.repeat(nat, nat).astype(np.float64), device="cuda")[:, None]
     nat_t = torch.tensor(nat.astype(np.float64), device="cuda")
+    pE, pF, pV = 0.02, 1.0, 0.5
     out = {"workload": f"{B} water frames x 192 atoms (seeds 1..{B}), targets from a second random-weight model",
-           "loss": "pE dE^2/N + pF |dF|^2/(3N), pE 0.02, pF 1, mean over frames"}
+           "loss": "Eq. (loss): pE dE^2/N + pF |dF|^2/(3N) + pXi |dXi|^2/(9N), pE 0.02, pF 1, pXi 0.5, mean over "
+                   "frames"}
     grads = {}
     for prec in ("fp64", "fp32"):
         m = dpgb.Model(cfg, p, precision=prec)
-        e, f, _, _ = dpgb.compute_batch(m, nat, coord, atype, boxes)
-        g_e = 2 * 0.02 * (e - e_ref) / (nat_t * B)
-        g_f = 2 * (f - f_ref) / (3 * per_n * B)
-        g = dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f)
+        e, f, v, _ = dpgb.compute_batch(m, nat, coord, atype, boxes)
+        g_e = 2 * pE * (e - e_ref) / (nat_t * B)
+        g_f = 2 * pF * (f - f_ref) / (3 * per_n * B)
+        g_v = 2 * pV * (v - v_ref) / (9 * nat_t[:, None, None] * B)
+        g = dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, g_virial=g_v)
         for _ in range(warmup):
-            dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, out=g)
+            dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, out=g, g_virial=g_v)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(steps):
-            dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, out=g)
+            dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, out=g, g_virial=g_v)
         b.record()
         torch.cuda.synchronize()
         grads[prec] = g.clone()
@@ -468,14 +473,17 @@ def run_training(steps=5, warmup=3, n_frames=32):
     out["fp32_grad_rel_err_vs_fp64"] = float(torch.linalg.norm(grads["fp32"] - grads["fp64"])
                                              / torch.linalg.norm(grads["fp64"]))
     m = dpgb.Model(cfg, p, precision="fp32")
-    tr = Trainer(m, p, lr=1e-3, pE=0.02, pF=1.0)
+    sched = Schedule(lr0=1e-3, lr_stop=3.51e-8, stop_steps=1000000, decay_steps=5000, pE=(pE, 1.0), pF=(pF, 1.0),
+                     pV=(pV, 0.5))
+    tr = Trainer(m, p, schedule=sched)
     for _ in range(warmup):
-        tr.step(nat, coord, atype, boxes, e_ref, f_ref)
+        tr.step(nat, coord, atype, boxes, e_ref, f_ref, v_ref)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = [tr.step(nat, coord, atype, boxes, e_ref, f_ref) for _ in range(steps)]
+    losses = [tr.step(nat, coord, atype, boxes, e_ref, f_ref, v_ref) for _ in range(steps)]
     torch.cuda.synchronize()
     out["adam_step_ms_fp32"] = (time.perf_counter() - t0) / steps * 1e3
+    out["schedule"] = "Eq. (learning_rate): lr 1e-3 -> 3.51e-8 over 1e6 steps, decay every 5000; p_eta(tau) start -> limit"
     out["atoms_per_batch"] = N
     out["loss_first_last"] = [losses[0], losses[-1]]
     m.free()

@@ -197,23 +197,26 @@ int dp_compute_batch(dp_model* model, int nframes, const int* natoms, const doub
                      const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
                      void* stream);
 
-/* ---- training: parameter gradient of an energy + force objective (Sec. II.B) ----
- * The loss of Sec. II.B weighs energy and force errors (prefactors p_e, p_f).  Its gradient
- * with respect to the parameters needs the derivative of the force F = -dE/dr with respect
- * to every weight: a second-order ("double backward") derivative of E.  This entry point
- * returns, for the model's current parameters,
- *   grad = d/dtheta [ sum_f g_energy[f] E_f + sum_i g_force[i] . F_i ]
- * i.e. the vector-Jacobian product of (E, F) with the cotangents (g_energy, g_force); with
- * g_energy[f] = dL/dE_f and g_force = dL/dF it is dL/dtheta for any loss L(E, F).  All of it
- * runs on the GPU: a tangent pass along g_force through the whole path, then a reverse pass
- * over the primal and tangent computations.
+/* ---- training: parameter gradient of an energy + force + virial objective (Sec. II.B) ----
+ * The loss of Sec. II.B (Eq. (loss)) weighs energy, force and virial errors (prefactors p_E,
+ * p_F, p_Xi).  Its gradient with respect to the parameters needs the derivatives of the force
+ * F = -dE/dr and of the virial with respect to every weight: second-order ("double backward")
+ * derivatives of E.  This entry point returns, for the model's current parameters,
+ *   grad = d/dtheta [ sum_f g_energy[f] E_f + sum_i g_force[i] . F_i + sum_f sum_ab g_virial[f][a][b] Xi_f,ab ]
+ * i.e. the vector-Jacobian product of (E, F, Xi) with the cotangents; with g = dL/d(E, F, Xi)
+ * it is dL/dtheta for any loss L(E, F, Xi).  All of it runs on the GPU: one tangent pass
+ * through the whole path along the pair-displacement tangent (w_j - w_i) + g_virial[f] r_ij
+ * (w = g_force; sum g:Xi is minus the derivative of E along that homogeneous deformation),
+ * then a reverse pass over the primal and tangent computations.
  *   Frames are passed as for dp_compute_batch (boxes may be NULL only when nframes == 1).
- *   g_energy [nframes], g_force [sum natoms][3] (input atom order), grad [n_params] in the
+ *   g_energy [nframes], g_force [sum natoms][3] (input atom order), g_virial [nframes][9]
+ *   (row-major, or NULL for no virial term; periodic frames only), grad [n_params] in the
  *   parameter layout of dp_model_create; each may be a host or a device pointer.
  * Only uncompressed FP64 and FP32 models (DP_E_UNSUPPORTED otherwise); the arithmetic runs
  * in the model's precision.  Synchronises `stream`.  Returns as dp_compute. */
 int dp_param_grad(dp_model* model, int nframes, const int* natoms, const double* coord, const int* type,
-                  const double* boxes, const double* g_energy, const double* g_force, double* grad, void* stream);
+                  const double* boxes, const double* g_energy, const double* g_force, const double* g_virial,
+                  double* grad, void* stream);
 
 /* Replace the parameters of an uncompressed model in place (a training step's update).
  * params [n_params] FP64, host or device, in the layout of dp_model_create.  Synchronises

@@ -288,21 +288,23 @@ def _pack_frames(cfg, frames):
         np.ascontiguousarray(np.concatenate(nss), dtype=np.int32)
 
 
-def loss_dir(cfg, params, vdir, frames, e_ref, f_ref, pE=1.0, pF=1.0):
-    """Energy+force loss of a batch of frames (Sec. II.B) and its derivative along the
-    parameter direction vdir (hyper-dual numbers).  Returns (L, dL . vdir)."""
+def loss_dir(cfg, params, vdir, frames, e_ref, f_ref, pE=1.0, pF=1.0, pV=0.0, v_ref=None):
+    """Energy + force (+ virial) loss of a batch of frames (Sec. II.B, Eq. (loss)) and its
+    derivative along the parameter direction vdir (hyper-dual numbers).  v_ref: [B, 3, 3]
+    reference virials, or None for no virial term.  Returns (L, dL . vdir)."""
     L_ = _L()
     if not hasattr(L_, "_loss_set"):
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         L_.orc_loss_dir.argtypes = [ctypes.POINTER(_Cfg), dp, dp, ctypes.c_int, ip, dp, ip, dp, ip, ip, dp, dp,
-                                    ctypes.c_double, ctypes.c_double, dp]
+                                    ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double]
         L_.orc_loss_dir.restype = ctypes.c_double
         L_._loss_set = True
     nat, coord, atype, boxes, nj, ns = _pack_frames(cfg, frames)
     dL = ctypes.c_double()
     c = _cfg(cfg)
+    vr = None if v_ref is None else np.ascontiguousarray(np.asarray(v_ref, dtype=np.float64).reshape(-1, 9))
     val = L_.orc_loss_dir(ctypes.byref(c), _d(_f64(params)), _d(_f64(vdir)), len(frames), _i(nat), _d(coord),
                           _i(atype), _d(boxes), _i(nj), _i(ns), _d(_f64(e_ref)), _d(_f64(np.concatenate(f_ref))),
-                          float(pE), float(pF), ctypes.byref(dL))
+                          float(pE), float(pF), ctypes.byref(dL), _d(vr), float(pV))
     return val, dL.value

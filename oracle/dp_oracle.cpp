@@ -948,15 +948,22 @@ int orc_force_subset(const OrcConfig* cfg, const double* params, int N, const do
   return ov;
 }
 
-// Loss of a batch of frames, Sec. II.B (loss function):
-//   L = (1/B) sum_f [ pE (E_f - E*_f)^2 / N_f + pF sum_i |F_i - F*_i|^2 / (3 N_f) ]
-// and its derivative along the parameter direction v.  Forces come from the reverse pass.
-// With Delta F = F - F*, sum_i Delta F_i . dF_i/dtheta . v = -d2E/(de1 de2) for the
-// perturbation r + e1 Delta F, theta + e2 v, which one hyper-dual evaluation gives exactly.
-// Frames are concatenated (natoms[f] atoms each); boxes [B][9]; lists [sum natoms][Nc] (+shift).
+// Loss of a batch of frames, Sec. II.B, Eq. (loss) with the energy, force and virial terms:
+//   L = (1/B) sum_f [ pE (E_f - E*_f)^2 / N_f + pF sum_i |F_i - F*_i|^2 / (3 N_f)
+//                     + pXi sum_ab (Xi_f,ab - Xi*_f,ab)^2 / (9 N_f) ]
+// and its derivative along the parameter direction v.  Forces and virials come from the reverse
+// pass.  With Delta F = F - F*, sum_i Delta F_i . dF_i/dtheta . v = -d2E/(de1 de2) for the
+// perturbation r + e1 Delta F, theta + e2 v; with G = Xi - Xi*, sum_ab G_ab dXi_ab/dtheta . v is
+// -d2E/(de1 de2) for the homogeneous deformation r -> r + e1 r G^T, h -> h + e1 h G^T (the
+// virial being minus the derivative of E under r -> r (I + eps), h -> h (I + eps) with respect
+// to eps transposed).  Both deformations go into the one e1 direction, weighted by their loss
+// coefficients, so one hyper-dual evaluation per frame gives the derivative exactly.
+// Frames are concatenated (natoms[f] atoms each); boxes [B][9]; lists [sum natoms][Nc] (+shift);
+// v_ref [B][9] may be null (no virial term).
 double orc_loss_dir(const OrcConfig* cfg, const double* params, const double* vdir, int B, const int* natoms,
                     const double* coord, const int* type, const double* boxes, const int* nl_j, const int* nl_shift,
-                    const double* e_ref, const double* f_ref, double pE, double pF, double* dL) {
+                    const double* e_ref, const double* f_ref, double pE, double pF, double* dL, const double* v_ref,
+                    double pXi) {
   Layout L = make_layout(*cfg);
   const int nc = L.nc;
   const long np = L.n_params;
@@ -979,20 +986,35 @@ double orc_loss_dir(const OrcConfig* cfg, const double* params, const double* vd
     orc_compute(cfg, params, n, x, ty, box, nj.data(), ns.data(), nullptr, 0, 0, 0, 0, 0, &e, force.data(), vir.data(),
                 ae.data(), 0);
     const double dE = e - e_ref[f];
+    const double cF = 2.0 * pF / (3.0 * n), cX = v_ref ? 2.0 * pXi / (9.0 * n) : 0.0;
+    double G[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, x2 = 0.0;
+    if (v_ref)
+      for (int k = 0; k < 9; ++k) {
+        G[k] = vir[k] - v_ref[9 * f + k];
+        x2 += G[k] * G[k];
+      }
     double f2 = 0.0;
     std::vector<HD> hx((size_t)3 * n), hb(9);
-    for (int i = 0; i < 3 * n; ++i) {
-      const double dF = force[i] - f_ref[3 * off + i];
-      f2 += dF * dF;
-      hx[i] = HD(x[i], dF, 0.0, 0.0);
-    }
-    for (int k = 0; k < 9; ++k) hb[k] = HD(box[k]);
+    for (int i = 0; i < n; ++i)
+      for (int b = 0; b < 3; ++b) {
+        const double dF = force[3 * i + b] - f_ref[3 * (off + i) + b];
+        f2 += dF * dF;
+        double t = cF * dF;  // e1 direction: force term ...
+        for (int a = 0; a < 3; ++a) t += cX * x[3 * i + a] * G[3 * b + a];  // ... and deformation (r G^T)_b
+        hx[3 * i + b] = HD(x[3 * i + b], t, 0.0, 0.0);
+      }
+    for (int g = 0; g < 3; ++g)
+      for (int b = 0; b < 3; ++b) {
+        double t = 0.0;
+        for (int a = 0; a < 3; ++a) t += cX * box[3 * g + a] * G[3 * b + a];  // (h G^T)_gb
+        hb[3 * g + b] = HD(box[3 * g + b], t, 0.0, 0.0);
+      }
     std::vector<int> code((size_t)n * nc);
     for (size_t k = 0; k < code.size(); ++k) code[k] = pack_shift(ns[3 * k], ns[3 * k + 1], ns[3 * k + 2]);
     const HD E = energy_generic<HD, HD>(*cfg, L, hp.data(), n, hx.data(), ty, hb.data(), nj.data(), code.data(),
                                         nullptr);
-    loss += pE * dE * dE / n + pF * f2 / (3.0 * n);
-    dloss += 2.0 * pE * dE / n * E.b - 2.0 * pF / (3.0 * n) * E.ab;
+    loss += pE * dE * dE / n + pF * f2 / (3.0 * n) + (v_ref ? pXi * x2 / (9.0 * n) : 0.0);
+    dloss += 2.0 * pE * dE / n * E.b - E.ab;
     off += n;
   }
   if (dL) *dL = dloss / B;

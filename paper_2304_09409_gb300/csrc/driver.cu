@@ -302,6 +302,7 @@ int run_path(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena&
 struct GradReq {
   const double* g_energy;  // [F] host or device
   const double* g_force;   // [N][3] host or device
+  const double* g_virial;  // [F][9] host or device, or null
   double* grad;            // [n_params] host or device
 };
 
@@ -346,15 +347,17 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
   carve(pre, m, T, own_nlist, copy_coord, copy_type, host_e, host_v, host_f, dev_ae, b);
   // gradient mode: device copies of the seeds and of the result where the caller's are host arrays
   const bool g_a_host = gr && !is_device_ptr(gr->g_energy), g_w_host = gr && !is_device_ptr(gr->g_force),
+             g_v_host = gr && gr->g_virial && !is_device_ptr(gr->g_virial),
              g_out_host = gr && !is_device_ptr(gr->grad);
-  double *d_ga = nullptr, *d_gw = nullptr, *d_gout = nullptr;
+  double *d_ga = nullptr, *d_gw = nullptr, *d_gv = nullptr, *d_gout = nullptr;
   auto carve_grad = [&](Arena& a) {
     d_ga = g_a_host ? a.get<double>(F) : const_cast<double*>(gr ? gr->g_energy : nullptr);
     d_gw = g_w_host ? a.get<double>(3L * N) : const_cast<double*>(gr ? gr->g_force : nullptr);
+    d_gv = g_v_host ? a.get<double>(9L * F) : const_cast<double*>(gr ? gr->g_virial : nullptr);
     d_gout = g_out_host ? a.get<double>(m.n_params) : (gr ? gr->grad : nullptr);
   };
   carve_grad(pre);
-  rc = gr ? run_param_grad(m, pc, io, nullptr, nullptr, -1.0, nullptr, pre, st) : run_path(m, pc, io, pre, st);
+  rc = gr ? run_param_grad(m, pc, io, nullptr, nullptr, nullptr, -1.0, nullptr, pre, st) : run_path(m, pc, io, pre, st);
   if (rc != DP_OK) return rc;
   rc = ensure_ws(md, pre.used);
   if (rc == DP_OK) rc = ensure_stage(md, T.bytes);
@@ -395,6 +398,7 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     if (copy_type) DP_CUDA_TRY(cudaMemcpyAsync(b.type, type, sizeof(int) * N, cudaMemcpyHostToDevice, s));
     if (g_a_host) DP_CUDA_TRY(cudaMemcpyAsync(d_ga, gr->g_energy, sizeof(double) * F, cudaMemcpyHostToDevice, s));
     if (g_w_host) DP_CUDA_TRY(cudaMemcpyAsync(d_gw, gr->g_force, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    if (g_v_host) DP_CUDA_TRY(cudaMemcpyAsync(d_gv, gr->g_virial, sizeof(double) * 9 * F, cudaMemcpyHostToDevice, s));
     T.pack(stage);
     DP_CUDA_TRY(cudaMemcpyAsync(b.ftab, stage, T.bytes, cudaMemcpyHostToDevice, s));
     const NlGeom* d_geoms = reinterpret_cast<const NlGeom*>(b.ftab + T.off_geoms);
@@ -460,7 +464,7 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
     if (gr) {
       {
         ProfScope _ps(&md->prof, "param_grad", s);
-        int r = run_param_grad(m, pc, io, d_gw, d_ga, -1.0, d_gout, ar, s);
+        int r = run_param_grad(m, pc, io, d_gw, d_ga, d_gv, -1.0, d_gout, ar, s);
         if (r != DP_OK) return r;
       }
       if (g_out_host)
@@ -622,7 +626,8 @@ int dp_compute_batch(dp_model* md, int nframes, const int* natoms, const double*
 }
 
 int dp_param_grad(dp_model* md, int nframes, const int* natoms, const double* coord, const int* type,
-                  const double* boxes, const double* g_energy, const double* g_force, double* grad, void* stream) {
+                  const double* boxes, const double* g_energy, const double* g_force, const double* g_virial,
+                  double* grad, void* stream) {
   if (!md || nframes < 1 || !natoms || !coord || !type || !g_energy || !g_force || !grad) {
     set_error("invalid argument");
     return DP_E_ARG;
@@ -631,7 +636,11 @@ int dp_param_grad(dp_model* md, int nframes, const int* natoms, const double* co
     set_error("batches of frames need periodic cells");
     return DP_E_UNSUPPORTED;
   }
-  const GradReq gr{g_energy, g_force, grad};
+  if (g_virial && !boxes) {
+    set_error("a virial seed needs periodic cells");
+    return DP_E_ARG;
+  }
+  const GradReq gr{g_energy, g_force, g_virial, grad};
   return run_frames(md, nullptr, nframes, natoms, coord, type, boxes, nullptr, nullptr, nullptr, nullptr,
                     (cudaStream_t)stream, &gr);
 }

@@ -39,8 +39,8 @@ inline int net_index(const PathConst& pc, int ti, int tj) { return pc.type_one_s
 // ---- pair geometry and its tangent along w -----------------------------------------------------
 template <class R>
 __global__ void k_env_tan(PathConst pc, const double* __restrict__ coord, const double* __restrict__ w,
-                          const int* __restrict__ perm, const int* __restrict__ nl_j, const int* __restrict__ nl_code,
-                          R* __restrict__ Renv, R* __restrict__ Rdot) {
+                          const double* __restrict__ gv, const int* __restrict__ perm, const int* __restrict__ nl_j,
+                          const int* __restrict__ nl_code, R* __restrict__ Renv, R* __restrict__ Rdot) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= (long)pc.natoms * pc.nc) return;
   const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
@@ -52,8 +52,17 @@ __global__ void k_env_tan(PathConst pc, const double* __restrict__ coord, const 
     listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d0, d1, d2);
     R r, s, ds, u[3];
     pair_env<R>(d0, d1, d2, norm2_exact(d0, d1, d2), pc.rs, pc.rc, pc.near2, r, s, ds, u);
-    // dd = w_j - w_i; dr = u . dd; du = (dd - dr u) / r; ds/de = s' dr
-    const R dd[3] = {R(w[3 * j] - w[3 * i]), R(w[3 * j + 1] - w[3 * i + 1]), R(w[3 * j + 2] - w[3 * i + 2])};
+    // dd = (w_j - w_i) + g_f r_ij (the virial seed of the frame: sum_ab g_ab Xi_ab is minus the
+    // derivative of E along the homogeneous deformation r_ij -> r_ij + g r_ij); dr = u . dd;
+    // du = (dd - dr u) / r; ds/de = s' dr
+    double e0 = w[3 * j] - w[3 * i], e1 = w[3 * j + 1] - w[3 * i + 1], e2 = w[3 * j + 2] - w[3 * i + 2];
+    if (gv) {
+      const double* g = gv + 9L * frame_of(pc, i);
+      e0 += g[0] * d0 + g[1] * d1 + g[2] * d2;
+      e1 += g[3] * d0 + g[4] * d1 + g[5] * d2;
+      e2 += g[6] * d0 + g[7] * d1 + g[8] * d2;
+    }
+    const R dd[3] = {R(e0), R(e1), R(e2)};
     const R dr = u[0] * dd[0] + u[1] * dd[1] + u[2] * dd[2];
     const R sd = ds * dr;
     o[0] = s;
@@ -435,7 +444,7 @@ void launch_wgrad(const RowMap& rm, const R* X, const R* Xd, int n_in, const R* 
 
 template <class R>
 int run_grad(const DeviceModel& m, const PathConst& pc, const R* params, const PathIO& io, const double* w_dev,
-             const double* a_dev, double b, Arena& ar, cudaStream_t st, R** grad_out) {
+             const double* a_dev, const double* gv_dev, double b, Arena& ar, cudaStream_t st, R** grad_out) {
   const long N = pc.natoms, nc = pc.nc, rows = N * nc;
   const int M = pc.M, A = pc.A, ne = m.cfg.n_embed, nfl = m.n_fit_layers, nt = pc.ntypes;
   // ---- scratch ----
@@ -489,7 +498,8 @@ int run_grad(const DeviceModel& m, const PathConst& pc, const R* params, const P
   // ---- forward: primal and tangent ----
   {
     ProfScope _ps(io.prof, "grad_env", st);
-    k_env_tan<R><<<nb(rows, 256), 256, 0, st>>>(pc, io.coord, w_dev, io.perm, io.nl_j, io.nl_code, Renv, Rdot);
+    k_env_tan<R><<<nb(rows, 256), 256, 0, st>>>(pc, io.coord, w_dev, gv_dev, io.perm, io.nl_j, io.nl_code, Renv,
+                                                 Rdot);
   }
   NetPtrs<R> nets;
   NetOffsets off;
@@ -618,20 +628,20 @@ int run_grad(const DeviceModel& m, const PathConst& pc, const R* params, const P
 }
 
 int run_param_grad(const DeviceModel& m, const PathConst& pc, const PathIO& io, const double* w_dev,
-                   const double* a_dev, double b, double* grad, Arena& ar, cudaStream_t st) {
+                   const double* a_dev, const double* gv_dev, double b, double* grad, Arena& ar, cudaStream_t st) {
   if (m.compressed || (m.precision != DP_PREC_FP64 && m.precision != DP_PREC_FP32)) {
     set_error("parameter gradients need an uncompressed FP64 or FP32 model");
     return DP_E_UNSUPPORTED;
   }
   if (m.precision == DP_PREC_FP64) {
     double* g = nullptr;
-    const int rc = run_grad<double>(m, pc, m.p64, io, w_dev, a_dev, b, ar, st, &g);
+    const int rc = run_grad<double>(m, pc, m.p64, io, w_dev, a_dev, gv_dev, b, ar, st, &g);
     if (rc != DP_OK || ar.measure) return rc;
     DP_CUDA_TRY(cudaMemcpyAsync(grad, g, sizeof(double) * m.n_params, cudaMemcpyDeviceToDevice, st));
     return DP_OK;
   }
   float* g = nullptr;
-  const int rc = run_grad<float>(m, pc, m.p32, io, w_dev, a_dev, b, ar, st, &g);
+  const int rc = run_grad<float>(m, pc, m.p32, io, w_dev, a_dev, gv_dev, b, ar, st, &g);
   if (rc != DP_OK || ar.measure) return rc;
   k_to_double<float><<<nb(m.n_params, 256), 256, 0, st>>>(g, m.n_params, grad);
   DP_CUDA_TRY(cudaGetLastError());

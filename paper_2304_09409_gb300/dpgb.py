@@ -340,14 +340,16 @@ def compute_batch(model: "Model", natoms, coord, atype, boxes, atom_energy: bool
     return e, f, v, ae
 
 
-def param_grad(model: "Model", natoms, coord, atype, boxes, g_energy, g_force, stream=None, out=None):
-    """dp_param_grad: d/dtheta [sum_f g_energy[f] E_f + sum_i g_force[i] . F_i] for the model's
-    current parameters.  natoms int32 [F]; coord [N, 3] and atype [N] (numpy or torch CUDA);
-    boxes [F, 3, 3] numpy, or None for one open-boundary frame; g_energy [F], g_force [N, 3].
-    Returns [n_params] FP64 (a torch CUDA tensor when coord is one, else numpy)."""
+def param_grad(model: "Model", natoms, coord, atype, boxes, g_energy, g_force, stream=None, out=None,
+               g_virial=None):
+    """dp_param_grad: d/dtheta [sum_f g_energy[f] E_f + sum_i g_force[i] . F_i + sum_f g_virial[f] : Xi_f]
+    for the model's current parameters.  natoms int32 [F]; coord [N, 3] and atype [N] (numpy or
+    torch CUDA); boxes [F, 3, 3] numpy, or None for one open-boundary frame; g_energy [F],
+    g_force [N, 3], g_virial [F, 3, 3] or None.  Returns [n_params] FP64 (a torch CUDA tensor
+    when coord is one, else numpy)."""
     L = lib()
     vp = ctypes.c_void_p
-    L.dp_param_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.dp_param_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     nat = np.ascontiguousarray(natoms, dtype=np.int32)
     F = int(nat.size)
     bx = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64).reshape(F, 9)
@@ -356,15 +358,19 @@ def param_grad(model: "Model", natoms, coord, atype, boxes, g_energy, g_force, s
         import torch
         g_energy = torch.as_tensor(g_energy, dtype=torch.float64, device=coord.device).contiguous()
         g_force = torch.as_tensor(g_force, dtype=torch.float64, device=coord.device).contiguous()
+        if g_virial is not None:
+            g_virial = torch.as_tensor(g_virial, dtype=torch.float64, device=coord.device).reshape(F, 9).contiguous()
         grad = out if out is not None else torch.empty(npar, dtype=torch.float64, device=coord.device)
     else:
         coord = np.ascontiguousarray(coord, dtype=np.float64)
         atype = np.ascontiguousarray(atype, dtype=np.int32)
         g_energy = np.ascontiguousarray(g_energy, dtype=np.float64)
         g_force = np.ascontiguousarray(g_force, dtype=np.float64)
+        if g_virial is not None:
+            g_virial = np.ascontiguousarray(g_virial, dtype=np.float64).reshape(F, 9)
         grad = out if out is not None else np.zeros(npar)
     _check(L.dp_param_grad(model.handle, F, nat.ctypes.data, _ptr(coord), _ptr(atype), _ptr(bx), _ptr(g_energy),
-                           _ptr(g_force), _ptr(grad), _stream_handle(stream)))
+                           _ptr(g_force), _ptr(g_virial), _ptr(grad), _stream_handle(stream)))
     return grad
 
 

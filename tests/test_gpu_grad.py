@@ -213,3 +213,83 @@ def test_grad_rejects_compressed_and_bad_sizes():
     m = dpgb.Model(cfg, p, precision="fp64")
     with pytest.raises(dpgb.DPError):
         m.set_params(p[:-1])
+
+
+def _targets_v(cfg, q, frames):
+    e, f, v = [], [], []
+    for fr in frames:
+        r = oracle.compute(cfg, q, fr.coord, fr.atype, fr.box)
+        e.append(r.energy)
+        f.append(r.force)
+        v.append(r.virial)
+    return np.array(e), f, np.array(v)
+
+
+@pytest.mark.parametrize("one_side", [0, 1])
+def test_grad_fp64_virial_term_matches_oracle(one_side):
+    """The virial term of Eq. (loss): dp_param_grad with a virial cotangent (FP64) against the
+    oracle's exact hyper-dual derivative, virial alone and with the energy and force terms."""
+    from paper_2304_09409_gb300 import dpgb
+    cfg = tiny_model(one_side)
+    p, q = I.make_params(cfg, 5), I.make_params(cfg, 6)
+    frames = [tiny_frame(seed=s) for s in (3, 4, 7)]
+    e_ref, f_ref, v_ref = _targets_v(cfg, q, frames)
+    m = dpgb.Model(cfg, p, precision="fp64")
+    nat, coord, atype, boxes = _pack(frames)
+    e, f, v, _ = dpgb.compute_batch(m, nat, coord, atype, boxes)
+    B = len(frames)
+    fref = np.concatenate(f_ref)
+    per_n = np.repeat(nat, nat).astype(np.float64)[:, None]
+    for pE, pF, pV in ((0.0, 0.0, 1.0), (0.3, 2.0, 0.7)):
+        g_e = 2 * pE * (e - e_ref) / (nat * B)
+        g_f = 2 * pF * (f - fref) / (3 * per_n * B)
+        g_v = 2 * pV * (v - v_ref) / (9 * nat[:, None, None] * B)
+        g = dpgb.param_grad(m, nat, coord, atype, boxes, g_e, g_f, g_virial=g_v)
+        for d in _directions(cfg, p.size, 31):
+            L_o, dL_o = oracle.loss_dir(cfg, p, d, frames, e_ref, f_ref, pE, pF, pV, v_ref)
+            assert abs(g @ d - dL_o) <= 1e-9 * max(abs(dL_o), 1e-6 * abs(L_o)), (pE, pF, pV, g @ d, dL_o)
+
+
+def test_trainer_with_virial_and_schedules():
+    """Eq. (loss) with all three terms through the autograd Function (its gradient equal to the
+    C ABI's), Eq. (learning_rate) and the prefactor schedule, and FP32 Adam steps that lower the
+    loss."""
+    from paper_2304_09409_gb300 import dpgb
+    from paper_2304_09409_gb300.autograd import DPForce, Schedule, Trainer, efv_loss, learning_rate, prefactor
+    cfg, frames = _c3_batch(4)
+    p, q = I.make_params(cfg, 0), I.make_params(cfg, 1)
+    nat, coord, atype, boxes = _pack(frames)
+    dev = "cuda"
+    coord_t, atype_t = torch.tensor(coord, device=dev), torch.tensor(atype, device=dev)
+    ref = dpgb.Model(cfg, q, precision="fp64")
+    e_ref, f_ref, v_ref, _ = dpgb.compute_batch(ref, nat, coord_t, atype_t, boxes)
+    m = dpgb.Model(cfg, p, precision="fp64")
+    params = torch.tensor(p, device=dev, requires_grad=True)
+    e, f, v = DPForce.apply(params, m, nat, coord_t, atype_t, boxes)
+    L = efv_loss(e, f, v, e_ref, f_ref, v_ref, nat, 0.02, 1.0, 0.5)
+    L.backward()
+    B = len(frames)
+    per_n = torch.tensor(np.repeat(nat, nat).astype(np.float64), device=dev)[:, None]
+    nat_t = torch.tensor(nat.astype(np.float64), device=dev)
+    g_e = 2 * 0.02 * (e.detach() - e_ref) / (nat_t * B)
+    g_f = 2 * (f.detach() - f_ref) / (3 * per_n * B)
+    g_v = 2 * 0.5 * (v.detach() - v_ref) / (9 * nat_t[:, None, None] * B)
+    g = dpgb.param_grad(m, nat, coord_t, atype_t, boxes, g_e, g_f, g_virial=g_v)
+    assert torch.allclose(params.grad, g, rtol=1e-10, atol=1e-12 * float(g.abs().max()))
+    # the schedules of Sec. II.B
+    assert learning_rate(0, 1e-3, 1e-5, 1000, 100) == pytest.approx(1e-3)
+    assert learning_rate(1000, 1e-3, 1e-5, 1000, 100) == pytest.approx(1e-5, rel=1e-9)
+    assert learning_rate(150, 1e-3, 1e-5, 1000, 100) == pytest.approx(1e-3 * (1e-2) ** 0.1, rel=1e-9)
+    assert prefactor(1e-3, 1e-3, 0.02, 1.0) == pytest.approx(0.02)
+    assert prefactor(0.0, 1e-3, 0.02, 1.0) == pytest.approx(1.0)
+    sched = Schedule(lr0=1e-3, lr_stop=1e-4, stop_steps=8, decay_steps=2, pE=(0.02, 1.0), pF=(1.0, 1.0),
+                     pV=(0.5, 0.1))
+    m32 = dpgb.Model(cfg, p, precision="fp32")
+    tr = Trainer(m32, p, schedule=sched)
+    fixed = (0.02, 1.0, 0.5)  # the prefactors move with the schedule: compare at fixed ones
+    L0 = float(tr.loss(nat, coord_t, atype_t, boxes, e_ref, f_ref, v_ref, pref=fixed).detach())
+    for _ in range(6):
+        tr.step(nat, coord_t, atype_t, boxes, e_ref, f_ref, v_ref)
+    assert tr.opt.param_groups[0]["lr"] == pytest.approx(learning_rate(5, 1e-3, 1e-4, 8, 2))
+    L1 = float(tr.loss(nat, coord_t, atype_t, boxes, e_ref, f_ref, v_ref, pref=fixed).detach())
+    assert L1 < L0, (L0, L1)

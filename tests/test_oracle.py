@@ -475,13 +475,15 @@ def test_compressed_forces_vs_dual_of_compressed_energy():
         assert r.force[i, a] == pytest.approx(-(ep - em) / (2 * h), abs=2e-7)
 
 
-def _loss_from_compute(cfg, p, frames, e_ref, f_ref, pE, pF):
-    """The Sec. II.B loss evaluated from the oracle's plain energy/force results."""
+def _loss_from_compute(cfg, p, frames, e_ref, f_ref, pE, pF, pV=0.0, v_ref=None):
+    """The Sec. II.B loss (Eq. (loss)) evaluated from the oracle's plain energy/force/virial results."""
     L = 0.0
-    for fr, er, fref in zip(frames, e_ref, f_ref):
+    for k, (fr, er, fref) in enumerate(zip(frames, e_ref, f_ref)):
         r = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
         n = fr.natoms
         L += pE * (r.energy - er) ** 2 / n + pF * float(((r.force - fref) ** 2).sum()) / (3 * n)
+        if v_ref is not None:
+            L += pV * float(((r.virial - v_ref[k]) ** 2).sum()) / (9 * n)
     return L / len(frames)
 
 
@@ -643,3 +645,33 @@ def test_force_subset_equals_full_oracle(case):
     fs = np.abs(full.force).max()
     np.testing.assert_allclose(f, full.force[idx], rtol=0, atol=1e-12 * fs)
     np.testing.assert_allclose(e, full.atom_energy[idx], rtol=1e-13, atol=1e-13)
+
+
+def test_loss_direction_derivative_with_virial_term():
+    """The virial term of Eq. (loss): its hyper-dual derivative (a homogeneous deformation in the
+    e1 direction) against central differences of the loss computed from plain oracle energies,
+    forces and virials, alone and together with the energy and force terms."""
+    cfg = tiny_model()
+    p = I.make_params(cfg, 5)
+    frames = [tiny_frame(seed=s) for s in (3, 4)]
+    q = I.make_params(cfg, 6)
+    e_ref, f_ref, v_ref = [], [], []
+    for fr in frames:
+        r = oracle.compute(cfg, q, fr.coord, fr.atype, fr.box)
+        e_ref.append(r.energy)
+        f_ref.append(r.force)
+        v_ref.append(r.virial)
+    e_ref, v_ref = np.array(e_ref), np.array(v_ref)
+    rng = I.Rng(23)
+    n = p.size
+    n_emb = sum(a * b + b for a, b in cfg.embed_layer_shapes()) * cfg.n_embed_nets
+    dirs = [rng.normal(n), np.r_[rng.normal(n_emb), np.zeros(n - n_emb)], np.r_[np.zeros(n_emb), rng.normal(n - n_emb)]]
+    for pE, pF, pV in ((0.0, 0.0, 1.0), (0.3, 2.0, 0.7)):
+        L0 = _loss_from_compute(cfg, p, frames, e_ref, f_ref, pE, pF, pV, v_ref)
+        for v in dirs:
+            L, dL = oracle.loss_dir(cfg, p, v, frames, e_ref, f_ref, pE, pF, pV, v_ref)
+            assert abs(L - L0) <= 1e-12 * max(1.0, abs(L0))
+            h = 1e-5
+            fd = (_loss_from_compute(cfg, p + h * v, frames, e_ref, f_ref, pE, pF, pV, v_ref)
+                  - _loss_from_compute(cfg, p - h * v, frames, e_ref, f_ref, pE, pF, pV, v_ref)) / (2 * h)
+            assert abs(dL - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(L0)), (pE, pF, pV, dL, fd)
