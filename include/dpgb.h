@@ -184,18 +184,43 @@ long dp_launch_count(const dp_model* model);
  * 0 for scopes whose work is a fixed function of the sizes.  DP_E_ARG for a bad index. */
 int dp_profile_work(const dp_model* model, int k, double* flop);
 
-/* Energies, forces and virials of several frames of one model in one pass (serving).
- * The frames keep their own periodic cells and atom counts; their atoms are concatenated.
+/* Energies, forces and virials of several frames, of one or several models, in one call
+ * (serving; the batching of frames of Sec. III.B).  The frames keep their own periodic cells and
+ * atom counts; their atoms are concatenated.  Consecutive frames of the same model are evaluated
+ * together by one pass of that model's kernels (frames of uneven size share every launch); the
+ * passes of the models follow each other in stream order.
+ *   models [nmodels] (host): the resident models, all on one device.
  *   natoms [nframes] (host): atoms of each frame, in order.
+ *   frame_model [nframes] (host): index into models of each frame (may be NULL when nmodels is 1).
  *   coord [sum(natoms)*3] FP64, type [sum(natoms)] int32: host or device, frames concatenated.
  *   boxes [nframes*9] (host): cell rows of every frame (periodic frames only).
  *   energy [nframes], force [sum(natoms)*3], virial [nframes*9], atom_energy [sum(natoms)] or
  *   NULL: host or device.
- * Each frame's result equals dp_compute on that frame alone up to the order of floating-point
- * accumulation.  Returns as dp_compute; DP_E_UNSUPPORTED for boxes == NULL. */
-int dp_compute_batch(dp_model* model, int nframes, const int* natoms, const double* coord, const int* type,
-                     const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
-                     void* stream);
+ * Each frame's result equals dp_compute of its model on that frame alone up to the order of
+ * floating-point accumulation.  Returns as dp_compute (the first error ends the call; the
+ * warnings DP_E_SEL_OVERFLOW / DP_E_RANGE are returned after all frames are done);
+ * DP_E_UNSUPPORTED for boxes == NULL. */
+int dp_compute_batch(dp_model** models, int nmodels, int nframes, const int* natoms, const int* frame_model,
+                     const double* coord, const int* type, const double* boxes, double* energy, double* force,
+                     double* virial, double* atom_energy, void* stream);
+
+/* ---- model deviation of an ensemble (Sec. II.C) ----
+ * The n_m = nmodels models (trained on the same data from independent initialisations) evaluate
+ * the same frame; their spread estimates the error of the model at that frame:
+ *   eps_F,i = sqrt(< |F_i(theta_k) - <F_i>|^2 >),   eps_Xi,ab = (1/N) sqrt(< (Xi_ab(theta_k) - <Xi_ab>)^2 >)
+ * with <.> the mean over the models.  nu > 0 selects the relative forms eps_F,i / (|<F_i>| + nu)
+ * and eps_Xi,ab / (|<Xi>| + nu) (|<Xi>| the Frobenius norm of the mean virial); nu = 0 the
+ * absolute ones.
+ *   models [nmodels >= 2] (host), all on one device; coord [natoms*3], type [natoms]: host or
+ *   device; box: host [9] or NULL (open boundaries).
+ *   devi_f [natoms] (eps_F,i), devi_v [9] (eps_Xi,ab row-major), force_mean [natoms*3] (<F_i>):
+ *   host or device, each may be NULL.  stats [6] (host or device): max, mean, min of eps_F,i over
+ *   the atoms, then max, mean, min of eps_Xi,ab over the nine components.
+ * Everything runs on the GPU in FP64 (the reductions in a fixed order); the models' own
+ * precision sets the accuracy of their forces.  Synchronises `stream`.  Returns as dp_compute. */
+int dp_model_deviation(dp_model** models, int nmodels, int natoms, const double* coord, const int* type,
+                       const double* box, double nu, double* devi_f, double* devi_v, double* stats,
+                       double* force_mean, void* stream);
 
 /* ---- training: parameter gradient of an energy + force + virial objective (Sec. II.B) ----
  * The loss of Sec. II.B (Eq. (loss)) weighs energy, force and virial errors (prefactors p_E,

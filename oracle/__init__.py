@@ -308,3 +308,25 @@ def loss_dir(cfg, params, vdir, frames, e_ref, f_ref, pE=1.0, pF=1.0, pV=0.0, v_
                           _i(atype), _d(boxes), _i(nj), _i(ns), _d(_f64(e_ref)), _d(_f64(np.concatenate(f_ref))),
                           float(pE), float(pF), ctypes.byref(dL), _d(vr), float(pV))
     return val, dL.value
+
+
+def model_deviation(cfg_params, coord, atype, box, nu: float = 0.0):
+    """Model deviation of an ensemble on one frame (Sec. II.C), from the oracle's forces and
+    virials of every model: eps_F,i = sqrt(<|F_i - <F_i>|^2>) and
+    eps_Xi,ab = (1/N) sqrt(<(Xi_ab - <Xi_ab>)^2>), <.> the ensemble mean; with nu > 0 the
+    relative forms eps_F,i / (|<F_i>| + nu) and eps_Xi,ab / (|<Xi>| + nu) (Frobenius norm).
+    cfg_params: [(cfg, params), ...].  Returns (devi_f [N], devi_v [3, 3], stats [6] =
+    (max, mean, min of eps_F,i, max, mean, min of eps_Xi,ab), force_mean [N, 3])."""
+    res = [compute(c, p, coord, atype, box) for c, p in cfg_params]
+    Fk = np.stack([r.force for r in res])      # [n_m, N, 3]
+    Vk = np.stack([r.virial for r in res])     # [n_m, 3, 3]
+    N = Fk.shape[1]
+    fm = Fk.mean(axis=0)
+    ef = np.sqrt(((Fk - fm[None]) ** 2).sum(axis=2).mean(axis=0))
+    vm = Vk.mean(axis=0)
+    ev = np.sqrt(((Vk - vm[None]) ** 2).mean(axis=0)) / N
+    if nu > 0.0:
+        ef = ef / (np.linalg.norm(fm, axis=1) + nu)
+        ev = ev / (np.linalg.norm(vm) + nu)
+    stats = np.array([ef.max(), ef.mean(), ef.min(), ev.max(), ev.mean(), ev.min()])
+    return ef, ev, stats, fm

@@ -614,15 +614,42 @@ int dp_compute(dp_model* md, dp_nlist* nlist, int N, const double* coord, const 
   return run_frames(md, nlist, 1, &N, coord, type, box, energy, force, virial, atom_energy, (cudaStream_t)stream);
 }
 
-int dp_compute_batch(dp_model* md, int nframes, const int* natoms, const double* coord, const int* type,
-                     const double* boxes, double* energy, double* force, double* virial, double* atom_energy,
-                     void* stream) {
-  if (!md || nframes < 1 || !natoms || !coord || !type || !boxes || !energy || !force || !virial) {
+int dp_compute_batch(dp_model** models, int nmodels, int nframes, const int* natoms, const int* frame_model,
+                     const double* coord, const int* type, const double* boxes, double* energy, double* force,
+                     double* virial, double* atom_energy, void* stream) {
+  if (!models || nmodels < 1 || nframes < 1 || !natoms || !coord || !type || !boxes || !energy || !force ||
+      !virial || (nmodels > 1 && !frame_model)) {
     set_error("invalid argument");
     return DP_E_ARG;
   }
-  return run_frames(md, nullptr, nframes, natoms, coord, type, boxes, energy, force, virial, atom_energy,
-                    (cudaStream_t)stream);
+  for (int k = 0; k < nmodels; ++k)
+    if (!models[k] || models[k]->m.device != models[0]->m.device) {
+      set_error("dp_compute_batch: every model must exist and live on the same device");
+      return DP_E_ARG;
+    }
+  for (int f = 0; f < nframes; ++f)
+    if (natoms[f] < 1 || (frame_model && (frame_model[f] < 0 || frame_model[f] >= nmodels))) {
+      set_error("dp_compute_batch: every frame needs at least one atom and a model index in [0, nmodels)");
+      return DP_E_ARG;
+    }
+  // consecutive frames of the same model run as one pass of that model's kernels, all in stream
+  // order; the first error ends the call, warnings (sel overflow, table range) are carried on
+  int warn = DP_OK;
+  long a0 = 0;
+  for (int f0 = 0; f0 < nframes;) {
+    const int k = frame_model ? frame_model[f0] : 0;
+    int f1 = f0 + 1;
+    long na = natoms[f0];
+    while (f1 < nframes && (frame_model ? frame_model[f1] : 0) == k) na += natoms[f1++];
+    const int rc = run_frames(models[k], nullptr, f1 - f0, natoms + f0, coord + 3 * a0, type + a0, boxes + 9L * f0,
+                              energy + f0, force + 3 * a0, virial + 9L * f0, atom_energy ? atom_energy + a0 : nullptr,
+                              (cudaStream_t)stream);
+    if (rc != DP_OK && rc != DP_E_SEL_OVERFLOW && rc != DP_E_RANGE) return rc;
+    if (rc != DP_OK && warn == DP_OK) warn = rc;
+    a0 += na;
+    f0 = f1;
+  }
+  return warn;
 }
 
 int dp_param_grad(dp_model* md, int nframes, const int* natoms, const double* coord, const int* type,

@@ -32,7 +32,7 @@ EXPORTED = [
     "dp_model_create", "dp_init_model", "dp_free_model", "dp_model_n_params", "dp_build_nlist",
     "dp_nlist_export", "dp_free_nlist", "dp_compute", "dp_model_export_table", "dp_last_error",
     "dp_build_nlist_noalloc", "dp_compute_batch", "dp_param_grad", "dp_model_set_params", "dp_wait_selftest",
-    "dp_profile_work",
+    "dp_profile_work", "dp_model_deviation",
 ]
 
 
@@ -188,6 +188,18 @@ class Model:
         self.device = device
         self.nc = int(sum(cfg.sel))
 
+    @classmethod
+    def from_file(cls, path: str, cfg, device: int = 0, precision: str = "fp64", compressed: bool = False):
+        """A model created by dp_init_model from a weight file (see write_weight_file); cfg is
+        the configuration the file holds (kept on the Python side for array shapes)."""
+        self = cls.__new__(cls)
+        self.cfg = cfg
+        self.c = Config.from_model(cfg)
+        self.handle = load_model_file(path, device, precision, compressed)
+        self.device = device
+        self.nc = int(sum(cfg.sel))
+        return self
+
     def free(self):
         if getattr(self, "handle", None):
             lib().dp_free_model(self.handle)
@@ -302,20 +314,26 @@ class Model:
 def _batch_argtypes():
     L = lib()
     vp = ctypes.c_void_p
-    L.dp_compute_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.dp_compute_batch.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     return L
 
 
-def compute_batch(model: "Model", natoms, coord, atype, boxes, atom_energy: bool = False, stream=None, out=None,
-                  allow=(DP_E_SEL_OVERFLOW,)):
-    """dp_compute_batch: several frames of one model in one pass.
+def compute_batch(model, natoms, coord, atype, boxes, atom_energy: bool = False, stream=None, out=None,
+                  allow=(DP_E_SEL_OVERFLOW,), frame_model=None):
+    """dp_compute_batch: several frames, of one model or of several, in one call.
 
+    model: a Model, or a list of Models with frame_model [F] (the index of each frame's model);
     natoms: int32 array [F]; coord [sum(natoms), 3], atype [sum(natoms)] (numpy or torch CUDA);
     boxes [F, 3, 3] numpy.  Returns (energy [F], force [sum, 3], virial [F, 3, 3], atom_energy)."""
     L = _batch_argtypes()
+    models = list(model) if isinstance(model, (list, tuple)) else [model]
+    handles = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
     nat = np.ascontiguousarray(natoms, dtype=np.int32)
     F = int(nat.size)
     N = int(nat.sum())
+    fm = None if frame_model is None else np.ascontiguousarray(frame_model, dtype=np.int32)
+    if len(models) > 1 and fm is None:
+        raise ValueError("several models need frame_model")
     bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(F, 9)
     if _is_torch(coord) and coord.is_cuda:
         import torch
@@ -334,10 +352,36 @@ def compute_batch(model: "Model", natoms, coord, atype, boxes, atom_energy: bool
             ae = np.zeros(N) if atom_energy else None
         else:
             e, f, v, ae = out
-    code = L.dp_compute_batch(model.handle, F, nat.ctypes.data, _ptr(coord), _ptr(atype), bx.ctypes.data, _ptr(e),
-                              _ptr(f), _ptr(v), _ptr(ae), _stream_handle(stream))
+    code = L.dp_compute_batch(handles, len(models), F, nat.ctypes.data, None if fm is None else fm.ctypes.data,
+                              _ptr(coord), _ptr(atype), bx.ctypes.data, _ptr(e), _ptr(f), _ptr(v), _ptr(ae),
+                              _stream_handle(stream))
     _check(code, allow=allow)
     return e, f, v, ae
+
+
+def model_deviation(models, coord, atype, box, nu: float = 0.0, stream=None):
+    """dp_model_deviation: (devi_f [N], devi_v [3, 3], stats [6], force_mean [N, 3]) of an ensemble on
+    one frame; stats = (eps_F max, mean, min, eps_Xi max, mean, min).  Arrays come back as
+    torch CUDA tensors when coord is one, else numpy."""
+    L = lib()
+    vp = ctypes.c_void_p
+    L.dp_model_deviation.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp]
+    handles = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    if _is_torch(coord) and coord.is_cuda:
+        import torch
+        N = int(coord.shape[0])
+        mk = lambda *s: torch.empty(s, dtype=torch.float64, device=coord.device)  # noqa: E731
+        df, dv, st, fm = mk(N), mk(3, 3), mk(6), mk(N, 3)
+    else:
+        coord = np.ascontiguousarray(coord, dtype=np.float64)
+        atype = np.ascontiguousarray(atype, dtype=np.int32)
+        N = int(coord.shape[0])
+        df, dv, st, fm = np.zeros(N), np.zeros((3, 3)), np.zeros(6), np.zeros((N, 3))
+    _check(L.dp_model_deviation(handles, len(models), N, _ptr(coord), _ptr(atype), None if bx is None else bx.ctypes.data,
+                                float(nu), _ptr(df), _ptr(dv), _ptr(st), _ptr(fm), _stream_handle(stream)),
+           allow=(DP_E_SEL_OVERFLOW,))
+    return df, dv, st, fm
 
 
 def param_grad(model: "Model", natoms, coord, atype, boxes, g_energy, g_force, stream=None, out=None,

@@ -675,3 +675,32 @@ def test_loss_direction_derivative_with_virial_term():
             fd = (_loss_from_compute(cfg, p + h * v, frames, e_ref, f_ref, pE, pF, pV, v_ref)
                   - _loss_from_compute(cfg, p - h * v, frames, e_ref, f_ref, pE, pF, pV, v_ref)) / (2 * h)
             assert abs(dL - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(L0)), (pE, pF, pV, dL, fd)
+
+
+# ----------------------------------------------------------------------------------------
+# Model deviation (Sec. II.C)
+# ----------------------------------------------------------------------------------------
+
+
+def test_model_deviation_special_cases():
+    """Identical models deviate by zero; for two models the deviation of atom i is exactly half
+    the distance between their forces, |F_i^1 - F_i^2| / 2 (and the virial one |Xi^1 - Xi^2| /(2N)),
+    and the statistics are the largest, mean and smallest of those; the relative form divides by
+    |<F_i>| + nu."""
+    cfg, fr = tiny_model(), tiny_frame(seed=5)
+    p1, p2 = I.make_params(cfg, 1), I.make_params(cfg, 2)
+    ef, ev, st, fm = oracle.model_deviation([(cfg, p1), (cfg, p1), (cfg, p1)], fr.coord, fr.atype, fr.box)
+    a = oracle.compute(cfg, p1, fr.coord, fr.atype, fr.box)
+    scale = np.abs(a.force).max()  # zero up to the rounding of a mean of equal values
+    assert np.abs(ef).max() <= 1e-15 * scale and np.abs(st).max() <= 1e-15 * scale
+    assert np.abs(ev).max() <= 1e-15 * np.abs(a.virial).max() / fr.natoms
+    b = oracle.compute(cfg, p2, fr.coord, fr.atype, fr.box)
+    ef, ev, st, fm = oracle.model_deviation([(cfg, p1), (cfg, p2)], fr.coord, fr.atype, fr.box)
+    half = np.linalg.norm(a.force - b.force, axis=1) / 2
+    np.testing.assert_allclose(ef, half, rtol=1e-12)
+    np.testing.assert_allclose(ev, np.abs(a.virial - b.virial) / (2 * fr.natoms), rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(fm, (a.force + b.force) / 2, rtol=1e-12)
+    assert st[0] == half.max() and st[2] == half.min() and st[1] == pytest.approx(half.mean(), rel=1e-12)
+    nu = 0.1
+    er, _, _, _ = oracle.model_deviation([(cfg, p1), (cfg, p2)], fr.coord, fr.atype, fr.box, nu=nu)
+    np.testing.assert_allclose(er, half / (np.linalg.norm((a.force + b.force) / 2, axis=1) + nu), rtol=1e-12)
