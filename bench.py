@@ -382,11 +382,13 @@ def time_path(model, coord, atype, box, steps, warmup, flush, profile=False):
     return total / steps, launches, prof, out
 
 
-def run_serving(n_frames=3000, rate=2000.0, slots=3, max_batch_atoms=65536, precision="fp32", compressed=True):
+def run_serving(n_frames=3000, rate=2000.0, slots=3, max_batch_atoms=65536, precision="fp32", compressed=True,
+                saturation_rate=50000.0, n_saturation=1500):
     """Continuous batching of a Poisson stream (mean `rate` frames/s) of water (24-3000 atoms)
     and FCC (108-19,652 atoms) frames, both force-scaled models resident, on the benchmark's
-    selected path; and the plain FP64 per-frame path on a sample of the same frames for
-    comparison."""
+    selected path; a second operating point offered far above capacity (`saturation_rate`),
+    whose throughput is the server's capacity; and the plain FP64 per-frame path on a sample of
+    the same frames for comparison."""
     import torch
     from paper_2304_09409_gb300 import dpgb, inputs as I, serve
     models = {"water": (I.water_model(), I.water_params_scaled(0)),
@@ -402,6 +404,16 @@ def run_serving(n_frames=3000, rate=2000.0, slots=3, max_batch_atoms=65536, prec
     reqs = serve.poisson_stream(water, fcc, n=n_frames, rate=rate, seed=1)
     st = srv.run(reqs, realtime=True)
     srv.close()
+    # saturation: offered load far above capacity, so batches form; throughput = capacity
+    srv = serve.Server(models, precision=precision, compressed=compressed, slots=slots, max_batch_atoms=max_batch_atoms)
+    for s in range(slots):
+        for name, pool in (("water", water), ("metal", fcc)):
+            big = max(pool, key=lambda f: f.natoms)
+            dpgb.compute_batch(srv.inst[s][name], [big.natoms], big.coord, big.atype, big.box[None])
+    torch.cuda.synchronize()
+    sat = srv.run(serve.poisson_stream(water, fcc, n=n_saturation, rate=saturation_rate, seed=2), realtime=True)
+    srv.close()
+    sat["offered_frames_per_s"] = saturation_rate
     # plain FP64 per-frame path (uncompressed networks, one dp_compute per frame) on a sample
     sample = [water[0], water[1], fcc[0], fcc[1]]
     f64 = {k: dpgb.Model(cfg, p, precision="fp64") for k, (cfg, p) in models.items()}
@@ -419,6 +431,9 @@ def run_serving(n_frames=3000, rate=2000.0, slots=3, max_batch_atoms=65536, prec
                "path": f"{precision}{'-compressed' if compressed else ''}",
                "fp64_per_frame_atom_evals_per_s": fp64_rate,
                "speedup_vs_fp64_per_frame": st["atom_evals_per_s"] / fp64_rate,
+               "saturation": sat,
+               "capacity_atom_evals_per_s": sat["atom_evals_per_s"],
+               "capacity_speedup_vs_fp64_per_frame": sat["atom_evals_per_s"] / fp64_rate,
                "fp64_sample": "2 water + 2 FCC frames of the pool, one dp_compute each"})
     return st
 
