@@ -56,8 +56,11 @@ extern "C" {
 #define DP_PREC_FP64 0 /* every step in FP64                                                 */
 #define DP_PREC_FP32 1 /* networks and contractions in FP32; FP64 for the pair distance, the
                           switch near r_c, the energy sum and the force/virial accumulation */
-#define DP_PREC_TF32 2 /* as FP32, with the embedding and fitting GEMMs on TF32 tensor cores */
-#define DP_PREC_BF16 3 /* as FP32, with the embedding and fitting GEMMs on BF16 tensor cores */
+#define DP_PREC_TF32 2 /* as FP32, with the embedding and fitting GEMMs on TF32 tensor cores (FP32
+                          accumulation); uncompressed models only                             */
+#define DP_PREC_BF16 3 /* as FP32, with the network GEMMs on BF16 tensor cores (FP32 accumulation):
+                          uncompressed, the embedding and fitting layers; compressed, the fitting
+                          net and the interval-moment contraction (FP16 operands)              */
 
 #define DP_MAX_TYPES 8
 #define DP_MAX_LAYERS 8

@@ -295,8 +295,15 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   m.M = cfg->embed[cfg->n_embed - 1];
   m.A = cfg->axis;
   m.n_embed_nets = cfg->type_one_side ? cfg->ntypes : cfg->ntypes * cfg->ntypes;
-  if (precision == DP_PREC_TF32 || (precision == DP_PREC_BF16 && !compressed)) {
-    set_error("this precision needs the compressed embedding (BF16) or is not available (TF32)");
+  if (precision == DP_PREC_TF32 && compressed) {
+    set_error("TF32 applies to the network GEMMs of the uncompressed model");
+    delete md;
+    return DP_E_UNSUPPORTED;
+  }
+  const bool tc_uncompressed = !compressed && (precision == DP_PREC_TF32 || precision == DP_PREC_BF16);
+  if (tc_uncompressed && !tc_uncompressed_supported(m)) {
+    set_error("tensor-core network GEMMs need widths <= 256, at most 8 (centre, neighbour) type pairs, "
+              "M * M_< a multiple of 16, two or more embedding layers and a hidden fitting layer");
     delete md;
     return DP_E_UNSUPPORTED;
   }
@@ -329,7 +336,14 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
     const LayerDesc& Lo = m.fit[(size_t)t * m.n_fit_layers + m.n_fit_layers - 1];
     m.fit_out_bias[t] = (float)params[Lo.w_off + Lo.n_in];
   }
-  if (precision == DP_PREC_BF16) {
+  if (tc_uncompressed) {
+    int rc = tc_uncompressed_prepare(m, params);
+    if (rc != DP_OK) {
+      dp_free_model(md);
+      return rc;
+    }
+  }
+  if (precision == DP_PREC_BF16 && compressed) {
     int rc = prepare_fit_bf16(m, params);
     if (rc != DP_OK) {
       dp_free_model(md);
@@ -489,6 +503,8 @@ int dp_free_model(dp_model* md) {
   cudaFree(md->m.fit_w_bf16);
   cudaFree(md->m.fit_wt_bf16_lo);
   cudaFree(md->m.fit_w_bf16_lo);
+  cudaFree(md->m.tc_wt);
+  cudaFree(md->m.tc_w);
   cudaFree(md->ws);
   cudaFree(md->status);
   if (md->status_host) cudaFreeHost(md->status_host);

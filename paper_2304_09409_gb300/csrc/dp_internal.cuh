@@ -113,6 +113,12 @@ struct DeviceModel {
   std::vector<long> fit_bf16_off;
   // tensor maps of those operands, keyed by (type, layer, direction, box rows)
   mutable std::vector<std::pair<long, std::vector<unsigned char>>> tmap_cache;
+  // uncompressed tensor-core path (emb_tc.cu): per layer, forward W^T [n_out][pad16(n_in)] and
+  // backward W [n_in][pad16(n_out)] operands in BF16 or FP32 (TF32 mode); embedding layers l >= 1
+  // of every net, then the hidden fitting layers of every type, at tc_off
+  void* tc_wt = nullptr;
+  void* tc_w = nullptr;
+  std::vector<long> tc_off;
   // interval-moment operands of the compressed embedding on the tensor cores (mom.cu)
   int mom_npass = 0;  // 0 none; 1 FP16 single pass; 3 BF16 high/low, three passes
   int mom_npad = 0, mom_lcp = 0;

@@ -220,4 +220,10 @@ template <class R>
 int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, const PathIO& io, Arena& ar,
                 cudaStream_t st);
 
+// Uncompressed path with the embedding and fitting GEMMs on the tensor cores (emb_tc.cu): BF16 or
+// TF32 operands by the model's precision.
+bool tc_uncompressed_supported(const DeviceModel& m);
+int tc_uncompressed_prepare(DeviceModel& m, const double* params_host);
+int run_tc_uncompressed(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& ar, cudaStream_t st);
+
 }  // namespace dpgb

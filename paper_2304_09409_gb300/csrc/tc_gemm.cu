@@ -368,6 +368,32 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int
   return DP_OK;
 }
 
+int make_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, long rows, long cols, int box_cols,
+                 int box_rows) {
+  if (!g_encode) {  // load the encoder (a map of a dummy aligned address; nothing is accessed)
+    CUtensorMap tmp;
+    if (make_tmap_bf16(&tmp, reinterpret_cast<const void*>(uintptr_t(256)), 1, 64, 1) != DP_OK || !g_encode)
+      return DP_E_CUDA;
+  }
+  if ((cols * elem_bytes) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || box_rows < 1 ||
+      box_rows > 256 || box_cols * elem_bytes != 128) {
+    set_error("tensor map: 16-byte aligned base and row pitch, 128-byte box rows, box rows in [1, 256]");
+    return DP_E_UNSUPPORTED;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * elem_bytes)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return DP_E_CUDA;
+  }
+  return DP_OK;
+}
+
 int tc_pick_bn(int N, int row_tiles) {
   int bn = ((N + 31) / 32) * 32;
   if (bn > 256) bn = 256;

@@ -59,6 +59,10 @@ struct TcLo {
 
 // Tensor map of a row-major [rows][cols] BF16 matrix, 128-byte swizzle, box {64, box_rows}.
 int make_tmap_bf16(CUtensorMap* map, const void* base, long rows, long cols, int box_rows);
+// Tensor map of a row-major [rows][cols] matrix of elem_bytes (2: BF16, 4: FP32) elements,
+// 128-byte swizzle, box {box_cols, box_rows} with box_cols * elem_bytes = 128.
+int make_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, long rows, long cols, int box_cols,
+                 int box_rows);
 // Tensor map of a row-major [rows][cols] FP32 matrix, 128-byte swizzle, box {32, 128}.
 int make_tmap_f32(CUtensorMap* map, const void* base, long rows, long cols);
 
