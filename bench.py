@@ -333,9 +333,13 @@ def run_fcc(local, flush, steps=5, warmup=3):
                        "embedding 32/64/128, axis 16, fitting 2048 -> 240x3, output layer scaled to ~1 eV/A RMS",
            "natoms": fr.natoms, "force_rms": frms,
            "paths": {"fp64": {"ms_per_step": ms64, "atom_evals_per_s": fr.natoms / (ms64 * 1e-3)}}}
-    for name, prec, comp in (("fp32-compressed", "fp32", True), ("bf16-compressed", "bf16", True)):
+    # the precision sweep: network GEMMs in FP64 (above), TF32 and BF16 on the tensor cores (uncompressed),
+    # and the compressed paths
+    for name, prec, comp in (("tf32", "tf32", False), ("bf16", "bf16", False), ("fp32-compressed", "fp32", True),
+                             ("bf16-compressed", "bf16", True)):
         m = dpgb.Model(cfg, params, device=local, precision=prec, compressed=comp)
-        ms, launches, _, out = time_path(m, coord, atype, fr.box, steps=steps, warmup=warmup, flush=flush)
+        st_, wu_ = (2, 1) if not comp else (steps, warmup)
+        ms, launches, _, out = time_path(m, coord, atype, fr.box, steps=st_, warmup=wu_, flush=flush)
         err = float(np.abs(out[1].cpu().numpy() - f64).max())
         res["paths"][name] = {"ms_per_step": ms, "atom_evals_per_s": fr.natoms / (ms * 1e-3),
                               "force_err_vs_fp64_gpu": err, "force_err_rel_rms": err / frms,
@@ -529,8 +533,8 @@ def run_ours(args):
 
     # every precision path on the force-scaled model: the fastest within the bar is measured
     cands = {}
-    for name, prec, comp in (("fp32", "fp32", False), ("fp32-compressed", "fp32", True),
-                             ("bf16-compressed", "bf16", True)):
+    for name, prec, comp in (("fp32", "fp32", False), ("tf32", "tf32", False), ("bf16", "bf16", False),
+                             ("fp32-compressed", "fp32", True), ("bf16-compressed", "bf16", True)):
         m = dpgb.Model(cfg, params, device=local, precision=prec, compressed=comp)
         ms, _, _, out = time_path(m, coord, atype, big.box, steps=3, warmup=3, flush=flush)
         err = float(np.abs(out[1].cpu().numpy() - f64).max())

@@ -1,0 +1,481 @@
+// The whole fitting net of the FP32 mode -- forward to E_i and backward to dE/dD -- in one tcgen05
+// kernel per 128-atom tile, on split BF16 operands (x = hi + lo, every product formed as
+// hi.hi + hi.lo + lo.hi: about 16 significant bits per operand, FP32 accumulation), Eq.
+// (fitting_energy) with the layers of Eq. (NN).
+//
+// Per tile the CTA runs the chain of GEMMs of the net: forward layers z_l = y_{l-1} W_l + b_l,
+// t_l = tanh z_l, y_l = t_l (+ y_{l-1}), E = y_last . w + b; backward gz_last = w (1 - t_last^2),
+// gy_{l-1} = gz_l W_l^T (+ gy_l), gz_{l-1} = gy_{l-1} (1 - t_{l-1}^2), dE/dD = gz_0 W_0^T.  Each GEMM
+// streams its A operand (the descriptor, or the previous phase's activations) and its weights
+// through one two-stage TMA ring of high and low halves (96 KB a stage); the accumulator lives in
+// tensor memory.  Activations go from each epilogue to the next phase through a per-tile scratch
+// that stays in L2 (high and low BF16 halves for the next A operand, FP32 for the skip and the
+// gates), so the shared memory holds only the ring; dE/dD leaves in 256-column chunks from two
+// alternating accumulators, so that one chunk's epilogue overlaps the next chunk's MMAs.  One
+// thread issues TMA, one issues tcgen05.mma, eight warps run the epilogues; every mbarrier wait
+// is bounded (on time-out the CTA records an error and finishes).
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "fit_tc.cuh"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace dpgb {
+
+namespace {
+
+using namespace ptx;
+
+constexpr int kSL = 4;  // hidden layers at most
+constexpr int kSEpi = 256;               // eight epilogue warps
+constexpr int kSThreads = kSEpi + 64;    // + a TMA producer warp and an MMA warp
+constexpr int SBM = 128, SBK = 64;
+constexpr int kSRing = 2;
+constexpr uint32_t kSA = SBM * SBK * 2;   // 16 KB: one 128 x 64 BF16 block of A
+constexpr uint32_t kSB = 256 * SBK * 2;   // 32 KB: up to 256 weight rows
+constexpr uint32_t kSStage = 2 * (kSA + kSB);  // [A hi | A lo | B hi | B lo]
+constexpr int kSLd = 256;  // row pitch of the activation scratch (elements)
+
+struct SplitMaps {
+  CUtensorMap d[2];                       // D hi / lo [rows][KD], box {64, 128}
+  CUtensorMap x[2][2];                    // activation scratch buffer b (hi / lo) [rows][kSLd], box {64, 128}
+  CUtensorMap w[DP_MAX_TYPES][2 * kSL][2];  // per type: forward W_l^T (slot l), backward W_l (slot nh + l); hi / lo
+};
+
+struct SplitArgs {
+  int ntypes, nh;
+  int width[kSL + 1];  // width[0] = KD, width[l + 1] = outputs of hidden layer l
+  int skip[kSL];
+  int row_start[DP_MAX_TYPES + 1];
+  int tile_start[DP_MAX_TYPES + 1];
+  const float* bias[DP_MAX_TYPES][kSL];
+  const float* w_last[DP_MAX_TYPES];
+  float b_last[DP_MAX_TYPES];
+  __nv_bfloat16* xs[2][2];  // activation scratch [2 buffers][hi, lo] [rows][kSLd]
+  float* gate;              // 1 - t_l^2 of the inner hidden layers [nh][rows][kSLd]
+  const int* perm;
+  double* atom_e;
+  float* gD;                // dE/dD FP32 [rows][KD]
+  int* err;
+};
+
+__device__ __forceinline__ void split2(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constant__ SplitMaps mp, const SplitArgs g) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSRing * kSStage);
+  uint64_t* empty = full + kSRing;
+  uint64_t* accf = empty + kSRing;  // [2] accumulator buffer ready (MMA -> epilogue)
+  uint64_t* accfree = accf + 2;     // [2] accumulator read and phase outputs written (epilogue -> MMA, TMA)
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accfree + 2);
+  float* s_e = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128]
+  float* s_bias = s_e + 2 * SBM;                           // [kSL][256] biases of the hidden layers
+  float* s_wl = s_bias + kSL * 256;                        // [256] weights of the output layer
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int t = 0;
+  while (t + 1 < g.ntypes && (int)blockIdx.x >= g.tile_start[t + 1]) ++t;
+  const int row0 = g.row_start[t] + ((int)blockIdx.x - g.tile_start[t]) * SBM;
+  const int row_end = g.row_start[t + 1];
+  const long rows = g.row_start[g.ntypes];
+  const int nh = g.nh, KD = g.width[0];
+  const int nch = (KD + 255) / 256;
+  // phases: forward layers 0 .. nh-1, backward layers nh-1 .. 1, then the nch dE/dD chunks
+  const int nphase = nh + (nh - 1) + nch;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSRing; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&accfree[b], kSEpi);
+    }
+    mbar_fence_init();
+  }
+  if (warp == 8) tmem_alloc(tmem_holder, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  // phase p: its GEMM (K, N), the A map pair, the weight slot, the accumulator buffer, and
+  // whether its A operand was written by the phase before (the producer then waits for it)
+  auto phase_info = [&](int p, int& K, int& N, const CUtensorMap*& ah, const CUtensorMap*& al, int& wslot, int& wrow,
+                        int& buf) {
+    buf = 0;
+    wrow = 0;
+    if (p < nh) {  // forward layer p: A = D (p == 0) or the scratch the previous layer wrote
+      K = g.width[p];
+      N = g.width[p + 1];
+      ah = p == 0 ? &mp.d[0] : &mp.x[(p - 1) & 1][0];
+      al = p == 0 ? &mp.d[1] : &mp.x[(p - 1) & 1][1];
+      wslot = p;
+    } else if (p < 2 * nh - 1) {  // backward layer l = nh - 1 - (p - nh): A = gz_l
+      const int l = nh - 1 - (p - nh);
+      K = g.width[l + 1];
+      N = g.width[l];
+      const int xb = (p - 1) & 1;
+      ah = &mp.x[xb][0];
+      al = &mp.x[xb][1];
+      wslot = nh + l;
+    } else {  // dE/dD chunk c = gz_0 W_0^T, columns [256 c, 256 c + 256)
+      const int c = p - (2 * nh - 1);
+      K = g.width[1];
+      N = min(256, KD - 256 * c);
+      const int xb = (2 * nh - 2) & 1;
+      ah = &mp.x[xb][0];
+      al = &mp.x[xb][1];
+      wslot = nh;
+      wrow = 256 * c;
+      buf = c & 1;
+    }
+  };
+
+  if (warp == 8) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int it = 0;
+      bool ok = true;
+      int fr[2] = {0, 0};  // accumulator-free phases waited for, per buffer
+      for (int p = 0; ok && p < nphase; ++p) {
+        int K, N, wslot, wrow, buf;
+        const CUtensorMap *ah, *al;
+        phase_info(p, K, N, ah, al, wslot, wrow, buf);
+        // the A operand of phases after the first was written by the previous phase's epilogue
+        if (p >= 1 && p <= 2 * nh - 1) {
+          const int pb = 0;  // chain phases use accumulator buffer 0
+          ok = mbar_wait(&accfree[pb], fr[pb] & 1, g.err);
+          ++fr[pb];
+          if (!ok) break;
+        }
+        const int nkb = (K + SBK - 1) / SBK;
+        for (int kb = 0; ok && kb < nkb; ++kb) {
+          const int s = it % kSRing;
+          if (it >= kSRing && !mbar_wait(&empty[s], ((it / kSRing) - 1) & 1, g.err)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = smem + s * kSStage;
+          // the weight boxes hold N rows (chain layers) or 256 (dE/dD chunks; rows beyond W_0 are zero-filled)
+          const uint32_t brows = p < 2 * nh - 1 ? (uint32_t)N : 256u;
+          mbar_expect_tx(&full[s], 2 * kSA + 2 * brows * 128u);
+          tma_load_2d(st, ah, &full[s], kb * SBK, row0);
+          tma_load_2d(st + kSA, al, &full[s], kb * SBK, row0);
+          tma_load_2d(st + 2 * kSA, &mp.w[t][wslot][0], &full[s], kb * SBK, wrow);
+          tma_load_2d(st + 2 * kSA + kSB, &mp.w[t][wslot][1], &full[s], kb * SBK, wrow);
+          ++it;
+        }
+      }
+      // every copy this thread started has landed before the CTA may exit
+      for (int s = 0; s < kSRing && s < it; ++s) {
+        const int last = s + kSRing * ((it - 1 - s) / kSRing);
+        mbar_wait(&full[s], (last / kSRing) & 1, g.err);
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      int it = 0;
+      bool ok = true;
+      int fr[2] = {0, 0};
+      for (int p = 0; ok && p < nphase; ++p) {
+        int K, N, wslot, wrow, buf;
+        const CUtensorMap *ah, *al;
+        phase_info(p, K, N, ah, al, wslot, wrow, buf);
+        // the accumulator buffer must have been read by the epilogue of its previous phase
+        if (p >= 1) {
+          int need;
+          if (p <= 2 * nh - 1) {
+            need = 1;  // chain: the previous phase's epilogue
+          } else {
+            const int c = p - (2 * nh - 1);
+            need = (buf == 0) ? 1 : (c >= 2 ? 1 : 0);  // buffer 0 follows the chain; buffer 1 from chunk 3 on
+          }
+          if (need) {
+            ok = mbar_wait(&accfree[buf], fr[buf] & 1, g.err);
+            ++fr[buf];
+            if (!ok) break;
+          }
+        }
+        tc_fence_after();
+        const uint32_t idesc = idesc_f16(SBM, N <= 256 ? ((N + 15) & ~15) : 256, 1);
+        const uint32_t acc = tmem + (uint32_t)(buf * 256);
+        const int nkb = (K + SBK - 1) / SBK;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % kSRing;
+          if (!mbar_wait(&full[s], (it / kSRing) & 1, g.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(smem + s * kSStage);
+          const uint64_t ah_ = sdesc_sw128(sa), al_ = sdesc_sw128(sa + kSA);
+          const uint64_t bh_ = sdesc_sw128(sa + 2 * kSA), bl_ = sdesc_sw128(sa + 2 * kSA + kSB);
+#pragma unroll
+          for (int k = 0; k < SBK / 16; ++k) {  // small terms first: lo.hi, hi.lo, then hi.hi
+            mma_f16(acc, al_ + 2 * k, bh_ + 2 * k, idesc, (kb | k) != 0);
+            mma_f16(acc, ah_ + 2 * k, bl_ + 2 * k, idesc, 1);
+            mma_f16(acc, ah_ + 2 * k, bh_ + 2 * k, idesc, 1);
+          }
+          mma_commit(&empty[s]);
+          ++it;
+        }
+        mma_commit(&accf[buf]);
+      }
+    }
+  } else {
+  // ---- epilogues: warps w and w + 4 own rows 32(w % 4) .. +31 and alternate 16-column pieces ----
+  // The FP32 residual stream (y_l forward, gy_l backward) stays in tensor-memory columns
+  // [256, 512) of the thread's row, which the chain phases leave free.
+  const int quad = warp & 3, half = warp >> 2;
+  const int rl = quad * 32 + lane;
+  const long row = row0 + rl;
+  const bool rv = row < row_end;
+  const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);
+  int af[2] = {0, 0};  // accumulator-ready phases waited for, per buffer
+  bool dead = false;   // after a timed-out wait: stop waiting, keep arriving
+  auto wait_acc = [&](int buf) {
+    if (!dead && !mbar_wait(&accf[buf], af[buf] & 1, g.err)) dead = true;
+    ++af[buf];
+    __syncwarp();
+    tc_fence_after();
+  };
+  auto release = [&](int buf, bool stored) {
+    if (stored) tmem_wait_st();
+    fence_async_global();  // this phase's global writes, read next by TMA
+    tc_fence_before();
+    mbar_arrive(&accfree[buf]);
+  };
+  auto xs_at = [&](int b, int hl, int col) -> __nv_bfloat16* { return g.xs[b][hl] + row * kSLd + col; };
+  auto gate_at = [&](int l, int col) -> float* { return g.gate + ((long)l * rows + row) * kSLd + col; };
+  auto put_x = [&](int xb, int c, const float* x) {
+    __align__(16) __nv_bfloat16 hi[16], lo[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) split2(x[i], hi[i], lo[i]);
+    uint4* dh = reinterpret_cast<uint4*>(xs_at(xb, 0, c));
+    uint4* dl = reinterpret_cast<uint4*>(xs_at(xb, 1, c));
+    dh[0] = *reinterpret_cast<const uint4*>(hi);
+    dh[1] = *reinterpret_cast<const uint4*>(hi + 8);
+    dl[0] = *reinterpret_cast<const uint4*>(lo);
+    dl[1] = *reinterpret_cast<const uint4*>(lo + 8);
+  };
+  // biases and output weights of this tile's type into shared memory
+  for (int l = 0; l < nh; ++l)
+    for (int c = threadIdx.x; c < 256; c += kSEpi)
+      s_bias[l * 256 + c] = c < g.width[l + 1] ? __ldg(g.bias[t][l] + c) : 0.f;
+  for (int c = threadIdx.x; c < 256; c += kSEpi) s_wl[c] = c < g.width[nh] ? __ldg(g.w_last[t] + c) : 0.f;
+  bar_sync(1, kSEpi);
+  // forward
+  for (int l = 0; l < nh; ++l) {
+    wait_acc(0);
+    const int N = g.width[l + 1];
+    const bool last = (l == nh - 1), sk = g.skip[l] == 1;
+    const float* bias = s_bias + l * 256;
+    const int xb = l & 1;
+    float e_acc = 0.f;
+    for (int c = half * 16; c < kSLd; c += 32) {  // zeros beyond N: the next A operand's K padding
+      uint32_t ra[16], ry[16];
+      tmem_ld16_async(tq + c, ra);
+      if (sk) tmem_ld16_async(tq + 256 + c, ry);
+      tmem_wait_ld();
+      float out[16], y[16], gt[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = c + i;
+        const float th = col < N ? tanhf(__uint_as_float(ra[i]) + bias[col]) : 0.f;
+        y[i] = th + (sk && col < N ? __uint_as_float(ry[i]) : 0.f);
+        gt[i] = 1.f - th * th;
+        if (last) {
+          const float w = s_wl[col];
+          e_acc += y[i] * w;
+          out[i] = w * gt[i];
+        } else {
+          out[i] = y[i];
+        }
+      }
+      if (!last) tmem_st16(tq + 256 + c, y);  // the residual stream of the next layer
+      if (!rv) continue;
+      if (!last && c < N) {
+        float4* gp = reinterpret_cast<float4*>(gate_at(l, c));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gp[q] = make_float4(gt[4 * q], gt[4 * q + 1], gt[4 * q + 2], gt[4 * q + 3]);
+      }
+      put_x(xb, c, out);
+    }
+    if (last) {
+      s_e[half * SBM + rl] = e_acc;
+      bar_sync(1, kSEpi);
+      if (half == 0 && rv) g.atom_e[g.perm[row]] = (double)(s_e[rl] + s_e[SBM + rl] + g.b_last[t]);
+    }
+    release(0, !last);
+  }
+  // backward of layers nh-1 .. 1: gz_{l-1} into the scratch, gy_{l-1} kept for the next skip
+  for (int l = nh - 1; l >= 1; --l) {
+    const int N = g.width[l];
+    if (rv)  // this row's gates towards L1 while the GEMM of this phase runs
+      for (int c = half * 16; c < N; c += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) prefetch_l1(gate_at(l - 1, c + 4 * q));
+    wait_acc(0);
+    const bool top = (l == nh - 1), sk = g.skip[l] == 1, keep = (l - 1 >= 1);
+    const int p = nh + (nh - 1 - l);  // phase index
+    const int xb = p & 1;
+    for (int c = half * 16; c < kSLd; c += 32) {  // zeros beyond N: the next A operand's K padding
+      uint32_t ra[16], ry[16];
+      tmem_ld16_async(tq + c, ra);
+      if (sk && !top) tmem_ld16_async(tq + 256 + c, ry);
+      tmem_wait_ld();
+      float gt[16];
+      if (rv && c < N) {
+        const float4* gp = reinterpret_cast<const float4*>(gate_at(l - 1, c));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 x = gp[q];
+          gt[4 * q] = x.x;
+          gt[4 * q + 1] = x.y;
+          gt[4 * q + 2] = x.z;
+          gt[4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) gt[i] = 0.f;
+      }
+      float gy[16], gz[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = c + i;
+        float v = col < N ? __uint_as_float(ra[i]) : 0.f;
+        if (sk && col < N) v += top ? s_wl[col] : __uint_as_float(ry[i]);
+        gy[i] = v;
+        gz[i] = v * gt[i];
+      }
+      if (keep) tmem_st16(tq + 256 + c, gy);
+      if (!rv) continue;
+      put_x(xb, c, gz);
+    }
+    release(0, keep);
+  }
+  // dE/dD in 256-column chunks from the two alternating accumulators
+  for (int c = 0; c < nch; ++c) {
+    const int buf = c & 1;
+    wait_acc(buf);
+    const int N = min(256, KD - 256 * c);
+    float* dst = g.gD + row * KD + 256 * c;
+    for (int q = half * 16; q < N; q += 32) {
+      float v[16];
+      tmem_ld16(tq + (uint32_t)(buf * 256) + q, v);
+      if (!rv) continue;
+      float4* d4 = reinterpret_cast<float4*>(dst + q);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    tc_fence_before();
+    mbar_arrive(&accfree[buf]);
+  }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8) tmem_dealloc(tmem, 512);
+}
+
+size_t split_smem() { return (size_t)kSRing * kSStage + 16 * 8 + 16 + (2 * SBM + kSL * 256 + 256) * 4 + 1024; }
+
+}  // namespace
+
+bool fit_split_supported(const DeviceModel& m) {
+  const int nfl = m.n_fit_layers, nh = nfl - 1;
+  if (nh < 1 || nh > kSL) return false;
+  const int KD = m.M * m.A;
+  if (KD % 16 != 0) return false;
+  for (int t = 0; t < m.cfg.ntypes; ++t)
+    for (int l = 0; l < nh; ++l) {
+      const LayerDesc& L = m.fit[(size_t)t * nfl + l];
+      const LayerDesc& L0 = m.fit[l];
+      if (L.n_in != L0.n_in || L.n_out != L0.n_out || L.skip != L0.skip) return false;
+      if (L.n_out % 16 || L.n_out > 256 || L.skip > 1 || (l == 0 && L.skip)) return false;
+    }
+  return m.fit[0].n_in == KD && m.fit_wt_bf16_lo != nullptr;
+}
+
+int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dhi, const __nv_bfloat16* Dlo,
+                      const PathIO& io, Arena& ar, cudaStream_t st, const float** gD_out) {
+  const long N = pc.natoms;
+  const int nfl = m.n_fit_layers, nh = nfl - 1;
+  const int nt = pc.ntypes;
+  const int KD = pc.M * pc.A;
+  __nv_bfloat16* xs = ar.get<__nv_bfloat16>(4 * N * kSLd);
+  float* gate = ar.get<float>((long)nh * N * kSLd);
+  float* gD = ar.get<float>(N * KD);
+  if (ar.measure) return DP_OK;
+  if (!ar.ok()) {
+    set_error("scratch allocation failed");
+    return DP_E_OOM;
+  }
+  SplitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.ntypes = nt;
+  a.nh = nh;
+  a.width[0] = KD;
+  for (int l = 0; l < nh; ++l) {
+    a.width[l + 1] = m.fit[l].n_out;
+    a.skip[l] = m.fit[l].skip;
+  }
+  int tiles = 0;
+  for (int t = 0; t <= nt; ++t) {
+    a.row_start[t] = io.type_start[t];
+    a.tile_start[t] = tiles;
+    if (t < nt) tiles += (io.type_start[t + 1] - io.type_start[t] + SBM - 1) / SBM;
+  }
+  SplitMaps mp;
+  std::memset(&mp, 0, sizeof(mp));
+  int rc = make_tmap_bf16(&mp.d[0], Dhi, N, KD, SBM);
+  if (rc == DP_OK) rc = make_tmap_bf16(&mp.d[1], Dlo, N, KD, SBM);
+  for (int b = 0; rc == DP_OK && b < 2; ++b)
+    for (int hl = 0; rc == DP_OK && hl < 2; ++hl) {
+      a.xs[b][hl] = xs + (long)(2 * b + hl) * N * kSLd;
+      rc = make_tmap_bf16(&mp.x[b][hl], a.xs[b][hl], N, kSLd, SBM);
+    }
+  if (rc != DP_OK) return rc;
+  const float* p32 = m.p32;
+  for (int t = 0; t < nt; ++t) {
+    for (int l = 0; l < nh; ++l) {
+      const LayerDesc& L = m.fit[(size_t)t * nfl + l];
+      a.bias[t][l] = p32 + L.w_off + (long)L.n_in * L.n_out;
+      for (int hl = 0; hl < 2; ++hl) {
+        const CUtensorMap* f = fit_weight_map(m, t, l, 0, L.n_out, hl == 1);
+        const CUtensorMap* b = fit_weight_map(m, t, l, 1, l == 0 ? 256 : L.n_in, hl == 1);
+        if (!f || !b) return DP_E_CUDA;
+        mp.w[t][l][hl] = *f;
+        mp.w[t][nh + l][hl] = *b;
+      }
+    }
+    const LayerDesc& Lo = m.fit[(size_t)t * nfl + nh];
+    a.w_last[t] = p32 + Lo.w_off;
+    a.b_last[t] = m.fit_out_bias[t];
+  }
+  a.gate = gate;
+  a.perm = io.perm;
+  a.atom_e = io.atom_energy;
+  a.gD = gD;
+  a.err = &io.status->timeout;
+  if (tiles > 0) {
+    ProfScope _ps(io.prof, "fit_split_tc", st);
+    const size_t smem = split_smem();
+    DP_CUDA_TRY(allow_max_smem(k_fit_split));
+    k_fit_split<<<tiles, kSThreads, smem, st>>>(mp, a);
+    DP_CUDA_TRY(cudaGetLastError());
+  }
+  *gD_out = gD;
+  return DP_OK;
+}
+
+}  // namespace dpgb

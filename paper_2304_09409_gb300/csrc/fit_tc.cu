@@ -131,6 +131,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     *gD_out = nullptr;
     return run_fitting_fused(m, pc, Dbf, io, ar, st, gDh_out);
   }
+  if (split && fit_split_supported(m)) return run_fitting_split(m, pc, Dbf, Dlo, io, ar, st, gD_out);
   if (split) gDh_out = nullptr;  // split operands: dE/dD in FP32
   const long N = pc.natoms;
   const int nfl = m.n_fit_layers, nh = nfl - 1;

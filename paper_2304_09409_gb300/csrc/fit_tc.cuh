@@ -26,6 +26,13 @@ bool fit_fused_supported(const DeviceModel& m);
 int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io,
                       Arena& ar, cudaStream_t st, const __nv_bfloat16** gDh_out);
 
+// The whole FP32-mode fitting net in one kernel per 128-atom tile on split BF16 operands (three
+// passes), for nets of at most four hidden layers of width <= 256 (multiples of 16) with skips of
+// kind 0 or 1; Dhi / Dlo the descriptor's high and low halves; dE/dD FP32 [rows][KD].
+bool fit_split_supported(const DeviceModel& m);
+int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dhi, const __nv_bfloat16* Dlo,
+                      const PathIO& io, Arena& ar, cudaStream_t st, const float** gD_out);
+
 // dE/dD of every atom: FP32 [rows][KD] into *gD_out, or BF16 into *gDh_out when that is given.
 // With Dlo (the low halves of the descriptor, FP32 mode) every GEMM runs on split operands
 // (three passes, hi.hi + hi.lo + lo.hi) and dE/dD is FP32.

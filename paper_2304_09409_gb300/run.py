@@ -4,7 +4,7 @@
 
 Workloads: water192 (the 192-atom water frame), water12288 (it tiled 4x4x4), water1536
 (tiled 2x2x2), fcc32000 (Cu-like FCC, 20^3 cells), fcc4000 (10^3 cells).  Paths: fp64,
-fp32, fp32-compressed, fp64-compressed, bf16-compressed.  Inputs live on the device; each step is one full
+fp32, tf32, bf16 (network GEMMs on the tensor cores), fp32-compressed, fp64-compressed, bf16-compressed.  Inputs live on the device; each step is one full
 dp_compute (neighbour list included).  Prints the mean device time per step.
 """
 from __future__ import annotations
@@ -33,8 +33,8 @@ def workload(name: str):
     return cfg, I.make_params(cfg, 0), fr
 
 
-PATHS = {"fp64": ("fp64", False), "fp32": ("fp32", False), "fp32-compressed": ("fp32", True),
-         "fp64-compressed": ("fp64", True), "bf16-compressed": ("bf16", True)}
+PATHS = {"fp64": ("fp64", False), "fp32": ("fp32", False), "tf32": ("tf32", False), "bf16": ("bf16", False),
+         "fp32-compressed": ("fp32", True), "fp64-compressed": ("fp64", True), "bf16-compressed": ("bf16", True)}
 
 
 def main(argv=None):
