@@ -16,7 +16,6 @@ exchange step within a frame of this size); value = atoms of all ranks / max ran
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -136,23 +135,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def _src_hash(*names):
-    h = hashlib.sha256()
-    for n in names:
-        with open(os.path.join(ROOT, "paper_2304_09409_gb300", "csrc", n), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 def _traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
-    the current source of that kernel (else None)."""
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json (written from ncu captures by
+    `python -m paper_2304_09409_gb300.run --ncu-summary ... --traffic profiles/traffic.json`), if
+    it was taken on the current source of that kernel (else None)."""
+    from paper_2304_09409_gb300.run import src_hash
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             t = json.load(fh)
         ent = t.get(kernel)
-        if ent and ent.get("src_hash") == _src_hash(*ent["sources"]):
+        if ent and ent.get("src_hash") == src_hash(ent["sources"]):
             return ent["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -220,6 +213,7 @@ def _kernel_rooflines(cfg, big, real_nb, prof, work, steps, peaks, fit_npass):
         "fit_fwd_last_tc": ("tensor", fit_npass * fwd_last / 1e12, ten, "TFLOP/s"),
         "fit_bwd_tc": ("tensor", fit_npass * bwd / 1e12, ten, "TFLOP/s"),
         "fit_fused_tc": ("tensor", (fwd + fwd_last + bwd) / 1e12, ten, "TFLOP/s"),
+        "fit_split_tc": ("tensor", fit_npass * (fwd + fwd_last + bwd) / 1e12, ten, "TFLOP/s"),
     }
     alu_equiv = {"mom_fwd": 18.0 * M * real_nb / 1e12, "mom_bwd": 36.0 * M * real_nb / 1e12}
     out = {}
@@ -244,6 +238,7 @@ def _kernel_rooflines(cfg, big, real_nb, prof, work, steps, peaks, fit_npass):
                      "us_per_step": t_step * 1e6, "launches_per_step": nl / max(steps, 1)}
         if bound == "tensor" and fit_npass > 1 and name != "fit_fused_tc":
             out[name]["work"] = f"issued MMA FLOPs ({fit_npass} passes of split BF16 operands)"
+            out[name]["algorithmic_tflops"] = amount / fit_npass / t_step
     return out, pairs
 
 

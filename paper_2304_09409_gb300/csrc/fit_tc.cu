@@ -131,7 +131,13 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
     *gD_out = nullptr;
     return run_fitting_fused(m, pc, Dbf, io, ar, st, gDh_out);
   }
-  if (split && fit_split_supported(m)) return run_fitting_split(m, pc, Dbf, Dlo, io, ar, st, gD_out);
+  // the fused kernel runs one CTA per 128-atom tile through the whole chain: it pays off once the
+  // tiles fill half the SMs; smaller batches spread each layer over more CTAs with per-layer launches
+  if (split && fit_split_supported(m)) {
+    long tiles = 0;
+    for (int t = 0; t < pc.ntypes; ++t) tiles += (io.type_start[t + 1] - io.type_start[t] + 127) / 128;
+    if (2 * tiles >= sm_count()) return run_fitting_split(m, pc, Dbf, Dlo, io, ar, st, gD_out);
+  }
   if (split) gDh_out = nullptr;  // split operands: dE/dD in FP32
   const long N = pc.natoms;
   const int nfl = m.n_fit_layers, nh = nfl - 1;

@@ -37,13 +37,118 @@ PATHS = {"fp64": ("fp64", False), "fp32": ("fp32", False), "tf32": ("tf32", Fals
          "fp32-compressed": ("fp32", True), "fp64-compressed": ("fp64", True), "bf16-compressed": ("bf16", True)}
 
 
+# Kernel scopes of the path (the names dp_profile_read reports) and the kernels and sources of each.
+SCOPES = {
+    "nlist": (("k_bin", "k_fill_scan", "k_scan_excl", "k_fill", "k_nlist_cell", "k_nlist"), ("nlist.cu", "dp_internal.cuh")),
+    "env": (("k_env_mom",), ("mom.cu", "mom.cuh", "tc_ptx.cuh", "env.cuh", "dp_internal.cuh")),
+    "mom_fwd": (("k_mom_fwd",), ("mom.cu", "mom.cuh", "tc_ptx.cuh", "env.cuh", "dp_internal.cuh")),
+    "mom_gT": (("k_mom_gT",), ("mom.cu", "mom.cuh", "tc_ptx.cuh", "env.cuh", "dp_internal.cuh")),
+    "mom_bwd": (("k_mom_bwd",), ("mom.cu", "mom.cuh", "tc_ptx.cuh", "env.cuh", "dp_internal.cuh")),
+    "mom_force": (("k_force_mom",), ("mom.cu", "mom.cuh", "tc_ptx.cuh", "env.cuh", "dp_internal.cuh")),
+    "fit_split_tc": (("k_fit_split",), ("fit_split.cu", "fit_tc.cuh", "tc_ptx.cuh", "dp_internal.cuh")),
+    "fit_fused_tc": (("k_fit_fused",), ("fit_fused.cu", "fit_tc.cuh", "tc_ptx.cuh", "dp_internal.cuh")),
+    "frame_sums": (("k_chunk_sums", "k_frame_sums"), ("driver.cu",)),
+}
+
+
+def src_hash(names) -> str:
+    """Hash of the CUDA sources a kernel scope is built from."""
+    import hashlib
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(here, n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _kernel_base(name: str) -> str:
+    """Kernel name with its template arguments, without namespaces and parameters."""
+    base = name.split("(")[0].strip()
+    for pre in ("void ", "unnamed>::", "(anonymous namespace)::", "dpgb::"):
+        base = base.replace(pre, "")
+    return base.strip()
+
+
+def ncu_summary(csv_paths, steps: int, command: str):
+    """Per-kernel launches, device time and share (and DRAM bytes per launch where the capture has
+    them) from ncu --csv logs; returns (markdown table, {scope: traffic record})."""
+    import csv
+    import io
+    times, dram, launches, full = {}, {}, {}, {}
+    for path in csv_paths:
+        text = open(path).read()
+        lines = text.splitlines()
+        start = next(k for k, ln in enumerate(lines) if ln.startswith('"ID"'))
+        for row in csv.DictReader(io.StringIO("\n".join(lines[start:]))):
+            name = row["Kernel Name"]
+            base = _kernel_base(name)
+            key = (path, row["ID"])
+            unit = row.get("Metric Unit", "")
+            try:
+                val = float(row["Metric Value"].replace(",", ""))
+            except ValueError:
+                continue
+            metric = row["Metric Name"]
+            if metric == "gpu__time_duration.sum":
+                scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3,
+                         "s": 1e6, "second": 1e6}.get(unit, 1.0)
+                times.setdefault(base, {})[key] = val * scale
+                full[base] = name.split("(")[0].replace("void ", "").replace("unnamed>::", "")
+            elif metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                scale = {"byte": 1.0, "B": 1.0, "Kbyte": 1e3, "KB": 1e3, "Mbyte": 1e6, "MB": 1e6, "Gbyte": 1e9,
+                         "GB": 1e9}.get(unit, 1.0)
+                dram.setdefault(base, {}).setdefault(key, 0.0)
+                dram[base][key] += val * scale
+    total = sum(sum(v.values()) for v in times.values()) or 1.0
+    out = ["| kernel | launches | total us | us/launch | share | DRAM MB/launch |", "|---|---:|---:|---:|---:|---:|"]
+    for base, v in sorted(times.items(), key=lambda kv: -sum(kv[1].values())):
+        t = sum(v.values())
+        d = dram.get(base)
+        dm = f"{sum(d.values()) / len(d) / 1e6:.2f}" if d else "-"
+        out.append(f"| {base} | {len(v)} | {t:.1f} | {t / len(v):.1f} | {100 * t / total:.1f}% | {dm} |")
+    out.append(f"\nTotal {total:.1f} us.")
+    traffic = {}
+    for scope, (kernels, sources) in SCOPES.items():
+        names = [b for b in dram if b.split("<")[0] in kernels]
+        per = [sum(dram[b].values()) / len(dram[b]) for b in names]
+        if per:
+            traffic[scope] = {"dram_bytes_per_launch": float(sum(per)), "kernels": " + ".join(names),
+                              "sources": list(sources), "src_hash": src_hash(sources), "command": command,
+                              "per": "one step (all launches of the scope)"}
+    return "\n".join(out), traffic
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="water12288")
     ap.add_argument("--path", default="fp32-compressed", choices=sorted(PATHS))
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--ncu-summary", nargs="+", default=None,
+                    help="summarise ncu --csv logs (launch list; DRAM bytes where captured) instead of running")
+    ap.add_argument("--md", default=None, help="with --ncu-summary: write the markdown table here")
+    ap.add_argument("--traffic", default=None, help="with --ncu-summary: merge DRAM bytes per scope into this JSON")
+    ap.add_argument("--command", default="", help="with --ncu-summary: the capture command, recorded with the figures")
     args = ap.parse_args(argv)
+    if args.ncu_summary:
+        import os
+        md, traffic = ncu_summary(args.ncu_summary, args.steps, args.command)
+        if args.md:
+            with open(args.md, "w") as fh:
+                fh.write(md + "\n")
+        else:
+            print(md)
+        if args.traffic:
+            old = {}
+            if os.path.exists(args.traffic):
+                with open(args.traffic) as fh:
+                    old = json.load(fh)
+            old.update(traffic)
+            with open(args.traffic, "w") as fh:
+                json.dump(old, fh, indent=1)
+        return 0
     import torch
     from . import dpgb
     cfg, p, fr = workload(args.workload)
