@@ -1,4 +1,4 @@
-"""Plain FP64 CPU oracle for the se_e2_a energy / force / virial path (ctypes wrapper).
+"""Plain FP64 CPU oracle for the Deep Potential energy / force / virial path (ctypes wrapper).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
 cpu_baseline / reference legs of bench.py.  The product path never imports it.
@@ -6,7 +6,9 @@ cpu_baseline / reference legs of bench.py.  The product path never imports it.
 The C++ source (dp_oracle.cpp) restates the DeePMD-kit v2 paper (arXiv 2304.09409)
 directly; see its header for the equation-by-equation map.  This wrapper only marshals
 numpy arrays.  Model configurations are duck-typed: any object with attributes
-ntypes, sel, rcut, rcut_smth, embed, axis, fit, type_one_side.
+ntypes, sel, rcut, rcut_smth, embed, axis, fit, type_one_side, and optionally descriptor
+(0 se_e2_a, 1 se_e2_r, 2 hybrid of the two on one neighbour list) and embed_r (the hybrid's
+se_e2_r embedding widths).
 """
 from __future__ import annotations
 
@@ -56,6 +58,9 @@ class _Cfg(ctypes.Structure):
         ("n_fit", ctypes.c_int),
         ("fit", ctypes.c_int * 8),
         ("type_one_side", ctypes.c_int),
+        ("descriptor", ctypes.c_int),
+        ("n_embed_r", ctypes.c_int),
+        ("embed_r", ctypes.c_int * 8),
     ]
 
 
@@ -107,6 +112,11 @@ def _cfg(cfg) -> _Cfg:
     for k, v in enumerate(cfg.fit):
         c.fit[k] = int(v)
     c.type_one_side = int(getattr(cfg, "type_one_side", 0))
+    c.descriptor = int(getattr(cfg, "descriptor", 0))
+    embed_r = tuple(getattr(cfg, "embed_r", ()))
+    c.n_embed_r = len(embed_r)
+    for k, v in enumerate(embed_r):
+        c.embed_r[k] = int(v)
     return c
 
 

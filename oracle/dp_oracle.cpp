@@ -1,4 +1,5 @@
-// Plain FP64 CPU oracle for the se_e2_a Deep Potential energy / force / virial path.
+// Plain FP64 CPU oracle for the Deep Potential energy / force / virial path (descriptors
+// se_e2_a, se_e2_r and their hybrid).
 //
 // TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
 // cpu_baseline leg (and its --impl reference arm) load this library.  The product path
@@ -10,7 +11,9 @@
 //   Eq. (rij)        R_j = (s, s x/r, s y/r, s z/r),  r_ij = r_j - r_i     Sec. II.A.1
 //   Eq. (switch)     s(r)                                                  Sec. II.A.1
 //   Eq. (G2)         G_j = N_{e,2}^{a_i,a_j}(s(r_ij))                      Sec. II.A.1
-//   descriptor       D = (1/Nc^2) G^T R R^T G_<                            Sec. II.A.1
+//   se_e2_a          D = (1/Nc^2) G^T R R^T G_<                            Sec. II.A.1
+//   se_e2_r          D = (1/Nc) G^T s  (R reduced to its radial column)    Sec. II.A.1
+//   hybrid           D = the two descriptors concatenated                  Sec. II.A.1
 //   Eq. (fitting)    E_i = F_0^{a_i}(D^i)                                  Sec. II.A.2
 //   force / virial   F = -dE/dr,  Xi = -sum_g dE/dh_{g a} h_{g b}           Sec. II.A.2
 //   Eq. (NN)         layer y = phi(x w + b) (+ x | + {x,x})                Sec. II.A.6
@@ -26,6 +29,11 @@
 //     left to right without fused multiply-add (build flag -ffp-contract=off).
 //   * ResNet timestep w_hat = 1; the last fitting layer (width 1) is linear.
 //   * Quintic pieces are evaluated at t = x - x_l (the offset inside the interval).
+//   * se_e2_r keeps s(r) as the weight of each row (the radial column of R), so a neighbour's
+//     term vanishes smoothly at r_c and padded rows contribute nothing; its 1/Nc is that of the
+//     contraction G^T R with one column.
+//   * The hybrid descriptor's parts share one neighbour list (r_c, r_s, sel) and the net index
+//     rule (type_one_side), each with its own embedding nets; the se_e2_a block comes first.
 //
 // Forces come from a hand-written reverse pass in plain loops.  A second, independent
 // mechanism -- forward-mode dual numbers through a templated energy -- exists only to
@@ -53,6 +61,9 @@ struct OrcConfig {
   int n_fit;
   int fit[8];
   int type_one_side;
+  int descriptor;  // 0: se_e2_a; 1: se_e2_r; 2: hybrid of se_e2_a and se_e2_r on one neighbour list
+  int n_embed_r;   // hybrid: layers of the se_e2_r part's embedding nets
+  int embed_r[8];
 };
 
 }  // extern "C"
@@ -127,33 +138,56 @@ inline HD dtanh(HD x) {
 // ------------------------------------------------------------------------------------------
 // Parameter layout helpers (flat FP64 array, see the inputs module)
 // ------------------------------------------------------------------------------------------
-struct Layout {
-  int ntypes, nc, m, axis, n_embed_nets;
-  std::vector<int> ein, eout;   // embedding layer shapes
-  std::vector<int> fin, fout;   // fitting layer shapes (last has fout = 1)
-  std::vector<long> eoff;       // per embedding net, per layer: offset of W (b follows W)
-  std::vector<long> foff;       // per fitting net, per layer
-  int sel_off[9];
-  long n_params;
+// One family of embedding nets: per net (in net-index order), layer by layer.
+struct NetSet {
+  int nl = 0, m = 0;          // layers, output width
+  std::vector<int> in, out;   // layer shapes
+  std::vector<long> off;      // per net, per layer: offset of W (b follows W)
 };
 
+struct Layout {
+  int ntypes, nc, m, axis, n_embed_nets;
+  NetSet e1;                  // nets of `embed` (parameters from offset 0)
+  NetSet e2;                  // nets of `embed_r` (hybrid only), after those of e1
+  bool ang, rad;              // the descriptor has an se_e2_a block / an se_e2_r block
+  int da, dw;                 // width of the se_e2_a block of D; total width of D
+  std::vector<int> fin, fout; // fitting layer shapes (last has fout = 1)
+  std::vector<long> foff;     // per fitting net, per layer
+  int sel_off[9];
+  long n_params;
+  const NetSet& radial() const { return ang ? e2 : e1; }
+};
+
+void add_nets(NetSet& S, int nl, const int* widths, int nnets, long& off) {
+  S.nl = nl;
+  S.m = widths[nl - 1];
+  int prev = 1;
+  for (int l = 0; l < nl; ++l) { S.in.push_back(prev); S.out.push_back(widths[l]); prev = widths[l]; }
+  for (int n = 0; n < nnets; ++n)
+    for (int l = 0; l < nl; ++l) { S.off.push_back(off); off += (long)S.in[l] * S.out[l] + S.out[l]; }
+}
+
+// Sec. II.A.1: se_e2_a gives D = T T_<^T (M x M_<); se_e2_r, with only the radial column s of R,
+// gives D = G^T s / N_c (M values); the hybrid descriptor is the concatenation of the two.
 Layout make_layout(const OrcConfig& c) {
   Layout L;
   L.ntypes = c.ntypes;
   L.nc = 0;
   for (int t = 0; t < c.ntypes; ++t) { L.sel_off[t] = L.nc; L.nc += c.sel[t]; }
   L.sel_off[c.ntypes] = L.nc;
-  L.m = c.embed[c.n_embed - 1];
   L.axis = c.axis;
+  L.ang = c.descriptor != 1;
+  L.rad = c.descriptor != 0;
   L.n_embed_nets = c.type_one_side ? c.ntypes : c.ntypes * c.ntypes;
-  int prev = 1;
-  for (int l = 0; l < c.n_embed; ++l) { L.ein.push_back(prev); L.eout.push_back(c.embed[l]); prev = c.embed[l]; }
-  prev = L.m * c.axis;
+  long off = 0;
+  add_nets(L.e1, c.n_embed, c.embed, L.n_embed_nets, off);
+  if (c.descriptor == 2) add_nets(L.e2, c.n_embed_r, c.embed_r, L.n_embed_nets, off);
+  L.m = L.e1.m;
+  L.da = L.ang ? L.m * c.axis : 0;
+  L.dw = L.da + (L.rad ? L.radial().m : 0);
+  int prev = L.dw;
   for (int l = 0; l < c.n_fit; ++l) { L.fin.push_back(prev); L.fout.push_back(c.fit[l]); prev = c.fit[l]; }
   L.fin.push_back(prev); L.fout.push_back(1);
-  long off = 0;
-  for (int n = 0; n < L.n_embed_nets; ++n)
-    for (size_t l = 0; l < L.ein.size(); ++l) { L.eoff.push_back(off); off += (long)L.ein[l] * L.eout[l] + L.eout[l]; }
   for (int n = 0; n < c.ntypes; ++n)
     for (size_t l = 0; l < L.fin.size(); ++l) { L.foff.push_back(off); off += (long)L.fin[l] * L.fout[l] + L.fout[l]; }
   L.n_params = off;
@@ -348,14 +382,17 @@ struct AtomOut {
   int range_err;
 };
 
-// Embedding forward for one scalar input: returns G (M) and stores tanh outputs per layer.
-void embed_forward(const OrcConfig& c, const Layout& L, const double* params, int net, double s,
-                   std::vector<std::vector<double>>& act, std::vector<std::vector<double>>& outs) {
+// Embedding forward of net `net` of family S for one scalar input; keeps the tanh outputs
+// and the layer outputs (the last is G, M values).
+void embed_forward(const NetSet& S, const double* params, int net, double s, std::vector<std::vector<double>>& act,
+                   std::vector<std::vector<double>>& outs) {
+  act.assign(S.nl, {});
+  outs.assign(S.nl, {});
   std::vector<double> x(1, s);
-  for (int l = 0; l < c.n_embed; ++l) {
-    const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
-    const double* b = W + (long)L.ein[l] * L.eout[l];
-    int ni = L.ein[l], no = L.eout[l];
+  for (int l = 0; l < S.nl; ++l) {
+    const double* W = params + S.off[(size_t)net * S.nl + l];
+    const double* b = W + (long)S.in[l] * S.out[l];
+    int ni = S.in[l], no = S.out[l];
     act[l].assign(no, 0.0);
     outs[l].assign(no, 0.0);
     int sk = skip_kind(ni, no);
@@ -371,12 +408,11 @@ void embed_forward(const OrcConfig& c, const Layout& L, const double* params, in
 }
 
 // Reverse pass of the embedding net: given dE/dG (M), returns dE/ds.
-double embed_backward(const OrcConfig& c, const Layout& L, const double* params, int net, double s,
-                      const std::vector<std::vector<double>>& act, const std::vector<std::vector<double>>& outs,
+double embed_backward(const NetSet& S, const double* params, int net, const std::vector<std::vector<double>>& act,
                       std::vector<double> gy) {
-  for (int l = c.n_embed - 1; l >= 0; --l) {
-    const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
-    int ni = L.ein[l], no = L.eout[l];
+  for (int l = S.nl - 1; l >= 0; --l) {
+    const double* W = params + S.off[(size_t)net * S.nl + l];
+    int ni = S.in[l], no = S.out[l];
     int sk = skip_kind(ni, no);
     std::vector<double> gx(ni, 0.0);
     for (int o = 0; o < no; ++o) {
@@ -387,20 +423,60 @@ double embed_backward(const OrcConfig& c, const Layout& L, const double* params,
     }
     gy = gx;
   }
-  (void)s;
   return gy[0];
 }
 
+// Embedding outputs of one neighbour for a family: by the nets (Eq. (G2)), or, when `tab` is
+// given, by the quintic pieces (Eq. (compress)) with their derivatives dG/ds.
+struct EmbedRow {
+  std::vector<double> G, dG;
+  std::vector<std::vector<double>> act, outs;
+};
+
+void embed_row(const NetSet& S, const double* params, const Table* tab, int net, double s, EmbedRow& e, int* oor) {
+  const int M = S.m;
+  e.G.assign(M, 0.0);
+  e.dG.assign(M, 0.0);
+  if (!tab) {
+    embed_forward(S, params, net, s, e.act, e.outs);
+    for (int mm = 0; mm < M; ++mm) e.G[mm] = e.outs[S.nl - 1][mm];
+    return;
+  }
+  // g(t) with t = s - x_l inside interval l
+  int l = tab->interval(s, oor);
+  double t = s - tab->node(l);
+  const double* co = tab->coef + (((size_t)net * tab->lc() + l) * M) * 6;
+  for (int mm = 0; mm < M; ++mm) {
+    const double* p = co + (size_t)mm * 6;
+    e.G[mm] = ((((p[0] * t + p[1]) * t + p[2]) * t + p[3]) * t + p[4]) * t + p[5];
+    e.dG[mm] = (((5.0 * p[0] * t + 4.0 * p[1]) * t + 3.0 * p[2]) * t + 2.0 * p[3]) * t + p[4];
+  }
+}
+
+// dE/ds through the embedding of one neighbour, given dE/dG.
+double embed_row_backward(const NetSet& S, const double* params, const Table* tab, int net, const EmbedRow& e,
+                          const std::vector<double>& gG) {
+  if (!tab) return embed_backward(S, params, net, e.act, gG);
+  double acc = 0.0;
+  for (int mm = 0; mm < S.m; ++mm) acc += gG[mm] * e.dG[mm];
+  return acc;
+}
+
+// One atom: descriptor, fitting net, and the reverse pass down to dE/dr_ij per slot (gd).
+// The table, when given, replaces the nets of `embed` (family e1); the se_e2_r nets of a hybrid
+// model (family e2) are always evaluated as networks.
 void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const Table* tab, int i, const double* coord,
                const int* type, const double* box, const int* nl_j, const int* nl_code, double* gd /*[Nc*3]*/,
                AtomOut* out) {
   const int nc = L.nc, M = L.m, A = L.axis;
   const int ai = type[i];
   const double rs = c.rcut_smth, rc = c.rcut;
+  const bool hyb = c.descriptor == 2;
+  const NetSet& Sr = L.radial();
+  const int Mr = L.rad ? Sr.m : 0;
   std::vector<double> R((size_t)nc * 4, 0.0), dvec((size_t)nc * 3, 0.0), rr(nc, 0.0), ss(nc, 0.0);
   std::vector<int> valid(nc, 0), netk(nc, 0);
-  std::vector<double> G((size_t)nc * M, 0.0), dG((size_t)nc * M, 0.0);
-  std::vector<std::vector<std::vector<double>>> act(nc), outs(nc);
+  std::vector<EmbedRow> e1(nc), e2(hyb ? nc : 0);
   out->range_err = 0;
   // Eq. (rij) with Eq. (switch)
   for (int t = 0; t < c.ntypes; ++t)
@@ -422,45 +498,42 @@ void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const 
       R[(size_t)k * 4 + 0] = s;
       for (int a = 0; a < 3; ++a) R[(size_t)k * 4 + 1 + a] = s * d[a] / r;
     }
-  // Eq. (G2): embedding rows of real neighbours (padded rows of R are zero and contribute nothing)
+  // Eq. (G2) / Eq. (compress): embedding rows of real neighbours (padded rows of R are zero and
+  // contribute nothing)
   for (int k = 0; k < nc; ++k) {
     if (!valid[k]) continue;
-    if (!tab) {
-      act[k].resize(c.n_embed);
-      outs[k].resize(c.n_embed);
-      embed_forward(c, L, params, netk[k], ss[k], act[k], outs[k]);
-      for (int mm = 0; mm < M; ++mm) G[(size_t)k * M + mm] = outs[k][c.n_embed - 1][mm];
-    } else {
-      // Eq. (compress): g(t) with t = s - x_l inside interval l
-      int oor = 0;
-      int l = tab->interval(ss[k], &oor);
-      if (oor) out->range_err = 1;
-      double t = ss[k] - tab->node(l);
-      const double* co = tab->coef + (((size_t)netk[k] * tab->lc() + l) * M) * 6;
-      for (int mm = 0; mm < M; ++mm) {
-        const double* p = co + (size_t)mm * 6;
-        double g = ((((p[0] * t + p[1]) * t + p[2]) * t + p[3]) * t + p[4]) * t + p[5];
-        double gp = (((5.0 * p[0] * t + 4.0 * p[1]) * t + 3.0 * p[2]) * t + 2.0 * p[3]) * t + p[4];
-        G[(size_t)k * M + mm] = g;
-        dG[(size_t)k * M + mm] = gp;
-      }
-    }
+    int oor = 0;
+    embed_row(L.e1, params, tab, netk[k], ss[k], e1[k], &oor);
+    if (oor) out->range_err = 1;
+    if (hyb) embed_row(L.e2, params, nullptr, netk[k], ss[k], e2[k], &oor);
   }
-  // T = (1/Nc) G^T R   (M x 4)
+  auto Gang = [&](int k) -> const std::vector<double>& { return e1[k].G; };
+  auto Grad = [&](int k) -> const std::vector<double>& { return hyb ? e2[k].G : e1[k].G; };
+  std::vector<double> D(L.dw, 0.0);
+  // se_e2_a block: T = (1/Nc) G^T R (M x 4), D = T T_<^T (M x M_<), flattened row-major
   std::vector<double> T((size_t)M * 4, 0.0);
-  for (int mm = 0; mm < M; ++mm)
-    for (int q = 0; q < 4; ++q) {
+  if (L.ang) {
+    for (int mm = 0; mm < M; ++mm)
+      for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < nc; ++k)
+          if (valid[k]) acc += Gang(k)[mm] * R[(size_t)k * 4 + q];
+        T[(size_t)mm * 4 + q] = acc / nc;
+      }
+    for (int mm = 0; mm < M; ++mm)
+      for (int l = 0; l < A; ++l) {
+        double acc = 0.0;
+        for (int q = 0; q < 4; ++q) acc += T[(size_t)mm * 4 + q] * T[(size_t)l * 4 + q];
+        D[(size_t)mm * A + l] = acc;
+      }
+  }
+  // se_e2_r block: D_m = (1/Nc) sum_k G_km s_k
+  if (L.rad)
+    for (int mm = 0; mm < Mr; ++mm) {
       double acc = 0.0;
-      for (int k = 0; k < nc; ++k) acc += G[(size_t)k * M + mm] * R[(size_t)k * 4 + q];
-      T[(size_t)mm * 4 + q] = acc / nc;
-    }
-  // D = T T_<^T  (M x M_<), flattened row-major
-  std::vector<double> D((size_t)M * A, 0.0);
-  for (int mm = 0; mm < M; ++mm)
-    for (int l = 0; l < A; ++l) {
-      double acc = 0.0;
-      for (int q = 0; q < 4; ++q) acc += T[(size_t)mm * 4 + q] * T[(size_t)l * 4 + q];
-      D[(size_t)mm * A + l] = acc;
+      for (int k = 0; k < nc; ++k)
+        if (valid[k]) acc += Grad(k)[mm] * ss[k];
+      D[L.da + mm] = acc / nc;
     }
   // Eq. (fitting): E_i = F_0^{a_i}(D)
   const int nfl = (int)L.fin.size();
@@ -499,47 +572,55 @@ void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const 
     }
     gy = gx;
   }
-  const std::vector<double>& gD = gy;  // dE_i/dD, M x M_<
-  // dE/dT[p][q] = sum_l gD[p][l] T[l][q] + [p < M_<] sum_m gD[m][p] T[m][q]
+  const std::vector<double>& gD = gy;  // dE_i/dD
+  // se_e2_a block: dE/dT[p][q] = sum_l gD[p][l] T[l][q] + [p < M_<] sum_m gD[m][p] T[m][q]
   std::vector<double> gT((size_t)M * 4, 0.0);
-  for (int p = 0; p < M; ++p)
-    for (int q = 0; q < 4; ++q) {
-      double acc = 0.0;
-      for (int l = 0; l < A; ++l) acc += gD[(size_t)p * A + l] * T[(size_t)l * 4 + q];
-      if (p < A)
-        for (int mm = 0; mm < M; ++mm) acc += gD[(size_t)mm * A + p] * T[(size_t)mm * 4 + q];
-      gT[(size_t)p * 4 + q] = acc;
-    }
+  if (L.ang)
+    for (int p = 0; p < M; ++p)
+      for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int l = 0; l < A; ++l) acc += gD[(size_t)p * A + l] * T[(size_t)l * 4 + q];
+        if (p < A)
+          for (int mm = 0; mm < M; ++mm) acc += gD[(size_t)mm * A + p] * T[(size_t)mm * 4 + q];
+        gT[(size_t)p * 4 + q] = acc;
+      }
   for (int k = 0; k < nc * 3; ++k) gd[k] = 0.0;
   for (int k = 0; k < nc; ++k) {
     if (!valid[k]) continue;
+    const double r = rr[k], s = ss[k];
     // dE/dR_k[q] = (1/Nc) sum_m gT[m][q] G_k[m];  dE/dG_k[m] = (1/Nc) sum_q gT[m][q] R_k[q]
-    double gR[4];
-    for (int q = 0; q < 4; ++q) {
-      double acc = 0.0;
-      for (int mm = 0; mm < M; ++mm) acc += gT[(size_t)mm * 4 + q] * G[(size_t)k * M + mm];
-      gR[q] = acc / nc;
+    double gR[4] = {0.0, 0.0, 0.0, 0.0};
+    std::vector<double> gG1(M, 0.0), gG2(hyb ? Mr : 0, 0.0);
+    if (L.ang) {
+      for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int mm = 0; mm < M; ++mm) acc += gT[(size_t)mm * 4 + q] * Gang(k)[mm];
+        gR[q] = acc / nc;
+      }
+      for (int mm = 0; mm < M; ++mm) {
+        double acc = 0.0;
+        for (int q = 0; q < 4; ++q) acc += gT[(size_t)mm * 4 + q] * R[(size_t)k * 4 + q];
+        gG1[mm] = acc / nc;
+      }
     }
-    std::vector<double> gG(M);
-    for (int mm = 0; mm < M; ++mm) {
-      double acc = 0.0;
-      for (int q = 0; q < 4; ++q) acc += gT[(size_t)mm * 4 + q] * R[(size_t)k * 4 + q];
-      gG[mm] = acc / nc;
+    // se_e2_r block: dE/dG_k[m] = gD_r[m] s_k / Nc and dE/ds_k (direct) = sum_m gD_r[m] G_k[m] / Nc
+    double gs_direct = 0.0;
+    if (L.rad) {
+      std::vector<double>& gGr = hyb ? gG2 : gG1;
+      for (int mm = 0; mm < Mr; ++mm) {
+        const double g = gD[L.da + mm];
+        gGr[mm] += g * s / nc;
+        gs_direct += g * Grad(k)[mm] / nc;
+      }
     }
-    double gs_embed;
-    if (!tab) {
-      gs_embed = embed_backward(c, L, params, netk[k], ss[k], act[k], outs[k], gG);
-    } else {
-      gs_embed = 0.0;
-      for (int mm = 0; mm < M; ++mm) gs_embed += gG[mm] * dG[(size_t)k * M + mm];
-    }
+    double gs_embed = embed_row_backward(L.e1, params, tab, netk[k], e1[k], gG1);
+    if (hyb) gs_embed += embed_row_backward(L.e2, params, nullptr, netk[k], e2[k], gG2);
     // chain through R_k = (s, s u) with u = d / r, and s = s(r), r = |d|
-    double r = rr[k], s = ss[k];
     double sp = switch_deriv(r, rs, rc);
     const double* d = &dvec[(size_t)k * 3];
     double u[3] = {d[0] / r, d[1] / r, d[2] / r};
     double gvu = gR[1] * u[0] + gR[2] * u[1] + gR[3] * u[2];
-    double gs = gs_embed + gR[0] + gvu;  // total dE/ds at fixed u
+    double gs = gs_embed + gs_direct + gR[0] + gvu;  // total dE/ds at fixed u
     for (int a = 0; a < 3; ++a) gd[(size_t)k * 3 + a] = sp * gs * u[a] + (s / r) * (gR[1 + a] - gvu * u[a]);
   }
 }
@@ -548,13 +629,27 @@ void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const 
 // Templated energy (for the dual-number pins only): same definitions, generic scalar.
 // ------------------------------------------------------------------------------------------
 template <class T, class P>
+std::vector<T> embed_generic(const NetSet& S, const P* params, int net, T s) {
+  std::vector<T> x(1, s), y;
+  for (int l = 0; l < S.nl; ++l) {
+    const P* W = params + S.off[(size_t)net * S.nl + l];
+    y.assign(S.out[l], T(0.0));
+    layer_forward(W, W + (long)S.in[l] * S.out[l], S.in[l], S.out[l], x.data(), y.data(), true, true);
+    x = y;
+  }
+  return x;
+}
+
+template <class T, class P>
 T energy_generic(const OrcConfig& c, const Layout& L, const P* params, int N, const T* coord, const int* type,
                  const T* box, const int* nl_j, const int* nl_code, T* atom_e) {
   const int nc = L.nc, M = L.m, A = L.axis;
+  const NetSet& Sr = L.radial();
+  const int Mr = L.rad ? Sr.m : 0;
   T E(0.0);
   for (int i = 0; i < N; ++i) {
     int ai = type[i];
-    std::vector<T> Tm((size_t)M * 4, T(0.0));
+    std::vector<T> Tm((size_t)M * 4, T(0.0)), Dr(Mr, T(0.0));
     for (int t = 0; t < c.ntypes; ++t)
       for (int q = 0; q < c.sel[t]; ++q) {
         int k = L.sel_off[t] + q;
@@ -572,24 +667,27 @@ T energy_generic(const OrcConfig& c, const Layout& L, const P* params, int N, co
         T s = switch_fn(r, c.rcut_smth, c.rcut);
         T Rk[4] = {s, s * d[0] / r, s * d[1] / r, s * d[2] / r};
         int net = embed_net_index(c, ai, t);
-        std::vector<T> x(1, s), y;
-        for (int l = 0; l < c.n_embed; ++l) {
-          const P* W = params + L.eoff[(size_t)net * c.n_embed + l];
-          y.assign(L.eout[l], T(0.0));
-          layer_forward(W, W + (long)L.ein[l] * L.eout[l], L.ein[l], L.eout[l], x.data(), y.data(), true, true);
-          x = y;
+        if (L.ang) {
+          std::vector<T> g = embed_generic<T, P>(L.e1, params, net, s);
+          for (int mm = 0; mm < M; ++mm)
+            for (int qq = 0; qq < 4; ++qq) Tm[(size_t)mm * 4 + qq] = Tm[(size_t)mm * 4 + qq] + g[mm] * Rk[qq];
         }
-        for (int mm = 0; mm < M; ++mm)
-          for (int q = 0; q < 4; ++q) Tm[(size_t)mm * 4 + q] = Tm[(size_t)mm * 4 + q] + x[mm] * Rk[q];
+        if (L.rad) {
+          std::vector<T> g = embed_generic<T, P>(Sr, params, net, s);
+          for (int mm = 0; mm < Mr; ++mm) Dr[mm] = Dr[mm] + g[mm] * s;
+        }
       }
-    for (auto& v : Tm) v = v / T((double)nc);
-    std::vector<T> x((size_t)M * A);
-    for (int mm = 0; mm < M; ++mm)
-      for (int l = 0; l < A; ++l) {
-        T acc(0.0);
-        for (int q = 0; q < 4; ++q) acc = acc + Tm[(size_t)mm * 4 + q] * Tm[(size_t)l * 4 + q];
-        x[(size_t)mm * A + l] = acc;
-      }
+    std::vector<T> x(L.dw, T(0.0));
+    if (L.ang) {
+      for (auto& v : Tm) v = v / T((double)nc);
+      for (int mm = 0; mm < M; ++mm)
+        for (int l = 0; l < A; ++l) {
+          T acc(0.0);
+          for (int qq = 0; qq < 4; ++qq) acc = acc + Tm[(size_t)mm * 4 + qq] * Tm[(size_t)l * 4 + qq];
+          x[(size_t)mm * A + l] = acc;
+        }
+    }
+    for (int mm = 0; mm < Mr; ++mm) x[L.da + mm] = Dr[mm] / T((double)nc);
     const int nfl = (int)L.fin.size();
     for (int l = 0; l < nfl; ++l) {
       const P* W = params + L.foff[(size_t)ai * nfl + l];
@@ -605,13 +703,14 @@ T energy_generic(const OrcConfig& c, const Layout& L, const P* params, int N, co
 }
 
 // Node values y, y', y'' of every output of embedding net `net` at input s (second-order jets).
-void embed_jets(const OrcConfig& c, const Layout& L, const double* params, int net, double s, double* y, double* y1,
+void embed_jets(const Layout& L, const double* params, int net, double s, double* y, double* y1,
                 double* y2) {
+  const NetSet& S = L.e1;
   std::vector<Jet> x(1, Jet(s, 1.0, 0.0));
-  for (int l = 0; l < c.n_embed; ++l) {
-    const double* W = params + L.eoff[(size_t)net * c.n_embed + l];
-    const double* b = W + (long)L.ein[l] * L.eout[l];
-    int ni = L.ein[l], no = L.eout[l];
+  for (int l = 0; l < S.nl; ++l) {
+    const double* W = params + S.off[(size_t)net * S.nl + l];
+    const double* b = W + (long)S.in[l] * S.out[l];
+    int ni = S.in[l], no = S.out[l];
     int sk = skip_kind(ni, no);
     std::vector<Jet> yv(no);
     for (int o = 0; o < no; ++o) {
@@ -673,7 +772,7 @@ void orc_embed_jets(const OrcConfig* c, const double* params, int net, int n, co
                     double* y1, double* y2) {
   Layout L = make_layout(*c);
   for (int q = 0; q < n; ++q)
-    embed_jets(*c, L, params, net, xs[q], y + (size_t)q * L.m, y1 + (size_t)q * L.m, y2 + (size_t)q * L.m);
+    embed_jets(L, params, net, xs[q], y + (size_t)q * L.m, y1 + (size_t)q * L.m, y2 + (size_t)q * L.m);
 }
 
 // Quintic table over nodes x_0 .. x_{n1+n2}: first n1 intervals of width stride1 from s0,
@@ -686,7 +785,7 @@ void orc_table_build(const OrcConfig* c, const double* params, double s0, double
   std::vector<double> y((size_t)(lc + 1) * M), y1(y.size()), y2(y.size());
   for (int net = 0; net < L.n_embed_nets; ++net) {
     for (int l = 0; l <= lc; ++l)
-      embed_jets(*c, L, params, net, tb.node(l), &y[(size_t)l * M], &y1[(size_t)l * M], &y2[(size_t)l * M]);
+      embed_jets(L, params, net, tb.node(l), &y[(size_t)l * M], &y1[(size_t)l * M], &y2[(size_t)l * M]);
     for (int l = 0; l < lc; ++l) {
       double dx = tb.node(l + 1) - tb.node(l);
       for (int mm = 0; mm < M; ++mm) {

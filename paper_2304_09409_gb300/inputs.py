@@ -76,6 +76,8 @@ class ModelConfig:
     axis: int                     # M_<
     fit: Tuple[int, ...]          # fitting net hidden widths; a final width-1 linear layer is implied
     type_one_side: int = 0        # 0: nets N^{a_i,a_j}; 1: nets N^{a_j}
+    descriptor: int = 0           # 0: se_e2_a; 1: se_e2_r; 2: hybrid of se_e2_a and se_e2_r on one list
+    embed_r: Tuple[int, ...] = () # hybrid: the se_e2_r part's embedding net widths
 
     @property
     def nc(self) -> int:
@@ -91,20 +93,36 @@ class ModelConfig:
 
     @property
     def descriptor_dim(self) -> int:
+        """Width of D: M * M_< (se_e2_a), M (se_e2_r), or their sum (hybrid)."""
+        if self.descriptor == 1:
+            return self.m
+        if self.descriptor == 2:
+            return self.m * self.axis + int(self.embed_r[-1])
         return self.m * self.axis
 
     def embed_layer_shapes(self) -> List[Tuple[int, int]]:
         dims = [1] + list(self.embed)
         return [(dims[k], dims[k + 1]) for k in range(len(self.embed))]
 
+    def embed_r_layer_shapes(self) -> List[Tuple[int, int]]:
+        """Layer shapes of the hybrid's se_e2_r nets (empty for the other descriptors)."""
+        if self.descriptor != 2:
+            return []
+        dims = [1] + list(self.embed_r)
+        return [(dims[k], dims[k + 1]) for k in range(len(self.embed_r))]
+
+    def embed_params(self) -> int:
+        """Parameters of all embedding nets (those of `embed`, then the hybrid's se_e2_r nets)."""
+        per = sum(a * b + b for a, b in self.embed_layer_shapes() + self.embed_r_layer_shapes())
+        return self.n_embed_nets * per
+
     def fit_layer_shapes(self) -> List[Tuple[int, int]]:
         dims = [self.descriptor_dim] + list(self.fit) + [1]
         return [(dims[k], dims[k + 1]) for k in range(len(dims) - 1)]
 
     def n_params(self) -> int:
-        ne = sum(a * b + b for a, b in self.embed_layer_shapes())
         nf = sum(a * b + b for a, b in self.fit_layer_shapes())
-        return self.n_embed_nets * ne + self.ntypes * nf
+        return self.embed_params() + self.ntypes * nf
 
 
 def water_model() -> ModelConfig:
@@ -119,16 +137,32 @@ def metal_model() -> ModelConfig:
                        fit=(240, 240, 240))
 
 
+def water_model_r() -> ModelConfig:
+    """Water-like se_e2_r model: the water model's list (r_c 6, r_s 0.5, sel [46, 92]) with
+    embedding 10/20/40 and the same fitting net (D has 40 values)."""
+    return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92), embed=(10, 20, 40), axis=0,
+                       fit=(240, 240, 240), descriptor=1)
+
+
+def water_model_hybrid() -> ModelConfig:
+    """Water-like hybrid model on the water model's list: the se_e2_a part of the water model
+    (embedding 25/50/100, M_< 16) and an se_e2_r part with embedding 10/20/40 (D has 1640 values)."""
+    return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92), embed=(25, 50, 100), axis=16,
+                       fit=(240, 240, 240), descriptor=2, embed_r=(10, 20, 40))
+
+
 def make_params(cfg: ModelConfig, seed: int = 0) -> np.ndarray:
     """Xavier-normal weights W ~ N(0, 2/(fan_in+fan_out)) and biases b ~ N(0, 1), FP64, flat.
 
     Layout (shared by every consumer): embedding nets in order of net index
-    (a_i * ntypes + a_j, or a_j when type_one_side), then fitting nets by type; inside a
-    net, layer by layer, W row-major [in][out] followed by b [out].
+    (a_i * ntypes + a_j, or a_j when type_one_side), then (hybrid only) the se_e2_r
+    embedding nets in the same order, then fitting nets by type; inside a net, layer by
+    layer, W row-major [in][out] followed by b [out].
     """
     rng = Rng(seed)
     out = []
-    nets = [(cfg.embed_layer_shapes(), cfg.n_embed_nets), (cfg.fit_layer_shapes(), cfg.ntypes)]
+    nets = [(cfg.embed_layer_shapes(), cfg.n_embed_nets), (cfg.embed_r_layer_shapes(), cfg.n_embed_nets),
+            (cfg.fit_layer_shapes(), cfg.ntypes)]
     for shapes, count in nets:
         for _ in range(count):
             for fi, fo in shapes:
@@ -153,7 +187,7 @@ def force_scaled(cfg: ModelConfig, params: np.ndarray, scale: float) -> np.ndarr
     weights and its bias -- multiplied by `scale`: atomic energies, forces and virials all
     scale by exactly that factor, while every other layer is unchanged."""
     out = np.array(params, dtype=np.float64, copy=True)
-    off = cfg.n_embed_nets * sum(a * b + b for a, b in cfg.embed_layer_shapes())
+    off = cfg.embed_params()
     shapes = cfg.fit_layer_shapes()
     per_type = sum(a * b + b for a, b in shapes)
     last_in = shapes[-1][0]

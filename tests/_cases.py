@@ -21,3 +21,15 @@ def tiny_frame(seed: int = 3, n: int = 14, triclinic: bool = True) -> I.Frame:
 
 def scaled_params(cfg, seed=0, scale=1.0):
     return I.make_params(cfg, seed) * scale
+
+
+def tiny_model_r(type_one_side: int = 0) -> I.ModelConfig:
+    """The tiny model's list and fitting net with the se_e2_r descriptor (embedding 4/8/16)."""
+    return I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(4, 8, 16), axis=0,
+                         fit=(12, 12), type_one_side=type_one_side, descriptor=1)
+
+
+def tiny_model_hybrid(type_one_side: int = 0) -> I.ModelConfig:
+    """The tiny model with an se_e2_r part (embedding 3/6/12) beside its se_e2_a part."""
+    return I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(4, 8, 16), axis=4,
+                         fit=(12, 12), type_one_side=type_one_side, descriptor=2, embed_r=(3, 6, 12))
