@@ -66,9 +66,21 @@ extern "C" {
 #define DP_MAX_LAYERS 8
 #define DP_MAX_CANDIDATES 1024 /* atoms within r_c of one atom the list builder can hold */
 
+/* Descriptors (Sec. II.A.1) */
+#define DP_DESC_SE_E2_A 0 /* D = T T_<^T, T = G^T R / Nc, R rows (s, s x/r, s y/r, s z/r): M x M_<   */
+#define DP_DESC_SE_E2_R 1 /* R reduced to its radial column s: D = G^T s / Nc, M values            */
+#define DP_DESC_HYBRID 2  /* [se_e2_a block, se_e2_r block] concatenated; both parts share r_c, r_s,
+                             sel (one neighbour list) and the net index rule, each with its own
+                             embedding nets (embed[] for se_e2_a, embed_r[] for se_e2_r)        */
+
 /* Model hyper-parameters (Sec. II.A.1, II.A.2, II.A.6).  embed[] are the embedding-net
  * widths (input width 1 is implied), fit[] the fitting-net hidden widths (a final linear
- * width-1 layer is implied).  ResNet skips follow Eq. (NN) with w_hat = 1. */
+ * width-1 layer is implied).  ResNet skips follow Eq. (NN) with w_hat = 1.
+ * descriptor DP_DESC_SE_E2_R uses embed[] for its nets and ignores axis; DP_DESC_HYBRID adds
+ * the se_e2_r nets embed_r[] (n_embed_r layers).  The fitting-net input width is M * M_<,
+ * M, or M * M_< + M_r (M_r = embed_r[n_embed_r - 1]).  Models other than se_e2_a run on the
+ * CUDA-core path only (DP_PREC_FP64 / DP_PREC_FP32, uncompressed); other combinations are
+ * refused with DP_E_UNSUPPORTED at creation. */
 typedef struct {
   int ntypes;
   int sel[DP_MAX_TYPES];
@@ -80,6 +92,9 @@ typedef struct {
   int n_fit;
   int fit[DP_MAX_LAYERS];
   int type_one_side; /* 0: nets N^{a_i,a_j}; 1: nets N^{a_j} */
+  int descriptor;    /* DP_DESC_*; 0 for an se_e2_a model */
+  int n_embed_r;     /* DP_DESC_HYBRID: layers of the se_e2_r embedding nets */
+  int embed_r[DP_MAX_LAYERS];
 } dp_model_config;
 
 typedef struct dp_model dp_model;
@@ -87,8 +102,9 @@ typedef struct dp_nlist dp_nlist;
 
 /* Create a model on `device` from host FP64 parameters.
  *   params: host, n_params doubles.  Layout: embedding nets in order of net index
- *           (a_i*ntypes + a_j, or a_j if type_one_side), then fitting nets by type;
- *           per net, layer by layer, W row-major [in][out] then b[out].
+ *           (a_i*ntypes + a_j, or a_j if type_one_side), then (hybrid) the se_e2_r nets in
+ *           the same order, then fitting nets by type; per net, layer by layer, W
+ *           row-major [in][out] then b[out].
  *   precision: DP_PREC_*.  compressed: 1 = replace the embedding nets by quintic
  *           tables (Eq. (compress)) built on the device at creation, over s in
  *           [0, 2] with stride 0.01 on [0, 1.8) and 0.1 on [1.8, 2].
@@ -97,8 +113,9 @@ typedef struct dp_nlist dp_nlist;
 int dp_model_create(const dp_model_config* cfg, const double* params, long n_params, int device, int precision,
                     int compressed, dp_model** out);
 
-/* Same as dp_model_create, reading a weight file: 8-byte magic "DPGBW001", the
- * dp_model_config struct as stored in memory, an int64 n_params, then n_params FP64. */
+/* Same as dp_model_create, reading a weight file: 8-byte magic "DPGBW002", the
+ * dp_model_config struct as stored in memory, an int64 n_params, then n_params FP64.
+ * Files with magic "DPGBW001" hold the struct without its last three fields (se_e2_a). */
 int dp_init_model(const char* weight_path, int device, int precision, int compressed, dp_model** out);
 
 int dp_free_model(dp_model* model);

@@ -1,6 +1,7 @@
 // C ABI of libdpgb: model and neighbour-list objects, scratch management, and the
 // per-frame driver that chains the kernels of the se_e2_a path.
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -54,26 +55,46 @@ int check_config(const dp_model_config* c) {
     if (c->embed[l] < 1) return DP_E_ARG;
   for (int l = 0; l < c->n_fit; ++l)
     if (c->fit[l] < 1) return DP_E_ARG;
-  if (c->axis < 1 || c->axis > c->embed[c->n_embed - 1]) return DP_E_ARG;
+  if (c->descriptor < DP_DESC_SE_E2_A || c->descriptor > DP_DESC_HYBRID) return DP_E_ARG;
+  if (c->descriptor != DP_DESC_SE_E2_R && (c->axis < 1 || c->axis > c->embed[c->n_embed - 1])) return DP_E_ARG;
+  if (c->descriptor == DP_DESC_HYBRID) {
+    if (c->n_embed_r < 1 || c->n_embed_r > DP_MAX_LAYERS) return DP_E_ARG;
+    for (int l = 0; l < c->n_embed_r; ++l)
+      if (c->embed_r[l] < 1) return DP_E_ARG;
+  }
   if (!(c->rcut > 0) || !(c->rcut_smth >= 0) || !(c->rcut_smth < c->rcut)) return DP_E_ARG;
   return DP_OK;
 }
 
-long layout(const dp_model_config& c, std::vector<LayerDesc>* emb, std::vector<LayerDesc>* fit) {
-  const int nets = c.type_one_side ? c.ntypes : c.ntypes * c.ntypes;
-  long off = 0;
+// Width of the descriptor D the fitting net reads (Sec. II.A.1).
+int descriptor_width(const dp_model_config& c) {
+  const int M = c.embed[c.n_embed - 1];
+  if (c.descriptor == DP_DESC_SE_E2_R) return M;
+  if (c.descriptor == DP_DESC_HYBRID) return M * c.axis + c.embed_r[c.n_embed_r - 1];
+  return M * c.axis;
+}
+
+void layout_nets(int nets, int nl, const int* widths, long& off, std::vector<LayerDesc>* emb) {
   for (int n = 0; n < nets; ++n) {
     int prev = 1;
-    for (int l = 0; l < c.n_embed; ++l) {
-      LayerDesc L{prev, c.embed[l], off, skip_kind(prev, c.embed[l]), 1};
+    for (int l = 0; l < nl; ++l) {
+      LayerDesc L{prev, widths[l], off, skip_kind(prev, widths[l]), 1};
       if (emb) emb->push_back(L);
-      off += (long)prev * c.embed[l] + c.embed[l];
-      prev = c.embed[l];
+      off += (long)prev * widths[l] + widths[l];
+      prev = widths[l];
     }
   }
-  const int M = c.embed[c.n_embed - 1];
+}
+
+// Parameter layout: nets of embed[], (hybrid) nets of embed_r[], fitting nets by type.
+long layout(const dp_model_config& c, std::vector<LayerDesc>* emb, std::vector<LayerDesc>* fit,
+            std::vector<LayerDesc>* emb_r = nullptr) {
+  const int nets = c.type_one_side ? c.ntypes : c.ntypes * c.ntypes;
+  long off = 0;
+  layout_nets(nets, c.n_embed, c.embed, off, emb);
+  if (c.descriptor == DP_DESC_HYBRID) layout_nets(nets, c.n_embed_r, c.embed_r, off, emb_r);
   for (int t = 0; t < c.ntypes; ++t) {
-    int prev = M * c.axis;
+    int prev = descriptor_width(c);
     for (int l = 0; l <= c.n_fit; ++l) {
       const bool last = (l == c.n_fit);
       const int no = last ? 1 : c.fit[l];
@@ -279,7 +300,7 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   m.device = device;
   m.precision = precision;
   m.compressed = compressed ? 1 : 0;
-  m.n_params = layout(*cfg, &m.emb, &m.fit);
+  m.n_params = layout(*cfg, &m.emb, &m.fit, &m.emb_r);
   m.n_fit_layers = cfg->n_fit + 1;
   if (n_params != m.n_params) {
     set_error("n_params does not match the configuration (" + std::to_string(m.n_params) + " expected)");
@@ -293,8 +314,16 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   }
   m.sel_off[cfg->ntypes] = m.nc;
   m.M = cfg->embed[cfg->n_embed - 1];
-  m.A = cfg->axis;
+  m.A = cfg->descriptor == DP_DESC_SE_E2_R ? 0 : cfg->axis;
+  m.Mr = cfg->descriptor == DP_DESC_SE_E2_A ? 0
+         : cfg->descriptor == DP_DESC_SE_E2_R ? m.M : cfg->embed_r[cfg->n_embed_r - 1];
+  m.Dw = descriptor_width(*cfg);
   m.n_embed_nets = cfg->type_one_side ? cfg->ntypes : cfg->ntypes * cfg->ntypes;
+  if (cfg->descriptor != DP_DESC_SE_E2_A && (compressed || precision > DP_PREC_FP32)) {
+    set_error("se_e2_r and hybrid models run uncompressed in FP64 or FP32");
+    delete md;
+    return DP_E_UNSUPPORTED;
+  }
   if (precision == DP_PREC_TF32 && compressed) {
     set_error("TF32 applies to the network GEMMs of the uncompressed model");
     delete md;
@@ -395,10 +424,15 @@ int dp_init_model(const char* path, int device, int precision, int compressed, d
   }
   char magic[8];
   dp_model_config cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
   long long n = 0;
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "DPGBW001", 8) == 0 &&
-            std::fread(&cfg, sizeof(cfg), 1, f) == 1 && std::fread(&n, sizeof(n), 1, f) == 1 && n > 0 &&
-            n < (1LL << 34);
+  bool ok = std::fread(magic, 1, 8, f) == 8;
+  // version 1 files hold the struct up to type_one_side (se_e2_a models)
+  const bool v1 = ok && std::memcmp(magic, "DPGBW001", 8) == 0;
+  ok = ok && (v1 || std::memcmp(magic, "DPGBW002", 8) == 0);
+  const size_t cfg_bytes = v1 ? offsetof(dp_model_config, descriptor) : sizeof(cfg);
+  ok = ok && std::fread(&cfg, 1, cfg_bytes, f) == cfg_bytes && std::fread(&n, sizeof(n), 1, f) == 1 && n > 0 &&
+       n < (1LL << 34);
   std::vector<double> p;
   if (ok) {
     p.resize((size_t)n);

@@ -92,8 +92,11 @@ struct DeviceModel {
   int precision;
   int compressed;
   int nc, M, A, n_embed_nets;
+  int Mr;  // width of the se_e2_r block of D (0 for se_e2_a)
+  int Dw;  // width of D: M * A, M (se_e2_r) or M * A + Mr (hybrid)
   int sel_off[DP_MAX_TYPES + 1];
-  std::vector<LayerDesc> emb;  // per net * n_embed + layer
+  std::vector<LayerDesc> emb;    // per net * n_embed + layer
+  std::vector<LayerDesc> emb_r;  // hybrid: the se_e2_r nets, per net * n_embed_r + layer
   std::vector<LayerDesc> fit;  // per type * n_fit_layers + layer
   int n_fit_layers;
   long n_params;

@@ -283,6 +283,8 @@ PathConst make_pc(const DeviceModel& m, int N) {
   pc.nc = m.nc;
   pc.M = m.M;
   pc.A = m.A;
+  pc.Mr = m.Mr;
+  pc.Dw = m.Dw;
   pc.ntypes = m.cfg.ntypes;
   pc.type_one_side = m.cfg.type_one_side;
   for (int t = 0; t < m.cfg.ntypes; ++t) pc.sel[t] = m.cfg.sel[t];
@@ -667,6 +669,10 @@ int dp_param_grad(dp_model* md, int nframes, const int* natoms, const double* co
   if (g_virial && !boxes) {
     set_error("a virial seed needs periodic cells");
     return DP_E_ARG;
+  }
+  if (md->m.cfg.descriptor != DP_DESC_SE_E2_A) {
+    set_error("parameter gradients are implemented for se_e2_a models");
+    return DP_E_UNSUPPORTED;
   }
   const GradReq gr{g_energy, g_force, g_virial, grad};
   return run_frames(md, nullptr, nframes, natoms, coord, type, boxes, nullptr, nullptr, nullptr, nullptr,

@@ -1,9 +1,12 @@
-// The se_e2_a energy / force / virial path on CUDA cores (FP64 or FP32 networks).
+// The energy / force / virial path on CUDA cores (FP64 or FP32 networks), for the se_e2_a,
+// se_e2_r and hybrid descriptors.
 //
 // Steps (sorted-atom index p, neighbour slot k, row = p * Nc + k):
 //   env      R_k = (s, s u) with u = r_ij / r, s = s(r)            Eqs. (rij), (switch)
 //   emb      G_k = N^{a_i, a_j}(s) layer by layer                  Eqs. (G2), (NN)
 //   contract T = G^T R / Nc,  D = T T_<^T                          se_e2_a descriptor
+//            D_r = G_r^T s / Nc                                    se_e2_r descriptor
+//            (hybrid: D = [D_a, D_r], each part with its own nets) Sec. II.A.1
 //   fit      E_i = F^{a_i}(D)                                      Eq. (fitting_energy)
 //   backward dE/dD -> dE/dT -> (dE/dG, dE/dR) -> dE/ds -> dE/dr_ij
 //   force    F_i += dE/dr_ij, F_j -= dE/dr_ij (FP64 atomics)        Sec. II.A.2
@@ -63,10 +66,11 @@ __global__ void k_emb_first(PathConst pc, NetPtrs<R> nets, const int* __restrict
   T[e] = t;
 }
 
+// dE/ds through the first layer; `accum` adds to gs (a second embedding family of a hybrid).
 template <class R>
 __global__ void k_emb_first_bwd(PathConst pc, NetPtrs<R> nets, const int* __restrict__ atom_type_sorted,
                                 const R* __restrict__ GY, const R* __restrict__ T, int w1, int skip,
-                                R* __restrict__ gs) {
+                                R* __restrict__ gs, int accum) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= (long)pc.natoms * pc.nc) return;
   const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
@@ -79,7 +83,7 @@ __global__ void k_emb_first_bwd(PathConst pc, NetPtrs<R> nets, const int* __rest
     acc += g * (R(1) - t * t) * w[o];
     if (skip) acc += g;
   }
-  gs[row] = acc;
+  gs[row] = accum ? gs[row] + acc : acc;
 }
 
 // ---- T = G^T R / Nc and D = T T_<^T, one block per atom -------------------------------------
@@ -115,7 +119,7 @@ __global__ void k_contract(PathConst pc, const R* __restrict__ G, const R* __res
   __syncthreads();
   for (int idx = threadIdx.x; idx < M * A; idx += blockDim.x) {
     const int m = idx / A, l = idx % A;
-    D[(long)p * M * A + idx] =
+    D[(long)p * pc.Dw + idx] =
         Ts[m * 4] * Ts[l * 4] + Ts[m * 4 + 1] * Ts[l * 4 + 1] + Ts[m * 4 + 2] * Ts[l * 4 + 2] + Ts[m * 4 + 3] * Ts[l * 4 + 3];
   }
 }
@@ -132,7 +136,7 @@ __global__ void k_descr_bwd(PathConst pc, const R* __restrict__ Tm, const R* __r
   R* gDs = gTs + M * 4;                  // [M][A]
   const int p = blockIdx.x;
   for (int e = threadIdx.x; e < M * 4; e += blockDim.x) Ts[e] = Tm[(long)p * M * 4 + e];
-  for (int e = threadIdx.x; e < M * A; e += blockDim.x) gDs[e] = gD[(long)p * M * A + e];
+  for (int e = threadIdx.x; e < M * A; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + e];
   __syncthreads();
   for (int e = threadIdx.x; e < M * 4; e += blockDim.x) {
     const int m = e / 4, c = e % 4;
@@ -166,6 +170,57 @@ __global__ void k_descr_bwd(PathConst pc, const R* __restrict__ Tm, const R* __r
     }
     if (lane == 0)
       reinterpret_cast<typename Vec4<R>::T*>(gR)[row] = Vec4<R>::make(a0 * inv_nc, a1 * inv_nc, a2 * inv_nc, a3 * inv_nc);
+  }
+}
+
+// ---- se_e2_r block: D_r[m] = (1/Nc) sum_k G_r[k][m] s_k, one block per atom -------------------
+// G rows hold Mr values; D_r is written at column `off` of D (row stride Dw).
+template <class R>
+__global__ void k_contract_r(PathConst pc, const R* __restrict__ G, const R* __restrict__ Renv, int off,
+                             R* __restrict__ D) {
+  const int p = blockIdx.x;
+  const int Mr = pc.Mr, nc = pc.nc;
+  const long rb = (long)p * nc;
+  for (int m = threadIdx.x; m < Mr; m += blockDim.x) {
+    R acc = 0;
+    for (int k = 0; k < nc; ++k) acc += G[(rb + k) * Mr + m] * Renv[(rb + k) * 4];
+    D[(long)p * pc.Dw + off + m] = acc / R(nc);
+  }
+}
+
+// Reverse of k_contract_r: dE/dG_r[k][m] = gD_r[m] s_k / Nc into gG, and the direct term
+// dE/ds_k = sum_m gD_r[m] G_r[k][m] / Nc into the radial component of gR (added to what the
+// se_e2_a block wrote when `accum`, else gR = (term, 0, 0, 0)).  One block per atom, a warp per row.
+template <class R>
+__global__ void k_descr_bwd_r(PathConst pc, const R* __restrict__ gD, int off, const R* __restrict__ G,
+                              const R* __restrict__ Renv, R* __restrict__ gG, R* __restrict__ gR, int accum) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  R* gDs = reinterpret_cast<R*>(sm_raw);  // [Mr]
+  const int p = blockIdx.x;
+  const int Mr = pc.Mr, nc = pc.nc;
+  for (int e = threadIdx.x; e < Mr; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + off + e];
+  __syncthreads();
+  const R inv_nc = R(1) / R(nc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < nc; k += nw) {
+    const long row = (long)p * nc + k;
+    const R s = Renv[row * 4];
+    R acc = 0;
+    for (int m = lane; m < Mr; m += 32) {
+      acc += gDs[m] * G[row * Mr + m];
+      gG[row * Mr + m] = gDs[m] * s * inv_nc;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      typename Vec4<R>::T* g4 = reinterpret_cast<typename Vec4<R>::T*>(gR) + row;
+      if (accum) {
+        typename Vec4<R>::T v = *g4;
+        v.x += acc * inv_nc;
+        *g4 = v;
+      } else {
+        *g4 = Vec4<R>::make(acc * inv_nc, R(0), R(0), R(0));
+      }
+    }
   }
 }
 
@@ -278,9 +333,8 @@ template <class R>
 int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, const R* D, const PathIO& io, Arena& ar,
                 cudaStream_t st, const R** gD_out) {
   const long N = pc.natoms;
-  const int M = pc.M, A = pc.A;
   const int nfl = m.n_fit_layers;
-  int maxw = M * A;
+  int maxw = pc.Dw;
   for (int l = 0; l < nfl; ++l) maxw = std::max(maxw, m.fit[l].n_out);
   std::vector<R*> Yf(nfl), Tf(nfl);
   for (int l = 0; l < nfl; ++l) {
@@ -334,22 +388,40 @@ int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, cons
   return DP_OK;
 }
 
+// One family of embedding nets (the se_e2_a nets, or the se_e2_r nets of a hybrid): layer
+// descriptors, layer count and per-layer outputs / tanh values over all rows.
+template <class R>
+struct EmbFamily {
+  const std::vector<LayerDesc>* layers;
+  int nl;
+  std::vector<R*> Y, T;
+};
+
 template <class R>
 int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, const PathIO& io, Arena& ar,
                 cudaStream_t st) {
   const long N = pc.natoms, nc = pc.nc, rows = N * nc;
-  const int M = pc.M, A = pc.A, ne = m.cfg.n_embed;
+  const int M = pc.M, A = pc.A, desc = m.cfg.descriptor;
+  const bool ang = desc != DP_DESC_SE_E2_R, rad = desc != DP_DESC_SE_E2_A;
+  // family 0: nets of embed[] (se_e2_a, or se_e2_r alone); family 1: the hybrid's se_e2_r nets
+  const int nfam = desc == DP_DESC_HYBRID ? 2 : 1;
+  EmbFamily<R> fam[2];
+  fam[0].layers = &m.emb;
+  fam[0].nl = m.cfg.n_embed;
+  fam[1].layers = &m.emb_r;
+  fam[1].nl = m.cfg.n_embed_r;
   // ---- scratch ----
   R* Renv = ar.get<R>(rows * 4);
-  std::vector<R*> Ye(ne), Te(ne);
-  for (int l = 0; l < ne; ++l) {
-    Ye[l] = ar.get<R>(rows * m.cfg.embed[l]);
-    Te[l] = ar.get<R>(rows * m.cfg.embed[l]);
-  }
-  R* Tm = ar.get<R>(N * M * 4);
-  R* D = ar.get<R>(N * M * A);
   int maxe = 1;
-  for (int l = 0; l < ne; ++l) maxe = std::max(maxe, m.cfg.embed[l]);
+  for (int f = 0; f < nfam; ++f)
+    for (int l = 0; l < fam[f].nl; ++l) {
+      const int w = (*fam[f].layers)[l].n_out;
+      fam[f].Y.push_back(ar.get<R>(rows * w));
+      fam[f].T.push_back(ar.get<R>(rows * w));
+      maxe = std::max(maxe, w);
+    }
+  R* Tm = ang ? ar.get<R>(N * M * 4) : nullptr;
+  R* D = ar.get<R>(N * pc.Dw);
   R* geA = ar.get<R>(rows * maxe);
   R* geB = ar.get<R>(rows * maxe);
   R* gR = ar.get<R>(rows * 4);
@@ -371,68 +443,79 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     ProfScope _ps(io.prof, "env", st);
     k_env<R><<<nblk(rows, 256), 256, 0, st>>>(pc, io.coord, io.perm, io.nl_j, io.nl_code, Renv);
   }
-  NetPtrs<R> nets;
-  for (int n = 0; n < m.n_embed_nets; ++n) {
-    const LayerDesc& L0 = m.emb[(size_t)n * ne];
-    nets.w0[n] = params + L0.w_off;
-    nets.b0[n] = params + L0.w_off + (long)L0.n_in * L0.n_out;
-  }
-  {
-    const LayerDesc& L0 = m.emb[0];
+  NetPtrs<R> nets[2];
+  for (int f = 0; f < nfam; ++f) {
+    const std::vector<LayerDesc>& Ls = *fam[f].layers;
+    const int ne = fam[f].nl;
+    for (int n = 0; n < m.n_embed_nets; ++n) {
+      const LayerDesc& L0 = Ls[(size_t)n * ne];
+      nets[f].w0[n] = params + L0.w_off;
+      nets[f].b0[n] = params + L0.w_off + (long)L0.n_in * L0.n_out;
+    }
+    const LayerDesc& L0 = Ls[0];
     {
       ProfScope _ps(io.prof, "emb_first", st);
-      k_emb_first<R><<<nblk(rows * L0.n_out, 256), 256, 0, st>>>(pc, nets, tsorted, Renv, L0.n_out, L0.skip, Ye[0],
-                                                                    Te[0]);
+      k_emb_first<R><<<nblk(rows * L0.n_out, 256), 256, 0, st>>>(pc, nets[f], tsorted, Renv, L0.n_out, L0.skip,
+                                                                    fam[f].Y[0], fam[f].T[0]);
     }
-  }
-  for (int ti = 0; ti < pc.ntypes; ++ti)
-    for (int tj = 0; tj < pc.ntypes; ++tj) {
-      const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
-      RowMap rm{1, 0, io.type_start[ti], pc.sel[tj], pc.sel_off[tj], (int)nc,
-                (io.type_start[ti + 1] - io.type_start[ti]) * pc.sel[tj]};
-      for (int l = 1; l < ne; ++l) {
-        const LayerDesc& L = m.emb[(size_t)net * ne + l];
-        const R* W = params + L.w_off;
-        {
-          ProfScope _ps(io.prof, "emb_fwd", st);
-          DP_CUDA_TRY(launch_dense_fwd<R>(rm, Ye[l - 1], L.n_in, W, W + (long)L.n_in * L.n_out, L.n_out, L.skip, 1,
-                                          Ye[l], Te[l], st));
-        }
-      }
-    }
-  const R* G = Ye[ne - 1];
-  {
-    ProfScope _ps(io.prof, "contract", st);
-    k_contract<R><<<(unsigned)N, 128, sizeof(R) * M * 4, st>>>(pc, G, Renv, Tm, D);
-  }
-  int rc = run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
-  if (rc != DP_OK) return rc;
-  {
-    ProfScope _ps(io.prof, "descr_bwd", st);
-    k_descr_bwd<R><<<(unsigned)N, 128, sizeof(R) * (M * 8 + M * A), st>>>(pc, Tm, gD, G, Renv, geA, gR);
-  }
-  // ---- backward through the embedding nets ----
-  R* gy = geA;
-  R* gx = geB;
-  for (int l = ne - 1; l >= 1; --l) {
     for (int ti = 0; ti < pc.ntypes; ++ti)
       for (int tj = 0; tj < pc.ntypes; ++tj) {
         const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
         RowMap rm{1, 0, io.type_start[ti], pc.sel[tj], pc.sel_off[tj], (int)nc,
                   (io.type_start[ti + 1] - io.type_start[ti]) * pc.sel[tj]};
-        const LayerDesc& L = m.emb[(size_t)net * ne + l];
-        {
-          ProfScope _ps(io.prof, "emb_bwd", st);
-          DP_CUDA_TRY(launch_dense_bwd<R>(rm, gy, Te[l], L.n_in, params + L.w_off, L.n_out, L.skip, gx, st));
+        for (int l = 1; l < ne; ++l) {
+          const LayerDesc& L = Ls[(size_t)net * ne + l];
+          const R* W = params + L.w_off;
+          ProfScope _ps(io.prof, "emb_fwd", st);
+          DP_CUDA_TRY(launch_dense_fwd<R>(rm, fam[f].Y[l - 1], L.n_in, W, W + (long)L.n_in * L.n_out, L.n_out, L.skip,
+                                          1, fam[f].Y[l], fam[f].T[l], st));
         }
       }
-    std::swap(gy, gx);
   }
-  {
-    const LayerDesc& L0 = m.emb[0];
+  const R* Ga = fam[0].Y[fam[0].nl - 1];
+  const R* Gr = fam[nfam - 1].Y[fam[nfam - 1].nl - 1];
+  const int da = ang ? M * A : 0;
+  if (ang) {
+    ProfScope _ps(io.prof, "contract", st);
+    k_contract<R><<<(unsigned)N, 128, sizeof(R) * M * 4, st>>>(pc, Ga, Renv, Tm, D);
+  }
+  if (rad) {
+    ProfScope _ps(io.prof, "contract_r", st);
+    k_contract_r<R><<<(unsigned)N, 64, 0, st>>>(pc, Gr, Renv, da, D);
+  }
+  int rc = run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
+  if (rc != DP_OK) return rc;
+  // ---- backward: per family, descriptor block -> dE/dG -> embedding layers -> dE/ds ----
+  for (int f = 0; f < nfam; ++f) {
+    const bool fam_ang = ang && f == 0;  // the se_e2_a block reads family 0 when present
+    const std::vector<LayerDesc>& Ls = *fam[f].layers;
+    const int ne = fam[f].nl;
+    if (fam_ang) {
+      ProfScope _ps(io.prof, "descr_bwd", st);
+      k_descr_bwd<R><<<(unsigned)N, 128, sizeof(R) * (M * 8 + M * A), st>>>(pc, Tm, gD, Ga, Renv, geA, gR);
+    } else {
+      ProfScope _ps(io.prof, "descr_bwd_r", st);
+      k_descr_bwd_r<R><<<(unsigned)N, 128, sizeof(R) * pc.Mr, st>>>(pc, gD, da, Gr, Renv, geA, gR, ang ? 1 : 0);
+    }
+    R* gy = geA;
+    R* gx = geB;
+    for (int l = ne - 1; l >= 1; --l) {
+      for (int ti = 0; ti < pc.ntypes; ++ti)
+        for (int tj = 0; tj < pc.ntypes; ++tj) {
+          const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
+          RowMap rm{1, 0, io.type_start[ti], pc.sel[tj], pc.sel_off[tj], (int)nc,
+                    (io.type_start[ti + 1] - io.type_start[ti]) * pc.sel[tj]};
+          const LayerDesc& L = Ls[(size_t)net * ne + l];
+          ProfScope _ps(io.prof, "emb_bwd", st);
+          DP_CUDA_TRY(launch_dense_bwd<R>(rm, gy, fam[f].T[l], L.n_in, params + L.w_off, L.n_out, L.skip, gx, st));
+        }
+      std::swap(gy, gx);
+    }
+    const LayerDesc& L0 = Ls[0];
     {
       ProfScope _ps(io.prof, "emb_first_bwd", st);
-      k_emb_first_bwd<R><<<nblk(rows, 256), 256, 0, st>>>(pc, nets, tsorted, gy, Te[0], L0.n_out, L0.skip, gs);
+      k_emb_first_bwd<R><<<nblk(rows, 256), 256, 0, st>>>(pc, nets[f], tsorted, gy, fam[f].T[0], L0.n_out, L0.skip, gs,
+                                                          f > 0 ? 1 : 0);
     }
   }
   // ---- forces and virial ----

@@ -18,6 +18,8 @@ struct PathConst {
   int nframes;
   const int* atom_frame;  // device [natoms] frame of each atom, or null (one frame)
   const double* boxes;    // device [frames][9] cell rows, or null (one frame: h)
+  int Mr;                 // width of the se_e2_r block of D (0: none)
+  int Dw;                 // width of D (row stride of D and dE/dD)
 };
 
 // Per-kernel CUDA-event timing and launch counting.  Every kernel launch of the path sits in

@@ -55,6 +55,9 @@ class Config(ctypes.Structure):
         ("n_fit", ctypes.c_int),
         ("fit", ctypes.c_int * 8),
         ("type_one_side", ctypes.c_int),
+        ("descriptor", ctypes.c_int),
+        ("n_embed_r", ctypes.c_int),
+        ("embed_r", ctypes.c_int * 8),
     ]
 
     @classmethod
@@ -73,6 +76,11 @@ class Config(ctypes.Structure):
         for k, v in enumerate(cfg.fit):
             c.fit[k] = int(v)
         c.type_one_side = int(getattr(cfg, "type_one_side", 0))
+        c.descriptor = int(getattr(cfg, "descriptor", 0))
+        embed_r = tuple(getattr(cfg, "embed_r", ()))
+        c.n_embed_r = len(embed_r)
+        for k, v in enumerate(embed_r):
+            c.embed_r[k] = int(v)
         return c
 
 
@@ -175,7 +183,7 @@ class NList:
 
 
 class Model:
-    """A se_e2_a model resident on one GPU."""
+    """A Deep Potential model (se_e2_a, se_e2_r or hybrid descriptor) resident on one GPU."""
 
     def __init__(self, cfg, params: np.ndarray, device: int = 0, precision: str = "fp64", compressed: bool = False):
         self.cfg = cfg
@@ -428,7 +436,7 @@ def write_weight_file(path: str, cfg, params: np.ndarray) -> None:
     c = Config.from_model(cfg)
     p = np.ascontiguousarray(params, dtype=np.float64)
     with open(path, "wb") as fh:
-        fh.write(b"DPGBW001")
+        fh.write(b"DPGBW002")
         fh.write(bytes(c))
         fh.write(np.int64(p.size).tobytes())
         fh.write(p.tobytes())

@@ -180,6 +180,9 @@ def make_params(cfg: ModelConfig, seed: int = 0) -> np.ndarray:
 # eV/A (1e-3 eV/A for the mixed-precision path) are only meaningful at that force scale.
 WATER_FORCE_SCALE = 2000.0
 METAL_FORCE_SCALE = 1.2e5
+# the same for the water-like se_e2_r model (seed 0: 4.4e-3 eV/A RMS) and hybrid model (9.2e-4)
+WATER_R_FORCE_SCALE = 230.0
+WATER_HYBRID_FORCE_SCALE = 1100.0
 
 
 def force_scaled(cfg: ModelConfig, params: np.ndarray, scale: float) -> np.ndarray:
@@ -201,6 +204,18 @@ def water_params_scaled(seed: int = 0) -> np.ndarray:
     """The water model's parameters with forces of about 1 eV/A RMS."""
     cfg = water_model()
     return force_scaled(cfg, make_params(cfg, seed), WATER_FORCE_SCALE)
+
+
+def water_r_params_scaled(seed: int = 0) -> np.ndarray:
+    """The water-like se_e2_r model's parameters with forces of about 1 eV/A RMS."""
+    cfg = water_model_r()
+    return force_scaled(cfg, make_params(cfg, seed), WATER_R_FORCE_SCALE)
+
+
+def water_hybrid_params_scaled(seed: int = 0) -> np.ndarray:
+    """The water-like hybrid model's parameters with forces of about 1 eV/A RMS."""
+    cfg = water_model_hybrid()
+    return force_scaled(cfg, make_params(cfg, seed), WATER_HYBRID_FORCE_SCALE)
 
 
 def metal_params_scaled(seed: int = 0) -> np.ndarray:

@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
 def test_n_params_matches_inputs_layout():
     from paper_2304_09409_gb300 import dpgb
     from paper_2304_09409_gb300 import inputs as I
-    for cfg in (I.water_model(), I.metal_model()):
+    for cfg in (I.water_model(), I.metal_model(), I.water_model_r(), I.water_model_hybrid()):
         assert dpgb.n_params(cfg) == cfg.n_params()
 
 
@@ -46,7 +46,21 @@ def test_weight_file_roundtrip_header(tmp_path):
     path = tmp_path / "w.bin"
     dpgb.write_weight_file(str(path), cfg, p)
     raw = path.read_bytes()
-    assert raw[:8] == b"DPGBW001"
+    assert raw[:8] == b"DPGBW002"
     n = ctypes.sizeof(dpgb.Config)
     assert np.frombuffer(raw[8 + n: 16 + n], dtype=np.int64)[0] == p.size
     np.testing.assert_array_equal(np.frombuffer(raw[16 + n:], dtype=np.float64), p)
+
+
+def test_config_checks_descriptor_fields():
+    """dp_model_n_params is host-only: it refuses unknown descriptors and a hybrid without
+    se_e2_r nets, and accepts se_e2_r without M_<."""
+    import dataclasses
+    from paper_2304_09409_gb300 import dpgb
+    from paper_2304_09409_gb300 import inputs as I
+    hyb = I.water_model_hybrid()
+    assert dpgb.n_params(hyb) == hyb.n_params()
+    assert dpgb.n_params(dataclasses.replace(hyb, embed_r=())) == -1
+    assert dpgb.n_params(dataclasses.replace(hyb, descriptor=3)) == -1
+    assert dpgb.n_params(dataclasses.replace(I.water_model_r(), axis=0)) == I.water_model_r().n_params()
+    assert dpgb.n_params(dataclasses.replace(I.water_model(), axis=0)) == -1
