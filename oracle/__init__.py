@@ -7,8 +7,8 @@ The C++ source (dp_oracle.cpp) restates the DeePMD-kit v2 paper (arXiv 2304.0940
 directly; see its header for the equation-by-equation map.  This wrapper only marshals
 numpy arrays.  Model configurations are duck-typed: any object with attributes
 ntypes, sel, rcut, rcut_smth, embed, axis, fit, type_one_side, and optionally descriptor
-(0 se_e2_a, 1 se_e2_r, 2 hybrid of the two on one neighbour list) and embed_r (the hybrid's
-se_e2_r embedding widths).
+(0 se_e2_a, 1 se_e2_r, 2 hybrid se_e2_a + se_e2_r, 3 se_e3, 4 hybrid se_e2_a + se_e3) with the
+hybrid's second part in rcut_2, rcut_smth_2, sel_2, embed_2.
 """
 from __future__ import annotations
 
@@ -59,8 +59,11 @@ class _Cfg(ctypes.Structure):
         ("fit", ctypes.c_int * 8),
         ("type_one_side", ctypes.c_int),
         ("descriptor", ctypes.c_int),
-        ("n_embed_r", ctypes.c_int),
-        ("embed_r", ctypes.c_int * 8),
+        ("rcut_2", ctypes.c_double),
+        ("rcut_smth_2", ctypes.c_double),
+        ("sel_2", ctypes.c_int * 8),
+        ("n_embed_2", ctypes.c_int),
+        ("embed_2", ctypes.c_int * 8),
     ]
 
 
@@ -113,10 +116,16 @@ def _cfg(cfg) -> _Cfg:
         c.fit[k] = int(v)
     c.type_one_side = int(getattr(cfg, "type_one_side", 0))
     c.descriptor = int(getattr(cfg, "descriptor", 0))
-    embed_r = tuple(getattr(cfg, "embed_r", ()))
-    c.n_embed_r = len(embed_r)
-    for k, v in enumerate(embed_r):
-        c.embed_r[k] = int(v)
+    if c.descriptor in (2, 4):  # hybrid: the second part's cutoffs, sel and nets
+        c.rcut_2 = float(getattr(cfg, "rcut_2", 0.0) or cfg.rcut)
+        c.rcut_smth_2 = float(getattr(cfg, "rcut_smth_2", 0.0) or cfg.rcut_smth)
+        sel_2 = tuple(getattr(cfg, "sel_2", ()) or cfg.sel)
+        for t, v in enumerate(sel_2):
+            c.sel_2[t] = int(v)
+        embed_2 = tuple(cfg.embed_2)
+        c.n_embed_2 = len(embed_2)
+        for k, v in enumerate(embed_2):
+            c.embed_2[k] = int(v)
     return c
 
 
@@ -167,7 +176,7 @@ def nlist(cfg, coord, atype, box):
     atype = _i32(atype)
     box = _f64(box)
     N = coord.shape[0]
-    nc = int(sum(cfg.sel))
+    nc = int(cfg.nc)
     nl_j = np.zeros((N, nc), dtype=np.int32)
     nl_s = np.zeros((N, nc, 3), dtype=np.int32)
     counts = np.zeros((N, cfg.ntypes), dtype=np.int32)
@@ -258,7 +267,7 @@ def atom_subset(cfg, params, coord, atype, box, idx):
     coord = _f64(coord)
     idx = _i32(np.atleast_1d(idx))
     S = idx.size
-    nc = int(sum(cfg.sel))
+    nc = int(cfg.nc)
     nl_j = np.zeros((S, nc), dtype=np.int32)
     nl_s = np.zeros((S, nc, 3), dtype=np.int32)
     e = np.zeros(S)

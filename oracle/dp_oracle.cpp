@@ -61,9 +61,13 @@ struct OrcConfig {
   int n_fit;
   int fit[8];
   int type_one_side;
-  int descriptor;  // 0: se_e2_a; 1: se_e2_r; 2: hybrid of se_e2_a and se_e2_r on one neighbour list
-  int n_embed_r;   // hybrid: layers of the se_e2_r part's embedding nets
-  int embed_r[8];
+  // 0 se_e2_a; 1 se_e2_r; 2 hybrid se_e2_a + se_e2_r; 3 se_e3; 4 hybrid se_e2_a + se_e3
+  int descriptor;
+  // hybrids: the second part's cutoffs, sel and embedding widths
+  double rcut_2, rcut_smth_2;
+  int sel_2[8];
+  int n_embed_2;
+  int embed_2[8];
 };
 
 }  // extern "C"
@@ -145,17 +149,32 @@ struct NetSet {
   std::vector<long> off;      // per net, per layer: offset of W (b follows W)
 };
 
+// One descriptor part (Sec. II.A.1): se_e2_a (A), se_e2_r (R) or se_e3 (E3), with its own
+// cutoffs, sel and embedding nets, writing the block [doff, doff + dwid) of D.
+enum { PART_A = 0, PART_R = 1, PART_E3 = 2 };
+struct Part {
+  int kind;
+  double rc, rs;
+  int sel[8], sel_off[9], nc;
+  NetSet nets;
+  int axis;        // A: M_<
+  int doff, dwid;
+};
+
 struct Layout {
-  int ntypes, nc, m, axis, n_embed_nets;
-  NetSet e1;                  // nets of `embed` (parameters from offset 0)
-  NetSet e2;                  // nets of `embed_r` (hybrid only), after those of e1
-  bool ang, rad;              // the descriptor has an se_e2_a block / an se_e2_r block
-  int da, dw;                 // width of the se_e2_a block of D; total width of D
-  std::vector<int> fin, fout; // fitting layer shapes (last has fout = 1)
-  std::vector<long> foff;     // per fitting net, per layer
-  int sel_off[9];
+  int ntypes;
+  // the neighbour list every part reads: cutoff and per-type sizes of the widest part
+  double lrc;
+  int lsel[8];
+  int nc, sel_off[9];
+  std::vector<Part> parts;
+  int dw;                      // width of D
+  // first part's nets (tables and jets are built for these)
+  NetSet e1;
+  int m, axis, n_embed_nets;
+  std::vector<int> fin, fout;  // fitting layer shapes (last has fout = 1)
+  std::vector<long> foff;      // per fitting net, per layer
   long n_params;
-  const NetSet& radial() const { return ang ? e2 : e1; }
 };
 
 void add_nets(NetSet& S, int nl, const int* widths, int nnets, long& off) {
@@ -167,30 +186,66 @@ void add_nets(NetSet& S, int nl, const int* widths, int nnets, long& off) {
     for (int l = 0; l < nl; ++l) { S.off.push_back(off); off += (long)S.in[l] * S.out[l] + S.out[l]; }
 }
 
+Part make_part(const OrcConfig& c, int kind, double rc, double rs, const int* sel, int nl, const int* widths,
+               long& off) {
+  Part P;
+  P.kind = kind;
+  P.rc = rc;
+  P.rs = rs;
+  P.nc = 0;
+  for (int t = 0; t < c.ntypes; ++t) { P.sel[t] = sel[t]; P.sel_off[t] = P.nc; P.nc += sel[t]; }
+  P.sel_off[c.ntypes] = P.nc;
+  // se_e3 nets are indexed by the two neighbours' types; the two-body nets by (a_i, a_j) or a_j
+  const int nnets = (kind == PART_E3 || !c.type_one_side) ? c.ntypes * c.ntypes : c.ntypes;
+  add_nets(P.nets, nl, widths, nnets, off);
+  P.axis = kind == PART_A ? c.axis : 0;
+  P.dwid = kind == PART_A ? P.nets.m * c.axis : P.nets.m;
+  return P;
+}
+
 // Sec. II.A.1: se_e2_a gives D = T T_<^T (M x M_<); se_e2_r, with only the radial column s of R,
-// gives D = G^T s / N_c (M values); the hybrid descriptor is the concatenation of the two.
+// gives D = G^T s / N_c (M values); se_e3 gives D = (R R^T) : G / N_c^2 (M values); a hybrid
+// descriptor is the concatenation of its parts.
 Layout make_layout(const OrcConfig& c) {
   Layout L;
   L.ntypes = c.ntypes;
-  L.nc = 0;
-  for (int t = 0; t < c.ntypes; ++t) { L.sel_off[t] = L.nc; L.nc += c.sel[t]; }
-  L.sel_off[c.ntypes] = L.nc;
-  L.axis = c.axis;
-  L.ang = c.descriptor != 1;
-  L.rad = c.descriptor != 0;
-  L.n_embed_nets = c.type_one_side ? c.ntypes : c.ntypes * c.ntypes;
   long off = 0;
-  add_nets(L.e1, c.n_embed, c.embed, L.n_embed_nets, off);
-  if (c.descriptor == 2) add_nets(L.e2, c.n_embed_r, c.embed_r, L.n_embed_nets, off);
+  const int d = c.descriptor;
+  const int k1 = (d == 1) ? PART_R : (d == 3 ? PART_E3 : PART_A);
+  L.parts.push_back(make_part(c, k1, c.rcut, c.rcut_smth, c.sel, c.n_embed, c.embed, off));
+  if (d == 2 || d == 4)
+    L.parts.push_back(make_part(c, d == 2 ? PART_R : PART_E3, c.rcut_2, c.rcut_smth_2, c.sel_2, c.n_embed_2,
+                                c.embed_2, off));
+  L.lrc = 0.0;
+  for (int t = 0; t < c.ntypes; ++t) L.lsel[t] = 0;
+  L.dw = 0;
+  for (Part& P : L.parts) {
+    L.lrc = std::max(L.lrc, P.rc);
+    for (int t = 0; t < c.ntypes; ++t) L.lsel[t] = std::max(L.lsel[t], P.sel[t]);
+    P.doff = L.dw;
+    L.dw += P.dwid;
+  }
+  L.nc = 0;
+  for (int t = 0; t < c.ntypes; ++t) { L.sel_off[t] = L.nc; L.nc += L.lsel[t]; }
+  L.sel_off[c.ntypes] = L.nc;
+  L.e1 = L.parts[0].nets;
   L.m = L.e1.m;
-  L.da = L.ang ? L.m * c.axis : 0;
-  L.dw = L.da + (L.rad ? L.radial().m : 0);
+  L.axis = c.axis;
+  L.n_embed_nets = (int)(L.e1.off.size() / std::max(1, L.e1.nl));
   int prev = L.dw;
   for (int l = 0; l < c.n_fit; ++l) { L.fin.push_back(prev); L.fout.push_back(c.fit[l]); prev = c.fit[l]; }
   L.fin.push_back(prev); L.fout.push_back(1);
   for (int n = 0; n < c.ntypes; ++n)
     for (size_t l = 0; l < L.fin.size(); ++l) { L.foff.push_back(off); off += (long)L.fin[l] * L.fout[l] + L.fout[l]; }
   L.n_params = off;
+  return L;
+}
+
+// The list geometry widened to n entries per type (every atom within the list cutoff).
+Layout widened(Layout L, int n) {
+  L.nc = 0;
+  for (int t = 0; t < L.ntypes; ++t) { L.lsel[t] = n; L.sel_off[t] = L.nc; L.nc += n; }
+  L.sel_off[L.ntypes] = L.nc;
   return L;
 }
 
@@ -285,7 +340,7 @@ void inverse3(const double* h, double* inv) {
 // Returns the number of (atom, type) blocks whose candidate count exceeded sel.
 int build_nlist(const OrcConfig& c, const Layout& L, int N, const double* coord, const int* type, const double* box,
                 int* nl_j, int* nl_code, int* counts /*[N*ntypes] or null*/) {
-  const double rc2 = c.rcut * c.rcut;
+  const double rc2 = L.lrc * L.lrc;
   std::vector<int> lo(3 * N, 0), hi(3 * N, 0);
   int K[3] = {0, 0, 0};
   std::vector<long> m(3 * (size_t)N, 0);
@@ -299,7 +354,7 @@ int build_nlist(const OrcConfig& c, const Layout& L, int N, const double* coord,
       const double* v = box + 3 * ((d + 2) % 3);
       double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
       double width = vol / std::sqrt(cx * cx + cy * cy + cz * cz);
-      K[d] = (int)std::ceil(c.rcut / width) + 1;
+      K[d] = (int)std::ceil(L.lrc / width) + 1;
     }
     for (int i = 0; i < N; ++i)
       for (int d = 0; d < 3; ++d) {
@@ -338,7 +393,7 @@ int build_nlist(const OrcConfig& c, const Layout& L, int N, const double* coord,
     std::vector<int> cnt(c.ntypes, 0);
     for (const Cand& e : cand) {
       int t = e.type;
-      if (cnt[t] < c.sel[t]) {
+      if (cnt[t] < L.lsel[t]) {
         long slot = (long)i * L.nc + L.sel_off[t] + cnt[t];
         nl_j[slot] = e.j;
         nl_code[slot] = e.code;
@@ -346,7 +401,7 @@ int build_nlist(const OrcConfig& c, const Layout& L, int N, const double* coord,
       cnt[t]++;
     }
     for (int t = 0; t < c.ntypes; ++t) {
-      if (cnt[t] > c.sel[t]) overflow++;
+      if (cnt[t] > L.lsel[t]) overflow++;
       if (counts) counts[(long)i * c.ntypes + t] = cnt[t];
     }
   }
@@ -462,79 +517,221 @@ double embed_row_backward(const NetSet& S, const double* params, const Table* ta
   return acc;
 }
 
-// One atom: descriptor, fitting net, and the reverse pass down to dE/dr_ij per slot (gd).
-// The table, when given, replaces the nets of `embed` (family e1); the se_e2_r nets of a hybrid
-// model (family e2) are always evaluated as networks.
-void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const Table* tab, int i, const double* coord,
-               const int* type, const double* box, const int* nl_j, const int* nl_code, double* gd /*[Nc*3]*/,
-               AtomOut* out) {
-  const int nc = L.nc, M = L.m, A = L.axis;
-  const int ai = type[i];
-  const double rs = c.rcut_smth, rc = c.rcut;
-  const bool hyb = c.descriptor == 2;
-  const NetSet& Sr = L.radial();
-  const int Mr = L.rad ? Sr.m : 0;
-  std::vector<double> R((size_t)nc * 4, 0.0), dvec((size_t)nc * 3, 0.0), rr(nc, 0.0), ss(nc, 0.0);
-  std::vector<int> valid(nc, 0), netk(nc, 0);
-  std::vector<EmbedRow> e1(nc), e2(hyb ? nc : 0);
-  out->range_err = 0;
-  // Eq. (rij) with Eq. (switch)
-  for (int t = 0; t < c.ntypes; ++t)
-    for (int q = 0; q < c.sel[t]; ++q) {
-      int k = L.sel_off[t] + q;
-      int j = nl_j[(long)i * nc + k];
-      netk[k] = embed_net_index(c, ai, t);
+// Environment of atom i for one part: its slots (type block t, position q < sel_P[t]) read the
+// same positions of the list's type blocks; a listed neighbour at or beyond the part's cutoff is
+// padding for that part.  The list holds, per type, the nearest neighbours within the widest
+// cutoff sorted by distance, so a part's own list is exactly this prefix.
+struct PartEnv {
+  std::vector<double> R, dvec, rr, ss;  // [nc*4] rows (s, s u), [nc*3] r_ij, [nc] r, [nc] s
+  std::vector<int> valid, tk, ls;       // per part slot: real neighbour, its type, list slot
+};
+
+void part_env(const Layout& L, const Part& P, int i, const double* coord, const double* box, const int* nl_j,
+              const int* nl_code, PartEnv& E) {
+  const int nc = P.nc;
+  E.R.assign((size_t)nc * 4, 0.0);
+  E.dvec.assign((size_t)nc * 3, 0.0);
+  E.rr.assign(nc, 0.0);
+  E.ss.assign(nc, 0.0);
+  E.valid.assign(nc, 0);
+  E.tk.assign(nc, 0);
+  E.ls.assign(nc, 0);
+  for (int t = 0; t < L.ntypes; ++t)
+    for (int q = 0; q < P.sel[t]; ++q) {
+      const int k = P.sel_off[t] + q, ls = L.sel_off[t] + q;
+      E.tk[k] = t;
+      E.ls[k] = ls;
+      const int j = nl_j[(long)i * L.nc + ls];
       if (j < 0) continue;
       int n[3];
-      unpack_shift(nl_code[(long)i * nc + k], n);
+      unpack_shift(nl_code[(long)i * L.nc + ls], n);
       double d[3];
       pair_disp(coord + 3 * i, coord + 3 * j, n, box, d);
-      double r = std::sqrt(norm2(d));
-      double s = switch_fn(r, rs, rc);
-      valid[k] = 1;
-      rr[k] = r;
-      ss[k] = s;
-      for (int a = 0; a < 3; ++a) dvec[(size_t)k * 3 + a] = d[a];
-      R[(size_t)k * 4 + 0] = s;
-      for (int a = 0; a < 3; ++a) R[(size_t)k * 4 + 1 + a] = s * d[a] / r;
+      const double r2 = norm2(d);
+      if (!(r2 < P.rc * P.rc)) continue;
+      const double r = std::sqrt(r2), sv = switch_fn(r, P.rs, P.rc);
+      E.valid[k] = 1;
+      E.rr[k] = r;
+      E.ss[k] = sv;
+      for (int a = 0; a < 3; ++a) E.dvec[(size_t)k * 3 + a] = d[a];
+      E.R[(size_t)k * 4 + 0] = sv;
+      for (int a = 0; a < 3; ++a) E.R[(size_t)k * 4 + 1 + a] = sv * d[a] / r;
     }
-  // Eq. (G2) / Eq. (compress): embedding rows of real neighbours (padded rows of R are zero and
-  // contribute nothing)
+}
+
+inline double dot4(const double* a, const double* b) { return ((a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]) + a[3] * b[3]; }
+
+// Forward state of one part of one atom, kept for its reverse pass.
+struct PartState {
+  PartEnv E;
+  std::vector<int> netk;      // two-body parts: net of each slot
+  std::vector<EmbedRow> emb;  // two-body parts: embedding rows
+  std::vector<double> T;      // se_e2_a: T (M x 4)
+};
+
+void part_forward(const OrcConfig& c, const Layout& L, const Part& P, const double* params, const Table* tab, int i,
+                  int ai, const double* coord, const double* box, const int* nl_j, const int* nl_code, PartState& S,
+                  double* D, int* range_err) {
+  part_env(L, P, i, coord, box, nl_j, nl_code, S.E);
+  const PartEnv& E = S.E;
+  const int nc = P.nc, M = P.nets.m;
+  if (P.kind == PART_E3) {
+    // D_m = (1/Nc^2) sum_{j,k} theta_jk G_jkm, theta_jk = R_j . R_k, G_jk = N^{a_j,a_k}(theta_jk)
+    std::vector<double> acc(M, 0.0);
+    std::vector<std::vector<double>> act, outs;
+    for (int j = 0; j < nc; ++j) {
+      if (!E.valid[j]) continue;
+      for (int k = 0; k < nc; ++k) {
+        if (!E.valid[k]) continue;
+        const double th = dot4(&E.R[(size_t)j * 4], &E.R[(size_t)k * 4]);
+        embed_forward(P.nets, params, E.tk[j] * L.ntypes + E.tk[k], th, act, outs);
+        for (int m = 0; m < M; ++m) acc[m] += th * outs[P.nets.nl - 1][m];
+      }
+    }
+    for (int m = 0; m < M; ++m) D[P.doff + m] = acc[m] / ((double)nc * nc);
+    return;
+  }
+  // two-body parts: Eq. (G2) / Eq. (compress) rows of real neighbours
+  S.netk.assign(nc, 0);
+  S.emb.assign(nc, EmbedRow());
   for (int k = 0; k < nc; ++k) {
-    if (!valid[k]) continue;
+    S.netk[k] = embed_net_index(c, ai, E.tk[k]);
+    if (!E.valid[k]) continue;
     int oor = 0;
-    embed_row(L.e1, params, tab, netk[k], ss[k], e1[k], &oor);
-    if (oor) out->range_err = 1;
-    if (hyb) embed_row(L.e2, params, nullptr, netk[k], ss[k], e2[k], &oor);
+    embed_row(P.nets, params, tab, S.netk[k], E.ss[k], S.emb[k], &oor);
+    if (oor) *range_err = 1;
   }
-  auto Gang = [&](int k) -> const std::vector<double>& { return e1[k].G; };
-  auto Grad = [&](int k) -> const std::vector<double>& { return hyb ? e2[k].G : e1[k].G; };
-  std::vector<double> D(L.dw, 0.0);
-  // se_e2_a block: T = (1/Nc) G^T R (M x 4), D = T T_<^T (M x M_<), flattened row-major
-  std::vector<double> T((size_t)M * 4, 0.0);
-  if (L.ang) {
-    for (int mm = 0; mm < M; ++mm)
-      for (int q = 0; q < 4; ++q) {
-        double acc = 0.0;
-        for (int k = 0; k < nc; ++k)
-          if (valid[k]) acc += Gang(k)[mm] * R[(size_t)k * 4 + q];
-        T[(size_t)mm * 4 + q] = acc / nc;
-      }
-    for (int mm = 0; mm < M; ++mm)
-      for (int l = 0; l < A; ++l) {
-        double acc = 0.0;
-        for (int q = 0; q < 4; ++q) acc += T[(size_t)mm * 4 + q] * T[(size_t)l * 4 + q];
-        D[(size_t)mm * A + l] = acc;
-      }
-  }
-  // se_e2_r block: D_m = (1/Nc) sum_k G_km s_k
-  if (L.rad)
-    for (int mm = 0; mm < Mr; ++mm) {
+  if (P.kind == PART_R) {
+    // D_m = (1/Nc) sum_k G_km s_k
+    for (int m = 0; m < M; ++m) {
       double acc = 0.0;
       for (int k = 0; k < nc; ++k)
-        if (valid[k]) acc += Grad(k)[mm] * ss[k];
-      D[L.da + mm] = acc / nc;
+        if (E.valid[k]) acc += S.emb[k].G[m] * E.ss[k];
+      D[P.doff + m] = acc / nc;
     }
+    return;
+  }
+  // se_e2_a: T = (1/Nc) G^T R (M x 4), D = T T_<^T (M x M_<), flattened row-major
+  const int A = P.axis;
+  S.T.assign((size_t)M * 4, 0.0);
+  for (int m = 0; m < M; ++m)
+    for (int q = 0; q < 4; ++q) {
+      double acc = 0.0;
+      for (int k = 0; k < nc; ++k)
+        if (E.valid[k]) acc += S.emb[k].G[m] * E.R[(size_t)k * 4 + q];
+      S.T[(size_t)m * 4 + q] = acc / nc;
+    }
+  for (int m = 0; m < M; ++m)
+    for (int l = 0; l < A; ++l) {
+      double acc = 0.0;
+      for (int q = 0; q < 4; ++q) acc += S.T[(size_t)m * 4 + q] * S.T[(size_t)l * 4 + q];
+      D[P.doff + (size_t)m * A + l] = acc;
+    }
+}
+
+// Reverse pass of one part: adds dE/dr_ij of each of its slots to gd at the slot's list position.
+void part_backward(const Layout& L, const Part& P, const double* params, const Table* tab, const PartState& S,
+                   const double* gD, double* gd) {
+  const PartEnv& E = S.E;
+  const int nc = P.nc, M = P.nets.m;
+  std::vector<double> gR((size_t)nc * 4, 0.0), gs(nc, 0.0);  // dE/dR rows; dE/ds through the nets
+  if (P.kind == PART_E3) {
+    // dE/dtheta_jk = (1/Nc^2) [ sum_m gD_m G_jkm + dE/dtheta through the net with dE/dG_jkm = gD_m theta ];
+    // dtheta_jk/dR_j = R_k, dtheta_jk/dR_k = R_j
+    const double inv = 1.0 / ((double)nc * nc);
+    std::vector<std::vector<double>> act, outs;
+    std::vector<double> gG(M);
+    for (int j = 0; j < nc; ++j) {
+      if (!E.valid[j]) continue;
+      for (int k = 0; k < nc; ++k) {
+        if (!E.valid[k]) continue;
+        const double* Rj = &E.R[(size_t)j * 4];
+        const double* Rk = &E.R[(size_t)k * 4];
+        const double th = dot4(Rj, Rk);
+        const int net = E.tk[j] * L.ntypes + E.tk[k];
+        embed_forward(P.nets, params, net, th, act, outs);
+        double direct = 0.0;
+        for (int m = 0; m < M; ++m) {
+          direct += gD[P.doff + m] * outs[P.nets.nl - 1][m];
+          gG[m] = gD[P.doff + m] * th * inv;
+        }
+        const double gth = direct * inv + embed_backward(P.nets, params, net, act, gG);
+        for (int q = 0; q < 4; ++q) {
+          gR[(size_t)j * 4 + q] += gth * Rk[q];
+          gR[(size_t)k * 4 + q] += gth * Rj[q];
+        }
+      }
+    }
+  } else {
+    std::vector<double> gT;
+    if (P.kind == PART_A) {
+      // dE/dT[p][q] = sum_l gD[p][l] T[l][q] + [p < M_<] sum_m gD[m][p] T[m][q]
+      const int A = P.axis;
+      const double* g = gD + P.doff;
+      gT.assign((size_t)M * 4, 0.0);
+      for (int p = 0; p < M; ++p)
+        for (int q = 0; q < 4; ++q) {
+          double acc = 0.0;
+          for (int l = 0; l < A; ++l) acc += g[(size_t)p * A + l] * S.T[(size_t)l * 4 + q];
+          if (p < A)
+            for (int m = 0; m < M; ++m) acc += g[(size_t)m * A + p] * S.T[(size_t)m * 4 + q];
+          gT[(size_t)p * 4 + q] = acc;
+        }
+    }
+    std::vector<double> gG(M);
+    for (int k = 0; k < nc; ++k) {
+      if (!E.valid[k]) continue;
+      const std::vector<double>& G = S.emb[k].G;
+      if (P.kind == PART_A) {
+        // dE/dR_k[q] = (1/Nc) sum_m gT[m][q] G_k[m];  dE/dG_k[m] = (1/Nc) sum_q gT[m][q] R_k[q]
+        for (int q = 0; q < 4; ++q) {
+          double acc = 0.0;
+          for (int m = 0; m < M; ++m) acc += gT[(size_t)m * 4 + q] * G[m];
+          gR[(size_t)k * 4 + q] = acc / nc;
+        }
+        for (int m = 0; m < M; ++m) {
+          double acc = 0.0;
+          for (int q = 0; q < 4; ++q) acc += gT[(size_t)m * 4 + q] * E.R[(size_t)k * 4 + q];
+          gG[m] = acc / nc;
+        }
+      } else {
+        // dE/dG_k[m] = gD_m s_k / Nc and the direct dE/ds_k = sum_m gD_m G_k[m] / Nc
+        double direct = 0.0;
+        for (int m = 0; m < M; ++m) {
+          gG[m] = gD[P.doff + m] * E.ss[k] / nc;
+          direct += gD[P.doff + m] * G[m] / nc;
+        }
+        gR[(size_t)k * 4 + 0] = direct;
+      }
+      gs[k] = embed_row_backward(P.nets, params, tab, S.netk[k], S.emb[k], gG);
+    }
+  }
+  // chain through R_k = (s, s u) with u = d / r, s = s(r), r = |d|
+  for (int k = 0; k < nc; ++k) {
+    if (!E.valid[k]) continue;
+    const double r = E.rr[k], sv = E.ss[k];
+    const double sp = switch_deriv(r, P.rs, P.rc);
+    const double* d = &E.dvec[(size_t)k * 3];
+    const double* g = &gR[(size_t)k * 4];
+    const double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+    const double gvu = g[1] * u[0] + g[2] * u[1] + g[3] * u[2];
+    const double gsum = gs[k] + g[0] + gvu;  // total dE/ds at fixed u
+    for (int a = 0; a < 3; ++a) gd[(size_t)E.ls[k] * 3 + a] += sp * gsum * u[a] + (sv / r) * (g[1 + a] - gvu * u[a]);
+  }
+}
+
+// One atom: descriptor (all parts), fitting net, and the reverse pass down to dE/dr_ij per list
+// slot (gd [L.nc * 3]).  The table, when given, replaces the nets of the first part (two-body).
+void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const Table* tab, int i, const double* coord,
+               const int* type, const double* box, const int* nl_j, const int* nl_code, double* gd, AtomOut* out) {
+  const int ai = type[i];
+  out->range_err = 0;
+  const size_t np = L.parts.size();
+  std::vector<PartState> S(np);
+  std::vector<double> D(L.dw, 0.0);
+  for (size_t q = 0; q < np; ++q)
+    part_forward(c, L, L.parts[q], params, q == 0 ? tab : nullptr, i, ai, coord, box, nl_j, nl_code, S[q], D.data(),
+                 &out->range_err);
   // Eq. (fitting): E_i = F_0^{a_i}(D)
   const int nfl = (int)L.fin.size();
   std::vector<std::vector<double>> fx(nfl + 1), fa(nfl);
@@ -572,57 +769,8 @@ void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const 
     }
     gy = gx;
   }
-  const std::vector<double>& gD = gy;  // dE_i/dD
-  // se_e2_a block: dE/dT[p][q] = sum_l gD[p][l] T[l][q] + [p < M_<] sum_m gD[m][p] T[m][q]
-  std::vector<double> gT((size_t)M * 4, 0.0);
-  if (L.ang)
-    for (int p = 0; p < M; ++p)
-      for (int q = 0; q < 4; ++q) {
-        double acc = 0.0;
-        for (int l = 0; l < A; ++l) acc += gD[(size_t)p * A + l] * T[(size_t)l * 4 + q];
-        if (p < A)
-          for (int mm = 0; mm < M; ++mm) acc += gD[(size_t)mm * A + p] * T[(size_t)mm * 4 + q];
-        gT[(size_t)p * 4 + q] = acc;
-      }
-  for (int k = 0; k < nc * 3; ++k) gd[k] = 0.0;
-  for (int k = 0; k < nc; ++k) {
-    if (!valid[k]) continue;
-    const double r = rr[k], s = ss[k];
-    // dE/dR_k[q] = (1/Nc) sum_m gT[m][q] G_k[m];  dE/dG_k[m] = (1/Nc) sum_q gT[m][q] R_k[q]
-    double gR[4] = {0.0, 0.0, 0.0, 0.0};
-    std::vector<double> gG1(M, 0.0), gG2(hyb ? Mr : 0, 0.0);
-    if (L.ang) {
-      for (int q = 0; q < 4; ++q) {
-        double acc = 0.0;
-        for (int mm = 0; mm < M; ++mm) acc += gT[(size_t)mm * 4 + q] * Gang(k)[mm];
-        gR[q] = acc / nc;
-      }
-      for (int mm = 0; mm < M; ++mm) {
-        double acc = 0.0;
-        for (int q = 0; q < 4; ++q) acc += gT[(size_t)mm * 4 + q] * R[(size_t)k * 4 + q];
-        gG1[mm] = acc / nc;
-      }
-    }
-    // se_e2_r block: dE/dG_k[m] = gD_r[m] s_k / Nc and dE/ds_k (direct) = sum_m gD_r[m] G_k[m] / Nc
-    double gs_direct = 0.0;
-    if (L.rad) {
-      std::vector<double>& gGr = hyb ? gG2 : gG1;
-      for (int mm = 0; mm < Mr; ++mm) {
-        const double g = gD[L.da + mm];
-        gGr[mm] += g * s / nc;
-        gs_direct += g * Grad(k)[mm] / nc;
-      }
-    }
-    double gs_embed = embed_row_backward(L.e1, params, tab, netk[k], e1[k], gG1);
-    if (hyb) gs_embed += embed_row_backward(L.e2, params, nullptr, netk[k], e2[k], gG2);
-    // chain through R_k = (s, s u) with u = d / r, and s = s(r), r = |d|
-    double sp = switch_deriv(r, rs, rc);
-    const double* d = &dvec[(size_t)k * 3];
-    double u[3] = {d[0] / r, d[1] / r, d[2] / r};
-    double gvu = gR[1] * u[0] + gR[2] * u[1] + gR[3] * u[2];
-    double gs = gs_embed + gs_direct + gR[0] + gvu;  // total dE/ds at fixed u
-    for (int a = 0; a < 3; ++a) gd[(size_t)k * 3 + a] = sp * gs * u[a] + (s / r) * (gR[1 + a] - gvu * u[a]);
-  }
+  for (int k = 0; k < L.nc * 3; ++k) gd[k] = 0.0;
+  for (size_t q = 0; q < np; ++q) part_backward(L, L.parts[q], params, q == 0 ? tab : nullptr, S[q], gy.data(), gd);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -643,51 +791,72 @@ std::vector<T> embed_generic(const NetSet& S, const P* params, int net, T s) {
 template <class T, class P>
 T energy_generic(const OrcConfig& c, const Layout& L, const P* params, int N, const T* coord, const int* type,
                  const T* box, const int* nl_j, const int* nl_code, T* atom_e) {
-  const int nc = L.nc, M = L.m, A = L.axis;
-  const NetSet& Sr = L.radial();
-  const int Mr = L.rad ? Sr.m : 0;
   T E(0.0);
   for (int i = 0; i < N; ++i) {
-    int ai = type[i];
-    std::vector<T> Tm((size_t)M * 4, T(0.0)), Dr(Mr, T(0.0));
-    for (int t = 0; t < c.ntypes; ++t)
-      for (int q = 0; q < c.sel[t]; ++q) {
-        int k = L.sel_off[t] + q;
-        int j = nl_j[(long)i * nc + k];
-        if (j < 0) continue;
-        int n[3];
-        unpack_shift(nl_code[(long)i * nc + k], n);
-        T d[3];
-        for (int a = 0; a < 3; ++a) {
-          T tt(0.0);
-          if (box) tt = T((double)n[0]) * box[a] + T((double)n[1]) * box[3 + a] + T((double)n[2]) * box[6 + a];
-          d[a] = (coord[3 * j + a] + tt) - coord[3 * i + a];
+    const int ai = type[i];
+    std::vector<T> x(L.dw, T(0.0));
+    for (const Part& Pt : L.parts) {
+      const int nc = Pt.nc, M = Pt.nets.m;
+      std::vector<std::vector<T>> R(nc);
+      std::vector<T> sv(nc, T(0.0));
+      std::vector<int> tk(nc, 0), valid(nc, 0);
+      for (int t = 0; t < c.ntypes; ++t)
+        for (int q = 0; q < Pt.sel[t]; ++q) {
+          const int k = Pt.sel_off[t] + q, ls = L.sel_off[t] + q;
+          tk[k] = t;
+          const int j = nl_j[(long)i * L.nc + ls];
+          if (j < 0) continue;
+          int n[3];
+          unpack_shift(nl_code[(long)i * L.nc + ls], n);
+          T d[3];
+          for (int a = 0; a < 3; ++a) {
+            T tt(0.0);
+            if (box) tt = T((double)n[0]) * box[a] + T((double)n[1]) * box[3 + a] + T((double)n[2]) * box[6 + a];
+            d[a] = (coord[3 * j + a] + tt) - coord[3 * i + a];
+          }
+          T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+          if (!(val(r2) < Pt.rc * Pt.rc)) continue;
+          T r = dsqrt(r2);
+          T s = switch_fn(r, Pt.rs, Pt.rc);
+          valid[k] = 1;
+          sv[k] = s;
+          R[k] = {s, s * d[0] / r, s * d[1] / r, s * d[2] / r};
         }
-        T r = dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        T s = switch_fn(r, c.rcut_smth, c.rcut);
-        T Rk[4] = {s, s * d[0] / r, s * d[1] / r, s * d[2] / r};
-        int net = embed_net_index(c, ai, t);
-        if (L.ang) {
-          std::vector<T> g = embed_generic<T, P>(L.e1, params, net, s);
-          for (int mm = 0; mm < M; ++mm)
-            for (int qq = 0; qq < 4; ++qq) Tm[(size_t)mm * 4 + qq] = Tm[(size_t)mm * 4 + qq] + g[mm] * Rk[qq];
-        }
-        if (L.rad) {
-          std::vector<T> g = embed_generic<T, P>(Sr, params, net, s);
-          for (int mm = 0; mm < Mr; ++mm) Dr[mm] = Dr[mm] + g[mm] * s;
+      if (Pt.kind == PART_E3) {
+        std::vector<T> acc(M, T(0.0));
+        for (int j = 0; j < nc; ++j)
+          for (int k = 0; k < nc; ++k) {
+            if (!valid[j] || !valid[k]) continue;
+            T th = ((R[j][0] * R[k][0] + R[j][1] * R[k][1]) + R[j][2] * R[k][2]) + R[j][3] * R[k][3];
+            std::vector<T> g = embed_generic<T, P>(Pt.nets, params, tk[j] * c.ntypes + tk[k], th);
+            for (int m = 0; m < M; ++m) acc[m] = acc[m] + th * g[m];
+          }
+        for (int m = 0; m < M; ++m) x[Pt.doff + m] = acc[m] / T((double)nc * nc);
+        continue;
+      }
+      std::vector<T> Tm((size_t)M * 4, T(0.0)), Dr(M, T(0.0));
+      for (int k = 0; k < nc; ++k) {
+        if (!valid[k]) continue;
+        std::vector<T> g = embed_generic<T, P>(Pt.nets, params, embed_net_index(c, ai, tk[k]), sv[k]);
+        for (int m = 0; m < M; ++m) {
+          if (Pt.kind == PART_R) Dr[m] = Dr[m] + g[m] * sv[k];
+          else
+            for (int q = 0; q < 4; ++q) Tm[(size_t)m * 4 + q] = Tm[(size_t)m * 4 + q] + g[m] * R[k][q];
         }
       }
-    std::vector<T> x(L.dw, T(0.0));
-    if (L.ang) {
+      if (Pt.kind == PART_R) {
+        for (int m = 0; m < M; ++m) x[Pt.doff + m] = Dr[m] / T((double)nc);
+        continue;
+      }
+      const int A = Pt.axis;
       for (auto& v : Tm) v = v / T((double)nc);
-      for (int mm = 0; mm < M; ++mm)
+      for (int m = 0; m < M; ++m)
         for (int l = 0; l < A; ++l) {
           T acc(0.0);
-          for (int qq = 0; qq < 4; ++qq) acc = acc + Tm[(size_t)mm * 4 + qq] * Tm[(size_t)l * 4 + qq];
-          x[(size_t)mm * A + l] = acc;
+          for (int q = 0; q < 4; ++q) acc = acc + Tm[(size_t)m * 4 + q] * Tm[(size_t)l * 4 + q];
+          x[Pt.doff + (size_t)m * A + l] = acc;
         }
     }
-    for (int mm = 0; mm < Mr; ++mm) x[L.da + mm] = Dr[mm] / T((double)nc);
     const int nfl = (int)L.fin.size();
     for (int l = 0; l < nfl; ++l) {
       const P* W = params + L.foff[(size_t)ai * nfl + l];
@@ -818,6 +987,7 @@ int orc_compute(const OrcConfig* cfg, const double* params, int N, const double*
   }
   Table tb{table, s0, stride1, stride2, n1, n2};
   const Table* tp = table ? &tb : nullptr;
+  if (table && L.parts[0].kind == PART_E3) return -2;  // tables replace two-body nets only
   std::vector<double> gd((size_t)N * nc * 3, 0.0);
   std::vector<AtomOut> ao(N);
 #ifdef _OPENMP
@@ -893,7 +1063,7 @@ struct RowBuilder {
   int K[3] = {0, 0, 0};
   RowBuilder(const OrcConfig& c_, const Layout& L_, int N_, const double* coord_, const int* type_,
              const double* box_)
-      : c(c_), L(L_), N(N_), coord(coord_), type(type_), box(box_), rc2(c_.rcut * c_.rcut) {
+      : c(c_), L(L_), N(N_), coord(coord_), type(type_), box(box_), rc2(L_.lrc * L_.lrc) {
     if (box) {
       inverse3(box, inv);
       double vol = std::fabs(box[0] * (box[4] * box[8] - box[5] * box[7]) -
@@ -902,7 +1072,7 @@ struct RowBuilder {
         const double* u = box + 3 * ((d + 1) % 3);
         const double* v = box + 3 * ((d + 2) % 3);
         double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
-        K[d] = (int)std::ceil(c.rcut / (vol / std::sqrt(cx * cx + cy * cy + cz * cz))) + 1;
+        K[d] = (int)std::ceil(L.lrc / (vol / std::sqrt(cx * cx + cy * cy + cz * cz))) + 1;
       }
     }
   }
@@ -942,14 +1112,14 @@ struct RowBuilder {
     }
     std::vector<int> cnt(c.ntypes, 0);
     for (const Cand& e : cand) {
-      if (cnt[e.type] < c.sel[e.type]) {
+      if (cnt[e.type] < L.lsel[e.type]) {
         nl_j[L.sel_off[e.type] + cnt[e.type]] = e.j;
         nl_code[L.sel_off[e.type] + cnt[e.type]] = e.code;
       }
       cnt[e.type]++;
     }
     int ov = 0;
-    for (int t = 0; t < c.ntypes; ++t) ov += cnt[t] > c.sel[t];
+    for (int t = 0; t < c.ntypes; ++t) ov += cnt[t] > L.lsel[t];
     return ov;
   }
 };
@@ -999,10 +1169,8 @@ int orc_force_subset(const OrcConfig* cfg, const double* params, int N, const do
   for (int s = 0; s < nsel; ++s) {
     need[idx[s]] = 1;
     // every atom within r_c of k, listed or beyond sel: a wider row with sel = the atom count
-    OrcConfig wide = c;
-    for (int t = 0; t < c.ntypes; ++t) wide.sel[t] = N * 27;
-    Layout Lw = make_layout(wide);
-    RowBuilder rw(wide, Lw, N, coord, type, box);
+    Layout Lw = widened(L, N * 27);
+    RowBuilder rw(c, Lw, N, coord, type, box);
     std::vector<int> wj(Lw.nc), wc(Lw.nc);
     rw.row(idx[s], wj.data(), wc.data());
     for (int k = 0; k < Lw.nc; ++k)

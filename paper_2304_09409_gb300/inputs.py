@@ -76,12 +76,35 @@ class ModelConfig:
     axis: int                     # M_<
     fit: Tuple[int, ...]          # fitting net hidden widths; a final width-1 linear layer is implied
     type_one_side: int = 0        # 0: nets N^{a_i,a_j}; 1: nets N^{a_j}
-    descriptor: int = 0           # 0: se_e2_a; 1: se_e2_r; 2: hybrid of se_e2_a and se_e2_r on one list
-    embed_r: Tuple[int, ...] = () # hybrid: the se_e2_r part's embedding net widths
+    # 0: se_e2_a; 1: se_e2_r; 2: hybrid se_e2_a + se_e2_r; 3: se_e3; 4: hybrid se_e2_a + se_e3
+    descriptor: int = 0
+    # hybrids: the second part's cutoffs (0: those of the first), sel (empty: that of the first)
+    # and embedding widths
+    rcut_2: float = 0.0
+    rcut_smth_2: float = 0.0
+    sel_2: Tuple[int, ...] = ()
+    embed_2: Tuple[int, ...] = ()
+
+    @property
+    def hybrid(self) -> bool:
+        return self.descriptor in (2, 4)
+
+    @property
+    def list_sel(self) -> Tuple[int, ...]:
+        """Per-type width of the neighbour list all parts read: the larger sel of the parts."""
+        if not self.hybrid:
+            return tuple(self.sel)
+        sel_2 = tuple(self.sel_2) or tuple(self.sel)
+        return tuple(max(a, b) for a, b in zip(self.sel, sel_2))
+
+    @property
+    def list_rcut(self) -> float:
+        return max(self.rcut, self.rcut_2 or self.rcut) if self.hybrid else self.rcut
 
     @property
     def nc(self) -> int:
-        return int(sum(self.sel))
+        """Width of the neighbour list (sum of list_sel)."""
+        return int(sum(self.list_sel))
 
     @property
     def m(self) -> int:
@@ -89,32 +112,44 @@ class ModelConfig:
 
     @property
     def n_embed_nets(self) -> int:
+        """Nets of the first part: N^{a_i,a_j} or N^{a_j}; se_e3 nets N^{a_j,a_k}."""
+        if self.descriptor == 3:
+            return self.ntypes * self.ntypes
+        return self.ntypes if self.type_one_side else self.ntypes * self.ntypes
+
+    @property
+    def n_embed_nets_2(self) -> int:
+        if not self.hybrid:
+            return 0
+        if self.descriptor == 4:
+            return self.ntypes * self.ntypes
         return self.ntypes if self.type_one_side else self.ntypes * self.ntypes
 
     @property
     def descriptor_dim(self) -> int:
-        """Width of D: M * M_< (se_e2_a), M (se_e2_r), or their sum (hybrid)."""
-        if self.descriptor == 1:
+        """Width of D: M * M_< (se_e2_a), M (se_e2_r, se_e3), or the sum of the parts (hybrid)."""
+        if self.descriptor in (1, 3):
             return self.m
-        if self.descriptor == 2:
-            return self.m * self.axis + int(self.embed_r[-1])
+        if self.hybrid:
+            return self.m * self.axis + int(self.embed_2[-1])
         return self.m * self.axis
 
     def embed_layer_shapes(self) -> List[Tuple[int, int]]:
         dims = [1] + list(self.embed)
         return [(dims[k], dims[k + 1]) for k in range(len(self.embed))]
 
-    def embed_r_layer_shapes(self) -> List[Tuple[int, int]]:
-        """Layer shapes of the hybrid's se_e2_r nets (empty for the other descriptors)."""
-        if self.descriptor != 2:
+    def embed_2_layer_shapes(self) -> List[Tuple[int, int]]:
+        """Layer shapes of the hybrid's second-part nets (empty for the other descriptors)."""
+        if not self.hybrid:
             return []
-        dims = [1] + list(self.embed_r)
-        return [(dims[k], dims[k + 1]) for k in range(len(self.embed_r))]
+        dims = [1] + list(self.embed_2)
+        return [(dims[k], dims[k + 1]) for k in range(len(self.embed_2))]
 
     def embed_params(self) -> int:
-        """Parameters of all embedding nets (those of `embed`, then the hybrid's se_e2_r nets)."""
-        per = sum(a * b + b for a, b in self.embed_layer_shapes() + self.embed_r_layer_shapes())
-        return self.n_embed_nets * per
+        """Parameters of all embedding nets (those of `embed`, then the hybrid's second part)."""
+        p1 = sum(a * b + b for a, b in self.embed_layer_shapes())
+        p2 = sum(a * b + b for a, b in self.embed_2_layer_shapes())
+        return self.n_embed_nets * p1 + self.n_embed_nets_2 * p2
 
     def fit_layer_shapes(self) -> List[Tuple[int, int]]:
         dims = [self.descriptor_dim] + list(self.fit) + [1]
@@ -145,23 +180,39 @@ def water_model_r() -> ModelConfig:
 
 
 def water_model_hybrid() -> ModelConfig:
-    """Water-like hybrid model on the water model's list: the se_e2_a part of the water model
-    (embedding 25/50/100, M_< 16) and an se_e2_r part with embedding 10/20/40 (D has 1640 values)."""
-    return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92), embed=(25, 50, 100), axis=16,
-                       fit=(240, 240, 240), descriptor=2, embed_r=(10, 20, 40))
+    """Water-like hybrid se_e2_a + se_e2_r: an se_e2_a part with r_c 4 (sel [20, 40], embedding
+    25/50/100, M_< 16) and an se_e2_r part with r_c 6 (sel [46, 92], embedding 10/20/40); D has
+    1640 values."""
+    return ModelConfig(ntypes=2, rcut=4.0, rcut_smth=0.5, sel=(20, 40), embed=(25, 50, 100), axis=16,
+                       fit=(240, 240, 240), descriptor=2, rcut_2=6.0, rcut_smth_2=0.5, sel_2=(46, 92),
+                       embed_2=(10, 20, 40))
+
+
+def water_model_e3() -> ModelConfig:
+    """Water-like se_e3 model: r_c 6, r_s 0.5, sel [46, 92], embedding 2/4/8 (D has 8 values)."""
+    return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92), embed=(2, 4, 8), axis=0,
+                       fit=(240, 240, 240), descriptor=3)
+
+
+def water_model_hybrid_e3() -> ModelConfig:
+    """Water-like hybrid se_e2_a + se_e3: the se_e2_a part with r_c 4 as in water_model_hybrid and
+    an se_e3 part with r_c 6 (sel [46, 92], embedding 2/4/8); D has 1608 values."""
+    return ModelConfig(ntypes=2, rcut=4.0, rcut_smth=0.5, sel=(20, 40), embed=(25, 50, 100), axis=16,
+                       fit=(240, 240, 240), descriptor=4, rcut_2=6.0, rcut_smth_2=0.5, sel_2=(46, 92),
+                       embed_2=(2, 4, 8))
 
 
 def make_params(cfg: ModelConfig, seed: int = 0) -> np.ndarray:
     """Xavier-normal weights W ~ N(0, 2/(fan_in+fan_out)) and biases b ~ N(0, 1), FP64, flat.
 
     Layout (shared by every consumer): embedding nets in order of net index
-    (a_i * ntypes + a_j, or a_j when type_one_side), then (hybrid only) the se_e2_r
-    embedding nets in the same order, then fitting nets by type; inside a net, layer by
-    layer, W row-major [in][out] followed by b [out].
+    (a_i * ntypes + a_j, or a_j when type_one_side; a_j * ntypes + a_k for se_e3), then
+    (hybrids only) the second part's embedding nets in the same order, then fitting nets by
+    type; inside a net, layer by layer, W row-major [in][out] followed by b [out].
     """
     rng = Rng(seed)
     out = []
-    nets = [(cfg.embed_layer_shapes(), cfg.n_embed_nets), (cfg.embed_r_layer_shapes(), cfg.n_embed_nets),
+    nets = [(cfg.embed_layer_shapes(), cfg.n_embed_nets), (cfg.embed_2_layer_shapes(), cfg.n_embed_nets_2),
             (cfg.fit_layer_shapes(), cfg.ntypes)]
     for shapes, count in nets:
         for _ in range(count):
@@ -180,9 +231,12 @@ def make_params(cfg: ModelConfig, seed: int = 0) -> np.ndarray:
 # eV/A (1e-3 eV/A for the mixed-precision path) are only meaningful at that force scale.
 WATER_FORCE_SCALE = 2000.0
 METAL_FORCE_SCALE = 1.2e5
-# the same for the water-like se_e2_r model (seed 0: 4.4e-3 eV/A RMS) and hybrid model (9.2e-4)
+# the same for the water-like se_e2_r (seed 0: 4.4e-3 eV/A RMS), hybrid se_e2_a + se_e2_r (1.1e-3),
+# se_e3 (5.2e-4) and hybrid se_e2_a + se_e3 (3.9e-3) models
 WATER_R_FORCE_SCALE = 230.0
-WATER_HYBRID_FORCE_SCALE = 1100.0
+WATER_HYBRID_FORCE_SCALE = 900.0
+WATER_E3_FORCE_SCALE = 1950.0
+WATER_HYBRID_E3_FORCE_SCALE = 255.0
 
 
 def force_scaled(cfg: ModelConfig, params: np.ndarray, scale: float) -> np.ndarray:
@@ -216,6 +270,18 @@ def water_hybrid_params_scaled(seed: int = 0) -> np.ndarray:
     """The water-like hybrid model's parameters with forces of about 1 eV/A RMS."""
     cfg = water_model_hybrid()
     return force_scaled(cfg, make_params(cfg, seed), WATER_HYBRID_FORCE_SCALE)
+
+
+def water_e3_params_scaled(seed: int = 0) -> np.ndarray:
+    """The water-like se_e3 model's parameters with forces of about 1 eV/A RMS."""
+    cfg = water_model_e3()
+    return force_scaled(cfg, make_params(cfg, seed), WATER_E3_FORCE_SCALE)
+
+
+def water_hybrid_e3_params_scaled(seed: int = 0) -> np.ndarray:
+    """The water-like hybrid se_e2_a + se_e3 model's parameters with forces of about 1 eV/A RMS."""
+    cfg = water_model_hybrid_e3()
+    return force_scaled(cfg, make_params(cfg, seed), WATER_HYBRID_E3_FORCE_SCALE)
 
 
 def metal_params_scaled(seed: int = 0) -> np.ndarray:

@@ -30,6 +30,20 @@ def tiny_model_r(type_one_side: int = 0) -> I.ModelConfig:
 
 
 def tiny_model_hybrid(type_one_side: int = 0) -> I.ModelConfig:
-    """The tiny model with an se_e2_r part (embedding 3/6/12) beside its se_e2_a part."""
+    """The tiny model with an se_e2_r part (same list, embedding 3/6/12) beside its se_e2_a part."""
     return I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(4, 8, 16), axis=4,
-                         fit=(12, 12), type_one_side=type_one_side, descriptor=2, embed_r=(3, 6, 12))
+                         fit=(12, 12), type_one_side=type_one_side, descriptor=2, embed_2=(3, 6, 12))
+
+
+def tiny_model_e3() -> I.ModelConfig:
+    """The tiny model's list and fitting net with the se_e3 descriptor (embedding 2/4/8)."""
+    return I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(2, 4, 8), axis=0,
+                         fit=(12, 12), descriptor=3)
+
+
+def tiny_model_hybrid_e3() -> I.ModelConfig:
+    """Hybrid se_e2_a (r_c 3.0, sel [8, 14], embedding 4/8/16, M_< 4) + se_e3 (r_c 3.5, sel
+    [12, 20], embedding 2/4/8): parts with different cutoffs and sel on one list."""
+    return I.ModelConfig(ntypes=2, rcut=3.0, rcut_smth=0.5, sel=(8, 14), embed=(4, 8, 16), axis=4,
+                         fit=(12, 12), descriptor=4, rcut_2=3.5, rcut_smth_2=0.4, sel_2=(12, 20),
+                         embed_2=(2, 4, 8))

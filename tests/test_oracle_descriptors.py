@@ -1,11 +1,13 @@
-"""Pins of the oracle's se_e2_r and hybrid descriptors (Sec. II.A.1).
+"""Pins of the oracle's se_e2_r, se_e3 and hybrid descriptors (Sec. II.A.1).
 
-se_e2_r keeps only the radial column of R: D^i = G^T s / N_c, M values per atom.  The hybrid
-descriptor concatenates the se_e2_a block (M x M_<) and the se_e2_r block.  Closed forms on
-dimers and trimers fix the formula (the s weight, the 1/N_c, no angular information); the
-decomposition of a hybrid model with a linear fitting net into its two parts fixes the
-concatenation order and the parameter layout; dual numbers, finite differences and the
-symmetries fix the reverse pass.
+se_e2_r keeps only the radial column of R: D^i = G^T s / N_c, M values per atom.  se_e3
+contracts R R^T with the three-body embedding: D^i = (R R^T) : G / N_c^2 with
+G_jk = N^{a_j,a_k}(R_j . R_k).  A hybrid descriptor concatenates its parts, each with its own
+cutoff, sel and nets.  Closed forms on dimers and trimers fix the formulas (the s weight, the
+1/N_c and 1/N_c^2, the angle, the type-pair nets); the decomposition of a hybrid model with a
+linear fitting net into stand-alone parts fixes the concatenation order, the parameter layout
+and the per-part neighbour lists; dual numbers, finite differences and the symmetries fix the
+reverse pass.
 """
 import math
 
@@ -15,7 +17,7 @@ import pytest
 import oracle
 from paper_2304_09409_gb300 import inputs as I
 
-from _cases import tiny_frame, tiny_model_hybrid, tiny_model_r
+from _cases import tiny_frame, tiny_model_e3, tiny_model_hybrid, tiny_model_hybrid_e3, tiny_model_r
 
 
 def _pair_model_r(M=1, sel=(4,), rc=4.0):
@@ -76,52 +78,131 @@ def test_se_e2_r_padding_scales_descriptor_by_inverse_nc():
     np.testing.assert_allclose(e2.force, e1.force * 24 / 60, rtol=1e-11, atol=1e-14)
 
 
-def _linear_parts(seed=3):
-    """A hybrid model with a linear fitting net, and its se_e2_a and se_e2_r halves."""
-    hyb = I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(4, 8), axis=3, fit=(),
-                        descriptor=2, embed_r=(2, 4, 5))
-    ang = I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(4, 8), axis=3, fit=())
-    rad = I.ModelConfig(ntypes=2, rcut=3.5, rcut_smth=0.5, sel=(12, 20), embed=(2, 4, 5), axis=0, fit=(),
-                        descriptor=1)
+def _linear_parts(second="r", rc=(3.0, 3.5), sel=((8, 14), (12, 20)), seed=3):
+    """A hybrid model with a linear fitting net, and its two parts as stand-alone models with their
+    own cutoffs and sel (each builds its own list by brute force)."""
+    kind2, emb2 = (1, (2, 4, 5)) if second == "r" else (3, (2, 4))
+    hyb = I.ModelConfig(ntypes=2, rcut=rc[0], rcut_smth=0.5, sel=sel[0], embed=(4, 8), axis=3, fit=(),
+                        descriptor=2 if second == "r" else 4, rcut_2=rc[1], rcut_smth_2=0.4, sel_2=sel[1],
+                        embed_2=emb2)
+    ang = I.ModelConfig(ntypes=2, rcut=rc[0], rcut_smth=0.5, sel=sel[0], embed=(4, 8), axis=3, fit=())
+    two = I.ModelConfig(ntypes=2, rcut=rc[1], rcut_smth=0.4, sel=sel[1], embed=emb2, axis=0, fit=(),
+                        descriptor=kind2)
     p = I.make_params(hyb, seed)
-    na = ang.n_embed_nets * sum(a * b + b for a, b in ang.embed_layer_shapes())
-    nr = rad.n_embed_nets * sum(a * b + b for a, b in rad.embed_layer_shapes())
-    da, dr = 8 * 3, 5
-    pa, pr, pf = p[:na], p[na:na + nr], p[na + nr:]
-    fa, fr_ = [], []
-    for t in range(2):  # per type: W [da + dr] then b
-        blk = pf[t * (da + dr + 1):(t + 1) * (da + dr + 1)]
+    na = ang.embed_params()
+    n2 = two.embed_params()
+    da, d2 = ang.descriptor_dim, two.descriptor_dim
+    pa, p2, pf = p[:na], p[na:na + n2], p[na + n2:]
+    fa, f2 = [], []
+    for t in range(2):  # per type: W [da + d2] then b
+        blk = pf[t * (da + d2 + 1):(t + 1) * (da + d2 + 1)]
         fa.append(np.concatenate([blk[:da], blk[-1:]]))
-        fr_.append(np.concatenate([blk[da:da + dr], [0.0]]))
-    return (hyb, p), (ang, np.concatenate([pa] + fa)), (rad, np.concatenate([pr] + fr_))
+        f2.append(np.concatenate([blk[da:da + d2], [0.0]]))
+    return (hyb, p), (ang, np.concatenate([pa] + fa)), (two, np.concatenate([p2] + f2))
 
 
-def test_hybrid_with_linear_fitting_is_sum_of_its_parts():
-    """E_i = W . [D_a, D_r] + b splits into an se_e2_a model with (W_a, b) and an se_e2_r model
-    with (W_r, 0): energies, per-atom energies, forces and virials add."""
-    (hyb, ph), (ang, pa), (rad, pr) = _linear_parts()
+@pytest.mark.parametrize("second", ["r", "e3"])
+@pytest.mark.parametrize("rc,sel", [((3.0, 3.5), ((8, 14), (12, 20))), ((3.5, 2.8), ((12, 20), (6, 9))),
+                                    ((3.5, 3.5), ((12, 20), (12, 20)))], ids=["wider2", "wider1", "same"])
+def test_hybrid_with_linear_fitting_is_sum_of_its_parts(second, rc, sel):
+    """E_i = W . [D_1, D_2] + b splits into the first part with (W_1, b) and the second part with
+    (W_2, 0), each a stand-alone model with its own cutoff, sel and brute-force list: energies,
+    per-atom energies, forces and virials add.  This fixes the concatenation order, the parameter
+    layout, and that a part reads the nearest sel_2 neighbours within its own r_c from the one list
+    built at the wider cutoff."""
+    (hyb, ph), (ang, pa), (two, p2) = _linear_parts(second, rc, sel)
     # the two halves each carry one bias per type; the hybrid carries one
-    assert hyb.n_params() == oracle.n_params(hyb) == pa.size + pr.size - hyb.ntypes
+    assert hyb.n_params() == oracle.n_params(hyb) == pa.size + p2.size - hyb.ntypes
     fr = tiny_frame(seed=6)
     h = oracle.compute(hyb, ph, fr.coord, fr.atype, fr.box)
     a = oracle.compute(ang, pa, fr.coord, fr.atype, fr.box)
-    r = oracle.compute(rad, pr, fr.coord, fr.atype, fr.box)
-    assert abs(r.energy) > 1e-3 and abs(a.energy) > 1e-3
+    r = oracle.compute(two, p2, fr.coord, fr.atype, fr.box)
+    assert abs(r.energy) > 1e-4 and abs(a.energy) > 1e-4
     assert h.energy == pytest.approx(a.energy + r.energy, rel=1e-13)
     np.testing.assert_allclose(h.atom_energy, a.atom_energy + r.atom_energy, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(h.force, a.force + r.force, rtol=1e-11, atol=1e-13)
     np.testing.assert_allclose(h.virial, a.virial + r.virial, rtol=1e-11, atol=1e-13)
 
 
+# ----------------------------------------------------------------------------------------
+# se_e3: closed forms
+# ----------------------------------------------------------------------------------------
+
+
+def _e3_model(ntypes=1, sel=(4,), rc=4.0, M=1):
+    return I.ModelConfig(ntypes=ntypes, rcut=rc, rcut_smth=0.5, sel=sel, embed=(M,), axis=0, fit=(), descriptor=3)
+
+
+def test_se_e3_dimer_closed_form_energy_and_force():
+    """Isolated pair, M = 1, linear fitting: atom i's only pair is (j, j) with theta = R_j . R_j
+    = 2 s^2, so E = 2 (wf theta G(theta) / Nc^2 + bf), G(x) = tanh(w x + b) + x; and
+    dE/dr = 2 wf / Nc^2 (G + theta G') 4 s s'(r)."""
+    cfg = _e3_model()
+    w, b, wf, bf = 0.35, -0.2, 1.3, 0.1
+    p = np.array([w, b, wf, bf])
+    for r in (0.4, 1.3, 2.7, 3.9):
+        u = np.array([0.3, -0.8, np.sqrt(1 - 0.73)])
+        coord = np.array([[0.0, 0.0, 0.0], r * u])
+        res = oracle.compute(cfg, p, coord, np.zeros(2, np.int32), None)
+        s, ds = oracle.switch(r, 0.5, 4.0)
+        th = 2 * s * s
+        t = np.tanh(w * th + b)
+        G, dG = t + th, w * (1 - t * t) + 1.0
+        assert res.energy == pytest.approx(2 * (wf * th * G / 16 + bf), rel=1e-13)
+        dEdr = 2 * wf / 16 * (G + th * dG) * 4 * s * ds
+        np.testing.assert_allclose(res.force[1], -dEdr * u, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(res.virial, -dEdr * r * np.outer(u, u), rtol=1e-12, atol=1e-15)
+
+
+def test_se_e3_trimer_type_pair_nets_and_angle():
+    """Centre of type 0 with neighbours j (type 0) and k (type 1) at angle gamma, M = 1:
+    D = [th_jj G00(th_jj) + th_kk G11(th_kk) + th_jk (G01(th_jk) + G10(th_jk))] / Nc^2 with
+    th_jj = 2 s_j^2, th_kk = 2 s_k^2, th_jk = s_j s_k (1 + cos gamma); nets N^{a_j, a_k} stored
+    in the order (0,0), (0,1), (1,0), (1,1)."""
+    cfg = _e3_model(ntypes=2, sel=(2, 3), rc=3.0)
+    nets = [(0.4, 0.1), (-0.3, 0.2), (0.7, -0.5), (0.25, 0.05)]
+    p = np.concatenate([np.array(nets).ravel(), [1.0, 0.0], [0.0, 0.0]])
+    rj, rk = 1.1, 1.7
+    G = lambda n, x: np.tanh(nets[n][0] * x + nets[n][1]) + x  # noqa: E731
+    sw = lambda r: oracle.switch(r, 0.5, 3.0)[0]  # noqa: E731
+    for gam in (0.7, 1.9, 2.8):
+        coord = np.array([[0.0, 0.0, 0.0], [rj, 0.0, 0.0], [rk * np.cos(gam), rk * np.sin(gam), 0.0]])
+        res = oracle.compute(cfg, p, coord, np.array([0, 0, 1], np.int32), None)
+        sj, sk = sw(rj), sw(rk)
+        tjj, tkk, tjk = 2 * sj * sj, 2 * sk * sk, sj * sk * (1 + np.cos(gam))
+        D = (tjj * G(0, tjj) + tkk * G(3, tkk) + tjk * (G(1, tjk) + G(2, tjk))) / 25.0
+        assert res.atom_energy[0] == pytest.approx(D, rel=1e-13)
+
+
+def test_se_e3_padding_scales_descriptor_by_inverse_nc_squared():
+    cfg1 = _e3_model(sel=(24,), rc=3.0, M=3)
+    cfg2 = _e3_model(sel=(60,), rc=3.0, M=3)
+    rng = I.Rng(5)
+    p = np.concatenate([rng.normal(6), rng.normal(3), [0.0]])
+    fr = tiny_frame(seed=8)
+    e1 = oracle.compute(cfg1, p, fr.coord, np.zeros(fr.natoms, np.int32), fr.box)
+    e2 = oracle.compute(cfg2, p, fr.coord, np.zeros(fr.natoms, np.int32), fr.box)
+    assert e1.status == 0 and e2.status == 0
+    assert e2.energy == pytest.approx(e1.energy * (24 / 60) ** 2, rel=1e-12)
+
+
+KINDS = ["r", "hybrid", "e3", "hybrid_e3"]
+
+
+def _model(kind):
+    return {"r": tiny_model_r, "hybrid": tiny_model_hybrid, "e3": tiny_model_e3,
+            "hybrid_e3": tiny_model_hybrid_e3}[kind]()
+
+
 def _case(kind, seed=3):
-    cfg = tiny_model_r() if kind == "r" else tiny_model_hybrid()
+    cfg = _model(kind)
     fr = tiny_frame(seed=seed)
     p = I.make_params(cfg, 1)
     nl = oracle.nlist(cfg, fr.coord, fr.atype, fr.box)[:2]
     return cfg, fr, p, nl
 
 
-@pytest.mark.parametrize("kind", ["r", "hybrid"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_forces_and_virial_vs_dual_numbers(kind):
     cfg, fr, p, nl = _case(kind)
     r = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, nl=nl)
@@ -140,7 +221,7 @@ def test_forces_and_virial_vs_dual_numbers(kind):
             assert r.virial[a, b_] == pytest.approx(-dE, rel=1e-10, abs=1e-13)
 
 
-@pytest.mark.parametrize("kind", ["r", "hybrid"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_forces_vs_central_differences(kind):
     cfg, fr, p, nl = _case(kind)
     r = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, nl=nl)
@@ -163,7 +244,7 @@ def _rotation(seed):
     return q
 
 
-@pytest.mark.parametrize("kind", ["r", "hybrid"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_symmetries(kind):
     cfg, fr, p, _ = _case(kind, seed=9)
     base = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
@@ -185,12 +266,12 @@ def test_symmetries(kind):
     np.testing.assert_allclose(pr.force, base.force[perm], atol=1e-11)
 
 
-@pytest.mark.parametrize("kind", ["r", "hybrid"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_energy_continuous_across_cutoff(kind):
     """Move one atom radially across r_c of another: E(r_c - d) - E(r_c + d) = O(d^3)."""
-    cfg = tiny_model_r() if kind == "r" else tiny_model_hybrid()
+    cfg = _model(kind)
     p = I.make_params(cfg, 2)
-    rc = cfg.rcut
+    rc = cfg.list_rcut  # the outer cutoff: every part's terms in the moved atom vanish there
     base = np.array([[0.0, 0.0, 0.0], [1.2, 0.3, -0.4], [-0.5, 1.1, 0.2], [0.0, 0.0, 0.0]])
     atype = np.array([0, 1, 0, 1], np.int32)
     direction = np.array([0.36, -0.48, 0.8])
