@@ -67,20 +67,24 @@ extern "C" {
 #define DP_MAX_CANDIDATES 1024 /* atoms within r_c of one atom the list builder can hold */
 
 /* Descriptors (Sec. II.A.1) */
-#define DP_DESC_SE_E2_A 0 /* D = T T_<^T, T = G^T R / Nc, R rows (s, s x/r, s y/r, s z/r): M x M_<   */
-#define DP_DESC_SE_E2_R 1 /* R reduced to its radial column s: D = G^T s / Nc, M values            */
-#define DP_DESC_HYBRID 2  /* [se_e2_a block, se_e2_r block] concatenated; both parts share r_c, r_s,
-                             sel (one neighbour list) and the net index rule, each with its own
-                             embedding nets (embed[] for se_e2_a, embed_r[] for se_e2_r)        */
+#define DP_DESC_SE_E2_A 0   /* D = T T_<^T, T = G^T R / Nc, R rows (s, s x/r, s y/r, s z/r): M x M_< */
+#define DP_DESC_SE_E2_R 1   /* R reduced to its radial column s: D = G^T s / Nc, M values          */
+#define DP_DESC_HYBRID_R 2  /* se_e2_a part, then an se_e2_r part: D = [D_a, D_r]                  */
+#define DP_DESC_SE_E3 3     /* D = (R R^T) : G / Nc^2, G_jk = N^{a_j,a_k}(R_j . R_k): M values      */
+#define DP_DESC_HYBRID_E3 4 /* se_e2_a part, then an se_e3 part: D = [D_a, D_e3]                   */
 
 /* Model hyper-parameters (Sec. II.A.1, II.A.2, II.A.6).  embed[] are the embedding-net
  * widths (input width 1 is implied), fit[] the fitting-net hidden widths (a final linear
  * width-1 layer is implied).  ResNet skips follow Eq. (NN) with w_hat = 1.
- * descriptor DP_DESC_SE_E2_R uses embed[] for its nets and ignores axis; DP_DESC_HYBRID adds
- * the se_e2_r nets embed_r[] (n_embed_r layers).  The fitting-net input width is M * M_<,
- * M, or M * M_< + M_r (M_r = embed_r[n_embed_r - 1]).  Models other than se_e2_a run on the
- * CUDA-core path only (DP_PREC_FP64 / DP_PREC_FP32, uncompressed); other combinations are
- * refused with DP_E_UNSUPPORTED at creation. */
+ * rcut, rcut_smth, sel, embed describe the descriptor's (first) part; axis is read by
+ * se_e2_a parts only.  Hybrids take their second part from rcut_2, rcut_smth_2, sel_2,
+ * n_embed_2, embed_2.  Every part reads one neighbour list built with the larger cutoff and,
+ * per type, the larger sel of the parts: a part's own list (its sel[t] nearest type-t
+ * neighbours within its cutoff) is the prefix of each type block closer than its cutoff.
+ * se_e3 nets are indexed by the two neighbours' types (ntypes^2 nets, type_one_side not
+ * applicable).  The fitting-net input is the concatenation of the parts' D.  Descriptors other
+ * than se_e2_a run on the CUDA-core path only (DP_PREC_FP64 / DP_PREC_FP32, uncompressed);
+ * other combinations are refused with DP_E_UNSUPPORTED at creation. */
 typedef struct {
   int ntypes;
   int sel[DP_MAX_TYPES];
@@ -92,9 +96,12 @@ typedef struct {
   int n_fit;
   int fit[DP_MAX_LAYERS];
   int type_one_side; /* 0: nets N^{a_i,a_j}; 1: nets N^{a_j} */
-  int descriptor;    /* DP_DESC_*; 0 for an se_e2_a model */
-  int n_embed_r;     /* DP_DESC_HYBRID: layers of the se_e2_r embedding nets */
-  int embed_r[DP_MAX_LAYERS];
+  int descriptor; /* DP_DESC_*; 0 for an se_e2_a model */
+  /* hybrids: the second part */
+  double rcut_2, rcut_smth_2;
+  int sel_2[DP_MAX_TYPES];
+  int n_embed_2;
+  int embed_2[DP_MAX_LAYERS];
 } dp_model_config;
 
 typedef struct dp_model dp_model;
@@ -102,9 +109,9 @@ typedef struct dp_nlist dp_nlist;
 
 /* Create a model on `device` from host FP64 parameters.
  *   params: host, n_params doubles.  Layout: embedding nets in order of net index
- *           (a_i*ntypes + a_j, or a_j if type_one_side), then (hybrid) the se_e2_r nets in
- *           the same order, then fitting nets by type; per net, layer by layer, W
- *           row-major [in][out] then b[out].
+ *           (a_i*ntypes + a_j, or a_j if type_one_side; a_j*ntypes + a_k for se_e3), then
+ *           (hybrids) the second part's nets in the same way, then fitting nets by type;
+ *           per net, layer by layer, W row-major [in][out] then b[out].
  *   precision: DP_PREC_*.  compressed: 1 = replace the embedding nets by quintic
  *           tables (Eq. (compress)) built on the device at creation, over s in
  *           [0, 2] with stride 0.01 on [0, 1.8) and 0.1 on [1.8, 2].
@@ -115,7 +122,7 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
 
 /* Same as dp_model_create, reading a weight file: 8-byte magic "DPGBW002", the
  * dp_model_config struct as stored in memory, an int64 n_params, then n_params FP64.
- * Files with magic "DPGBW001" hold the struct without its last three fields (se_e2_a). */
+ * Files with magic "DPGBW001" hold the struct up to type_one_side (se_e2_a models). */
 int dp_init_model(const char* weight_path, int device, int precision, int compressed, dp_model** out);
 
 int dp_free_model(dp_model* model);
@@ -142,7 +149,8 @@ int dp_build_nlist(dp_model* model, int natoms, const double* coord, const int* 
  * where dp_build_nlist prefers a cell-centred kernel whose staging buffer is sized per frame)
  * but needs no model object and calls no allocating routine: its cell-list scratch is one
  * static device array of about 13.3 MiB that every GPU loading the library keeps until exit.
- *   cfg: only ntypes, sel and rcut are used.
+ *   cfg: only ntypes, sel and rcut are used (for a hybrid descriptor also rcut_2 and sel_2: the
+ *   list is the one its parts read, with the larger cutoff and per type the larger sel).
  *   coord [natoms*3] FP64, type [natoms]: device pointers.  box: host pointer (or NULL for
  *   open boundaries).  nl_j [natoms*Nc], nl_shift [natoms*Nc*3] int32: device pointers the
  *   caller owns, filled exactly as dp_nlist_export fills its host arrays.

@@ -45,6 +45,10 @@ __global__ void k_narrow(const double* __restrict__ x, long n, float* __restrict
 
 int skip_kind(int n_in, int n_out) { return n_out == n_in ? 1 : (n_out == 2 * n_in ? 2 : 0); }
 
+bool is_hybrid(const dp_model_config& c) {
+  return c.descriptor == DP_DESC_HYBRID_R || c.descriptor == DP_DESC_HYBRID_E3;
+}
+
 int check_config(const dp_model_config* c) {
   if (!c) return DP_E_ARG;
   if (c->ntypes < 1 || c->ntypes > DP_MAX_TYPES) return DP_E_ARG;
@@ -55,46 +59,72 @@ int check_config(const dp_model_config* c) {
     if (c->embed[l] < 1) return DP_E_ARG;
   for (int l = 0; l < c->n_fit; ++l)
     if (c->fit[l] < 1) return DP_E_ARG;
-  if (c->descriptor < DP_DESC_SE_E2_A || c->descriptor > DP_DESC_HYBRID) return DP_E_ARG;
-  if (c->descriptor != DP_DESC_SE_E2_R && (c->axis < 1 || c->axis > c->embed[c->n_embed - 1])) return DP_E_ARG;
-  if (c->descriptor == DP_DESC_HYBRID) {
-    if (c->n_embed_r < 1 || c->n_embed_r > DP_MAX_LAYERS) return DP_E_ARG;
-    for (int l = 0; l < c->n_embed_r; ++l)
-      if (c->embed_r[l] < 1) return DP_E_ARG;
-  }
+  if (c->descriptor < DP_DESC_SE_E2_A || c->descriptor > DP_DESC_HYBRID_E3) return DP_E_ARG;
+  const bool first_a = c->descriptor != DP_DESC_SE_E2_R && c->descriptor != DP_DESC_SE_E3;
+  if (first_a && (c->axis < 1 || c->axis > c->embed[c->n_embed - 1])) return DP_E_ARG;
   if (!(c->rcut > 0) || !(c->rcut_smth >= 0) || !(c->rcut_smth < c->rcut)) return DP_E_ARG;
+  if (is_hybrid(*c)) {
+    if (c->n_embed_2 < 1 || c->n_embed_2 > DP_MAX_LAYERS) return DP_E_ARG;
+    for (int l = 0; l < c->n_embed_2; ++l)
+      if (c->embed_2[l] < 1) return DP_E_ARG;
+    for (int t = 0; t < c->ntypes; ++t)
+      if (c->sel_2[t] < 1) return DP_E_ARG;
+    if (!(c->rcut_2 > 0) || !(c->rcut_smth_2 >= 0) || !(c->rcut_smth_2 < c->rcut_2)) return DP_E_ARG;
+  }
   return DP_OK;
 }
 
-// Width of the descriptor D the fitting net reads (Sec. II.A.1).
-int descriptor_width(const dp_model_config& c) {
-  const int M = c.embed[c.n_embed - 1];
-  if (c.descriptor == DP_DESC_SE_E2_R) return M;
-  if (c.descriptor == DP_DESC_HYBRID) return M * c.axis + c.embed_r[c.n_embed_r - 1];
-  return M * c.axis;
-}
-
-void layout_nets(int nets, int nl, const int* widths, long& off, std::vector<LayerDesc>* emb) {
-  for (int n = 0; n < nets; ++n) {
-    int prev = 1;
-    for (int l = 0; l < nl; ++l) {
-      LayerDesc L{prev, widths[l], off, skip_kind(prev, widths[l]), 1};
-      if (emb) emb->push_back(L);
-      off += (long)prev * widths[l] + widths[l];
-      prev = widths[l];
+// The parts of a descriptor (Sec. II.A.1), their nets' parameter layout from `off` on, and
+// their blocks of D (Dw receives the width of D).
+std::vector<PartDesc> make_parts(const dp_model_config& c, long& off, int& Dw) {
+  std::vector<PartDesc> parts;
+  auto add = [&](int kind, double rc, double rs, const int* sel, int nl, const int* widths) {
+    PartDesc P;
+    P.kind = kind;
+    P.rc = rc;
+    P.rs = rs;
+    P.nc = 0;
+    for (int t = 0; t < c.ntypes; ++t) {
+      P.sel[t] = sel[t];
+      P.sel_off[t] = P.nc;
+      P.nc += sel[t];
     }
-  }
+    P.sel_off[c.ntypes] = P.nc;
+    P.M = widths[nl - 1];
+    P.A = kind == PART_A ? c.axis : 0;
+    P.nl = nl;
+    // se_e3 nets are indexed by the two neighbours' types; two-body nets by (a_i, a_j) or a_j
+    P.n_nets = (kind == PART_E3 || !c.type_one_side) ? c.ntypes * c.ntypes : c.ntypes;
+    P.w_off = off;
+    for (int n = 0; n < P.n_nets; ++n) {
+      int prev = 1;
+      for (int l = 0; l < nl; ++l) {
+        P.emb.push_back(LayerDesc{prev, widths[l], off, skip_kind(prev, widths[l]), 1});
+        off += (long)prev * widths[l] + widths[l];
+        prev = widths[l];
+      }
+    }
+    P.per_net = (off - P.w_off) / P.n_nets;
+    P.doff = Dw;
+    Dw += kind == PART_A ? P.M * P.A : P.M;
+    parts.push_back(P);
+  };
+  Dw = 0;
+  const int d = c.descriptor;
+  const int k1 = d == DP_DESC_SE_E2_R ? PART_R : (d == DP_DESC_SE_E3 ? PART_E3 : PART_A);
+  add(k1, c.rcut, c.rcut_smth, c.sel, c.n_embed, c.embed);
+  if (is_hybrid(c))
+    add(d == DP_DESC_HYBRID_R ? PART_R : PART_E3, c.rcut_2, c.rcut_smth_2, c.sel_2, c.n_embed_2, c.embed_2);
+  return parts;
 }
 
-// Parameter layout: nets of embed[], (hybrid) nets of embed_r[], fitting nets by type.
-long layout(const dp_model_config& c, std::vector<LayerDesc>* emb, std::vector<LayerDesc>* fit,
-            std::vector<LayerDesc>* emb_r = nullptr) {
-  const int nets = c.type_one_side ? c.ntypes : c.ntypes * c.ntypes;
+// Parameter layout: the parts' embedding nets, then the fitting nets by type.
+long layout(const dp_model_config& c, std::vector<PartDesc>* parts_out, std::vector<LayerDesc>* fit, int* Dw_out) {
   long off = 0;
-  layout_nets(nets, c.n_embed, c.embed, off, emb);
-  if (c.descriptor == DP_DESC_HYBRID) layout_nets(nets, c.n_embed_r, c.embed_r, off, emb_r);
+  int Dw = 0;
+  std::vector<PartDesc> parts = make_parts(c, off, Dw);
   for (int t = 0; t < c.ntypes; ++t) {
-    int prev = descriptor_width(c);
+    int prev = Dw;
     for (int l = 0; l <= c.n_fit; ++l) {
       const bool last = (l == c.n_fit);
       const int no = last ? 1 : c.fit[l];
@@ -104,10 +134,21 @@ long layout(const dp_model_config& c, std::vector<LayerDesc>* emb, std::vector<L
       prev = no;
     }
   }
+  if (parts_out) *parts_out = parts;
+  if (Dw_out) *Dw_out = Dw;
   return off;
 }
 
 }  // namespace
+
+dp_model_config list_config(const dp_model_config& c) {
+  dp_model_config l = c;
+  if (is_hybrid(c)) {
+    l.rcut = std::max(c.rcut, c.rcut_2);
+    for (int t = 0; t < c.ntypes; ++t) l.sel[t] = std::max(c.sel[t], c.sel_2[t]);
+  }
+  return l;
+}
 
 int check_finite_host(const double* x, long n) {
   for (long k = 0; k < n; ++k)
@@ -276,7 +317,7 @@ int dp_wait_selftest(long spin_limit, void* stream) {
 
 long dp_model_n_params(const dp_model_config* cfg) {
   if (check_config(cfg) != DP_OK) return -1;
-  return layout(*cfg, nullptr, nullptr);
+  return layout(*cfg, nullptr, nullptr, nullptr);
 }
 
 int dp_model_create(const dp_model_config* cfg, const double* params, long n_params, int device, int precision,
@@ -300,7 +341,9 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   m.device = device;
   m.precision = precision;
   m.compressed = compressed ? 1 : 0;
-  m.n_params = layout(*cfg, &m.emb, &m.fit, &m.emb_r);
+  m.n_params = layout(*cfg, &m.parts, &m.fit, &m.Dw);
+  m.emb = m.parts[0].emb;
+  m.lcfg = list_config(*cfg);
   m.n_fit_layers = cfg->n_fit + 1;
   if (n_params != m.n_params) {
     set_error("n_params does not match the configuration (" + std::to_string(m.n_params) + " expected)");
@@ -310,20 +353,23 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   m.nc = 0;
   for (int t = 0; t < cfg->ntypes; ++t) {
     m.sel_off[t] = m.nc;
-    m.nc += cfg->sel[t];
+    m.nc += m.lcfg.sel[t];
   }
   m.sel_off[cfg->ntypes] = m.nc;
-  m.M = cfg->embed[cfg->n_embed - 1];
-  m.A = cfg->descriptor == DP_DESC_SE_E2_R ? 0 : cfg->axis;
-  m.Mr = cfg->descriptor == DP_DESC_SE_E2_A ? 0
-         : cfg->descriptor == DP_DESC_SE_E2_R ? m.M : cfg->embed_r[cfg->n_embed_r - 1];
-  m.Dw = descriptor_width(*cfg);
-  m.n_embed_nets = cfg->type_one_side ? cfg->ntypes : cfg->ntypes * cfg->ntypes;
+  m.M = m.parts[0].M;
+  m.A = m.parts[0].A;
+  m.n_embed_nets = m.parts[0].n_nets;
   if (cfg->descriptor != DP_DESC_SE_E2_A && (compressed || precision > DP_PREC_FP32)) {
-    set_error("se_e2_r and hybrid models run uncompressed in FP64 or FP32");
+    set_error("se_e2_r, se_e3 and hybrid models run uncompressed in FP64 or FP32");
     delete md;
     return DP_E_UNSUPPORTED;
   }
+  for (const PartDesc& P : m.parts)
+    if (P.kind == PART_E3 && !e3_supported(P, precision)) {
+      set_error("se_e3 embedding widths above 32, or nets too large for shared memory");
+      delete md;
+      return DP_E_UNSUPPORTED;
+    }
   if (precision == DP_PREC_TF32 && compressed) {
     set_error("TF32 applies to the network GEMMs of the uncompressed model");
     delete md;

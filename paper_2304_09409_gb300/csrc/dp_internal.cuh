@@ -81,6 +81,24 @@ struct LayerDesc {
   int tanh_act;
 };
 
+// One descriptor part (Sec. II.A.1): its own cutoffs, sel and embedding nets, writing the
+// block [doff, doff + width) of D.  A model has one part, or two for a hybrid.
+enum PartKind { PART_A = 0, PART_R = 1, PART_E3 = 2 };
+struct PartDesc {
+  int kind;
+  double rc, rs;
+  int sel[DP_MAX_TYPES];
+  int sel_off[DP_MAX_TYPES + 1];
+  int nc;
+  int M, A;      // output width of its nets; M_< (se_e2_a parts)
+  int doff;      // first column of its block of D
+  int nl;        // embedding layers
+  int n_nets;    // N_t^2, or N_t (two-body nets with type_one_side)
+  long w_off;    // offset of its first net's parameters
+  long per_net;  // parameters of one net
+  std::vector<LayerDesc> emb;  // per net * nl + layer
+};
+
 struct TableDesc {
   double s0, stride1, stride2;
   int n1, n2;
@@ -92,11 +110,13 @@ struct DeviceModel {
   int precision;
   int compressed;
   int nc, M, A, n_embed_nets;
-  int Mr;  // width of the se_e2_r block of D (0 for se_e2_a)
-  int Dw;  // width of D: M * A, M (se_e2_r) or M * A + Mr (hybrid)
+  int Dw;  // width of D (the fitting net's input)
+  // neighbour-list geometry (nc, sel_off, lcfg.rcut, lcfg.sel): for a hybrid, the larger cutoff
+  // and per type the larger sel of its parts; for one part, the part's own
   int sel_off[DP_MAX_TYPES + 1];
-  std::vector<LayerDesc> emb;    // per net * n_embed + layer
-  std::vector<LayerDesc> emb_r;  // hybrid: the se_e2_r nets, per net * n_embed_r + layer
+  dp_model_config lcfg;
+  std::vector<PartDesc> parts;
+  std::vector<LayerDesc> emb;  // first part's nets, per net * n_embed + layer
   std::vector<LayerDesc> fit;  // per type * n_fit_layers + layer
   int n_fit_layers;
   long n_params;
@@ -133,6 +153,9 @@ struct DeviceModel {
 // Error state and helpers (capi.cu)
 // ------------------------------------------------------------------------------------------
 void set_error(const std::string& msg);
+// The configuration the neighbour list is built with: the larger cutoff and, per type, the larger
+// sel of a hybrid's parts (a one-part configuration unchanged).
+dp_model_config list_config(const dp_model_config& c);
 #define DP_CUDA_TRY(expr)                                                                   \
   do {                                                                                      \
     cudaError_t _e = (expr);                                                                \

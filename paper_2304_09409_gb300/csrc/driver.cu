@@ -176,7 +176,7 @@ int build_tables_host(dp_model* md, int F, const int* natoms, const double* boxe
   T.boxes.assign(9 * (size_t)F, 0.0);
   T.cap = 0;
   for (int f = 0; f < F; ++f) {
-    const int rc = host_geometry(md->m.cfg, natoms[f], boxes ? boxes + 9 * f : nullptr, lohi, T.geoms[f]);
+    const int rc = host_geometry(md->m.lcfg, natoms[f], boxes ? boxes + 9 * f : nullptr, lohi, T.geoms[f]);
     if (rc != DP_OK) return rc;
     NlGeom& g = T.geoms[f];
     if (md->nl_full_cap) g.cap = DP_MAX_CANDIDATES;
@@ -283,14 +283,18 @@ PathConst make_pc(const DeviceModel& m, int N) {
   pc.nc = m.nc;
   pc.M = m.M;
   pc.A = m.A;
-  pc.Mr = m.Mr;
   pc.Dw = m.Dw;
+  pc.doff = 0;
+  pc.kind = m.parts[0].kind;
   pc.ntypes = m.cfg.ntypes;
   pc.type_one_side = m.cfg.type_one_side;
-  for (int t = 0; t < m.cfg.ntypes; ++t) pc.sel[t] = m.cfg.sel[t];
-  for (int t = 0; t <= m.cfg.ntypes; ++t) pc.sel_off[t] = m.sel_off[t];
-  pc.rs = m.cfg.rcut_smth;
-  pc.rc = m.cfg.rcut;
+  // list geometry (for a one-part model, the part's own)
+  for (int t = 0; t < m.cfg.ntypes; ++t) pc.sel[t] = m.lcfg.sel[t];
+  for (int t = 0; t <= m.cfg.ntypes; ++t) pc.sel_off[t] = pc.lsel_off[t] = m.sel_off[t];
+  pc.lnc = m.nc;
+  pc.rs = m.parts[0].rs;
+  pc.rc = m.lcfg.rcut;
+  pc.rc2 = m.lcfg.rcut * m.lcfg.rcut;
   return pc;
 }
 

@@ -146,6 +146,12 @@ __device__ __forceinline__ int slot_block(const PathConst& pc, int k) {
   return t;
 }
 
+// List slot read by slot k of the current part (the same position in the same type block).
+__device__ __forceinline__ int list_slot(const PathConst& pc, int k) {
+  const int t = slot_block(pc, k);
+  return pc.lsel_off[t] + (k - pc.sel_off[t]);
+}
+
 __device__ __forceinline__ int net_of(const PathConst& pc, int ti, int tj) {
   return pc.type_one_side ? tj : ti * pc.ntypes + tj;
 }

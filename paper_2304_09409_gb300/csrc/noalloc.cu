@@ -130,6 +130,9 @@ extern "C" int dp_build_nlist_noalloc(const dp_model_config* cfg, int natoms, co
     set_error("invalid model configuration");
     return DP_E_ARG;
   }
+  // a hybrid descriptor's list: the larger cutoff and, per type, the larger sel of its parts
+  const dp_model_config lcfg = list_config(*cfg);
+  cfg = &lcfg;
   long nc = 0;
   for (int t = 0; t < cfg->ntypes; ++t) {
     if (cfg->sel[t] < 1) {

@@ -1,12 +1,13 @@
 // The energy / force / virial path on CUDA cores (FP64 or FP32 networks), for the se_e2_a,
-// se_e2_r and hybrid descriptors.
+// se_e2_r, se_e3 and hybrid descriptors.
 //
 // Steps (sorted-atom index p, neighbour slot k, row = p * Nc + k):
 //   env      R_k = (s, s u) with u = r_ij / r, s = s(r)            Eqs. (rij), (switch)
 //   emb      G_k = N^{a_i, a_j}(s) layer by layer                  Eqs. (G2), (NN)
 //   contract T = G^T R / Nc,  D = T T_<^T                          se_e2_a descriptor
 //            D_r = G_r^T s / Nc                                    se_e2_r descriptor
-//            (hybrid: D = [D_a, D_r], each part with its own nets) Sec. II.A.1
+//            D_3 = (R R^T) : G_3 / Nc^2                            se_e3 descriptor
+//            (hybrid: D = [D_1, D_2], each part with its own cutoffs, sel and nets)  Sec. II.A.1
 //   fit      E_i = F^{a_i}(D)                                      Eq. (fitting_energy)
 //   backward dE/dD -> dE/dT -> (dE/dG, dE/dR) -> dE/ds -> dE/dr_ij
 //   force    F_i += dE/dr_ij, F_j -= dE/dr_ij (FP64 atomics)        Sec. II.A.2
@@ -31,12 +32,15 @@ __global__ void k_env(PathConst pc, const double* __restrict__ coord, const int*
   if (row >= (long)pc.natoms * pc.nc) return;
   const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
   const int i = perm[p];
-  const int j = nl_j[(long)i * pc.nc + k];
+  const long ls = (long)i * pc.lnc + list_slot(pc, k);
+  const int j = nl_j[ls];
   R o[4] = {R(0), R(0), R(0), R(0)};
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0, r2 = 0.0;
   if (j >= 0) {
-    double d0, d1, d2;
-    listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d0, d1, d2);
-    const double r2 = norm2_exact(d0, d1, d2);
+    listed_disp(coord + 3 * i, coord + 3 * j, nl_code[ls], pc, frame_of(pc, i), d0, d1, d2);
+    r2 = norm2_exact(d0, d1, d2);
+  }
+  if (j >= 0 && r2 < pc.rc2) {
     R r, s, ds, u[3];
     pair_env<R>(d0, d1, d2, r2, pc.rs, pc.rc, pc.near2, r, s, ds, u);
     o[0] = s;
@@ -66,11 +70,10 @@ __global__ void k_emb_first(PathConst pc, NetPtrs<R> nets, const int* __restrict
   T[e] = t;
 }
 
-// dE/ds through the first layer; `accum` adds to gs (a second embedding family of a hybrid).
 template <class R>
 __global__ void k_emb_first_bwd(PathConst pc, NetPtrs<R> nets, const int* __restrict__ atom_type_sorted,
                                 const R* __restrict__ GY, const R* __restrict__ T, int w1, int skip,
-                                R* __restrict__ gs, int accum) {
+                                R* __restrict__ gs) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= (long)pc.natoms * pc.nc) return;
   const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
@@ -83,7 +86,7 @@ __global__ void k_emb_first_bwd(PathConst pc, NetPtrs<R> nets, const int* __rest
     acc += g * (R(1) - t * t) * w[o];
     if (skip) acc += g;
   }
-  gs[row] = accum ? gs[row] + acc : acc;
+  gs[row] = acc;
 }
 
 // ---- T = G^T R / Nc and D = T T_<^T, one block per atom -------------------------------------
@@ -119,7 +122,7 @@ __global__ void k_contract(PathConst pc, const R* __restrict__ G, const R* __res
   __syncthreads();
   for (int idx = threadIdx.x; idx < M * A; idx += blockDim.x) {
     const int m = idx / A, l = idx % A;
-    D[(long)p * pc.Dw + idx] =
+    D[(long)p * pc.Dw + pc.doff + idx] =
         Ts[m * 4] * Ts[l * 4] + Ts[m * 4 + 1] * Ts[l * 4 + 1] + Ts[m * 4 + 2] * Ts[l * 4 + 2] + Ts[m * 4 + 3] * Ts[l * 4 + 3];
   }
 }
@@ -136,7 +139,7 @@ __global__ void k_descr_bwd(PathConst pc, const R* __restrict__ Tm, const R* __r
   R* gDs = gTs + M * 4;                  // [M][A]
   const int p = blockIdx.x;
   for (int e = threadIdx.x; e < M * 4; e += blockDim.x) Ts[e] = Tm[(long)p * M * 4 + e];
-  for (int e = threadIdx.x; e < M * A; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + e];
+  for (int e = threadIdx.x; e < M * A; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + pc.doff + e];
   __syncthreads();
   for (int e = threadIdx.x; e < M * 4; e += blockDim.x) {
     const int m = e / 4, c = e % 4;
@@ -174,31 +177,30 @@ __global__ void k_descr_bwd(PathConst pc, const R* __restrict__ Tm, const R* __r
 }
 
 // ---- se_e2_r block: D_r[m] = (1/Nc) sum_k G_r[k][m] s_k, one block per atom -------------------
-// G rows hold Mr values; D_r is written at column `off` of D (row stride Dw).
+// G rows hold M values; D_r goes to the part's block of D (row stride Dw).
 template <class R>
-__global__ void k_contract_r(PathConst pc, const R* __restrict__ G, const R* __restrict__ Renv, int off,
-                             R* __restrict__ D) {
+__global__ void k_contract_r(PathConst pc, const R* __restrict__ G, const R* __restrict__ Renv, R* __restrict__ D) {
   const int p = blockIdx.x;
-  const int Mr = pc.Mr, nc = pc.nc;
+  const int M = pc.M, nc = pc.nc;
   const long rb = (long)p * nc;
-  for (int m = threadIdx.x; m < Mr; m += blockDim.x) {
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
     R acc = 0;
-    for (int k = 0; k < nc; ++k) acc += G[(rb + k) * Mr + m] * Renv[(rb + k) * 4];
-    D[(long)p * pc.Dw + off + m] = acc / R(nc);
+    for (int k = 0; k < nc; ++k) acc += G[(rb + k) * M + m] * Renv[(rb + k) * 4];
+    D[(long)p * pc.Dw + pc.doff + m] = acc / R(nc);
   }
 }
 
 // Reverse of k_contract_r: dE/dG_r[k][m] = gD_r[m] s_k / Nc into gG, and the direct term
-// dE/ds_k = sum_m gD_r[m] G_r[k][m] / Nc into the radial component of gR (added to what the
-// se_e2_a block wrote when `accum`, else gR = (term, 0, 0, 0)).  One block per atom, a warp per row.
+// dE/ds_k = sum_m gD_r[m] G_r[k][m] / Nc as the radial component of gR (the other three zero).
+// One block per atom, a warp per row.
 template <class R>
-__global__ void k_descr_bwd_r(PathConst pc, const R* __restrict__ gD, int off, const R* __restrict__ G,
-                              const R* __restrict__ Renv, R* __restrict__ gG, R* __restrict__ gR, int accum) {
+__global__ void k_descr_bwd_r(PathConst pc, const R* __restrict__ gD, const R* __restrict__ G,
+                              const R* __restrict__ Renv, R* __restrict__ gG, R* __restrict__ gR) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  R* gDs = reinterpret_cast<R*>(sm_raw);  // [Mr]
+  R* gDs = reinterpret_cast<R*>(sm_raw);  // [M]
   const int p = blockIdx.x;
-  const int Mr = pc.Mr, nc = pc.nc;
-  for (int e = threadIdx.x; e < Mr; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + off + e];
+  const int M = pc.M, nc = pc.nc;
+  for (int e = threadIdx.x; e < M; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + pc.doff + e];
   __syncthreads();
   const R inv_nc = R(1) / R(nc);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -206,21 +208,195 @@ __global__ void k_descr_bwd_r(PathConst pc, const R* __restrict__ gD, int off, c
     const long row = (long)p * nc + k;
     const R s = Renv[row * 4];
     R acc = 0;
-    for (int m = lane; m < Mr; m += 32) {
-      acc += gDs[m] * G[row * Mr + m];
-      gG[row * Mr + m] = gDs[m] * s * inv_nc;
+    for (int m = lane; m < M; m += 32) {
+      acc += gDs[m] * G[row * M + m];
+      gG[row * M + m] = gDs[m] * s * inv_nc;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      typename Vec4<R>::T* g4 = reinterpret_cast<typename Vec4<R>::T*>(gR) + row;
-      if (accum) {
-        typename Vec4<R>::T v = *g4;
-        v.x += acc * inv_nc;
-        *g4 = v;
+    if (lane == 0) reinterpret_cast<typename Vec4<R>::T*>(gR)[row] = Vec4<R>::make(acc * inv_nc, R(0), R(0), R(0));
+  }
+}
+
+// ---- se_e3 part: fused pair kernel, one block per atom -------------------------------------------
+// Over the pairs (j, k) of the atom's real neighbours (rows with s > 0), theta = R_j . R_k and
+// G = N^{a_j,a_k}(theta), with dG/dtheta carried forward alongside (the nets have a scalar input):
+//   forward   D_m = (1/Nc^2) sum_jk theta G_m
+//   backward  dE/dtheta_jk = (1/Nc^2) sum_m gD_m (G_m + theta G'_m),
+//             dE/dR_j += dE/dtheta_jk R_k,  dE/dR_k += dE/dtheta_jk R_j
+// Nothing of G is stored: the backward pass evaluates the nets again.  All of the part's nets sit
+// in shared memory; a warp takes rows j, its lanes the partners k.
+struct E3Net {
+  int nl;
+  int in[DP_MAX_LAYERS], out[DP_MAX_LAYERS], skip[DP_MAX_LAYERS];
+  int loff[DP_MAX_LAYERS];  // offset of layer l's W inside one net (b follows W)
+  int per_net;              // parameters per net
+};
+
+template <class R, int W>
+__device__ __forceinline__ void e3_eval(const E3Net& nt, const R* __restrict__ w, R th, R* g, R* dg) {
+  R x[W], dx[W];
+#pragma unroll
+  for (int o = 0; o < W; ++o) {
+    x[o] = R(0);
+    dx[o] = R(0);
+  }
+  x[0] = th;
+  dx[0] = R(1);
+  for (int l = 0; l < nt.nl; ++l) {
+    const int ni = nt.in[l], no = nt.out[l], sk = nt.skip[l];
+    const R* Wl = w + nt.loff[l];
+    const R* bl = Wl + ni * no;
+    R y[W], dy[W];
+#pragma unroll
+    for (int o = 0; o < W; ++o) {
+      if (o < no) {
+        R z = bl[o], dz = R(0);
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+          if (i < ni) {
+            const R wv = Wl[i * no + o];
+            z += x[i] * wv;
+            dz += dx[i] * wv;
+          }
+        const R t = tanh_r(z);
+        R yo = t, dyo = (R(1) - t * t) * dz;
+        if (sk == 1) {
+          yo += x[o];
+          dyo += dx[o];
+        } else if (sk == 2) {
+          const int q = o < ni ? o : o - ni;  // {x, x}: n_out = 2 n_in
+          R xq = R(0), dxq = R(0);
+#pragma unroll
+          for (int i = 0; i < W; ++i)  // a select chain keeps x in registers
+            if (i == q) {
+              xq = x[i];
+              dxq = dx[i];
+            }
+          yo += xq;
+          dyo += dxq;
+        }
+        y[o] = yo;
+        dy[o] = dyo;
       } else {
-        *g4 = Vec4<R>::make(acc * inv_nc, R(0), R(0), R(0));
+        y[o] = R(0);
+        dy[o] = R(0);
       }
     }
+#pragma unroll
+    for (int o = 0; o < W; ++o) {
+      x[o] = y[o];
+      dx[o] = dy[o];
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < W; ++o) {
+    g[o] = x[o];
+    dg[o] = dx[o];
+  }
+}
+
+// BWD = 0: D block; BWD = 1: dE/dR rows (gR, [rows][4], every row of the atom written).
+template <class R, int W, int BWD>
+__global__ void __launch_bounds__(128)
+    k_e3(PathConst pc, E3Net nt, const R* __restrict__ params, int n_nets, const R* __restrict__ Renv,
+         const R* __restrict__ gD, R* __restrict__ D, R* __restrict__ gR) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  typedef typename Vec4<R>::T V4;
+  const int nc = pc.nc, M = pc.M, nt_types = pc.ntypes;
+  V4* Rv = reinterpret_cast<V4*>(sm_raw);     // [nc] rows of the real neighbours, compacted
+  V4* gRv = Rv + nc;                          // [nc] dE/dR of those rows (backward)
+  R* wsm = reinterpret_cast<R*>(gRv + nc);    // [n_nets * per_net]
+  R* red = wsm + (long)n_nets * nt.per_net;   // [W] D sums / gD
+  int* tv = reinterpret_cast<int*>(red + W);  // [nc] neighbour type of each compacted row
+  int* kv = tv + nc;                          // [nc] slot of each compacted row
+  __shared__ int nv_s;
+  const int p = blockIdx.x;
+  const long rb = (long)p * nc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (long e = tid; e < (long)n_nets * nt.per_net; e += blockDim.x) wsm[e] = params[e];
+  if (tid < W) red[tid] = (BWD && tid < M) ? gD[(long)p * pc.Dw + pc.doff + tid] : R(0);
+  if (warp == 0) {  // compaction of the rows with s > 0, in slot order
+    int nv = 0;
+    for (int base = 0; base < nc; base += 32) {
+      const int k = base + lane;
+      const bool v = k < nc && Renv[(rb + k) * 4] != R(0);
+      const unsigned mask = __ballot_sync(0xffffffffu, v);
+      if (v) {
+        const int at = nv + __popc(mask & ((1u << lane) - 1u));
+        Rv[at] = reinterpret_cast<const V4*>(Renv)[rb + k];
+        tv[at] = slot_block(pc, k);
+        kv[at] = k;
+      }
+      nv += __popc(mask);
+    }
+    if (lane == 0) nv_s = nv;
+  }
+  __syncthreads();
+  const int nv = nv_s;
+  if (BWD)
+    for (int e = tid; e < nv; e += blockDim.x) gRv[e] = Vec4<R>::make(R(0), R(0), R(0), R(0));
+  __syncthreads();
+  const R inv = R(1) / (R(nc) * R(nc));
+  R acc[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) acc[m] = R(0);
+  for (int j = warp; j < nv; j += nw) {
+    const V4 rj = Rv[j];
+    const int tj = tv[j];
+    R gj0 = 0, gj1 = 0, gj2 = 0, gj3 = 0;
+    for (int k = lane; k < nv; k += 32) {
+      const V4 rk = Rv[k];
+      const R th = ((rj.x * rk.x + rj.y * rk.y) + rj.z * rk.z) + rj.w * rk.w;
+      R g[W], dg[W];
+      e3_eval<R, W>(nt, wsm + (long)(tj * nt_types + tv[k]) * nt.per_net, th, g, dg);
+      if (!BWD) {
+#pragma unroll
+        for (int m = 0; m < W; ++m) acc[m] += th * g[m];
+      } else {
+        R gth = 0;
+#pragma unroll
+        for (int m = 0; m < W; ++m) gth += red[m] * (g[m] + th * dg[m]);
+        gth *= inv;
+        gj0 += gth * rk.x;
+        gj1 += gth * rk.y;
+        gj2 += gth * rk.z;
+        gj3 += gth * rk.w;
+        atomicAdd(&gRv[k].x, gth * rj.x);
+        atomicAdd(&gRv[k].y, gth * rj.y);
+        atomicAdd(&gRv[k].z, gth * rj.z);
+        atomicAdd(&gRv[k].w, gth * rj.w);
+      }
+    }
+    if (BWD) {
+      for (int o = 16; o > 0; o >>= 1) {
+        gj0 += __shfl_xor_sync(0xffffffffu, gj0, o);
+        gj1 += __shfl_xor_sync(0xffffffffu, gj1, o);
+        gj2 += __shfl_xor_sync(0xffffffffu, gj2, o);
+        gj3 += __shfl_xor_sync(0xffffffffu, gj3, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&gRv[j].x, gj0);
+        atomicAdd(&gRv[j].y, gj1);
+        atomicAdd(&gRv[j].z, gj2);
+        atomicAdd(&gRv[j].w, gj3);
+      }
+    }
+  }
+  if (!BWD) {
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+      R v = acc[m];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && m < M) atomicAdd(&red[m], v);
+    }
+    __syncthreads();
+    if (tid < M) D[(long)p * pc.Dw + pc.doff + tid] = red[tid] * inv;
+  } else {
+    __syncthreads();
+    V4* out = reinterpret_cast<V4*>(gR) + rb;
+    for (int k = tid; k < nc; k += blockDim.x) out[k] = Vec4<R>::make(R(0), R(0), R(0), R(0));
+    __syncthreads();
+    for (int e = tid; e < nv; e += blockDim.x) out[kv[e]] = gRv[e];
   }
 }
 
@@ -234,16 +410,19 @@ __global__ void __launch_bounds__(256)
   if (row < (long)pc.natoms * pc.nc) {
     const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
     const int i = perm[p];
-    const int j = nl_j[(long)i * pc.nc + k];
+    const long ls = (long)i * pc.lnc + list_slot(pc, k);
+    const int j = nl_j[ls];
+    double d[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
     if (j >= 0) {
-      double d[3];
-      listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d[0], d[1], d[2]);
-      const double r2 = norm2_exact(d[0], d[1], d[2]);
+      listed_disp(coord + 3 * i, coord + 3 * j, nl_code[ls], pc, frame_of(pc, i), d[0], d[1], d[2]);
+      r2 = norm2_exact(d[0], d[1], d[2]);
+    }
+    if (j >= 0 && r2 < pc.rc2) {
       R r, s, ds, u[3];
       pair_env<R>(d[0], d[1], d[2], r2, pc.rs, pc.rc, pc.near2, r, s, ds, u);
       const typename Vec4<R>::T g4 = reinterpret_cast<const typename Vec4<R>::T*>(gR)[row];
       const R gvu = g4.y * u[0] + g4.z * u[1] + g4.w * u[2];
-      const R gsum = gs_emb[row] + g4.x + gvu;
+      const R gsum = (gs_emb ? gs_emb[row] : R(0)) + g4.x + gvu;
       const R a = ds * gsum, b = s / r;
       const R gv[3] = {g4.y, g4.z, g4.w};
       double gd[3];
@@ -388,141 +567,197 @@ int run_fitting(const DeviceModel& m, const PathConst& pc, const R* params, cons
   return DP_OK;
 }
 
-// One family of embedding nets (the se_e2_a nets, or the se_e2_r nets of a hybrid): layer
-// descriptors, layer count and per-layer outputs / tanh values over all rows.
+// Per-part scratch of the CUDA-core path.
 template <class R>
-struct EmbFamily {
-  const std::vector<LayerDesc>* layers;
-  int nl;
-  std::vector<R*> Y, T;
+struct PartBufs {
+  PathConst pc;
+  R* Renv = nullptr;       // [rows][4]
+  std::vector<R*> Y, T;    // two-body parts: per layer outputs and tanh values
+  R* Tm = nullptr;         // se_e2_a: [N][M][4]
+  R* gR = nullptr;         // [rows][4]
+  R* gs = nullptr;         // two-body parts: dE/ds through the nets [rows]
+  NetPtrs<R> nets;         // first layers of the part's nets
 };
 
+bool e3_supported(const PartDesc& P, int precision) {
+  int w = 1;
+  for (int l = 0; l < P.nl; ++l) w = std::max(w, P.emb[l].n_out);
+  const size_t bytes = (size_t)P.n_nets * P.per_net * (precision == DP_PREC_FP64 ? 8 : 4);
+  return w <= 32 && bytes <= 96 * 1024 && P.nc <= 4096;
+}
+
+template <class R, int W>
+cudaError_t launch_e3_w(const PathConst& pc, const E3Net& nt, const R* w, int n_nets, const R* Renv, const R* gD,
+                        R* D, R* gR, bool bwd, cudaStream_t st) {
+  const size_t smem = sizeof(typename Vec4<R>::T) * 2 * pc.nc + sizeof(R) * ((size_t)n_nets * nt.per_net + W) +
+                      sizeof(int) * 2 * pc.nc;
+  auto kf = k_e3<R, W, 0>;
+  auto kb = k_e3<R, W, 1>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_max_smem(bwd ? kb : kf);
+    if (e != cudaSuccess) return e;
+  }
+  if (bwd)
+    kb<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, nt, w, n_nets, Renv, gD, D, gR);
+  else
+    kf<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, nt, w, n_nets, Renv, gD, D, gR);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_e3(const PartDesc& P, const PathConst& pc, const R* params, const R* Renv, const R* gD, R* D,
+                      R* gR, bool bwd, cudaStream_t st) {
+  E3Net nt;
+  std::memset(&nt, 0, sizeof(nt));
+  nt.nl = P.nl;
+  int w = 1;
+  for (int l = 0; l < P.nl; ++l) {
+    const LayerDesc& L = P.emb[l];
+    nt.in[l] = L.n_in;
+    nt.out[l] = L.n_out;
+    nt.skip[l] = L.skip;
+    nt.loff[l] = (int)(L.w_off - P.w_off);
+    w = std::max(w, L.n_out);
+  }
+  nt.per_net = (int)P.per_net;
+  const R* wp = params + P.w_off;
+  if (w <= 8) return launch_e3_w<R, 8>(pc, nt, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
+  if (w <= 16) return launch_e3_w<R, 16>(pc, nt, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
+  return launch_e3_w<R, 32>(pc, nt, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
+}
+
+// The whole path on CUDA cores for any descriptor: each part (Sec. II.A.1) builds its own
+// environment rows from its slots of the one neighbour list, runs its embedding nets and writes
+// its block of D; one fitting net reads D; each part then runs its reverse pass and scatters its
+// pair forces and virials.
 template <class R>
 int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, const PathIO& io, Arena& ar,
                 cudaStream_t st) {
-  const long N = pc.natoms, nc = pc.nc, rows = N * nc;
-  const int M = pc.M, A = pc.A, desc = m.cfg.descriptor;
-  const bool ang = desc != DP_DESC_SE_E2_R, rad = desc != DP_DESC_SE_E2_A;
-  // family 0: nets of embed[] (se_e2_a, or se_e2_r alone); family 1: the hybrid's se_e2_r nets
-  const int nfam = desc == DP_DESC_HYBRID ? 2 : 1;
-  EmbFamily<R> fam[2];
-  fam[0].layers = &m.emb;
-  fam[0].nl = m.cfg.n_embed;
-  fam[1].layers = &m.emb_r;
-  fam[1].nl = m.cfg.n_embed_r;
-  // ---- scratch ----
-  R* Renv = ar.get<R>(rows * 4);
-  int maxe = 1;
-  for (int f = 0; f < nfam; ++f)
-    for (int l = 0; l < fam[f].nl; ++l) {
-      const int w = (*fam[f].layers)[l].n_out;
-      fam[f].Y.push_back(ar.get<R>(rows * w));
-      fam[f].T.push_back(ar.get<R>(rows * w));
-      maxe = std::max(maxe, w);
+  const long N = pc.natoms;
+  const int nparts = (int)m.parts.size();
+  std::vector<PartBufs<R>> pb(nparts);
+  long maxe = 1;  // widest embedding-gradient buffer over the parts
+  for (int q = 0; q < nparts; ++q) {
+    const PartDesc& P = m.parts[q];
+    PartBufs<R>& b = pb[q];
+    b.pc = part_pc(pc, P);
+    const long rows = N * P.nc;
+    b.Renv = ar.get<R>(rows * 4);
+    b.gR = ar.get<R>(rows * 4);
+    if (P.kind == PART_E3) continue;
+    for (int l = 0; l < P.nl; ++l) {
+      const int w = P.emb[l].n_out;
+      b.Y.push_back(ar.get<R>(rows * w));
+      b.T.push_back(ar.get<R>(rows * w));
+      maxe = std::max(maxe, rows * w);
     }
-  R* Tm = ang ? ar.get<R>(N * M * 4) : nullptr;
+    if (P.kind == PART_A) b.Tm = ar.get<R>(N * P.M * 4);
+    b.gs = ar.get<R>(rows);
+  }
   R* D = ar.get<R>(N * pc.Dw);
-  R* geA = ar.get<R>(rows * maxe);
-  R* geB = ar.get<R>(rows * maxe);
-  R* gR = ar.get<R>(rows * 4);
-  R* gs = ar.get<R>(rows);
+  R* geA = ar.get<R>(maxe);
+  R* geB = ar.get<R>(maxe);
   int* tsorted = ar.get<int>(N);
-  const unsigned fblocks = nblk(rows, 256);
   const R* gD = nullptr;
   if (ar.measure) return run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
   if (!ar.ok()) {
     set_error("scratch allocation failed");
     return DP_E_OOM;
   }
-  // ---- forward ----
   {
     ProfScope _ps(io.prof, "sorted_types", st);
     k_sorted_types<<<nblk(N, 256), 256, 0, st>>>(io.type, io.perm, (int)N, tsorted);
   }
-  {
-    ProfScope _ps(io.prof, "env", st);
-    k_env<R><<<nblk(rows, 256), 256, 0, st>>>(pc, io.coord, io.perm, io.nl_j, io.nl_code, Renv);
-  }
-  NetPtrs<R> nets[2];
-  for (int f = 0; f < nfam; ++f) {
-    const std::vector<LayerDesc>& Ls = *fam[f].layers;
-    const int ne = fam[f].nl;
-    for (int n = 0; n < m.n_embed_nets; ++n) {
-      const LayerDesc& L0 = Ls[(size_t)n * ne];
-      nets[f].w0[n] = params + L0.w_off;
-      nets[f].b0[n] = params + L0.w_off + (long)L0.n_in * L0.n_out;
-    }
-    const LayerDesc& L0 = Ls[0];
+  // ---- forward, part by part ----
+  for (int q = 0; q < nparts; ++q) {
+    const PartDesc& P = m.parts[q];
+    PartBufs<R>& b = pb[q];
+    const PathConst& pq = b.pc;
+    const long rows = N * P.nc;
     {
+      ProfScope _ps(io.prof, "env", st);
+      k_env<R><<<nblk(rows, 256), 256, 0, st>>>(pq, io.coord, io.perm, io.nl_j, io.nl_code, b.Renv);
+    }
+    if (P.kind == PART_E3) {
+      ProfScope _ps(io.prof, "e3_fwd", st);
+      DP_CUDA_TRY(launch_e3<R>(P, pq, params, b.Renv, nullptr, D, nullptr, false, st));
+      continue;
+    }
+    for (int n = 0; n < P.n_nets; ++n) {
+      const LayerDesc& L0 = P.emb[(size_t)n * P.nl];
+      b.nets.w0[n] = params + L0.w_off;
+      b.nets.b0[n] = params + L0.w_off + (long)L0.n_in * L0.n_out;
+    }
+    {
+      const LayerDesc& L0 = P.emb[0];
       ProfScope _ps(io.prof, "emb_first", st);
-      k_emb_first<R><<<nblk(rows * L0.n_out, 256), 256, 0, st>>>(pc, nets[f], tsorted, Renv, L0.n_out, L0.skip,
-                                                                    fam[f].Y[0], fam[f].T[0]);
+      k_emb_first<R><<<nblk(rows * L0.n_out, 256), 256, 0, st>>>(pq, b.nets, tsorted, b.Renv, L0.n_out, L0.skip,
+                                                                    b.Y[0], b.T[0]);
     }
     for (int ti = 0; ti < pc.ntypes; ++ti)
       for (int tj = 0; tj < pc.ntypes; ++tj) {
         const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
-        RowMap rm{1, 0, io.type_start[ti], pc.sel[tj], pc.sel_off[tj], (int)nc,
-                  (io.type_start[ti + 1] - io.type_start[ti]) * pc.sel[tj]};
-        for (int l = 1; l < ne; ++l) {
-          const LayerDesc& L = Ls[(size_t)net * ne + l];
+        RowMap rm{1, 0, io.type_start[ti], pq.sel[tj], pq.sel_off[tj], P.nc,
+                  (io.type_start[ti + 1] - io.type_start[ti]) * pq.sel[tj]};
+        for (int l = 1; l < P.nl; ++l) {
+          const LayerDesc& L = P.emb[(size_t)net * P.nl + l];
           const R* W = params + L.w_off;
           ProfScope _ps(io.prof, "emb_fwd", st);
-          DP_CUDA_TRY(launch_dense_fwd<R>(rm, fam[f].Y[l - 1], L.n_in, W, W + (long)L.n_in * L.n_out, L.n_out, L.skip,
-                                          1, fam[f].Y[l], fam[f].T[l], st));
+          DP_CUDA_TRY(launch_dense_fwd<R>(rm, b.Y[l - 1], L.n_in, W, W + (long)L.n_in * L.n_out, L.n_out, L.skip, 1,
+                                          b.Y[l], b.T[l], st));
         }
       }
-  }
-  const R* Ga = fam[0].Y[fam[0].nl - 1];
-  const R* Gr = fam[nfam - 1].Y[fam[nfam - 1].nl - 1];
-  const int da = ang ? M * A : 0;
-  if (ang) {
-    ProfScope _ps(io.prof, "contract", st);
-    k_contract<R><<<(unsigned)N, 128, sizeof(R) * M * 4, st>>>(pc, Ga, Renv, Tm, D);
-  }
-  if (rad) {
-    ProfScope _ps(io.prof, "contract_r", st);
-    k_contract_r<R><<<(unsigned)N, 64, 0, st>>>(pc, Gr, Renv, da, D);
+    const R* G = b.Y[P.nl - 1];
+    if (P.kind == PART_A) {
+      ProfScope _ps(io.prof, "contract", st);
+      k_contract<R><<<(unsigned)N, 128, sizeof(R) * P.M * 4, st>>>(pq, G, b.Renv, b.Tm, D);
+    } else {
+      ProfScope _ps(io.prof, "contract_r", st);
+      k_contract_r<R><<<(unsigned)N, 64, 0, st>>>(pq, G, b.Renv, D);
+    }
   }
   int rc = run_fitting<R>(m, pc, params, D, io, ar, st, &gD);
   if (rc != DP_OK) return rc;
-  // ---- backward: per family, descriptor block -> dE/dG -> embedding layers -> dE/ds ----
-  for (int f = 0; f < nfam; ++f) {
-    const bool fam_ang = ang && f == 0;  // the se_e2_a block reads family 0 when present
-    const std::vector<LayerDesc>& Ls = *fam[f].layers;
-    const int ne = fam[f].nl;
-    if (fam_ang) {
-      ProfScope _ps(io.prof, "descr_bwd", st);
-      k_descr_bwd<R><<<(unsigned)N, 128, sizeof(R) * (M * 8 + M * A), st>>>(pc, Tm, gD, Ga, Renv, geA, gR);
+  // ---- backward and forces, part by part ----
+  for (int q = 0; q < nparts; ++q) {
+    const PartDesc& P = m.parts[q];
+    PartBufs<R>& b = pb[q];
+    const PathConst& pq = b.pc;
+    const long rows = N * P.nc;
+    if (P.kind == PART_E3) {
+      ProfScope _ps(io.prof, "e3_bwd", st);
+      DP_CUDA_TRY(launch_e3<R>(P, pq, params, b.Renv, gD, nullptr, b.gR, true, st));
     } else {
-      ProfScope _ps(io.prof, "descr_bwd_r", st);
-      k_descr_bwd_r<R><<<(unsigned)N, 128, sizeof(R) * pc.Mr, st>>>(pc, gD, da, Gr, Renv, geA, gR, ang ? 1 : 0);
-    }
-    R* gy = geA;
-    R* gx = geB;
-    for (int l = ne - 1; l >= 1; --l) {
-      for (int ti = 0; ti < pc.ntypes; ++ti)
-        for (int tj = 0; tj < pc.ntypes; ++tj) {
-          const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
-          RowMap rm{1, 0, io.type_start[ti], pc.sel[tj], pc.sel_off[tj], (int)nc,
-                    (io.type_start[ti + 1] - io.type_start[ti]) * pc.sel[tj]};
-          const LayerDesc& L = Ls[(size_t)net * ne + l];
-          ProfScope _ps(io.prof, "emb_bwd", st);
-          DP_CUDA_TRY(launch_dense_bwd<R>(rm, gy, fam[f].T[l], L.n_in, params + L.w_off, L.n_out, L.skip, gx, st));
-        }
-      std::swap(gy, gx);
-    }
-    const LayerDesc& L0 = Ls[0];
-    {
+      const R* G = b.Y[P.nl - 1];
+      if (P.kind == PART_A) {
+        ProfScope _ps(io.prof, "descr_bwd", st);
+        k_descr_bwd<R><<<(unsigned)N, 128, sizeof(R) * (P.M * 8 + P.M * P.A), st>>>(pq, b.Tm, gD, G, b.Renv, geA,
+                                                                                    b.gR);
+      } else {
+        ProfScope _ps(io.prof, "descr_bwd_r", st);
+        k_descr_bwd_r<R><<<(unsigned)N, 128, sizeof(R) * P.M, st>>>(pq, gD, G, b.Renv, geA, b.gR);
+      }
+      R* gy = geA;
+      R* gx = geB;
+      for (int l = P.nl - 1; l >= 1; --l) {
+        for (int ti = 0; ti < pc.ntypes; ++ti)
+          for (int tj = 0; tj < pc.ntypes; ++tj) {
+            const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
+            RowMap rm{1, 0, io.type_start[ti], pq.sel[tj], pq.sel_off[tj], P.nc,
+                      (io.type_start[ti + 1] - io.type_start[ti]) * pq.sel[tj]};
+            const LayerDesc& L = P.emb[(size_t)net * P.nl + l];
+            ProfScope _ps(io.prof, "emb_bwd", st);
+            DP_CUDA_TRY(launch_dense_bwd<R>(rm, gy, b.T[l], L.n_in, params + L.w_off, L.n_out, L.skip, gx, st));
+          }
+        std::swap(gy, gx);
+      }
+      const LayerDesc& L0 = P.emb[0];
       ProfScope _ps(io.prof, "emb_first_bwd", st);
-      k_emb_first_bwd<R><<<nblk(rows, 256), 256, 0, st>>>(pc, nets[f], tsorted, gy, fam[f].T[0], L0.n_out, L0.skip, gs,
-                                                          f > 0 ? 1 : 0);
+      k_emb_first_bwd<R><<<nblk(rows, 256), 256, 0, st>>>(pq, b.nets, tsorted, gy, b.T[0], L0.n_out, L0.skip, b.gs);
     }
-  }
-  // ---- forces and virial ----
-  {
     ProfScope _ps(io.prof, "force", st);
-    k_force<R><<<fblocks, 256, 0, st>>>(pc, io.coord, io.perm, io.nl_j, io.nl_code, gs, gR, io.force,
-                                         io.atom_virial);
+    k_force<R><<<nblk(rows, 256), 256, 0, st>>>(pq, io.coord, io.perm, io.nl_j, io.nl_code, b.gs, b.gR, io.force,
+                                                io.atom_virial);
   }
   DP_CUDA_TRY(cudaGetLastError());
   return DP_OK;

@@ -18,9 +18,36 @@ struct PathConst {
   int nframes;
   const int* atom_frame;  // device [natoms] frame of each atom, or null (one frame)
   const double* boxes;    // device [frames][9] cell rows, or null (one frame: h)
-  int Mr;                 // width of the se_e2_r block of D (0: none)
   int Dw;                 // width of D (row stride of D and dE/dD)
+  // descriptor part (Sec. II.A.1) whose slots the fields above describe: its kind, its block of
+  // D, and where its slots sit in the neighbour list (slot q of type block t reads list slot
+  // lsel_off[t] + q of a row of lnc entries); a listed pair with r^2 >= rc2 is padding for it
+  int kind;
+  int doff;
+  int lnc;
+  int lsel_off[DP_MAX_TYPES + 1];
+  double rc2;
 };
+
+// The PathConst of one part of a model, from the model-level one (list geometry).
+inline PathConst part_pc(const PathConst& pc, const PartDesc& P) {
+  PathConst q = pc;
+  q.kind = P.kind;
+  q.nc = P.nc;
+  for (int t = 0; t < pc.ntypes; ++t) q.sel[t] = P.sel[t];
+  for (int t = 0; t <= pc.ntypes; ++t) q.sel_off[t] = P.sel_off[t];
+  q.rc = P.rc;
+  q.rs = P.rs;
+  q.rc2 = P.rc * P.rc;
+  q.M = P.M;
+  q.A = P.A;
+  q.doff = P.doff;
+  return q;
+}
+
+// se_e3 parts run on the fused pair kernel (path.cu): embedding widths up to 32 and all of the
+// part's nets in shared memory.
+bool e3_supported(const PartDesc& P, int precision);
 
 // Per-kernel CUDA-event timing and launch counting.  Every kernel launch of the path sits in
 // a ProfScope; when timing is on, start/stop events are recorded on the launch stream around

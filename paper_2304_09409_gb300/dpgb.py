@@ -56,8 +56,11 @@ class Config(ctypes.Structure):
         ("fit", ctypes.c_int * 8),
         ("type_one_side", ctypes.c_int),
         ("descriptor", ctypes.c_int),
-        ("n_embed_r", ctypes.c_int),
-        ("embed_r", ctypes.c_int * 8),
+        ("rcut_2", ctypes.c_double),
+        ("rcut_smth_2", ctypes.c_double),
+        ("sel_2", ctypes.c_int * 8),
+        ("n_embed_2", ctypes.c_int),
+        ("embed_2", ctypes.c_int * 8),
     ]
 
     @classmethod
@@ -77,10 +80,15 @@ class Config(ctypes.Structure):
             c.fit[k] = int(v)
         c.type_one_side = int(getattr(cfg, "type_one_side", 0))
         c.descriptor = int(getattr(cfg, "descriptor", 0))
-        embed_r = tuple(getattr(cfg, "embed_r", ()))
-        c.n_embed_r = len(embed_r)
-        for k, v in enumerate(embed_r):
-            c.embed_r[k] = int(v)
+        if c.descriptor in (2, 4):  # hybrid: the second part (defaults: the first part's list)
+            c.rcut_2 = float(getattr(cfg, "rcut_2", 0.0) or cfg.rcut)
+            c.rcut_smth_2 = float(getattr(cfg, "rcut_smth_2", 0.0) or cfg.rcut_smth)
+            for t, v in enumerate(tuple(getattr(cfg, "sel_2", ()) or cfg.sel)):
+                c.sel_2[t] = int(v)
+            embed_2 = tuple(getattr(cfg, "embed_2", ()))
+            c.n_embed_2 = len(embed_2)
+            for k, v in enumerate(embed_2):
+                c.embed_2[k] = int(v)
         return c
 
 
@@ -183,7 +191,7 @@ class NList:
 
 
 class Model:
-    """A Deep Potential model (se_e2_a, se_e2_r or hybrid descriptor) resident on one GPU."""
+    """A Deep Potential model (se_e2_a, se_e2_r, se_e3 or hybrid descriptor) resident on one GPU."""
 
     def __init__(self, cfg, params: np.ndarray, device: int = 0, precision: str = "fp64", compressed: bool = False):
         self.cfg = cfg
@@ -194,7 +202,7 @@ class Model:
                                      1 if compressed else 0, ctypes.byref(h)))
         self.handle = h
         self.device = device
-        self.nc = int(sum(cfg.sel))
+        self.nc = int(cfg.nc)
 
     @classmethod
     def from_file(cls, path: str, cfg, device: int = 0, precision: str = "fp64", compressed: bool = False):
@@ -205,7 +213,7 @@ class Model:
         self.c = Config.from_model(cfg)
         self.handle = load_model_file(path, device, precision, compressed)
         self.device = device
-        self.nc = int(sum(cfg.sel))
+        self.nc = int(cfg.nc)
         return self
 
     def free(self):
@@ -455,7 +463,7 @@ def build_nlist_noalloc(cfg, coord, atype, box, nl_j=None, nl_shift=None, stream
     import torch
     c = Config.from_model(cfg)
     N = int(coord.shape[0])
-    nc = int(sum(cfg.sel))
+    nc = int(cfg.nc)
     if nl_j is None:
         nl_j = torch.empty((N, nc), dtype=torch.int32, device=coord.device)
     if nl_shift is None:

@@ -53,14 +53,18 @@ def test_weight_file_roundtrip_header(tmp_path):
 
 
 def test_config_checks_descriptor_fields():
-    """dp_model_n_params is host-only: it refuses unknown descriptors and a hybrid without
-    se_e2_r nets, and accepts se_e2_r without M_<."""
+    """dp_model_n_params is host-only: it refuses unknown descriptors, a hybrid without
+    second-part nets or with a bad second cutoff, and accepts se_e2_r without M_<; se_e3 nets
+    are N_t^2 whatever type_one_side says."""
     import dataclasses
     from paper_2304_09409_gb300 import dpgb
     from paper_2304_09409_gb300 import inputs as I
     hyb = I.water_model_hybrid()
     assert dpgb.n_params(hyb) == hyb.n_params()
-    assert dpgb.n_params(dataclasses.replace(hyb, embed_r=())) == -1
-    assert dpgb.n_params(dataclasses.replace(hyb, descriptor=3)) == -1
+    assert dpgb.n_params(dataclasses.replace(hyb, embed_2=())) == -1
+    assert dpgb.n_params(dataclasses.replace(hyb, descriptor=5)) == -1
+    assert dpgb.n_params(dataclasses.replace(hyb, rcut_2=0.4)) == -1  # r_s of the second part above its r_c
+    for cfg in (I.water_model_e3(), I.water_model_hybrid_e3(), dataclasses.replace(I.water_model_e3(), type_one_side=1)):
+        assert dpgb.n_params(cfg) == cfg.n_params()
     assert dpgb.n_params(dataclasses.replace(I.water_model_r(), axis=0)) == I.water_model_r().n_params()
     assert dpgb.n_params(dataclasses.replace(I.water_model(), axis=0)) == -1
