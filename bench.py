@@ -194,7 +194,7 @@ def _kernel_rooflines(cfg, big, real_nb, prof, work, steps, peaks, fit_npass):
     Peaks: HBM and BF16 tensor as measured (the sustained tensor figure: these kernels run inside a
     long step); FP32 ALU 152 SM x 128 lanes x 2 x 2070 MHz for the side figures."""
     N = big.natoms
-    nc = int(sum(cfg.sel))
+    nc = int(cfg.nc)
     M, A = cfg.m, cfg.axis
     fit = [M * A] + list(cfg.fit)
     fwd = sum(2 * N * fit[k] * fit[k + 1] for k in range(len(fit) - 2))
@@ -347,6 +347,70 @@ def run_fcc(local, flush, steps=5, warmup=3):
                     "force_err_vs_fp64_gpu": ok[best]["force_err_vs_fp64_gpu"],
                     "speedup_vs_fp64_gpu": ms64 / ok[best]["ms_per_step"]})
     return res
+
+
+def _e3_flops_per_pair(widths, M):
+    """Algorithmic FP32 FLOPs of one (j, k) pair of an se_e3 part: theta = R_j . R_k (7); the net's
+    value (2 n_in n_out + 1 skip add per output and layer; tanh counted apart); forward adds
+    theta G to D (2 M); backward also carries dG/dtheta (2 n_in n_out + 3 per output and layer),
+    forms dE/dtheta (3 M) and adds it into both rows (16)."""
+    dims = [1] + list(widths)
+    mm = sum(dims[k] * dims[k + 1] for k in range(len(widths)))
+    outs = sum(widths)
+    fwd = 7 + 2 * mm + outs + 2 * M
+    bwd = 7 + 2 * mm + outs + 2 * mm + 3 * outs + 3 * M + 16
+    return fwd, bwd
+
+
+def run_descriptors(local, flush, steps=5, warmup=3):
+    """The other descriptors of Sec. II.A.1 on the same 12,288-atom water frame, FP32 CUDA-core path
+    (the path these models run on), forces compared with the FP64 GPU path: se_e2_r; hybrid
+    se_e2_a (r_c 4) + se_e2_r (r_c 6); se_e3; hybrid se_e2_a (r_c 4) + se_e3 (r_c 6), each with its
+    output layer scaled to forces of ~1 eV/A RMS.  se_e3 parts also report their pair kernels
+    against the FP32 ALU peak (pairs = sum over atoms of real neighbours squared)."""
+    import torch
+    from paper_2304_09409_gb300 import dpgb, inputs as I
+    _, _, _, big = _workload()
+    coord = torch.tensor(big.coord, device="cuda")
+    atype = torch.tensor(big.atype, device="cuda")
+    legs = {"se_e2_r": (I.water_model_r(), I.water_r_params_scaled(0)),
+            "hybrid_se_e2_a+se_e2_r": (I.water_model_hybrid(), I.water_hybrid_params_scaled(0)),
+            "se_e3": (I.water_model_e3(), I.water_e3_params_scaled(0)),
+            "hybrid_se_e2_a+se_e3": (I.water_model_hybrid_e3(), I.water_hybrid_e3_params_scaled(0))}
+    out = {"workload": "water 12,288 atoms (192-atom frame tiled 4x4x4), models of inputs.water_model_r / "
+                       "_hybrid / _e3 / _hybrid_e3, FP32 networks, L2 flushed between steps"}
+    for name, (cfg, params) in legs.items():
+        m64 = dpgb.Model(cfg, params, device=local, precision="fp64")
+        ms64, _, _, o64 = time_path(m64, coord, atype, big.box, steps=1, warmup=1, flush=flush)
+        f64 = o64[1].cpu().numpy()
+        nl = m64.build_nlist(big.coord, big.atype, big.box)
+        nj, _ = nl.export()
+        m64.free()
+        m = dpgb.Model(cfg, params, device=local, precision="fp32")
+        ms, launches, _, o = time_path(m, coord, atype, big.box, steps=steps, warmup=warmup, flush=flush)
+        _, _, prof, _ = time_path(m, coord, atype, big.box, steps=steps, warmup=2, flush=flush, profile=True)
+        m.free()
+        err = float(np.abs(o[1].cpu().numpy() - f64).max())
+        leg = {"ms_per_step": ms, "atom_evals_per_s": big.natoms / (ms * 1e-3), "fp64_ms_per_step": ms64,
+               "force_err_vs_fp64_gpu": err, "force_rms": float(np.sqrt((f64 ** 2).mean())),
+               "meets_bar": err <= FORCE_BAR, "gpu_launches": launches, "descriptor_dim": cfg.descriptor_dim,
+               "kernels_ms_per_step": {k: v[0] / steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+        if cfg.descriptor in (3, 4):
+            # the se_e3 part reads the whole list here (its r_c and sel are the list's)
+            widths = cfg.embed if cfg.descriptor == 3 else cfg.embed_2
+            n_i = (nj >= 0).sum(axis=1).astype(np.float64)
+            pairs = float((n_i ** 2).sum())
+            fpp, bpp = _e3_flops_per_pair(widths, widths[-1])
+            leg["e3_pairs_per_step"] = pairs
+            for scope, per in (("e3_fwd", fpp), ("e3_bwd", bpp)):
+                if scope in prof:
+                    t = prof[scope][0] / steps * 1e-3
+                    ach = pairs * per / t / 1e12
+                    leg[scope] = {"bound": "alu", "achieved": ach, "peak": ALU_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": ach / ALU_FP32_PEAK_TFLOPS, "us_per_step": t * 1e6,
+                                  "flops_per_pair": per, "pairs_per_s": pairs / t}
+        out[name] = leg
+    return out
 
 
 def time_path(model, coord, atype, box, steps, warmup, flush, profile=False):
@@ -619,6 +683,11 @@ def run_ours(args):
             line["fcc32000"] = run_fcc(local, flush)
         except Exception as exc:
             line["fcc32000"] = {"error": repr(exc)}
+    if not args.no_descriptors and rank == 0 and world == 1:
+        try:
+            line["descriptors"] = run_descriptors(local, flush)
+        except Exception as exc:
+            line["descriptors"] = {"error": repr(exc)}
     if not args.no_training:
         try:
             line["training"] = run_training()
@@ -651,6 +720,8 @@ def main():
                     help="skip the continuous-batching serving measurement")
     ap.add_argument("--no-training", dest="no_training", action="store_true",
                     help="skip the parameter-gradient (training step) measurement")
+    ap.add_argument("--no-descriptors", dest="no_descriptors", action="store_true",
+                    help="skip the se_e2_r / se_e3 / hybrid legs")
     ap.add_argument("--no-fcc", dest="no_fcc", action="store_true",
                     help="skip the 32,000-atom FCC metal configuration (precision sweep)")
     args = ap.parse_args()
