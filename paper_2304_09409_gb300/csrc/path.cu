@@ -232,88 +232,222 @@ struct E3Net {
   int per_net;              // parameters per net
 };
 
+// Any net of widths <= W: the parameters in shared memory in their own layout, every layer a
+// W x W loop with the shapes as run-time bounds.
 template <class R, int W>
-__device__ __forceinline__ void e3_eval(const E3Net& nt, const R* __restrict__ w, R th, R* g, R* dg) {
-  R x[W], dx[W];
-#pragma unroll
-  for (int o = 0; o < W; ++o) {
-    x[o] = R(0);
-    dx[o] = R(0);
+struct E3Any {
+  static constexpr int kM = W;
+  E3Net nt;
+  __device__ int per_net() const { return nt.per_net; }
+  __device__ void fill(R* wsm, const R* __restrict__ params, int n_nets, int tid, int nth) const {
+    for (long e = tid; e < (long)n_nets * nt.per_net; e += nth) wsm[e] = params[e];
   }
-  x[0] = th;
-  dx[0] = R(1);
-  for (int l = 0; l < nt.nl; ++l) {
-    const int ni = nt.in[l], no = nt.out[l], sk = nt.skip[l];
-    const R* Wl = w + nt.loff[l];
-    const R* bl = Wl + ni * no;
-    R y[W], dy[W];
+  template <bool DERIV>
+  __device__ __forceinline__ void eval(const R* __restrict__ w, R th, R* g, R* dg) const {
+    R x[W], dx[W];
 #pragma unroll
     for (int o = 0; o < W; ++o) {
-      if (o < no) {
-        R z = bl[o], dz = R(0);
+      x[o] = R(0);
+      dx[o] = R(0);
+    }
+    x[0] = th;
+    dx[0] = R(1);
+    for (int l = 0; l < nt.nl; ++l) {
+      const int ni = nt.in[l], no = nt.out[l], sk = nt.skip[l];
+      const R* Wl = w + nt.loff[l];
+      const R* bl = Wl + ni * no;
+      R y[W], dy[W];
 #pragma unroll
-        for (int i = 0; i < W; ++i)
-          if (i < ni) {
-            const R wv = Wl[i * no + o];
-            z += x[i] * wv;
-            dz += dx[i] * wv;
-          }
-        const R t = tanh_r(z);
-        R yo = t, dyo = (R(1) - t * t) * dz;
-        if (sk == 1) {
-          yo += x[o];
-          dyo += dx[o];
-        } else if (sk == 2) {
-          const int q = o < ni ? o : o - ni;  // {x, x}: n_out = 2 n_in
-          R xq = R(0), dxq = R(0);
+      for (int o = 0; o < W; ++o) {
+        if (o < no) {
+          R z = bl[o], dz = R(0);
 #pragma unroll
-          for (int i = 0; i < W; ++i)  // a select chain keeps x in registers
-            if (i == q) {
-              xq = x[i];
-              dxq = dx[i];
+          for (int i = 0; i < W; ++i)
+            if (i < ni) {
+              const R wv = Wl[i * no + o];
+              z += x[i] * wv;
+              if (DERIV) dz += dx[i] * wv;
             }
-          yo += xq;
-          dyo += dxq;
+          const R t = tanh_r(z);
+          R yo = t, dyo = DERIV ? (R(1) - t * t) * dz : R(0);
+          if (sk == 1) {
+            yo += x[o];
+            if (DERIV) dyo += dx[o];
+          } else if (sk == 2) {
+            const int q = o < ni ? o : o - ni;  // {x, x}: n_out = 2 n_in
+            R xq = R(0), dxq = R(0);
+#pragma unroll
+            for (int i = 0; i < W; ++i)  // a select chain keeps x in registers
+              if (i == q) {
+                xq = x[i];
+                dxq = dx[i];
+              }
+            yo += xq;
+            if (DERIV) dyo += dxq;
+          }
+          y[o] = yo;
+          dy[o] = dyo;
+        } else {
+          y[o] = R(0);
+          dy[o] = R(0);
         }
-        y[o] = yo;
-        dy[o] = dyo;
-      } else {
-        y[o] = R(0);
-        dy[o] = R(0);
+      }
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        x[o] = y[o];
+        dx[o] = dy[o];
       }
     }
 #pragma unroll
     for (int o = 0; o < W; ++o) {
-      x[o] = y[o];
-      dx[o] = dy[o];
+      g[o] = x[o];
+      dg[o] = dx[o];
     }
   }
-#pragma unroll
-  for (int o = 0; o < W; ++o) {
-    g[o] = x[o];
-    dg[o] = dx[o];
+};
+
+// Three layers of widths A, B, C known at compile time (the paper's se_e3 nets are 2/4/8): every
+// loop unrolled without bounds, skip kinds fixed, and each net's rows padded to multiples of four
+// values in shared memory so that a row loads as 16-byte vectors.
+template <class R, int A, int B, int C>
+struct E3Fixed {
+  static constexpr int kM = C;
+  static constexpr int PA = (A + 3) / 4 * 4, PB = (B + 3) / 4 * 4, PC = (C + 3) / 4 * 4;
+  // padded layout of one net: w0 [PA], b0 [PA], W1 [A][PB], b1 [PB], W2 [B][PC], b2 [PC]
+  static constexpr int OW0 = 0, OB0 = PA, OW1 = 2 * PA, OB1 = OW1 + A * PB, OW2 = OB1 + PB, OB2 = OW2 + B * PC;
+  static constexpr int PN = OB2 + PC;
+  static constexpr int SK0 = (A == 1) ? 1 : (A == 2 ? 2 : 0);
+  static constexpr int SK1 = (B == A) ? 1 : (B == 2 * A ? 2 : 0);
+  static constexpr int SK2 = (C == B) ? 1 : (C == 2 * B ? 2 : 0);
+  int per_net_global;  // parameters of one net in the global layout
+  __device__ int per_net() const { return PN; }
+  __device__ void fill(R* wsm, const R* __restrict__ params, int n_nets, int tid, int nth) const {
+    for (int e = tid; e < n_nets * PN; e += nth) {
+      const int n = e / PN, q = e % PN;
+      const R* src = params + (long)n * per_net_global;  // global: W0 [1][A] b0 [A] W1 [A][B] b1 [B] W2 [B][C] b2 [C]
+      R v = R(0);
+      if (q < OB0) {
+        if (q < A) v = src[q];
+      } else if (q < OW1) {
+        if (q - OB0 < A) v = src[A + (q - OB0)];
+      } else if (q < OB1) {
+        const int i = (q - OW1) / PB, o = (q - OW1) % PB;
+        if (o < B) v = src[2 * A + i * B + o];
+      } else if (q < OW2) {
+        if (q - OB1 < B) v = src[2 * A + A * B + (q - OB1)];
+      } else if (q < OB2) {
+        const int i = (q - OW2) / PC, o = (q - OW2) % PC;
+        if (o < C) v = src[2 * A + A * B + B + i * C + o];
+      } else {
+        if (q - OB2 < C) v = src[2 * A + A * B + B + B * C + (q - OB2)];
+      }
+      wsm[e] = v;
+    }
   }
-}
+  template <int P>
+  static __device__ __forceinline__ void ldrow(const R* __restrict__ p, R* v) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int c = 0; c < P / 4; ++c) {
+        const float4 f = reinterpret_cast<const float4*>(p)[c];
+        v[4 * c] = f.x;
+        v[4 * c + 1] = f.y;
+        v[4 * c + 2] = f.z;
+        v[4 * c + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < P / 2; ++c) {
+        const double2 f = reinterpret_cast<const double2*>(p)[c];
+        v[2 * c] = f.x;
+        v[2 * c + 1] = f.y;
+      }
+    }
+  }
+  template <bool DERIV>
+  __device__ __forceinline__ void eval(const R* __restrict__ w, R th, R* g, R* dg) const {
+    R x0[A], d0[A], x1[B], d1[B];
+    {
+      R wv[PA], bv[PA];
+      ldrow<PA>(w + OW0, wv);
+      ldrow<PA>(w + OB0, bv);
+#pragma unroll
+      for (int o = 0; o < A; ++o) {
+        const R t = tanh_r(th * wv[o] + bv[o]);
+        x0[o] = t + (SK0 ? th : R(0));
+        if (DERIV) d0[o] = (R(1) - t * t) * wv[o] + (SK0 ? R(1) : R(0));
+      }
+    }
+    {
+      R z[PB], dz[PB];
+      ldrow<PB>(w + OB1, z);
+#pragma unroll
+      for (int o = 0; o < B; ++o) dz[o] = R(0);
+#pragma unroll
+      for (int i = 0; i < A; ++i) {
+        R wr[PB];
+        ldrow<PB>(w + OW1 + i * PB, wr);
+#pragma unroll
+        for (int o = 0; o < B; ++o) {
+          z[o] += x0[i] * wr[o];
+          if (DERIV) dz[o] += d0[i] * wr[o];
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < B; ++o) {
+        const R t = tanh_r(z[o]);
+        const int q = SK1 == 2 ? o % A : o;
+        x1[o] = t + (SK1 ? x0[q] : R(0));
+        if (DERIV) d1[o] = (R(1) - t * t) * dz[o] + (SK1 ? d0[q] : R(0));
+      }
+    }
+    {
+      R z[PC], dz[PC];
+      ldrow<PC>(w + OB2, z);
+#pragma unroll
+      for (int o = 0; o < C; ++o) dz[o] = R(0);
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        R wr[PC];
+        ldrow<PC>(w + OW2 + i * PC, wr);
+#pragma unroll
+        for (int o = 0; o < C; ++o) {
+          z[o] += x1[i] * wr[o];
+          if (DERIV) dz[o] += d1[i] * wr[o];
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < C; ++o) {
+        const R t = tanh_r(z[o]);
+        const int q = SK2 == 2 ? o % B : o;
+        g[o] = t + (SK2 ? x1[q] : R(0));
+        if (DERIV) dg[o] = (R(1) - t * t) * dz[o] + (SK2 ? d1[q] : R(0));
+      }
+    }
+  }
+};
 
 // BWD = 0: D block; BWD = 1: dE/dR rows (gR, [rows][4], every row of the atom written).
-template <class R, int W, int BWD>
+template <class R, class Ev, int BWD>
 __global__ void __launch_bounds__(128)
-    k_e3(PathConst pc, E3Net nt, const R* __restrict__ params, int n_nets, const R* __restrict__ Renv,
+    k_e3(PathConst pc, Ev ev, const R* __restrict__ params, int n_nets, const R* __restrict__ Renv,
          const R* __restrict__ gD, R* __restrict__ D, R* __restrict__ gR) {
+  constexpr int W = Ev::kM;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   typedef typename Vec4<R>::T V4;
   const int nc = pc.nc, M = pc.M, nt_types = pc.ntypes;
+  const int pn = ev.per_net();
   V4* Rv = reinterpret_cast<V4*>(sm_raw);     // [nc] rows of the real neighbours, compacted
   V4* gRv = Rv + nc;                          // [nc] dE/dR of those rows (backward)
   R* wsm = reinterpret_cast<R*>(gRv + nc);    // [n_nets * per_net]
-  R* red = wsm + (long)n_nets * nt.per_net;   // [W] D sums / gD
+  R* red = wsm + (long)n_nets * pn;           // [W] D sums / gD
   int* tv = reinterpret_cast<int*>(red + W);  // [nc] neighbour type of each compacted row
   int* kv = tv + nc;                          // [nc] slot of each compacted row
   __shared__ int nv_s;
   const int p = blockIdx.x;
   const long rb = (long)p * nc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (long e = tid; e < (long)n_nets * nt.per_net; e += blockDim.x) wsm[e] = params[e];
+  ev.fill(wsm, params, n_nets, tid, blockDim.x);
   if (tid < W) red[tid] = (BWD && tid < M) ? gD[(long)p * pc.Dw + pc.doff + tid] : R(0);
   if (warp == 0) {  // compaction of the rows with s > 0, in slot order
     int nv = 0;
@@ -348,7 +482,7 @@ __global__ void __launch_bounds__(128)
       const V4 rk = Rv[k];
       const R th = ((rj.x * rk.x + rj.y * rk.y) + rj.z * rk.z) + rj.w * rk.w;
       R g[W], dg[W];
-      e3_eval<R, W>(nt, wsm + (long)(tj * nt_types + tv[k]) * nt.per_net, th, g, dg);
+      ev.template eval<BWD != 0>(wsm + (long)(tj * nt_types + tv[k]) * pn, th, g, dg);
       if (!BWD) {
 #pragma unroll
         for (int m = 0; m < W; ++m) acc[m] += th * g[m];
@@ -586,44 +720,57 @@ bool e3_supported(const PartDesc& P, int precision) {
   return w <= 32 && bytes <= 96 * 1024 && P.nc <= 4096;
 }
 
-template <class R, int W>
-cudaError_t launch_e3_w(const PathConst& pc, const E3Net& nt, const R* w, int n_nets, const R* Renv, const R* gD,
-                        R* D, R* gR, bool bwd, cudaStream_t st) {
-  const size_t smem = sizeof(typename Vec4<R>::T) * 2 * pc.nc + sizeof(R) * ((size_t)n_nets * nt.per_net + W) +
-                      sizeof(int) * 2 * pc.nc;
-  auto kf = k_e3<R, W, 0>;
-  auto kb = k_e3<R, W, 1>;
+template <class R, class Ev>
+cudaError_t launch_e3_ev(const PathConst& pc, const Ev& ev, int per_net_smem, const R* w, int n_nets, const R* Renv,
+                         const R* gD, R* D, R* gR, bool bwd, cudaStream_t st) {
+  const size_t smem = sizeof(typename Vec4<R>::T) * 2 * pc.nc +
+                      sizeof(R) * ((size_t)n_nets * per_net_smem + Ev::kM) + sizeof(int) * 2 * pc.nc;
+  auto kf = k_e3<R, Ev, 0>;
+  auto kb = k_e3<R, Ev, 1>;
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_smem(bwd ? kb : kf);
     if (e != cudaSuccess) return e;
   }
   if (bwd)
-    kb<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, nt, w, n_nets, Renv, gD, D, gR);
+    kb<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR);
   else
-    kf<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, nt, w, n_nets, Renv, gD, D, gR);
+    kf<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR);
   return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_e3(const PartDesc& P, const PathConst& pc, const R* params, const R* Renv, const R* gD, R* D,
                       R* gR, bool bwd, cudaStream_t st) {
+  const R* wp = params + P.w_off;
+  int w = 1;
+  for (int l = 0; l < P.nl; ++l) w = std::max(w, P.emb[l].n_out);
+  if (P.nl == 3) {  // the paper's shapes, unrolled
+    const int a = P.emb[0].n_out, b = P.emb[1].n_out, c = P.emb[2].n_out;
+#define DP_E3_FIXED(A_, B_, C_)                                                                           \
+    if (a == A_ && b == B_ && c == C_) {                                                                   \
+      E3Fixed<R, A_, B_, C_> ev;                                                                           \
+      ev.per_net_global = (int)P.per_net;                                                                  \
+      return launch_e3_ev<R>(pc, ev, E3Fixed<R, A_, B_, C_>::PN, wp, P.n_nets, Renv, gD, D, gR, bwd, st); \
+    }
+    DP_E3_FIXED(2, 4, 8)
+    DP_E3_FIXED(4, 8, 16)
+    DP_E3_FIXED(8, 16, 32)
+#undef DP_E3_FIXED
+  }
   E3Net nt;
   std::memset(&nt, 0, sizeof(nt));
   nt.nl = P.nl;
-  int w = 1;
   for (int l = 0; l < P.nl; ++l) {
     const LayerDesc& L = P.emb[l];
     nt.in[l] = L.n_in;
     nt.out[l] = L.n_out;
     nt.skip[l] = L.skip;
     nt.loff[l] = (int)(L.w_off - P.w_off);
-    w = std::max(w, L.n_out);
   }
   nt.per_net = (int)P.per_net;
-  const R* wp = params + P.w_off;
-  if (w <= 8) return launch_e3_w<R, 8>(pc, nt, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
-  if (w <= 16) return launch_e3_w<R, 16>(pc, nt, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
-  return launch_e3_w<R, 32>(pc, nt, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
+  if (w <= 8) return launch_e3_ev<R>(pc, E3Any<R, 8>{nt}, nt.per_net, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
+  if (w <= 16) return launch_e3_ev<R>(pc, E3Any<R, 16>{nt}, nt.per_net, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
+  return launch_e3_ev<R>(pc, E3Any<R, 32>{nt}, nt.per_net, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
 }
 
 // The whole path on CUDA cores for any descriptor: each part (Sec. II.A.1) builds its own
