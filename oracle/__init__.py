@@ -197,9 +197,22 @@ def embed_jets(cfg, params, net: int, xs):
     return y, y1, y2
 
 
+def table_layout(cfg):
+    """Node grid (x0, stride1, n1, stride2, n2) of the first part's tables: s in [0, 1/r_s] with stride
+    0.01 on the first 90 % and 0.1 on the rest; for se_e3 the pieces are in theta = R_j . R_k, which
+    lies in [0, 2 s_max^2] (|R_j|^2 = 2 s_j^2 and 1 + cos >= 0), the same grid scaled by 2 / r_s."""
+    smax = 1.0 / cfg.rcut_smth
+    n1 = int(np.floor(0.9 * smax / 0.01 + 0.5))
+    rest = smax - n1 * 0.01
+    n2 = max(1, int(np.ceil(rest / 0.1 - 1e-9))) if rest > 0 else 1
+    scale = 2.0 / cfg.rcut_smth if getattr(cfg, "descriptor", 0) == 3 else 1.0
+    return (0.0, 0.01 * scale, n1, 0.1 * scale, n2)
+
+
 def table_build(cfg, params, s0=TABLE_S0, stride1=TABLE_STRIDE1, n1=TABLE_N1, stride2=TABLE_STRIDE2, n2=TABLE_N2):
     """Eq. (compress) tables for every embedding net: [nets, n1+n2, M, 6] (a..f)."""
-    nets = cfg.ntypes if getattr(cfg, "type_one_side", 0) else cfg.ntypes ** 2
+    nets = int(cfg.n_embed_nets) if hasattr(cfg, "n_embed_nets") else (
+        cfg.ntypes if getattr(cfg, "type_one_side", 0) else cfg.ntypes ** 2)
     M = int(cfg.embed[-1])
     tab = np.zeros((nets, n1 + n2, M, 6))
     c = _cfg(cfg)

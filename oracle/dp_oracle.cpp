@@ -577,15 +577,18 @@ void part_forward(const OrcConfig& c, const Layout& L, const Part& P, const doub
   const int nc = P.nc, M = P.nets.m;
   if (P.kind == PART_E3) {
     // D_m = (1/Nc^2) sum_{j,k} theta_jk G_jkm, theta_jk = R_j . R_k, G_jk = N^{a_j,a_k}(theta_jk)
+    // (by the nets, or by the quintic pieces in theta when a table is given)
     std::vector<double> acc(M, 0.0);
-    std::vector<std::vector<double>> act, outs;
+    EmbedRow row;
     for (int j = 0; j < nc; ++j) {
       if (!E.valid[j]) continue;
       for (int k = 0; k < nc; ++k) {
         if (!E.valid[k]) continue;
         const double th = dot4(&E.R[(size_t)j * 4], &E.R[(size_t)k * 4]);
-        embed_forward(P.nets, params, E.tk[j] * L.ntypes + E.tk[k], th, act, outs);
-        for (int m = 0; m < M; ++m) acc[m] += th * outs[P.nets.nl - 1][m];
+        int oor = 0;
+        embed_row(P.nets, params, tab, E.tk[j] * L.ntypes + E.tk[k], th, row, &oor);
+        if (oor) *range_err = 1;
+        for (int m = 0; m < M; ++m) acc[m] += th * row.G[m];
       }
     }
     for (int m = 0; m < M; ++m) D[P.doff + m] = acc[m] / ((double)nc * nc);
@@ -639,7 +642,7 @@ void part_backward(const Layout& L, const Part& P, const double* params, const T
     // dE/dtheta_jk = (1/Nc^2) [ sum_m gD_m G_jkm + dE/dtheta through the net with dE/dG_jkm = gD_m theta ];
     // dtheta_jk/dR_j = R_k, dtheta_jk/dR_k = R_j
     const double inv = 1.0 / ((double)nc * nc);
-    std::vector<std::vector<double>> act, outs;
+    EmbedRow row;
     std::vector<double> gG(M);
     for (int j = 0; j < nc; ++j) {
       if (!E.valid[j]) continue;
@@ -649,13 +652,14 @@ void part_backward(const Layout& L, const Part& P, const double* params, const T
         const double* Rk = &E.R[(size_t)k * 4];
         const double th = dot4(Rj, Rk);
         const int net = E.tk[j] * L.ntypes + E.tk[k];
-        embed_forward(P.nets, params, net, th, act, outs);
+        int oor = 0;
+        embed_row(P.nets, params, tab, net, th, row, &oor);
         double direct = 0.0;
         for (int m = 0; m < M; ++m) {
-          direct += gD[P.doff + m] * outs[P.nets.nl - 1][m];
+          direct += gD[P.doff + m] * row.G[m];
           gG[m] = gD[P.doff + m] * th * inv;
         }
-        const double gth = direct * inv + embed_backward(P.nets, params, net, act, gG);
+        const double gth = direct * inv + embed_row_backward(P.nets, params, tab, net, row, gG);
         for (int q = 0; q < 4; ++q) {
           gR[(size_t)j * 4 + q] += gth * Rk[q];
           gR[(size_t)k * 4 + q] += gth * Rj[q];
@@ -721,7 +725,8 @@ void part_backward(const Layout& L, const Part& P, const double* params, const T
 }
 
 // One atom: descriptor (all parts), fitting net, and the reverse pass down to dE/dr_ij per list
-// slot (gd [L.nc * 3]).  The table, when given, replaces the nets of the first part (two-body).
+// slot (gd [L.nc * 3]).  The table, when given, replaces the nets of the first part: pieces in s for
+// a two-body part, in theta for se_e3.
 void atom_pass(const OrcConfig& c, const Layout& L, const double* params, const Table* tab, int i, const double* coord,
                const int* type, const double* box, const int* nl_j, const int* nl_code, double* gd, AtomOut* out) {
   const int ai = type[i];
@@ -987,7 +992,6 @@ int orc_compute(const OrcConfig* cfg, const double* params, int N, const double*
   }
   Table tb{table, s0, stride1, stride2, n1, n2};
   const Table* tp = table ? &tb : nullptr;
-  if (table && L.parts[0].kind == PART_E3) return -2;  // tables replace two-body nets only
   std::vector<double> gd((size_t)N * nc * 3, 0.0);
   std::vector<AtomOut> ao(N);
 #ifdef _OPENMP

@@ -284,3 +284,68 @@ def test_energy_continuous_across_cutoff(kind):
     jumps = [abs(e(rc - d) - e(rc + d)) for d in (4e-2, 2e-2, 1e-2)]
     assert jumps[0] > 0
     assert jumps[0] / jumps[1] > 7.0 and jumps[1] / jumps[2] > 7.0
+
+
+# ----------------------------------------------------------------------------------------
+# Compressed se_e2_r and se_e3 (Eq. (compress); for se_e3 the pieces are in theta)
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("kind", ["r", "e3"])
+def test_table_layout_and_nodes(kind):
+    """The e3 grid covers theta in [0, 2 / r_s^2] (R_j . R_k <= |R_j| |R_k| = 2 s_j s_k); at every
+    node each piece reproduces the net's value, slope and curvature, and its right end the next value."""
+    cfg = I.water_model_r() if kind == "r" else I.water_model_e3()
+    p = I.make_params(cfg, 0)
+    lay = oracle.table_layout(cfg)
+    x0, h1, n1, h2, n2 = lay
+    top = x0 + n1 * h1 + n2 * h2
+    assert top == pytest.approx(1 / cfg.rcut_smth if kind == "r" else 2 / cfg.rcut_smth ** 2, rel=1e-12)
+    tab = oracle.table_build(cfg, p, *lay)
+    nodes = np.concatenate([x0 + np.arange(n1 + 1) * h1, x0 + n1 * h1 + np.arange(1, n2 + 1) * h2])
+    for net in range(cfg.n_embed_nets):
+        y, y1, y2 = oracle.embed_jets(cfg, p, net, nodes)
+        c = tab[net]
+        np.testing.assert_allclose(c[:, :, 5], y[:-1], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(c[:, :, 4], y1[:-1], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(2 * c[:, :, 3], y2[:-1], rtol=0, atol=1e-11)
+        dx = np.diff(nodes)[:, None]
+        right = ((((c[..., 0] * dx + c[..., 1]) * dx + c[..., 2]) * dx + c[..., 3]) * dx + c[..., 4]) * dx + c[..., 5]
+        np.testing.assert_allclose(right, y[1:], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["r", "e3"])
+def test_compressed_close_to_network(kind):
+    cfg = I.water_model_r() if kind == "r" else I.water_model_e3()
+    p = I.make_params(cfg, 0)
+    fr = I.water_frame(0)
+    lay = oracle.table_layout(cfg)
+    tab = oracle.table_build(cfg, p, *lay)
+    a = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
+    b = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, table=tab, table_layout=lay)
+    assert b.status == 0
+    assert abs(a.energy - b.energy) / fr.natoms < 1e-8
+    assert np.abs(a.force - b.force).max() < 1e-7
+    np.testing.assert_allclose(b.virial, a.virial, atol=1e-7)
+
+
+@pytest.mark.parametrize("kind", ["r", "e3"])
+def test_compressed_forces_vs_differences_of_compressed_energy(kind):
+    """The compressed reverse pass uses each piece's analytic slope (in s, or in theta for se_e3)."""
+    cfg = tiny_model_r() if kind == "r" else tiny_model_e3()
+    fr = tiny_frame(seed=3)
+    p = I.make_params(cfg, 1)
+    nl = oracle.nlist(cfg, fr.coord, fr.atype, fr.box)[:2]
+    lay = oracle.table_layout(cfg)
+    tab = oracle.table_build(cfg, p, *lay)
+    r = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, nl=nl, table=tab, table_layout=lay)
+    assert r.status == 0
+    h = 1e-5
+    for i, a in ((0, 0), (3, 1), (7, 2), (11, 0)):
+        cp = fr.coord.copy()
+        cm = fr.coord.copy()
+        cp[i, a] += h
+        cm[i, a] -= h
+        ep = oracle.compute(cfg, p, cp, fr.atype, fr.box, nl=nl, table=tab, table_layout=lay).energy
+        em = oracle.compute(cfg, p, cm, fr.atype, fr.box, nl=nl, table=tab, table_layout=lay).energy
+        assert r.force[i, a] == pytest.approx(-(ep - em) / (2 * h), abs=2e-7)
