@@ -359,8 +359,9 @@ int dp_model_create(const dp_model_config* cfg, const double* params, long n_par
   m.M = m.parts[0].M;
   m.A = m.parts[0].A;
   m.n_embed_nets = m.parts[0].n_nets;
-  if (cfg->descriptor != DP_DESC_SE_E2_A && (compressed || precision > DP_PREC_FP32)) {
-    set_error("se_e2_r, se_e3 and hybrid models run uncompressed in FP64 or FP32");
+  const bool one_part = cfg->descriptor == DP_DESC_SE_E2_R || cfg->descriptor == DP_DESC_SE_E3;
+  if (cfg->descriptor != DP_DESC_SE_E2_A && (precision > DP_PREC_FP32 || (compressed && !one_part))) {
+    set_error("se_e2_r and se_e3 models run in FP64 or FP32, compressed or not; hybrids uncompressed");
     delete md;
     return DP_E_UNSUPPORTED;
   }

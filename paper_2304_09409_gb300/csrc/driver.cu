@@ -299,7 +299,7 @@ PathConst make_pc(const DeviceModel& m, int N) {
 }
 
 int run_path(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& ar, cudaStream_t st) {
-  if (m.compressed) return run_compressed(m, pc, io, ar, st);
+  if (m.compressed && m.cfg.descriptor == DP_DESC_SE_E2_A) return run_compressed(m, pc, io, ar, st);
   if (m.precision == DP_PREC_TF32 || m.precision == DP_PREC_BF16) return run_tc_uncompressed(m, pc, io, ar, st);
   if (m.precision == DP_PREC_FP64) return run_generic<double>(m, pc, m.p64, io, ar, st);
   return run_generic<float>(m, pc, m.p32, io, ar, st);

@@ -16,9 +16,12 @@
 // The pair displacement is always rebuilt from the neighbour list with the exact FP64
 // formula.  In FP32 mode the switch and its derivative are evaluated in FP32 in a form without
 // cancellation near r_c (env.cuh); energy, force and virial accumulate in FP64.
+#include <type_traits>
+
 #include "dp_internal.cuh"
 #include "path.cuh"
 #include "env.cuh"
+#include "tabeval.cuh"
 
 namespace dpgb {
 
@@ -217,6 +220,64 @@ __global__ void k_descr_bwd_r(PathConst pc, const R* __restrict__ gD, const R* _
   }
 }
 
+// ---- compressed se_e2_r part (Eq. (compress)): G_k from the pieces in s, folded into D_r on the
+// fly (operator merging: G never reaches memory); one block per atom, a thread per output m.
+template <class R>
+__global__ void k_rtab_fwd(PathConst pc, const R* __restrict__ tab, TabConst tc, const int* __restrict__ tsorted,
+                           const R* __restrict__ Renv, R* __restrict__ D, int* __restrict__ range_flag) {
+  const int p = blockIdx.x;
+  const int M = pc.M, nc = pc.nc, ti = tsorted[p];
+  const long rb = (long)p * nc;
+  bool oor = false;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    R acc = 0;
+    for (int k = 0; k < nc; ++k) {
+      const R s = Renv[(rb + k) * 4];
+      if (s == R(0)) continue;  // padding (or beyond this part's cutoff)
+      R tt;
+      const int l = tab_interval<R>(tc, s, tt, oor);
+      const int net = net_of(pc, ti, slot_block(pc, k));
+      const Quint<R> q = load_quint(tab + ((((long)net * tc.lc + l) * M) + m) * kCoefStride);
+      acc += quint_value(q, tt) * s;
+    }
+    D[(long)p * pc.Dw + pc.doff + m] = acc / R(nc);
+  }
+  if (oor && range_flag) atomicOr(range_flag, 1);
+}
+
+// Its reverse: dE/ds_k = (1/Nc) sum_m gD_m (G_m'(s_k) s_k + G_m(s_k)) into the radial component of
+// gR (the other three zero); one block per atom, a warp per row, lanes over m.
+template <class R>
+__global__ void k_rtab_bwd(PathConst pc, const R* __restrict__ tab, TabConst tc, const int* __restrict__ tsorted,
+                           const R* __restrict__ Renv, const R* __restrict__ gD, R* __restrict__ gR) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  R* gDs = reinterpret_cast<R*>(sm_raw);  // [M]
+  const int p = blockIdx.x;
+  const int M = pc.M, nc = pc.nc, ti = tsorted[p];
+  for (int e = threadIdx.x; e < M; e += blockDim.x) gDs[e] = gD[(long)p * pc.Dw + pc.doff + e];
+  __syncthreads();
+  const R inv_nc = R(1) / R(nc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  bool oor = false;
+  for (int k = warp; k < nc; k += nw) {
+    const long row = (long)p * nc + k;
+    const R s = Renv[row * 4];
+    R acc = 0;
+    if (s != R(0)) {
+      R tt;
+      const int l = tab_interval<R>(tc, s, tt, oor);
+      const int net = net_of(pc, ti, slot_block(pc, k));
+      const R* base = tab + (((long)net * tc.lc + l) * M) * kCoefStride;
+      for (int m = lane; m < M; m += 32) {
+        const Quint<R> q = load_quint(base + (long)m * kCoefStride);
+        acc += gDs[m] * (quint_slope(q, tt) * s + quint_value(q, tt));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) reinterpret_cast<typename Vec4<R>::T*>(gR)[row] = Vec4<R>::make(acc * inv_nc, R(0), R(0), R(0));
+  }
+}
+
 // ---- se_e3 part: fused pair kernel, one block per atom -------------------------------------------
 // Over the pairs (j, k) of the atom's real neighbours (rows with s > 0), theta = R_j . R_k and
 // G = N^{a_j,a_k}(theta), with dG/dtheta carried forward alongside (the nets have a scalar input):
@@ -243,7 +304,8 @@ struct E3Any {
     for (long e = tid; e < (long)n_nets * nt.per_net; e += nth) wsm[e] = params[e];
   }
   template <bool DERIV>
-  __device__ __forceinline__ void eval(const R* __restrict__ w, R th, R* g, R* dg) const {
+  __device__ __forceinline__ void eval(const R* __restrict__ wsm, int net, R th, R* g, R* dg, bool&) const {
+    const R* w = wsm + (long)net * nt.per_net;
     R x[W], dx[W];
 #pragma unroll
     for (int o = 0; o < W; ++o) {
@@ -365,7 +427,8 @@ struct E3Fixed {
     }
   }
   template <bool DERIV>
-  __device__ __forceinline__ void eval(const R* __restrict__ w, R th, R* g, R* dg) const {
+  __device__ __forceinline__ void eval(const R* __restrict__ wsm, int net, R th, R* g, R* dg, bool&) const {
+    const R* w = wsm + net * PN;
     R x0[A], d0[A], x1[B], d1[B];
     {
       R wv[PA], bv[PA];
@@ -427,11 +490,40 @@ struct E3Fixed {
   }
 };
 
+// Compressed nets (Eq. (compress)): G and dG/dtheta from the quintic pieces in theta of each net;
+// the M <= MW outputs' coefficients are read through the L1 cache (the tables stay in L2).
+template <class R, int MW>
+struct E3Tab {
+  static constexpr int kM = MW;
+  const R* tab;  // [net][interval][M][kCoefStride]
+  TabConst tc;
+  int M;
+  __device__ int per_net() const { return 0; }
+  __device__ void fill(R*, const R* __restrict__, int, int, int) const {}
+  template <bool DERIV>
+  __device__ __forceinline__ void eval(const R* __restrict__, int net, R th, R* g, R* dg, bool& oor) const {
+    R tt;
+    const int l = tab_interval<R>(tc, th, tt, oor);
+    const R* row = tab + (((long)net * tc.lc + l) * M) * kCoefStride;
+#pragma unroll
+    for (int m = 0; m < MW; ++m) {
+      if (m < M) {
+        const Quint<R> q = load_quint(row + (long)m * kCoefStride);
+        g[m] = quint_value(q, tt);
+        dg[m] = DERIV ? quint_slope(q, tt) : R(0);
+      } else {
+        g[m] = R(0);
+        dg[m] = R(0);
+      }
+    }
+  }
+};
+
 // BWD = 0: D block; BWD = 1: dE/dR rows (gR, [rows][4], every row of the atom written).
 template <class R, class Ev, int BWD>
 __global__ void __launch_bounds__(128)
     k_e3(PathConst pc, Ev ev, const R* __restrict__ params, int n_nets, const R* __restrict__ Renv,
-         const R* __restrict__ gD, R* __restrict__ D, R* __restrict__ gR) {
+         const R* __restrict__ gD, R* __restrict__ D, R* __restrict__ gR, int* __restrict__ range_flag) {
   constexpr int W = Ev::kM;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   typedef typename Vec4<R>::T V4;
@@ -471,6 +563,7 @@ __global__ void __launch_bounds__(128)
     for (int e = tid; e < nv; e += blockDim.x) gRv[e] = Vec4<R>::make(R(0), R(0), R(0), R(0));
   __syncthreads();
   const R inv = R(1) / (R(nc) * R(nc));
+  bool oor = false;
   R acc[W];
 #pragma unroll
   for (int m = 0; m < W; ++m) acc[m] = R(0);
@@ -482,7 +575,7 @@ __global__ void __launch_bounds__(128)
       const V4 rk = Rv[k];
       const R th = ((rj.x * rk.x + rj.y * rk.y) + rj.z * rk.z) + rj.w * rk.w;
       R g[W], dg[W];
-      ev.template eval<BWD != 0>(wsm + (long)(tj * nt_types + tv[k]) * pn, th, g, dg);
+      ev.template eval<BWD != 0>(wsm, tj * nt_types + tv[k], th, g, dg, oor);
       if (!BWD) {
 #pragma unroll
         for (int m = 0; m < W; ++m) acc[m] += th * g[m];
@@ -516,6 +609,7 @@ __global__ void __launch_bounds__(128)
       }
     }
   }
+  if (oor && range_flag) atomicOr(range_flag, 1);
   if (!BWD) {
 #pragma unroll
     for (int m = 0; m < W; ++m) {
@@ -722,7 +816,7 @@ bool e3_supported(const PartDesc& P, int precision) {
 
 template <class R, class Ev>
 cudaError_t launch_e3_ev(const PathConst& pc, const Ev& ev, int per_net_smem, const R* w, int n_nets, const R* Renv,
-                         const R* gD, R* D, R* gR, bool bwd, cudaStream_t st) {
+                         const R* gD, R* D, R* gR, bool bwd, cudaStream_t st, int* range_flag = nullptr) {
   const size_t smem = sizeof(typename Vec4<R>::T) * 2 * pc.nc +
                       sizeof(R) * ((size_t)n_nets * per_net_smem + Ev::kM) + sizeof(int) * 2 * pc.nc;
   auto kf = k_e3<R, Ev, 0>;
@@ -732,10 +826,22 @@ cudaError_t launch_e3_ev(const PathConst& pc, const Ev& ev, int per_net_smem, co
     if (e != cudaSuccess) return e;
   }
   if (bwd)
-    kb<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR);
+    kb<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR, range_flag);
   else
-    kf<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR);
+    kf<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR, range_flag);
   return cudaGetLastError();
+}
+
+// se_e3 part with compressed nets: the quintic pieces in theta (tab: the model's FP64 or FP32 copy).
+template <class R>
+cudaError_t launch_e3_tab(const DeviceModel& m, const PartDesc& P, const PathConst& pc, const R* tab, const R* Renv,
+                          const R* gD, R* D, R* gR, bool bwd, int* range_flag, cudaStream_t st) {
+  const TabConst tc = tab_const(m);
+  if (P.M <= 8)
+    return launch_e3_ev<R>(pc, E3Tab<R, 8>{tab, tc, P.M}, 0, nullptr, P.n_nets, Renv, gD, D, gR, bwd, st, range_flag);
+  if (P.M <= 16)
+    return launch_e3_ev<R>(pc, E3Tab<R, 16>{tab, tc, P.M}, 0, nullptr, P.n_nets, Renv, gD, D, gR, bwd, st, range_flag);
+  return launch_e3_ev<R>(pc, E3Tab<R, 32>{tab, tc, P.M}, 0, nullptr, P.n_nets, Renv, gD, D, gR, bwd, st, range_flag);
 }
 
 template <class R>
@@ -783,6 +889,11 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   const long N = pc.natoms;
   const int nparts = (int)m.parts.size();
   std::vector<PartBufs<R>> pb(nparts);
+  // compressed models (se_e2_r, se_e3): the first part's nets are replaced by the quintic pieces
+  const R* tab = reinterpret_cast<const R*>(std::is_same<R, double>::value ? (const void*)m.tab64
+                                                                           : (const void*)m.tab32);
+  auto tabulated = [&](int q) { return m.compressed && q == 0; };
+  int* range_flag = &io.status->table_range;
   long maxe = 1;  // widest embedding-gradient buffer over the parts
   for (int q = 0; q < nparts; ++q) {
     const PartDesc& P = m.parts[q];
@@ -791,7 +902,7 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     const long rows = N * P.nc;
     b.Renv = ar.get<R>(rows * 4);
     b.gR = ar.get<R>(rows * 4);
-    if (P.kind == PART_E3) continue;
+    if (P.kind == PART_E3 || tabulated(q)) continue;
     for (int l = 0; l < P.nl; ++l) {
       const int w = P.emb[l].n_out;
       b.Y.push_back(ar.get<R>(rows * w));
@@ -827,7 +938,15 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     }
     if (P.kind == PART_E3) {
       ProfScope _ps(io.prof, "e3_fwd", st);
-      DP_CUDA_TRY(launch_e3<R>(P, pq, params, b.Renv, nullptr, D, nullptr, false, st));
+      if (tabulated(q))
+        DP_CUDA_TRY(launch_e3_tab<R>(m, P, pq, tab, b.Renv, nullptr, D, nullptr, false, range_flag, st));
+      else
+        DP_CUDA_TRY(launch_e3<R>(P, pq, params, b.Renv, nullptr, D, nullptr, false, st));
+      continue;
+    }
+    if (tabulated(q)) {  // se_e2_r
+      ProfScope _ps(io.prof, "rtab_fwd", st);
+      k_rtab_fwd<R><<<(unsigned)N, 64, 0, st>>>(pq, tab, tab_const(m), tsorted, b.Renv, D, range_flag);
       continue;
     }
     for (int n = 0; n < P.n_nets; ++n) {
@@ -873,7 +992,13 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     const long rows = N * P.nc;
     if (P.kind == PART_E3) {
       ProfScope _ps(io.prof, "e3_bwd", st);
-      DP_CUDA_TRY(launch_e3<R>(P, pq, params, b.Renv, gD, nullptr, b.gR, true, st));
+      if (tabulated(q))
+        DP_CUDA_TRY(launch_e3_tab<R>(m, P, pq, tab, b.Renv, gD, nullptr, b.gR, true, nullptr, st));
+      else
+        DP_CUDA_TRY(launch_e3<R>(P, pq, params, b.Renv, gD, nullptr, b.gR, true, st));
+    } else if (tabulated(q)) {  // se_e2_r
+      ProfScope _ps(io.prof, "rtab_bwd", st);
+      k_rtab_bwd<R><<<(unsigned)N, 128, sizeof(R) * P.M, st>>>(pq, tab, tab_const(m), tsorted, b.Renv, gD, b.gR);
     } else {
       const R* G = b.Y[P.nl - 1];
       if (P.kind == PART_A) {

@@ -21,36 +21,11 @@
 #include "fit_tc.cuh"
 #include "mom.cuh"
 #include "table.cuh"
+#include "tabeval.cuh"
 
 namespace dpgb {
 
 namespace {
-
-struct TabConst {
-  double s0, stride1, stride2, split, smax;
-  int n1, n2, lc;
-};
-
-// Coefficients of one (interval, output) pair: a..f padded to 8 values (two 16-byte loads in
-// FP32), table layout [net][interval][output][8].
-constexpr int kCoefStride = 8;
-
-TabConst tab_const(const DeviceModel& m) {
-  TabConst c;
-  c.s0 = m.tab.s0;
-  c.stride1 = m.tab.stride1;
-  c.stride2 = m.tab.stride2;
-  c.n1 = m.tab.n1;
-  c.n2 = m.tab.n2;
-  c.lc = c.n1 + c.n2;
-  c.split = c.s0 + c.n1 * c.stride1;
-  c.smax = c.split + c.n2 * c.stride2;
-  return c;
-}
-
-__host__ __device__ inline double node_at(const TabConst& c, int l) {
-  return l <= c.n1 ? c.s0 + l * c.stride1 : c.s0 + c.n1 * c.stride1 + (l - c.n1) * c.stride2;
-}
 
 // Values, first and second derivatives of every output of net `net` at node l (jets).
 __global__ void k_table_nodes(const double* __restrict__ p64, const LayerDesc* __restrict__ layers, int n_embed,
@@ -139,48 +114,6 @@ __global__ void k_table_coef(TabConst tc, int M, int nets, const double* __restr
     tab32[o + q] = q < 6 ? (float)c[q] : 0.f;
   }
 }
-
-// One interval's coefficients of one output, loaded with 16-byte vector loads.
-template <class R>
-struct Quint {
-  R a, b, c, d, e, f;
-};
-__device__ __forceinline__ Quint<float> load_quint(const float* __restrict__ p) {
-  const float4 x = *reinterpret_cast<const float4*>(p);
-  const float4 y = *reinterpret_cast<const float4*>(p + 4);
-  return Quint<float>{x.x, x.y, x.z, x.w, y.x, y.y};
-}
-__device__ __forceinline__ Quint<double> load_quint(const double* __restrict__ p) {
-  const double2 x = reinterpret_cast<const double2*>(p)[0];
-  const double2 y = reinterpret_cast<const double2*>(p)[1];
-  const double2 z = reinterpret_cast<const double2*>(p)[2];
-  return Quint<double>{x.x, x.y, y.x, y.y, z.x, z.y};
-}
-template <class R>
-__device__ __forceinline__ R quint_value(const Quint<R>& q, R t) {
-  return ((((q.a * t + q.b) * t + q.c) * t + q.d) * t + q.e) * t + q.f;
-}
-template <class R>
-__device__ __forceinline__ R quint_slope(const Quint<R>& q, R t) {
-  return (((R(5) * q.a * t + R(4) * q.b) * t + R(3) * q.c) * t + R(2) * q.d) * t + q.e;
-}
-
-template <class R>
-__device__ __forceinline__ int tab_interval(const TabConst& tc, R s, R& tt, bool& oor) {
-  int l;
-  if (s < R(tc.split)) {
-    l = (int)floor((s - R(tc.s0)) * R(1.0 / tc.stride1));
-    l = l < 0 ? 0 : (l > tc.n1 - 1 ? tc.n1 - 1 : l);
-    tt = s - (R(tc.s0) + R(l) * R(tc.stride1));
-  } else {
-    l = tc.n1 + (int)floor((s - R(tc.split)) * R(1.0 / tc.stride2));
-    if (l > tc.lc - 1) l = tc.lc - 1;
-    tt = s - (R(tc.split) + R(l - tc.n1) * R(tc.stride2));
-    if (s > R(tc.smax)) oor = true;
-  }
-  return l;
-}
-
 
 // ---- per-slot environment of the listed pairs: (s, u) and (ds/dr, r), once per step --------
 template <class R>
@@ -525,12 +458,14 @@ int build_tables(DeviceModel& m) {
     set_error("compressed path supports M <= 256 and M_< <= 32");
     return DP_E_UNSUPPORTED;
   }
-  // s in [0, 1/r_s]: stride 0.01 on the first 90 % of the range, 0.1 on the rest
+  // s in [0, 1/r_s]: stride 0.01 on the first 90 % of the range, 0.1 on the rest; se_e3 pieces are
+  // in theta = R_j . R_k in [0, 2/r_s^2] (|R_j|^2 = 2 s_j^2, 1 + cos >= 0): the same grid scaled by 2/r_s
   const double smax = 1.0 / c.rcut_smth;
+  const double scale = c.descriptor == DP_DESC_SE_E3 ? 2.0 / c.rcut_smth : 1.0;
   m.tab.s0 = 0.0;
-  m.tab.stride1 = 0.01;
+  m.tab.stride1 = 0.01 * scale;
   m.tab.n1 = (int)std::floor(0.9 * smax / 0.01 + 0.5);
-  m.tab.stride2 = 0.1;
+  m.tab.stride2 = 0.1 * scale;
   const double rest = smax - m.tab.n1 * 0.01;
   m.tab.n2 = rest > 0 ? (int)std::ceil(rest / 0.1 - 1e-9) : 1;
   if (m.tab.n2 < 1) m.tab.n2 = 1;
@@ -558,6 +493,7 @@ int build_tables(DeviceModel& m) {
   DP_CUDA_TRY(cudaDeviceSynchronize());
   cudaFree(y);
   cudaFree(dl);
+  if (c.descriptor != DP_DESC_SE_E2_A) return DP_OK;  // the moment path is se_e2_a's
   return build_mom_tables(m);
 }
 

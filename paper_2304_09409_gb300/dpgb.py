@@ -283,7 +283,7 @@ class Model:
         return NList(h, N, self.nc, ov.value)
 
     def export_table(self) -> np.ndarray:
-        nets = self.cfg.ntypes if getattr(self.cfg, "type_one_side", 0) else self.cfg.ntypes ** 2
+        nets = int(self.cfg.n_embed_nets)
         M = int(self.cfg.embed[-1])
         lc = ctypes.c_int(0)
         smax = 1.0 / float(self.cfg.rcut_smth)

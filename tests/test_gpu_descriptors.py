@@ -159,13 +159,76 @@ def test_weight_file_roundtrip(tmp_path):
     b.free()
 
 
-@pytest.mark.parametrize("prec,compressed", [("fp64", True), ("fp32", True), ("bf16", False), ("tf32", False)])
-def test_other_paths_refuse(prec, compressed):
+@pytest.mark.parametrize("kind,prec,compressed", [("hybrid", "fp64", True), ("hybrid_e3", "fp32", True),
+                                                  ("r", "bf16", False), ("e3", "tf32", False), ("e3", "bf16", True)])
+def test_other_paths_refuse(kind, prec, compressed):
     dpgb = _dp()
-    cfg = _tiny("r")
+    cfg = _tiny(kind)
     with pytest.raises(dpgb.DPError) as ei:
         dpgb.Model(cfg, I.make_params(cfg, 0), precision=prec, compressed=compressed)
     assert ei.value.code == dpgb.DP_E_UNSUPPORTED
+
+
+# ---- compressed se_e2_r and se_e3 (Eq. (compress); se_e3 pieces in theta) -------------------------
+
+@pytest.mark.parametrize("kind", ["r", "e3"])
+def test_compressed_tables_equal_oracle(kind):
+    dpgb = _dp()
+    cfg = _water(kind)[0]
+    p = I.make_params(cfg, 0)
+    m = dpgb.Model(cfg, p, precision="fp64", compressed=True)
+    got = m.export_table()
+    x0, h1, n1, h2, n2 = oracle.table_layout(cfg)
+    want = oracle.table_build(cfg, p, x0, h1, n1, h2, n2)
+    assert got.shape == want.shape
+    # the t^5..t^3 coefficients divide node data by dx^5..dx^3 (ulp-level node differences show
+    # there magnified): compare the low coefficients, and the pieces where they are used
+    np.testing.assert_allclose(got[..., 3:], want[..., 3:], rtol=1e-11, atol=1e-12)
+    nodes = np.concatenate([x0 + np.arange(n1 + 1) * h1, x0 + n1 * h1 + np.arange(1, n2 + 1) * h2])
+    dx = np.diff(nodes)[None, :, None]
+    scale = max(1.0, np.abs(want[..., 5]).max())
+    for frac in (0.0, 0.3, 0.7, 1.0):
+        t = frac * dx
+        g = lambda c: ((((c[..., 0] * t + c[..., 1]) * t + c[..., 2]) * t + c[..., 3]) * t + c[..., 4]) * t + c[..., 5]  # noqa: E731
+        assert np.abs(g(got) - g(want)).max() <= 1e-12 * scale
+    m.free()
+
+
+@pytest.mark.parametrize("kind", ["r", "e3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_compressed_water192_vs_oracle(kind, prec):
+    """Against the oracle's compressed result on the same pieces: FP64 to the FP64 bars, FP32 to the
+    FP32 ones (forces of ~1 eV/A RMS)."""
+    dpgb = _dp()
+    cfg, p = _water(kind)
+    fr = I.water_frame(0)
+    lay = oracle.table_layout(cfg)
+    ref = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, table=oracle.table_build(cfg, p, *lay), table_layout=lay)
+    assert ref.status == 0
+    m = dpgb.Model(cfg, p, precision=prec, compressed=True)
+    e, f, v, ae = m.compute(fr.coord, fr.atype, fr.box, atom_energy=True)
+    if prec == "fp64":
+        assert abs(float(e[0]) - ref.energy) <= 1e-12 * abs(ref.energy)
+        assert np.abs(f - ref.force).max() <= 1e-10
+        assert np.abs(v - ref.virial).max() <= 1e-12 * np.abs(ref.virial).max()
+    else:
+        assert np.abs(f - ref.force).max() <= 1e-3
+        assert abs(float(e[0]) - ref.energy) / fr.natoms <= 1e-6 * abs(ref.energy) / fr.natoms
+        assert np.abs(v - ref.virial).max() <= 1e-5 * np.abs(ref.virial).max()
+    m.free()
+
+
+@pytest.mark.parametrize("kind", ["r", "e3"])
+def test_compressed_tiny_triclinic_fp64(kind):
+    dpgb = _dp()
+    cfg = _tiny(kind)
+    fr = tiny_frame(seed=5)
+    p = I.make_params(cfg, 1)
+    lay = oracle.table_layout(cfg)
+    ref = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box, table=oracle.table_build(cfg, p, *lay), table_layout=lay)
+    m = dpgb.Model(cfg, p, precision="fp64", compressed=True)
+    _assert_fp64(m.compute(fr.coord, fr.atype, fr.box, atom_energy=True), ref, fr.natoms)
+    m.free()
 
 
 def test_param_grad_refuses():
