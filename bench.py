@@ -364,29 +364,32 @@ def _e3_flops_per_pair(widths, M):
 
 def run_descriptors(local, flush, steps=5, warmup=3):
     """The other descriptors of Sec. II.A.1 on the same 12,288-atom water frame, FP32 CUDA-core path
-    (the path these models run on), forces compared with the FP64 GPU path: se_e2_r; hybrid
-    se_e2_a (r_c 4) + se_e2_r (r_c 6); se_e3; hybrid se_e2_a (r_c 4) + se_e3 (r_c 6), each with its
-    output layer scaled to forces of ~1 eV/A RMS.  se_e3 parts also report their pair kernels
+    (the path these models run on), forces compared with the FP64 GPU path (uncompressed): se_e2_r,
+    also compressed; hybrid se_e2_a (r_c 4) + se_e2_r (r_c 6); se_e3, also compressed (pieces in
+    theta); hybrid se_e2_a (r_c 4) + se_e3 (r_c 6), each with its output layer scaled to forces of
+    ~1 eV/A RMS.  se_e3 parts also report their pair kernels
     against the FP32 ALU peak (pairs = sum over atoms of real neighbours squared)."""
     import torch
     from paper_2304_09409_gb300 import dpgb, inputs as I
     _, _, _, big = _workload()
     coord = torch.tensor(big.coord, device="cuda")
     atype = torch.tensor(big.atype, device="cuda")
-    legs = {"se_e2_r": (I.water_model_r(), I.water_r_params_scaled(0)),
-            "hybrid_se_e2_a+se_e2_r": (I.water_model_hybrid(), I.water_hybrid_params_scaled(0)),
-            "se_e3": (I.water_model_e3(), I.water_e3_params_scaled(0)),
-            "hybrid_se_e2_a+se_e3": (I.water_model_hybrid_e3(), I.water_hybrid_e3_params_scaled(0))}
+    legs = {"se_e2_r": (I.water_model_r(), I.water_r_params_scaled(0), False),
+            "se_e2_r-compressed": (I.water_model_r(), I.water_r_params_scaled(0), True),
+            "hybrid_se_e2_a+se_e2_r": (I.water_model_hybrid(), I.water_hybrid_params_scaled(0), False),
+            "se_e3": (I.water_model_e3(), I.water_e3_params_scaled(0), False),
+            "se_e3-compressed": (I.water_model_e3(), I.water_e3_params_scaled(0), True),
+            "hybrid_se_e2_a+se_e3": (I.water_model_hybrid_e3(), I.water_hybrid_e3_params_scaled(0), False)}
     out = {"workload": "water 12,288 atoms (192-atom frame tiled 4x4x4), models of inputs.water_model_r / "
                        "_hybrid / _e3 / _hybrid_e3, FP32 networks, L2 flushed between steps"}
-    for name, (cfg, params) in legs.items():
+    for name, (cfg, params, comp) in legs.items():
         m64 = dpgb.Model(cfg, params, device=local, precision="fp64")
         ms64, _, _, o64 = time_path(m64, coord, atype, big.box, steps=1, warmup=1, flush=flush)
         f64 = o64[1].cpu().numpy()
         nl = m64.build_nlist(big.coord, big.atype, big.box)
         nj, _ = nl.export()
         m64.free()
-        m = dpgb.Model(cfg, params, device=local, precision="fp32")
+        m = dpgb.Model(cfg, params, device=local, precision="fp32", compressed=comp)
         ms, launches, _, o = time_path(m, coord, atype, big.box, steps=steps, warmup=warmup, flush=flush)
         _, _, prof, _ = time_path(m, coord, atype, big.box, steps=steps, warmup=2, flush=flush, profile=True)
         m.free()
