@@ -56,8 +56,15 @@ constexpr int kRows = 128;        // accumulator rows: (atom, c)
 constexpr int kMomThreads = 192;  // 4 builder / epilogue warps, an MMA warp and a TMA producer warp
 constexpr int kABlock = kRows * 128;  // one 64-column K block of 128 rows (bytes)
 constexpr int kGroupAtoms = 4;        // backward: atoms per staged group of dE/dD rows
-constexpr int kAccBufs = 2;           // backward: 64-column TMEM accumulators in rotation
-constexpr int kBwdStages = 2;         // backward: coefficient ring depth (three CTAs fit an SM)
+// backward: 64-column TMEM accumulators in rotation, and the coefficient ring depth.  The one-pass
+// (mixed) kernel keeps two of each so that three CTAs fit an SM (3 x 128 TMEM columns); the
+// three-pass kernel runs one CTA per SM and takes four accumulators and three stages, so the MMAs
+// of the next chunks run while the epilogue drains one.
+template <int NPASS>
+struct BwdDepth {
+  static constexpr int acc = NPASS == 1 ? 2 : 4;
+  static constexpr int stages = NPASS == 1 ? 2 : 3;
+};
 
 struct MomArgs {
   int ntypes, nc, M, A, lc, lcp, n1;
@@ -217,10 +224,12 @@ __device__ __forceinline__ void stage_runs(const MomArgs& g, int row0, int row_e
   }
 }
 
-// Ring depth of the forward's operand stages.
+// Ring depth of the forward's operand stages: two keep three CTAs (mixed mode) on an SM, one wave of
+// tiles; the three-pass kernel (one CTA per SM, 60 KB stages) takes three, two blocks of run-record
+// copies in flight per builder thread.
 template <int NPASS>
 struct MomStages {
-  static constexpr int value = 2;  // two stages keep three CTAs (mixed mode) on an SM: one wave of tiles
+  static constexpr int value = NPASS == 1 ? 2 : 3;
 };
 
 
@@ -481,7 +490,7 @@ __global__ void __launch_bounds__(256, 3)
 // block kb are released to the MMA once they have landed, up to S - 1 blocks later.
 // =============================================================================================
 template <int NPASS, int NPAD>
-__global__ void __launch_bounds__(kMomThreads, 3)
+__global__ void __launch_bounds__(kMomThreads, NPASS == 1 ? 3 : 1)
     k_mom_fwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
   constexpr int S = MomStages<NPASS>::value;
@@ -882,7 +891,8 @@ template <int NPASS, int NPAD>
 __global__ void __launch_bounds__(kMomThreads, 1)
     k_mom_bwd(const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, const MomArgs g) {
   constexpr int PARTS = NPASS == 1 ? 1 : 2;
-  constexpr int S = kBwdStages;
+  constexpr int S = BwdDepth<NPASS>::stages;
+  constexpr int kAccBufs = BwdDepth<NPASS>::acc;
   constexpr int A_BYTES = 2 * kABlock;  // K = m in two 64-column blocks
   constexpr int B_KBLK = 64 * 128;      // 64 rows (8 intervals x 8 powers) x 128 B
   constexpr int B_STAGE = PARTS * 2 * B_KBLK;
@@ -1215,14 +1225,16 @@ __global__ void k_mom_tables(const double* __restrict__ tab, int ntypes, int one
 }
 
 size_t fwd_smem(int npass, int npad, int nc) {
-  const int parts = npass == 1 ? 1 : 2, S = 2;
+  const int parts = npass == 1 ? 1 : 2, S = npass == 1 ? MomStages<1>::value : MomStages<3>::value;
   return (size_t)S * parts * (kABlock + npad * 128) + (size_t)kAtoms * nc * 2 + (2 * S + 1) * 8 + 4 +
          4 * DP_MAX_TYPES + 1024 + 64;
 }
 size_t bwd_smem(int npass, int nc) {
   const int parts = npass == 1 ? 1 : 2;
-  return (size_t)parts * 2 * kABlock + kBwdStages * (size_t)parts * 2 * 64 * 128 + (size_t)kAtoms * nc * 2 +
-         kRows * 4 + (2 * kBwdStages + 1 + 2 * kAccBufs) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
+  const int S = npass == 1 ? BwdDepth<1>::stages : BwdDepth<3>::stages;
+  const int nacc = npass == 1 ? BwdDepth<1>::acc : BwdDepth<3>::acc;
+  return (size_t)parts * 2 * kABlock + S * (size_t)parts * 2 * 64 * 128 + (size_t)kAtoms * nc * 2 +
+         kRows * 4 + (2 * S + 1 + 2 * nacc) * 8 + 4 + 4 * DP_MAX_TYPES + 1024 + 64;
 }
 
 template <int NPASS, int NPAD>
