@@ -9,8 +9,10 @@
 // streams its A operand (the descriptor, or the previous phase's activations) and its weights
 // through one two-stage TMA ring of high and low halves (96 KB a stage); the accumulator lives in
 // tensor memory.  Activations go from each epilogue to the next phase through a per-tile scratch
-// that stays in L2 (high and low BF16 halves for the next A operand, FP32 for the skip and the
-// gates), so the shared memory holds only the ring; dE/dD leaves in 256-column chunks from two
+// that stays in L2 (high and low BF16 halves for the next A operand, FP32 for the gates): the
+// epilogue writes the next A operand into the idle ring in the swizzled layout of the TMA box and
+// stores it with four tiled TMA stores per half (coalesced), clipped at the end of the tile's
+// type; the FP32 residual stream stays in tensor memory; dE/dD leaves in 256-column chunks from two
 // alternating accumulators, so that one chunk's epilogue overlaps the next chunk's MMAs.  One
 // thread issues TMA, one issues tcgen05.mma, eight warps run the epilogues; every mbarrier wait
 // is bounded (on time-out the CTA records an error and finishes).
@@ -41,6 +43,7 @@ constexpr int kSLd = 256;  // row pitch of the activation scratch (elements)
 struct SplitMaps {
   CUtensorMap d[2];                       // D hi / lo [rows][KD], box {64, 128}
   CUtensorMap x[2][2];                    // activation scratch buffer b (hi / lo) [rows][kSLd], box {64, 128}
+  CUtensorMap xt[DP_MAX_TYPES][2][2];     // the same per type, over the type's rows only (stores)
   CUtensorMap w[DP_MAX_TYPES][2 * kSL][2];  // per type: forward W_l^T (slot l), backward W_l (slot nh + l); hi / lo
 };
 
@@ -60,6 +63,27 @@ struct SplitArgs {
   float* gD;                // dE/dD FP32 [rows][KD]
   int* err;
 };
+
+// 32-byte global accesses (one full sector per lane): half the instructions and no partial-sector
+// writes where each lane owns a row of the tile.
+__device__ __forceinline__ void st_v8(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void ld_v8(const float* p, float* v) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+
+// tanh from the exponential, tanh x = 1 - 2 / (1 + e^{2x}) (x clamped to +-15, where tanh is 1 to
+// FP32): absolute error a few 1e-7, below the ~2^-17 relative rounding the next GEMM's split
+// operands apply anyway.
+__device__ __forceinline__ float tanh_ex(float x) {
+  const float e = __expf(2.f * fminf(fmaxf(x, -15.f), 15.f));
+  return 1.f - __fdividef(2.f, 1.f + e);
+}
 
 __device__ __forceinline__ void split2(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
@@ -255,18 +279,31 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     tc_fence_before();
     mbar_arrive(&accfree[buf]);
   };
-  auto xs_at = [&](int b, int hl, int col) -> __nv_bfloat16* { return g.xs[b][hl] + row * kSLd + col; };
   auto gate_at = [&](int l, int col) -> float* { return g.gate + ((long)l * rows + row) * kSLd + col; };
-  auto put_x = [&](int xb, int c, const float* x) {
+  // the next A operand, staged in the idle ring: 64-column block kb of half hl at (2 kb + hl) * kSA,
+  // row rl at rl * 128 bytes, 16-byte chunk j at (j ^ (rl % 8)) * 16 (the TMA box's 128-byte swizzle)
+  auto put_x = [&](int c, const float* x) {
     __align__(16) __nv_bfloat16 hi[16], lo[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) split2(x[i], hi[i], lo[i]);
-    uint4* dh = reinterpret_cast<uint4*>(xs_at(xb, 0, c));
-    uint4* dl = reinterpret_cast<uint4*>(xs_at(xb, 1, c));
-    dh[0] = *reinterpret_cast<const uint4*>(hi);
-    dh[1] = *reinterpret_cast<const uint4*>(hi + 8);
-    dl[0] = *reinterpret_cast<const uint4*>(lo);
-    dl[1] = *reinterpret_cast<const uint4*>(lo + 8);
+    const int kb = c >> 6, j = (c & 63) >> 3;
+    unsigned char* bh = smem + (2 * kb) * kSA + rl * 128;
+    unsigned char* bl = bh + kSA;
+    *reinterpret_cast<uint4*>(bh + ((j ^ (rl & 7)) << 4)) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(bh + (((j + 1) ^ (rl & 7)) << 4)) = *reinterpret_cast<const uint4*>(hi + 8);
+    *reinterpret_cast<uint4*>(bl + ((j ^ (rl & 7)) << 4)) = *reinterpret_cast<const uint4*>(lo);
+    *reinterpret_cast<uint4*>(bl + (((j + 1) ^ (rl & 7)) << 4)) = *reinterpret_cast<const uint4*>(lo + 8);
+  };
+  // the staged operand to scratch buffer xb: eight TMA stores, complete before the phase is released
+  auto flush_x = [&](int xb) {
+    fence_async_smem();
+    bar_sync(1, kSEpi);
+    if (threadIdx.x == 0) {
+      for (int kb = 0; kb < kSLd / 64; ++kb)
+        for (int hl = 0; hl < 2; ++hl) tma_store_2d(&mp.xt[t][xb][hl], smem + (2 * kb + hl) * kSA, kb * 64, row0 - g.row_start[t]);
+      bulk_commit();
+      bulk_wait0();
+    }
   };
   // biases and output weights of this tile's type into shared memory
   for (int l = 0; l < nh; ++l)
@@ -282,16 +319,27 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     const float* bias = s_bias + l * 256;
     const int xb = l & 1;
     float e_acc = 0.f;
+    // the accumulator (and residual) pieces load one ahead of the piece being processed
+    uint32_t na[16], ny[16];
+    tmem_ld16_async(tq + half * 16, na);
+    if (sk) tmem_ld16_async(tq + 256 + half * 16, ny);
+    tmem_wait_ld();
     for (int c = half * 16; c < kSLd; c += 32) {  // zeros beyond N: the next A operand's K padding
       uint32_t ra[16], ry[16];
-      tmem_ld16_async(tq + c, ra);
-      if (sk) tmem_ld16_async(tq + 256 + c, ry);
-      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        ra[i] = na[i];
+        ry[i] = ny[i];
+      }
+      if (c + 32 < kSLd) {
+        tmem_ld16_async(tq + c + 32, na);
+        if (sk) tmem_ld16_async(tq + 256 + c + 32, ny);
+      }
       float out[16], y[16], gt[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int col = c + i;
-        const float th = col < N ? tanhf(__uint_as_float(ra[i]) + bias[col]) : 0.f;
+        const float th = col < N ? tanh_ex(__uint_as_float(ra[i]) + bias[col]) : 0.f;
         y[i] = th + (sk && col < N ? __uint_as_float(ry[i]) : 0.f);
         gt[i] = 1.f - th * th;
         if (last) {
@@ -302,20 +350,21 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
           out[i] = y[i];
         }
       }
+      tmem_wait_ld();                          // the next piece has landed
       if (!last) tmem_st16(tq + 256 + c, y);  // the residual stream of the next layer
+      put_x(c, out);
       if (!rv) continue;
       if (!last && c < N) {
-        float4* gp = reinterpret_cast<float4*>(gate_at(l, c));
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gp[q] = make_float4(gt[4 * q], gt[4 * q + 1], gt[4 * q + 2], gt[4 * q + 3]);
+        st_v8(gate_at(l, c), gt);
+        st_v8(gate_at(l, c + 8), gt + 8);
       }
-      put_x(xb, c, out);
     }
     if (last) {
       s_e[half * SBM + rl] = e_acc;
       bar_sync(1, kSEpi);
       if (half == 0 && rv) g.atom_e[g.perm[row]] = (double)(s_e[rl] + s_e[SBM + rl] + g.b_last[t]);
     }
+    flush_x(xb);
     release(0, !last);
   }
   // backward of layers nh-1 .. 1: gz_{l-1} into the scratch, gy_{l-1} kept for the next skip
@@ -329,22 +378,26 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     const bool top = (l == nh - 1), sk = g.skip[l] == 1, keep = (l - 1 >= 1);
     const int p = nh + (nh - 1 - l);  // phase index
     const int xb = p & 1;
+    const bool ldy = sk && !top;
+    uint32_t na[16], ny[16];
+    tmem_ld16_async(tq + half * 16, na);
+    if (ldy) tmem_ld16_async(tq + 256 + half * 16, ny);
+    tmem_wait_ld();
     for (int c = half * 16; c < kSLd; c += 32) {  // zeros beyond N: the next A operand's K padding
       uint32_t ra[16], ry[16];
-      tmem_ld16_async(tq + c, ra);
-      if (sk && !top) tmem_ld16_async(tq + 256 + c, ry);
-      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        ra[i] = na[i];
+        ry[i] = ny[i];
+      }
+      if (c + 32 < kSLd) {
+        tmem_ld16_async(tq + c + 32, na);
+        if (ldy) tmem_ld16_async(tq + 256 + c + 32, ny);
+      }
       float gt[16];
       if (rv && c < N) {
-        const float4* gp = reinterpret_cast<const float4*>(gate_at(l - 1, c));
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 x = gp[q];
-          gt[4 * q] = x.x;
-          gt[4 * q + 1] = x.y;
-          gt[4 * q + 2] = x.z;
-          gt[4 * q + 3] = x.w;
-        }
+        ld_v8(gate_at(l - 1, c), gt);
+        ld_v8(gate_at(l - 1, c + 8), gt + 8);
       } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) gt[i] = 0.f;
@@ -358,10 +411,11 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
         gy[i] = v;
         gz[i] = v * gt[i];
       }
+      tmem_wait_ld();
       if (keep) tmem_st16(tq + 256 + c, gy);
-      if (!rv) continue;
-      put_x(xb, c, gz);
+      put_x(c, gz);
     }
+    flush_x(xb);
     release(0, keep);
   }
   // dE/dD in 256-column chunks from the two alternating accumulators
@@ -370,13 +424,22 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     wait_acc(buf);
     const int N = min(256, KD - 256 * c);
     float* dst = g.gD + row * KD + 256 * c;
+    const uint32_t tb = tq + (uint32_t)(buf * 256);
+    uint32_t nv[16];
+    if (half * 16 < N) {
+      tmem_ld16_async(tb + half * 16, nv);
+      tmem_wait_ld();
+    }
     for (int q = half * 16; q < N; q += 32) {
       float v[16];
-      tmem_ld16(tq + (uint32_t)(buf * 256) + q, v);
-      if (!rv) continue;
-      float4* d4 = reinterpret_cast<float4*>(dst + q);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) d4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(nv[i]);
+      if (q + 32 < N) tmem_ld16_async(tb + q + 32, nv);
+      if (rv) {
+        st_v8(dst + q, v);
+        st_v8(dst + q + 8, v + 8);
+      }
+      tmem_wait_ld();
     }
     tc_fence_before();
     mbar_arrive(&accfree[buf]);
@@ -443,6 +506,11 @@ int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bflo
     for (int hl = 0; rc == DP_OK && hl < 2; ++hl) {
       a.xs[b][hl] = xs + (long)(2 * b + hl) * N * kSLd;
       rc = make_tmap_bf16(&mp.x[b][hl], a.xs[b][hl], N, kSLd, SBM);
+      for (int t = 0; rc == DP_OK && t < nt; ++t) {
+        const long n_t = io.type_start[t + 1] - io.type_start[t];
+        if (n_t > 0)
+          rc = make_tmap_bf16(&mp.xt[t][b][hl], a.xs[b][hl] + (long)io.type_start[t] * kSLd, n_t, kSLd, SBM);
+      }
     }
   if (rc != DP_OK) return rc;
   const float* p32 = m.p32;
