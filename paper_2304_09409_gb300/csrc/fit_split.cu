@@ -14,7 +14,7 @@
 // stores it with four tiled TMA stores per half (coalesced), clipped at the end of the tile's
 // type; the FP32 residual stream stays in tensor memory; dE/dD leaves in 256-column chunks from two
 // alternating accumulators, so that one chunk's epilogue overlaps the next chunk's MMAs.  One
-// thread issues TMA, one issues tcgen05.mma, eight warps run the epilogues; every mbarrier wait
+// thread issues TMA, one issues tcgen05.mma, sixteen warps run the epilogues; every mbarrier wait
 // is bounded (on time-out the CTA records an error and finishes).
 #include <cuda_bf16.h>
 
@@ -31,8 +31,11 @@ namespace {
 using namespace ptx;
 
 constexpr int kSL = 4;  // hidden layers at most
-constexpr int kSEpi = 256;               // eight epilogue warps
+constexpr int kSEpi = 512;               // sixteen epilogue warps: four per 32-row quarter of the tile
 constexpr int kSThreads = kSEpi + 64;    // + a TMA producer warp and an MMA warp
+constexpr int kProd = kSEpi / 32, kMmaW = kProd + 1;  // their warp indices
+constexpr int kParts = kSEpi / 128;      // epilogue warps sharing a row quarter, interleaved by 16 columns
+constexpr int kStep = 16 * kParts;       // column stride of one epilogue thread
 constexpr int SBM = 128, SBK = 64;
 constexpr int kSRing = 2;
 constexpr uint32_t kSA = SBM * SBK * 2;   // 16 KB: one 128 x 64 BF16 block of A
@@ -99,8 +102,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
   uint64_t* accf = empty + kSRing;  // [2] accumulator buffer ready (MMA -> epilogue)
   uint64_t* accfree = accf + 2;     // [2] accumulator read and phase outputs written (epilogue -> MMA, TMA)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accfree + 2);
-  float* s_e = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128]
-  float* s_bias = s_e + 2 * SBM;                           // [kSL][256] biases of the hidden layers
+  float* s_e = reinterpret_cast<float*>(tmem_holder + 4);  // [kParts][128]
+  float* s_bias = s_e + kParts * SBM;                      // [kSL][256] biases of the hidden layers
   float* s_wl = s_bias + kSL * 256;                        // [256] weights of the output layer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     }
     mbar_fence_init();
   }
-  if (warp == 8) tmem_alloc(tmem_holder, 512);
+  if (warp == kProd) tmem_alloc(tmem_holder, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     }
   };
 
-  if (warp == 8) {
+  if (warp == kProd) {
     if (lane == 0) {
       // ---- TMA producer ----
       int it = 0;
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
         mbar_wait(&full[s], (last / kSRing) & 1, g.err);
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == kMmaW) {
     if (lane == 0) {
       // ---- MMA issuer ----
       int it = 0;
@@ -257,10 +260,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
       }
     }
   } else {
-  // ---- epilogues: warps w and w + 4 own rows 32(w % 4) .. +31 and alternate 16-column pieces ----
+  // ---- epilogues: warps w, w + 4, w + 8, w + 12 own rows 32(w % 4) .. +31 and take 16-column pieces in turn ----
   // The FP32 residual stream (y_l forward, gy_l backward) stays in tensor-memory columns
   // [256, 512) of the thread's row, which the chain phases leave free.
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, part = warp >> 2;
   const int rl = quad * 32 + lane;
   const long row = row0 + rl;
   const bool rv = row < row_end;
@@ -321,19 +324,19 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     float e_acc = 0.f;
     // the accumulator (and residual) pieces load one ahead of the piece being processed
     uint32_t na[16], ny[16];
-    tmem_ld16_async(tq + half * 16, na);
-    if (sk) tmem_ld16_async(tq + 256 + half * 16, ny);
+    tmem_ld16_async(tq + part * 16, na);
+    if (sk) tmem_ld16_async(tq + 256 + part * 16, ny);
     tmem_wait_ld();
-    for (int c = half * 16; c < kSLd; c += 32) {  // zeros beyond N: the next A operand's K padding
+    for (int c = part * 16; c < kSLd; c += kStep) {  // zeros beyond N: the next A operand's K padding
       uint32_t ra[16], ry[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         ra[i] = na[i];
         ry[i] = ny[i];
       }
-      if (c + 32 < kSLd) {
-        tmem_ld16_async(tq + c + 32, na);
-        if (sk) tmem_ld16_async(tq + 256 + c + 32, ny);
+      if (c + kStep < kSLd) {
+        tmem_ld16_async(tq + c + kStep, na);
+        if (sk) tmem_ld16_async(tq + 256 + c + kStep, ny);
       }
       float out[16], y[16], gt[16];
 #pragma unroll
@@ -360,9 +363,14 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
       }
     }
     if (last) {
-      s_e[half * SBM + rl] = e_acc;
+      s_e[part * SBM + rl] = e_acc;
       bar_sync(1, kSEpi);
-      if (half == 0 && rv) g.atom_e[g.perm[row]] = (double)(s_e[rl] + s_e[SBM + rl] + g.b_last[t]);
+      if (part == 0 && rv) {
+        float e = 0.f;
+#pragma unroll
+        for (int q = 0; q < kParts; ++q) e += s_e[q * SBM + rl];
+        g.atom_e[g.perm[row]] = (double)(e + g.b_last[t]);
+      }
     }
     flush_x(xb);
     release(0, !last);
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
   for (int l = nh - 1; l >= 1; --l) {
     const int N = g.width[l];
     if (rv)  // this row's gates towards L1 while the GEMM of this phase runs
-      for (int c = half * 16; c < N; c += 32)
+      for (int c = part * 16; c < N; c += kStep)
 #pragma unroll
         for (int q = 0; q < 4; ++q) prefetch_l1(gate_at(l - 1, c + 4 * q));
     wait_acc(0);
@@ -380,19 +388,19 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     const int xb = p & 1;
     const bool ldy = sk && !top;
     uint32_t na[16], ny[16];
-    tmem_ld16_async(tq + half * 16, na);
-    if (ldy) tmem_ld16_async(tq + 256 + half * 16, ny);
+    tmem_ld16_async(tq + part * 16, na);
+    if (ldy) tmem_ld16_async(tq + 256 + part * 16, ny);
     tmem_wait_ld();
-    for (int c = half * 16; c < kSLd; c += 32) {  // zeros beyond N: the next A operand's K padding
+    for (int c = part * 16; c < kSLd; c += kStep) {  // zeros beyond N: the next A operand's K padding
       uint32_t ra[16], ry[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         ra[i] = na[i];
         ry[i] = ny[i];
       }
-      if (c + 32 < kSLd) {
-        tmem_ld16_async(tq + c + 32, na);
-        if (ldy) tmem_ld16_async(tq + 256 + c + 32, ny);
+      if (c + kStep < kSLd) {
+        tmem_ld16_async(tq + c + kStep, na);
+        if (ldy) tmem_ld16_async(tq + 256 + c + kStep, ny);
       }
       float gt[16];
       if (rv && c < N) {
@@ -426,15 +434,15 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     float* dst = g.gD + row * KD + 256 * c;
     const uint32_t tb = tq + (uint32_t)(buf * 256);
     uint32_t nv[16];
-    if (half * 16 < N) {
-      tmem_ld16_async(tb + half * 16, nv);
+    if (part * 16 < N) {
+      tmem_ld16_async(tb + part * 16, nv);
       tmem_wait_ld();
     }
-    for (int q = half * 16; q < N; q += 32) {
+    for (int q = part * 16; q < N; q += kStep) {
       float v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(nv[i]);
-      if (q + 32 < N) tmem_ld16_async(tb + q + 32, nv);
+      if (q + kStep < N) tmem_ld16_async(tb + q + kStep, nv);
       if (rv) {
         st_v8(dst + q, v);
         st_v8(dst + q + 8, v + 8);
@@ -447,10 +455,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) tmem_dealloc(tmem, 512);
+  if (warp == kProd) tmem_dealloc(tmem, 512);
 }
 
-size_t split_smem() { return (size_t)kSRing * kSStage + 16 * 8 + 16 + (2 * SBM + kSL * 256 + 256) * 4 + 1024; }
+size_t split_smem() { return (size_t)kSRing * kSStage + 16 * 8 + 16 + (kParts * SBM + kSL * 256 + 256) * 4 + 1024; }
 
 }  // namespace
 
