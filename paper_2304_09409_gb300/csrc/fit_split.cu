@@ -18,6 +18,7 @@
 // is bounded (on time-out the CTA records an error and finishes).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "fit_tc.cuh"
@@ -31,7 +32,7 @@ namespace {
 using namespace ptx;
 
 constexpr int kSL = 4;  // hidden layers at most
-constexpr int kSEpi = 512;               // sixteen epilogue warps: four per 32-row quarter of the tile
+constexpr int kSEpi = 256;               // eight epilogue warps: two per 32-row quarter of the tile
 constexpr int kSThreads = kSEpi + 64;    // + a TMA producer warp and an MMA warp
 constexpr int kProd = kSEpi / 32, kMmaW = kProd + 1;  // their warp indices
 constexpr int kParts = kSEpi / 128;      // epilogue warps sharing a row quarter, interleaved by 16 columns
@@ -63,7 +64,13 @@ struct SplitArgs {
   float* gate;              // 1 - t_l^2 of the inner hidden layers [nh][rows][kSLd]
   const int* perm;
   double* atom_e;
-  float* gD;                // dE/dD FP32 [rows][KD]
+  float* gD;                // dE/dD FP32 [rows][KD], or null when gT is formed instead
+  // dE/dT of the se_e2_a contraction (M_< = 16), formed from each dE/dD chunk in the epilogue:
+  // gT[m][c] = sum_l gD[m][l] T[l][c] + [m < 16] sum_q gD[q][m] T[q][c], stored m-major
+  // [M][rows][4] FP32 (consecutive rows of one m are contiguous)
+  float* gT;
+  const float* Tm;          // T [rows][M][4] FP32
+  int M;
   int* err;
 };
 
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
       }
     }
   } else {
-  // ---- epilogues: warps w, w + 4, w + 8, w + 12 own rows 32(w % 4) .. +31 and take 16-column pieces in turn ----
+  // ---- epilogues: warps w and w + 4 own rows 32(w % 4) .. +31 and take 16-column pieces in turn ----
   // The FP32 residual stream (y_l forward, gy_l backward) stays in tensor-memory columns
   // [256, 512) of the thread's row, which the chain phases leave free.
   const int quad = warp & 3, part = warp >> 2;
@@ -426,31 +433,83 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     flush_x(xb);
     release(0, keep);
   }
-  // dE/dD in 256-column chunks from the two alternating accumulators
+  // dE/dD in 256-column chunks from the two alternating accumulators: stored, or (gT mode, 16-column
+  // pieces = one m) folded at once into dE/dT, term 1 per piece and term 2 accumulated per row
+  const bool gtm = g.gT != nullptr;
+  float ext[16][4];
+#pragma unroll
+  for (int l = 0; l < 16; ++l)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ext[l][q] = 0.f;
+  // T_< of the tile's rows in shared memory over the forward's dead biases and energies: row rl's
+  // float4 l at rl * 16 + (l ^ (rl % 8)), so that the 32 rows of a warp read without conflicts
+  float4* s_tl = reinterpret_cast<float4*>(s_e);
+  if (gtm) {
+    for (int e = threadIdx.x; e < SBM * 16; e += kSEpi) {
+      const int r = e >> 4, l = e & 15;
+      const long rr = row0 + r;
+      s_tl[r * 16 + (l ^ (r & 7))] = rr < row_end ? __ldg(reinterpret_cast<const float4*>(g.Tm + (rr * g.M + l) * 4))
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    bar_sync(1, kSEpi);
+  }
   for (int c = 0; c < nch; ++c) {
     const int buf = c & 1;
     wait_acc(buf);
     const int N = min(256, KD - 256 * c);
-    float* dst = g.gD + row * KD + 256 * c;
+    float* dst = gtm ? nullptr : g.gD + row * KD + 256 * c;
     const uint32_t tb = tq + (uint32_t)(buf * 256);
-    uint32_t nv[16];
-    if (part * 16 < N) {
-      tmem_ld16_async(tb + part * 16, nv);
-      tmem_wait_ld();
-    }
     for (int q = part * 16; q < N; q += kStep) {
       float v[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(nv[i]);
-      if (q + kStep < N) tmem_ld16_async(tb + q + kStep, nv);
+      tmem_ld16(tb + q, v);
       if (rv) {
-        st_v8(dst + q, v);
-        st_v8(dst + q + 8, v + 8);
+        if (gtm) {
+          const int m = (256 * c + q) >> 4;
+          const float4 tm = __ldg(reinterpret_cast<const float4*>(g.Tm + (row * g.M + m) * 4));
+          float t1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int l = 0; l < 16; ++l) {
+            const float4 tl = s_tl[rl * 16 + (l ^ (rl & 7))];
+            t1[0] += v[l] * tl.x;
+            t1[1] += v[l] * tl.y;
+            t1[2] += v[l] * tl.z;
+            t1[3] += v[l] * tl.w;
+            ext[l][0] += v[l] * tm.x;
+            ext[l][1] += v[l] * tm.y;
+            ext[l][2] += v[l] * tm.z;
+            ext[l][3] += v[l] * tm.w;
+          }
+          reinterpret_cast<float4*>(g.gT)[(long)m * rows + row] = make_float4(t1[0], t1[1], t1[2], t1[3]);
+        } else {
+          st_v8(dst + q, v);
+          st_v8(dst + q + 8, v + 8);
+        }
       }
-      tmem_wait_ld();
     }
     tc_fence_before();
     mbar_arrive(&accfree[buf]);
+  }
+  if (gtm) {
+    // term 2 of the rows' first 16 m: the parts' partial sums meet in the idle ring (every load and
+    // MMA of the tile completed before the last chunk's accumulator became ready)
+    float* s_ext = reinterpret_cast<float*>(smem);  // [kParts][128][64]
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+      *reinterpret_cast<float4*>(s_ext + ((part * SBM) + rl) * 64 + l * 4) =
+          make_float4(ext[l][0], ext[l][1], ext[l][2], ext[l][3]);
+    bar_sync(1, kSEpi);
+    if (rv)
+      for (int l = part; l < 16; l += kParts) {
+        float4 a = reinterpret_cast<float4*>(g.gT)[(long)l * rows + row];
+        for (int pp = 0; pp < kParts; ++pp) {
+          const float4 e = *reinterpret_cast<const float4*>(s_ext + ((pp * SBM) + rl) * 64 + l * 4);
+          a.x += e.x;
+          a.y += e.y;
+          a.z += e.z;
+          a.w += e.w;
+        }
+        reinterpret_cast<float4*>(g.gT)[(long)l * rows + row] = a;
+      }
   }
   }
   tc_fence_before();
@@ -458,7 +517,11 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
   if (warp == kProd) tmem_dealloc(tmem, 512);
 }
 
-size_t split_smem() { return (size_t)kSRing * kSStage + 16 * 8 + 16 + (kParts * SBM + kSL * 256 + 256) * 4 + 1024; }
+// ring, barriers, then either the forward's energies, biases and output weights or (dE/dT mode) T_< rows
+size_t split_smem() {
+  const size_t tail = std::max<size_t>((kParts * SBM + kSL * 256 + 256) * 4, (size_t)SBM * 16 * 16);
+  return (size_t)kSRing * kSStage + 16 * 8 + 16 + tail + 1024;
+}
 
 }  // namespace
 
@@ -478,14 +541,16 @@ bool fit_split_supported(const DeviceModel& m) {
 }
 
 int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dhi, const __nv_bfloat16* Dlo,
-                      const PathIO& io, Arena& ar, cudaStream_t st, const float** gD_out) {
+                      const PathIO& io, Arena& ar, cudaStream_t st, const float** gD_out, const float* Tm,
+                      float* gT) {
   const long N = pc.natoms;
   const int nfl = m.n_fit_layers, nh = nfl - 1;
   const int nt = pc.ntypes;
   const int KD = pc.M * pc.A;
+  const bool gtm = gT != nullptr && Tm != nullptr && pc.A == 16;
   __nv_bfloat16* xs = ar.get<__nv_bfloat16>(4 * N * kSLd);
   float* gate = ar.get<float>((long)nh * N * kSLd);
-  float* gD = ar.get<float>(N * KD);
+  float* gD = gtm ? nullptr : ar.get<float>(N * KD);
   if (ar.measure) return DP_OK;
   if (!ar.ok()) {
     set_error("scratch allocation failed");
@@ -542,6 +607,9 @@ int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bflo
   a.perm = io.perm;
   a.atom_e = io.atom_energy;
   a.gD = gD;
+  a.gT = gtm ? gT : nullptr;
+  a.Tm = Tm;
+  a.M = pc.M;
   a.err = &io.status->timeout;
   if (tiles > 0) {
     ProfScope _ps(io.prof, "fit_split_tc", st);

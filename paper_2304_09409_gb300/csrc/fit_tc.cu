@@ -125,7 +125,8 @@ int prepare_fit_bf16(DeviceModel& m, const double* params_host, bool split) {
 }
 
 int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io, Arena& ar,
-                   cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out, const __nv_bfloat16* Dlo) {
+                   cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out, const __nv_bfloat16* Dlo,
+                   const float* Tm, float* gT) {
   const bool split = Dlo != nullptr;
   if (!split && gDh_out && fit_fused_supported(m)) {  // the whole net in one kernel per tile
     *gD_out = nullptr;
@@ -136,7 +137,7 @@ int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat1
   if (split && fit_split_supported(m)) {
     long tiles = 0;
     for (int t = 0; t < pc.ntypes; ++t) tiles += (io.type_start[t + 1] - io.type_start[t] + 127) / 128;
-    if (2 * tiles >= sm_count()) return run_fitting_split(m, pc, Dbf, Dlo, io, ar, st, gD_out);
+    if (2 * tiles >= sm_count()) return run_fitting_split(m, pc, Dbf, Dlo, io, ar, st, gD_out, Tm, gT);
   }
   if (split) gDh_out = nullptr;  // split operands: dE/dD in FP32
   const long N = pc.natoms;

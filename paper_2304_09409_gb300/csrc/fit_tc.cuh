@@ -28,10 +28,13 @@ int run_fitting_fused(const DeviceModel& m, const PathConst& pc, const __nv_bflo
 
 // The whole FP32-mode fitting net in one kernel per 128-atom tile on split BF16 operands (three
 // passes), for nets of at most four hidden layers of width <= 256 (multiples of 16) with skips of
-// kind 0 or 1; Dhi / Dlo the descriptor's high and low halves; dE/dD FP32 [rows][KD].
+// kind 0 or 1; Dhi / Dlo the descriptor's high and low halves; dE/dD FP32 [rows][KD].  With Tm
+// (T [rows][M][4]) and gT given and M_< = 16, dE/dD is not stored: the kernel forms dE/dT of the
+// se_e2_a contraction into gT (m-major [M][rows][4]) and *gD_out is set to null.
 bool fit_split_supported(const DeviceModel& m);
 int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dhi, const __nv_bfloat16* Dlo,
-                      const PathIO& io, Arena& ar, cudaStream_t st, const float** gD_out);
+                      const PathIO& io, Arena& ar, cudaStream_t st, const float** gD_out, const float* Tm = nullptr,
+                      float* gT = nullptr);
 
 // dE/dD of every atom: FP32 [rows][KD] into *gD_out, or BF16 into *gDh_out when that is given.
 // With Dlo (the low halves of the descriptor, FP32 mode) every GEMM runs on split operands
@@ -40,8 +43,10 @@ int run_fitting_split(const DeviceModel& m, const PathConst& pc, const __nv_bflo
 // row; tile rows [row0, row0 + nr) occupy [row0 * KD, (row0 + nr) * KD) and element (row0 + r, col)
 // sits at ((col / 8) * nr + r) * 8 + col % 8 within it (8-column groups, rows contiguous), so
 // thread-per-row epilogues write whole 512-byte runs per warp.
+// Tm / gT as for run_fitting_split: used when the split kernel runs (then *gD_out is null and gT holds
+// dE/dT), ignored otherwise.
 int run_fitting_tc(const DeviceModel& m, const PathConst& pc, const __nv_bfloat16* Dbf, const PathIO& io, Arena& ar,
                    cudaStream_t st, const float** gD_out, const __nv_bfloat16** gDh_out = nullptr,
-                   const __nv_bfloat16* Dlo = nullptr);
+                   const __nv_bfloat16* Dlo = nullptr, const float* Tm = nullptr, float* gT = nullptr);
 
 }  // namespace dpgb

@@ -94,6 +94,9 @@ struct MomArgs {
   double* avir;     // [N][9] input order
   unsigned char* gta;  // backward A operand per tile: the shared-memory image of dE/dT rows
   int* gtx;            // its row scales [tiles][128]
+  // or, FP32 mode with the split fitting kernel, dE/dT itself, m-major [M][N][4] FP32: the backward
+  // kernel then forms its A operand image in its prologue (no k_mom_gT)
+  const float* gTt;
   int* table_range;
   int* err;
   unsigned int* mma_blocks;  // [2] blocks issued by the forward / backward MMA threads (work count)
@@ -924,7 +927,7 @@ __global__ void __launch_bounds__(kMomThreads, 1)
       mbar_init(&bfull[s], 1);
       mbar_init(&bempty[s], 1);
     }
-    mbar_init(afull, 1);
+    mbar_init(afull, g.gTt ? kRows : 1);
     for (int b = 0; b < kAccBufs; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], kRows);
@@ -971,10 +974,12 @@ __global__ void __launch_bounds__(kMomThreads, 1)
     }
   } else if (warp == 4) {
     if (lane == 0) {
-      // ---- the A operand of this tile and its row scales ----
-      mbar_expect_tx(afull, PARTS * A_BYTES + kRows * 4);
-      bulk_load(As, g.gta + (long)blockIdx.x * PARTS * A_BYTES, PARTS * A_BYTES, afull);
-      bulk_load(ex_s, g.gtx + (long)blockIdx.x * kRows, kRows * 4, afull);
+      // ---- the A operand of this tile and its row scales (copied, or formed by the builder warps) ----
+      if (!g.gTt) {
+        mbar_expect_tx(afull, PARTS * A_BYTES + kRows * 4);
+        bulk_load(As, g.gta + (long)blockIdx.x * PARTS * A_BYTES, PARTS * A_BYTES, afull);
+        bulk_load(ex_s, g.gtx + (long)blockIdx.x * kRows, kRows * 4, afull);
+      }
       bool ok = mbar_wait(afull, 0, g.err);
       // ---- MMA issuer ----
       const uint32_t idesc = idesc_f16(kRows, 64, NPASS == 1 ? 0 : 1);
@@ -1010,6 +1015,32 @@ __global__ void __launch_bounds__(kMomThreads, 1)
       if (ok && nch > 0) atomicAdd(&g.mma_blocks[1], (unsigned)nch);
     }
   } else {
+    if constexpr (NPASS == 3) if (g.gTt) {
+      // row r = (atom ae, component c) of the A operand: dE/dT[m][c] for m < M (zero to NPAD),
+      // scaled by a power of two to its largest magnitude, in the swizzled K-major image
+      const bool va = pe < row_end;
+      const long stride = (long)g.row_start[g.ntypes] * 4;  // one m of every row
+      const float* src = g.gTt + (long)pe * 4 + c;
+      float v[NPAD];  // every load in flight at once (for one m the warp reads 8 rows x 16 B, contiguous)
+#pragma unroll
+      for (int m = 0; m < NPAD; ++m) v[m] = (va && m < g.M) ? __ldg(src + m * stride) : 0.f;
+      float mx = 0.f;
+#pragma unroll
+      for (int m = 0; m < NPAD; ++m) mx = fmaxf(mx, fabsf(v[m]));
+      int ex = 0;
+      if (mx > 0.f) frexpf(mx, &ex);
+#pragma unroll
+      for (int qq = 0; qq < NPAD / 8; ++qq) {
+        float w[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) w[e] = ldexpf(v[8 * qq + e], -ex);
+        const uint32_t off = (uint32_t)((qq >> 3) * kABlock) + sw_off(r, qq & 7);
+        store_chunk<NPASS>(As + off, As + A_BYTES + off, w);
+      }
+      ex_s[r] = ex;
+      fence_async_smem();
+      mbar_arrive(afull);
+    }
     mbar_wait(afull, 0, g.err);  // the row scales arrived with the A operand
     const float pscale = ldexpf(g.inv_nc, ex_s[r]);
     int cur_t = -1, ptr = 0, selt = 0;
@@ -1341,12 +1372,15 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   const long max_tiles = (N + kAtoms - 1) / kAtoms + pc.ntypes;  // every type's last tile may be short
   unsigned char* gta = ar.get<unsigned char>(max_tiles * (bf16 ? 1 : 2) * 2 * kABlock);
   int* gtx = ar.get<int>(max_tiles * kRows);
+  // FP32 mode: dE/dT straight from the split fitting kernel when it runs (M_< = 16)
+  float* gTt = split_fit && A == 16 ? ar.get<float>(N * M * 4) : nullptr;
   const float* gD = nullptr;
   const __nv_bfloat16* gDh = nullptr;
   if (ar.measure) {
     if (bf16) return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, &gDh);
     if (split_fit)
-      return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, nullptr, D_lo);
+      return run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, nullptr, D_lo, Tm,
+                            gTt);
     return run_fitting<float>(m, pc, m.p32, reinterpret_cast<const float*>(D), io, ar, st, &gD);
   }
   if (!ar.ok()) {
@@ -1427,14 +1461,15 @@ int run_mom(const DeviceModel& m, const PathConst& pc, const PathIO& io, Arena& 
   if (bf16)
     rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, &gDh);
   else if (split_fit)
-    rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, nullptr, D_lo);
+    rc = run_fitting_tc(m, pc, reinterpret_cast<const __nv_bfloat16*>(D), io, ar, st, &gD, nullptr, D_lo, Tm, gTt);
   else
     rc = run_fitting<float>(m, pc, m.p32, reinterpret_cast<const float*>(D), io, ar, st, &gD);
   if (rc != DP_OK) return rc;
   g.gD = gD;
   g.gDh = gDh;
+  g.gTt = (split_fit && gD == nullptr) ? gTt : nullptr;  // the split kernel formed dE/dT itself
   if (tiles > 0) {
-    {
+    if (!g.gTt) {
       ProfScope _ps(io.prof, "mom_gT", st);
       rc = bf16 ? launch_mom_np<1>(m, g, tiles, 1, st) : launch_mom_np<3>(m, g, tiles, 1, st);
       if (rc != DP_OK) return rc;
