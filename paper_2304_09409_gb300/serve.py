@@ -229,13 +229,23 @@ class Server:
                 self.completed.extend(batch)
                 self.batches.append((len(batch), N, t_end - t_start, len(set(fmodel.tolist()))))
 
-    def run(self, requests: List[Request], realtime: bool = True) -> dict:
-        """Replay `requests` (arrival times in seconds) and serve them; returns statistics."""
+    def run(self, requests: List[Request], realtime: bool = True, prefill: bool = False) -> dict:
+        """Replay `requests` (arrival times in seconds) and serve them; returns statistics.
+
+        prefill: every request arrives (and is uploaded) before the slots start, all at time 0 --
+        the operating point of a queue that never runs dry, whose throughput is the capacity of
+        the GPU path rather than of the submitting thread."""
         threads = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(self.slots)]
+        if prefill:
+            for r in sorted(requests, key=lambda r: r.arrival):
+                r.arrival = 0.0
+                self.submit(r)
+            if self.upload is not None:
+                self.upload.synchronize()
         self.t0 = time.perf_counter()
         for t in threads:
             t.start()
-        for r in sorted(requests, key=lambda r: r.arrival):
+        for r in ([] if prefill else sorted(requests, key=lambda r: r.arrival)):
             if realtime:
                 delay = r.arrival - (time.perf_counter() - self.t0)
                 if delay > 0:
