@@ -101,3 +101,17 @@ def test_poisson_stream_is_seeded_and_has_the_requested_rate():
     assert (t[-1] / len(t)) == pytest.approx(1 / 2000.0, rel=0.05)  # mean gap 1/rate
     frac_water = np.mean([r.model == "water" for r in a])
     assert frac_water == pytest.approx(0.5, abs=0.03)
+
+
+def test_prefill_queues_every_request_at_time_zero_in_arrival_order():
+    """The capacity operating point: every request is queued (arrival 0) before a slot starts, in
+    arrival order, and the first batch takes the oldest ones up to the budget."""
+    srv = _server(max_batch_atoms=1000)
+    srv._worker = lambda slot: None  # no device work: only the queue is examined
+    reqs = [_req(0, "water", 300, 0.30), _req(1, "metal", 500, 0.05), _req(2, "water", 400, 0.20)]
+    srv.stats = lambda wall: {}
+    srv.run(reqs, prefill=True)
+    assert [r.rid for r in srv.queue] == [1, 2, 0]
+    assert all(r.arrival == 0.0 for r in reqs)
+    srv.closed = False
+    assert [r.rid for r in srv._take()] == [1, 2]

@@ -47,6 +47,26 @@ def test_noalloc_nlist_equals_allocating_entry_point_on_two_calls():
         assert gov == rov
 
 
+def test_noalloc_on_dense_fcc_and_hybrid_lists():
+    """The per-atom kernel this entry point always runs against the cell-centred kernel the
+    allocating entry point prefers, on a dense FCC frame (sel [512], lattice shells whose FP32
+    keys fall inside the tie window) and on a hybrid model's list (the larger cutoff and sel of
+    its two parts)."""
+    from paper_2304_09409_gb300 import dpgb
+    cases = [(I.metal_model(), I.fcc_frame((6, 6, 6), seed=3)),                   # 864 atoms
+             (I.water_model_hybrid(), I.replicate(I.water_frame(0), (2, 2, 2)))]  # r_c 4 + 6
+    for cfg, fr in cases:
+        rj, rs, rov = _reference(cfg, fr)
+        assert rj.shape[1] == cfg.nc
+        c = torch.tensor(fr.coord, device="cuda")
+        t = torch.tensor(fr.atype, device="cuda")
+        gj, gs, gov = dpgb.build_nlist_noalloc(cfg, c, t, fr.box)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(gj.cpu().numpy(), rj)
+        np.testing.assert_array_equal(gs.cpu().numpy(), rs)
+        assert gov == rov
+
+
 def test_noalloc_rejects_frames_beyond_its_limit():
     from paper_2304_09409_gb300 import dpgb
     cfg = I.water_model()
