@@ -89,10 +89,17 @@ __device__ __forceinline__ void ld_v8(const float* p, float* v) {
 
 // tanh from the exponential, tanh x = 1 - 2 / (1 + e^{2x}) (x clamped to +-15, where tanh is 1 to
 // FP32): absolute error a few 1e-7, below the ~2^-17 relative rounding the next GEMM's split
-// operands apply anyway.
+// operands apply anyway.  Only the exponential goes to the special-function unit, the epilogues'
+// narrowest pipe: 1/d comes from the bit pattern of d (first guess within 5.1 %, the constant
+// fitted to the mantissa range [1, 2)) and three Newton steps y <- y (2 - d y) on the FMA pipe.
 __device__ __forceinline__ float tanh_ex(float x) {
   const float e = __expf(2.f * fminf(fmaxf(x, -15.f), 15.f));
-  return 1.f - __fdividef(2.f, 1.f + e);
+  const float d = 1.f + e;  // [1, 1 + e^30]: a normal number
+  float y = __int_as_float(0x7EF311C0 - __float_as_int(d));
+  y = y * (2.f - d * y);
+  y = y * (2.f - d * y);
+  y = y * (2.f - d * y);
+  return 1.f - 2.f * y;
 }
 
 __device__ __forceinline__ void split2(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -304,16 +311,23 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     *reinterpret_cast<uint4*>(bl + ((j ^ (rl & 7)) << 4)) = *reinterpret_cast<const uint4*>(lo);
     *reinterpret_cast<uint4*>(bl + (((j + 1) ^ (rl & 7)) << 4)) = *reinterpret_cast<const uint4*>(lo + 8);
   };
-  // the staged operand to scratch buffer xb: eight TMA stores, complete before the phase is released
-  auto flush_x = [&](int xb) {
+  // the staged operand to scratch buffer xb, one 64-column block at a time: after its second pieces
+  // of block kb (loop iteration k odd) every thread has staged its part of the block, and one
+  // thread starts the block's two TMA stores while the epilogue goes on; all complete before the
+  // phase is released
+  auto store_block = [&](int k, int xb) {
+    if (!(k & 1)) return;
+    const int kb = k >> 1;
     fence_async_smem();
     bar_sync(1, kSEpi);
     if (threadIdx.x == 0) {
-      for (int kb = 0; kb < kSLd / 64; ++kb)
-        for (int hl = 0; hl < 2; ++hl) tma_store_2d(&mp.xt[t][xb][hl], smem + (2 * kb + hl) * kSA, kb * 64, row0 - g.row_start[t]);
+      for (int hl = 0; hl < 2; ++hl)
+        tma_store_2d(&mp.xt[t][xb][hl], smem + (2 * kb + hl) * kSA, kb * 64, row0 - g.row_start[t]);
       bulk_commit();
-      bulk_wait0();
     }
+  };
+  auto flush_wait = [&]() {
+    if (threadIdx.x == 0) bulk_wait0();
   };
   // biases and output weights of this tile's type into shared memory
   for (int l = 0; l < nh; ++l)
@@ -334,7 +348,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     tmem_ld16_async(tq + part * 16, na);
     if (sk) tmem_ld16_async(tq + 256 + part * 16, ny);
     tmem_wait_ld();
-    for (int c = part * 16; c < kSLd; c += kStep) {  // zeros beyond N: the next A operand's K padding
+    for (int c = part * 16, k = 0; c < kSLd; c += kStep, ++k) {  // zeros beyond N: the next A operand's K padding
       uint32_t ra[16], ry[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -346,28 +360,33 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
         if (sk) tmem_ld16_async(tq + 256 + c + kStep, ny);
       }
       float out[16], y[16], gt[16];
+      if (c < N) {  // widths are multiples of 16: a piece is all real columns or all padding
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = c + i;
-        const float th = col < N ? tanh_ex(__uint_as_float(ra[i]) + bias[col]) : 0.f;
-        y[i] = th + (sk && col < N ? __uint_as_float(ry[i]) : 0.f);
-        gt[i] = 1.f - th * th;
-        if (last) {
-          const float w = s_wl[col];
-          e_acc += y[i] * w;
-          out[i] = w * gt[i];
-        } else {
-          out[i] = y[i];
+        for (int i = 0; i < 16; ++i) {
+          const int col = c + i;
+          const float th = tanh_ex(__uint_as_float(ra[i]) + bias[col]);
+          y[i] = th + (sk ? __uint_as_float(ry[i]) : 0.f);
+          gt[i] = 1.f - th * th;
+          if (last) {
+            const float w = s_wl[col];
+            e_acc += y[i] * w;
+            out[i] = w * gt[i];
+          } else {
+            out[i] = y[i];
+          }
         }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out[i] = y[i] = gt[i] = 0.f;
       }
       tmem_wait_ld();                          // the next piece has landed
       if (!last) tmem_st16(tq + 256 + c, y);  // the residual stream of the next layer
       put_x(c, out);
-      if (!rv) continue;
-      if (!last && c < N) {
+      if (rv && !last && c < N) {
         st_v8(gate_at(l, c), gt);
         st_v8(gate_at(l, c + 8), gt + 8);
       }
+      store_block(k, xb);
     }
     if (last) {
       s_e[part * SBM + rl] = e_acc;
@@ -379,7 +398,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
         g.atom_e[g.perm[row]] = (double)(e + g.b_last[t]);
       }
     }
-    flush_x(xb);
+    flush_wait();
     release(0, !last);
   }
   // backward of layers nh-1 .. 1: gz_{l-1} into the scratch, gy_{l-1} kept for the next skip
@@ -398,7 +417,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
     tmem_ld16_async(tq + part * 16, na);
     if (ldy) tmem_ld16_async(tq + 256 + part * 16, ny);
     tmem_wait_ld();
-    for (int c = part * 16; c < kSLd; c += kStep) {  // zeros beyond N: the next A operand's K padding
+    for (int c = part * 16, k = 0; c < kSLd; c += kStep, ++k) {  // zeros beyond N: the next A operand's K padding
       uint32_t ra[16], ry[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -429,8 +448,9 @@ __global__ void __launch_bounds__(kSThreads, 1) k_fit_split(const __grid_constan
       tmem_wait_ld();
       if (keep) tmem_st16(tq + 256 + c, gy);
       put_x(c, gz);
+      store_block(k, xb);
     }
-    flush_x(xb);
+    flush_wait();
     release(0, keep);
   }
   // dE/dD in 256-column chunks from the two alternating accumulators: stored, or (gT mode, 16-column
