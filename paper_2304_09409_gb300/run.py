@@ -3,7 +3,9 @@
   python -m paper_2304_09409_gb300.run --workload water12288 --path fp32-compressed --steps 5
 
 Workloads: water192 (the 192-atom water frame), water12288 (it tiled 4x4x4), water1536
-(tiled 2x2x2), fcc32000 (Cu-like FCC, 20^3 cells), fcc4000 (10^3 cells).  Paths: fp64,
+(tiled 2x2x2), fcc32000 (Cu-like FCC, 20^3 cells), fcc4000 (10^3 cells); a water workload with the
+suffix -r, -hybrid, -e3 or -hybrid_e3 takes the se_e2_r, se_e2_a + se_e2_r, se_e3 or
+se_e2_a + se_e3 model of the inputs module instead.  Paths: fp64,
 fp32, tf32, bf16 (network GEMMs on the tensor cores), fp32-compressed, fp64-compressed, bf16-compressed.  Inputs live on the device; each step is one full
 dp_compute (neighbour list included).  Prints the mean device time per step.
 """
@@ -19,9 +21,11 @@ import numpy as np
 def workload(name: str):
     from . import inputs as I
     if name.startswith("water"):
-        cfg = I.water_model()
+        base, _, desc = name.partition("-")
+        cfg = {"": I.water_model, "r": I.water_model_r, "hybrid": I.water_model_hybrid, "e3": I.water_model_e3,
+               "hybrid_e3": I.water_model_hybrid_e3}[desc]()
         fr = I.water_frame(0)
-        reps = {"water192": 1, "water1536": 2, "water12288": 4, "water98304": 8}[name]
+        reps = {"water192": 1, "water1536": 2, "water12288": 4, "water98304": 8}[base]
         if reps > 1:
             fr = I.replicate(fr, (reps, reps, reps))
     elif name.startswith("fcc"):
@@ -48,6 +52,8 @@ SCOPES = {
     "fit_split_tc": (("k_fit_split",), ("fit_split.cu", "fit_tc.cuh", "tc_ptx.cuh", "dp_internal.cuh")),
     "fit_fused_tc": (("k_fit_fused",), ("fit_fused.cu", "fit_tc.cuh", "tc_ptx.cuh", "dp_internal.cuh")),
     "frame_sums": (("k_chunk_sums", "k_frame_sums"), ("driver.cu",)),
+    "e3_fwd": (("k_e3",), ("path.cu", "path.cuh", "env.cuh", "tabeval.cuh", "dp_internal.cuh")),
+    "e3_bwd": (("k_e3",), ("path.cu", "path.cuh", "env.cuh", "tabeval.cuh", "dp_internal.cuh")),
 }
 
 
