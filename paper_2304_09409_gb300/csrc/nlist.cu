@@ -551,9 +551,58 @@ __global__ void __launch_bounds__(kNlWarps * 32)
 constexpr int kCellWarps = 8;
 constexpr int kMaxRanges = 256;  // (type, surrounding cell) ranges of one cell
 
-// Dynamic shared memory: S staged candidates (24 bytes each) and one entry buffer per warp.
+// Dynamic shared memory: S staged candidates (24 bytes each) and per warp an entry buffer of
+// cap + 4 entries (FP32 key, 16-bit stream position, 16-bit entry index in bucket order) and
+// cap bucket counters (the FP32 keys of one type group are bucketed over [0, r_c^2 + eps], as
+// many buckets as the buffer has entries).
 __host__ __device__ constexpr size_t cell_smem_bytes(int cap, int S) {
-  return (size_t)S * 24 + (size_t)kCellWarps * (size_t)(cap + 4) * 8;
+  return (size_t)S * 24 + (size_t)kCellWarps * ((size_t)(cap + 4) * 8 + (size_t)cap * 4);
+}
+
+// Bucket of an FP32 key: monotone in x, so that every key of a lower bucket is smaller and every
+// key of a higher bucket larger.
+template <int NB>
+__device__ __forceinline__ int key_bucket(float x, float inv_w) {
+  return min(NB - 1, max(0, __float2int_rz(x * inv_w)));
+}
+
+// Cell of an orthogonal periodic box (zero off-diagonal entries): the diagonal and its negation.
+struct OrthoCell {
+  bool on;
+  double h[3], nh[3];
+};
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ OrthoCell ortho_cell(const NlGeom& g) {
+  OrthoCell o;
+  o.on = g.periodic && is_zero_bits(g.h[1]) && is_zero_bits(g.h[2]) && is_zero_bits(g.h[3]) &&
+         is_zero_bits(g.h[5]) && is_zero_bits(g.h[6]) && is_zero_bits(g.h[7]);
+  for (int a = 0; a < 3; ++a) {
+    o.h[a] = g.h[4 * a];
+    o.nh[a] = __longlong_as_double(__double_as_longlong(o.h[a]) ^ (long long)0x8000000000000000ull);
+  }
+  return o;
+}
+
+// exact_r2 for the membership test and the ranking, which use only r^2.  In an orthogonal cell
+// with every |n_a| <= 1 the translation component t_a = n_0 h_0a + n_1 h_1a + n_2 h_2a is n_a h_aa
+// plus products with zero entries: -h_aa, a zero or h_aa exactly, taken without a multiplication.
+// Zero terms leave the sums unchanged up to the sign of a zero, which r^2 does not see, so the
+// result is the one of exact_r2 bit for bit.
+__device__ __forceinline__ double exact_r2_rank(const NlGeom& g, const OrthoCell& oc, const double* xi,
+                                                const double* __restrict__ coord, int j, int code) {
+  int n0, n1, n2;
+  unpack_shift(code, n0, n1, n2);
+  if (code != pack_shift(0, 0, 0) && oc.on && abs(n0) <= 1 && abs(n1) <= 1 && abs(n2) <= 1) {
+    const double* xj = coord + 3 * j;
+    const double t0 = n0 == 0 ? 0.0 : (n0 > 0 ? oc.h[0] : oc.nh[0]);
+    const double t1 = n1 == 0 ? 0.0 : (n1 > 0 ? oc.h[1] : oc.nh[1]);
+    const double t2 = n2 == 0 ? 0.0 : (n2 > 0 ? oc.h[2] : oc.nh[2]);
+    const double d0 = __dsub_rn(__dadd_rn(xj[0], t0), xi[0]);
+    const double d1 = __dsub_rn(__dadd_rn(xj[1], t1), xi[1]);
+    const double d2 = __dsub_rn(__dadd_rn(xj[2], t2), xi[2]);
+    return norm2_exact(d0, d1, d2);
+  }
+  return exact_r2(g, xi, coord, j, code);
 }
 
 // W - m_j as three 21-bit two's-complement fields; bit 63 marks a value outside that range.
@@ -594,8 +643,11 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
   __shared__ int s_sel[DP_MAX_TYPES], s_seloff[DP_MAX_TYPES];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-  float* e_key = reinterpret_cast<float*>(smem + (size_t)S * 24 + (size_t)warp * CAPP * 8);  // FP32 r^2
-  int* e_ref = reinterpret_cast<int*>(e_key + CAPP);                                         // stream position
+  constexpr int NB = CAP;  // key buckets
+  float* e_key = reinterpret_cast<float*>(smem + (size_t)S * 24 + (size_t)warp * (CAPP * 8 + NB * 4));
+  unsigned short* e_ref = reinterpret_cast<unsigned short*>(e_key + CAPP);  // stream position (S < 2^16)
+  unsigned short* e_idx = e_ref + CAPP;                                     // entries in bucket order
+  int* e_hist = reinterpret_cast<int*>(e_idx + CAPP);                       // bucket ends
 
   const int gc = blockIdx.x;  // cell, all frames
   int fr = 0;
@@ -731,6 +783,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
   __syncthreads();
 
   const float rc2_in = g.rc2_in, rc2_out = g.rc2_out, tw = g.tie_w;
+  const float inv_bw = (float)NB / rc2_out;
+  const OrthoCell ocell = ortho_cell(g);
   const int nc = g.nc;
   const unsigned lt = (1u << lane) - 1u;
   const float kInf = __int_as_float(0x7f800000);
@@ -768,14 +822,14 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
           const int pos = cnt + __popc(ma & lt);
           if (pos < CAP) {
             e_key[pos] = ra;
-            e_ref[pos] = p;
+            e_ref[pos] = (unsigned short)p;
           }
         }
         if (pb) {
           const int pos = cnt + na + __popc(mb & lt);
           if (pos < CAP) {
             e_key[pos] = rb;
-            e_ref[pos] = p + 32;
+            e_ref[pos] = (unsigned short)(p + 32);
           }
         }
         cnt += na + __popc(mb);
@@ -783,29 +837,81 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
       over |= cnt > CAP;
       const int ge = min(cnt, CAP);
       __syncwarp();
-      // ---- entries within the FP32 error of r_c: the exact FP64 test decides membership ----
+      // ---- bucket order of the surviving FP32 keys ----
+      // Counting sort into NB buckets of the keys' range: counts, exclusive scan, scatter of the
+      // entry indices; afterwards e_hist[b] is the end of bucket b in e_idx.  The counting pass
+      // first settles the entries within the FP32 error of r_c by the exact FP64 test (dropped
+      // entries get the key +inf and no bucket).
+      for (int b = lane; b < NB; b += 32) e_hist[b] = 0;
+      __syncwarp();
       int removed = 0;
       for (int e0 = 0; e0 < ge; e0 += 32) {
         const int e = e0 + lane;
-        const bool need = e < ge && e_key[e] >= rc2_in;
+        float k = e < ge ? e_key[e] : kInf;
+        const bool need = k != kInf && k >= rc2_in;
         if (__ballot_sync(0xffffffffu, need)) {
           bool drop = false;
           if (need) {
             const int p = e_ref[e];
             int code;
             if (staged_code(stg_w[p], mi0, mi1, mi2, code))
-              drop = !(exact_r2(g, xi, coord, __float_as_int(stg[p].w), code) < g.rc2);
+              drop = !(exact_r2_rank(g, ocell, xi, coord, __float_as_int(stg[p].w), code) < g.rc2);
             else
               drop = bad_shift = true;
-            if (drop) e_key[e] = kInf;
+            if (drop) {
+              e_key[e] = kInf;
+              k = kInf;
+            }
           }
           removed += __popc(__ballot_sync(0xffffffffu, drop));
         }
+        if (k != kInf) atomicAdd(&e_hist[key_bucket<NB>(k, inv_bw)], 1);
       }
-      const int ge4 = (ge + 3) & ~3;
-      if (ge + lane < ge4) e_key[ge + lane] = kInf;  // +inf: never smaller, always larger
+      __syncwarp();
+      {
+        constexpr int PER = NB / 32;  // buckets per lane, contiguous
+        int c[PER];
+        int sum = 0;
+#pragma unroll
+        for (int v = 0; v < PER / 4; ++v) {
+          const int4 x = reinterpret_cast<const int4*>(e_hist)[lane * (PER / 4) + v];
+          c[4 * v] = x.x;
+          c[4 * v + 1] = x.y;
+          c[4 * v + 2] = x.z;
+          c[4 * v + 3] = x.w;
+          sum += x.x + x.y + x.z + x.w;
+        }
+        int incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int x = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += x;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int v = 0; v < PER / 4; ++v) {
+          int4 x;
+          x.x = run;
+          run += c[4 * v];
+          x.y = run;
+          run += c[4 * v + 1];
+          x.z = run;
+          run += c[4 * v + 2];
+          x.w = run;
+          run += c[4 * v + 3];
+          reinterpret_cast<int4*>(e_hist)[lane * (PER / 4) + v] = x;
+        }
+      }
+      __syncwarp();
+      for (int e = lane; e < ge; e += 32) {
+        const float k = e_key[e];
+        if (k != kInf) e_idx[atomicAdd(&e_hist[key_bucket<NB>(k, inv_bw)], 1)] = (unsigned short)e;
+      }
       __syncwarp();
       // ---- rank under the exact total order (r^2, j, image code) ----
+      // Entries more than the tie window below an entry's key are certainly smaller: all of the
+      // buckets below the window's lower edge and the smaller keys of the edge bucket.  Entries
+      // inside the window (in bucket order between the two edge buckets) take exact keys.
       const int sel = s_sel[tj];
       const long row = (long)i * nc + s_seloff[tj];
       for (int e0 = 0; e0 < ge; e0 += 32) {
@@ -813,14 +919,27 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
         const float ke = e < ge ? e_key[e] : kInf;
         const bool valid = ke != kInf;
         const float lo_t = ke - tw, hi_t = ke + tw;
-        int lo = 0, hi = 0;  // certainly smaller; certainly larger
-        if (valid)
-#pragma unroll 4
-          for (int f = 0; f < ge4; f += 4) {
-            const float4 k4 = *reinterpret_cast<const float4*>(e_key + f);
-            lo += (k4.x < lo_t) + (k4.y < lo_t) + (k4.z < lo_t) + (k4.w < lo_t);
-            hi += (k4.x > hi_t) + (k4.y > hi_t) + (k4.z > hi_t) + (k4.w > hi_t);
+        int lo = 0, nle = 0;  // keys certainly smaller; keys not certainly larger
+        int wa = 0, wb = 0;   // bucket-order positions spanning the window
+        if (valid) {
+          const int bl = key_bucket<NB>(lo_t, inv_bw), bh = key_bucket<NB>(hi_t, inv_bw);
+          wa = bl ? e_hist[bl - 1] : 0;
+          wb = e_hist[bh];
+          lo = wa;
+          if (bl == bh) {  // the usual case: the window inside one bucket
+            nle = wa;
+            for (int q = wa; q < wb; ++q) {
+              const float kq = e_key[e_idx[q]];
+              lo += kq < lo_t;
+              nle += kq <= hi_t;
+            }
+          } else {
+            for (int q = wa, qe = e_hist[bl]; q < qe; ++q) lo += e_key[e_idx[q]] < lo_t;
+            const int sh = e_hist[bh - 1];
+            nle = sh;
+            for (int q = sh; q < wb; ++q) nle += e_key[e_idx[q]] <= hi_t;
           }
+        }
         int je = 0, ce = 0;
         if (valid) {
           const int p = e_ref[e];
@@ -828,35 +947,43 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
           if (!staged_code(stg_w[p], mi0, mi1, mi2, ce)) bad_shift = true;
         }
         int rank = lo;
-        const bool amb = valid && ge4 - lo - hi > 1;
+        const bool amb = valid && nle - lo > 1;  // the window holds another entry
         unsigned am = __ballot_sync(0xffffffffu, amb);
         if (am) {  // FP32 cannot order some pairs: their exact keys decide
-          const double re = amb ? exact_r2(g, xi, coord, je, ce) : 0.0;
+          const double re = amb ? exact_r2_rank(g, ocell, xi, coord, je, ce) : 0.0;
+          const unsigned am0 = am;
           while (am) {
             const int s = __ffs(am) - 1;
             am &= am - 1;
             const float lo_s = __shfl_sync(0xffffffffu, lo_t, s), hi_s = __shfl_sync(0xffffffffu, hi_t, s);
             const int je_s = __shfl_sync(0xffffffffu, je, s), ce_s = __shfl_sync(0xffffffffu, ce, s);
             const double re_s = __shfl_sync(0xffffffffu, re, s);
+            const int wa_s = __shfl_sync(0xffffffffu, wa, s), wb_s = __shfl_sync(0xffffffffu, wb, s);
             int add = 0;
-            for (int f0 = 0; f0 < ge; f0 += 32) {
-              const int f = f0 + lane;
-              const float kf = f < ge ? e_key[f] : kInf;
-              const bool in = f != e0 + s && kf >= lo_s && kf <= hi_s;
+            for (int q0 = wa_s; q0 < wb_s; q0 += 32) {
+              const int q = q0 + lane;
+              const int f = q < wb_s ? e_idx[q] : -1;
+              const float kf = f >= 0 ? e_key[f] : kInf;
+              const bool in = f >= 0 && f != e0 + s && kf >= lo_s && kf <= hi_s;
+              // a partner that is an ambiguous entry of this pass has its exact key in its lane
+              const int src = (f - e0) & 31;
+              const double r_src = __shfl_sync(0xffffffffu, re, src);
+              const int j_src = __shfl_sync(0xffffffffu, je, src), c_src = __shfl_sync(0xffffffffu, ce, src);
+              const bool known = f >= e0 && f < e0 + 32 && ((am0 >> src) & 1u);
               if (__ballot_sync(0xffffffffu, in)) {
                 bool less = false;
                 if (in) {
                   int jf, cf;
                   double rf;
-                  if (f0 == e0 && amb) {  // the partner is this lane's own entry: its exact key is known
-                    jf = je;
-                    cf = ce;
-                    rf = re;
+                  if (known) {
+                    jf = j_src;
+                    cf = c_src;
+                    rf = r_src;
                   } else {
                     const int p = e_ref[f];
                     jf = __float_as_int(stg[p].w);
                     staged_code(stg_w[p], mi0, mi1, mi2, cf);
-                    rf = exact_r2(g, xi, coord, jf, cf);
+                    rf = exact_r2_rank(g, ocell, xi, coord, jf, cf);
                   }
                   less = rf != re_s ? rf < re_s : (jf != je_s ? jf < je_s : (unsigned)cf < (unsigned)ce_s);
                 }
@@ -877,11 +1004,16 @@ __global__ void __launch_bounds__(kCellWarps * 32, 4)
         }
       }
       // ---- padding, counts and overflow accounting of this type ----
+      // The displacements' reader walks a type block in 32-slot batches and stops after the first
+      // batch that holds padding, so padding displacements are written only up to the end of the
+      // batch after the last real neighbour.
       const int ng = cnt - removed;  // entries beyond CAP (an error) are not in the list
-      for (int k = ge - removed + lane; k < sel; k += 32) {
+      const int nreal = ge - removed;
+      const int dlim = min(sel, ((nreal >> 5) + 1) << 5);
+      for (int k = nreal + lane; k < sel; k += 32) {
         nl_j[row + k] = -1;
         nl_code[row + k] = pack_shift(0, 0, 0);
-        if (disp) disp[(long)w * nc + s_seloff[tj] + k] = make_float4(0.f, 0.f, 0.f, -1.f);
+        if (disp && k < dlim) disp[(long)w * nc + s_seloff[tj] + k] = make_float4(0.f, 0.f, 0.f, -1.f);
       }
       if (lane == 0) {
         if (counts) counts[(long)i * ntypes + tj] = ng;
@@ -1133,7 +1265,7 @@ cudaError_t launch_nlist_build(const NlLaunch& L, int ntypes, const double* coor
                                               : (double)L.natoms / std::max(1, L.ncells_total) * std::max(1, L.max_noff);
   const int S = std::max(1024, ((int)(1.25 * mean_stream) + 64 * ntypes + 64 + 127) & ~127);
   const size_t csm = cell_smem_bytes(cap, S);
-  if (L.max_noff > 0 && (long)L.max_noff * ntypes <= kMaxRanges && cap <= 512 && csm <= 160 * 1024) {
+  if (L.max_noff > 0 && (long)L.max_noff * ntypes <= kMaxRanges && cap <= 512 && csm <= 160 * 1024 && S < 65536) {
 #define DPGB_NLC_LAUNCH(C)                                                                                       \
   do {                                                                                                           \
     e = allow_max_smem(k_nlist_cell<C>);                                                                         \
