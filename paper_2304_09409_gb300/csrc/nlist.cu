@@ -1149,7 +1149,11 @@ int screening_bounds(NlGeom& g, double rc) {
   const double eps = 2.0 * (2.0 * std::sqrt(3.0) * R * dc + 3.0 * dc * dc + 3.0 * u * R * R);
   g.rc2_in = round_down(g.rc2 - eps);
   g.rc2_out = round_up(g.rc2 + eps);
-  g.tie_w = round_up(2.5 * eps + 8.0 * u * (g.rc2_out + 1.0));
+  // Each FP32 key is within eps / 2 of its pair's FP64 r^2, and forming a window edge key -+ tie_w
+  // in FP32 moves it by at most u (r_c^2 + eps): keys further apart than eps + 2u (r_c^2 + eps + 1)
+  // keep their order in FP64.  The window is a quarter wider than that on the eps term and four
+  // times on the rounding term.
+  g.tie_w = round_up(1.25 * eps + 8.0 * u * (g.rc2_out + 1.0));
   return DP_OK;
 }
 
