@@ -45,11 +45,18 @@ __global__ void k_shift_tables(const double* __restrict__ boxes, double* __restr
                                          __dmul_rn((double)n2, h[6 + a]));
 }
 
-// Per-chunk sums of atom energies and atom virials (10 values), fixed order.
-__global__ void __launch_bounds__(256)
+// Per-chunk sums of atom energies and atom virials (10 values), fixed order; the block that
+// finishes a frame's last chunk then forms the frame's sums from the chunk partials, thread k
+// adding chunks k, k + 128, ... of the frame and a fixed tree over the threads (the order depends
+// on the frame alone, not on the batch or on which block finished last).  fcount[f] counts the
+// finished chunks of frame f; it is zero on entry and left zero.
+__global__ void __launch_bounds__(kChunk)
     k_chunk_sums(const int* __restrict__ chunk, const double* __restrict__ ae, const double* __restrict__ av,
-                 double* __restrict__ cpart) {
-  __shared__ double red[8][10];
+                 double* __restrict__ cpart, const int* __restrict__ frame_chunk, int nframes, int* __restrict__ fcount,
+                 double* __restrict__ energy, double* __restrict__ virial) {
+  static_assert(kChunk == 128, "four warps per chunk block");
+  __shared__ double red[4][10];
+  __shared__ int s_last;
   const int c = blockIdx.x;
   const int beg = chunk[2 * c], end = chunk[2 * c + 1];
   double acc[10];
@@ -68,27 +75,33 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) red[w][q] = x;
   }
   __syncthreads();
+  int f = 0;  // frame of this chunk
+  {
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (frame_chunk[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    f = lo;
+  }
+  const int c0 = frame_chunk[f], c1 = frame_chunk[f + 1];
   if (threadIdx.x < 10) {
     double x = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x += red[k][threadIdx.x];
+    for (int k = 0; k < 4; ++k) x += red[k][threadIdx.x];
     cpart[10L * c + threadIdx.x] = x;
+    __threadfence();
   }
-}
-
-// Per-frame sums of the chunk partials: thread k adds chunks k, k + 128, ... of its frame, then a
-// fixed tree over the threads (the order depends on the frame alone, not on the batch).
-__global__ void __launch_bounds__(128)
-    k_frame_sums(const int* __restrict__ frame_chunk, const double* __restrict__ cpart, double* __restrict__ energy,
-                 double* __restrict__ virial) {
-  __shared__ double red[4][10];
-  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int c0 = frame_chunk[f], c1 = frame_chunk[f + 1];
-  double acc[10];
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&fcount[f], 1) == c1 - c0 - 1;
+  __syncthreads();
+  if (!s_last) return;  // block-uniform
+  __threadfence();
+  const int tid = threadIdx.x;
 #pragma unroll
   for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-  for (int c = c0 + tid; c < c1; c += 128)
+  for (int cc = c0 + tid; cc < c1; cc += kChunk)
 #pragma unroll
-    for (int q = 0; q < 10; ++q) acc[q] += cpart[10L * c + q];
+    for (int q = 0; q < 10; ++q) acc[q] += __ldcg(cpart + 10L * cc + q);
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
     double x = acc[q];
@@ -103,6 +116,7 @@ __global__ void __launch_bounds__(128)
     else
       virial[9L * f + tid - 1] = x;
   }
+  if (tid == 0) fcount[f] = 0;
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -213,6 +227,7 @@ struct Bufs {
   double* tshift;
   int *perm, *type_start;
   double *energy, *virial, *force, *atom_energy, *atom_virial, *cpart, *epart;
+  int* fcount;  // finished chunks per frame (k_chunk_sums)
 };
 
 void carve(Arena& ar, const DeviceModel& m, const FrameTables& T, bool own_nlist, bool copy_coord, bool copy_type,
@@ -246,6 +261,7 @@ void carve(Arena& ar, const DeviceModel& m, const FrameTables& T, bool own_nlist
   if (!dev_ae) b.atom_energy = ar.get<double>(N);
   b.atom_virial = ar.get<double>(9 * N);
   b.cpart = ar.get<double>(10L * T.C);
+  b.fcount = ar.get<int>(T.F);
   b.epart = ar.get<double>((N + 255) / 256);
 }
 
@@ -479,15 +495,16 @@ int run_frames(dp_model* md, dp_nlist* nlist, int F, const int* natoms, const do
       return DP_OK;
     }
     DP_CUDA_TRY(cudaMemsetAsync(io.force, 0, sizeof(double) * 3 * N, s));
+    DP_CUDA_TRY(cudaMemsetAsync(b.fcount, 0, sizeof(int) * F, s));
     if (!m.compressed) DP_CUDA_TRY(cudaMemsetAsync(io.atom_virial, 0, sizeof(double) * 9 * N, s));
     int r = run_path(m, pc, io, ar, s);
     if (r != DP_OK) return r;
     double* d_energy = host_e ? b.energy : energy;
     double* d_virial = host_v ? b.virial : virial;
     {
-      ProfScope _ps(&md->prof, "frame_sums", s, 2);
-      k_chunk_sums<<<T.C, kChunk, 0, s>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart);
-      k_frame_sums<<<F, 128, 0, s>>>(d_fchunk, b.cpart, d_energy, d_virial);
+      ProfScope _ps(&md->prof, "frame_sums", s);
+      k_chunk_sums<<<T.C, kChunk, 0, s>>>(d_chunk, io.atom_energy, io.atom_virial, b.cpart, d_fchunk, F, b.fcount,
+                                          d_energy, d_virial);
     }
     DP_CUDA_TRY(cudaGetLastError());
     if (host_e) DP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * F, cudaMemcpyDeviceToHost, s));

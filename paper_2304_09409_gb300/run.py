@@ -51,7 +51,7 @@ SCOPES = {
     "mom_force": (("k_force_mom",), ("mom.cu", "mom.cuh", "tc_ptx.cuh", "env.cuh", "dp_internal.cuh")),
     "fit_split_tc": (("k_fit_split",), ("fit_split.cu", "fit_tc.cuh", "tc_ptx.cuh", "dp_internal.cuh")),
     "fit_fused_tc": (("k_fit_fused",), ("fit_fused.cu", "fit_tc.cuh", "tc_ptx.cuh", "dp_internal.cuh")),
-    "frame_sums": (("k_chunk_sums", "k_frame_sums"), ("driver.cu",)),
+    "frame_sums": (("k_chunk_sums",), ("driver.cu",)),
     "e3_fwd": (("k_e3",), ("path.cu", "path.cuh", "env.cuh", "tabeval.cuh", "dp_internal.cuh")),
     "e3_bwd": (("k_e3",), ("path.cu", "path.cuh", "env.cuh", "tabeval.cuh", "dp_internal.cuh")),
 }
