@@ -69,7 +69,7 @@ __device__ __forceinline__ void pair_env_f32(float x0, float x1, float x2, doubl
 }
 
 // The same with one reciprocal square root and no division (inv_w = 1 / (r_c - r_s)): a few ulps
-// of FP32, for the mixed mode, whose values go on as FP16 / BF16 operands.
+// of FP32, for the moment path, whose values go on as FP16 or split-BF16 tensor-core operands.
 __device__ __forceinline__ void pair_env_f32_fast(float x0, float x1, float x2, float frs, float frc, float inv_w,
                                                   float& r, float& s, float& ds, float* u) {
   const float r2 = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));

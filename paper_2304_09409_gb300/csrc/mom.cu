@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(256, 3)
     }
     return d;
   };
+  const float frs = (float)pc.rs, frc = (float)pc.rc, inv_w = 1.0f / (frc - frs);
   long task = (long)blockIdx.x * 8 + warp;
   float4 dnext = disp_batch(task, task < ntask ? g.sel_off[task % pc.ntypes] : 0);
   for (; task < ntask; task += wstride) {  // warp-uniform
@@ -294,7 +295,6 @@ __global__ void __launch_bounds__(256, 3)
   // The cell-centred list build hands this same value over per slot (disp); the per-atom one
   // does not, and then it is formed here from the gathered positions, rounded the same way.
   const bool f32d = NPASS == 1 && g.atom_l != nullptr && g.disp == nullptr;
-  const float frs = (float)pc.rs, frc = (float)pc.rc, inv_w = 1.0f / (frc - frs);
   float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
   int4 mi = make_int4(0, 0, 0, 0);
   const NlGeom* G = nullptr;
@@ -359,10 +359,8 @@ __global__ void __launch_bounds__(256, 3)
         x1 = (float)d1;
         x2 = (float)d2;
       }
-      if (NPASS == 1)
-        pair_env_f32_fast(x0, x1, x2, frs, frc, inv_w, r, s, ds, u);
-      else
-        pair_env_f32(x0, x1, x2, pc.rs, pc.rc, r, s, ds, u);
+      // a few ulps of FP32: the moments go on as FP16 or split-BF16 operands (2^-11, 2^-17)
+      pair_env_f32_fast(x0, x1, x2, frs, frc, inv_w, r, s, ds, u);
       float invd;
       l = mom_interval(g, s, INT_MAX, tau, invd, oor);
     }
