@@ -367,8 +367,9 @@ def run_descriptors(local, flush, steps=5, warmup=3):
     (the path these models run on), forces compared with the FP64 GPU path (uncompressed): se_e2_r,
     also compressed; hybrid se_e2_a (r_c 4) + se_e2_r (r_c 6); se_e3, also compressed (pieces in
     theta); hybrid se_e2_a (r_c 4) + se_e3 (r_c 6), each with its output layer scaled to forces of
-    ~1 eV/A RMS.  se_e3 parts also report their pair kernels
-    against the FP32 ALU peak (pairs = sum over atoms of real neighbours squared)."""
+    ~1 eV/A RMS.  se_e3 parts also report their pair kernels against the FP32 ALU peak, rated on the
+    net evaluations they make: theta is symmetric and a pair of neighbours of one type takes one net
+    both ways, so per atom n^2 ordered pairs need n^2 - sum_t n_t (n_t - 1) / 2 evaluations."""
     import torch
     from paper_2304_09409_gb300 import dpgb, inputs as I
     _, _, _, big = _workload()
@@ -401,17 +402,22 @@ def run_descriptors(local, flush, steps=5, warmup=3):
         if cfg.descriptor in (3, 4):
             # the se_e3 part reads the whole list here (its r_c and sel are the list's)
             widths = cfg.embed if cfg.descriptor == 3 else cfg.embed_2
-            n_i = (nj >= 0).sum(axis=1).astype(np.float64)
+            off = np.concatenate([[0], np.cumsum(cfg.list_sel)])
+            n_t = np.stack([(nj[:, off[t]:off[t + 1]] >= 0).sum(axis=1) for t in range(cfg.ntypes)], 1)
+            n_t = n_t.astype(np.float64)
+            n_i = n_t.sum(axis=1)
             pairs = float((n_i ** 2).sum())
+            evals = float((n_i ** 2 - (n_t * (n_t - 1) / 2).sum(axis=1)).sum())
             fpp, bpp = _e3_flops_per_pair(widths, widths[-1])
             leg["e3_pairs_per_step"] = pairs
+            leg["e3_evals_per_step"] = evals
             for scope, per in (("e3_fwd", fpp), ("e3_bwd", bpp)):
                 if scope in prof:
                     t = prof[scope][0] / steps * 1e-3
-                    ach = pairs * per / t / 1e12
+                    ach = evals * per / t / 1e12
                     leg[scope] = {"bound": "alu", "achieved": ach, "peak": ALU_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                   "frac": ach / ALU_FP32_PEAK_TFLOPS, "us_per_step": t * 1e6,
-                                  "flops_per_pair": per, "pairs_per_s": pairs / t}
+                                  "flops_per_eval": per, "pairs_per_s": pairs / t, "evals_per_s": evals / t}
         out[name] = leg
     return out
 

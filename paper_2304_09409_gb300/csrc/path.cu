@@ -298,6 +298,7 @@ struct E3Net {
 template <class R, int W>
 struct E3Any {
   static constexpr int kM = W;
+  static constexpr bool kItemBwd = true;  // backward over the warp's item stream (evaluation-bound)
   E3Net nt;
   __device__ int per_net() const { return nt.per_net; }
   __device__ void fill(R* wsm, const R* __restrict__ params, int n_nets, int tid, int nth) const {
@@ -374,6 +375,7 @@ struct E3Any {
 template <class R, int A, int B, int C>
 struct E3Fixed {
   static constexpr int kM = C;
+  static constexpr bool kItemBwd = true;
   static constexpr int PA = (A + 3) / 4 * 4, PB = (B + 3) / 4 * 4, PC = (C + 3) / 4 * 4;
   // padded layout of one net: w0 [PA], b0 [PA], W1 [A][PB], b1 [PB], W2 [B][PC], b2 [PC]
   static constexpr int OW0 = 0, OB0 = PA, OW1 = 2 * PA, OB1 = OW1 + A * PB, OW2 = OB1 + PB, OB2 = OW2 + B * PC;
@@ -495,6 +497,9 @@ struct E3Fixed {
 template <class R, int MW>
 struct E3Tab {
   static constexpr int kM = MW;
+  // backward a warp per row: the table pieces are L1 loads, whose latencies the lanes overlap best
+  // without a warp-wide step per item
+  static constexpr bool kItemBwd = false;
   const R* tab;  // [net][interval][M][kCoefStride]
   TabConst tc;
   int M;
@@ -519,9 +524,11 @@ struct E3Tab {
   }
 };
 
+constexpr int kE3Warps = 4;  // warps per CTA of the se_e3 pair kernel
+
 // BWD = 0: D block; BWD = 1: dE/dR rows (gR, [rows][4], every row of the atom written).
 template <class R, class Ev, int BWD>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kE3Warps * 32)
     k_e3(PathConst pc, Ev ev, const R* __restrict__ params, int n_nets, const R* __restrict__ Renv,
          const R* __restrict__ gD, R* __restrict__ D, R* __restrict__ gR, int* __restrict__ range_flag) {
   constexpr int W = Ev::kM;
@@ -536,6 +543,7 @@ __global__ void __launch_bounds__(128)
   int* tv = reinterpret_cast<int*>(red + W);  // [nc] neighbour type of each compacted row
   int* kv = tv + nc;                          // [nc] slot of each compacted row
   __shared__ int nv_s;
+  __shared__ int tstart_s[DP_MAX_TYPES + 1];  // first compacted row of each neighbour type
   const int p = blockIdx.x;
   const long rb = (long)p * nc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -556,6 +564,15 @@ __global__ void __launch_bounds__(128)
       nv += __popc(mask);
     }
     if (lane == 0) nv_s = nv;
+    __syncwarp();
+    if (lane <= nt_types) {  // the compacted rows keep the slot order, so their types never decrease
+      int lo = 0, hi = nv;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (tv[mid] < lane) lo = mid + 1; else hi = mid;
+      }
+      tstart_s[lane] = lo;
+    }
   }
   __syncthreads();
   const int nv = nv_s;
@@ -567,23 +584,60 @@ __global__ void __launch_bounds__(128)
   R acc[W];
 #pragma unroll
   for (int m = 0; m < W; ++m) acc[m] = R(0);
-  for (int j = warp; j < nv; j += nw) {
-    const V4 rj = Rv[j];
-    const int tj = tv[j];
-    R gj0 = 0, gj1 = 0, gj2 = 0, gj3 = 0;
-    for (int k = lane; k < nv; k += 32) {
+  // theta_jk = theta_kj, and a pair of neighbours of one type takes one net both ways: such a pair
+  // is evaluated once, from its lower row, with weight 2 (the diagonal j = k once, weight 1).  Row j
+  // pairs with every row k outside its type block and with the rows of its own type from j on:
+  // nv - (j - b0) partners, partner q at k = q below the block start b0, else q + (j - b0).
+  if (!BWD) {
+    // forward: warp w's rows w, w + nw, ... as one stream of (row, partner) items, so that a lane
+    // moves on to the next row without waiting for the others (the sums go to D, not to the rows)
+    int jr = warp, rbeg = 0, rlen = 0, b0 = 0, tj = 0;
+    V4 rj = Vec4<R>::make(R(0), R(0), R(0), R(0));
+    auto open_row = [&]() {
+      if (jr < nv) {
+        rj = Rv[jr];
+        tj = tv[jr];
+        b0 = tstart_s[tj];
+        rlen = nv - (jr - b0);
+      }
+    };
+    open_row();
+    for (int t = lane;; t += 32) {
+      while (jr < nv && t >= rbeg + rlen) {
+        rbeg += rlen;
+        jr += nw;
+        open_row();
+      }
+      if (jr >= nv) break;
+      const int q = t - rbeg;
+      const int k = q < b0 ? q : q + (jr - b0);
       const V4 rk = Rv[k];
+      const int tk = tv[k];
       const R th = ((rj.x * rk.x + rj.y * rk.y) + rj.z * rk.z) + rj.w * rk.w;
       R g[W], dg[W];
-      ev.template eval<BWD != 0>(wsm, tj * nt_types + tv[k], th, g, dg, oor);
-      if (!BWD) {
+      ev.template eval<false>(wsm, tj * nt_types + tk, th, g, dg, oor);
+      const R wth = ((tk == tj && k != jr) ? R(2) : R(1)) * th;
 #pragma unroll
-        for (int m = 0; m < W; ++m) acc[m] += th * g[m];
-      } else {
+      for (int m = 0; m < W; ++m) acc[m] += wth * g[m];
+    }
+  } else if (!Ev::kItemBwd) {
+    // backward, a warp per row: its own term summed over the lanes
+    for (int j = warp; j < nv; j += nw) {
+      const V4 rj = Rv[j];
+      const int tj = tv[j];
+      const int b0 = tstart_s[tj], skip = j - b0;
+      R gj0 = 0, gj1 = 0, gj2 = 0, gj3 = 0;
+      for (int q = lane; q < nv - skip; q += 32) {
+        const int k = q < b0 ? q : q + skip;
+        const V4 rk = Rv[k];
+        const int tk = tv[k];
+        const R th = ((rj.x * rk.x + rj.y * rk.y) + rj.z * rk.z) + rj.w * rk.w;
+        R g[W], dg[W];
+        ev.template eval<true>(wsm, tj * nt_types + tk, th, g, dg, oor);
         R gth = 0;
 #pragma unroll
         for (int m = 0; m < W; ++m) gth += red[m] * (g[m] + th * dg[m]);
-        gth *= inv;
+        gth *= inv * ((tk == tj && k != j) ? R(2) : R(1));
         gj0 += gth * rk.x;
         gj1 += gth * rk.y;
         gj2 += gth * rk.z;
@@ -593,8 +647,6 @@ __global__ void __launch_bounds__(128)
         atomicAdd(&gRv[k].z, gth * rj.z);
         atomicAdd(&gRv[k].w, gth * rj.w);
       }
-    }
-    if (BWD) {
       for (int o = 16; o > 0; o >>= 1) {
         gj0 += __shfl_xor_sync(0xffffffffu, gj0, o);
         gj1 += __shfl_xor_sync(0xffffffffu, gj1, o);
@@ -608,7 +660,90 @@ __global__ void __launch_bounds__(128)
         atomicAdd(&gRv[j].w, gj3);
       }
     }
+  } else {
+    // backward: the same item streams.  Row j's own term (sum over partners of dE/dtheta R_k) is
+    // summed per lane while the lane is in the row; a lane leaving a row of 32 or more items (every
+    // lane has items there) parks its sum in a slot of part[] chosen by the parity of the long rows
+    // passed, and once lane 0 -- the last lane out of any row -- has left it, the warp adds the 32
+    // sums; a lane leaving a shorter row adds its sum itself.  A lane cannot leave the next long row
+    // but one before lane 0 has left this one, so two slots suffice.
+    __shared__ V4 part[2][kE3Warps][32];
+    int jr = warp, rbeg = 0, rlen = 0, b0 = 0, tj = 0;
+    V4 rj = Vec4<R>::make(R(0), R(0), R(0), R(0));
+    auto open_row = [&]() {
+      if (jr < nv) {
+        rj = Rv[jr];
+        tj = tv[jr];
+        b0 = tstart_s[tj];
+        rlen = nv - (jr - b0);
+      }
+    };
+    open_row();
+    R gj0 = 0, gj1 = 0, gj2 = 0, gj3 = 0;
+    int nlong = 0, done = 0;  // long rows this lane has left; long rows the warp has added
+    int lrow0 = 0, lrow1 = 0;  // row index of the long rows in slots 0 and 1
+    for (int t = lane;; t += 32) {
+      while (jr < nv && t >= rbeg + rlen) {  // leaving row jr
+        if (rlen >= 32) {
+          part[nlong & 1][warp][lane] = Vec4<R>::make(gj0, gj1, gj2, gj3);
+          if (nlong & 1) lrow1 = jr; else lrow0 = jr;
+          ++nlong;
+        } else if (gj0 != R(0) || gj1 != R(0) || gj2 != R(0) || gj3 != R(0)) {
+          atomicAdd(&gRv[jr].x, gj0);
+          atomicAdd(&gRv[jr].y, gj1);
+          atomicAdd(&gRv[jr].z, gj2);
+          atomicAdd(&gRv[jr].w, gj3);
+        }
+        gj0 = gj1 = gj2 = gj3 = R(0);
+        rbeg += rlen;
+        jr += nw;
+        open_row();
+      }
+      __syncwarp();
+      if (__shfl_sync(0xffffffffu, nlong, 0) > done) {  // lane 0 left long row number done
+        const V4 v = part[done & 1][warp][lane];
+        R x = v.x, y = v.y, z = v.z, w = v.w;
+        for (int o = 16; o > 0; o >>= 1) {
+          x += __shfl_xor_sync(0xffffffffu, x, o);
+          y += __shfl_xor_sync(0xffffffffu, y, o);
+          z += __shfl_xor_sync(0xffffffffu, z, o);
+          w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (lane == 0) {
+          const int jd = (done & 1) ? lrow1 : lrow0;
+          atomicAdd(&gRv[jd].x, x);
+          atomicAdd(&gRv[jd].y, y);
+          atomicAdd(&gRv[jd].z, z);
+          atomicAdd(&gRv[jd].w, w);
+        }
+        ++done;
+        __syncwarp();
+      }
+      if (__all_sync(0xffffffffu, jr >= nv)) break;
+      if (jr < nv) {
+        const int q = t - rbeg;
+        const int k = q < b0 ? q : q + (jr - b0);
+        const V4 rk = Rv[k];
+        const int tk = tv[k];
+        const R th = ((rj.x * rk.x + rj.y * rk.y) + rj.z * rk.z) + rj.w * rk.w;
+        R g[W], dg[W];
+        ev.template eval<true>(wsm, tj * nt_types + tk, th, g, dg, oor);
+        R gth = 0;
+#pragma unroll
+        for (int m = 0; m < W; ++m) gth += red[m] * (g[m] + th * dg[m]);
+        gth *= inv * ((tk == tj && k != jr) ? R(2) : R(1));
+        gj0 += gth * rk.x;
+        gj1 += gth * rk.y;
+        gj2 += gth * rk.z;
+        gj3 += gth * rk.w;
+        atomicAdd(&gRv[k].x, gth * rj.x);
+        atomicAdd(&gRv[k].y, gth * rj.y);
+        atomicAdd(&gRv[k].z, gth * rj.z);
+        atomicAdd(&gRv[k].w, gth * rj.w);
+      }
+    }
   }
+  __syncwarp();
   if (oor && range_flag) atomicOr(range_flag, 1);
   if (!BWD) {
 #pragma unroll
@@ -826,9 +961,9 @@ cudaError_t launch_e3_ev(const PathConst& pc, const Ev& ev, int per_net_smem, co
     if (e != cudaSuccess) return e;
   }
   if (bwd)
-    kb<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR, range_flag);
+    kb<<<(unsigned)pc.natoms, kE3Warps * 32, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR, range_flag);
   else
-    kf<<<(unsigned)pc.natoms, 128, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR, range_flag);
+    kf<<<(unsigned)pc.natoms, kE3Warps * 32, smem, st>>>(pc, ev, w, n_nets, Renv, gD, D, gR, range_flag);
   return cudaGetLastError();
 }
 
