@@ -1014,6 +1014,155 @@ cudaError_t launch_e3(const PartDesc& P, const PathConst& pc, const R* params, c
   return launch_e3_ev<R>(pc, E3Any<R, 32>{nt}, nt.per_net, wp, P.n_nets, Renv, gD, D, gR, bwd, st);
 }
 
+// ---- se_e2_r part: fused per-neighbour kernel -------------------------------------------------
+// D_m = (1/Nc) sum_k G_m(s_k) s_k over the atom's real neighbours (rows with s > 0) and, in
+// reverse, dE/ds_k = (1/Nc) sum_m gD_m (G_m(s_k) + s_k G_m'(s_k)) into the radial component of gR
+// (the other three zero).  The nets have a scalar input, as the se_e3 nets do, and run on the same
+// evaluators (dG/ds carried forward alongside), all of the part's nets in shared memory: nothing of
+// G is stored.  Persistent blocks of eight warps, a warp per atom, its lanes over the atom's real
+// neighbours, compacted first.
+constexpr int kRWarps = 8;
+
+template <class R, class Ev, int BWD>
+__global__ void __launch_bounds__(kRWarps * 32)
+    k_rnet(PathConst pc, Ev ev, const R* __restrict__ params, int n_nets, const int* __restrict__ tsorted,
+           const R* __restrict__ Renv, const R* __restrict__ gD, R* __restrict__ D, R* __restrict__ gR) {
+  constexpr int W = Ev::kM;
+  typedef typename Vec4<R>::T V4;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nc = pc.nc, M = pc.M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R* wsm = reinterpret_cast<R*>(sm_raw);                   // [n_nets * per_net]
+  R* gdw = wsm + (long)n_nets * ev.per_net() + warp * W;   // [kRWarps][W] the atom's dE/dD block
+  int* kw = reinterpret_cast<int*>(wsm + (long)n_nets * ev.per_net() + kRWarps * W) + warp * nc;  // [kRWarps][nc]
+  ev.fill(wsm, params, n_nets, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const R inv_nc = R(1) / R(nc);
+  bool oor = false;
+  for (long p = (long)blockIdx.x * kRWarps + warp; p < pc.natoms; p += (long)gridDim.x * kRWarps) {  // warp-uniform
+    const int ti = tsorted[p];
+    const long rb = p * nc;
+    int nv = 0;
+    for (int base = 0; base < nc; base += 32) {
+      const int k = base + lane;
+      const bool v = k < nc && Renv[(rb + k) * 4] != R(0);
+      const unsigned mask = __ballot_sync(0xffffffffu, v);
+      if (v) kw[nv + __popc(mask & ((1u << lane) - 1u))] = k;
+      if (BWD && k < nc && !v) reinterpret_cast<V4*>(gR)[rb + k] = Vec4<R>::make(R(0), R(0), R(0), R(0));
+      nv += __popc(mask);
+    }
+    if (BWD)
+      for (int m = lane; m < W; m += 32) gdw[m] = m < M ? gD[p * pc.Dw + pc.doff + m] : R(0);
+    __syncwarp();
+    if (!BWD) {
+      R acc[W];
+#pragma unroll
+      for (int m = 0; m < W; ++m) acc[m] = R(0);
+      for (int e = lane; e < nv; e += 32) {
+        const int k = kw[e];
+        const R sk = Renv[(rb + k) * 4];
+        R g[W], dg[W];
+        ev.template eval<false>(wsm, net_of(pc, ti, slot_block(pc, k)), sk, g, dg, oor);
+#pragma unroll
+        for (int m = 0; m < W; ++m) acc[m] += g[m] * sk;
+      }
+#pragma unroll
+      for (int m = 0; m < W; ++m) {
+        R v = acc[m];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == (m & 31) && m < M) D[p * pc.Dw + pc.doff + m] = v * inv_nc;
+      }
+    } else {
+      for (int e = lane; e < nv; e += 32) {
+        const int k = kw[e];
+        const R sk = Renv[(rb + k) * 4];
+        R g[W], dg[W];
+        ev.template eval<true>(wsm, net_of(pc, ti, slot_block(pc, k)), sk, g, dg, oor);
+        R gs = R(0);
+#pragma unroll
+        for (int m = 0; m < W; ++m) gs += gdw[m] * (g[m] + sk * dg[m]);
+        reinterpret_cast<V4*>(gR)[rb + k] = Vec4<R>::make(gs * inv_nc, R(0), R(0), R(0));
+      }
+    }
+    __syncwarp();  // kw and gdw are rewritten for the warp's next atom
+  }
+}
+
+template <class R, class Ev>
+cudaError_t launch_rnet_ev(const PathConst& pc, const Ev& ev, int per_net_smem, const R* w, int n_nets,
+                           const int* tsorted, const R* Renv, const R* gD, R* D, R* gR, bool bwd, cudaStream_t st) {
+  const size_t smem = sizeof(R) * ((size_t)n_nets * per_net_smem + (size_t)kRWarps * Ev::kM) +
+                      sizeof(int) * (size_t)kRWarps * pc.nc;
+  auto kf = k_rnet<R, Ev, 0>;
+  auto kb = k_rnet<R, Ev, 1>;
+  cudaError_t e = allow_max_smem(bwd ? kb : kf);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;  // persistent: as many blocks as fit the SMs at once (each fills the nets once)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd ? kb : kf, kRWarps * 32, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const long warps = pc.natoms;
+  const unsigned blocks =
+      (unsigned)std::max<long>(1, std::min<long>((warps + kRWarps - 1) / kRWarps, (long)per_sm * sm_count()));
+  if (bwd)
+    kb<<<blocks, kRWarps * 32, smem, st>>>(pc, ev, w, n_nets, tsorted, Renv, gD, D, gR);
+  else
+    kf<<<blocks, kRWarps * 32, smem, st>>>(pc, ev, w, n_nets, tsorted, Renv, gD, D, gR);
+  return cudaGetLastError();
+}
+
+// The se_e2_r part's nets on the fused kernel: three-layer nets of the shapes below, or any nets of
+// widths up to 32 whose parameters fit shared memory beside the compaction lists.
+bool rnet_supported(const PartDesc& P, int precision) {
+  if (P.kind != PART_R) return false;
+  int w = 1;
+  for (int l = 0; l < P.nl; ++l) w = std::max(w, P.emb[l].n_out);
+  const bool fixed = P.nl == 3 && P.emb[0].n_out == 10 && P.emb[1].n_out == 20 && P.emb[2].n_out == 40;
+  const size_t bytes = (size_t)P.n_nets * (P.per_net + 64) * (precision == DP_PREC_FP64 ? 8 : 4);
+  return (fixed || w <= 32) && bytes <= 96 * 1024 && P.nc <= 2048;
+}
+
+template <class R>
+cudaError_t launch_rnet(const PartDesc& P, const PathConst& pc, const R* params, const int* tsorted, const R* Renv,
+                        const R* gD, R* D, R* gR, bool bwd, cudaStream_t st) {
+  const R* wp = params + P.w_off;
+  int w = 1;
+  for (int l = 0; l < P.nl; ++l) w = std::max(w, P.emb[l].n_out);
+  if (P.nl == 3) {
+    const int a = P.emb[0].n_out, b = P.emb[1].n_out, c = P.emb[2].n_out;
+#define DP_RNET_FIXED(A_, B_, C_)                                                                              \
+    if (a == A_ && b == B_ && c == C_) {                                                                        \
+      E3Fixed<R, A_, B_, C_> ev;                                                                                \
+      ev.per_net_global = (int)P.per_net;                                                                       \
+      return launch_rnet_ev<R>(pc, ev, E3Fixed<R, A_, B_, C_>::PN, wp, P.n_nets, tsorted, Renv, gD, D, gR, bwd, \
+                               st);                                                                             \
+    }
+    DP_RNET_FIXED(10, 20, 40)
+    DP_RNET_FIXED(2, 4, 8)
+    DP_RNET_FIXED(4, 8, 16)
+    DP_RNET_FIXED(8, 16, 32)
+#undef DP_RNET_FIXED
+  }
+  E3Net nt;
+  std::memset(&nt, 0, sizeof(nt));
+  nt.nl = P.nl;
+  for (int l = 0; l < P.nl; ++l) {
+    const LayerDesc& L = P.emb[l];
+    nt.in[l] = L.n_in;
+    nt.out[l] = L.n_out;
+    nt.skip[l] = L.skip;
+    nt.loff[l] = (int)(L.w_off - P.w_off);
+  }
+  nt.per_net = (int)P.per_net;
+  if (w <= 8)
+    return launch_rnet_ev<R>(pc, E3Any<R, 8>{nt}, nt.per_net, wp, P.n_nets, tsorted, Renv, gD, D, gR, bwd, st);
+  if (w <= 16)
+    return launch_rnet_ev<R>(pc, E3Any<R, 16>{nt}, nt.per_net, wp, P.n_nets, tsorted, Renv, gD, D, gR, bwd, st);
+  return launch_rnet_ev<R>(pc, E3Any<R, 32>{nt}, nt.per_net, wp, P.n_nets, tsorted, Renv, gD, D, gR, bwd, st);
+}
+
 // The whole path on CUDA cores for any descriptor: each part (Sec. II.A.1) builds its own
 // environment rows from its slots of the one neighbour list, runs its embedding nets and writes
 // its block of D; one fitting net reads D; each part then runs its reverse pass and scatters its
@@ -1028,6 +1177,8 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
   const R* tab = reinterpret_cast<const R*>(std::is_same<R, double>::value ? (const void*)m.tab64
                                                                            : (const void*)m.tab32);
   auto tabulated = [&](int q) { return m.compressed && q == 0; };
+  // se_e2_r parts on the fused per-neighbour kernel (uncompressed nets)
+  auto rfused = [&](int q) { return !tabulated(q) && rnet_supported(m.parts[q], m.precision); };
   int* range_flag = &io.status->table_range;
   long maxe = 1;  // widest embedding-gradient buffer over the parts
   for (int q = 0; q < nparts; ++q) {
@@ -1037,7 +1188,7 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     const long rows = N * P.nc;
     b.Renv = ar.get<R>(rows * 4);
     b.gR = ar.get<R>(rows * 4);
-    if (P.kind == PART_E3 || tabulated(q)) continue;
+    if (P.kind == PART_E3 || tabulated(q) || rfused(q)) continue;
     for (int l = 0; l < P.nl; ++l) {
       const int w = P.emb[l].n_out;
       b.Y.push_back(ar.get<R>(rows * w));
@@ -1082,6 +1233,11 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     if (tabulated(q)) {  // se_e2_r
       ProfScope _ps(io.prof, "rtab_fwd", st);
       k_rtab_fwd<R><<<(unsigned)N, 64, 0, st>>>(pq, tab, tab_const(m), tsorted, b.Renv, D, range_flag);
+      continue;
+    }
+    if (rfused(q)) {
+      ProfScope _ps(io.prof, "rnet_fwd", st);
+      DP_CUDA_TRY(launch_rnet<R>(P, pq, params, tsorted, b.Renv, nullptr, D, nullptr, false, st));
       continue;
     }
     for (int n = 0; n < P.n_nets; ++n) {
@@ -1134,6 +1290,9 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
     } else if (tabulated(q)) {  // se_e2_r
       ProfScope _ps(io.prof, "rtab_bwd", st);
       k_rtab_bwd<R><<<(unsigned)N, 128, sizeof(R) * P.M, st>>>(pq, tab, tab_const(m), tsorted, b.Renv, gD, b.gR);
+    } else if (rfused(q)) {
+      ProfScope _ps(io.prof, "rnet_bwd", st);
+      DP_CUDA_TRY(launch_rnet<R>(P, pq, params, tsorted, b.Renv, gD, nullptr, b.gR, true, st));
     } else {
       const R* G = b.Y[P.nl - 1];
       if (P.kind == PART_A) {
