@@ -79,6 +79,58 @@ __device__ __forceinline__ void store_a(void* base, long idx, float x) {
     reinterpret_cast<float*>(base)[idx] = x;
 }
 
+// 16 consecutive values of one row (64-byte aligned: row pitches and column pieces are multiples
+// of 16) as two 32-byte accesses, one full sector each: an epilogue thread owns a row, so scalar
+// accesses would touch a different line per lane and per element.
+__device__ __forceinline__ void ld16f(const float* p, float* v) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+               : "l"(p + 8));
+}
+__device__ __forceinline__ void st16f(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p + 8), "f"(v[8]), "f"(v[9]),
+               "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+               : "memory");
+}
+// 16 values of the next A operand at element index idx (a multiple of 16)
+template <int EB>
+__device__ __forceinline__ void store16_a(void* base, long idx, const float* x) {
+  if (EB == 2) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(base) + idx;
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+  } else {
+    st16f(reinterpret_cast<float*>(base) + idx, x);
+  }
+}
+
+// tanh x = 1 - 2 / (1 + e^{2x}), x clamped to +-15 (where tanh is 1 to FP32): absolute error a few
+// 1e-7, below the BF16 / TF32 rounding of the operands these layers feed.  The exponential takes
+// the special-function unit; 1/d comes from the bit pattern of d (first guess within 5.1 %) and
+// three Newton steps on the FMA pipe.
+__device__ __forceinline__ float tanh_op(float x) {
+  const float e = __expf(2.f * fminf(fmaxf(x, -15.f), 15.f));
+  const float d = 1.f + e;
+  float y = __int_as_float(0x7EF311C0 - __float_as_int(d));
+  y = y * (2.f - d * y);
+  y = y * (2.f - d * y);
+  y = y * (2.f - d * y);
+  return 1.f - 2.f * y;
+}
+
 // One dense layer (or its backward) on a 128-row tile: C = A . B^T on the tensor cores, then the
 // epilogue of MODE.  A: [rows][K] (EB-byte elements), B^T: [N][K] per group.
 template <int EB, int MODE>
@@ -182,49 +234,67 @@ __global__ void __launch_bounds__(kDThreads)
   for (int c = half * 16; c < BN; c += 32) {
     float v[16];
     tmem_ld16(tb + c, v);
-    if (!rv) continue;
-#pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
-      const int cg = col0 + c + i;
-      if (cg >= g.ldo) break;
-      const long o = row * g.ldo + cg;
-      const bool real = cg < g.N;
-      if (MODE == DM_PLAIN) {
-        g.out_y[o] = real ? v[i] : 0.f;
-      } else if (MODE == DM_FWD || MODE == DM_FWD_LAST) {
-        float t = 0.f, y = 0.f;
-        if (real) {
-          t = tanhf(v[i] + __ldg(bias + cg));
-          y = t;
-          if (g.skip == 1) y += __ldg(g.skip_in + row * g.ld_skip + cg);
-          if (g.skip == 2) y += __ldg(g.skip_in + row * g.ld_skip + cg % g.n_in_skip);
+    const int cg0 = col0 + c;  // a piece is all inside the padded width or all beyond it
+    if (!rv || cg0 >= g.ldo) continue;
+    const long o = row * g.ldo + cg0;
+    if (MODE == DM_PLAIN) {
+      float y[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) y[i] = cg0 + i < g.N ? v[i] : 0.f;
+      st16f(g.out_y + o, y);
+    } else if (MODE == DM_FWD || MODE == DM_FWD_LAST) {
+      float xs[16];
+      if (g.skip == 1) ld16f(g.skip_in + row * g.ld_skip + cg0, xs);  // n_out = n_in: the same padded width
+      float y[16], t[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int cg = cg0 + i;
+        float tt = 0.f, yy = 0.f;
+        if (cg < g.N) {
+          tt = tanh_op(v[i] + __ldg(bias + cg));
+          yy = tt;
+          if (g.skip == 1) yy += xs[i];
+          if (g.skip == 2) yy += __ldg(g.skip_in + row * g.ld_skip + cg % g.n_in_skip);
         }
-        if (MODE == DM_FWD) {
-          g.out_y[o] = y;
-          if (g.out_t) g.out_t[o] = t;
-          if (g.out_a) store_a<EB>(g.out_a, o, y);
-        } else {
-          const float w = real ? __ldg(wl + cg) : 0.f;
-          e_acc += y * w;
-          store_a<EB>(g.out_a, o, w * (1.f - t * t));
-        }
-      } else {  // DM_BWD
-        float gy = 0.f, gz = 0.f;
-        if (real) {
-          gy = v[i];
-          if (g.skip == 1) gy += __ldg(g.skip_in + row * g.ld_skip + cg);
-          if (g.skip == 2)
-            gy += __ldg(g.skip_in + row * g.ld_skip + cg) + __ldg(g.skip_in + row * g.ld_skip + cg + g.N);
-          if (g.skip == 3) gy += __ldg(wl + cg);
-          gz = gy;
-          if (g.tbelow) {
-            const float tt = __ldg(g.tbelow + row * g.ld_tb + cg);
-            gz = gy * (1.f - tt * tt);
-          }
-        }
-        if (g.out_y) g.out_y[o] = gy;
-        if (g.out_a) store_a<EB>(g.out_a, o, gz);
+        y[i] = yy;
+        t[i] = tt;
       }
+      if (MODE == DM_FWD) {
+        st16f(g.out_y + o, y);
+        if (g.out_t) st16f(g.out_t + o, t);
+        if (g.out_a) store16_a<EB>(g.out_a, o, y);
+      } else {
+        float ga[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int cg = cg0 + i;
+          const float w = cg < g.N ? __ldg(wl + cg) : 0.f;
+          e_acc += y[i] * w;
+          ga[i] = w * (1.f - t[i] * t[i]);
+        }
+        store16_a<EB>(g.out_a, o, ga);
+      }
+    } else {  // DM_BWD
+      float xs[16], tb16[16];
+      if (g.skip == 1 || g.skip == 2) ld16f(g.skip_in + row * g.ld_skip + cg0, xs);  // gy[c]: the wider width
+      if (g.tbelow) ld16f(g.tbelow + row * g.ld_tb + cg0, tb16);
+      float gyv[16], gzv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int cg = cg0 + i;
+        float gy = 0.f, gz = 0.f;
+        if (cg < g.N) {
+          gy = v[i];
+          if (g.skip == 1) gy += xs[i];
+          if (g.skip == 2) gy += xs[i] + __ldg(g.skip_in + row * g.ld_skip + cg + g.N);
+          if (g.skip == 3) gy += __ldg(wl + cg);
+          gz = g.tbelow ? gy * (1.f - tb16[i] * tb16[i]) : gy;
+        }
+        gyv[i] = gy;
+        gzv[i] = gz;
+      }
+      if (g.out_y) st16f(g.out_y + o, gyv);
+      if (g.out_a) store16_a<EB>(g.out_a, o, gzv);
     }
   }
   if (MODE == DM_FWD_LAST) {
@@ -323,15 +393,22 @@ __global__ void k_env_l0(PathConst pc, const double* __restrict__ coord, const i
   const int net = pc.type_one_side ? t : tsorted[p] * pc.ntypes + t;
   const float* w = nets.w0[net];
   const float* b = nets.b0[net];
-  for (int c = 0; c < ld1; ++c) {
-    float tt = 0.f, y = 0.f;
-    if (c < w1) {
-      tt = tanhf(o[0] * __ldg(w + c) + __ldg(b + c));
-      y = tt + (skip ? o[0] : 0.f);
+  for (int c0 = 0; c0 < ld1; c0 += 16) {  // ld1 is a multiple of 16: 16-value vector stores per row
+    float tv[16], yv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int c = c0 + q;
+      float tt = 0.f, y = 0.f;
+      if (c < w1) {
+        tt = tanh_op(o[0] * __ldg(w + c) + __ldg(b + c));
+        y = tt + (skip ? o[0] : 0.f);
+      }
+      tv[q] = tt;
+      yv[q] = y;
     }
-    Y0[row * ld1 + c] = y;
-    T0[row * ld1 + c] = tt;
-    if (A0) store_a<EB>(A0, row * ld1 + c, y);
+    st16f(Y0 + row * ld1 + c0, yv);
+    st16f(T0 + row * ld1 + c0, tv);
+    if (A0) store16_a<EB>(A0, row * ld1 + c0, yv);
   }
 }
 
@@ -349,8 +426,11 @@ __global__ void k_contract_b(PathConst pc, const float* __restrict__ G, int ldg,
     for (int t = 0; t < pc.ntypes; ++t)
       for (int k = pc.sel_off[t]; k < pc.sel_off[t + 1]; ++k) {
         const long row = brow(pc, p, k, t);
-        const float gv = G[row * ldg + m];
         const float4 r4 = Renv[row];
+        // the block's real neighbours come first, nearest first, and s falls with r: past the first
+        // zero row (padding, or s rounded to zero just inside r_c) every row adds zero
+        if (r4.x == 0.f) break;
+        const float gv = G[row * ldg + m];
         a0 += gv * r4.x;
         a1 += gv * r4.y;
         a2 += gv * r4.z;
