@@ -493,10 +493,14 @@ __global__ void k_descr_bwd_b(PathConst pc, const float4* __restrict__ Tm, const
     const int t = block_of_slot(pc, k);
     const long row = brow(pc, p, k, t);
     const float4 r4 = Renv[row];
+    // a zero row (padding, or s rounded to zero within ~1e-15 of r_c): dE/dG is zero; its dE/dR is
+    // read only for a listed pair, whose force terms then carry s = 0 and |ds/dr| below 1e-29, and
+    // is taken as zero
+    const bool zr = r4.x == 0.f;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     for (int m = lane; m < ldg; m += 32) {
       float gg = 0.f, gz = 0.f;
-      if (m < M) {
+      if (m < M && !zr) {
         const float gv = G[row * ldg + m];
         a0 += gTs[m * 4] * gv;
         a1 += gTs[m * 4 + 1] * gv;
