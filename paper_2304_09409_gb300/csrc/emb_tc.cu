@@ -68,6 +68,9 @@ struct DenseArgs {
   void* out_a;   // next A operand (EB-byte elements), or null
   float* e_out;  // FWD_LAST: energy partial per column block [col blocks][e_ld]
   long e_ld;
+  // embedding layers: the slot rows' environment rows; a row whose s is zero (padding) gets no
+  // epilogue, and its outputs are left as they are (null: every row)
+  const float4* zrow;
   int* err;
 };
 
@@ -231,11 +234,15 @@ __global__ void __launch_bounds__(kDThreads)
   const float* bias = g.bias[grp];
   const float* wl = g.wlast[grp];
   float e_acc = 0.f;
+  // a zero environment row (padding) is read by nobody downstream: the contraction and the
+  // descriptor backward stop at or skip zero rows, and the first layer's backward does not read the
+  // rows of a pair whose s is zero
+  const bool rz = rv && g.zrow != nullptr && g.zrow[row].x == 0.f;
   for (int c = half * 16; c < BN; c += 32) {
     float v[16];
     tmem_ld16(tb + c, v);
     const int cg0 = col0 + c;  // a piece is all inside the padded width or all beyond it
-    if (!rv || cg0 >= g.ldo) continue;
+    if (!rv || rz || cg0 >= g.ldo) continue;
     const long o = row * g.ldo + cg0;
     if (MODE == DM_PLAIN) {
       float y[16];
@@ -541,16 +548,19 @@ __global__ void __launch_bounds__(256)
   const long row = brow(pc, p, k, t);
   const int net = pc.type_one_side ? t : tsorted[p] * pc.ntypes + t;
   const float* w = nets.w0[net];
+  double d[3];
+  listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d[0], d[1], d[2]);
+  float r, s, ds, u[3];
+  pair_env<float>(d[0], d[1], d[2], norm2_exact(d[0], d[1], d[2]), pc.rs, pc.rc, pc.near2, r, s, ds, u);
+  // a pair whose s rounded to zero (within ~1e-15 of r_c) had no layer epilogues: its rows are not
+  // read, and its force terms (s = 0, |ds/dr| below 1e-29) are zero
+  if (s == 0.f) return;
   float gs = 0.f;
   for (int c = 0; c < w1; ++c) {
     const float gy = G0[row * ld1 + c], tt = T0[row * ld1 + c];
     gs += gy * (1.f - tt * tt) * __ldg(w + c);
     if (skip) gs += gy;
   }
-  double d[3];
-  listed_disp(coord + 3 * i, coord + 3 * j, nl_code[(long)i * pc.nc + k], pc, frame_of(pc, i), d[0], d[1], d[2]);
-  float r, s, ds, u[3];
-  pair_env<float>(d[0], d[1], d[2], norm2_exact(d[0], d[1], d[2]), pc.rs, pc.rc, pc.near2, r, s, ds, u);
   const float4 g4 = gR[row];
   const float gvu = g4.y * u[0] + g4.z * u[1] + g4.w * u[2];
   const float a = ds * (gs + g4.x + gvu), b = s / r;
@@ -736,6 +746,7 @@ int run_tc_impl(const DeviceModel& m, const PathConst& pc0, const PathIO& io, Ar
     return DP_E_UNSUPPORTED;
   }
   eg.err = &io.status->timeout;
+  eg.zrow = Renv;
   DenseArgs fg;
   std::memset(&fg, 0, sizeof(fg));
   {
