@@ -397,6 +397,7 @@ __global__ void k_env_l0(PathConst pc, const double* __restrict__ coord, const i
     o[3] = s * u[2];
   }
   Renv[row] = make_float4(o[0], o[1], o[2], o[3]);
+  if (o[0] == 0.f) return;  // a zero row: its layer outputs are read by nobody (see k_dense_tc)
   const int net = pc.type_one_side ? t : tsorted[p] * pc.ntypes + t;
   const float* w = nets.w0[net];
   const float* b = nets.b0[net];
@@ -500,14 +501,14 @@ __global__ void k_descr_bwd_b(PathConst pc, const float4* __restrict__ Tm, const
     const int t = block_of_slot(pc, k);
     const long row = brow(pc, p, k, t);
     const float4 r4 = Renv[row];
-    // a zero row (padding, or s rounded to zero within ~1e-15 of r_c): dE/dG is zero; its dE/dR is
-    // read only for a listed pair, whose force terms then carry s = 0 and |ds/dr| below 1e-29, and
-    // is taken as zero
-    const bool zr = r4.x == 0.f;
+    // a zero row (padding, or s rounded to zero within ~1e-15 of r_c) is read by nobody downstream:
+    // the embedding layers' backward epilogues skip it and the first layer's backward does not read
+    // the rows of a pair whose s is zero
+    if (r4.x == 0.f) continue;  // warp-uniform
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     for (int m = lane; m < ldg; m += 32) {
       float gg = 0.f, gz = 0.f;
-      if (m < M && !zr) {
+      if (m < M) {
         const float gv = G[row * ldg + m];
         a0 += gTs[m * 4] * gv;
         a1 += gTs[m * 4 + 1] * gv;
