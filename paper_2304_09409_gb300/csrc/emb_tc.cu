@@ -137,7 +137,7 @@ __device__ __forceinline__ float tanh_op(float x) {
 // One dense layer (or its backward) on a 128-row tile: C = A . B^T on the tensor cores, then the
 // epilogue of MODE.  A: [rows][K] (EB-byte elements), B^T: [N][K] per group.
 template <int EB, int MODE>
-__global__ void __launch_bounds__(kDThreads)
+__global__ void __launch_bounds__(kDThreads, 3)  // three CTAs per SM: the epilogues are latency-bound
     k_dense_tc(const __grid_constant__ DenseMaps mp, const DenseArgs g) {
   __shared__ float s_e[2][DBM];
   extern __shared__ unsigned char smem_raw[];
@@ -161,6 +161,11 @@ __global__ void __launch_bounds__(kDThreads)
   const int col0 = blockIdx.y * BN;
   uint32_t ncols = 32;
   while ((int)ncols < BN) ncols <<= 1;
+  if (g.zrow != nullptr) {  // a tile of zero environment rows only (padding) has nothing to compute
+    const long r = row0 + threadIdx.x;
+    const bool live = threadIdx.x < DBM && r < row_end && g.zrow[r].x != 0.f;
+    if (!__syncthreads_or(live)) return;  // block-uniform
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -251,7 +256,10 @@ __global__ void __launch_bounds__(kDThreads)
       st16f(g.out_y + o, y);
     } else if (MODE == DM_FWD || MODE == DM_FWD_LAST) {
       float xs[16];
-      if (g.skip == 1) ld16f(g.skip_in + row * g.ld_skip + cg0, xs);  // n_out = n_in: the same padded width
+      // n_out = n_in: the same padded width; {x, x} with n_in a multiple of 16: the piece's inputs are
+      // 16 consecutive values too
+      const bool xv = g.skip == 1 || (g.skip == 2 && (g.n_in_skip & 15) == 0);
+      if (xv) ld16f(g.skip_in + row * g.ld_skip + (g.skip == 1 ? cg0 : cg0 % g.n_in_skip), xs);
       float y[16], t[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -260,8 +268,8 @@ __global__ void __launch_bounds__(kDThreads)
         if (cg < g.N) {
           tt = tanh_op(v[i] + __ldg(bias + cg));
           yy = tt;
-          if (g.skip == 1) yy += xs[i];
-          if (g.skip == 2) yy += __ldg(g.skip_in + row * g.ld_skip + cg % g.n_in_skip);
+          if (xv) yy += xs[i];
+          else if (g.skip == 2) yy += __ldg(g.skip_in + row * g.ld_skip + cg % g.n_in_skip);
         }
         y[i] = yy;
         t[i] = tt;
@@ -284,6 +292,13 @@ __global__ void __launch_bounds__(kDThreads)
     } else {  // DM_BWD
       float xs[16], tb16[16];
       if (g.skip == 1 || g.skip == 2) ld16f(g.skip_in + row * g.ld_skip + cg0, xs);  // gy[c]: the wider width
+      const bool x2v = g.skip == 2 && (g.N & 15) == 0;  // gy[c + N] as 16 consecutive values too
+      if (x2v) {
+        float x2[16];
+        ld16f(g.skip_in + row * g.ld_skip + cg0 + g.N, x2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) xs[i] += x2[i];
+      }
       if (g.tbelow) ld16f(g.tbelow + row * g.ld_tb + cg0, tb16);
       float gyv[16], gzv[16];
 #pragma unroll
@@ -293,7 +308,7 @@ __global__ void __launch_bounds__(kDThreads)
         if (cg < g.N) {
           gy = v[i];
           if (g.skip == 1) gy += xs[i];
-          if (g.skip == 2) gy += xs[i] + __ldg(g.skip_in + row * g.ld_skip + cg + g.N);
+          if (g.skip == 2) gy += xs[i] + (x2v ? 0.f : __ldg(g.skip_in + row * g.ld_skip + cg + g.N));
           if (g.skip == 3) gy += __ldg(wl + cg);
           gz = g.tbelow ? gy * (1.f - tb16[i] * tb16[i]) : gy;
         }
