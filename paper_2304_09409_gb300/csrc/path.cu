@@ -1019,9 +1019,9 @@ cudaError_t launch_e3(const PartDesc& P, const PathConst& pc, const R* params, c
 // reverse, dE/ds_k = (1/Nc) sum_m gD_m (G_m(s_k) + s_k G_m'(s_k)) into the radial component of gR
 // (the other three zero).  The nets have a scalar input, as the se_e3 nets do, and run on the same
 // evaluators (dG/ds carried forward alongside), all of the part's nets in shared memory: nothing of
-// G is stored.  Persistent blocks of eight warps, a warp per atom, its lanes over the atom's real
+// G is stored.  Persistent blocks of four warps, a warp per atom, its lanes over the atom's real
 // neighbours, compacted first.
-constexpr int kRWarps = 8;
+constexpr int kRWarps = 4;  // four warps: the evaluator's registers leave room for three blocks per SM
 
 template <class R, class Ev, int BWD>
 __global__ void __launch_bounds__(kRWarps * 32)
