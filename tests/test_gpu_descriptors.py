@@ -240,3 +240,31 @@ def test_param_grad_refuses():
         dpgb.param_grad(m, [fr.natoms], fr.coord, fr.atype, fr.box[None], np.ones(1), np.zeros((fr.natoms, 3)))
     assert ei.value.code == dpgb.DP_E_UNSUPPORTED
     m.free()
+
+
+# ---- one neighbour type: every pair of the se_e3 part has one net both ways ---------------------
+
+def _single_type(descriptor, embed):
+    return I.ModelConfig(ntypes=1, rcut=5.0, rcut_smth=0.5, sel=(64,), embed=embed, axis=0, fit=(16, 16),
+                         descriptor=descriptor)
+
+
+@pytest.mark.parametrize("descriptor,embed", [(3, (2, 4, 8)), (3, (3, 6, 12)), (1, (10, 20, 40)), (1, (5, 10, 20))])
+def test_single_type_fcc_vs_oracle(descriptor, embed):
+    """A 108-atom FCC box with ~44 neighbours per atom in one type block: the se_e3 kernels take
+    every pair once with weight 2 (rows of 32 partners and more, and shorter ones), and the se_e2_r
+    kernel its nets on the same neighbours; fixed-shape and general evaluators, FP64 against the
+    oracle and FP32 within 1e-4 of the force scale."""
+    cfg = _single_type(descriptor, embed)
+    fr = I.fcc_frame((3, 3, 3), seed=11)
+    p = I.make_params(cfg, 3)
+    ref = oracle.compute(cfg, p, fr.coord, fr.atype, fr.box)
+    m = _dp().Model(cfg, p, precision="fp64")
+    _assert_fp64(m.compute(fr.coord, fr.atype, fr.box, atom_energy=True), ref, fr.natoms)
+    m.free()
+    m = _dp().Model(cfg, p, precision="fp32")
+    e, f, v, _ = m.compute(fr.coord, fr.atype, fr.box)
+    fs = np.abs(ref.force).max()
+    assert np.abs(f - ref.force).max() <= 1e-4 * fs
+    assert abs(float(e[0]) - ref.energy) <= 1e-5 * max(abs(ref.energy), 1.0)
+    m.free()
