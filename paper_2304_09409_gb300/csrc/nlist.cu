@@ -545,7 +545,8 @@ __global__ void __launch_bounds__(kNlWarps * 32)
 // comparison against the outer FP32 bound per candidate; the accepted entries keep the FP32 r^2
 // and the stream position.  Everything else happens on the few accepted entries of one type:
 // the exact FP64 membership test of entries inside the FP32 error of r_c, the ranking under the
-// exact total order, and the image codes, all from shared memory.  Membership, ranking and
+// exact total order (a bucket sort of the FP32 keys; exact keys only for entries with another key
+// inside their tie window), and the image codes, all from shared memory.  Membership, ranking and
 // outputs are those of k_nlist.
 // =============================================================================================
 constexpr int kCellWarps = 8;

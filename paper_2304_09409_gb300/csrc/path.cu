@@ -285,7 +285,7 @@ __global__ void k_rtab_bwd(PathConst pc, const R* __restrict__ tab, TabConst tc,
 //   backward  dE/dtheta_jk = (1/Nc^2) sum_m gD_m (G_m + theta G'_m),
 //             dE/dR_j += dE/dtheta_jk R_k,  dE/dR_k += dE/dtheta_jk R_j
 // Nothing of G is stored: the backward pass evaluates the nets again.  All of the part's nets sit
-// in shared memory; a warp takes rows j, its lanes the partners k.
+// in shared memory; a warp takes rows j, its lanes the partners k (below).
 struct E3Net {
   int nl;
   int in[DP_MAX_LAYERS], out[DP_MAX_LAYERS], skip[DP_MAX_LAYERS];
