@@ -21,6 +21,20 @@ __device__ __forceinline__ long row_index(const RowMap& m, int r) {
   return (long)(m.p0 + r / m.nk) * m.nc + m.k0 + r % m.nk;
 }
 
+// A row whose environment row has s = 0 (padding slot), when the map carries environment rows.
+template <class R>
+__device__ __forceinline__ bool zero_row(const RowMap& m, long row) {
+  return m.zrow != nullptr && reinterpret_cast<const R*>(m.zrow)[row * 4] == R(0);
+}
+// True for every thread when the block's BM rows from r0 are all zero rows (a tile of padding).
+template <class R>
+__device__ __forceinline__ bool zero_tile(const RowMap& m, int r0) {
+  if (m.zrow == nullptr) return false;
+  const int r = r0 + (int)threadIdx.x;
+  const bool live = threadIdx.x < BM && r < m.nrows && !zero_row<R>(m, row_index(m, r));
+  return !__syncthreads_or(live);
+}
+
 __device__ __forceinline__ double act_tanh(double z) { return tanh(z); }
 __device__ __forceinline__ float act_tanh(float z) { return tanhf(z); }
 
@@ -33,6 +47,7 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
+  if (zero_tile<R>(rm, r0)) return;  // block-uniform
   R acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -72,6 +87,7 @@ __global__ void __launch_bounds__(256)
     const int r = r0 + ty * 4 + p;
     if (r >= rm.nrows) continue;
     const long row = row_index(rm, r);
+    if (zero_row<R>(rm, row)) continue;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = c0 + tx * 4 + q;
@@ -96,6 +112,7 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;  // columns are input features
+  if (zero_tile<R>(rm, r0)) return;  // block-uniform
   R acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -142,6 +159,7 @@ __global__ void __launch_bounds__(256)
     const int r = r0 + ty * 4 + p;
     if (r >= rm.nrows) continue;
     const long row = row_index(rm, r);
+    if (zero_row<R>(rm, row)) continue;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = c0 + tx * 4 + q;

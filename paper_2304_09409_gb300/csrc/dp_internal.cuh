@@ -275,6 +275,9 @@ struct RowMap {
   long r0;
   int p0, nk, k0, nc;
   int nrows;
+  // slot rows: the environment rows ([rows][4], the layer's element type) -- a row whose s is zero
+  // (padding) is left unwritten, and a tile of such rows only is skipped; null: every row
+  const void* zrow = nullptr;
 };
 
 template <class R>

@@ -66,6 +66,9 @@ __global__ void k_emb_first(PathConst pc, NetPtrs<R> nets, const int* __restrict
   const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
   const int net = net_of(pc, atom_type_sorted[p], slot_block(pc, k));
   const R s = Renv[row * 4];
+  // a zero row (padding; or, in FP32, s rounded to zero within ~1e-15 of r_c) is read by nobody:
+  // the layers above skip it, and so do the contraction, its reverse and the force kernel
+  if (s == R(0)) return;
   const R t = tanh_r(s * nets.w0[net][o] + nets.b0[net][o]);
   R y = t;
   if (skip) y += s;  // n_in = 1: both +x and +{x,x} add the scalar input
@@ -75,10 +78,11 @@ __global__ void k_emb_first(PathConst pc, NetPtrs<R> nets, const int* __restrict
 
 template <class R>
 __global__ void k_emb_first_bwd(PathConst pc, NetPtrs<R> nets, const int* __restrict__ atom_type_sorted,
-                                const R* __restrict__ GY, const R* __restrict__ T, int w1, int skip,
-                                R* __restrict__ gs) {
+                                const R* __restrict__ Renv, const R* __restrict__ GY, const R* __restrict__ T,
+                                int w1, int skip, R* __restrict__ gs) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= (long)pc.natoms * pc.nc) return;
+  if (Renv[row * 4] == R(0)) return;  // a zero row: no layer outputs, not read by the force kernel
   const int p = (int)(row / pc.nc), k = (int)(row % pc.nc);
   const int net = net_of(pc, atom_type_sorted[p], slot_block(pc, k));
   const R* w = nets.w0[net];
@@ -92,19 +96,43 @@ __global__ void k_emb_first_bwd(PathConst pc, NetPtrs<R> nets, const int* __rest
   gs[row] = acc;
 }
 
+// End of each type block's leading nonzero environment rows of atom row rb (one warp): a block's
+// listed pairs come nearest first and s falls with r, so its zero rows (padding, pairs beyond this
+// part's cutoff, s rounded to zero just inside it) close the block.
+template <class R>
+__device__ __forceinline__ void block_ends(const PathConst& pc, const R* __restrict__ Renv, long rb, int* ends) {
+  const int lane = threadIdx.x & 31;
+  for (int t = 0; t < pc.ntypes; ++t) {
+    int end = pc.sel_off[t + 1];
+    for (int k0 = pc.sel_off[t]; k0 < pc.sel_off[t + 1]; k0 += 32) {
+      const int k = k0 + lane;
+      const unsigned zm = __ballot_sync(0xffffffffu, k < pc.sel_off[t + 1] && Renv[(rb + k) * 4] == R(0));
+      if (zm) {
+        end = k0 + __ffs(zm) - 1;
+        break;
+      }
+    }
+    if (lane == 0) ends[t] = end;
+  }
+}
+
 // ---- T = G^T R / Nc and D = T T_<^T, one block per atom -------------------------------------
 template <class R>
 __global__ void k_contract(PathConst pc, const R* __restrict__ G, const R* __restrict__ Renv, R* __restrict__ Tm,
                            R* __restrict__ D) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   R* Ts = reinterpret_cast<R*>(sm_raw);  // [M][4]
+  __shared__ int s_end[DP_MAX_TYPES];
   const int p = blockIdx.x;
   const int M = pc.M, A = pc.A, nc = pc.nc;
   const R inv_nc = R(1) / R(nc);
+  const long rb = (long)p * nc;
+  if (threadIdx.x < 32) block_ends<R>(pc, Renv, rb, s_end);  // zero rows add exact zeros; their G is not computed
+  __syncthreads();
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
     R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    const long rb = (long)p * nc;
-    for (int k = 0; k < nc; ++k) {
+    for (int t = 0; t < pc.ntypes; ++t)
+    for (int k = pc.sel_off[t]; k < s_end[t]; ++k) {
       const R g = G[(rb + k) * M + m];
       const typename Vec4<R>::T r4 = reinterpret_cast<const typename Vec4<R>::T*>(Renv)[rb + k];
       a0 += g * r4.x;
@@ -158,6 +186,7 @@ __global__ void k_descr_bwd(PathConst pc, const R* __restrict__ Tm, const R* __r
   for (int k = warp; k < nc; k += nw) {
     const long row = (long)p * nc + k;
     const typename Vec4<R>::T r4 = reinterpret_cast<const typename Vec4<R>::T*>(Renv)[row];
+    if (r4.x == R(0)) continue;  // warp-uniform: a zero row is read by nobody downstream
     R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int m = lane; m < M; m += 32) {
       const R g = G[row * M + m];
@@ -183,12 +212,16 @@ __global__ void k_descr_bwd(PathConst pc, const R* __restrict__ Tm, const R* __r
 // G rows hold M values; D_r goes to the part's block of D (row stride Dw).
 template <class R>
 __global__ void k_contract_r(PathConst pc, const R* __restrict__ G, const R* __restrict__ Renv, R* __restrict__ D) {
+  __shared__ int s_end[DP_MAX_TYPES];
   const int p = blockIdx.x;
   const int M = pc.M, nc = pc.nc;
   const long rb = (long)p * nc;
+  if (threadIdx.x < 32) block_ends<R>(pc, Renv, rb, s_end);  // zero rows add exact zeros; their G is not computed
+  __syncthreads();
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
     R acc = 0;
-    for (int k = 0; k < nc; ++k) acc += G[(rb + k) * M + m] * Renv[(rb + k) * 4];
+    for (int t = 0; t < pc.ntypes; ++t)
+      for (int k = pc.sel_off[t]; k < s_end[t]; ++k) acc += G[(rb + k) * M + m] * Renv[(rb + k) * 4];
     D[(long)p * pc.Dw + pc.doff + m] = acc / R(nc);
   }
 }
@@ -210,6 +243,7 @@ __global__ void k_descr_bwd_r(PathConst pc, const R* __restrict__ gD, const R* _
   for (int k = warp; k < nc; k += nw) {
     const long row = (long)p * nc + k;
     const R s = Renv[row * 4];
+    if (s == R(0)) continue;  // warp-uniform: a zero row is read by nobody downstream
     R acc = 0;
     for (int m = lane; m < M; m += 32) {
       acc += gDs[m] * G[row * M + m];
@@ -783,6 +817,9 @@ __global__ void __launch_bounds__(256)
     if (j >= 0 && r2 < pc.rc2) {
       R r, s, ds, u[3];
       pair_env<R>(d[0], d[1], d[2], r2, pc.rs, pc.rc, pc.near2, r, s, ds, u);
+      // s rounded to zero (FP32, within ~1e-15 of r_c): its rows were not written, and its force
+      // terms (s = 0, |ds/dr| below 1e-29) are zero
+      if (s == R(0)) return;
       const typename Vec4<R>::T g4 = reinterpret_cast<const typename Vec4<R>::T*>(gR)[row];
       const R gvu = g4.y * u[0] + g4.z * u[1] + g4.w * u[2];
       const R gsum = (gs_emb ? gs_emb[row] : R(0)) + g4.x + gvu;
@@ -1256,6 +1293,7 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
         const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
         RowMap rm{1, 0, io.type_start[ti], pq.sel[tj], pq.sel_off[tj], P.nc,
                   (io.type_start[ti + 1] - io.type_start[ti]) * pq.sel[tj]};
+        rm.zrow = b.Renv;  // padding rows: no layer outputs
         for (int l = 1; l < P.nl; ++l) {
           const LayerDesc& L = P.emb[(size_t)net * P.nl + l];
           const R* W = params + L.w_off;
@@ -1311,6 +1349,7 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
             const int net = pc.type_one_side ? tj : ti * pc.ntypes + tj;
             RowMap rm{1, 0, io.type_start[ti], pq.sel[tj], pq.sel_off[tj], P.nc,
                       (io.type_start[ti + 1] - io.type_start[ti]) * pq.sel[tj]};
+            rm.zrow = b.Renv;
             const LayerDesc& L = P.emb[(size_t)net * P.nl + l];
             ProfScope _ps(io.prof, "emb_bwd", st);
             DP_CUDA_TRY(launch_dense_bwd<R>(rm, gy, b.T[l], L.n_in, params + L.w_off, L.n_out, L.skip, gx, st));
@@ -1319,7 +1358,8 @@ int run_generic(const DeviceModel& m, const PathConst& pc, const R* params, cons
       }
       const LayerDesc& L0 = P.emb[0];
       ProfScope _ps(io.prof, "emb_first_bwd", st);
-      k_emb_first_bwd<R><<<nblk(rows, 256), 256, 0, st>>>(pq, b.nets, tsorted, gy, b.T[0], L0.n_out, L0.skip, b.gs);
+      k_emb_first_bwd<R><<<nblk(rows, 256), 256, 0, st>>>(pq, b.nets, tsorted, b.Renv, gy, b.T[0], L0.n_out, L0.skip,
+                                                         b.gs);
     }
     ProfScope _ps(io.prof, "force", st);
     k_force<R><<<nblk(rows, 256), 256, 0, st>>>(pq, io.coord, io.perm, io.nl_j, io.nl_code, b.gs, b.gR, io.force,
