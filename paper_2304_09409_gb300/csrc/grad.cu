@@ -213,21 +213,34 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---- weight and bias gradients: gW += X^T GZ + Xd^T GZd, gb += sum_rows GZ ----------------------
-// One block owns a 32 x 32 tile of gW and a slab of rows; partial sums go to gW with atomics.
-constexpr int WT = 32, WR = 32;
+// One block owns a TI x TI tile of gW and a slab of rows; partial sums go to gW with atomics.  Each
+// thread keeps PT x PT outputs; FP32 takes 4 x 4 with 16-byte shared loads (two loads per eight
+// FMAs), FP64 2 x 2 (its pipe, not the loads, is the limit there).
+template <class R>
+struct WGrad;
+template <>
+struct WGrad<float> {
+  static constexpr int TI = 64, PT = 4, RR = 32, LD = TI + 4;  // rows 16-byte aligned
+};
+template <>
+struct WGrad<double> {
+  static constexpr int TI = 32, PT = 2, RR = 32, LD = TI + 1;
+};
+
 template <class R>
 __global__ void __launch_bounds__(256)
     k_wgrad(RowMap rm, const R* __restrict__ X, const R* __restrict__ Xd, int n_in, const R* __restrict__ GZ,
             const R* __restrict__ GZd, int n_out, int rows_per_block, R* __restrict__ gW, R* __restrict__ gb) {
-  __shared__ R xs[WR][WT + 1], xds[WR][WT + 1], gs[WR][WT + 1], gds[WR][WT + 1];
+  constexpr int TI = WGrad<R>::TI, PT = WGrad<R>::PT, RR = WGrad<R>::RR, LD = WGrad<R>::LD;
+  __shared__ __align__(16) R xs[RR][LD], xds[RR][LD], gs[RR][LD], gds[RR][LD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int i0 = blockIdx.x * WT, o0 = blockIdx.y * WT;
+  const int i0 = blockIdx.x * TI, o0 = blockIdx.y * TI;
   const int rbeg = blockIdx.z * rows_per_block;
   const int rend = min(rm.nrows, rbeg + rows_per_block);
-  R acc[2][2] = {}, bacc[2] = {};
-  for (int r0 = rbeg; r0 < rend; r0 += WR) {
-    for (int e = tid; e < WR * WT; e += 256) {
-      const int r = e / WT, c = e % WT;
+  R acc[PT][PT] = {}, bacc[PT] = {};
+  for (int r0 = rbeg; r0 < rend; r0 += RR) {
+    for (int e = tid; e < RR * TI; e += 256) {
+      const int r = e / TI, c = e % TI;
       const bool rv = r0 + r < rend;
       const long row = rv ? rowi(rm, r0 + r) : 0;
       xs[r][c] = (rv && i0 + c < n_in) ? X[row * n_in + i0 + c] : R(0);
@@ -237,30 +250,47 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
 #pragma unroll 4
-    for (int r = 0; r < WR; ++r) {
+    for (int r = 0; r < RR; ++r) {
+      R xa[PT], xda[PT], ga[PT], gda[PT];
+      if constexpr (PT == 4) {
+        const float4 x4 = *reinterpret_cast<const float4*>(&xs[r][ty * 4]);
+        const float4 xd4 = *reinterpret_cast<const float4*>(&xds[r][ty * 4]);
+        const float4 g4 = *reinterpret_cast<const float4*>(&gs[r][tx * 4]);
+        const float4 gd4 = *reinterpret_cast<const float4*>(&gds[r][tx * 4]);
+        xa[0] = x4.x; xa[1] = x4.y; xa[2] = x4.z; xa[3] = x4.w;
+        xda[0] = xd4.x; xda[1] = xd4.y; xda[2] = xd4.z; xda[3] = xd4.w;
+        ga[0] = g4.x; ga[1] = g4.y; ga[2] = g4.z; ga[3] = g4.w;
+        gda[0] = gd4.x; gda[1] = gd4.y; gda[2] = gd4.z; gda[3] = gd4.w;
+      } else {
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-          acc[a][b] += xs[r][ty * 2 + a] * gs[r][tx * 2 + b] + xds[r][ty * 2 + a] * gds[r][tx * 2 + b];
-      if (blockIdx.x == 0 && ty == 0) {
-        bacc[0] += gs[r][tx * 2];
-        bacc[1] += gs[r][tx * 2 + 1];
+        for (int a = 0; a < PT; ++a) {
+          xa[a] = xs[r][ty * PT + a];
+          xda[a] = xds[r][ty * PT + a];
+          ga[a] = gs[r][tx * PT + a];
+          gda[a] = gds[r][tx * PT + a];
+        }
       }
+#pragma unroll
+      for (int a = 0; a < PT; ++a)
+#pragma unroll
+        for (int b = 0; b < PT; ++b) acc[a][b] += xa[a] * ga[b] + xda[a] * gda[b];
+      if (blockIdx.x == 0 && ty == 0)
+#pragma unroll
+        for (int b = 0; b < PT; ++b) bacc[b] += ga[b];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < PT; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int i = i0 + ty * 2 + a, o = o0 + tx * 2 + b;
+    for (int b = 0; b < PT; ++b) {
+      const int i = i0 + ty * PT + a, o = o0 + tx * PT + b;
       if (i < n_in && o < n_out) atomicAdd(gW + (long)i * n_out + o, acc[a][b]);
     }
   if (blockIdx.x == 0 && ty == 0 && gb)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int o = o0 + tx * 2 + b;
+    for (int b = 0; b < PT; ++b) {
+      const int o = o0 + tx * PT + b;
       if (o < n_out) atomicAdd(gb + o, bacc[b]);
     }
 }
@@ -435,8 +465,12 @@ template <class R>
 void launch_wgrad(const RowMap& rm, const R* X, const R* Xd, int n_in, const R* GZ, const R* GZd, int n_out, R* gW,
                   R* gb, cudaStream_t st) {
   if (rm.nrows <= 0) return;
-  const int rpb = 4096;
-  dim3 grid(nb(n_in, WT), nb(n_out, WT), nb(rm.nrows, rpb));
+  constexpr int TI = WGrad<R>::TI;
+  const long tiles = (long)nb(n_in, TI) * nb(n_out, TI);
+  // row slabs of 4096, fewer rows when that leaves under two blocks per SM (small layers)
+  int rpb = 4096;
+  while (rpb > 512 && tiles * nb(rm.nrows, rpb) < 2L * 152) rpb /= 2;
+  dim3 grid(nb(n_in, TI), nb(n_out, TI), nb(rm.nrows, rpb));
   k_wgrad<R><<<grid, 256, 0, st>>>(rm, X, Xd, n_in, GZ, GZd, n_out, rpb, gW, gb);
 }
 
