@@ -42,8 +42,10 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_dense_fwd(RowMap rm, const R* __restrict__ X, int n_in, const R* __restrict__ W, const R* __restrict__ b,
                 int n_out, int skip, int tanh_act, R* __restrict__ Y, R* __restrict__ Tact) {
-  __shared__ R As[BK][BM + 1];
-  __shared__ R Bs[BK][BN];
+  // FP32: the transposed A tile's rows padded to 68 values, so that a thread's four rows (and
+  // its four B columns) load as one 16-byte vector each
+  __shared__ __align__(16) R As[BK][BM + (sizeof(R) == 4 ? 4 : 1)];
+  __shared__ __align__(16) R Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
@@ -70,10 +72,17 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       R a[4], bb[4];
+      if constexpr (sizeof(R) == 4) {
+        const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
+        bb[0] = bv.x; bb[1] = bv.y; bb[2] = bv.z; bb[3] = bv.w;
+      } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty * 4 + q];
-        bb[q] = Bs[kk][tx * 4 + q];
+        for (int q = 0; q < 4; ++q) {
+          a[q] = As[kk][ty * 4 + q];
+          bb[q] = Bs[kk][tx * 4 + q];
+        }
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
@@ -107,8 +116,10 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_dense_bwd(RowMap rm, const R* __restrict__ GY, const R* __restrict__ Tact, int n_in,
                 const R* __restrict__ W, int n_out, int skip, R* __restrict__ GX) {
-  __shared__ R As[BK][BM + 1];
-  __shared__ R Bs[BK][BN];
+  // FP32: the transposed A tile's rows padded to 68 values, so that a thread's four rows (and
+  // its four B columns) load as one 16-byte vector each
+  __shared__ __align__(16) R As[BK][BM + (sizeof(R) == 4 ? 4 : 1)];
+  __shared__ __align__(16) R Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;  // columns are input features
@@ -142,10 +153,17 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       R a[4], bb[4];
+      if constexpr (sizeof(R) == 4) {
+        const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
+        bb[0] = bv.x; bb[1] = bv.y; bb[2] = bv.z; bb[3] = bv.w;
+      } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty * 4 + q];
-        bb[q] = Bs[kk][tx * 4 + q];
+        for (int q = 0; q < 4; ++q) {
+          a[q] = As[kk][ty * 4 + q];
+          bb[q] = Bs[kk][tx * 4 + q];
+        }
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)

@@ -108,8 +108,10 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_dense_tan(RowMap rm, const R* __restrict__ Xd, int n_in, const R* __restrict__ W, int n_out, int skip,
                 int tanh_act, const R* __restrict__ T, R* __restrict__ Yd, R* __restrict__ Zd) {
-  __shared__ R As[BK][BM + 1];
-  __shared__ R Bs[BK][BN];
+  // FP32: the transposed A tile's rows padded to 68 values, so that a thread's four rows (and
+  // its four B columns) load as one 16-byte vector each
+  __shared__ __align__(16) R As[BK][BM + (sizeof(R) == 4 ? 4 : 1)];
+  __shared__ __align__(16) R Bs[BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
   R acc[4][4] = {};
@@ -124,11 +126,25 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk)
+    for (int kk = 0; kk < BK; ++kk) {
+      R av[4], bv[4];
+      if constexpr (sizeof(R) == 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+        bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          av[q] = As[kk][ty * 4 + q];
+          bv[q] = Bs[kk][tx * 4 + q];
+        }
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += As[kk][ty * 4 + a] * Bs[kk][tx * 4 + b];
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -172,8 +188,10 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_dense_bx(RowMap rm, const R* __restrict__ GZ, const R* __restrict__ GY, int n_in, const R* __restrict__ W,
                int n_out, int skip, R* __restrict__ GX) {
-  __shared__ R As[BK][BM + 1];
-  __shared__ R Bs[BK][BN];
+  // FP32: the transposed A tile's rows padded to 68 values, so that a thread's four rows (and
+  // its four B columns) load as one 16-byte vector each
+  __shared__ __align__(16) R As[BK][BM + (sizeof(R) == 4 ? 4 : 1)];
+  __shared__ __align__(16) R Bs[BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
   R acc[4][4] = {};
@@ -188,11 +206,25 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk)
+    for (int kk = 0; kk < BK; ++kk) {
+      R av[4], bv[4];
+      if constexpr (sizeof(R) == 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+        bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          av[q] = As[kk][ty * 4 + q];
+          bv[q] = Bs[kk][tx * 4 + q];
+        }
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += As[kk][ty * 4 + a] * Bs[kk][tx * 4 + b];
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
     __syncthreads();
   }
 #pragma unroll
