@@ -33,15 +33,22 @@ TABLE_STRIDE2 = 0.1
 TABLE_N2 = 2
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one oracle source file into the shared library `out` with g++ (no fused
+    multiply-add contraction, OpenMP over atoms)."""
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           src, "-o", out]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no fused multiply-add contraction, OpenMP over atoms)."""
+    """Compile the oracle (dp_oracle.cpp) into oracle/_build, unless the library is newer than it."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-           _SRC, "-o", tmp]
-    subprocess.run(cmd, check=True)
+    compile_source(_SRC, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -73,7 +80,9 @@ _lib = None
 def _L():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        # DP_ORACLE_LIB names a library compiled from a modified copy of dp_oracle.cpp: the
+        # pin-strength test plants one mistake per copy and runs the pins against each
+        _lib = ctypes.CDLL(os.environ.get("DP_ORACLE_LIB") or build())
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         cp = ctypes.POINTER(_Cfg)
