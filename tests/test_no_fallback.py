@@ -60,3 +60,11 @@ def test_no_gpu_raises():
     cfg = I.water_model()
     with pytest.raises(dpgb.DPError):
         dpgb.Model(cfg, I.make_params(cfg, 0), precision="fp64")
+
+
+def test_oracle_includes_nothing_of_the_cuda_path():
+    """The oracle and the CUDA path share no code: the oracle's source includes system headers only."""
+    src = open(os.path.join(ROOT, "oracle", "dp_oracle.cpp")).read()
+    for line in src.splitlines():
+        if line.strip().startswith("#include"):
+            assert "<" in line and '"' not in line, line
