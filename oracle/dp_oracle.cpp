@@ -1,5 +1,6 @@
 // Plain FP64 CPU oracle for the Deep Potential energy / force / virial path (descriptors
-// se_e2_a, se_e2_r and their hybrid).
+// se_e2_a, se_e2_r, se_e3 and the hybrids of se_e2_a with either), and the derivative of the
+// training loss along a parameter direction.
 //
 // TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
 // cpu_baseline leg (and its --impl reference arm) load this library.  The product path
@@ -13,12 +14,14 @@
 //   Eq. (G2)         G_j = N_{e,2}^{a_i,a_j}(s(r_ij))                      Sec. II.A.1
 //   se_e2_a          D = (1/Nc^2) G^T R R^T G_<                            Sec. II.A.1
 //   se_e2_r          D = (1/Nc) G^T s  (R reduced to its radial column)    Sec. II.A.1
+//   se_e3            D = (1/Nc^2) sum_jk theta_jk G(theta_jk), theta = R_j . R_k   Sec. II.A.1
 //   hybrid           D = the two descriptors concatenated                  Sec. II.A.1
 //   Eq. (fitting)    E_i = F_0^{a_i}(D^i)                                  Sec. II.A.2
 //   force / virial   F = -dE/dr,  Xi = -sum_g dE/dh_{g a} h_{g b}           Sec. II.A.2
 //   Eq. (NN)         layer y = phi(x w + b) (+ x | + {x,x})                Sec. II.A.6
 //   Eq. (compress)   quintic tabulation of the embedding net               Sec. II.A.6
 //   neighbour order  by (type, distance, index)                            Sec. III.B.1
+//   Eq. (loss)       pE dE^2/N + pF |dF|^2/(3N) + pXi |dXi|^2/(9N)         Sec. II.B
 //
 // Readings of the paper used here (where it is silent or ambiguous):
 //   * Nc in 1/Nc^2 is the padded sum of sel; padded rows of R are zero.
@@ -32,8 +35,12 @@
 //   * se_e2_r keeps s(r) as the weight of each row (the radial column of R), so a neighbour's
 //     term vanishes smoothly at r_c and padded rows contribute nothing; its 1/Nc is that of the
 //     contraction G^T R with one column.
-//   * The hybrid descriptor's parts share one neighbour list (r_c, r_s, sel) and the net index
-//     rule (type_one_side), each with its own embedding nets; the se_e2_a block comes first.
+//   * se_e3: theta_jk over all four columns of R, j = k included; nets indexed a_j * ntypes + a_k
+//     (ntypes^2 nets whatever type_one_side says).
+//   * A hybrid descriptor's parts each have their own r_c, r_s, sel and embedding nets and share the
+//     net index rule (type_one_side); they read one neighbour list built with the larger cutoff and,
+//     per type, the larger sel, of which each part takes the entries inside its own r_c and sel;
+//     the se_e2_a block comes first.
 //
 // Forces come from a hand-written reverse pass in plain loops.  A second, independent
 // mechanism -- forward-mode dual numbers through a templated energy -- exists only to
