@@ -1,17 +1,23 @@
 /*
- * dpgb.h -- C ABI of the GB300 (sm_103a) Deep Potential se_e2_a engine.
+ * dpgb.h -- C ABI of the GB300 (sm_103a) Deep Potential engine.
  *
  * The library evaluates the energy E, forces F and virial Xi of a smooth-edition
- * two-body-embedding Deep Potential (DeePMD-kit v2, arXiv 2304.09409):
+ * Deep Potential (DeePMD-kit v2, arXiv 2304.09409):
  *
  *   neighbour list n(i) with a fixed per-type sel       (Sec. II.A.1 "Handling the
  *                                                        systems composed of multiple
  *                                                        chemical species"; Sec. III.B.1)
  *   environment matrix R with the switch s(r)           (Eqs. (rij), (switch))
  *   embedding G = N_{e,2}^{a_i,a_j}(s)  or its quintic  (Eqs. (G2), (NN), (compress))
- *   descriptor D = (1/Nc^2) G^T R R^T G_<               (Sec. II.A.1, se_e2_a)
+ *   descriptor D = (1/Nc^2) G^T R R^T G_<               (Sec. II.A.1, se_e2_a; also se_e2_r,
+ *                                                        se_e3 and the hybrids of se_e2_a with
+ *                                                        either, see dp_model_config)
  *   E_i = F_0^{a_i}(D^i),  E = sum_i E_i                (Eq. (fitting_energy))
  *   F = -dE/dr,  Xi_ab = -sum_g dE/dh_ga h_gb            (Sec. II.A.2)
+ *
+ * and, for training and active learning, the parameter gradient of the loss of Eq. (loss)
+ * (dp_param_grad, Sec. II.B) and the model deviation of an ensemble (dp_model_deviation,
+ * Sec. II.C).
  *
  * Conventions shared by every entry point
  *   - Every call returns a status code (DP_OK = 0); nothing aborts.  On error,
