@@ -698,12 +698,14 @@ def run_ours(args):
             line["descriptors"] = run_descriptors(local, flush)
         except Exception as exc:
             line["descriptors"] = {"error": repr(exc)}
-    if not args.no_training:
+    # the side legs below build their models on the default device: under torchrun (N > 1) they would
+    # all land on GPU 0 with tensors of other GPUs, so they run in the single-GPU run only
+    if not args.no_training and rank == 0 and world == 1:
         try:
             line["training"] = run_training()
         except Exception as exc:
             line["training"] = {"error": repr(exc)}
-    if not args.no_serving:
+    if not args.no_serving and rank == 0 and world == 1:
         try:
             srv = run_serving(precision=sel["prec"], compressed=sel["compressed"])
             line["serving"] = srv
